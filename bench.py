@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark: 720p scale-hyperprior encode + decode frames/s on B300.
+
+One step = encode then decode of a batch of 8 synthetic 1280x720 frames
+(replicate-padded to 1280x768 inside the codec), N=128, M=192, FP32 chain,
+inputs resident in HBM, timed with CUDA events on the codec's stream, with
+an L2 flush (a 512 MB write) before every step outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica (frames are independent, the
+path has no exchange step); rank 0 prints one JSON line.  --impl reference
+times the FP64 CPU oracle on a bounded crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "720p hyperprior enc+dec frames/s (FP32 plain vs BF16/FP8/student) at PSNR; p99 ms"
+N_CH, M_CH = 128, 192
+PAD_H, PAD_W = 768, 1280
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--height", type=int, default=720)
+    ap.add_argument("--width", type=int, default=1280)
+    ap.add_argument("--conv", default="auto", choices=["auto", "simt"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample(side_h, side_w, seed_frame=0):
+    """FP64 oracle hyperprior encode + decode of one crop of a synthetic 720p
+    frame; returns (seconds, pixels of the padded crop)."""
+    import numpy as np
+    import oracle as O
+    from paper_2208_01641_b300 import synth
+    W = synth.make_weights(1, N_CH, M_CH)
+    oc = O.Codec(1, N_CH, M_CH, W)
+    x = synth.make_frames(1, 720, 1280, first=seed_frame)[:, :, 200:200 + side_h, 300:300 + side_w]
+    x = np.ascontiguousarray(x)
+    t0 = time.perf_counter()
+    bs, _ = O.encode(oc, x)
+    O.decode(oc, bs)
+    return time.perf_counter() - t0, side_h * side_w
+
+
+def cpu_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def reference_arm(args, ws, rank):
+    """The oracle, as it stands, on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    nsteps = args.steps + args.warmup
+    side = 384 if nsteps <= 5 else (256 if nsteps <= 12 else 128)
+    for _ in range(args.warmup):
+        oracle_sample(side, side)
+    times = []
+    for _ in range(args.steps):
+        t, px = oracle_sample(side, side)
+        times.append(t)
+    frac = (side * side) / (PAD_H * PAD_W)
+    total = sum(times)
+    fps = frac * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "hyperprior N=128 M=192, 8 x 1280x720 frames padded to 1280x768, enc+dec",
+                   "global_batch": args.batch, "parallelism": "replicas"},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cpu_threads(), "kind": "oracle",
+                         "sample": f"FP64 oracle enc+dec of one {side}x{side} crop per step, scaled by "
+                                   f"pixels to a 1280x768 padded frame"},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+    import paper_2208_01641_b300 as lic
+    from paper_2208_01641_b300 import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    B, H, W = args.batch, args.height, args.width
+    impl = lic.CONV_SIMT if args.conv == "simt" else lic.CONV_AUTO
+    Wt = synth.make_weights(lic.HYPERPRIOR, N_CH, M_CH)
+    codec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, conv_impl=impl)
+    frames_np = synth.make_frames(B, H, W, first=8 * rank)
+    frames = torch.from_numpy(frames_np).cuda()
+    out = torch.empty_like(frames)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    sid = stream.cuda_stream
+
+    def step():
+        bs = codec.encode(frames, stream=sid)
+        codec.decode(bs, H, W, out, stream=sid)
+        return bs
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step()
+        codec.sync(sid)
+
+    # ---- timed region: device time of K steps, L2 flushed before each ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = codec.launch_count()
+    sampler = ClockSampler(local)
+    with sampler, torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            bs = codec.encode(frames, stream=sid)
+            ev[k][1].record(stream)
+            codec.decode(bs, H, W, out, stream=sid)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+    status = codec.sync_status(sid)
+    if dist:
+        dist.barrier()
+    launches = codec.launch_count() - launches0
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    enc_ms = [a.elapsed_time(b) for a, b, c in ev]
+    dec_ms = [b.elapsed_time(c) for a, b, c in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * B * args.steps / (total_ms / 1000.0)
+    frame_bytes = bs.sizes()
+
+    # ---- roofline of the dominant kernel: per-launch CUDA events, live ----
+    with torch.cuda.stream(stream):
+        codec.profile(True)
+        for _ in range(3):
+            flush.zero_()
+            step()
+        codec.sync(sid)
+        rep = codec.profile_report()
+        codec.profile(False)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    roof = roofline(rep, peaks)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hin = torch.from_numpy(frames_np).pin_memory()
+        hout = torch.empty(hin.shape, dtype=torch.float32).pin_memory()
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                bs2 = codec.encode(hin, stream=sid)
+                codec.decode(bs2, H, W, hout, stream=sid)
+            codec.sync(sid)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                bs2 = codec.encode(hin, stream=sid)
+                codec.decode(bs2, H, W, hout, stream=sid)
+            codec.sync(sid)
+            dt = time.perf_counter() - t0
+        nbytes = B * 3 * H * W * 4
+        e2e = {"value": ws * B * args.steps / dt, "unit": "frames/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+
+    # ---- reconstruction vs the FP64 oracle on sampled windows ----
+    psnr = None
+    if rank == 0 and not args.no_cpu_baseline:
+        psnr = psnr_vs_oracle(codec, Wt, B)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t, px = oracle_sample(384, 384)
+        frac = px / (PAD_H * PAD_W)
+        cpu = {"value": frac / t, "unit": "frames/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": "FP64 oracle hyperprior enc+dec of one 384x384 crop of a synthetic 720p frame, "
+                         "scaled by pixels to one 1280x768 padded frame"}
+
+    if rank == 0:
+        srt = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "hyperprior N=128 M=192, 8 x 1280x720 frames padded to 1280x768, enc+dec",
+                       "global_batch": B * ws, "seq_len": None, "parallelism": f"replicas{ws}",
+                       "conv": args.conv, "l2": "512 MB write before every step, outside the timed events"},
+            "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+            "enc_fps": B * args.steps / (sum(enc_ms) / 1000), "dec_fps": B * args.steps / (sum(dec_ms) / 1000),
+            "bits_per_pixel": 8.0 * statistics.mean(frame_bytes) / (H * W),
+            "psnr_vs_oracle_db": psnr if psnr is None or psnr < 1e9 else "inf", "decode_status": status,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": sampler.summary(), "kernels": rep,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def roofline(rep, peaks):
+    """Dominant launch name by total time; achieved = algorithmic work per
+    launch / mean launch time; peak from MEASURED_PEAKS.json."""
+    if not rep:
+        return None
+    top = max(rep, key=lambda r: r["ms"])
+    per_ms = top["ms"] / top["launches"]
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    bf16 = peaks.get("bf16_tflops", 1800.0)
+    sm_mhz = peaks.get("sm_max_mhz", 2032.0)
+    name = top["name"]
+    if name.endswith(":tc"):
+        # TF32 tensor peak = measured BF16 dense x nominal TF32/BF16 ratio (1.1/2.25)
+        peak = bf16 * 1.1 / 2.25
+        ach = top["flop"] / top["launches"] / (per_ms * 1e-3) / 1e12
+        bound, unit = "tensor", "TFLOP/s"
+        note = "3xTF32 on tcgen05: algorithmic FP32 flops over the TF32 peak (measured BF16 x 1.1/2.25)"
+    elif top["flop"] > 0:
+        # FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock
+        peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        ach = top["flop"] / top["launches"] / (per_ms * 1e-3) / 1e12
+        bound, unit = "alu", "TFLOP/s"
+        note = "CUDA-core FP32 FMA peak: 148 SMs x 128 lanes x 2 x max SM clock"
+    else:
+        peak = hbm
+        ach = top["bytes"] / top["launches"] / (per_ms * 1e-3) / 1e9
+        bound, unit = "hbm", "GB/s"
+        note = "measured HBM copy bandwidth"
+    return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+            "traffic": None, "launch_ms": per_ms, "launches_per_step": top["launches"] / 3, "note": note}
+
+
+def psnr_vs_oracle(codec, Wt, B):
+    """Decoder output vs the oracle's g_s on two 12x12-latent windows of the
+    decoded symbols of the last batch (64x64 interior pixels each)."""
+    import numpy as np
+    import oracle as O
+    import paper_2208_01641_b300 as lic
+    sy = np.zeros((B, M_CH, PAD_H // 16, PAD_W // 16), np.int32)
+    xpre = np.zeros((B, 3, PAD_H, PAD_W), np.float32)
+    codec.read_tensor(lic.T_SY, sy)
+    codec.read_tensor(lic.T_XPRE, xpre)
+    se, n = 0.0, 0
+    for (b, iy, ix) in [(0, 20, 30), (B - 1, 30, 60)]:
+        win = sy[b:b + 1, :, iy:iy + 12, ix:ix + 12].astype(np.float32)
+        rx = np.clip(O.g_s(Wt, win)[0][:, 64:128, 64:128], 0, 1)
+        gx = np.clip(xpre[b, :, 16 * iy + 64:16 * iy + 128, 16 * ix + 64:16 * ix + 128], 0, 1)
+        se += float(((gx - rx) ** 2).sum())
+        n += gx.size
+    mse = se / n
+    return 1e10 if mse == 0 else float(10 * np.log10(1.0 / mse))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * lic.h -- C ABI of the B300 learned-image-codec library (liblic.so).
+ *
+ * The library runs the encode/decode chain of the two learned image codecs
+ * that arXiv 2208.01641 pipelines -- the factorized prior (Ballé et al. 2017,
+ * the paper's [1]) and the scale hyperprior (Ballé et al. 2018, [2]) -- on one
+ * GPU (Sec. III-A, III-B and Fig. 1 of the paper):
+ *
+ *   encoder:  x -> g_a -> y -> Q -> rANS            (factorized, Sec. III-A)
+ *             y -> h_a -> z -> Q -> rANS,  z_hat -> h_s -> scales -> index
+ *                                                   (hyperprior, Sec. III-B)
+ *   decoder:  rANS^-1 -> Q^-1 -> g_s -> x_hat       (hyperprior: z first, then
+ *             h_s -> scales -> index, then y: the 4-stage order of Sec. III-B)
+ *
+ * Every step runs in the library's own CUDA kernels for sm_103a; there is no
+ * CPU fallback.  The paper's CPU-thread pipeline, zero-copy and pooling are
+ * replaced by an all-device chain (see the design notes).
+ *
+ * Conventions
+ *  - Return value: LIC_OK (0) or a negative LIC_E_* code.  No exception or
+ *    abort crosses this boundary.
+ *  - Streams: `stream` is a cudaStream_t passed as void*.  Calls are
+ *    stream-ordered and return once the work is enqueued, except where a
+ *    host buffer must be filled (stated per call).
+ *  - Errors found by kernels (corrupt bitstream, bounded waits that ran out)
+ *    are latched in a per-codec device status word; lic_sync() waits for the
+ *    stream and returns (and clears) the latched status.
+ *  - Frames are float32, NCHW (B x 3 x H x W), values in [0, 1].  A frame
+ *    pointer may be device memory or host memory (pinned or pageable); the
+ *    library detects which and stages host memory through its own device
+ *    buffers.
+ *  - Stage tensors exchanged by the diagnostic calls are NCHW as well.
+ *  - Thread safety: one codec must not be used by two host threads at once.
+ */
+#ifndef LIC_H
+#define LIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LIC_OK 0
+#define LIC_E_INVALID_ARG (-1)
+#define LIC_E_UNSUPPORTED (-2)
+#define LIC_E_OOM (-3)
+#define LIC_E_CORRUPT_STREAM (-4)
+#define LIC_E_TIMEOUT (-5)
+#define LIC_E_CUDA (-6)
+
+typedef enum { LIC_FACTORIZED = 0, LIC_HYPERPRIOR = 1 } lic_kind;
+typedef enum { LIC_FP32 = 0 } lic_precision;
+
+/* Convolution implementation: LIC_CONV_AUTO picks the tcgen05 tensor-core
+ * kernels where they exist and the CUDA-core (SIMT) kernels elsewhere;
+ * LIC_CONV_SIMT forces the CUDA-core kernels everywhere. */
+typedef enum { LIC_CONV_AUTO = 0, LIC_CONV_SIMT = 1 } lic_conv_impl;
+
+/* One named host float32 parameter tensor.  Names and shapes:
+ *   g_a.conv{0..3}.{weight [Cout,Cin,5,5], bias [Cout]}     3->N->N->N->M
+ *   g_a.gdn{0..2}.{beta [N], gamma [N,N]}
+ *   g_s.deconv{0..3}.{weight [Cin,Cout,5,5], bias [Cout]}   M->N->N->N->3
+ *   g_s.igdn{0..2}.{beta [N], gamma [N,N]}
+ *   hyperprior only:
+ *   h_a.conv0 [N,M,3,3], h_a.conv1 [N,N,5,5], h_a.conv2 [N,N,5,5] (+ .bias)
+ *   h_s.deconv0 [N,N,5,5], h_s.deconv1 [N,N,5,5] (transposed-conv layout),
+ *   h_s.conv2 [M,N,3,3] (+ .bias)
+ *   entropy bottleneck over C channels (C = M factorized, N hyperprior):
+ *   eb.H0 [C,3,1] eb.H1..H3 [C,3,3] eb.H4 [C,1,3], eb.b0..b3 [C,3],
+ *   eb.b4 [C,1], eb.a0..a3 [C,3]   (Ballé 2018 appendix 6.1)            */
+typedef struct {
+    const char *name;
+    const float *data;   /* host memory; copied by lic_codec_create */
+    int64_t numel;
+} lic_param;
+
+typedef struct {
+    const lic_param *params;
+    int count;
+} lic_weights;
+
+typedef struct {
+    int precision;   /* lic_precision; LIC_FP32 */
+    int band_rows;   /* latent rows per y substream; 0 -> 16 */
+    int conv_impl;   /* lic_conv_impl */
+    int reserved[5];
+} lic_options;
+
+typedef struct lic_codec lic_codec;
+
+/* A batch of frame bitstreams laid out back to back.  Frame i occupies
+ * bytes [offsets[i], offsets[i] + sizes[i]) of `data`.  Each frame is one
+ * self-describing container (magic "LIC1", see the design notes):
+ *   'LIC1' u16 version=1, u16 kind, u16 N, u16 M, u32 H, u32 W, u32 Hp,
+ *   u32 Wp, u16 R, u16 0, u32 nsub, u32 off[nsub+1] (16-bit word offsets),
+ *   u16 payload[off[nsub]]                               (little endian)  */
+typedef struct {
+    int count;                 /* frames */
+    int on_device;             /* 1: data and d_offsets are device pointers */
+    const uint8_t *data;       /* containers back to back */
+    const int64_t *offsets;    /* host, count+1 byte offsets (sizes are
+                                  offsets[i+1]-offsets[i] minus alignment
+                                  padding: use sizes[]) */
+    const int64_t *sizes;      /* host, count sizes in bytes */
+    const int64_t *d_offsets;  /* device copy of offsets (on_device only) */
+    const int64_t *d_sizes;    /* device copy of sizes (on_device only) */
+} lic_bitstreams;
+
+/* ---------------------------------------------------------------------- */
+/* Codec lifetime                                                          */
+/* ---------------------------------------------------------------------- */
+
+/* Create a codec of `kind` with N transform channels and M latent channels
+ * on the current CUDA device.  The weights are validated (every name above
+ * present with the right numel), copied, re-laid-out for the kernels, and
+ * the entropy-model CDF tables are built once on the host in FP64 (the
+ * factorized entropy bottleneck of [2] app. 6.1 and the 64-scale Gaussian
+ * conditional of [2]) and uploaded.  opts may be NULL (defaults).
+ * Errors: INVALID_ARG (bad kind/N/M/weights), UNSUPPORTED (table support
+ * above 4096 symbols, N or M not a multiple of 32, N > 256), OOM, CUDA. */
+int lic_codec_create(int kind, int N, int M, const lic_weights *weights,
+                     const lic_options *opts, lic_codec **out);
+
+/* Free every device and host resource of the codec (synchronizes the
+ * device first).  NULL is accepted. */
+void lic_codec_destroy(lic_codec *codec);
+
+/* Wait for `stream`, then return and clear the status latched by kernels
+ * since the previous lic_sync: LIC_OK, LIC_E_CORRUPT_STREAM or
+ * LIC_E_TIMEOUT (or LIC_E_CUDA if the stream itself failed). */
+int lic_sync(lic_codec *codec, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Encode / decode                                                         */
+/* ---------------------------------------------------------------------- */
+
+/* Encode B frames (B x 3 x H x W float32, device or host memory).  The
+ * frames are replicate-padded on the bottom/right to multiples of 64
+ * internally.  On return *out describes library-owned buffers: data,
+ * d_offsets and d_sizes on the device (valid in stream order), offsets and
+ * sizes on the host (pinned; valid once the stream has synchronized).  They
+ * stay valid until the next lic_encode/lic_encode_latents on this codec or
+ * lic_codec_destroy.  Errors: INVALID_ARG (B < 1, H or W < 1, null
+ * pointers), OOM, CUDA. */
+int lic_encode(lic_codec *codec, const float *frames, int B, int H, int W,
+               lic_bitstreams *out, void *stream);
+
+/* Decode in->count frames of size H x W into `frames` (count x 3 x H x W
+ * float32, device or host memory; a host destination makes the call wait
+ * for the stream).  in may live on the device (on_device = 1, e.g. the
+ * output of lic_encode) or on the host.  Headers are validated on the
+ * device against (kind, N, M, H, W); a mismatch or a corrupt substream is
+ * latched as LIC_E_CORRUPT_STREAM (read it with lic_sync) and the frames of
+ * a corrupt stream are left unspecified.  The entropy decoder bounds every
+ * read; a corrupt stream never faults the device. */
+int lic_decode(lic_codec *codec, const lic_bitstreams *in, int H, int W,
+               float *frames, void *stream);
+
+/* Copy a device-resident batch (in->on_device = 1, e.g. from lic_encode)
+ * to host memory after waiting for `stream`: bytes [0, offsets[count]) of
+ * in->data, so frame i starts at dst + offsets[i] and is sizes[i] bytes.
+ * dst_cap is the capacity of dst.  Returns the bytes copied (>= 0) or
+ * INVALID_ARG (capacity too small, not a device batch) / CUDA. */
+int64_t lic_bitstreams_download(const lic_bitstreams *in, uint8_t *dst, int64_t dst_cap,
+                                void *stream);
+
+/* Parse the header of one host-resident frame container: original size
+ * and kind.  Returns INVALID_ARG / CORRUPT_STREAM on a bad header. */
+int lic_decoded_shape(const uint8_t *frame, int64_t size, int *kind, int *H, int *W);
+
+/* ---------------------------------------------------------------------- */
+/* Stage-level calls (tests, diagnostics, custom pipelines)                */
+/* All tensors NCHW; device or host memory unless stated.                  */
+/* ---------------------------------------------------------------------- */
+
+/* Intermediate tensors of the most recent lic_encode / lic_decode. */
+typedef enum {
+    LIC_T_Y = 0,      /* float32 B x M x Hp/16 x Wp/16, encoder latent y    */
+    LIC_T_SY = 1,     /* int32, quantized y symbols (encoder or decoder)    */
+    LIC_T_Z = 2,      /* float32 B x N x Hp/64 x Wp/64, hyper latent z      */
+    LIC_T_SZ = 3,     /* int32, quantized z symbols                         */
+    LIC_T_SIGMA = 4,  /* float32 B x M x Hp/16 x Wp/16, h_s scales          */
+    LIC_T_IDX = 5,    /* uint8, scale-table index                           */
+    LIC_T_XPRE = 6    /* float32 B x 3 x Hp x Wp, decoder output before
+                         clamp and crop                                     */
+} lic_tensor;
+
+/* Copy intermediate `which` of the last call into dst (NCHW); `count`
+ * receives the element count (dst may be NULL to query it).  Errors:
+ * INVALID_ARG if the tensor does not exist for this codec/last call. */
+int lic_read_tensor(lic_codec *codec, int which, void *dst, int64_t *count,
+                    void *stream);
+
+/* y = g_a(pad(frames)): B x M x Hp/16 x Wp/16 float32. */
+int lic_analysis(lic_codec *codec, const float *frames, int B, int H, int W,
+                 float *y, void *stream);
+/* x = g_s(y_hat), unclamped: B x 3 x 16Hy x 16Wy float32. */
+int lic_synthesis(lic_codec *codec, const float *yhat, int B, int Hy, int Wy,
+                  float *x, void *stream);
+/* z = h_a(y) (hyperprior): B x N x Hy/4 x Wy/4. */
+int lic_hyper_analysis(lic_codec *codec, const float *y, int B, int Hy, int Wy,
+                       float *z, void *stream);
+/* sigma = h_s(z_hat) and idx = scale index of sigma (hyperprior):
+ * B x M x 4Hz x 4Wz float32 and uint8 (idx may be NULL). */
+int lic_hyper_synthesis(lic_codec *codec, const float *zhat, int B, int Hz, int Wz,
+                        float *sigma, uint8_t *idx, void *stream);
+
+/* Entropy-code given integer symbols (device int32/uint8, NCHW) into frame
+ * containers, exactly as lic_encode does after quantization: s_y is
+ * B x M x Hy x Wy; idx (hyperprior) the same shape; s_z (hyperprior)
+ * B x N x Hy/4 x Wy/4.  H, W are the original frame size recorded in the
+ * headers (Hp = 16 Hy, Wp = 16 Wy).  Output as for lic_encode. */
+int lic_encode_latents(lic_codec *codec, const int32_t *s_y, const uint8_t *idx,
+                       const int32_t *s_z, int B, int H, int W, int Hy, int Wy,
+                       lic_bitstreams *out, void *stream);
+
+/* Entropy-decode the symbols of in->count frames of size H x W (device
+ * int32 outputs; s_z ignored for the factorized codec).  The hyperprior
+ * path runs h_s on the decoded z to obtain the indices of y, as the
+ * decoder must. */
+int lic_decode_latents(lic_codec *codec, const lic_bitstreams *in, int H, int W,
+                       int32_t *s_y, int32_t *s_z, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Host-only: entropy-model tables (no GPU needed)                         */
+/* ---------------------------------------------------------------------- */
+
+/* Build the quantized 16-bit CDF tables exactly as lic_codec_create does.
+ * Factorized entropy bottleneck over C channels from the eb.* parameters
+ * (pass weights with the eb.* entries; C from eb.H0's numel / 3), then, if
+ * gauss != 0, the 64 Gaussian tables.  Table t has support [-lo[t], hi[t]]
+ * plus an escape symbol; its cdf occupies cdf[start[t] .. start[t]+n[t]]
+ * (n[t]+1 entries, n[t] = lo[t]+hi[t]+2).  medians[c] is the float32 median
+ * of channel c.  Capacities: tables <= max_tables, cdf entries <= cdf_cap.
+ * Returns the number of tables written (>= 0) or a negative LIC_E_*. */
+int lic_build_tables(const lic_weights *weights, int gauss, int max_tables,
+                     int64_t cdf_cap, float *medians, int32_t *lo, int32_t *hi,
+                     int64_t *start, uint32_t *cdf);
+
+/* The 64 scales of the Gaussian conditional (0.11 .. 256, log-spaced). */
+void lic_scale_table(float T[64]);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* enable = 1: start recording a CUDA event pair around every kernel launch
+ * the codec issues (on the stream it is given), discarding earlier records;
+ * enable = 0: stop recording.  Recording adds a small gap between launches;
+ * time the chain without it. */
+int lic_profile_enable(lic_codec *codec, int enable);
+
+/* Write the records as JSON into buf: a list of {"name", "launches", "ms",
+ * "flop", "bytes"} aggregated by launch name, where flop and bytes are the
+ * algorithmic work of those launches (2 x multiply-adds of the definition;
+ * bytes of the inputs read once, outputs written once and weights).  Waits
+ * for the recorded events.  Returns the string length (excluding the
+ * terminator; buf may be NULL to query it) or a negative code. */
+int lic_profile_report(lic_codec *codec, char *buf, int cap);
+
+/* Kernel launches issued by this codec since it was created. */
+int64_t lic_launch_count(lic_codec *codec);
+
+/* Human-readable message for an error code. */
+const char *lic_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIC_H */

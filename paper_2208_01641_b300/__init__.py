@@ -1,0 +1,329 @@
+"""Python binding of liblic (include/lic.h): argument marshalling only.
+
+Every step of the codec chain runs in the library's CUDA kernels; this
+module only converts torch tensors / numpy arrays into pointers and calls the
+C ABI by the same names.  PyTorch is used for device memory and streams.
+If liblic.so is missing the import of the binding fails loudly: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblic.so")
+
+FACTORIZED = 0
+HYPERPRIOR = 1
+CONV_AUTO = 0
+CONV_SIMT = 1
+
+T_Y, T_SY, T_Z, T_SZ, T_SIGMA, T_IDX, T_XPRE = range(7)
+
+OK = 0
+E_INVALID_ARG, E_UNSUPPORTED, E_OOM, E_CORRUPT_STREAM, E_TIMEOUT, E_CUDA = -1, -2, -3, -4, -5, -6
+
+EXPORTED = [
+    "lic_codec_create", "lic_codec_destroy", "lic_sync", "lic_encode", "lic_decode",
+    "lic_bitstreams_download", "lic_decoded_shape", "lic_read_tensor", "lic_analysis",
+    "lic_synthesis", "lic_hyper_analysis", "lic_hyper_synthesis", "lic_encode_latents",
+    "lic_decode_latents", "lic_build_tables", "lic_scale_table", "lic_strerror",
+    "lic_profile_enable", "lic_profile_report", "lic_launch_count",
+]
+
+
+class LicError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_lib().lic_strerror(code).decode()} ({code})")
+
+
+class _Param(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("data", ctypes.POINTER(ctypes.c_float)),
+                ("numel", ctypes.c_int64)]
+
+
+class _Weights(ctypes.Structure):
+    _fields_ = [("params", ctypes.POINTER(_Param)), ("count", ctypes.c_int)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("band_rows", ctypes.c_int),
+                ("conv_impl", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class _Bitstreams(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("on_device", ctypes.c_int),
+                ("data", ctypes.c_void_p), ("offsets", ctypes.POINTER(ctypes.c_int64)),
+                ("sizes", ctypes.POINTER(ctypes.c_int64)), ("d_offsets", ctypes.c_void_p),
+                ("d_sizes", ctypes.c_void_p)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is not built; run python paper_2208_01641_b300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        L.lic_codec_create.argtypes = [i, i, i, ctypes.POINTER(_Weights), ctypes.POINTER(_Options),
+                                       ctypes.POINTER(vp)]
+        L.lic_codec_destroy.argtypes = [vp]
+        L.lic_codec_destroy.restype = None
+        L.lic_sync.argtypes = [vp, vp]
+        L.lic_encode.argtypes = [vp, vp, i, i, i, ctypes.POINTER(_Bitstreams), vp]
+        L.lic_decode.argtypes = [vp, ctypes.POINTER(_Bitstreams), i, i, vp, vp]
+        L.lic_bitstreams_download.argtypes = [ctypes.POINTER(_Bitstreams), vp, i64, vp]
+        L.lic_bitstreams_download.restype = i64
+        L.lic_decoded_shape.argtypes = [vp, i64, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.lic_read_tensor.argtypes = [vp, i, vp, ctypes.POINTER(i64), vp]
+        L.lic_analysis.argtypes = [vp, vp, i, i, i, vp, vp]
+        L.lic_synthesis.argtypes = [vp, vp, i, i, i, vp, vp]
+        L.lic_hyper_analysis.argtypes = [vp, vp, i, i, i, vp, vp]
+        L.lic_hyper_synthesis.argtypes = [vp, vp, i, i, i, vp, vp, vp]
+        L.lic_encode_latents.argtypes = [vp, vp, vp, vp, i, i, i, i, i, ctypes.POINTER(_Bitstreams), vp]
+        L.lic_decode_latents.argtypes = [vp, ctypes.POINTER(_Bitstreams), i, i, vp, vp, vp]
+        L.lic_build_tables.argtypes = [ctypes.POINTER(_Weights), i, i, i64, vp, vp, vp, vp, vp]
+        L.lic_scale_table.argtypes = [vp]
+        L.lic_scale_table.restype = None
+        L.lic_profile_enable.argtypes = [vp, i]
+        L.lic_profile_report.argtypes = [vp, ctypes.c_char_p, i]
+        L.lic_launch_count.argtypes = [vp]
+        L.lic_launch_count.restype = i64
+        L.lic_strerror.argtypes = [i]
+        L.lic_strerror.restype = ctypes.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def lib():
+    """The loaded liblic.so (ctypes handle)."""
+    return _lib()
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise LicError(rc, what)
+    return rc
+
+
+def _ptr(t) -> int:
+    """Data pointer of a torch tensor or numpy array (no copies)."""
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _weights_struct(weights: Dict[str, np.ndarray]):
+    keep = []
+    arr = (_Param * len(weights))()
+    for k, (name, a) in enumerate(weights.items()):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        nb = name.encode()
+        keep += [a, nb]
+        arr[k].name = nb
+        arr[k].data = a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        arr[k].numel = a.size
+    w = _Weights(arr, len(weights))
+    return w, (keep, arr)
+
+
+def build_tables(weights: Dict[str, np.ndarray], gauss: bool):
+    """Host-only table build (lic_build_tables): (medians, lo, hi, start, cdf)."""
+    w, keep = _weights_struct(weights)
+    C = weights["eb.H0"].shape[0]
+    cap_t, cap_c = C + 64, (C + 64) * 4097
+    med = np.zeros(C, np.float32)
+    lo = np.zeros(cap_t, np.int32)
+    hi = np.zeros(cap_t, np.int32)
+    start = np.zeros(cap_t, np.int64)
+    cdf = np.zeros(cap_c, np.uint32)
+    n = _check(_lib().lic_build_tables(ctypes.byref(w), 1 if gauss else 0, cap_t, cap_c, _ptr(med), _ptr(lo),
+                                       _ptr(hi), _ptr(start), _ptr(cdf)), "lic_build_tables")
+    return med, lo[:n], hi[:n], start[:n], cdf
+
+
+def scale_table():
+    T = np.zeros(64, np.float32)
+    _lib().lic_scale_table(_ptr(T))
+    return T
+
+
+class Bitstreams:
+    """A batch of frame containers returned by encode (library-owned buffers,
+    valid until the codec's next encode)."""
+
+    def __init__(self, codec: "Codec", s: _Bitstreams, stream):
+        self.codec, self.s, self.stream = codec, s, stream
+
+    @property
+    def count(self):
+        return self.s.count
+
+    def sizes(self):
+        """Frame sizes in bytes (synchronizes the stream)."""
+        self.codec.sync(self.stream)
+        return [int(self.s.sizes[i]) for i in range(self.s.count)]
+
+    def to_bytes(self):
+        """Per-frame bytes objects (synchronizes the stream)."""
+        self.codec.sync(self.stream)
+        total = int(self.s.offsets[self.s.count])
+        buf = np.zeros(max(total, 1), np.uint8)
+        _check(_lib().lic_bitstreams_download(ctypes.byref(self.s), _ptr(buf), buf.size, self.stream),
+               "lic_bitstreams_download")
+        return [buf[self.s.offsets[i]:self.s.offsets[i] + self.s.sizes[i]].tobytes()
+                for i in range(self.s.count)]
+
+
+def host_bitstreams(frames):
+    """A lic_bitstreams view of host bytes objects (for lic_decode)."""
+    sizes = np.array([len(f) for f in frames], np.int64)
+    offs = np.zeros(len(frames) + 1, np.int64)
+    offs[1:] = np.cumsum(sizes)
+    data = np.frombuffer(b"".join(frames) or b"\0", np.uint8).copy()
+    s = _Bitstreams(len(frames), 0, data.ctypes.data, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                    sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), None, None)
+    s._keep = (data, offs, sizes)
+    return s
+
+
+class Codec:
+    """One codec on the current CUDA device (lic_codec_create)."""
+
+    def __init__(self, kind: int, N: int, M: int, weights: Dict[str, np.ndarray], band_rows: int = 16,
+                 conv_impl: int = CONV_AUTO):
+        self.kind, self.N, self.M = kind, N, M
+        w, keep = _weights_struct(weights)
+        opt = _Options(0, band_rows, conv_impl)
+        h = ctypes.c_void_p()
+        _check(_lib().lic_codec_create(kind, N, M, ctypes.byref(w), ctypes.byref(opt), ctypes.byref(h)),
+               "lic_codec_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().lic_codec_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self, stream=None):
+        return _check(_lib().lic_sync(self.h, _stream(stream)), "lic_sync")
+
+    def sync_status(self, stream=None) -> int:
+        """lic_sync's return code without raising."""
+        return _lib().lic_sync(self.h, _stream(stream))
+
+    def profile(self, enable: bool):
+        _check(_lib().lic_profile_enable(self.h, 1 if enable else 0), "lic_profile_enable")
+
+    def profile_report(self):
+        import json
+        n = _check(_lib().lic_profile_report(self.h, None, 0), "lic_profile_report")
+        buf = ctypes.create_string_buffer(n + 1)
+        _check(_lib().lic_profile_report(self.h, buf, n + 1), "lic_profile_report")
+        return json.loads(buf.value.decode())
+
+    def launch_count(self) -> int:
+        return int(_lib().lic_launch_count(self.h))
+
+    def encode(self, frames, stream=None) -> Bitstreams:
+        B, C, H, W = frames.shape
+        assert C == 3
+        st = _stream(stream)
+        s = _Bitstreams()
+        _check(_lib().lic_encode(self.h, _ptr(frames), B, H, W, ctypes.byref(s), st), "lic_encode")
+        return Bitstreams(self, s, st)
+
+    def decode(self, bs, H: int, W: int, out, stream=None):
+        st = _stream(stream)
+        s = bs.s if isinstance(bs, Bitstreams) else bs
+        _check(_lib().lic_decode(self.h, ctypes.byref(s), H, W, _ptr(out), st), "lic_decode")
+        return out
+
+    def decode_status(self, bs, H: int, W: int, out, stream=None) -> int:
+        st = _stream(stream)
+        s = bs.s if isinstance(bs, Bitstreams) else bs
+        return _lib().lic_decode(self.h, ctypes.byref(s), H, W, _ptr(out), st)
+
+    def read_tensor(self, which: int, dst, stream=None):
+        n = ctypes.c_int64()
+        need = self.tensor_count(which)
+        have = dst.size if isinstance(dst, np.ndarray) else dst.numel()
+        if have != need:
+            raise ValueError(f"read_tensor: destination holds {have} elements, tensor has {need}")
+        _check(_lib().lic_read_tensor(self.h, which, _ptr(dst), ctypes.byref(n), _stream(stream)),
+               "lic_read_tensor")
+        return dst
+
+    def tensor_count(self, which: int) -> int:
+        n = ctypes.c_int64()
+        _check(_lib().lic_read_tensor(self.h, which, None, ctypes.byref(n), None), "lic_read_tensor")
+        return n.value
+
+    def analysis(self, frames, y, stream=None):
+        B, _, H, W = frames.shape
+        _check(_lib().lic_analysis(self.h, _ptr(frames), B, H, W, _ptr(y), _stream(stream)), "lic_analysis")
+        return y
+
+    def synthesis(self, yhat, x, stream=None):
+        B, _, Hy, Wy = yhat.shape
+        _check(_lib().lic_synthesis(self.h, _ptr(yhat), B, Hy, Wy, _ptr(x), _stream(stream)), "lic_synthesis")
+        return x
+
+    def hyper_analysis(self, y, z, stream=None):
+        B, _, Hy, Wy = y.shape
+        _check(_lib().lic_hyper_analysis(self.h, _ptr(y), B, Hy, Wy, _ptr(z), _stream(stream)),
+               "lic_hyper_analysis")
+        return z
+
+    def hyper_synthesis(self, zhat, sigma, idx=None, stream=None):
+        B, _, Hz, Wz = zhat.shape
+        _check(_lib().lic_hyper_synthesis(self.h, _ptr(zhat), B, Hz, Wz, _ptr(sigma),
+                                          _ptr(idx) if idx is not None else None, _stream(stream)),
+               "lic_hyper_synthesis")
+        return sigma
+
+    def encode_latents(self, s_y, idx, s_z, H: int, W: int, stream=None) -> Bitstreams:
+        B, _, Hy, Wy = s_y.shape
+        st = _stream(stream)
+        s = _Bitstreams()
+        _check(_lib().lic_encode_latents(self.h, _ptr(s_y), _ptr(idx) if idx is not None else None,
+                                         _ptr(s_z) if s_z is not None else None, B, H, W, Hy, Wy,
+                                         ctypes.byref(s), st), "lic_encode_latents")
+        return Bitstreams(self, s, st)
+
+    def decode_latents(self, bs, H: int, W: int, s_y, s_z=None, stream=None):
+        s = bs.s if isinstance(bs, Bitstreams) else bs
+        _check(_lib().lic_decode_latents(self.h, ctypes.byref(s), H, W, _ptr(s_y),
+                                         _ptr(s_z) if s_z is not None else None, _stream(stream)),
+               "lic_decode_latents")
+
+
+def decoded_shape(frame: bytes):
+    k, h, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    buf = np.frombuffer(frame, np.uint8).copy()
+    _check(_lib().lic_decoded_shape(_ptr(buf), len(frame), ctypes.byref(k), ctypes.byref(h), ctypes.byref(w)),
+           "lic_decoded_shape")
+    return k.value, h.value, w.value

@@ -1,0 +1,1038 @@
+// The C ABI (include/lic.h): codec object, weight re-layout, workspace, and
+// the encode / decode chains of the factorized-prior [1] and
+// scale-hyperprior [2] codecs in the order of the paper's Fig. 1 and
+// Sec. III-A/B, all on one CUDA stream.
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "conv_tc.h"
+#include "lic_internal.h"
+
+namespace lic {
+
+static thread_local char g_last_error[512];
+
+void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+}
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        else p = nullptr;
+        return e;
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+struct HostPinned {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~HostPinned() { if (p) cudaFreeHost(p); }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMallocHost(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+};
+
+// One GEMM launch of a layer: a full convolution, or one sub-pixel phase of
+// a transposed convolution.
+struct ConvOp {
+    DevBuf w;     // [Cout][T][Cin] float32
+    tc::TcWeights tcw;  // tensor-core operand copy (built when the op qualifies)
+    int T = 0;
+    int8_t du[MAX_TAPS] = {}, dv[MAX_TAPS] = {};
+    int py = 0, px = 0;
+};
+
+struct Layer {
+    std::string name;
+    bool deconv = false;
+    int Cin = 0, Cout = 0, k = 0, stride = 1;
+    int in_xform = IN_NONE, epi = EPI_NONE;
+    DevBuf bias;
+    DevBuf w_small;  // transposed conv to <= 4 channels: [Cin][5][5][4]
+    std::vector<std::unique_ptr<ConvOp>> ops;
+};
+
+struct Gdn {
+    std::string name;
+    int C = 0;
+    bool inverse = false;
+    DevBuf gamma;  // [C][1][C]
+    DevBuf beta;
+    tc::TcWeights tcw;
+};
+
+}  // namespace
+}  // namespace lic
+
+struct lic_codec {
+    int kind = 0, N = 0, M = 0;
+    lic_options opt{};
+    int device = 0;
+    // transforms
+    lic::Layer ga[4], gs[4], ha[3], hs[3];
+    lic::Gdn gdn[3], igdn[3];
+    // entropy models
+    lic::HostTables ht;
+    lic::DevBuf cdf, start, lo, hi, med;
+    lic::DevTables dt{};
+    lic::DevBuf status;
+    // workspace
+    lic::DevBuf xin, act0, act1, y, s_y, h1, h2, z, s_z, zhat, g1, g2, sigma, idx, yhat, xpre;
+    lic::DevBuf scratch, counts, sub_off, frame_bytes, offs, data, stage_in, stage_out, in_data, in_offs;
+    lic::HostPinned h_offs;
+    // measurement
+    struct ProfRec {
+        std::string name;
+        cudaEvent_t a, b;
+        double flop, bytes;
+        int launches;
+    };
+    bool prof_on = false;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    int64_t launches = 0;
+    ~lic_codec() {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    }
+    // last call (for lic_read_tensor)
+    int last_B = 0, last_Hp = 0, last_Wp = 0;
+    bool have_y = false, have_sy = false, have_z = false, have_sz = false, have_sigma = false, have_idx = false,
+         have_xpre = false;
+};
+
+namespace lic {
+namespace {
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaEvent_t next_event(lic_codec *cd) {
+    if (cd->ev_used == cd->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cd->ev_pool.push_back(e);
+    }
+    return cd->ev_pool[cd->ev_used++];
+}
+
+// Every kernel launch goes through here: counts it and, when profiling is
+// on, brackets it with CUDA events on its stream.
+template <typename F>
+void timed(lic_codec *cd, const std::string &name, double flop, double bytes, int nlaunch, cudaStream_t st, F &&f) {
+    cd->launches += nlaunch;
+    if (!cd->prof_on) {
+        f();
+        return;
+    }
+    cudaEvent_t a = next_event(cd), b = next_event(cd);
+    cudaEventRecord(a, st);
+    f();
+    cudaEventRecord(b, st);
+    cd->prof.push_back({name, a, b, flop, bytes, nlaunch});
+}
+
+using ParamMap = std::map<std::string, std::pair<const float *, int64_t>>;
+
+int get_param(const ParamMap &pm, const std::string &name, int64_t numel, const float **out) {
+    auto it = pm.find(name);
+    if (it == pm.end() || it->second.first == nullptr || it->second.second != numel) {
+        snprintf(g_last_error, sizeof(g_last_error), "parameter %s missing or of wrong size (want %lld)",
+                 name.c_str(), (long long)numel);
+        return LIC_E_INVALID_ARG;
+    }
+    *out = it->second.first;
+    return LIC_OK;
+}
+
+int upload(DevBuf &b, const void *src, size_t bytes) {
+    LIC_CUDA_TRY(b.ensure(bytes));
+    LIC_CUDA_TRY(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice));
+    return LIC_OK;
+}
+
+// conv weight [Cout][Cin][k][k] -> [Cout][k*k][Cin]; taps (u - k/2, v - k/2)
+int make_conv(Layer &L, const ParamMap &pm, const std::string &name, int Cin, int Cout, int k, int stride,
+              int in_xform, int epi) {
+    L.name = name;
+    L.deconv = false;
+    L.Cin = Cin;
+    L.Cout = Cout;
+    L.k = k;
+    L.stride = stride;
+    L.in_xform = in_xform;
+    L.epi = epi;
+    const float *w, *b;
+    int rc = get_param(pm, name + ".weight", (int64_t)Cout * Cin * k * k, &w);
+    if (rc) return rc;
+    rc = get_param(pm, name + ".bias", Cout, &b);
+    if (rc) return rc;
+    auto op = std::make_unique<ConvOp>();
+    op->T = k * k;
+    std::vector<float> r((size_t)Cout * k * k * Cin);
+    for (int o = 0; o < Cout; ++o)
+        for (int c = 0; c < Cin; ++c)
+            for (int u = 0; u < k; ++u)
+                for (int v = 0; v < k; ++v)
+                    r[((size_t)o * k * k + u * k + v) * Cin + c] = w[(((size_t)o * Cin + c) * k + u) * k + v];
+    for (int u = 0; u < k; ++u)
+        for (int v = 0; v < k; ++v) {
+            op->du[u * k + v] = (int8_t)(u - k / 2);
+            op->dv[u * k + v] = (int8_t)(v - k / 2);
+        }
+    if ((rc = upload(op->w, r.data(), r.size() * sizeof(float)))) return rc;
+    tc::build_weights(r.data(), Cout, op->T, Cin, &op->tcw);
+    L.ops.push_back(std::move(op));
+    return upload(L.bias, b, Cout * sizeof(float));
+}
+
+// transposed conv weight [Cin][Cout][k][k] (k = 5, stride 2, pad 2, output
+// padding 1) -> four sub-pixel phases.  Output row Y = 2m + py receives
+// input row a = m + (py + 2 - u) / 2 through tap u whenever u = py (mod 2).
+int make_deconv(Layer &L, const ParamMap &pm, const std::string &name, int Cin, int Cout, int epi) {
+    const int k = 5;
+    L.name = name;
+    L.deconv = true;
+    L.Cin = Cin;
+    L.Cout = Cout;
+    L.k = k;
+    L.stride = 2;
+    L.in_xform = IN_NONE;
+    L.epi = epi;
+    const float *w, *b;
+    int rc = get_param(pm, name + ".weight", (int64_t)Cin * Cout * k * k, &w);
+    if (rc) return rc;
+    rc = get_param(pm, name + ".bias", Cout, &b);
+    if (rc) return rc;
+    if (Cout <= 4 && Cin % 32 == 0) {
+        std::vector<float> r((size_t)Cin * 25 * 4, 0.f);
+        for (int c = 0; c < Cin; ++c)
+            for (int o = 0; o < Cout; ++o)
+                for (int u = 0; u < k; ++u)
+                    for (int v = 0; v < k; ++v)
+                        r[(((size_t)c * 25) + u * 5 + v) * 4 + o] = w[(((size_t)c * Cout + o) * k + u) * k + v];
+        if ((rc = upload(L.w_small, r.data(), r.size() * sizeof(float)))) return rc;
+    }
+    for (int py = 0; py < 2; ++py)
+        for (int px = 0; px < 2; ++px) {
+            auto op = std::make_unique<ConvOp>();
+            op->py = py;
+            op->px = px;
+            std::vector<int> us, vs;
+            for (int u = py; u < k; u += 2) us.push_back(u);
+            for (int v = px; v < k; v += 2) vs.push_back(v);
+            op->T = (int)(us.size() * vs.size());
+            std::vector<float> r((size_t)Cout * op->T * Cin);
+            int t = 0;
+            for (int u : us)
+                for (int v : vs) {
+                    op->du[t] = (int8_t)((py + 2 - u) / 2);
+                    op->dv[t] = (int8_t)((px + 2 - v) / 2);
+                    for (int o = 0; o < Cout; ++o)
+                        for (int c = 0; c < Cin; ++c)
+                            r[((size_t)o * op->T + t) * Cin + c] = w[(((size_t)c * Cout + o) * k + u) * k + v];
+                    ++t;
+                }
+            if ((rc = upload(op->w, r.data(), r.size() * sizeof(float)))) return rc;
+            tc::build_weights(r.data(), Cout, op->T, Cin, &op->tcw);
+            L.ops.push_back(std::move(op));
+        }
+    return upload(L.bias, b, Cout * sizeof(float));
+}
+
+int make_gdn(Gdn &G, const ParamMap &pm, const std::string &name, int C, bool inverse) {
+    G.name = name;
+    G.C = C;
+    G.inverse = inverse;
+    const float *beta, *gamma;
+    int rc = get_param(pm, name + ".beta", C, &beta);
+    if (rc) return rc;
+    rc = get_param(pm, name + ".gamma", (int64_t)C * C, &gamma);
+    if (rc) return rc;
+    if ((rc = upload(G.gamma, gamma, (size_t)C * C * sizeof(float)))) return rc;
+    tc::build_weights(gamma, C, 1, C, &G.tcw);
+    return upload(G.beta, beta, C * sizeof(float));
+}
+
+// ---------------------------------------------------------------------------
+// running layers
+// ---------------------------------------------------------------------------
+
+void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *in, int B, int Hi, int Wi,
+            float *out, int Ho, int Wo, cudaStream_t st) {
+    ConvDesc d{};
+    d.in = in;
+    d.out = out;
+    d.w = op.w.as<float>();
+    d.bias = L.bias.as<float>();
+    d.gdn_x = nullptr;
+    d.B = B;
+    d.Hi = Hi;
+    d.Wi = Wi;
+    d.Cin = L.Cin;
+    d.Ho = Ho;
+    d.Wo = Wo;
+    d.Cout = L.Cout;
+    d.T = op.T;
+    for (int t = 0; t < op.T; ++t) {
+        d.du[t] = op.du[t];
+        d.dv[t] = op.dv[t];
+    }
+    d.in_xform = L.in_xform;
+    d.epi = L.epi;
+    if (L.deconv) {
+        d.Gh = Hi;
+        d.Gw = Wi;
+        d.s = 1;
+        d.oym = 2;
+        d.oyo = op.py;
+        d.oxm = 2;
+        d.oxo = op.px;
+    } else {
+        d.Gh = Ho;
+        d.Gw = Wo;
+        d.s = L.stride;
+        d.oym = 1;
+        d.oyo = 0;
+        d.oxm = 1;
+        d.oxo = 0;
+    }
+    const double rows = (double)B * d.Gh * d.Gw;
+    const double flop = 2.0 * rows * d.Cout * d.T * d.Cin;
+    const double bytes = 4.0 * ((double)B * Hi * Wi * d.Cin + rows * d.Cout + (double)d.Cout * d.T * d.Cin);
+    const bool use_tc = cd->opt.conv_impl != LIC_CONV_SIMT && tc::can_run(d, op.tcw);
+    std::string nm = L.name + (L.deconv ? ".p" + std::to_string(2 * op.py + op.px) : std::string()) +
+                     (use_tc ? ":tc" : ":simt");
+    timed(const_cast<lic_codec *>(cd), nm, flop, bytes, 1, st, [&] {
+        if (use_tc) tc::launch(d, op.tcw, st);
+        else launch_conv_simt(d, st);
+    });
+}
+
+void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out,
+               cudaStream_t st) {
+    int Ho, Wo;
+    if (L.deconv) {
+        Ho = 2 * Hi;
+        Wo = 2 * Wi;
+    } else {
+        int p = L.k / 2;
+        Ho = (Hi + 2 * p - L.k) / L.stride + 1;
+        Wo = (Wi + 2 * p - L.k) / L.stride + 1;
+    }
+    if (L.deconv && L.w_small.p) {
+        const double flop = 2.0 * B * Ho * Wo * L.Cout * L.Cin * 6.25;
+        const double bytes = 4.0 * ((double)B * Hi * Wi * L.Cin + (double)B * Ho * Wo * L.Cout + 100.0 * L.Cin);
+        timed(const_cast<lic_codec *>(cd), L.name + ":small", flop, bytes, 1, st, [&] {
+            launch_deconv_small(in, B, Hi, Wi, L.Cin, L.w_small.as<float>(), L.bias.as<float>(), L.Cout, out, st);
+        });
+        return;
+    }
+    for (auto &op : L.ops) run_op(cd, L, *op, in, B, Hi, Wi, out, Ho, Wo, st);
+}
+
+void run_gdn(const lic_codec *cd, const Gdn &G, const float *in, int B, int H, int W, float *out, cudaStream_t st) {
+    ConvDesc d{};
+    d.in = in;
+    d.out = out;
+    d.w = G.gamma.as<float>();
+    d.bias = G.beta.as<float>();
+    d.gdn_x = in;
+    d.B = B;
+    d.Hi = H;
+    d.Wi = W;
+    d.Cin = G.C;
+    d.Gh = H;
+    d.Gw = W;
+    d.s = 1;
+    d.Ho = H;
+    d.Wo = W;
+    d.Cout = G.C;
+    d.oym = 1;
+    d.oxm = 1;
+    d.T = 1;
+    d.in_xform = IN_SQUARE;
+    d.epi = G.inverse ? EPI_IGDN : EPI_GDN;
+    const double rows = (double)B * H * W;
+    const bool use_tc = cd->opt.conv_impl != LIC_CONV_SIMT && tc::can_run(d, G.tcw);
+    timed(const_cast<lic_codec *>(cd), G.name + (use_tc ? ":tc" : ":simt"), 2.0 * rows * G.C * G.C,
+          4.0 * (2.0 * rows * G.C + (double)G.C * G.C), 1, st, [&] {
+              if (use_tc) tc::launch(d, G.tcw, st);
+              else launch_conv_simt(d, st);
+          });
+}
+
+int pad64(int v) { return (v + 63) / 64 * 64; }
+
+template <typename T>
+cudaError_t ensure_n(DevBuf &b, int64_t n) {
+    return b.ensure((size_t)n * sizeof(T) + 256);
+}
+
+// Workspace for a batch of B frames padded to Hp x Wp.
+int ensure_workspace(lic_codec *cd, int B, int Hp, int Wp) {
+    const int N = cd->N, M = cd->M;
+    const int64_t Hy = Hp / 16, Wy = Wp / 16, Hz = Hp / 64, Wz = Wp / 64;
+    const int64_t big = (int64_t)B * (Hp / 2) * (Wp / 2) * N;
+    LIC_CUDA_TRY(ensure_n<float>(cd->xin, (int64_t)B * Hp * Wp * 3));
+    LIC_CUDA_TRY(ensure_n<float>(cd->act0, big));
+    LIC_CUDA_TRY(ensure_n<float>(cd->act1, big));
+    LIC_CUDA_TRY(ensure_n<float>(cd->y, (int64_t)B * Hy * Wy * M));
+    LIC_CUDA_TRY(ensure_n<int32_t>(cd->s_y, (int64_t)B * Hy * Wy * M));
+    LIC_CUDA_TRY(ensure_n<float>(cd->yhat, (int64_t)B * Hy * Wy * M));
+    LIC_CUDA_TRY(ensure_n<float>(cd->xpre, (int64_t)B * Hp * Wp * 3));
+    if (cd->kind == LIC_HYPERPRIOR) {
+        LIC_CUDA_TRY(ensure_n<float>(cd->h1, (int64_t)B * Hy * Wy * N));
+        LIC_CUDA_TRY(ensure_n<float>(cd->h2, (int64_t)B * (Hy / 2) * (Wy / 2) * N));
+        LIC_CUDA_TRY(ensure_n<float>(cd->z, (int64_t)B * Hz * Wz * N));
+        LIC_CUDA_TRY(ensure_n<int32_t>(cd->s_z, (int64_t)B * Hz * Wz * N));
+        LIC_CUDA_TRY(ensure_n<float>(cd->zhat, (int64_t)B * Hz * Wz * N));
+        LIC_CUDA_TRY(ensure_n<float>(cd->g1, (int64_t)B * (Hy / 2) * (Wy / 2) * N));
+        LIC_CUDA_TRY(ensure_n<float>(cd->g2, (int64_t)B * Hy * Wy * N));
+        LIC_CUDA_TRY(ensure_n<float>(cd->sigma, (int64_t)B * Hy * Wy * M));
+        LIC_CUDA_TRY(ensure_n<uint8_t>(cd->idx, (int64_t)B * Hy * Wy * M));
+    }
+    return LIC_OK;
+}
+
+int ensure_entropy(lic_codec *cd, const StreamGeom &g, int B) {
+    const int64_t subs = (int64_t)B * g.nsub;
+    LIC_CUDA_TRY(ensure_n<uint16_t>(cd->scratch, subs * g.cap_words));
+    LIC_CUDA_TRY(ensure_n<int64_t>(cd->counts, subs));
+    LIC_CUDA_TRY(ensure_n<int64_t>(cd->sub_off, subs));
+    LIC_CUDA_TRY(ensure_n<int64_t>(cd->frame_bytes, B));
+    LIC_CUDA_TRY(ensure_n<int64_t>(cd->offs, 2 * (int64_t)B + 1));
+    const int64_t frame_cap = g.header_bytes + 2 * (int64_t)g.nsub * g.cap_words + 16;
+    LIC_CUDA_TRY(ensure_n<uint8_t>(cd->data, (int64_t)B * frame_cap));
+    LIC_CUDA_TRY(cd->h_offs.ensure((2 * (size_t)B + 1) * sizeof(int64_t)));
+    return LIC_OK;
+}
+
+cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
+
+// ---- the transforms ----
+
+// g_a: x (NHWC, xin) -> y (NHWC); 4 x conv5x5/2 with GDN after the first three
+void analysis(lic_codec *cd, int B, int Hp, int Wp, cudaStream_t st) {
+    float *a = cd->act0.as<float>(), *b = cd->act1.as<float>();
+    int H = Hp, W = Wp;
+    const float *in = cd->xin.as<float>();
+    for (int i = 0; i < 3; ++i) {
+        run_layer(cd, cd->ga[i], in, B, H, W, a, st);
+        H /= 2;
+        W /= 2;
+        run_gdn(cd, cd->gdn[i], a, B, H, W, b, st);
+        in = b;
+    }
+    run_layer(cd, cd->ga[3], in, B, H, W, cd->y.as<float>(), st);
+}
+
+// h_a: y -> z; conv3x3/1 on |y| + ReLU, conv5x5/2 + ReLU, conv5x5/2
+void hyper_analysis(lic_codec *cd, const float *y, int B, int Hy, int Wy, cudaStream_t st) {
+    run_layer(cd, cd->ha[0], y, B, Hy, Wy, cd->h1.as<float>(), st);
+    run_layer(cd, cd->ha[1], cd->h1.as<float>(), B, Hy, Wy, cd->h2.as<float>(), st);
+    run_layer(cd, cd->ha[2], cd->h2.as<float>(), B, Hy / 2, Wy / 2, cd->z.as<float>(), st);
+}
+
+// h_s: z_hat -> sigma; deconv+ReLU, deconv+ReLU, conv3x3+ReLU; then the index
+void hyper_synthesis(lic_codec *cd, const float *zhat, int B, int Hz, int Wz, cudaStream_t st) {
+    run_layer(cd, cd->hs[0], zhat, B, Hz, Wz, cd->g1.as<float>(), st);
+    run_layer(cd, cd->hs[1], cd->g1.as<float>(), B, 2 * Hz, 2 * Wz, cd->g2.as<float>(), st);
+    run_layer(cd, cd->hs[2], cd->g2.as<float>(), B, 4 * Hz, 4 * Wz, cd->sigma.as<float>(), st);
+    const double n = 16.0 * B * Hz * Wz * cd->M;
+    timed(cd, "scale_index", 0, 5 * n, 1, st, [&] {
+        launch_scale_index(cd->sigma.as<float>(), B, 16 * Hz * Wz, cd->M, cd->idx.as<uint8_t>(), nullptr, st);
+    });
+}
+
+// g_s: y_hat (NHWC) -> xpre (NHWC, 3 channels); deconvs with IGDN between
+void synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, cudaStream_t st) {
+    float *a = cd->act0.as<float>(), *b = cd->act1.as<float>();
+    int H = Hy, W = Wy;
+    const float *in = yhat;
+    for (int i = 0; i < 3; ++i) {
+        run_layer(cd, cd->gs[i], in, B, H, W, a, st);
+        H *= 2;
+        W *= 2;
+        run_gdn(cd, cd->igdn[i], a, B, H, W, b, st);
+        in = b;
+    }
+    run_layer(cd, cd->gs[3], in, B, H, W, cd->xpre.as<float>(), st);
+}
+
+void fill_out(lic_codec *cd, int B, lic_bitstreams *out) {
+    int64_t *h = static_cast<int64_t *>(cd->h_offs.p);
+    const int64_t *d = cd->offs.as<int64_t>();
+    out->count = B;
+    out->on_device = 1;
+    out->data = cd->data.as<uint8_t>();
+    out->offsets = h;
+    out->sizes = h + B + 1;
+    out->d_offsets = d;
+    out->d_sizes = d + B + 1;
+}
+
+int entropy_encode(lic_codec *cd, const StreamGeom &g, int B, const int32_t *s_y, const uint8_t *idx,
+                   const int32_t *s_z, lic_bitstreams *out, cudaStream_t st) {
+    int rc = ensure_entropy(cd, g, B);
+    if (rc) return rc;
+    const double nsym = (double)B * ((double)g.M * g.Hy * g.Wy + (double)g.nz * g.Hz * g.Wz);
+    timed(cd, "rans_encode", 0, 5 * nsym, 1, st, [&] {
+        launch_rans_encode(g, B, cd->dt, s_y, idx, s_z, cd->scratch.as<uint16_t>(), cd->counts.as<int64_t>(), st);
+    });
+    timed(cd, "rans_compact", 0, 0, 3, st, [&] {
+        launch_rans_compact(g, B, cd->scratch.as<uint16_t>(), cd->counts.as<int64_t>(), cd->sub_off.as<int64_t>(),
+                            cd->frame_bytes.as<int64_t>(), cd->offs.as<int64_t>(), cd->data.as<uint8_t>(), st);
+    });
+    LIC_CUDA_TRY(cudaMemcpyAsync(cd->h_offs.p, cd->offs.p, (2 * (size_t)B + 1) * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, st));
+    fill_out(cd, B, out);
+    LIC_CUDA_TRY(cudaGetLastError());
+    return LIC_OK;
+}
+
+// Bring a bitstream batch onto the device: returns device data/offsets/sizes.
+int stage_bitstreams(lic_codec *cd, const lic_bitstreams *in, const uint8_t **data, const int64_t **offs,
+                     const int64_t **sizes, cudaStream_t st) {
+    const int B = in->count;
+    if (in->on_device) {
+        if (!in->d_offsets || !in->d_sizes || !in->data) return LIC_E_INVALID_ARG;
+        *data = in->data;
+        *offs = in->d_offsets;
+        *sizes = in->d_sizes;
+        return LIC_OK;
+    }
+    if (!in->offsets || !in->sizes || !in->data) return LIC_E_INVALID_ARG;
+    std::vector<int64_t> ho(2 * (size_t)B + 1);
+    int64_t o = 0;
+    for (int b = 0; b < B; ++b) {
+        if (in->sizes[b] < 0) return LIC_E_INVALID_ARG;
+        ho[b] = o;
+        ho[B + 1 + b] = in->sizes[b];
+        o += (in->sizes[b] + 15) / 16 * 16;
+    }
+    ho[B] = o;
+    LIC_CUDA_TRY(cd->in_data.ensure((size_t)o + 16));
+    LIC_CUDA_TRY(cd->in_offs.ensure(ho.size() * sizeof(int64_t)));
+    for (int b = 0; b < B; ++b)
+        if (in->sizes[b] > 0)
+            LIC_CUDA_TRY(cudaMemcpyAsync(cd->in_data.as<uint8_t>() + ho[b], in->data + in->offsets[b],
+                                         (size_t)in->sizes[b], cudaMemcpyHostToDevice, st));
+    LIC_CUDA_TRY(cudaMemcpyAsync(cd->in_offs.p, ho.data(), ho.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    // the host vector dies here: make the copy complete before returning
+    LIC_CUDA_TRY(cudaStreamSynchronize(st));
+    *data = cd->in_data.as<uint8_t>();
+    *offs = cd->in_offs.as<int64_t>();
+    *sizes = cd->in_offs.as<int64_t>() + B + 1;
+    return LIC_OK;
+}
+
+// Entropy decoding of a batch (and, for the hyperprior, h_s in between);
+// leaves s_y / yhat (and s_z / zhat / sigma / idx) in the workspace.
+int entropy_decode(lic_codec *cd, const lic_bitstreams *in, int H, int W, cudaStream_t st) {
+    const int B = in->count;
+    const int Hp = pad64(H), Wp = pad64(W);
+    int rc = ensure_workspace(cd, B, Hp, Wp);
+    if (rc) return rc;
+    const uint8_t *data;
+    const int64_t *offs, *sizes;
+    if ((rc = stage_bitstreams(cd, in, &data, &offs, &sizes, st))) return rc;
+    StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows);
+    uint32_t *status = cd->status.as<uint32_t>();
+    if (cd->kind == LIC_HYPERPRIOR) {
+        timed(cd, "rans_decode_z", 0, 8.0 * B * g.nz * g.Hz * g.Wz, 1, st, [&] {
+            launch_rans_decode(g, B, 0, cd->dt, data, offs, sizes, nullptr, cd->med.as<float>(),
+                               cd->s_z.as<int32_t>(), cd->zhat.as<float>(), status, st);
+        });
+        hyper_synthesis(cd, cd->zhat.as<float>(), B, g.Hz, g.Wz, st);
+    }
+    timed(cd, "rans_decode_y", 0, 9.0 * B * g.M * g.Hy * g.Wy, 1, st, [&] {
+        launch_rans_decode(g, B, 1, cd->dt, data, offs, sizes,
+                           cd->kind == LIC_HYPERPRIOR ? cd->idx.as<uint8_t>() : nullptr, cd->med.as<float>(),
+                           cd->s_y.as<int32_t>(), cd->yhat.as<float>(), status, st);
+    });
+    cd->last_B = B;
+    cd->last_Hp = Hp;
+    cd->last_Wp = Wp;
+    cd->have_y = false;
+    cd->have_sy = true;
+    cd->have_z = false;
+    cd->have_sz = cd->kind == LIC_HYPERPRIOR;
+    cd->have_sigma = cd->have_idx = cd->kind == LIC_HYPERPRIOR;
+    cd->have_xpre = false;
+    LIC_CUDA_TRY(cudaGetLastError());
+    return LIC_OK;
+}
+
+int copy_in(lic_codec *cd, DevBuf &stage, const void *src, size_t bytes, const void **dev, cudaStream_t st) {
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return LIC_OK;
+    }
+    LIC_CUDA_TRY(stage.ensure(bytes));
+    LIC_CUDA_TRY(cudaMemcpyAsync(stage.p, src, bytes, cudaMemcpyHostToDevice, st));
+    *dev = stage.p;
+    return LIC_OK;
+}
+
+}  // namespace
+}  // namespace lic
+
+using namespace lic;
+
+extern "C" {
+
+const char *lic_strerror(int code) {
+    switch (code) {
+        case LIC_OK: return "ok";
+        case LIC_E_INVALID_ARG: return g_last_error[0] ? g_last_error : "invalid argument";
+        case LIC_E_UNSUPPORTED: return "unsupported configuration";
+        case LIC_E_OOM: return "out of device memory";
+        case LIC_E_CORRUPT_STREAM: return "corrupt bitstream";
+        case LIC_E_TIMEOUT: return "device wait timed out";
+        case LIC_E_CUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+        default: return "unknown error";
+    }
+}
+
+void lic_scale_table(float T[64]) { lic::scale_table(T); }
+
+static int pack_eb(const ParamMap &pm, int C, std::vector<double> *out) {
+    static const int f[6] = {1, 3, 3, 3, 3, 1};
+    std::vector<const float *> H(5), b(5), a(4);
+    for (int k = 0; k < 5; ++k) {
+        int rc = get_param(pm, "eb.H" + std::to_string(k), (int64_t)C * f[k + 1] * f[k], &H[k]);
+        if (rc) return rc;
+        rc = get_param(pm, "eb.b" + std::to_string(k), (int64_t)C * f[k + 1], &b[k]);
+        if (rc) return rc;
+        if (k < 4 && (rc = get_param(pm, "eb.a" + std::to_string(k), (int64_t)C * f[k + 1], &a[k]))) return rc;
+    }
+    out->assign((size_t)C * 58, 0.0);
+    for (int c = 0; c < C; ++c) {
+        double *p = out->data() + (size_t)c * 58;
+        for (int k = 0; k < 5; ++k)
+            for (int e = 0; e < f[k + 1] * f[k]; ++e) *p++ = H[k][(size_t)c * f[k + 1] * f[k] + e];
+        for (int k = 0; k < 5; ++k)
+            for (int e = 0; e < f[k + 1]; ++e) *p++ = b[k][(size_t)c * f[k + 1] + e];
+        for (int k = 0; k < 4; ++k)
+            for (int e = 0; e < f[k + 1]; ++e) *p++ = a[k][(size_t)c * f[k + 1] + e];
+    }
+    return LIC_OK;
+}
+
+static ParamMap param_map(const lic_weights *w) {
+    ParamMap pm;
+    for (int i = 0; i < w->count; ++i)
+        if (w->params[i].name) pm[w->params[i].name] = {w->params[i].data, w->params[i].numel};
+    return pm;
+}
+
+int lic_build_tables(const lic_weights *weights, int gauss, int max_tables, int64_t cdf_cap, float *medians,
+                     int32_t *lo, int32_t *hi, int64_t *start, uint32_t *cdf) {
+    if (!weights || !weights->params) return LIC_E_INVALID_ARG;
+    ParamMap pm = param_map(weights);
+    auto it = pm.find("eb.H0");
+    if (it == pm.end() || it->second.second % 3 != 0) return LIC_E_INVALID_ARG;
+    int C = (int)(it->second.second / 3);
+    std::vector<double> P;
+    int rc = pack_eb(pm, C, &P);
+    if (rc) return rc;
+    HostTables t;
+    if ((rc = build_tables(P, C, gauss != 0, &t))) return rc;
+    int nt = (int)t.lo.size();
+    if (nt > max_tables || (int64_t)t.cdf.size() > cdf_cap) return LIC_E_INVALID_ARG;
+    if (medians) memcpy(medians, t.medians.data(), C * sizeof(float));
+    memcpy(lo, t.lo.data(), nt * sizeof(int32_t));
+    memcpy(hi, t.hi.data(), nt * sizeof(int32_t));
+    memcpy(start, t.start.data(), nt * sizeof(int64_t));
+    memcpy(cdf, t.cdf.data(), t.cdf.size() * sizeof(uint32_t));
+    return nt;
+}
+
+int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const lic_options *opts, lic_codec **out) {
+    g_last_error[0] = 0;
+    if (!out || !weights || !weights->params) return LIC_E_INVALID_ARG;
+    *out = nullptr;
+    if (kind != LIC_FACTORIZED && kind != LIC_HYPERPRIOR) return LIC_E_INVALID_ARG;
+    if (N <= 0 || M <= 0) return LIC_E_INVALID_ARG;
+    if (N % 32 || M % 32 || N > 256 || M > 512) return LIC_E_UNSUPPORTED;
+    auto cd = std::make_unique<lic_codec>();
+    cd->kind = kind;
+    cd->N = N;
+    cd->M = M;
+    if (opts) cd->opt = *opts;
+    if (cd->opt.band_rows <= 0) cd->opt.band_rows = 16;
+    if (cd->opt.precision != LIC_FP32) return LIC_E_UNSUPPORTED;
+    LIC_CUDA_TRY(cudaGetDevice(&cd->device));
+    LIC_CUDA_TRY(upload_scale_table());
+    ParamMap pm = param_map(weights);
+    int rc;
+    const int ch[5] = {3, N, N, N, M};
+    for (int i = 0; i < 4; ++i) {
+        if ((rc = make_conv(cd->ga[i], pm, "g_a.conv" + std::to_string(i), ch[i], ch[i + 1], 5, 2, IN_NONE, EPI_NONE)))
+            return rc;
+        if ((rc = make_deconv(cd->gs[i], pm, "g_s.deconv" + std::to_string(i), ch[4 - i], ch[3 - i], EPI_NONE)))
+            return rc;
+    }
+    for (int i = 0; i < 3; ++i) {
+        if ((rc = make_gdn(cd->gdn[i], pm, "g_a.gdn" + std::to_string(i), N, false))) return rc;
+        if ((rc = make_gdn(cd->igdn[i], pm, "g_s.igdn" + std::to_string(i), N, true))) return rc;
+    }
+    if (kind == LIC_HYPERPRIOR) {
+        if ((rc = make_conv(cd->ha[0], pm, "h_a.conv0", M, N, 3, 1, IN_ABS, EPI_RELU))) return rc;
+        if ((rc = make_conv(cd->ha[1], pm, "h_a.conv1", N, N, 5, 2, IN_NONE, EPI_RELU))) return rc;
+        if ((rc = make_conv(cd->ha[2], pm, "h_a.conv2", N, N, 5, 2, IN_NONE, EPI_NONE))) return rc;
+        if ((rc = make_deconv(cd->hs[0], pm, "h_s.deconv0", N, N, EPI_RELU))) return rc;
+        if ((rc = make_deconv(cd->hs[1], pm, "h_s.deconv1", N, N, EPI_RELU))) return rc;
+        if ((rc = make_conv(cd->hs[2], pm, "h_s.conv2", N, M, 3, 1, IN_NONE, EPI_RELU))) return rc;
+    }
+    // entropy models: the bottleneck codes y (factorized) or z (hyperprior)
+    const int C = kind == LIC_FACTORIZED ? M : N;
+    std::vector<double> P;
+    if ((rc = pack_eb(pm, C, &P))) return rc;
+    if ((rc = build_tables(P, C, kind == LIC_HYPERPRIOR, &cd->ht))) return rc;
+    if ((rc = upload(cd->cdf, cd->ht.cdf.data(), cd->ht.cdf.size() * 4))) return rc;
+    if ((rc = upload(cd->start, cd->ht.start.data(), cd->ht.start.size() * 8))) return rc;
+    if ((rc = upload(cd->lo, cd->ht.lo.data(), cd->ht.lo.size() * 4))) return rc;
+    if ((rc = upload(cd->hi, cd->ht.hi.data(), cd->ht.hi.size() * 4))) return rc;
+    if ((rc = upload(cd->med, cd->ht.medians.data(), cd->ht.medians.size() * 4))) return rc;
+    cd->dt.cdf = cd->cdf.as<uint32_t>();
+    cd->dt.start = cd->start.as<int64_t>();
+    cd->dt.lo = cd->lo.as<int32_t>();
+    cd->dt.hi = cd->hi.as<int32_t>();
+    cd->dt.n_eb = C;
+    cd->dt.gauss_base = kind == LIC_HYPERPRIOR ? C : -1;
+    LIC_CUDA_TRY(cd->status.ensure(256));
+    LIC_CUDA_TRY(cudaMemset(cd->status.p, 0, 256));
+    LIC_CUDA_TRY(cudaDeviceSynchronize());
+    *out = cd.release();
+    return LIC_OK;
+}
+
+void lic_codec_destroy(lic_codec *codec) {
+    if (!codec) return;
+    cudaDeviceSynchronize();
+    delete codec;
+}
+
+int lic_sync(lic_codec *cd, void *stream) {
+    if (!cd) return LIC_E_INVALID_ARG;
+    LIC_CUDA_TRY(cudaStreamSynchronize(S(stream)));
+    uint32_t st = 0;
+    LIC_CUDA_TRY(cudaMemcpy(&st, cd->status.p, 4, cudaMemcpyDeviceToHost));
+    if (st) LIC_CUDA_TRY(cudaMemset(cd->status.p, 0, 4));
+    if (st & ST_CORRUPT) return LIC_E_CORRUPT_STREAM;
+    if (st & ST_TIMEOUT) return LIC_E_TIMEOUT;
+    return LIC_OK;
+}
+
+int lic_encode(lic_codec *cd, const float *frames, int B, int H, int W, lic_bitstreams *out, void *stream) {
+    if (!cd || !frames || !out || B < 1 || H < 1 || W < 1) return LIC_E_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    const int Hp = pad64(H), Wp = pad64(W);
+    int rc = ensure_workspace(cd, B, Hp, Wp);
+    if (rc) return rc;
+    const void *src;
+    if ((rc = copy_in(cd, cd->stage_in, frames, (size_t)B * 3 * H * W * sizeof(float), &src, st))) return rc;
+    timed(cd, "pad_pack", 0, 12.0 * B * ((double)H * W + (double)Hp * Wp), 1, st, [&] {
+        launch_pad_pack(static_cast<const float *>(src), B, H, W, Hp, Wp, cd->xin.as<float>(), st);
+    });
+    analysis(cd, B, Hp, Wp, st);
+    const int Hy = Hp / 16, Wy = Wp / 16;
+    StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows);
+    if (cd->kind == LIC_HYPERPRIOR) {
+        timed(cd, "quantize_y", 0, 8.0 * B * Hy * Wy * cd->M, 1, st, [&] {
+            launch_quantize(cd->y.as<float>(), B, Hy * Wy, cd->M, nullptr, cd->s_y.as<int32_t>(), nullptr, st);
+        });
+        hyper_analysis(cd, cd->y.as<float>(), B, Hy, Wy, st);
+        timed(cd, "quantize_z", 0, 12.0 * B * g.Hz * g.Wz * cd->N, 1, st, [&] {
+            launch_quantize(cd->z.as<float>(), B, g.Hz * g.Wz, cd->N, cd->med.as<float>(), cd->s_z.as<int32_t>(),
+                            cd->zhat.as<float>(), st);
+        });
+        hyper_synthesis(cd, cd->zhat.as<float>(), B, g.Hz, g.Wz, st);
+    } else {
+        timed(cd, "quantize_y", 0, 8.0 * B * Hy * Wy * cd->M, 1, st, [&] {
+            launch_quantize(cd->y.as<float>(), B, Hy * Wy, cd->M, cd->med.as<float>(), cd->s_y.as<int32_t>(),
+                            nullptr, st);
+        });
+    }
+    if ((rc = entropy_encode(cd, g, B, cd->s_y.as<int32_t>(), cd->idx.as<uint8_t>(), cd->s_z.as<int32_t>(), out, st)))
+        return rc;
+    cd->last_B = B;
+    cd->last_Hp = Hp;
+    cd->last_Wp = Wp;
+    cd->have_y = cd->have_sy = true;
+    cd->have_z = cd->have_sz = cd->have_sigma = cd->have_idx = cd->kind == LIC_HYPERPRIOR;
+    cd->have_xpre = false;
+    return LIC_OK;
+}
+
+int lic_encode_latents(lic_codec *cd, const int32_t *s_y, const uint8_t *idx, const int32_t *s_z, int B, int H, int W,
+                       int Hy, int Wy, lic_bitstreams *out, void *stream) {
+    if (!cd || !s_y || !out || B < 1 || Hy < 1 || Wy < 1) return LIC_E_INVALID_ARG;
+    if (cd->kind == LIC_HYPERPRIOR && (!idx || !s_z || Hy % 4 || Wy % 4)) return LIC_E_INVALID_ARG;
+    if (!is_device_ptr(s_y) || (idx && !is_device_ptr(idx)) || (s_z && !is_device_ptr(s_z))) return LIC_E_INVALID_ARG;
+    StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, 16 * Hy, 16 * Wy, cd->opt.band_rows);
+    return entropy_encode(cd, g, B, s_y, idx, s_z, out, S(stream));
+}
+
+int lic_decode_latents(lic_codec *cd, const lic_bitstreams *in, int H, int W, int32_t *s_y, int32_t *s_z,
+                       void *stream) {
+    if (!cd || !in || !s_y || in->count < 1 || H < 1 || W < 1) return LIC_E_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    int rc = entropy_decode(cd, in, H, W, st);
+    if (rc) return rc;
+    const int B = in->count, Hp = pad64(H), Wp = pad64(W);
+    const int64_t ny = (int64_t)B * cd->M * (Hp / 16) * (Wp / 16);
+    LIC_CUDA_TRY(cudaMemcpyAsync(s_y, cd->s_y.p, ny * 4, cudaMemcpyDefault, st));
+    if (cd->kind == LIC_HYPERPRIOR && s_z) {
+        const int64_t nz = (int64_t)B * cd->N * (Hp / 64) * (Wp / 64);
+        LIC_CUDA_TRY(cudaMemcpyAsync(s_z, cd->s_z.p, nz * 4, cudaMemcpyDefault, st));
+    }
+    return LIC_OK;
+}
+
+int lic_decode(lic_codec *cd, const lic_bitstreams *in, int H, int W, float *frames, void *stream) {
+    if (!cd || !in || !frames || in->count < 1 || H < 1 || W < 1) return LIC_E_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    int rc = entropy_decode(cd, in, H, W, st);
+    if (rc) return rc;
+    const int B = in->count, Hp = pad64(H), Wp = pad64(W);
+    synthesis(cd, cd->yhat.as<float>(), B, Hp / 16, Wp / 16, st);
+    cd->have_xpre = true;
+    const size_t bytes = (size_t)B * 3 * H * W * sizeof(float);
+    if (is_device_ptr(frames)) {
+        timed(cd, "crop_unpack", 0, 24.0 * B * H * W, 1, st,
+              [&] { launch_crop_unpack(cd->xpre.as<float>(), B, Hp, Wp, H, W, frames, st); });
+    } else {
+        LIC_CUDA_TRY(cd->stage_out.ensure(bytes));
+        timed(cd, "crop_unpack", 0, 24.0 * B * H * W, 1, st,
+              [&] { launch_crop_unpack(cd->xpre.as<float>(), B, Hp, Wp, H, W, cd->stage_out.as<float>(), st); });
+        LIC_CUDA_TRY(cudaMemcpyAsync(frames, cd->stage_out.p, bytes, cudaMemcpyDeviceToHost, st));
+        LIC_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    LIC_CUDA_TRY(cudaGetLastError());
+    return LIC_OK;
+}
+
+int64_t lic_bitstreams_download(const lic_bitstreams *in, uint8_t *dst, int64_t dst_cap, void *stream) {
+    if (!in || !dst || !in->on_device || !in->offsets || in->count < 1) return LIC_E_INVALID_ARG;
+    LIC_CUDA_TRY(cudaStreamSynchronize(S(stream)));
+    const int64_t n = in->offsets[in->count];
+    if (n > dst_cap || n < 0) return LIC_E_INVALID_ARG;
+    LIC_CUDA_TRY(cudaMemcpy(dst, in->data, (size_t)n, cudaMemcpyDeviceToHost));
+    return n;
+}
+
+int lic_profile_enable(lic_codec *cd, int enable) {
+    if (!cd) return LIC_E_INVALID_ARG;
+    if (enable) {
+        cd->prof.clear();
+        cd->ev_used = 0;
+    }
+    cd->prof_on = enable != 0;
+    return LIC_OK;
+}
+
+int lic_profile_report(lic_codec *cd, char *buf, int cap) {
+    if (!cd) return LIC_E_INVALID_ARG;
+    struct Agg {
+        int launches = 0;
+        double ms = 0, flop = 0, bytes = 0;
+    };
+    std::vector<std::string> order;
+    std::map<std::string, Agg> agg;
+    for (auto &r : cd->prof) {
+        LIC_CUDA_TRY(cudaEventSynchronize(r.b));
+        float ms = 0;
+        LIC_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+        if (!agg.count(r.name)) order.push_back(r.name);
+        Agg &a = agg[r.name];
+        a.launches += r.launches;
+        a.ms += ms;
+        a.flop += r.flop;
+        a.bytes += r.bytes;
+    }
+    std::string js = "[";
+    char tmp[512];
+    for (size_t i = 0; i < order.size(); ++i) {
+        const Agg &a = agg[order[i]];
+        snprintf(tmp, sizeof(tmp), "%s{\"name\": \"%s\", \"launches\": %d, \"ms\": %.6f, \"flop\": %.6e, \"bytes\": %.6e}",
+                 i ? ", " : "", order[i].c_str(), a.launches, a.ms, a.flop, a.bytes);
+        js += tmp;
+    }
+    js += "]";
+    if (buf && cap > 0) {
+        size_t n = std::min((size_t)cap - 1, js.size());
+        memcpy(buf, js.data(), n);
+        buf[n] = 0;
+    }
+    return (int)js.size();
+}
+
+int64_t lic_launch_count(lic_codec *cd) { return cd ? cd->launches : LIC_E_INVALID_ARG; }
+
+int lic_decoded_shape(const uint8_t *f, int64_t size, int *kind, int *H, int *W) {
+    if (!f || size < 36) return LIC_E_INVALID_ARG;
+    if (memcmp(f, "LIC1", 4) != 0) return LIC_E_CORRUPT_STREAM;
+    uint16_t ver, k;
+    uint32_t h, w;
+    memcpy(&ver, f + 4, 2);
+    memcpy(&k, f + 6, 2);
+    memcpy(&h, f + 12, 4);
+    memcpy(&w, f + 16, 4);
+    if (ver != 1 || k > 1) return LIC_E_CORRUPT_STREAM;
+    if (kind) *kind = k;
+    if (H) *H = (int)h;
+    if (W) *W = (int)w;
+    return LIC_OK;
+}
+
+// ---- stage calls ----
+
+// copy a device NHWC float tensor into dst (NCHW, device or host)
+static int emit_nchw(lic_codec *cd, const float *src, int B, int H, int W, int C, void *dst, cudaStream_t st) {
+    const size_t bytes = (size_t)B * C * H * W * sizeof(float);
+    if (is_device_ptr(dst)) {
+        timed(cd, "to_nchw", 0, 8.0 * B * H * W * C, 1, st,
+              [&] { launch_nhwc_to_nchw(src, B, H, W, C, static_cast<float *>(dst), st); });
+    } else {
+        LIC_CUDA_TRY(cd->stage_out.ensure(bytes));
+        timed(cd, "to_nchw", 0, 8.0 * B * H * W * C, 1, st,
+              [&] { launch_nhwc_to_nchw(src, B, H, W, C, cd->stage_out.as<float>(), st); });
+        LIC_CUDA_TRY(cudaMemcpyAsync(dst, cd->stage_out.p, bytes, cudaMemcpyDeviceToHost, st));
+        LIC_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    LIC_CUDA_TRY(cudaGetLastError());
+    return LIC_OK;
+}
+
+static int ingest_nchw(lic_codec *cd, const float *src, int B, int C, int H, int W, float *dst_nhwc, cudaStream_t st) {
+    const void *dev;
+    int rc = copy_in(cd, cd->stage_in, src, (size_t)B * C * H * W * sizeof(float), &dev, st);
+    if (rc) return rc;
+    timed(cd, "to_nhwc", 0, 8.0 * B * H * W * C, 1, st,
+          [&] { launch_nchw_to_nhwc(static_cast<const float *>(dev), B, C, H, W, dst_nhwc, st); });
+    return LIC_OK;
+}
+
+int lic_analysis(lic_codec *cd, const float *frames, int B, int H, int W, float *y, void *stream) {
+    if (!cd || !frames || !y || B < 1 || H < 1 || W < 1) return LIC_E_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    const int Hp = pad64(H), Wp = pad64(W);
+    int rc = ensure_workspace(cd, B, Hp, Wp);
+    if (rc) return rc;
+    const void *src;
+    if ((rc = copy_in(cd, cd->stage_in, frames, (size_t)B * 3 * H * W * sizeof(float), &src, st))) return rc;
+    timed(cd, "pad_pack", 0, 12.0 * B * ((double)H * W + (double)Hp * Wp), 1, st, [&] {
+        launch_pad_pack(static_cast<const float *>(src), B, H, W, Hp, Wp, cd->xin.as<float>(), st);
+    });
+    analysis(cd, B, Hp, Wp, st);
+    return emit_nchw(cd, cd->y.as<float>(), B, Hp / 16, Wp / 16, cd->M, y, st);
+}
+
+int lic_synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, float *x, void *stream) {
+    if (!cd || !yhat || !x || B < 1 || Hy < 1 || Wy < 1) return LIC_E_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    int rc = ensure_workspace(cd, B, 16 * Hy, 16 * Wy);
+    if (rc) return rc;
+    if ((rc = ingest_nchw(cd, yhat, B, cd->M, Hy, Wy, cd->yhat.as<float>(), st))) return rc;
+    synthesis(cd, cd->yhat.as<float>(), B, Hy, Wy, st);
+    return emit_nchw(cd, cd->xpre.as<float>(), B, 16 * Hy, 16 * Wy, 3, x, st);
+}
+
+int lic_hyper_analysis(lic_codec *cd, const float *y, int B, int Hy, int Wy, float *z, void *stream) {
+    if (!cd || !y || !z || B < 1 || Hy < 4 || Wy < 4 || Hy % 4 || Wy % 4) return LIC_E_INVALID_ARG;
+    if (cd->kind != LIC_HYPERPRIOR) return LIC_E_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    int rc = ensure_workspace(cd, B, 16 * Hy, 16 * Wy);
+    if (rc) return rc;
+    if ((rc = ingest_nchw(cd, y, B, cd->M, Hy, Wy, cd->y.as<float>(), st))) return rc;
+    hyper_analysis(cd, cd->y.as<float>(), B, Hy, Wy, st);
+    return emit_nchw(cd, cd->z.as<float>(), B, Hy / 4, Wy / 4, cd->N, z, st);
+}
+
+int lic_hyper_synthesis(lic_codec *cd, const float *zhat, int B, int Hz, int Wz, float *sigma, uint8_t *idx,
+                        void *stream) {
+    if (!cd || !zhat || !sigma || B < 1 || Hz < 1 || Wz < 1) return LIC_E_INVALID_ARG;
+    if (cd->kind != LIC_HYPERPRIOR) return LIC_E_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    int rc = ensure_workspace(cd, B, 64 * Hz, 64 * Wz);
+    if (rc) return rc;
+    if ((rc = ingest_nchw(cd, zhat, B, cd->N, Hz, Wz, cd->zhat.as<float>(), st))) return rc;
+    hyper_synthesis(cd, cd->zhat.as<float>(), B, Hz, Wz, st);
+    if ((rc = emit_nchw(cd, cd->sigma.as<float>(), B, 4 * Hz, 4 * Wz, cd->M, sigma, st))) return rc;
+    if (idx) {
+        const size_t n = (size_t)B * cd->M * 16 * Hz * Wz;
+        LIC_CUDA_TRY(cudaMemcpyAsync(idx, cd->idx.p, n, cudaMemcpyDefault, st));
+        LIC_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return LIC_OK;
+}
+
+int lic_read_tensor(lic_codec *cd, int which, void *dst, int64_t *count, void *stream) {
+    if (!cd) return LIC_E_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    const int B = cd->last_B, Hp = cd->last_Hp, Wp = cd->last_Wp;
+    const int Hy = Hp / 16, Wy = Wp / 16, Hz = Hp / 64, Wz = Wp / 64;
+    int64_t n = 0;
+    bool ok = false;
+    switch (which) {
+        case LIC_T_Y: n = (int64_t)B * cd->M * Hy * Wy; ok = cd->have_y; break;
+        case LIC_T_SY: n = (int64_t)B * cd->M * Hy * Wy; ok = cd->have_sy; break;
+        case LIC_T_Z: n = (int64_t)B * cd->N * Hz * Wz; ok = cd->have_z; break;
+        case LIC_T_SZ: n = (int64_t)B * cd->N * Hz * Wz; ok = cd->have_sz; break;
+        case LIC_T_SIGMA: n = (int64_t)B * cd->M * Hy * Wy; ok = cd->have_sigma; break;
+        case LIC_T_IDX: n = (int64_t)B * cd->M * Hy * Wy; ok = cd->have_idx; break;
+        case LIC_T_XPRE: n = (int64_t)B * 3 * Hp * Wp; ok = cd->have_xpre; break;
+        default: return LIC_E_INVALID_ARG;
+    }
+    if (!ok || B == 0) return LIC_E_INVALID_ARG;
+    if (count) *count = n;
+    if (!dst) return LIC_OK;
+    switch (which) {
+        case LIC_T_Y: return emit_nchw(cd, cd->y.as<float>(), B, Hy, Wy, cd->M, dst, st);
+        case LIC_T_Z: return emit_nchw(cd, cd->z.as<float>(), B, Hz, Wz, cd->N, dst, st);
+        case LIC_T_SIGMA: return emit_nchw(cd, cd->sigma.as<float>(), B, Hy, Wy, cd->M, dst, st);
+        case LIC_T_XPRE: return emit_nchw(cd, cd->xpre.as<float>(), B, Hp, Wp, 3, dst, st);
+        case LIC_T_SY: LIC_CUDA_TRY(cudaMemcpyAsync(dst, cd->s_y.p, n * 4, cudaMemcpyDefault, st)); break;
+        case LIC_T_SZ: LIC_CUDA_TRY(cudaMemcpyAsync(dst, cd->s_z.p, n * 4, cudaMemcpyDefault, st)); break;
+        case LIC_T_IDX: LIC_CUDA_TRY(cudaMemcpyAsync(dst, cd->idx.p, n, cudaMemcpyDefault, st)); break;
+    }
+    LIC_CUDA_TRY(cudaStreamSynchronize(st));
+    return LIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,32 @@
+// Tensor-core (tcgen05) implicit-GEMM convolution: interface used by the
+// layer runner.  The kernels live in conv_tc.cu.
+#pragma once
+
+#include "lic_internal.h"
+
+namespace lic {
+namespace tc {
+
+// Weights of one GEMM launch, split for 3xTF32 (w = hi + lo, both exactly
+// representable in TF32) and laid out as the B operand of the kernel.
+struct TcWeights {
+    void *hi = nullptr, *lo = nullptr;
+    int Cout = 0, T = 0, Cin = 0, Npad = 0, Kpad = 0;
+    bool valid = false;
+    TcWeights() = default;
+    TcWeights(const TcWeights &) = delete;
+    TcWeights &operator=(const TcWeights &) = delete;
+    ~TcWeights();
+};
+
+// Build the tensor-core copy of weights [Cout][T][Cin] (host float32).
+// Leaves valid = false when the shape is not handled by the kernels.
+void build_weights(const float *w, int Cout, int T, int Cin, TcWeights *out);
+
+// Whether the tensor-core kernel handles this launch.
+bool can_run(const ConvDesc &d, const TcWeights &w);
+
+void launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
+
+}  // namespace tc
+}  // namespace lic

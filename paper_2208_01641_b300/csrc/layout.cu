@@ -1,0 +1,196 @@
+// Layout, quantization and scale-index kernels (all HBM-bound, elementwise).
+//
+//  * pad/pack: the codec input is replicate-padded on the bottom/right to
+//    multiples of 64 (the four stride-2 stages of g_a and two of h_a) and
+//    turned from NCHW into the NHWC layout of the conv kernels.
+//  * crop/unpack: clamp the reconstruction to [0, 1], crop, back to NCHW.
+//  * quantize (Sec. III-A: "quantization of y with a channel-wise mean"):
+//    s = rint(fl32(y - mu_c)), round half to even, in float32.
+//  * scale index (the Gaussian conditional of [2]): the smallest of the 64
+//    table scales that is >= max(sigma, 0.11).
+#include "lic_internal.h"
+
+namespace lic {
+namespace {
+
+__constant__ float c_scales[64];
+
+__global__ void pad_pack_kernel(const float *__restrict__ f, int B, int H, int W, int Hp, int Wp,
+                                float *__restrict__ out) {
+    int64_t n = (int64_t)B * Hp * Wp;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int x = (int)(p % Wp);
+        int y = (int)((p / Wp) % Hp);
+        int b = (int)(p / ((int64_t)Wp * Hp));
+        int ys = min(y, H - 1), xs = min(x, W - 1);
+        const float *src = f + (int64_t)b * 3 * H * W + (int64_t)ys * W + xs;
+        out[p * 3 + 0] = src[0];
+        out[p * 3 + 1] = src[(int64_t)H * W];
+        out[p * 3 + 2] = src[2 * (int64_t)H * W];
+    }
+}
+
+__global__ void crop_unpack_kernel(const float *__restrict__ x, int B, int Hp, int Wp, int H, int W,
+                                   float *__restrict__ f) {
+    int64_t n = (int64_t)B * 3 * H * W;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int xx = (int)(e % W);
+        int yy = (int)((e / W) % H);
+        int c = (int)((e / ((int64_t)W * H)) % 3);
+        int b = (int)(e / ((int64_t)W * H * 3));
+        float v = x[(((int64_t)b * Hp + yy) * Wp + xx) * 3 + c];
+        f[e] = fminf(fmaxf(v, 0.f), 1.f);
+    }
+}
+
+// 32 x 32 tiled transposes between [B][P][C] (NHWC, P = H*W) and [B][C][P].
+template <typename Fn>
+__device__ __forceinline__ void tile_nhwc_to_nchw(int B, int P, int C, Fn fn) {
+    // blockIdx.x: tile of P, blockIdx.y: tile of C, blockIdx.z: batch; 32x8 threads
+    __shared__ float tile[32][33];
+    (void)B;
+    int b = blockIdx.z;
+    int p0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        int p = p0 + r, c = c0 + threadIdx.x;
+        fn.load(b, p, c, p < P && c < C, tile[r][threadIdx.x]);
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        int c = c0 + r, p = p0 + threadIdx.x;
+        if (c < C && p < P) fn.store(b, p, c, tile[threadIdx.x][r]);
+    }
+}
+
+struct CopyF {
+    const float *in;
+    float *out;
+    int P, C;
+    __device__ void load(int b, int p, int c, bool ok, float &v) const {
+        v = ok ? in[((int64_t)b * P + p) * C + c] : 0.f;
+    }
+    __device__ void store(int b, int p, int c, float v) const { out[((int64_t)b * C + c) * P + p] = v; }
+};
+
+__global__ void nhwc_to_nchw_kernel(CopyF fn, int B) { tile_nhwc_to_nchw(B, fn.P, fn.C, fn); }
+
+__global__ void nchw_to_nhwc_kernel(const float *__restrict__ in, int B, int C, int P, float *__restrict__ out) {
+    __shared__ float tile[32][33];
+    int b = blockIdx.z;
+    int p0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        int c = c0 + r, p = p0 + threadIdx.x;
+        tile[r][threadIdx.x] = (c < C && p < P) ? in[((int64_t)b * C + c) * P + p] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        int p = p0 + r, c = c0 + threadIdx.x;
+        if (c < C && p < P) out[((int64_t)b * P + p) * C + c] = tile[threadIdx.x][r];
+    }
+}
+
+__device__ __forceinline__ int32_t quantize_one(float y, float mu) {
+    float d = __fsub_rn(y, mu);
+    float r = rintf(d);
+    if (r != r) r = 0.f;
+    r = fminf(fmaxf(r, -1073741824.f), 1073741824.f);
+    return (int32_t)r;
+}
+
+struct QuantF {
+    const float *y;
+    const float *mu;
+    int32_t *s;
+    float *yhat;
+    int P, C;
+    __device__ void load(int b, int p, int c, bool ok, float &v) const {
+        if (!ok) { v = 0.f; return; }
+        int64_t i = ((int64_t)b * P + p) * C + c;
+        float m = mu ? mu[c] : 0.f;
+        int32_t q = quantize_one(y[i], m);
+        if (yhat) yhat[i] = __fadd_rn(__int2float_rn(q), m);
+        v = __int_as_float(q);
+    }
+    __device__ void store(int b, int p, int c, float v) const {
+        s[((int64_t)b * C + c) * P + p] = __float_as_int(v);
+    }
+};
+
+__global__ void quantize_kernel(QuantF fn, int B) { tile_nhwc_to_nchw(B, fn.P, fn.C, fn); }
+
+__device__ __forceinline__ uint8_t index_one(float sg) {
+    if (sg != sg) return 63;
+    sg = fmaxf(sg, c_scales[0]);
+    // smallest k with scales[k] >= sg (scales increasing), else 63
+    int lo = 0, hi = 63;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (c_scales[mid] >= sg) hi = mid; else lo = mid + 1;
+    }
+    return (uint8_t)lo;
+}
+
+struct IndexF {
+    const float *sigma;
+    uint8_t *idx;
+    float *sig_nchw;
+    int P, C;
+    __device__ void load(int b, int p, int c, bool ok, float &v) const {
+        v = ok ? sigma[((int64_t)b * P + p) * C + c] : 0.f;
+    }
+    __device__ void store(int b, int p, int c, float v) const {
+        int64_t o = ((int64_t)b * C + c) * P + p;
+        idx[o] = index_one(v);
+        if (sig_nchw) sig_nchw[o] = v;
+    }
+};
+
+__global__ void index_kernel(IndexF fn, int B) { tile_nhwc_to_nchw(B, fn.P, fn.C, fn); }
+
+int grid_for(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    return (int)(g < 148 * 32 ? (g < 1 ? 1 : g) : 148 * 32);
+}
+
+dim3 tile_grid(int B, int P, int C) { return dim3((P + 31) / 32, (C + 31) / 32, B); }
+
+}  // namespace
+
+cudaError_t upload_scale_table() {
+    float T[64];
+    scale_table(T);
+    return cudaMemcpyToSymbol(c_scales, T, sizeof(T));
+}
+
+void launch_pad_pack(const float *frames, int B, int H, int W, int Hp, int Wp, float *out, cudaStream_t st) {
+    pad_pack_kernel<<<grid_for((int64_t)B * Hp * Wp), 256, 0, st>>>(frames, B, H, W, Hp, Wp, out);
+}
+
+void launch_crop_unpack(const float *x, int B, int Hp, int Wp, int H, int W, float *frames, cudaStream_t st) {
+    crop_unpack_kernel<<<grid_for((int64_t)B * 3 * H * W), 256, 0, st>>>(x, B, Hp, Wp, H, W, frames);
+}
+
+void launch_nhwc_to_nchw(const float *in, int B, int H, int W, int C, float *out, cudaStream_t st) {
+    CopyF fn{in, out, H * W, C};
+    nhwc_to_nchw_kernel<<<tile_grid(B, H * W, C), dim3(32, 8), 0, st>>>(fn, B);
+}
+
+void launch_nchw_to_nhwc(const float *in, int B, int C, int H, int W, float *out, cudaStream_t st) {
+    nchw_to_nhwc_kernel<<<tile_grid(B, H * W, C), dim3(32, 8), 0, st>>>(in, B, C, H * W, out);
+}
+
+void launch_quantize(const float *y, int B, int HW, int C, const float *mu, int32_t *s, float *yhat,
+                     cudaStream_t st) {
+    QuantF fn{y, mu, s, yhat, HW, C};
+    quantize_kernel<<<tile_grid(B, HW, C), dim3(32, 8), 0, st>>>(fn, B);
+}
+
+void launch_scale_index(const float *sigma, int B, int HW, int C, uint8_t *idx, float *sigma_nchw,
+                        cudaStream_t st) {
+    IndexF fn{sigma, idx, sigma_nchw, HW, C};
+    index_kernel<<<tile_grid(B, HW, C), dim3(32, 8), 0, st>>>(fn, B);
+}
+
+}  // namespace lic

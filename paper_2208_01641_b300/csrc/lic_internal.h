@@ -1,0 +1,169 @@
+// Internal declarations of liblic: device data structures, kernel launchers
+// and the codec object.  Not part of the public ABI (include/lic.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/lic.h"
+
+namespace lic {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+
+// Bits of the per-codec device status word (latched by kernels, read and
+// cleared by lic_sync).
+enum : uint32_t {
+    ST_CORRUPT = 1u,   // a bitstream failed a check in the entropy decoder
+    ST_TIMEOUT = 2u,   // a bounded wait ran out
+};
+
+#define LIC_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) {                             \
+            lic::set_last_cuda_error(_e, #expr, __FILE__, __LINE__); \
+            return _e == cudaErrorMemoryAllocation ? LIC_E_OOM : LIC_E_CUDA; \
+        }                                                    \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// ---------------------------------------------------------------------------
+// entropy tables (host build, tables.cpp)
+// ---------------------------------------------------------------------------
+
+struct HostTables {
+    std::vector<float> medians;     // per entropy-bottleneck channel
+    std::vector<int32_t> lo, hi;    // per table
+    std::vector<int64_t> start;     // per table, into cdf
+    std::vector<uint32_t> cdf;      // concatenated, n+1 entries per table
+    int n_eb = 0;                   // tables [0, n_eb) are the bottleneck's
+    int n_gauss = 0;                // tables [n_eb, n_eb+64) Gaussian
+};
+
+// Build the factorized-bottleneck tables from per-channel parameter blocks
+// (58 doubles per channel) and, optionally, the 64 Gaussian tables.
+// Returns 0 or a negative LIC_E_* code.
+int build_tables(const std::vector<double> &eb_params, int channels, bool gauss, HostTables *out);
+void scale_table(float T[64]);
+
+// ---------------------------------------------------------------------------
+// conv descriptor shared by the conv kernels
+// ---------------------------------------------------------------------------
+
+enum InXform : int { IN_NONE = 0, IN_ABS = 1, IN_SQUARE = 2 };
+enum Epi : int { EPI_NONE = 0, EPI_RELU = 1, EPI_GDN = 2, EPI_IGDN = 3 };
+
+constexpr int MAX_TAPS = 25;
+
+// One implicit-GEMM convolution over NHWC float32 tensors.
+//  GEMM row r = (b, i, j) over a Gh x Gw grid; input pixel of tap t is
+//  (s*i + du[t], s*j + dv[t]) of a Hi x Wi input (zero outside); the result
+//  goes to output pixel (oym*i + oyo, oxm*j + oxo) of a Ho x Wo output.
+//  Weights: [Cout][T][Cin] float32 (K index = t*Cin + c).
+struct ConvDesc {
+    const float *in;
+    float *out;
+    const float *w;
+    const float *bias;     // [Cout] or null
+    const float *gdn_x;    // EPI_GDN/IGDN: x that the norm divides, NHWC with Cout channels
+    int B, Hi, Wi, Cin;
+    int Gh, Gw, s;
+    int Ho, Wo, Cout;
+    int oym, oyo, oxm, oxo;
+    int T;
+    int8_t du[MAX_TAPS], dv[MAX_TAPS];
+    int in_xform, epi;
+};
+
+void launch_conv_simt(const ConvDesc &d, cudaStream_t st);
+
+// Transposed conv 5x5 / stride 2 (pad 2, output padding 1) to at most 4
+// output channels, all four sub-pixel phases in one launch (the last layer
+// of g_s).  in: NHWC [B][Hi][Wi][Cin] (Cin % 32 == 0); w: [Cin][5][5][4]
+// (output channel padded to 4); out: NHWC [B][2Hi][2Wi][Cout].
+void launch_deconv_small(const float *in, int B, int Hi, int Wi, int Cin, const float *w, const float *bias,
+                         int Cout, float *out, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// elementwise / layout kernels (layout.cu)
+// ---------------------------------------------------------------------------
+
+// frames NCHW [B][3][H][W] -> NHWC [B][Hp][Wp][3], replicate padding
+void launch_pad_pack(const float *frames, int B, int H, int W, int Hp, int Wp, float *out,
+                     cudaStream_t st);
+// NHWC [B][Hp][Wp][3] -> NCHW [B][3][H][W], clamped to [0, 1]
+void launch_crop_unpack(const float *x, int B, int Hp, int Wp, int H, int W, float *frames,
+                        cudaStream_t st);
+// generic NHWC <-> NCHW float32 / int32 conversions
+void launch_nhwc_to_nchw(const float *in, int B, int H, int W, int C, float *out, cudaStream_t st);
+void launch_nchw_to_nhwc(const float *in, int B, int C, int H, int W, float *out, cudaStream_t st);
+
+// s = rint(fl32(y - mu[c])) (mu may be null), saturated to +-2^30, NaN -> 0.
+// y NHWC [B][HW][C] -> s NCHW [B][C][HW]; if yhat != null also writes the
+// dequantized value fl32(s + mu[c]) in NHWC.
+void launch_quantize(const float *y, int B, int HW, int C, const float *mu, int32_t *s,
+                     float *yhat, cudaStream_t st);
+// idx = smallest k with T[k] >= max(sigma, T[0]); NaN / > T[63] -> 63.
+// sigma NHWC [B][HW][C] -> idx NCHW [B][C][HW]; sigma_nchw (optional) copy.
+// Copies the 64 scales into the constant bank of the current device (once
+// per device, at codec creation).
+cudaError_t upload_scale_table();
+void launch_scale_index(const float *sigma, int B, int HW, int C, uint8_t *idx,
+                        float *sigma_nchw, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// entropy coder (rans.cu)
+// ---------------------------------------------------------------------------
+
+struct DevTables {
+    const uint32_t *cdf;
+    const int64_t *start;
+    const int32_t *lo, *hi;
+    int n_eb;        // bottleneck tables: table c for channel c
+    int gauss_base;  // first Gaussian table (or -1)
+};
+
+// Geometry of the substreams of one frame (identical for every frame).
+struct StreamGeom {
+    int kind;
+    int N, M;
+    int Hy, Wy;      // y latent
+    int Hz, Wz;      // z latent (hyperprior)
+    int R;           // band rows
+    int nbands;
+    int nz;          // z substreams per frame (N or 0)
+    int nsub;        // substreams per frame
+    int H, W, Hp, Wp;
+    int64_t header_bytes;  // 36 + 4 (nsub + 1)
+    int64_t cap_words;     // scratch words per substream, max over substreams
+};
+
+StreamGeom make_geom(int kind, int N, int M, int H, int W, int Hp, int Wp, int R);
+
+// Encoder: symbols NCHW (s_y [B][M][Hy][Wy], idx same, s_z [B][N][Hz][Wz])
+// -> per substream words in scratch (decoder order, right-aligned) + counts.
+void launch_rans_encode(const StreamGeom &g, int B, const DevTables &t, const int32_t *s_y,
+                        const uint8_t *idx, const int32_t *s_z, uint16_t *scratch,
+                        int64_t *counts, cudaStream_t st);
+// Containers: scans, headers and payload copy into data (frames 16-byte
+// aligned); offsets [B+1] and sizes [B] on the device.
+void launch_rans_compact(const StreamGeom &g, int B, const uint16_t *scratch,
+                         const int64_t *counts, int64_t *sub_off, int64_t *frame_bytes,
+                         int64_t *offsets, uint8_t *data, cudaStream_t st);
+// Decoder: validates headers, decodes the z substreams (part 0) or the y
+// substreams (part 1).  z: s_z NCHW + zhat NHWC (fl32(s + med)).  y: s_y
+// NCHW + yhat NHWC (factorized: fl32(s + med); hyperprior: s).
+void launch_rans_decode(const StreamGeom &g, int B, int part, const DevTables &t,
+                        const uint8_t *data, const int64_t *offsets, const int64_t *sizes,
+                        const uint8_t *idx, const float *med, int32_t *s_out, float *hat_out,
+                        uint32_t *status, cudaStream_t st);
+
+}  // namespace lic

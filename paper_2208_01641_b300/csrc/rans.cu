@@ -1,0 +1,447 @@
+// Interleaved rANS entropy coder on the GPU (integer kernels).
+//
+// The paper runs CompressAI's CPU entropy coder (Sec. IV-B) and calls
+// entropy coding the CPU-intensive part of the codec (Sec. III-A).  Here it
+// runs on the device: every substream (one z channel, or one band of R
+// latent rows of one y channel) is coded by one warp whose 32 lanes are the
+// 32 interleaved rANS states of that substream (Giesen's interleaving of
+// Duda's rANS).  Symbol i of a substream belongs to state i mod 32.
+//
+// Coder: state x in [2^16, 2^32), 16-bit renormalisation words, 16-bit CDFs.
+//   encode(start, f): if x >= f * 2^16 emit x & 0xffff, x >>= 16;
+//                     x = floor(x / f) * 2^16 + x mod f + start
+//   decode: slot = x & 0xffff -> symbol with cdf[s] <= slot < cdf[s+1];
+//           x = f * (x >> 16) + slot - start; if x < 2^16 refill one word.
+// A value outside a table's support is sent as the escape symbol followed by
+// uniform 4-bit symbols on the same state: (nibble count - 1), then the
+// nibbles of zigzag(overflow), least significant first.
+//
+// Word order (the format): the encoder walks the symbols from last to first;
+// inside a group of 32 symbols lane 31 emits first.  After the last symbol
+// the states flush from lane 31 down to 0, high half then low half.  The
+// substream is the emitted sequence reversed, so a decoder reads 32 initial
+// states (lane 0 first, low half first) and then words in symbol order.  The
+// warp reproduces that order exactly with ballots (one word per lane at
+// most) or, in groups holding an escape, with a suffix sum of word counts.
+#include "lic_internal.h"
+
+namespace lic {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WARPS = 4;
+constexpr int MAX_WORDS_PER_SYMBOL = 10;  // escape + count nibble + 8 nibbles
+constexpr uint32_t RANS_L = 1u << 16;
+
+struct SubInfo {
+    const int32_t *sym;   // first symbol of the substream
+    const uint8_t *idx;   // per-symbol scale index (hyperprior y) or null
+    int n;                // symbols
+    int table;            // fixed table (z, factorized y) when idx is null
+    int c;                // channel
+    int p0;               // first latent pixel (row0 * width) in the plane
+    bool is_z;
+};
+
+__device__ __forceinline__ SubInfo sub_info(const StreamGeom &g, int b, int q, const int32_t *s_y,
+                                            const uint8_t *idx, const int32_t *s_z, const DevTables &t) {
+    SubInfo si;
+    if (q < g.nz) {
+        int HWz = g.Hz * g.Wz;
+        si.sym = s_z ? s_z + ((int64_t)b * g.N + q) * HWz : nullptr;
+        si.idx = nullptr;
+        si.n = HWz;
+        si.table = q;
+        si.c = q;
+        si.p0 = 0;
+        si.is_z = true;
+    } else {
+        int qq = q - g.nz;
+        int c = qq / g.nbands, band = qq % g.nbands;
+        int r0 = band * g.R;
+        int rows = min(g.R, g.Hy - r0);
+        int64_t plane = ((int64_t)b * g.M + c) * g.Hy * g.Wy;
+        si.p0 = r0 * g.Wy;
+        si.sym = s_y ? s_y + plane + si.p0 : nullptr;
+        si.idx = (g.kind == LIC_HYPERPRIOR && idx) ? idx + plane + si.p0 : nullptr;
+        si.n = rows * g.Wy;
+        si.table = (g.kind == LIC_HYPERPRIOR) ? -1 : c;
+        si.c = c;
+        si.is_z = false;
+    }
+    return si;
+}
+
+__device__ __forceinline__ int nibble_count(uint32_t v) {
+    int nn = 1;
+    while (nn < 8 && (v >> (4 * nn)) != 0u) ++nn;
+    return nn;
+}
+
+// One encode step; returns true (and the word) when it renormalised.
+__device__ __forceinline__ bool enc_put(uint32_t &x, uint32_t start, uint32_t f, uint16_t &word) {
+    bool emit = x >= (f << 16);
+    if (emit) {
+        word = (uint16_t)(x & 0xffffu);
+        x >>= 16;
+    }
+    uint32_t q = x / f;
+    x = (q << 16) + (x - q * f) + start;
+    return emit;
+}
+
+__global__ void __launch_bounds__(WARPS * 32) rans_encode_kernel(const StreamGeom g, int B, const DevTables t,
+                                                                 const int32_t *__restrict__ s_y,
+                                                                 const uint8_t *__restrict__ idx,
+                                                                 const int32_t *__restrict__ s_z,
+                                                                 uint16_t *__restrict__ scratch,
+                                                                 int64_t *__restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (warp >= (int64_t)B * g.nsub) return;
+    const int b = (int)(warp / g.nsub), q = (int)(warp % g.nsub);
+    const SubInfo si = sub_info(g, b, q, s_y, idx, s_z, t);
+    const int64_t cap = g.cap_words;
+    uint16_t *out = scratch + warp * cap;  // emitted word k -> out[cap - 1 - k]
+    uint32_t x = RANS_L;
+    int64_t E = 0;
+
+    const int ngroups = (si.n + 31) / 32;
+    for (int grp = ngroups - 1; grp >= 0; --grp) {
+        const int i = grp * 32 + lane;
+        const bool active = i < si.n;
+        int tab = 0, lo = 0, hi = 0, sym = 0, esc = 0;
+        uint32_t v = 0;
+        int32_t s = 0;
+        if (active) {
+            s = si.sym[i];
+            tab = si.idx ? t.gauss_base + si.idx[i] : si.table;
+            lo = t.lo[tab];
+            hi = t.hi[tab];
+            esc = lo + hi + 1;
+            if (s >= -lo && s <= hi) {
+                sym = s + lo;
+            } else {
+                sym = esc;
+                v = (s > hi) ? 2u * (uint32_t)(s - hi - 1) : 2u * (uint32_t)(-s - lo - 1) + 1u;
+            }
+        }
+        const bool is_esc = active && sym == esc;
+        if (!__any_sync(FULL, is_esc)) {
+            // fast path: at most one word per lane; lanes above come first
+            uint16_t w = 0;
+            bool emit = false;
+            if (active) {
+                const uint32_t *cdf = t.cdf + t.start[tab];
+                uint32_t st = cdf[sym], f = cdf[sym + 1] - st;
+                emit = enc_put(x, st, f, w);
+            }
+            unsigned m = __ballot_sync(FULL, emit);
+            if (emit) {
+                int before = __popc(m & ~((2u << lane) - 1u));  // lanes > lane
+                out[cap - 1 - (E + before)] = w;
+            }
+            E += __popc(m);
+        } else {
+            uint16_t w[MAX_WORDS_PER_SYMBOL];
+            int cnt = 0;
+            if (active) {
+                if (is_esc) {
+                    int nn = nibble_count(v);
+                    for (int j = nn - 1; j >= 0; --j)
+                        if (enc_put(x, 4096u * ((v >> (4 * j)) & 15u), 4096u, w[cnt])) ++cnt;
+                    if (enc_put(x, 4096u * (uint32_t)(nn - 1), 4096u, w[cnt])) ++cnt;
+                }
+                const uint32_t *cdf = t.cdf + t.start[tab];
+                uint32_t st = cdf[sym], f = cdf[sym + 1] - st;
+                if (enc_put(x, st, f, w[cnt])) ++cnt;
+            }
+            // suffix sum over lanes: words of lanes > lane come first
+            int incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                int o = __shfl_down_sync(FULL, incl, d);
+                if (lane + d < 32) incl += o;
+            }
+            int before = incl - cnt;
+            int total = __shfl_sync(FULL, incl, 0);
+            for (int j = 0; j < cnt; ++j) out[cap - 1 - (E + before + j)] = w[j];
+            E += total;
+        }
+    }
+    // flush: lane 31 first, high half then low half
+    int64_t k = E + 2 * (31 - lane);
+    out[cap - 1 - k] = (uint16_t)(x >> 16);
+    out[cap - 2 - k] = (uint16_t)(x & 0xffffu);
+    E += 64;
+    if (lane == 0) counts[warp] = E;
+}
+
+// Per frame: exclusive scan of substream word counts, frame size in bytes.
+__global__ void rans_scan_kernel(const StreamGeom g, const int64_t *__restrict__ counts,
+                                 int64_t *__restrict__ sub_off, int64_t *__restrict__ frame_bytes) {
+    __shared__ int64_t part[1024];
+    __shared__ int64_t carry;
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < g.nsub; base += blockDim.x) {
+        int q = base + threadIdx.x;
+        int64_t v = q < g.nsub ? counts[(int64_t)b * g.nsub + q] : 0;
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+            int64_t o = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0;
+            __syncthreads();
+            part[threadIdx.x] += o;
+            __syncthreads();
+        }
+        if (q < g.nsub) sub_off[(int64_t)b * g.nsub + q] = carry + part[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) frame_bytes[b] = g.header_bytes + 2 * carry;
+}
+
+// Frame placement: 16-byte aligned starts.  offsets has B+1 entries, then
+// sizes (B entries) follow it in the same allocation.
+__global__ void frame_place_kernel(int B, const int64_t *__restrict__ frame_bytes, int64_t *__restrict__ offsets) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t o = 0;
+    for (int b = 0; b < B; ++b) {
+        offsets[b] = o;
+        offsets[B + 1 + b] = frame_bytes[b];
+        o += (frame_bytes[b] + 15) / 16 * 16;
+    }
+    offsets[B] = o;
+}
+
+__global__ void __launch_bounds__(WARPS * 32) rans_write_kernel(const StreamGeom g, int B,
+                                                                const uint16_t *__restrict__ scratch,
+                                                                const int64_t *__restrict__ counts,
+                                                                const int64_t *__restrict__ sub_off,
+                                                                const int64_t *__restrict__ offsets,
+                                                                uint8_t *__restrict__ data) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (warp >= (int64_t)B * g.nsub) return;
+    const int b = (int)(warp / g.nsub), q = (int)(warp % g.nsub);
+    uint8_t *frame = data + offsets[b];
+    uint32_t *hdr = reinterpret_cast<uint32_t *>(frame);
+    const int64_t nw = counts[warp];
+    const int64_t off = sub_off[warp];
+    if (q == 0 && lane == 0) {
+        hdr[0] = 0x3143494Cu;  // "LIC1"
+        hdr[1] = 1u | ((uint32_t)g.kind << 16);
+        hdr[2] = (uint32_t)g.N | ((uint32_t)g.M << 16);
+        hdr[3] = (uint32_t)g.H;
+        hdr[4] = (uint32_t)g.W;
+        hdr[5] = (uint32_t)g.Hp;
+        hdr[6] = (uint32_t)g.Wp;
+        hdr[7] = (uint32_t)g.R;
+        hdr[8] = (uint32_t)g.nsub;
+    }
+    if (lane == 0) {
+        hdr[9 + q] = (uint32_t)off;
+        if (q == g.nsub - 1) hdr[9 + g.nsub] = (uint32_t)(off + nw);
+    }
+    uint16_t *dst = reinterpret_cast<uint16_t *>(frame + g.header_bytes) + off;
+    const uint16_t *src = scratch + warp * g.cap_words + (g.cap_words - nw);
+    for (int64_t k = lane; k < nw; k += 32) dst[k] = src[k];
+}
+
+__device__ __forceinline__ uint32_t rd_u32(const uint8_t *p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+__device__ __forceinline__ int find_symbol(const uint32_t *cdf, int n, uint32_t slot) {
+    // largest s in [0, n) with cdf[s] <= slot (cdf[0] = 0, cdf[n] = 2^16)
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (cdf[mid] <= slot) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(WARPS * 32) rans_decode_kernel(const StreamGeom g, int B, int part,
+                                                                 const DevTables t,
+                                                                 const uint8_t *__restrict__ data,
+                                                                 const int64_t *__restrict__ offsets,
+                                                                 const int64_t *__restrict__ sizes,
+                                                                 const uint8_t *__restrict__ idx,
+                                                                 const float *__restrict__ med,
+                                                                 int32_t *__restrict__ s_out,
+                                                                 float *__restrict__ hat_out,
+                                                                 uint32_t *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int nq = part == 0 ? g.nz : g.nsub - g.nz;
+    const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (warp >= (int64_t)B * nq) return;
+    const int b = (int)(warp / nq);
+    const int q = (int)(warp % nq) + (part == 0 ? 0 : g.nz);
+
+    // ---- header checks (bounded, never trust the stream) ----
+    const int64_t fsize = sizes[b];
+    const uint8_t *frame = data + offsets[b];
+    bool bad = (offsets[b] & 1) != 0 || fsize < g.header_bytes;
+    if (!bad) {
+        bad = rd_u32(frame) != 0x3143494Cu || rd_u32(frame + 4) != (1u | ((uint32_t)g.kind << 16)) ||
+              rd_u32(frame + 8) != ((uint32_t)g.N | ((uint32_t)g.M << 16)) ||
+              rd_u32(frame + 12) != (uint32_t)g.H || rd_u32(frame + 16) != (uint32_t)g.W ||
+              rd_u32(frame + 20) != (uint32_t)g.Hp || rd_u32(frame + 24) != (uint32_t)g.Wp ||
+              rd_u32(frame + 28) != (uint32_t)g.R || rd_u32(frame + 32) != (uint32_t)g.nsub;
+    }
+    int64_t w0 = 0, w1 = 0;
+    if (!bad) {
+        int64_t avail = (fsize - g.header_bytes) / 2;
+        w0 = rd_u32(frame + 36 + 4 * (int64_t)q);
+        w1 = rd_u32(frame + 36 + 4 * (int64_t)(q + 1));
+        int64_t wend = rd_u32(frame + 36 + 4 * (int64_t)g.nsub);
+        bad = w1 < w0 || w1 > wend || wend > avail || (w1 - w0) < 64;
+    }
+    if (bad) {
+        if (lane == 0) atomicOr(status, ST_CORRUPT);
+        return;
+    }
+    const uint16_t *words = reinterpret_cast<const uint16_t *>(frame + g.header_bytes) + w0;
+    const int64_t nw = w1 - w0;
+
+    const SubInfo si = sub_info(g, b, q, nullptr, idx, nullptr, t);
+    const int C = si.is_z ? g.N : g.M;
+    const int HW = si.is_z ? g.Hz * g.Wz : g.Hy * g.Wy;
+    int32_t *sdst = s_out + ((int64_t)b * C + si.c) * HW + si.p0;
+    float *hdst = hat_out ? hat_out + ((int64_t)b * HW + si.p0) * C + si.c : nullptr;
+    const float mu = (si.is_z || g.kind == LIC_FACTORIZED) ? med[si.c] : 0.f;
+
+    uint32_t x = (uint32_t)words[2 * lane] | ((uint32_t)words[2 * lane + 1] << 16);
+    int64_t pos = 64;
+    bool corrupt = false;
+    const int ngroups = (si.n + 31) / 32;
+    for (int grp = 0; grp < ngroups; ++grp) {
+        const int i = grp * 32 + lane;
+        const bool active = i < si.n;
+        int tab = 0, lo = 0, nt = 2, sym = 0;
+        bool need = false;
+        if (active) {
+            tab = si.idx ? t.gauss_base + si.idx[i] : si.table;
+            lo = t.lo[tab];
+            nt = lo + t.hi[tab] + 2;
+            const uint32_t *cdf = t.cdf + t.start[tab];
+            uint32_t slot = x & 0xffffu;
+            sym = find_symbol(cdf, nt, slot);
+            uint32_t st = cdf[sym], f = cdf[sym + 1] - st;
+            x = f * (x >> 16) + slot - st;
+            need = x < RANS_L;
+        }
+        const bool is_esc = active && sym == nt - 1;
+        int32_t val = sym - lo;
+        if (!__any_sync(FULL, is_esc)) {
+            unsigned m = __ballot_sync(FULL, need);
+            if (need) {
+                int64_t p = pos + __popc(m & ((1u << lane) - 1u));
+                if (p < nw) x = (x << 16) | words[p]; else corrupt = true;
+            }
+            pos += __popc(m);
+        } else {
+            // serial over lanes: an escape's nibbles sit between its word and
+            // the next lane's word
+            for (int l = 0; l < 32; ++l) {
+                if (lane == l && active) {
+                    if (need) {
+                        if (pos < nw) x = (x << 16) | words[pos]; else corrupt = true;
+                        ++pos;
+                    }
+                    if (is_esc && !corrupt) {
+                        uint32_t v = 0, nn = 0;
+                        for (int j = -1; j < (int)nn && !corrupt; ++j) {
+                            uint32_t slot = x & 0xffffu;
+                            uint32_t nib = slot >> 12;
+                            x = 4096u * (x >> 16) + slot - 4096u * nib;
+                            if (x < RANS_L) {
+                                if (pos < nw) x = (x << 16) | words[pos]; else corrupt = true;
+                                ++pos;
+                            }
+                            if (j < 0) {
+                                nn = nib + 1;
+                                if (nn > 8) corrupt = true;
+                            } else {
+                                v |= nib << (4 * j);
+                            }
+                        }
+                        int64_t r = (v & 1u) ? -(int64_t)lo - 1 - (int64_t)(v >> 1)
+                                             : (int64_t)(nt - 2 - lo) + 1 + (int64_t)(v >> 1);
+                        if (r > 1073741824LL || r < -1073741824LL) corrupt = true;
+                        val = (int32_t)r;
+                    }
+                }
+                pos = __shfl_sync(FULL, pos, l);
+            }
+        }
+        if (__any_sync(FULL, corrupt)) {
+            if (lane == 0) atomicOr(status, ST_CORRUPT);
+            return;
+        }
+        if (active) {
+            sdst[i] = val;
+            if (hdst) hdst[(int64_t)i * C] = __fadd_rn(__int2float_rn(val), mu);
+        }
+    }
+}
+
+int64_t blocks_for(int64_t warps) { return (warps + WARPS - 1) / WARPS; }
+
+}  // namespace
+
+StreamGeom make_geom(int kind, int N, int M, int H, int W, int Hp, int Wp, int R) {
+    StreamGeom g{};
+    g.kind = kind;
+    g.N = N;
+    g.M = M;
+    g.H = H;
+    g.W = W;
+    g.Hp = Hp;
+    g.Wp = Wp;
+    g.Hy = Hp / 16;
+    g.Wy = Wp / 16;
+    g.Hz = Hp / 64;
+    g.Wz = Wp / 64;
+    g.R = R;
+    g.nbands = (g.Hy + R - 1) / R;
+    g.nz = kind == LIC_HYPERPRIOR ? N : 0;
+    g.nsub = g.nz + M * g.nbands;
+    g.header_bytes = 36 + 4 * (int64_t)(g.nsub + 1);
+    int64_t nmax = (int64_t)std::min(R, g.Hy) * g.Wy;
+    if (kind == LIC_HYPERPRIOR) nmax = std::max<int64_t>(nmax, (int64_t)g.Hz * g.Wz);
+    g.cap_words = MAX_WORDS_PER_SYMBOL * nmax + 64;
+    return g;
+}
+
+void launch_rans_encode(const StreamGeom &g, int B, const DevTables &t, const int32_t *s_y, const uint8_t *idx,
+                        const int32_t *s_z, uint16_t *scratch, int64_t *counts, cudaStream_t st) {
+    int64_t warps = (int64_t)B * g.nsub;
+    rans_encode_kernel<<<(unsigned)blocks_for(warps), WARPS * 32, 0, st>>>(g, B, t, s_y, idx, s_z, scratch, counts);
+}
+
+void launch_rans_compact(const StreamGeom &g, int B, const uint16_t *scratch, const int64_t *counts,
+                         int64_t *sub_off, int64_t *frame_bytes, int64_t *offsets, uint8_t *data,
+                         cudaStream_t st) {
+    rans_scan_kernel<<<B, 1024, 0, st>>>(g, counts, sub_off, frame_bytes);
+    frame_place_kernel<<<1, 32, 0, st>>>(B, frame_bytes, offsets);
+    int64_t warps = (int64_t)B * g.nsub;
+    rans_write_kernel<<<(unsigned)blocks_for(warps), WARPS * 32, 0, st>>>(g, B, scratch, counts, sub_off, offsets,
+                                                                          data);
+}
+
+void launch_rans_decode(const StreamGeom &g, int B, int part, const DevTables &t, const uint8_t *data,
+                        const int64_t *offsets, const int64_t *sizes, const uint8_t *idx, const float *med,
+                        int32_t *s_out, float *hat_out, uint32_t *status, cudaStream_t st) {
+    int nq = part == 0 ? g.nz : g.nsub - g.nz;
+    int64_t warps = (int64_t)B * nq;
+    if (warps == 0) return;
+    rans_decode_kernel<<<(unsigned)blocks_for(warps), WARPS * 32, 0, st>>>(g, B, part, t, data, offsets, sizes, idx,
+                                                                           med, s_out, hat_out, status);
+}
+
+}  // namespace lic
