@@ -215,6 +215,41 @@ int lic_encode_latents(lic_codec *codec, const int32_t *s_y, const uint8_t *idx,
                        const int32_t *s_z, int B, int H, int W, int Hy, int Wy,
                        lic_bitstreams *out, void *stream);
 
+/* Working memory of lic_encode_latents_noalloc: a fixed array compiled into
+ * the library, present on every device that loads it until the process
+ * exits. */
+#define LIC_NOALLOC_SCRATCH_BYTES (32ll << 20)
+
+/* lic_encode_latents without any allocation (the paper has no counterpart:
+ * it is an interface for callers that cannot allocate device memory when
+ * they encode -- a real-time thread that must not stall in cudaMalloc or
+ * cudaFree, which wait on the device; a host that gives all device memory
+ * to its own fixed-budget allocator; a plugin handed buffers by its host).
+ * Produces the same frame containers as lic_encode_latents, byte for byte,
+ * from the same inputs (device pointers, NCHW, as there).  Outputs are the
+ * caller's device buffers:
+ *   data      containers, frame i at byte d_layout[i]; data_cap bytes, at
+ *             least B * (36 + 4 (nsub+1) + 2 nsub (10 n_max + 64) + 16)
+ *             (the worst case for escapes in every symbol; nsub substreams
+ *             per frame, n_max symbols in the longest one), else INVALID_ARG;
+ *   d_layout  2B+1 int64: byte offsets of the frames [0..B] followed by
+ *             their sizes [B+1..2B].
+ * Working memory comes from one array of LIC_NOALLOC_SCRATCH_BYTES inside
+ * the library; a batch needing more (about 2 nsub (10 n_max + 64) B bytes)
+ * returns UNSUPPORTED before anything is launched.  The call allocates
+ * nothing and calls no allocating routine.  Its first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All
+ * calls share the one array and it keeps the previous call's contents
+ * (none of which a call reads), so calls whose work overlaps on the GPU --
+ * on two streams, or from two host threads -- race and corrupt each other:
+ * order them on one stream or synchronize between them.  Stream-ordered;
+ * returns once the work is enqueued. */
+int lic_encode_latents_noalloc(lic_codec *codec, const int32_t *s_y, const uint8_t *idx,
+                               const int32_t *s_z, int B, int H, int W, int Hy, int Wy,
+                               uint8_t *data, int64_t data_cap, int64_t *d_layout,
+                               void *stream);
+
 /* Entropy-decode the symbols of in->count frames of size H x W (device
  * int32 outputs; s_z ignored for the factorized codec).  The hyperprior
  * path runs h_s on the decoded z to obtain the indices of y, as the

@@ -32,8 +32,10 @@ EXPORTED = [
     "lic_bitstreams_download", "lic_decoded_shape", "lic_read_tensor", "lic_analysis",
     "lic_synthesis", "lic_hyper_analysis", "lic_hyper_synthesis", "lic_encode_latents",
     "lic_decode_latents", "lic_build_tables", "lic_scale_table", "lic_strerror",
-    "lic_profile_enable", "lic_profile_report", "lic_launch_count",
+    "lic_profile_enable", "lic_profile_report", "lic_launch_count", "lic_encode_latents_noalloc",
 ]
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class LicError(RuntimeError):
@@ -90,6 +92,7 @@ def _lib():
         L.lic_hyper_synthesis.argtypes = [vp, vp, i, i, i, vp, vp, vp]
         L.lic_encode_latents.argtypes = [vp, vp, vp, vp, i, i, i, i, i, ctypes.POINTER(_Bitstreams), vp]
         L.lic_decode_latents.argtypes = [vp, ctypes.POINTER(_Bitstreams), i, i, vp, vp, vp]
+        L.lic_encode_latents_noalloc.argtypes = [vp, vp, vp, vp, i, i, i, i, i, vp, i64, vp, vp]
         L.lic_build_tables.argtypes = [ctypes.POINTER(_Weights), i, i, i64, vp, vp, vp, vp, vp]
         L.lic_scale_table.argtypes = [vp]
         L.lic_scale_table.restype = None
@@ -313,6 +316,14 @@ class Codec:
                                          _ptr(s_z) if s_z is not None else None, B, H, W, Hy, Wy,
                                          ctypes.byref(s), st), "lic_encode_latents")
         return Bitstreams(self, s, st)
+
+    def encode_latents_noalloc(self, s_y, idx, s_z, H: int, W: int, data, layout, stream=None) -> int:
+        """lic_encode_latents_noalloc into caller buffers (data: device
+        uint8, layout: device int64[2B+1]); returns the ABI's code."""
+        B, _, Hy, Wy = s_y.shape
+        return _lib().lic_encode_latents_noalloc(
+            self.h, _ptr(s_y), _ptr(idx) if idx is not None else None, _ptr(s_z) if s_z is not None else None,
+            B, H, W, Hy, Wy, _ptr(data), data.numel(), _ptr(layout), _stream(stream))
 
     def decode_latents(self, bs, H: int, W: int, s_y, s_z=None, stream=None):
         s = bs.s if isinstance(bs, Bitstreams) else bs

@@ -610,6 +610,18 @@ int copy_in(lic_codec *cd, DevBuf &stage, const void *src, size_t bytes, const v
 }  // namespace
 }  // namespace lic
 
+namespace lic {
+int codec_entropy_view(const lic_codec *cd, CodecEntropyView *out) {
+    if (!cd || !out) return LIC_E_INVALID_ARG;
+    out->kind = cd->kind;
+    out->N = cd->N;
+    out->M = cd->M;
+    out->R = cd->opt.band_rows;
+    out->tables = cd->dt;
+    return LIC_OK;
+}
+}  // namespace lic
+
 using namespace lic;
 
 extern "C" {

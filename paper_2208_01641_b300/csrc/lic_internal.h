@@ -166,4 +166,12 @@ void launch_rans_decode(const StreamGeom &g, int B, int part, const DevTables &t
                         const uint8_t *idx, const float *med, int32_t *s_out, float *hat_out,
                         uint32_t *status, cudaStream_t st);
 
+// Read-only view of a codec's entropy-coding state, for entry points that
+// live outside api.cu.
+struct CodecEntropyView {
+    int kind, N, M, R;
+    DevTables tables;
+};
+int codec_entropy_view(const lic_codec *codec, CodecEntropyView *out);
+
 }  // namespace lic
