@@ -298,6 +298,7 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
     d.w = op.w.as<float>();
     d.bias = L.bias.as<float>();
     d.gdn_x = nullptr;
+    d.status = cd->status.as<uint32_t>();
     d.B = B;
     d.Hi = Hi;
     d.Wi = Wi;
@@ -336,8 +337,7 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
     std::string nm = L.name + (L.deconv ? ".p" + std::to_string(2 * op.py + op.px) : std::string()) +
                      (use_tc ? ":tc" : ":simt");
     timed(const_cast<lic_codec *>(cd), nm, flop, bytes, 1, st, [&] {
-        if (use_tc) tc::launch(d, op.tcw, st);
-        else launch_conv_simt(d, st);
+        if (!use_tc || !tc::launch(d, op.tcw, st)) launch_conv_simt(d, st);
     });
 }
 
@@ -370,6 +370,7 @@ void run_gdn(const lic_codec *cd, const Gdn &G, const float *in, int B, int H, i
     d.w = G.gamma.as<float>();
     d.bias = G.beta.as<float>();
     d.gdn_x = in;
+    d.status = cd->status.as<uint32_t>();
     d.B = B;
     d.Hi = H;
     d.Wi = W;
@@ -389,8 +390,7 @@ void run_gdn(const lic_codec *cd, const Gdn &G, const float *in, int B, int H, i
     const bool use_tc = cd->opt.conv_impl != LIC_CONV_SIMT && tc::can_run(d, G.tcw);
     timed(const_cast<lic_codec *>(cd), G.name + (use_tc ? ":tc" : ":simt"), 2.0 * rows * G.C * G.C,
           4.0 * (2.0 * rows * G.C + (double)G.C * G.C), 1, st, [&] {
-              if (use_tc) tc::launch(d, G.tcw, st);
-              else launch_conv_simt(d, st);
+              if (!use_tc || !tc::launch(d, G.tcw, st)) launch_conv_simt(d, st);
           });
 }
 

@@ -1,25 +1,659 @@
-// Tensor-core (tcgen05) implicit-GEMM convolution -- not built yet; every
-// launch is reported as unsupported so the CUDA-core kernels run.
+// Tensor-core (tcgen05) implicit-GEMM convolution for sm_103a, FP32-accurate
+// through 3xTF32.
+//
+// The conv-like steps of g_a, g_s, h_a, h_s (Ballé 2017 [1], 2018 [2]) and the
+// channel sums of GDN / IGDN [9] are dense contractions: GEMM rows are output
+// pixels, columns output channels, K = taps x input channels.  One CTA owns
+// a tile of 128 output pixels x all Cout channels:
+//
+//   warp 0      TMA producer: per K chunk (one tap, 32 input channels) a
+//               128 x 32 float32 activation box and the 32-wide slices of
+//               the split weights (hi, lo), 128-byte swizzled, into a stage
+//   warp 1      allocates TMEM; one lane issues, per 8-wide K step,
+//               D += Ahi*Bhi + Ahi*Blo + Alo*Bhi (kind::tf32) and commits each
+//               stage back to the producer
+//   warps 2..9  split each activation box in place into TF32 hi and lo parts
+//               (x = hi + lo, both TF32-exact), fold partial sums (below),
+//               then run the epilogue (bias, ReLU or GDN / IGDN)
+//
+// Dropping only Alo*Blo leaves a relative product error of about 2^-21.
+//
+// Accumulation: the tensor core adds each MMA's products into the TMEM
+// accumulator with truncation, so one accumulator taking all K steps of a
+// 3200-long reduction drifts toward zero by ~1e-5 relative.  The K chunks are
+// therefore summed in groups of FOLD: each group into one of two TMEM partial
+// buffers (ping-pong), and the epilogue warps fold every finished partial
+// into a float32 master sum in registers with round-to-nearest adds, one
+// group behind the MMAs so the folds overlap the main loop.
+//
+// The activation boxes are plain tiled TMA loads with out-of-range zero fill,
+// which implements the zero padding of the convolution:
+//   * stride 2: the NHWC input viewed as (2C, W/2, 2, H/2, B) -- an input
+//     pixel pair shares one "row" of 2C values, and rows of one parity are
+//     contiguous -- so input (2i + du, 2j + dv) for an R x Wt block of
+//     outputs is one box at (wp*C + c0, j0 + (dv >> 1), du & 1, i0 + (du >> 1), b);
+//   * stride 1 (3x3 convs, sub-pixel phases of the transposed convs):
+//     (C, W, H, B) at (c0, j0 + dv, i0 + du, b);
+//   * 1x1 (GDN): (C, rows) at (c0, p0).
+// Every wait on an mbarrier is bounded; a wait that runs out latches
+// ST_TIMEOUT in the codec status word and the CTA winds down.
+#include <cuda.h>
+
+#include <cstring>
+#include <mutex>
+
 #include "conv_tc.h"
 
 namespace lic {
 namespace tc {
+namespace {
+
+constexpr int BLOCK_M = 128;
+constexpr int KCH = 32;                          // K chunk: 32 float32 = one 128-byte swizzle row
+constexpr int A_BYTES = BLOCK_M * KCH * 4;       // 16 KB
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int FOLD = 4;                          // K chunks per TMEM partial sum
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_THREADS = EPI_WARPS * 32;
+
+enum Mode : int { MODE_S2 = 0, MODE_S1 = 1, MODE_FLAT = 2 };
+
+struct Params {
+    float *out;
+    const float *bias;
+    const float *gdn_x;
+    uint32_t *status;
+    int mode, T, Cin, cpt;        // cpt: K chunks per tap
+    int Gh, Gw, R, Wt, tiles_x, tiles_y, B;
+    int64_t rows;                 // MODE_FLAT: total pixels
+    int Ho, Wo, Cout;
+    int oym, oyo, oxm, oxo;
+    int epi, in_xform;
+    int kchunks;
+    uint32_t tmem_cols;
+    int8_t du[MAX_TAPS], dv[MAX_TAPS];
+};
+
+// ------------------------------------------------------------------ PTX
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false if the phase did not complete within WAIT_CYCLES.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, uint64_t *bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tm, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+        "%6}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *tm, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+        "%6, %7}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_128B).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;            // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1u << 46;            // descriptor version
+    d |= (uint64_t)2u << 61;            // SWIZZLE_128B
+    return d;
+}
+
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4)                       // D: f32
+           | (2u << 7) | (2u << 10)        // A, B: tf32
+           | ((uint32_t)(N >> 3) << 17)    // N / 8
+           | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+// ------------------------------------------------------------------ kernel
+
+template <int STAGES, int HALF>  // HALF: 32-column blocks per epilogue thread (Cout = 64 * HALF)
+__global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                      const __grid_constant__ CUtensorMap tmBh,
+                                                                      const __grid_constant__ CUtensorMap tmBl,
+                                                                      const __grid_constant__ Params p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int COUT = 64 * HALF;
+    constexpr int B_BYTES = COUT * KCH * 4;
+    constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *full = bars, *conv = bars + STAGES, *empty = bars + 2 * STAGES;
+    uint64_t *pfull = bars + 3 * STAGES, *pempty = pfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(pempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int groups = (p.kchunks + FOLD - 1) / FOLD;
+
+    int b = 0, i0 = 0, j0 = 0;
+    int64_t p0 = 0;
+    if (p.mode == MODE_FLAT) {
+        p0 = (int64_t)blockIdx.x * BLOCK_M;
+    } else {
+        int t = blockIdx.x;
+        const int tx = t % p.tiles_x;
+        t /= p.tiles_x;
+        const int ty = t % p.tiles_y;
+        b = t / p.tiles_y;
+        i0 = ty * p.R;
+        j0 = tx * p.Wt;
+    }
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], EPI_THREADS);
+            mbar_init(&empty[s], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&pfull[q], 1);
+            mbar_init(&pempty[q], EPI_THREADS);
+        }
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, p.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto stage_a = [&](int s) { return smem + s * STAGE_BYTES; };
+    auto stage_alo = [&](int s) { return smem + s * STAGE_BYTES + A_BYTES; };
+    auto stage_bh = [&](int s) { return smem + s * STAGE_BYTES + 2 * A_BYTES; };
+    auto stage_bl = [&](int s) { return smem + s * STAGE_BYTES + 2 * A_BYTES + B_BYTES; };
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(p.status, ST_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            const uint32_t tx_bytes = A_BYTES + 2 * B_BYTES;
+            int issued = 0;
+            for (int kc = 0; kc < p.kchunks && !*abort_flag; ++kc) {
+                const int s = kc % STAGES;
+                const uint32_t ph = (kc / STAGES) & 1;
+                if (!mbar_wait(&empty[s], ph ^ 1)) {
+                    fail();
+                    break;
+                }
+                const int t = kc / p.cpt;
+                const int c0 = (kc % p.cpt) * KCH;
+                mbar_expect_tx(&full[s], tx_bytes);
+                if (p.mode == MODE_S2) {
+                    const int du = p.du[t], dv = p.dv[t];
+                    tma_load_5d(stage_a(s), &tmA, &full[s], (dv & 1) * p.Cin + c0, j0 + (dv >> 1), du & 1,
+                                i0 + (du >> 1), b);
+                } else if (p.mode == MODE_S1) {
+                    tma_load_4d(stage_a(s), &tmA, &full[s], c0, j0 + p.dv[t], i0 + p.du[t], b);
+                } else {
+                    tma_load_2d(stage_a(s), &tmA, &full[s], c0, (int)p0);
+                }
+                tma_load_2d(stage_bh(s), &tmBh, &full[s], kc * KCH, 0);
+                tma_load_2d(stage_bl(s), &tmBl, &full[s], kc * KCH, 0);
+                issued = kc + 1;
+            }
+            if (*abort_flag) {  // wait (bounded) for loads still in flight
+                for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc)
+                    mbar_wait(&full[kc % STAGES], (kc / STAGES) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(BLOCK_M, COUT);
+            for (int kc = 0; kc < p.kchunks; ++kc) {
+                const int s = kc % STAGES;
+                const int g = kc / FOLD, q = g & 1;
+                const uint32_t dt = tmem + (uint32_t)(q * COUT);
+                if (kc % FOLD == 0 && g >= 2) {  // partial buffer q must have been folded
+                    if (*abort_flag || !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1)) {
+                        fail();
+                        break;
+                    }
+                }
+                if (*abort_flag || !mbar_wait(&conv[s], (kc / STAGES) & 1)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t ah = smem_u32(stage_a(s)), al = smem_u32(stage_alo(s));
+                const uint32_t bh = smem_u32(stage_bh(s)), bl = smem_u32(stage_bl(s));
+#pragma unroll
+                for (int kk = 0; kk < KCH / 8; ++kk) {
+                    const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
+                    const uint64_t dah = sdesc(ah + off), dal = sdesc(al + off);
+                    const uint64_t dbh = sdesc(bh + off), dbl = sdesc(bl + off);
+                    mma_tf32(dt, dah, dbh, idesc, (kc % FOLD != 0 || kk > 0) ? 1u : 0u);
+                    mma_tf32(dt, dah, dbl, idesc, 1u);
+                    mma_tf32(dt, dal, dbh, idesc, 1u);
+                }
+                mma_commit(&empty[s]);
+                if (kc % FOLD == FOLD - 1 || kc == p.kchunks - 1) mma_commit(&pfull[q]);
+            }
+        }
+    } else {
+        // ---------------- split, fold and epilogue (warps 2..9) ----------------
+        const int et = threadIdx.x - 64;   // 0..255
+        const int quarter = warp & 3;      // TMEM lanes 32*quarter ..
+        const int half = (warp - 2) >> 2;  // column half
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * HALF * 32);
+        float master[HALF * 32];
+#pragma unroll
+        for (int i = 0; i < HALF * 32; ++i) master[i] = 0.f;
+        int folded = 0;
+        bool ok = true;
+        auto fold = [&](int g) {
+            if (!ok) return;
+            if (!mbar_wait(&pfull[g & 1], (g >> 1) & 1)) {
+                fail();
+                ok = false;
+                return;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int h = 0; h < HALF; ++h) {
+                float v[32];
+                tmem_ld32(lane_base + (uint32_t)((g & 1) * COUT + h * 32), v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) master[h * 32 + i] += v[i];
+            }
+            tc_fence_before();
+            mbar_arrive(&pempty[g & 1]);
+        };
+        for (int kc = 0; kc < p.kchunks && ok; ++kc) {
+            const int s = kc % STAGES;
+            if (*abort_flag || !mbar_wait(&full[s], (kc / STAGES) & 1)) {
+                fail();
+                ok = false;
+                break;
+            }
+            float4 *a = reinterpret_cast<float4 *>(stage_a(s));
+            float4 *alo = reinterpret_cast<float4 *>(stage_alo(s));
+#pragma unroll
+            for (int q = 0; q < A_BYTES / 16 / EPI_THREADS; ++q) {
+                const int idx = et + q * EPI_THREADS;
+                float4 v = a[idx];
+                if (p.in_xform == IN_ABS) {
+                    v.x = fabsf(v.x); v.y = fabsf(v.y); v.z = fabsf(v.z); v.w = fabsf(v.w);
+                } else if (p.in_xform == IN_SQUARE) {
+                    v.x *= v.x; v.y *= v.y; v.z *= v.z; v.w *= v.w;
+                }
+                float4 h, l;
+                h.x = tf32_rna(v.x); l.x = tf32_rna(v.x - h.x);
+                h.y = tf32_rna(v.y); l.y = tf32_rna(v.y - h.y);
+                h.z = tf32_rna(v.z); l.z = tf32_rna(v.z - h.z);
+                h.w = tf32_rna(v.w); l.w = tf32_rna(v.w - h.w);
+                a[idx] = h;
+                alo[idx] = l;
+            }
+            fence_proxy_async();
+            mbar_arrive(&conv[s]);
+            // mid-way through group g, the MMAs of group g-1 are done: fold it
+            if (kc % FOLD == FOLD / 2 && kc / FOLD >= 1 && folded < kc / FOLD) fold(folded++);
+        }
+        while (ok && folded < groups) fold(folded++);
+        if (ok && !*abort_flag) {
+            const int m = quarter * 32 + lane;
+            bool valid;
+            int64_t opix;
+            if (p.mode == MODE_FLAT) {
+                valid = p0 + m < p.rows;
+                opix = p0 + m;
+            } else {
+                const int r = m / p.Wt, w = m % p.Wt;
+                const int gi = i0 + r, gj = j0 + w;
+                valid = gi < p.Gh && gj < p.Gw;
+                opix = ((int64_t)b * p.Ho + p.oym * gi + p.oyo) * p.Wo + p.oxm * gj + p.oxo;
+            }
+            if (valid) {
+                const int cbase = half * HALF * 32;
+                float *dst = p.out + opix * COUT + cbase;
+#pragma unroll
+                for (int q = 0; q < HALF * 8; ++q) {
+                    float4 o;
+                    float *op = reinterpret_cast<float *>(&o);
+                    float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (p.epi == EPI_GDN || p.epi == EPI_IGDN)
+                        xg = *reinterpret_cast<const float4 *>(p.gdn_x + opix * COUT + cbase + 4 * q);
+                    const float *xp = reinterpret_cast<const float *>(&xg);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        float y = master[4 * q + e] + __ldg(p.bias + cbase + 4 * q + e);
+                        if (p.epi == EPI_RELU) y = fmaxf(y, 0.f);
+                        else if (p.epi == EPI_GDN) y = xp[e] * rsqrtf(y);
+                        else if (p.epi == EPI_IGDN) y = xp[e] * sqrtf(y);
+                        op[e] = y;
+                    }
+                    reinterpret_cast<float4 *>(dst)[q] = o;
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, p.tmem_cols);
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
+              const uint32_t *box) {
+    EncodeFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t gd[5], gs[4];
+    cuuint32_t bx[5], es[5];
+    for (int i = 0; i < rank; ++i) {
+        gd[i] = dims[i];
+        bx[i] = box[i];
+        es[i] = 1;
+        if (i > 0) gs[i - 1] = strides_bytes[i - 1];
+    }
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void *>(base), gd, gs, bx, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Round a float to TF32 (10 mantissa bits), nearest, ties away from zero.
+uint32_t tf32_rna_host(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u & ~0x1fffu;  // inf / nan: truncate
+    u += 0x1000u;                                                // half of the dropped 13 bits
+    return u & ~0x1fffu;
+}
+
+int stages_for(int Cout) {
+    const int stage = 2 * A_BYTES + 2 * Cout * KCH * 4;
+    const int n = (220 * 1024) / stage;
+    return n >= 3 ? 3 : n;
+}
+
+int smem_bytes(int stages, int Cout) { return stages * (2 * A_BYTES + 2 * Cout * KCH * 4) + 256 + 1024; }
+
+template <int STAGES, int HALF>
+void launch_kernel(unsigned grid, int smem, cudaStream_t st, const CUtensorMap &a, const CUtensorMap &bh,
+                   const CUtensorMap &bl, const Params &p) {
+    cudaFuncSetAttribute(conv_tc_kernel<STAGES, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    conv_tc_kernel<STAGES, HALF><<<grid, 64 + EPI_THREADS, smem, st>>>(a, bh, bl, p);
+}
+
+bool is_flat(const ConvDesc &d) {
+    return d.T == 1 && d.du[0] == 0 && d.dv[0] == 0 && d.s == 1 && d.Gh == d.Hi && d.Gw == d.Wi && d.oym == 1 &&
+           d.oxm == 1 && d.Ho == d.Hi && d.Wo == d.Wi;
+}
+
+// Choose the R x Wt output block (R * Wt = 128) with the least padding.
+void pick_tile(int Gh, int Gw, int *R, int *Wt) {
+    double best = 1e30;
+    for (int wt = 128; wt >= 4; wt /= 2) {
+        const int r = BLOCK_M / wt;
+        const double area = (double)((Gw + wt - 1) / wt * wt) * ((Gh + r - 1) / r * r);
+        if (area < best - 1e-9) {
+            best = area;
+            *R = r;
+            *Wt = wt;
+        }
+    }
+}
+
+}  // namespace
 
 TcWeights::~TcWeights() {
     if (hi) cudaFree(hi);
     if (lo) cudaFree(lo);
+    delete[] reinterpret_cast<CUtensorMap *>(maps);
 }
 
-void build_weights(const float *, int Cout, int T, int Cin, TcWeights *out) {
+void build_weights(const float *w, int Cout, int T, int Cin, TcWeights *out) {
     out->Cout = Cout;
     out->T = T;
     out->Cin = Cin;
     out->valid = false;
+    if (Cin % KCH || (Cout != 128 && Cout != 192) || stages_for(Cout) < 2) return;
+    if (!encode_fn()) return;
+    const int64_t K = (int64_t)T * Cin;
+    std::vector<uint32_t> hi((size_t)Cout * K), lo((size_t)Cout * K);
+    for (int64_t e = 0; e < (int64_t)Cout * K; ++e) {
+        const uint32_t h = tf32_rna_host(w[e]);
+        float hf;
+        memcpy(&hf, &h, 4);
+        hi[e] = h;
+        lo[e] = tf32_rna_host(w[e] - hf);
+    }
+    if (cudaMalloc(&out->hi, hi.size() * 4) != cudaSuccess) return;
+    if (cudaMalloc(&out->lo, lo.size() * 4) != cudaSuccess) return;
+    if (cudaMemcpy(out->hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return;
+    if (cudaMemcpy(out->lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return;
+    CUtensorMap *maps = new CUtensorMap[2];
+    const uint64_t dims[2] = {(uint64_t)K, (uint64_t)Cout};
+    const uint64_t strides[1] = {(uint64_t)K * 4};
+    const uint32_t box[2] = {KCH, (uint32_t)Cout};
+    if (!make_map(&maps[0], out->hi, 2, dims, strides, box) || !make_map(&maps[1], out->lo, 2, dims, strides, box)) {
+        delete[] maps;
+        return;
+    }
+    out->maps = maps;
+    out->Kpad = (int)K;
+    out->Npad = Cout;
+    out->valid = true;
 }
 
-bool can_run(const ConvDesc &, const TcWeights &) { return false; }
+bool can_run(const ConvDesc &d, const TcWeights &w) {
+    if (!w.valid || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout || !d.bias || !d.status) return false;
+    if ((reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15)) return false;
+    if ((d.epi == EPI_GDN || d.epi == EPI_IGDN) && !d.gdn_x) return false;
+    if (is_flat(d)) return true;
+    if (d.s == 2) return (d.Hi % 2 == 0) && (d.Wi % 2 == 0) && d.oym == 1 && d.oxm == 1;
+    return d.s == 1;
+}
 
-void launch(const ConvDesc &, const TcWeights &, cudaStream_t) {}
+bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
+    Params p{};
+    p.out = d.out;
+    p.bias = d.bias;
+    p.gdn_x = d.gdn_x;
+    p.status = d.status;
+    p.T = d.T;
+    p.Cin = d.Cin;
+    p.cpt = d.Cin / KCH;
+    p.kchunks = d.T * p.cpt;
+    p.Gh = d.Gh;
+    p.Gw = d.Gw;
+    p.B = d.B;
+    p.Ho = d.Ho;
+    p.Wo = d.Wo;
+    p.Cout = d.Cout;
+    p.oym = d.oym;
+    p.oyo = d.oyo;
+    p.oxm = d.oxm;
+    p.oxo = d.oxo;
+    p.epi = d.epi;
+    p.in_xform = d.in_xform;
+    p.tmem_cols = 2 * d.Cout <= 256 ? 256 : 512;  // two partial buffers
+    for (int t = 0; t < d.T; ++t) {
+        p.du[t] = d.du[t];
+        p.dv[t] = d.dv[t];
+    }
+    CUtensorMap tmA;
+    unsigned grid;
+    const uint64_t C = (uint64_t)d.Cin;
+    if (is_flat(d)) {
+        p.mode = MODE_FLAT;
+        p.rows = (int64_t)d.B * d.Hi * d.Wi;
+        const uint64_t dims[2] = {C, (uint64_t)p.rows};
+        const uint64_t strides[1] = {C * 4};
+        const uint32_t box[2] = {KCH, BLOCK_M};
+        if (!make_map(&tmA, d.in, 2, dims, strides, box)) return false;
+        grid = (unsigned)((p.rows + BLOCK_M - 1) / BLOCK_M);
+    } else {
+        pick_tile(d.Gh, d.Gw, &p.R, &p.Wt);
+        p.tiles_x = (d.Gw + p.Wt - 1) / p.Wt;
+        p.tiles_y = (d.Gh + p.R - 1) / p.R;
+        grid = (unsigned)(p.tiles_x * p.tiles_y * d.B);
+        if (d.s == 2) {
+            p.mode = MODE_S2;
+            const uint64_t dims[5] = {2 * C, (uint64_t)d.Wi / 2, 2, (uint64_t)d.Hi / 2, (uint64_t)d.B};
+            const uint64_t strides[4] = {2 * C * 4, (uint64_t)d.Wi * C * 4, 2ull * d.Wi * C * 4,
+                                         (uint64_t)d.Hi * d.Wi * C * 4};
+            const uint32_t box[5] = {KCH, (uint32_t)p.Wt, 1, (uint32_t)p.R, 1};
+            if (!make_map(&tmA, d.in, 5, dims, strides, box)) return false;
+        } else {
+            p.mode = MODE_S1;
+            const uint64_t dims[4] = {C, (uint64_t)d.Wi, (uint64_t)d.Hi, (uint64_t)d.B};
+            const uint64_t strides[3] = {C * 4, (uint64_t)d.Wi * C * 4, (uint64_t)d.Hi * d.Wi * C * 4};
+            const uint32_t box[4] = {KCH, (uint32_t)p.Wt, (uint32_t)p.R, 1};
+            if (!make_map(&tmA, d.in, 4, dims, strides, box)) return false;
+        }
+    }
+    if (grid == 0) return true;
+    const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(w.maps);
+    const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
+    if (d.Cout == 128)
+        launch_kernel<3, 2>(grid, smem, st, tmA, maps[0], maps[1], p);
+    else
+        launch_kernel<2, 3>(grid, smem, st, tmA, maps[0], maps[1], p);
+    return true;
+}
 
 }  // namespace tc
 }  // namespace lic

@@ -11,6 +11,7 @@ namespace tc {
 // representable in TF32) and laid out as the B operand of the kernel.
 struct TcWeights {
     void *hi = nullptr, *lo = nullptr;
+    void *maps = nullptr;   // two CUtensorMap (hi, lo), host copies passed as kernel parameters
     int Cout = 0, T = 0, Cin = 0, Npad = 0, Kpad = 0;
     bool valid = false;
     TcWeights() = default;
@@ -26,7 +27,9 @@ void build_weights(const float *w, int Cout, int T, int Cin, TcWeights *out);
 // Whether the tensor-core kernel handles this launch.
 bool can_run(const ConvDesc &d, const TcWeights &w);
 
-void launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
+// Launches the kernel; false (nothing launched) if a tensor map could not be
+// encoded, in which case the caller runs the CUDA-core kernel instead.
+bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
 
 }  // namespace tc
 }  // namespace lic

@@ -74,6 +74,7 @@ struct ConvDesc {
     const float *w;
     const float *bias;     // [Cout] or null
     const float *gdn_x;    // EPI_GDN/IGDN: x that the norm divides, NHWC with Cout channels
+    uint32_t *status;      // device status word (bounded waits that run out set ST_TIMEOUT)
     int B, Hi, Wi, Cin;
     int Gh, Gw, s;
     int Ho, Wo, Cout;
