@@ -290,8 +290,8 @@ int make_gdn(Gdn &G, const ParamMap &pm, const std::string &name, int C, bool in
 // running layers
 // ---------------------------------------------------------------------------
 
-void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *in, int B, int Hi, int Wi,
-            float *out, int Ho, int Wo, cudaStream_t st) {
+ConvDesc op_desc(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *in, int B, int Hi, int Wi,
+                 float *out, int Ho, int Wo) {
     ConvDesc d{};
     d.in = in;
     d.out = out;
@@ -330,12 +330,27 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
         d.oxm = 1;
         d.oxo = 0;
     }
+    return d;
+}
+
+// One GEMM launch of a layer; with G, the GDN / IGDN that follows the layer
+// runs in the same launch (the caller has checked that it can).
+void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *in, int B, int Hi, int Wi,
+            float *out, int Ho, int Wo, cudaStream_t st, const Gdn *G = nullptr) {
+    ConvDesc d = op_desc(cd, L, op, in, B, Hi, Wi, out, Ho, Wo);
     const double rows = (double)B * d.Gh * d.Gw;
-    const double flop = 2.0 * rows * d.Cout * d.T * d.Cin;
+    double flop = 2.0 * rows * d.Cout * d.T * d.Cin;
     const double bytes = 4.0 * ((double)B * Hi * Wi * d.Cin + rows * d.Cout + (double)d.Cout * d.T * d.Cin);
+    std::string nm = L.name + (L.deconv ? ".p" + std::to_string(2 * op.py + op.px) : std::string());
+    if (G) {
+        d.fuse_gdn = G->inverse ? 2 : 1;
+        d.gdn_beta = G->beta.as<float>();
+        d.gdn_w = &G->tcw;
+        flop += 2.0 * rows * G->C * G->C;
+        nm += "+" + G->name.substr(G->name.find('.') + 1);
+    }
     const bool use_tc = cd->opt.conv_impl != LIC_CONV_SIMT && tc::can_run(d, op.tcw);
-    std::string nm = L.name + (L.deconv ? ".p" + std::to_string(2 * op.py + op.px) : std::string()) +
-                     (use_tc ? ":tc" : ":simt");
+    nm += use_tc ? ":tc" : ":simt";
     timed(const_cast<lic_codec *>(cd), nm, flop, bytes, 1, st, [&] {
         if (!use_tc || !tc::launch(d, op.tcw, st)) launch_conv_simt(d, st);
     });
@@ -394,6 +409,48 @@ void run_gdn(const lic_codec *cd, const Gdn &G, const float *in, int B, int H, i
           });
 }
 
+int out_size(const Layer &L, int Hi, int Wi, int *Ho, int *Wo) {
+    if (L.deconv) {
+        *Ho = 2 * Hi;
+        *Wo = 2 * Wi;
+    } else {
+        const int p = L.k / 2;
+        *Ho = (Hi + 2 * p - L.k) / L.stride + 1;
+        *Wo = (Wi + 2 * p - L.k) / L.stride + 1;
+    }
+    return 0;
+}
+
+// A layer followed by GDN / IGDN, ping-ponging between buffers a and b;
+// returns the buffer holding the result.  One fused tensor-core launch per
+// GEMM (writing the buffer that is not the input) when every launch of the
+// layer qualifies; else the layer into that buffer and a separate
+// normalisation into the other one (which may be the consumed input).
+float *run_layer_gdn(const lic_codec *cd, const Layer &L, const Gdn &G, const float *in, int B, int Hi, int Wi,
+                     float *a, float *b, cudaStream_t st) {
+    float *other = (in == a) ? b : a;
+    float *out = other;
+    int Ho, Wo;
+    out_size(L, Hi, Wi, &Ho, &Wo);
+    bool fuse = cd->opt.conv_impl != LIC_CONV_SIMT && !L.w_small.p && !L.ops.empty();
+    for (auto &op : L.ops) {
+        if (!fuse) break;
+        ConvDesc d = op_desc(cd, L, *op, in, B, Hi, Wi, out, Ho, Wo);
+        d.fuse_gdn = G.inverse ? 2 : 1;
+        d.gdn_beta = G.beta.as<float>();
+        d.gdn_w = &G.tcw;
+        fuse = tc::can_run(d, op->tcw);
+    }
+    if (fuse) {
+        for (auto &op : L.ops) run_op(cd, L, *op, in, B, Hi, Wi, out, Ho, Wo, st, &G);
+        return out;
+    }
+    float *norm_out = (other == a) ? b : a;
+    run_layer(cd, L, in, B, Hi, Wi, other, st);
+    run_gdn(cd, G, other, B, Ho, Wo, norm_out, st);
+    return norm_out;
+}
+
 int pad64(int v) { return (v + 63) / 64 * 64; }
 
 template <typename T>
@@ -450,11 +507,9 @@ void analysis(lic_codec *cd, int B, int Hp, int Wp, cudaStream_t st) {
     int H = Hp, W = Wp;
     const float *in = cd->xin.as<float>();
     for (int i = 0; i < 3; ++i) {
-        run_layer(cd, cd->ga[i], in, B, H, W, a, st);
+        in = run_layer_gdn(cd, cd->ga[i], cd->gdn[i], in, B, H, W, a, b, st);
         H /= 2;
         W /= 2;
-        run_gdn(cd, cd->gdn[i], a, B, H, W, b, st);
-        in = b;
     }
     run_layer(cd, cd->ga[3], in, B, H, W, cd->y.as<float>(), st);
 }
@@ -483,11 +538,9 @@ void synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, cudaStre
     int H = Hy, W = Wy;
     const float *in = yhat;
     for (int i = 0; i < 3; ++i) {
-        run_layer(cd, cd->gs[i], in, B, H, W, a, st);
+        in = run_layer_gdn(cd, cd->gs[i], cd->igdn[i], in, B, H, W, a, b, st);
         H *= 2;
         W *= 2;
-        run_gdn(cd, cd->igdn[i], a, B, H, W, b, st);
-        in = b;
     }
     run_layer(cd, cd->gs[3], in, B, H, W, cd->xpre.as<float>(), st);
 }

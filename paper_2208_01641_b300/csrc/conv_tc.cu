@@ -69,6 +69,8 @@ struct Params {
     int Ho, Wo, Cout;
     int oym, oyo, oxm, oxo;
     int epi, in_xform;
+    int fuse_gdn;                 // 0, 1 (GDN) or 2 (IGDN) applied after bias
+    const float *gdn_beta;
     int kchunks;
     uint32_t tmem_cols;
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
@@ -220,10 +222,21 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 
 // ------------------------------------------------------------------ kernel
 
+//
+// Fused GDN / IGDN (p.fuse_gdn): once the convolution sum y of the tile is
+// complete, its channel norm  n_i = beta_i + sum_j gamma_ij y_j^2  is a second
+// GEMM of y^2 (128 pixels x C) with gamma^T.  The epilogue warps write y^2,
+// split into TF32 hi / lo, into the (now idle) stage buffers as the A
+// operand, the producer loads gamma's hi / lo slices as B, and the MMA lane
+// accumulates n (K = C, short enough for one TMEM accumulator) in HALF
+// passes of two 32-channel chunks each.  The output is y * rsqrt(n) (GDN) or
+// y * sqrt(n) (IGDN); y itself never reaches global memory.
 template <int STAGES, int HALF>  // HALF: 32-column blocks per epilogue thread (Cout = 64 * HALF)
 __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                       const __grid_constant__ CUtensorMap tmBh,
                                                                       const __grid_constant__ CUtensorMap tmBl,
+                                                                      const __grid_constant__ CUtensorMap tmGh,
+                                                                      const __grid_constant__ CUtensorMap tmGl,
                                                                       const __grid_constant__ Params p) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -233,7 +246,8 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
     uint64_t *full = bars, *conv = bars + STAGES, *empty = bars + 2 * STAGES;
     uint64_t *pfull = bars + 3 * STAGES, *pempty = pfull + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(pempty + 2);
+    uint64_t *gdn_full = pempty + 2, *gdn_ready = gdn_full + 1, *mma_done = gdn_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gdn_full + 3);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -263,6 +277,9 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
             mbar_init(&pfull[q], 1);
             mbar_init(&pempty[q], EPI_THREADS);
         }
+        mbar_init(gdn_full, 1);
+        mbar_init(gdn_ready, EPI_THREADS);
+        mbar_init(mma_done, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -309,6 +326,19 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 tma_load_2d(stage_bl(s), &tmBl, &full[s], kc * KCH, 0);
                 issued = kc + 1;
             }
+            // gamma slices for the fused norm: pass h uses stages 0 and 1 once
+            // the MMAs that read them (main loop, then pass h-1) are done
+            for (int h = 0; p.fuse_gdn && h < HALF && !*abort_flag; ++h) {
+                if (!mbar_wait(mma_done, h & 1)) {
+                    fail();
+                    break;
+                }
+                mbar_expect_tx(gdn_full, 4 * B_BYTES);
+                tma_load_2d(stage_bh(0), &tmGh, gdn_full, h * KCH, 0);
+                tma_load_2d(stage_bl(0), &tmGl, gdn_full, h * KCH, 0);
+                tma_load_2d(stage_bh(1), &tmGh, gdn_full, (HALF + h) * KCH, 0);
+                tma_load_2d(stage_bl(1), &tmGl, gdn_full, (HALF + h) * KCH, 0);
+            }
             if (*abort_flag) {  // wait (bounded) for loads still in flight
                 for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc)
                     mbar_wait(&full[kc % STAGES], (kc / STAGES) & 1);
@@ -346,6 +376,29 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 }
                 mma_commit(&empty[s]);
                 if (kc % FOLD == FOLD - 1 || kc == p.kchunks - 1) mma_commit(&pfull[q]);
+            }
+            mma_commit(mma_done);   // phase 0: the main loop's MMAs are complete
+            for (int h = 0; p.fuse_gdn && h < HALF; ++h) {
+                if (*abort_flag || !mbar_wait(gdn_ready, h & 1) || !mbar_wait(gdn_full, h & 1)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const uint32_t ah = smem_u32(stage_a(c)), al = smem_u32(stage_alo(c));
+                    const uint32_t bh = smem_u32(stage_bh(c)), bl = smem_u32(stage_bl(c));
+#pragma unroll
+                    for (int kk = 0; kk < KCH / 8; ++kk) {
+                        const uint32_t off = kk * 32;
+                        const uint64_t dah = sdesc(ah + off), dal = sdesc(al + off);
+                        const uint64_t dbh = sdesc(bh + off), dbl = sdesc(bl + off);
+                        mma_tf32(tmem, dah, dbh, idesc, (h > 0 || c > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32(tmem, dah, dbl, idesc, 1u);
+                        mma_tf32(tmem, dal, dbh, idesc, 1u);
+                    }
+                }
+                mma_commit(mma_done);   // phase h + 1
             }
         }
     } else {
@@ -409,6 +462,58 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
             if (kc % FOLD == FOLD / 2 && kc / FOLD >= 1 && folded < kc / FOLD) fold(folded++);
         }
         while (ok && folded < groups) fold(folded++);
+        const int cbase = half * HALF * 32;
+        if (ok && p.fuse_gdn) {
+            // y = conv + bias, then the norm GEMM on y^2 (see above)
+#pragma unroll
+            for (int i = 0; i < HALF * 32; ++i) master[i] += __ldg(p.bias + cbase + i);
+            const int m = quarter * 32 + lane;
+#pragma unroll
+            for (int h = 0; h < HALF; ++h) {
+                if (h > 0 && (*abort_flag || !mbar_wait(mma_done, h & 1))) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                // chunk h of this half -> stage `half` (A: hi, Alo: lo), row m, 128-byte swizzle
+                uint8_t *ahi = stage_a(half), *alo = stage_alo(half);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    float4 v, hv, lv;
+                    v.x = master[h * 32 + 4 * u + 0]; v.y = master[h * 32 + 4 * u + 1];
+                    v.z = master[h * 32 + 4 * u + 2]; v.w = master[h * 32 + 4 * u + 3];
+                    v.x *= v.x; v.y *= v.y; v.z *= v.z; v.w *= v.w;
+                    hv.x = tf32_rna(v.x); lv.x = tf32_rna(v.x - hv.x);
+                    hv.y = tf32_rna(v.y); lv.y = tf32_rna(v.y - hv.y);
+                    hv.z = tf32_rna(v.z); lv.z = tf32_rna(v.z - hv.z);
+                    hv.w = tf32_rna(v.w); lv.w = tf32_rna(v.w - hv.w);
+                    const int off = m * 128 + ((u ^ (m & 7)) << 4);
+                    *reinterpret_cast<float4 *>(ahi + off) = hv;
+                    *reinterpret_cast<float4 *>(alo + off) = lv;
+                }
+                fence_proxy_async();
+                tc_fence_before();
+                mbar_arrive(gdn_ready);
+            }
+            if (ok && (*abort_flag || !mbar_wait(mma_done, HALF & 1))) {
+                fail();
+                ok = false;
+            }
+            if (ok) {
+                tc_fence_after();
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    float v[32];
+                    tmem_ld32(lane_base + (uint32_t)(h * 32), v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float n = v[i] + __ldg(p.gdn_beta + cbase + h * 32 + i);
+                        const float y = master[h * 32 + i];
+                        master[h * 32 + i] = p.fuse_gdn == 1 ? y * rsqrtf(n) : y * sqrtf(n);
+                    }
+                }
+            }
+        }
         if (ok && !*abort_flag) {
             const int m = quarter * 32 + lane;
             bool valid;
@@ -422,8 +527,12 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 valid = gi < p.Gh && gj < p.Gw;
                 opix = ((int64_t)b * p.Ho + p.oym * gi + p.oyo) * p.Wo + p.oxm * gj + p.oxo;
             }
-            if (valid) {
-                const int cbase = half * HALF * 32;
+            if (valid && p.fuse_gdn) {
+                float4 *dst = reinterpret_cast<float4 *>(p.out + opix * COUT + cbase);
+#pragma unroll
+                for (int q = 0; q < HALF * 8; ++q)
+                    dst[q] = make_float4(master[4 * q], master[4 * q + 1], master[4 * q + 2], master[4 * q + 3]);
+            } else if (valid) {
                 float *dst = p.out + opix * COUT + cbase;
 #pragma unroll
                 for (int q = 0; q < HALF * 8; ++q) {
@@ -512,9 +621,9 @@ int smem_bytes(int stages, int Cout) { return stages * (2 * A_BYTES + 2 * Cout *
 
 template <int STAGES, int HALF>
 void launch_kernel(unsigned grid, int smem, cudaStream_t st, const CUtensorMap &a, const CUtensorMap &bh,
-                   const CUtensorMap &bl, const Params &p) {
+                   const CUtensorMap &bl, const CUtensorMap &gh, const CUtensorMap &gl, const Params &p) {
     cudaFuncSetAttribute(conv_tc_kernel<STAGES, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    conv_tc_kernel<STAGES, HALF><<<grid, 64 + EPI_THREADS, smem, st>>>(a, bh, bl, p);
+    conv_tc_kernel<STAGES, HALF><<<grid, 64 + EPI_THREADS, smem, st>>>(a, bh, bl, gh, gl, p);
 }
 
 bool is_flat(const ConvDesc &d) {
@@ -582,6 +691,11 @@ bool can_run(const ConvDesc &d, const TcWeights &w) {
     if (!w.valid || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout || !d.bias || !d.status) return false;
     if ((reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15)) return false;
     if ((d.epi == EPI_GDN || d.epi == EPI_IGDN) && !d.gdn_x) return false;
+    if (d.fuse_gdn) {
+        const TcWeights *g = static_cast<const TcWeights *>(d.gdn_w);
+        if (!g || !g->valid || g->T != 1 || g->Cin != d.Cout || g->Cout != d.Cout || !d.gdn_beta) return false;
+        if (d.epi != EPI_NONE) return false;
+    }
     if (is_flat(d)) return true;
     if (d.s == 2) return (d.Hi % 2 == 0) && (d.Wi % 2 == 0) && d.oym == 1 && d.oxm == 1;
     return d.s == 1;
@@ -609,6 +723,8 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.oxo = d.oxo;
     p.epi = d.epi;
     p.in_xform = d.in_xform;
+    p.fuse_gdn = d.fuse_gdn;
+    p.gdn_beta = d.gdn_beta;
     p.tmem_cols = 2 * d.Cout <= 256 ? 256 : 512;  // two partial buffers
     for (int t = 0; t < d.T; ++t) {
         p.du[t] = d.du[t];
@@ -647,11 +763,15 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     }
     if (grid == 0) return true;
     const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(w.maps);
+    // without fusion the gamma maps are unused: pass the weight maps
+    const CUtensorMap *gmaps = d.fuse_gdn
+                                   ? reinterpret_cast<const CUtensorMap *>(static_cast<const TcWeights *>(d.gdn_w)->maps)
+                                   : maps;
     const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
     if (d.Cout == 128)
-        launch_kernel<3, 2>(grid, smem, st, tmA, maps[0], maps[1], p);
+        launch_kernel<3, 2>(grid, smem, st, tmA, maps[0], maps[1], gmaps[0], gmaps[1], p);
     else
-        launch_kernel<2, 3>(grid, smem, st, tmA, maps[0], maps[1], p);
+        launch_kernel<2, 3>(grid, smem, st, tmA, maps[0], maps[1], gmaps[0], gmaps[1], p);
     return true;
 }
 

@@ -75,6 +75,12 @@ struct ConvDesc {
     const float *bias;     // [Cout] or null
     const float *gdn_x;    // EPI_GDN/IGDN: x that the norm divides, NHWC with Cout channels
     uint32_t *status;      // device status word (bounded waits that run out set ST_TIMEOUT)
+    // GDN / IGDN fused into the epilogue of this convolution (tensor-core
+    // kernel only): 0 none, 1 GDN, 2 IGDN; gdn_w is the tc::TcWeights of gamma
+    // ([C][1][C]), gdn_beta its beta.
+    int fuse_gdn;
+    const float *gdn_beta;
+    const void *gdn_w;
     int B, Hi, Wi, Cin;
     int Gh, Gw, s;
     int Ho, Wo, Cout;
