@@ -56,7 +56,11 @@ constexpr int FOLD = 4;                          // K chunks per TMEM partial su
 constexpr int EPI_WARPS = 8;
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 
-enum Mode : int { MODE_S2 = 0, MODE_S1 = 1, MODE_FLAT = 2 };
+// MODE_IM2COL: inputs with few channels (the 3-channel frame into g_a): the
+// epilogue warps gather each 128 x 32 slice of the im2col matrix (K index
+// t * Cin + c, zero past T * Cin) straight from global memory, split it and
+// write it swizzled into the stage; TMA brings only the weights.
+enum Mode : int { MODE_S2 = 0, MODE_S1 = 1, MODE_FLAT = 2, MODE_IM2COL = 3 };
 
 struct Params {
     float *out;
@@ -69,6 +73,8 @@ struct Params {
     int Ho, Wo, Cout;
     int oym, oyo, oxm, oxo;
     int epi, in_xform;
+    const float *in;              // MODE_IM2COL: NHWC input
+    int Hi, Wi, s;                // MODE_IM2COL: input size, stride
     int fuse_gdn;                 // 0, 1 (GDN) or 2 (IGDN) applied after bias
     const float *gdn_beta;
     int kchunks;
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
     int64_t p0 = 0;
     if (p.mode == MODE_FLAT) {
         p0 = (int64_t)blockIdx.x * BLOCK_M;
-    } else {
+    } else {   // S2, S1 and IM2COL tile the output grid the same way
         int t = blockIdx.x;
         const int tx = t % p.tiles_x;
         t /= p.tiles_x;
@@ -301,7 +307,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            const uint32_t tx_bytes = A_BYTES + 2 * B_BYTES;
+            const uint32_t tx_bytes = (p.mode == MODE_IM2COL ? 0 : A_BYTES) + 2 * B_BYTES;
             int issued = 0;
             for (int kc = 0; kc < p.kchunks && !*abort_flag; ++kc) {
                 const int s = kc % STAGES;
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                                 i0 + (du >> 1), b);
                 } else if (p.mode == MODE_S1) {
                     tma_load_4d(stage_a(s), &tmA, &full[s], c0, j0 + p.dv[t], i0 + p.du[t], b);
-                } else {
+                } else if (p.mode == MODE_FLAT) {
                     tma_load_2d(stage_a(s), &tmA, &full[s], c0, (int)p0);
                 }
                 tma_load_2d(stage_bh(s), &tmBh, &full[s], kc * KCH, 0);
@@ -439,6 +445,36 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
             }
             float4 *a = reinterpret_cast<float4 *>(stage_a(s));
             float4 *alo = reinterpret_cast<float4 *>(stage_alo(s));
+            if (p.mode == MODE_IM2COL) {
+                // row m of the tile, 16 consecutive K entries [kc*32 + 16*kh, +16)
+                const int m = et >> 1, kh = et & 1;
+                const int gi = i0 + m / p.Wt, gj = j0 + m % p.Wt;
+                float v[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int k = kc * KCH + 16 * kh + e;
+                    const int t = k / p.Cin, c = k - t * p.Cin;
+                    float x = 0.f;
+                    if (t < p.T) {
+                        const int yi = p.s * gi + p.du[t], xi = p.s * gj + p.dv[t];
+                        if (yi >= 0 && yi < p.Hi && xi >= 0 && xi < p.Wi)
+                            x = __ldg(p.in + (((int64_t)b * p.Hi + yi) * p.Wi + xi) * p.Cin + c);
+                    }
+                    v[e] = x;
+                }
+                uint8_t *ah = reinterpret_cast<uint8_t *>(a), *al = reinterpret_cast<uint8_t *>(alo);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 hv, lv;
+                    hv.x = tf32_rna(v[4 * q + 0]); lv.x = tf32_rna(v[4 * q + 0] - hv.x);
+                    hv.y = tf32_rna(v[4 * q + 1]); lv.y = tf32_rna(v[4 * q + 1] - hv.y);
+                    hv.z = tf32_rna(v[4 * q + 2]); lv.z = tf32_rna(v[4 * q + 2] - hv.z);
+                    hv.w = tf32_rna(v[4 * q + 3]); lv.w = tf32_rna(v[4 * q + 3] - hv.w);
+                    const int off = m * 128 + (((4 * kh + q) ^ (m & 7)) << 4);
+                    *reinterpret_cast<float4 *>(ah + off) = hv;
+                    *reinterpret_cast<float4 *>(al + off) = lv;
+                }
+            } else
 #pragma unroll
             for (int q = 0; q < A_BYTES / 16 / EPI_THREADS; ++q) {
                 const int idx = et + q * EPI_THREADS;
@@ -658,17 +694,23 @@ void build_weights(const float *w, int Cout, int T, int Cin, TcWeights *out) {
     out->T = T;
     out->Cin = Cin;
     out->valid = false;
-    if (Cin % KCH || (Cout != 128 && Cout != 192) || stages_for(Cout) < 2) return;
+    if ((Cout != 128 && Cout != 192) || stages_for(Cout) < 2) return;
+    // Cin % 32 != 0: the im2col path, K = T * Cin zero-padded to a chunk multiple
+    out->im2col = Cin % KCH != 0;
+    if (out->im2col && (Cin > 4 || T * Cin > 8 * KCH)) return;
     if (!encode_fn()) return;
-    const int64_t K = (int64_t)T * Cin;
-    std::vector<uint32_t> hi((size_t)Cout * K), lo((size_t)Cout * K);
-    for (int64_t e = 0; e < (int64_t)Cout * K; ++e) {
-        const uint32_t h = tf32_rna_host(w[e]);
-        float hf;
-        memcpy(&hf, &h, 4);
-        hi[e] = h;
-        lo[e] = tf32_rna_host(w[e] - hf);
-    }
+    const int64_t K0 = (int64_t)T * Cin;
+    const int64_t K = (K0 + KCH - 1) / KCH * KCH;
+    std::vector<uint32_t> hi((size_t)Cout * K, 0u), lo((size_t)Cout * K, 0u);
+    for (int64_t o = 0; o < Cout; ++o)
+        for (int64_t k = 0; k < K0; ++k) {
+            const float x = w[o * K0 + k];
+            const uint32_t h = tf32_rna_host(x);
+            float hf;
+            memcpy(&hf, &h, 4);
+            hi[o * K + k] = h;
+            lo[o * K + k] = tf32_rna_host(x - hf);
+        }
     if (cudaMalloc(&out->hi, hi.size() * 4) != cudaSuccess) return;
     if (cudaMalloc(&out->lo, lo.size() * 4) != cudaSuccess) return;
     if (cudaMemcpy(out->hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return;
@@ -696,6 +738,8 @@ bool can_run(const ConvDesc &d, const TcWeights &w) {
         if (!g || !g->valid || g->T != 1 || g->Cin != d.Cout || g->Cout != d.Cout || !d.gdn_beta) return false;
         if (d.epi != EPI_NONE) return false;
     }
+    if (w.im2col) return d.epi != EPI_GDN && d.epi != EPI_IGDN && d.in_xform == IN_NONE && d.oym == 1 && d.oxm == 1;
+
     if (is_flat(d)) return true;
     if (d.s == 2) return (d.Hi % 2 == 0) && (d.Wi % 2 == 0) && d.oym == 1 && d.oxm == 1;
     return d.s == 1;
@@ -711,6 +755,10 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.Cin = d.Cin;
     p.cpt = d.Cin / KCH;
     p.kchunks = d.T * p.cpt;
+    p.in = d.in;
+    p.Hi = d.Hi;
+    p.Wi = d.Wi;
+    p.s = d.s;
     p.Gh = d.Gh;
     p.Gw = d.Gw;
     p.B = d.B;
@@ -733,7 +781,16 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     CUtensorMap tmA;
     unsigned grid;
     const uint64_t C = (uint64_t)d.Cin;
-    if (is_flat(d)) {
+    if (w.im2col) {
+        p.mode = MODE_IM2COL;
+        p.cpt = 1;
+        p.kchunks = w.Kpad / KCH;
+        pick_tile(d.Gh, d.Gw, &p.R, &p.Wt);
+        p.tiles_x = (d.Gw + p.Wt - 1) / p.Wt;
+        p.tiles_y = (d.Gh + p.R - 1) / p.R;
+        grid = (unsigned)(p.tiles_x * p.tiles_y * d.B);
+        tmA = reinterpret_cast<const CUtensorMap *>(w.maps)[0];   // unused in this mode
+    } else if (is_flat(d)) {
         p.mode = MODE_FLAT;
         p.rows = (int64_t)d.B * d.Hi * d.Wi;
         const uint64_t dims[2] = {C, (uint64_t)p.rows};

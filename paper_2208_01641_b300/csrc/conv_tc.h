@@ -13,6 +13,7 @@ struct TcWeights {
     void *hi = nullptr, *lo = nullptr;
     void *maps = nullptr;   // two CUtensorMap (hi, lo), host copies passed as kernel parameters
     int Cout = 0, T = 0, Cin = 0, Npad = 0, Kpad = 0;
+    bool im2col = false;    // few input channels: A gathered by the kernel, K zero-padded
     bool valid = false;
     TcWeights() = default;
     TcWeights(const TcWeights &) = delete;
