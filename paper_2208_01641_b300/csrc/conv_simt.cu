@@ -154,88 +154,101 @@ __global__ void __launch_bounds__(NT) conv_simt_kernel(const ConvDesc d) {
 }
 
 // ---------------------------------------------------------------------------
-// Transposed conv to <= 4 channels.  Input position (m, n) feeds output
-// pixels (2m + py, 2n + px) through tap u = py + 2 - 2 du of input row
-// m + du (du in {-1, 0, 1}, valid when 0 <= u <= 4), likewise for columns:
-// every output of the four phases at (m, n) reads only the 3 x 3 input
-// neighbourhood of (m, n).  One thread owns one input position and its
-// 4 phases x 4 channels of accumulators.
-constexpr int DS_TR = 8, DS_TC = 32, DS_CH = 16;
+// Transposed conv to <= 4 channels (the last layer of g_s).  Input position
+// (m, n) feeds output pixels (2m + py, 2n + px) through tap u = py + 2 - 2 du
+// of input row m + du (du in {-1, 0, 1}, valid when 0 <= u <= 4), likewise
+// for columns: all four phases at (m, n) read only the 3 x 3 neighbourhood
+// of (m, n).  A thread owns a 2 x 2 block of input positions -- 16 output
+// pixels -- so its 4 x 4 input neighbourhood and every (broadcast) weight
+// load are shared by four positions; the kernel is bound by FMA issue.
+constexpr int DS_TR = 8, DS_TC = 64, DS_CH = 8, DS_THREADS = 128;
+constexpr int DS_PITCH = DS_TC + 4;   // row pitch in floats
 
-__global__ void __launch_bounds__(DS_TR * DS_TC) deconv_small_kernel(const float *__restrict__ in, int B, int Hi,
-                                                                     int Wi, int Cin, const float *__restrict__ w,
-                                                                     const float *__restrict__ bias, int Cout,
-                                                                     float *__restrict__ out) {
-    __shared__ float xs[DS_TR + 2][DS_TC + 2][DS_CH + 1];
+template <int COUT>
+__global__ void __launch_bounds__(DS_THREADS) deconv_small_kernel(const float *__restrict__ in, int B, int Hi,
+                                                                  int Wi, int Cin, const float *__restrict__ w,
+                                                                  const float *__restrict__ bias,
+                                                                  float *__restrict__ out) {
+    __shared__ float xs[DS_CH][DS_TR + 2][DS_PITCH];
     __shared__ __align__(16) float ws[DS_CH][25][4];
     const int tid = threadIdx.x;
-    const int tr = tid / DS_TC, tc = tid % DS_TC;
+    const int tr = tid / 32, tc = tid % 32;      // positions (m0 + 2tr + a, n0 + 2tc + c)
     const int b = blockIdx.z;
     const int m0 = blockIdx.y * DS_TR, n0 = blockIdx.x * DS_TC;
-    const int m = m0 + tr, n = n0 + tc;
-    float acc[2][2][4];
+    float acc[2][2][2][2][COUT];                 // [a][c][py][px][o]
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-            for (int o = 0; o < 4; ++o) acc[a][c][o] = 0.f;
+    for (int i = 0; i < 2 * 2 * 2 * 2 * COUT; ++i) (&acc[0][0][0][0][0])[i] = 0.f;
 
     for (int c0 = 0; c0 < Cin; c0 += DS_CH) {
         // input tile with a one-pixel halo, zero outside the image
-        for (int e = tid; e < (DS_TR + 2) * (DS_TC + 2) * (DS_CH / 4); e += DS_TR * DS_TC) {
-            int q = e % (DS_CH / 4);
-            int pos = e / (DS_CH / 4);
-            int rr = pos / (DS_TC + 2), cc = pos % (DS_TC + 2);
-            int yi = m0 - 1 + rr, xi = n0 - 1 + cc;
+        for (int e = tid; e < (DS_TR + 2) * (DS_TC + 2) * (DS_CH / 4); e += DS_THREADS) {
+            const int q = e % (DS_CH / 4);
+            const int pos = e / (DS_CH / 4);
+            const int rr = pos / (DS_TC + 2), cc = pos % (DS_TC + 2);
+            const int yi = m0 - 1 + rr, xi = n0 - 1 + cc;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (yi >= 0 && yi < Hi && xi >= 0 && xi < Wi)
                 v = *reinterpret_cast<const float4 *>(in + (((int64_t)b * Hi + yi) * Wi + xi) * Cin + c0 + 4 * q);
-            xs[rr][cc][4 * q + 0] = v.x;
-            xs[rr][cc][4 * q + 1] = v.y;
-            xs[rr][cc][4 * q + 2] = v.z;
-            xs[rr][cc][4 * q + 3] = v.w;
+            xs[4 * q + 0][rr][cc] = v.x;
+            xs[4 * q + 1][rr][cc] = v.y;
+            xs[4 * q + 2][rr][cc] = v.z;
+            xs[4 * q + 3][rr][cc] = v.w;
         }
-        for (int e = tid; e < DS_CH * 25; e += DS_TR * DS_TC) {
+        for (int e = tid; e < DS_CH * 25; e += DS_THREADS) {
             const float4 v = *reinterpret_cast<const float4 *>(w + ((int64_t)(c0 + e / 25) * 25 + e % 25) * 4);
             *reinterpret_cast<float4 *>(&ws[e / 25][e % 25][0]) = v;
         }
         __syncthreads();
+#pragma unroll 1
         for (int c = 0; c < DS_CH; ++c) {
+            float x[4][4];   // neighbourhood rows m0+2tr-1 .. +2, cols n0+2tc-1 .. +2
 #pragma unroll
-            for (int du = -1; du <= 1; ++du)
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int dv = -1; dv <= 1; ++dv) {
-                    const float x = xs[tr + 1 + du][tc + 1 + dv][c];
+                for (int q = 0; q < 4; ++q) x[r][q] = xs[c][2 * tr + r][2 * tc + q];
 #pragma unroll
-                    for (int py = 0; py < 2; ++py) {
-                        const int u = py + 2 - 2 * du;
-                        if (u < 0 || u > 4) continue;
+            for (int py = 0; py < 2; ++py)
 #pragma unroll
-                        for (int px = 0; px < 2; ++px) {
+                for (int du = -1; du <= 1; ++du) {
+                    const int u = py + 2 - 2 * du;
+                    if (u < 0 || u > 4) continue;
+#pragma unroll
+                    for (int px = 0; px < 2; ++px)
+#pragma unroll
+                        for (int dv = -1; dv <= 1; ++dv) {
                             const int v = px + 2 - 2 * dv;
                             if (v < 0 || v > 4) continue;
                             const float4 wv = *reinterpret_cast<const float4 *>(&ws[c][u * 5 + v][0]);
-                            acc[py][px][0] = fmaf(x, wv.x, acc[py][px][0]);
-                            acc[py][px][1] = fmaf(x, wv.y, acc[py][px][1]);
-                            acc[py][px][2] = fmaf(x, wv.z, acc[py][px][2]);
-                            acc[py][px][3] = fmaf(x, wv.w, acc[py][px][3]);
+                            const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+                            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                                for (int cc = 0; cc < 2; ++cc) {
+                                    const float xv = x[1 + a + du][1 + cc + dv];
+#pragma unroll
+                                    for (int o = 0; o < COUT; ++o)
+                                        acc[a][cc][py][px][o] = fmaf(xv, wk[o], acc[a][cc][py][px][o]);
+                                }
                         }
-                    }
                 }
         }
         __syncthreads();
     }
-    if (m >= Hi || n >= Wi) return;
     const int Ho = 2 * Hi, Wo = 2 * Wi;
 #pragma unroll
-    for (int py = 0; py < 2; ++py)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int px = 0; px < 2; ++px) {
-            float *o = out + (((int64_t)b * Ho + 2 * m + py) * Wo + 2 * n + px) * Cout;
+        for (int cc = 0; cc < 2; ++cc) {
+            const int m = m0 + 2 * tr + a, n = n0 + 2 * tc + cc;
+            if (m >= Hi || n >= Wi) continue;
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (k < Cout) o[k] = acc[py][px][k] + bias[k];
+            for (int py = 0; py < 2; ++py)
+#pragma unroll
+                for (int px = 0; px < 2; ++px) {
+                    float *o = out + (((int64_t)b * Ho + 2 * m + py) * Wo + 2 * n + px) * COUT;
+#pragma unroll
+                    for (int k = 0; k < COUT; ++k) o[k] = acc[a][cc][py][px][k] + __ldg(bias + k);
+                }
         }
 }
 
@@ -244,7 +257,12 @@ __global__ void __launch_bounds__(DS_TR * DS_TC) deconv_small_kernel(const float
 void launch_deconv_small(const float *in, int B, int Hi, int Wi, int Cin, const float *w, const float *bias, int Cout,
                          float *out, cudaStream_t st) {
     dim3 grid((Wi + DS_TC - 1) / DS_TC, (Hi + DS_TR - 1) / DS_TR, B);
-    deconv_small_kernel<<<grid, DS_TR * DS_TC, 0, st>>>(in, B, Hi, Wi, Cin, w, bias, Cout, out);
+    switch (Cout) {
+        case 1: deconv_small_kernel<1><<<grid, DS_THREADS, 0, st>>>(in, B, Hi, Wi, Cin, w, bias, out); break;
+        case 2: deconv_small_kernel<2><<<grid, DS_THREADS, 0, st>>>(in, B, Hi, Wi, Cin, w, bias, out); break;
+        case 3: deconv_small_kernel<3><<<grid, DS_THREADS, 0, st>>>(in, B, Hi, Wi, Cin, w, bias, out); break;
+        default: deconv_small_kernel<4><<<grid, DS_THREADS, 0, st>>>(in, B, Hi, Wi, Cin, w, bias, out); break;
+    }
 }
 
 void launch_conv_simt(const ConvDesc &d, cudaStream_t st) {

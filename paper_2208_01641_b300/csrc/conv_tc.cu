@@ -180,6 +180,32 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// A operand from tensor memory (lanes = rows, one 32-bit column per K element)
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+        "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+        "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -201,10 +227,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Round to TF32 (10 stored mantissa bits), to nearest, ties away from zero:
+// add half of the 13 dropped bits to the magnitude, then clear them.  Same
+// result as cvt.rna.tf32.f32 for finite values, at integer-ALU rate.
 __device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
@@ -237,6 +264,11 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 // accumulates n (K = C, short enough for one TMEM accumulator) in HALF
 // passes of two 32-channel chunks each.  The output is y * rsqrt(n) (GDN) or
 // y * sqrt(n) (IGDN); y itself never reaches global memory.
+// ATM (Cout = 128): the split A operand lives in TMEM instead of shared
+// memory (tcgen05.mma with A from tensor memory).  A stage then holds only
+// the float32 box and the weights (48 KB), so four stages fit and buffer
+// more MMA work against the latency of TMA plus the split; TMEM holds two
+// partial sums (2 x 128 columns) and a hi / lo A slot per stage (4 x 64).
 template <int STAGES, int HALF>  // HALF: 32-column blocks per epilogue thread (Cout = 64 * HALF)
 __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                       const __grid_constant__ CUtensorMap tmBh,
@@ -248,7 +280,15 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int COUT = 64 * HALF;
     constexpr int B_BYTES = COUT * KCH * 4;
-    constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    constexpr bool ATM = (HALF == 2);
+    constexpr int A_STAGE_BYTES = ATM ? A_BYTES : 2 * A_BYTES;
+    constexpr int STAGE_BYTES = A_STAGE_BYTES + 2 * B_BYTES;
+    static_assert(!ATM || 2 * COUT + STAGES * 2 * KCH <= 512, "TMEM budget");
+    // fused GDN: ATM runs the norm GEMM as one pass over all COUT/32 chunks
+    // (one per stage and A slot); otherwise HALF passes of two chunks
+    constexpr int GPASS = ATM ? 1 : HALF;
+    constexpr int GCH = ATM ? COUT / KCH : 2;
+    static_assert(!ATM || GCH <= STAGES, "one stage per norm chunk");
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
     uint64_t *full = bars, *conv = bars + STAGES, *empty = bars + 2 * STAGES;
     uint64_t *pfull = bars + 3 * STAGES, *pempty = pfull + 2;
@@ -296,9 +336,12 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
     const uint32_t tmem = *tmem_slot;
 
     auto stage_a = [&](int s) { return smem + s * STAGE_BYTES; };
-    auto stage_alo = [&](int s) { return smem + s * STAGE_BYTES + A_BYTES; };
-    auto stage_bh = [&](int s) { return smem + s * STAGE_BYTES + 2 * A_BYTES; };
-    auto stage_bl = [&](int s) { return smem + s * STAGE_BYTES + 2 * A_BYTES + B_BYTES; };
+    auto stage_alo = [&](int s) { return smem + s * STAGE_BYTES + A_BYTES; };   // !ATM only
+    auto stage_bh = [&](int s) { return smem + s * STAGE_BYTES + A_STAGE_BYTES; };
+    auto stage_bl = [&](int s) { return smem + s * STAGE_BYTES + A_STAGE_BYTES + B_BYTES; };
+    // ATM: TMEM columns of the hi / lo A slot of stage s
+    auto slot_hi = [&](int s) { return tmem + (uint32_t)(2 * COUT + s * 2 * KCH); };
+    auto slot_lo = [&](int s) { return tmem + (uint32_t)(2 * COUT + s * 2 * KCH + KCH); };
     auto fail = [&]() {
         *abort_flag = 1;
         atomicOr(p.status, ST_TIMEOUT);
@@ -334,16 +377,17 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
             }
             // gamma slices for the fused norm: pass h uses stages 0 and 1 once
             // the MMAs that read them (main loop, then pass h-1) are done
-            for (int h = 0; p.fuse_gdn && h < HALF && !*abort_flag; ++h) {
+            for (int h = 0; p.fuse_gdn && h < GPASS && !*abort_flag; ++h) {
                 if (!mbar_wait(mma_done, h & 1)) {
                     fail();
                     break;
                 }
-                mbar_expect_tx(gdn_full, 4 * B_BYTES);
-                tma_load_2d(stage_bh(0), &tmGh, gdn_full, h * KCH, 0);
-                tma_load_2d(stage_bl(0), &tmGl, gdn_full, h * KCH, 0);
-                tma_load_2d(stage_bh(1), &tmGh, gdn_full, (HALF + h) * KCH, 0);
-                tma_load_2d(stage_bl(1), &tmGl, gdn_full, (HALF + h) * KCH, 0);
+                mbar_expect_tx(gdn_full, 2 * GCH * B_BYTES);
+                for (int c = 0; c < GCH; ++c) {
+                    const int chunk = ATM ? c : (c == 0 ? h : HALF + h);
+                    tma_load_2d(stage_bh(c), &tmGh, gdn_full, chunk * KCH, 0);
+                    tma_load_2d(stage_bl(c), &tmGl, gdn_full, chunk * KCH, 0);
+                }
             }
             if (*abort_flag) {  // wait (bounded) for loads still in flight
                 for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc)
@@ -369,39 +413,57 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                     break;
                 }
                 tc_fence_after();
-                const uint32_t ah = smem_u32(stage_a(s)), al = smem_u32(stage_alo(s));
                 const uint32_t bh = smem_u32(stage_bh(s)), bl = smem_u32(stage_bl(s));
+                if constexpr (ATM) {
 #pragma unroll
-                for (int kk = 0; kk < KCH / 8; ++kk) {
-                    const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
-                    const uint64_t dah = sdesc(ah + off), dal = sdesc(al + off);
-                    const uint64_t dbh = sdesc(bh + off), dbl = sdesc(bl + off);
-                    mma_tf32(dt, dah, dbh, idesc, (kc % FOLD != 0 || kk > 0) ? 1u : 0u);
-                    mma_tf32(dt, dah, dbl, idesc, 1u);
-                    mma_tf32(dt, dal, dbh, idesc, 1u);
+                    for (int kk = 0; kk < KCH / 8; ++kk) {
+                        const uint32_t off = kk * 32;   // 8 tf32 along K: 32 bytes in smem, 8 columns in TMEM
+                        const uint64_t dbh = sdesc(bh + off), dbl = sdesc(bl + off);
+                        mma_tf32_ts(dt, slot_hi(s) + 8 * kk, dbh, idesc, (kc % FOLD != 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32_ts(dt, slot_hi(s) + 8 * kk, dbl, idesc, 1u);
+                        mma_tf32_ts(dt, slot_lo(s) + 8 * kk, dbh, idesc, 1u);
+                    }
+                } else {
+                    const uint32_t ah = smem_u32(stage_a(s)), al = smem_u32(stage_alo(s));
+#pragma unroll
+                    for (int kk = 0; kk < KCH / 8; ++kk) {
+                        const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
+                        const uint64_t dah = sdesc(ah + off), dal = sdesc(al + off);
+                        const uint64_t dbh = sdesc(bh + off), dbl = sdesc(bl + off);
+                        mma_tf32(dt, dah, dbh, idesc, (kc % FOLD != 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32(dt, dah, dbl, idesc, 1u);
+                        mma_tf32(dt, dal, dbh, idesc, 1u);
+                    }
                 }
                 mma_commit(&empty[s]);
                 if (kc % FOLD == FOLD - 1 || kc == p.kchunks - 1) mma_commit(&pfull[q]);
             }
             mma_commit(mma_done);   // phase 0: the main loop's MMAs are complete
-            for (int h = 0; p.fuse_gdn && h < HALF; ++h) {
+            for (int h = 0; p.fuse_gdn && h < GPASS; ++h) {
                 if (*abort_flag || !mbar_wait(gdn_ready, h & 1) || !mbar_wait(gdn_full, h & 1)) {
                     fail();
                     break;
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const uint32_t ah = smem_u32(stage_a(c)), al = smem_u32(stage_alo(c));
+                for (int c = 0; c < GCH; ++c) {
                     const uint32_t bh = smem_u32(stage_bh(c)), bl = smem_u32(stage_bl(c));
 #pragma unroll
                     for (int kk = 0; kk < KCH / 8; ++kk) {
                         const uint32_t off = kk * 32;
-                        const uint64_t dah = sdesc(ah + off), dal = sdesc(al + off);
                         const uint64_t dbh = sdesc(bh + off), dbl = sdesc(bl + off);
-                        mma_tf32(tmem, dah, dbh, idesc, (h > 0 || c > 0 || kk > 0) ? 1u : 0u);
-                        mma_tf32(tmem, dah, dbl, idesc, 1u);
-                        mma_tf32(tmem, dal, dbh, idesc, 1u);
+                        const uint32_t acc = (h > 0 || c > 0 || kk > 0) ? 1u : 0u;
+                        if constexpr (ATM) {
+                            mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dbh, idesc, acc);
+                            mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dbl, idesc, 1u);
+                            mma_tf32_ts(tmem, slot_lo(c) + 8 * kk, dbh, idesc, 1u);
+                        } else {
+                            const uint64_t dah = sdesc(smem_u32(stage_a(c)) + off);
+                            const uint64_t dal = sdesc(smem_u32(stage_alo(c)) + off);
+                            mma_tf32(tmem, dah, dbh, idesc, acc);
+                            mma_tf32(tmem, dah, dbl, idesc, 1u);
+                            mma_tf32(tmem, dal, dbh, idesc, 1u);
+                        }
                     }
                 }
                 mma_commit(mma_done);   // phase h + 1
@@ -438,6 +500,26 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
         };
         for (int kc = 0; kc < p.kchunks && ok; ++kc) {
             const int s = kc % STAGES;
+            // MODE_IM2COL (ATM): gather this chunk's A values from global memory
+            // first, overlapping the weights' TMA; slot s is written only after
+            // full[s] shows the stage (and so the slot) is free again
+            float gv[16];
+            if (ATM && p.mode == MODE_IM2COL) {
+                const int m = quarter * 32 + lane;
+                const int gi = i0 + m / p.Wt, gj = j0 + m % p.Wt;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int k = kc * KCH + 16 * half + e;
+                    const int t = k / p.Cin, c = k - t * p.Cin;
+                    float x = 0.f;
+                    if (t < p.T) {
+                        const int yi = p.s * gi + p.du[t], xi = p.s * gj + p.dv[t];
+                        if (yi >= 0 && yi < p.Hi && xi >= 0 && xi < p.Wi)
+                            x = __ldg(p.in + (((int64_t)b * p.Hi + yi) * p.Wi + xi) * p.Cin + c);
+                    }
+                    gv[e] = x;
+                }
+            }
             if (*abort_flag || !mbar_wait(&full[s], (kc / STAGES) & 1)) {
                 fail();
                 ok = false;
@@ -445,7 +527,34 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
             }
             float4 *a = reinterpret_cast<float4 *>(stage_a(s));
             float4 *alo = reinterpret_cast<float4 *>(stage_alo(s));
-            if (p.mode == MODE_IM2COL) {
+            if constexpr (ATM) {
+                // row m = this thread's TMEM lane, columns [16 * hc, 16 * hc + 16) of the chunk
+                const int m = quarter * 32 + lane, hc = half;
+                float v[16], hv[16], lv[16];
+                if (p.mode == MODE_IM2COL) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[e] = gv[e];
+                } else {
+                    const uint8_t *row = stage_a(s) + m * 128;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 f = *reinterpret_cast<const float4 *>(row + (((4 * hc + q) ^ (m & 7)) << 4));
+                        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    float x = v[e];
+                    if (p.in_xform == IN_ABS) x = fabsf(x);
+                    else if (p.in_xform == IN_SQUARE) x = x * x;
+                    hv[e] = tf32_rna(x);
+                    lv[e] = tf32_rna(x - hv[e]);
+                }
+                tmem_st16(slot_hi(s) + ((uint32_t)(quarter * 32) << 16) + 16 * hc, hv);
+                tmem_st16(slot_lo(s) + ((uint32_t)(quarter * 32) << 16) + 16 * hc, lv);
+                tmem_st_wait();
+                tc_fence_before();
+            } else if (p.mode == MODE_IM2COL) {
                 // row m of the tile, 16 consecutive K entries [kc*32 + 16*kh, +16)
                 const int m = et >> 1, kh = et & 1;
                 const int gi = i0 + m / p.Wt, gj = j0 + m % p.Wt;
@@ -504,8 +613,30 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
 #pragma unroll
             for (int i = 0; i < HALF * 32; ++i) master[i] += __ldg(p.bias + cbase + i);
             const int m = quarter * 32 + lane;
+            if constexpr (ATM) {
+                // this thread's chunks (HALF of them) -> TMEM A slots HALF*half + h, its lane
+                const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
 #pragma unroll
-            for (int h = 0; h < HALF; ++h) {
+                for (int h = 0; h < HALF; ++h) {
+                    float hv[32], lv[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float sq = master[h * 32 + i] * master[h * 32 + i];
+                        hv[i] = tf32_rna(sq);
+                        lv[i] = tf32_rna(sq - hv[i]);
+                    }
+                    const int slot = HALF * half + h;
+                    tmem_st16(slot_hi(slot) + lane_off, hv);
+                    tmem_st16(slot_hi(slot) + lane_off + 16, hv + 16);
+                    tmem_st16(slot_lo(slot) + lane_off, lv);
+                    tmem_st16(slot_lo(slot) + lane_off + 16, lv + 16);
+                }
+                tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(gdn_ready);
+            }
+#pragma unroll
+            for (int h = 0; h < (ATM ? 0 : HALF); ++h) {
                 if (h > 0 && (*abort_flag || !mbar_wait(mma_done, h & 1))) {
                     fail();
                     ok = false;
@@ -531,7 +662,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 tc_fence_before();
                 mbar_arrive(gdn_ready);
             }
-            if (ok && (*abort_flag || !mbar_wait(mma_done, HALF & 1))) {
+            if (ok && (*abort_flag || !mbar_wait(mma_done, GPASS & 1))) {
                 fail();
                 ok = false;
             }
@@ -647,13 +778,14 @@ uint32_t tf32_rna_host(float x) {
     return u & ~0x1fffu;
 }
 
-int stages_for(int Cout) {
-    const int stage = 2 * A_BYTES + 2 * Cout * KCH * 4;
-    const int n = (220 * 1024) / stage;
-    return n >= 3 ? 3 : n;
-}
+// Cout = 128: A in TMEM, 4 stages of 48 KB; Cout = 192: A in shared memory,
+// 2 stages of 80 KB.
+int stages_for(int Cout) { return Cout == 128 ? 4 : 2; }
 
-int smem_bytes(int stages, int Cout) { return stages * (2 * A_BYTES + 2 * Cout * KCH * 4) + 256 + 1024; }
+int smem_bytes(int stages, int Cout) {
+    const int a = Cout == 128 ? A_BYTES : 2 * A_BYTES;
+    return stages * (a + 2 * Cout * KCH * 4) + 256 + 1024;
+}
 
 template <int STAGES, int HALF>
 void launch_kernel(unsigned grid, int smem, cudaStream_t st, const CUtensorMap &a, const CUtensorMap &bh,
@@ -773,7 +905,7 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.in_xform = d.in_xform;
     p.fuse_gdn = d.fuse_gdn;
     p.gdn_beta = d.gdn_beta;
-    p.tmem_cols = 2 * d.Cout <= 256 ? 256 : 512;  // two partial buffers
+    p.tmem_cols = 512;  // partial sums (+ A slots when Cout = 128)
     for (int t = 0; t < d.T; ++t) {
         p.du[t] = d.du[t];
         p.dv[t] = d.dv[t];
@@ -826,7 +958,7 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
                                    : maps;
     const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
     if (d.Cout == 128)
-        launch_kernel<3, 2>(grid, smem, st, tmA, maps[0], maps[1], gmaps[0], gmaps[1], p);
+        launch_kernel<4, 2>(grid, smem, st, tmA, maps[0], maps[1], gmaps[0], gmaps[1], p);
     else
         launch_kernel<2, 3>(grid, smem, st, tmA, maps[0], maps[1], gmaps[0], gmaps[1], p);
     return true;
