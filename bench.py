@@ -315,12 +315,15 @@ def roofline(rep, peaks):
     bf16 = peaks.get("bf16_tflops", 1800.0)
     sm_mhz = peaks.get("sm_max_mhz", 2032.0)
     name = top["name"]
+    extra = {}
     if name.endswith(":tc"):
         # TF32 tensor peak = measured BF16 dense x nominal TF32/BF16 ratio (1.1/2.25)
         peak = bf16 * 1.1 / 2.25
         ach = top["flop"] / top["launches"] / (per_ms * 1e-3) / 1e12
         bound, unit = "tensor", "TFLOP/s"
-        note = "3xTF32 on tcgen05: algorithmic FP32 flops over the TF32 peak (measured BF16 x 1.1/2.25)"
+        note = ("FP32-accurate 3xTF32 on tcgen05: algorithmic FP32 flops over the TF32 peak (measured BF16 "
+                "x 1.1/2.25); three TF32 MMAs per product bound the algorithmic rate at a third of it")
+        extra = {"ceiling_3xtf32": peak / 3, "frac_of_3xtf32_ceiling": ach / (peak / 3)}
     elif top["flop"] > 0:
         # FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock
         peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -332,8 +335,16 @@ def roofline(rep, peaks):
         ach = top["bytes"] / top["launches"] / (per_ms * 1e-3) / 1e9
         bound, unit = "hbm", "GB/s"
         note = "measured HBM copy bandwidth"
-    return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-            "traffic": None, "launch_ms": per_ms, "launches_per_step": top["launches"] / 3, "note": note}
+    out = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+           "traffic": TRAFFIC.get(name), "launch_ms": per_ms, "launches_per_step": top["launches"] / 3,
+           "note": note, "peak_source": "MEASURED_PEAKS.json" if peaks else "fallback"}
+    out.update(extra)
+    return out
+
+
+# DRAM bytes (read + write) per launch of the dominant kernels, from the ncu
+# captures summarised in profiles/ (None until a capture of the current build)
+TRAFFIC = {}
 
 
 def psnr_vs_oracle(codec, Wt, B):
