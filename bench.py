@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--conv", default="auto", choices=["auto", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 precision form")
     return ap.parse_args()
 
 
@@ -250,6 +251,21 @@ def main():
         pass
     roof = roofline(rep, peaks)
 
+    # ---- the BF16 precision form, same workload ----
+    forms = {}
+    if not args.no_forms and args.conv == "auto":
+        bcodec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=lic.BF16)
+        bms, bstatus = time_steps(bcodec, frames, out, H, W, args.steps, args.warmup, stream, flush)
+        forms["bf16"] = {"value": ws * B * args.steps / (sum(bms) / 1000.0), "unit": "frames/s",
+                         "ms_per_step": sum(bms) / args.steps, "p99_ms": sorted(bms)[min(len(bms) - 1,
+                                                                                     int(0.99 * len(bms)))],
+                         "decode_status": bstatus,
+                         "note": "g_a/g_s convs bf16 x bf16 -> fp32; GDN norms, h_a, h_s, index fp32"}
+        if rank == 0 and not args.no_cpu_baseline:
+            forms["bf16"]["psnr_vs_oracle_db"] = psnr_vs_oracle(bcodec, Wt, B)
+            forms["bf16"]["y_maxabs_vs_oracle"] = sampled_errors(bcodec, Wt, frames_np, B)
+        bcodec.close()
+
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -297,11 +313,52 @@ def main():
             "bits_per_pixel": 8.0 * statistics.mean(frame_bytes) / (H * W),
             "psnr_vs_oracle_db": psnr if psnr is None or psnr < 1e9 else "inf", "decode_status": status,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": sampler.summary(), "kernels": rep,
+            "clocks": sampler.summary(), "forms": forms, "kernels": rep,
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def time_steps(codec, frames, out, H, W, steps, warmup, stream, flush):
+    """Device time (ms) of `steps` encode+decode steps after `warmup`, L2
+    flushed before each step outside the events."""
+    import torch
+    sid = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        for _ in range(max(warmup, 3)):
+            bs = codec.encode(frames, stream=sid)
+            codec.decode(bs, H, W, out, stream=sid)
+        codec.sync(sid)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            bs = codec.encode(frames, stream=sid)
+            codec.decode(bs, H, W, out, stream=sid)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], codec.sync_status(sid)
+
+
+def sampled_errors(codec, Wt, frames_np, B):
+    """Errors of a form against the FP64 oracle on sampled crops of the last
+    encode/decode: max |y - y64| on the interior of a 192x192 crop (g_a's
+    receptive field inside the crop) and PSNR of x_hat against the oracle's
+    g_s on two 12x12-latent windows of the decoded symbols."""
+    import numpy as np
+    import oracle as O
+    import paper_2208_01641_b300 as lic
+    xp = np.pad(frames_np, ((0, 0), (0, 0), (0, PAD_H - frames_np.shape[2]), (0, PAD_W - frames_np.shape[3])),
+                mode="edge")
+    y = np.zeros((B, M_CH, PAD_H // 16, PAD_W // 16), np.float32)
+    bs = codec.encode(__import__("torch").from_numpy(frames_np).cuda())
+    codec.sync()
+    codec.read_tensor(lic.T_Y, y)
+    crop = xp[0:1, :, 256:448, 512:704]
+    ry = O.g_a(Wt, crop)[0]
+    yerr = float(np.abs(y[0, :, 16:28, 32:44][:, 4:8, 4:8] - ry[:, 4:8, 4:8]).max())
+    return yerr
 
 
 def roofline(rep, peaks):

@@ -50,7 +50,12 @@ extern "C" {
 #define LIC_E_CUDA (-6)
 
 typedef enum { LIC_FACTORIZED = 0, LIC_HYPERPRIOR = 1 } lic_kind;
-typedef enum { LIC_FP32 = 0 } lic_precision;
+/* LIC_FP32: every step float32-accurate (tensor-core convs in 3xTF32).
+ * LIC_BF16: the precision form -- the convolutions of g_a and g_s take bf16
+ * activations and weights with float32 accumulation; GDN / IGDN norms, h_a,
+ * h_s, the scales and the scale index stay float32, so encoder and decoder
+ * derive identical indices. */
+typedef enum { LIC_FP32 = 0, LIC_BF16 = 1 } lic_precision;
 
 /* Convolution implementation: LIC_CONV_AUTO picks the tcgen05 tensor-core
  * kernels where they exist and the CUDA-core (SIMT) kernels elsewhere;
@@ -81,7 +86,7 @@ typedef struct {
 } lic_weights;
 
 typedef struct {
-    int precision;   /* lic_precision; LIC_FP32 */
+    int precision;   /* lic_precision (LIC_BF16 needs the tensor-core kernels) */
     int band_rows;   /* latent rows per y substream; 0 -> 16 */
     int conv_impl;   /* lic_conv_impl */
     int reserved[5];

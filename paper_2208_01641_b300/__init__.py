@@ -21,6 +21,8 @@ FACTORIZED = 0
 HYPERPRIOR = 1
 CONV_AUTO = 0
 CONV_SIMT = 1
+FP32 = 0
+BF16 = 1
 
 T_Y, T_SY, T_Z, T_SZ, T_SIGMA, T_IDX, T_XPRE = range(7)
 
@@ -211,10 +213,10 @@ class Codec:
     """One codec on the current CUDA device (lic_codec_create)."""
 
     def __init__(self, kind: int, N: int, M: int, weights: Dict[str, np.ndarray], band_rows: int = 16,
-                 conv_impl: int = CONV_AUTO):
+                 conv_impl: int = CONV_AUTO, precision: int = FP32):
         self.kind, self.N, self.M = kind, N, M
         w, keep = _weights_struct(weights)
-        opt = _Options(0, band_rows, conv_impl)
+        opt = _Options(precision, band_rows, conv_impl)
         h = ctypes.c_void_p()
         _check(_lib().lic_codec_create(kind, N, M, ctypes.byref(w), ctypes.byref(opt), ctypes.byref(h)),
                "lic_codec_create")

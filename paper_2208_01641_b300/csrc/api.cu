@@ -75,6 +75,7 @@ struct Layer {
     int in_xform = IN_NONE, epi = EPI_NONE;
     DevBuf bias;
     DevBuf w_small;  // transposed conv to <= 4 channels: [Cin][5][5][4]
+    int in_bf16 = 0, out_bf16 = 0;   // BF16 form: activation storage of this layer
     std::vector<std::unique_ptr<ConvOp>> ops;
 };
 
@@ -137,6 +138,14 @@ bool is_device_ptr(const void *p) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void atomic_status(const lic_codec *cd, uint32_t bits) {
+    // a launch that could not be made (host side): latch it like a kernel would
+    uint32_t cur = 0;
+    cudaMemcpy(&cur, cd->status.p, 4, cudaMemcpyDeviceToHost);
+    cur |= bits;
+    cudaMemcpy(cd->status.p, &cur, 4, cudaMemcpyHostToDevice);
 }
 
 cudaEvent_t next_event(lic_codec *cd) {
@@ -313,6 +322,8 @@ ConvDesc op_desc(const lic_codec *cd, const Layer &L, const ConvOp &op, const fl
     }
     d.in_xform = L.in_xform;
     d.epi = L.epi;
+    d.in_bf16 = L.in_bf16;
+    d.out_bf16 = L.out_bf16;
     if (L.deconv) {
         d.Gh = Hi;
         d.Gw = Wi;
@@ -348,6 +359,13 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
         d.gdn_w = &G->tcw;
         flop += 2.0 * rows * G->C * G->C;
         nm += "+" + G->name.substr(G->name.find('.') + 1);
+    }
+    if (d.in_bf16) {   // BF16 form: checked at codec creation
+        nm += ":bf16";
+        timed(const_cast<lic_codec *>(cd), nm, flop, bytes, 1, st, [&] {
+            if (!tc::launch_bf16(d, op.tcw, st)) atomic_status(cd, ST_TIMEOUT);
+        });
+        return;
     }
     const bool use_tc = cd->opt.conv_impl != LIC_CONV_SIMT && tc::can_run(d, op.tcw);
     nm += use_tc ? ":tc" : ":simt";
@@ -439,7 +457,7 @@ float *run_layer_gdn(const lic_codec *cd, const Layer &L, const Gdn &G, const fl
         d.fuse_gdn = G.inverse ? 2 : 1;
         d.gdn_beta = G.beta.as<float>();
         d.gdn_w = &G.tcw;
-        fuse = tc::can_run(d, op->tcw);
+        fuse = d.in_bf16 ? tc::can_run_bf16(d, op->tcw) : tc::can_run(d, op->tcw);
     }
     if (fuse) {
         for (auto &op : L.ops) run_op(cd, L, *op, in, B, Hi, Wi, out, Ho, Wo, st, &G);
@@ -537,6 +555,11 @@ void synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, cudaStre
     float *a = cd->act0.as<float>(), *b = cd->act1.as<float>();
     int H = Hy, W = Wy;
     const float *in = yhat;
+    if (cd->gs[0].in_bf16) {   // BF16 form: g_s takes y_hat as bf16
+        const int64_t n = (int64_t)B * Hy * Wy * cd->M;
+        timed(cd, "to_bf16", 0, 6.0 * n, 1, st, [&] { launch_to_bf16(yhat, n, a, st); });
+        in = a;
+    }
     for (int i = 0; i < 3; ++i) {
         in = run_layer_gdn(cd, cd->gs[i], cd->igdn[i], in, B, H, W, a, b, st);
         H *= 2;
@@ -759,7 +782,8 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
     cd->M = M;
     if (opts) cd->opt = *opts;
     if (cd->opt.band_rows <= 0) cd->opt.band_rows = 16;
-    if (cd->opt.precision != LIC_FP32) return LIC_E_UNSUPPORTED;
+    if (cd->opt.precision != LIC_FP32 && cd->opt.precision != LIC_BF16) return LIC_E_UNSUPPORTED;
+    if (cd->opt.precision == LIC_BF16 && cd->opt.conv_impl == LIC_CONV_SIMT) return LIC_E_UNSUPPORTED;
     LIC_CUDA_TRY(cudaGetDevice(&cd->device));
     LIC_CUDA_TRY(upload_scale_table());
     ParamMap pm = param_map(weights);
@@ -782,6 +806,29 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
         if ((rc = make_deconv(cd->hs[0], pm, "h_s.deconv0", N, N, EPI_RELU))) return rc;
         if ((rc = make_deconv(cd->hs[1], pm, "h_s.deconv1", N, N, EPI_RELU))) return rc;
         if ((rc = make_conv(cd->hs[2], pm, "h_s.conv2", N, M, 3, 1, IN_NONE, EPI_RELU))) return rc;
+    }
+    if (cd->opt.precision == LIC_BF16) {
+        // bf16 activations flow g_a conv0 -> conv1 -> conv2 -> conv3 and
+        // y_hat -> g_s deconv0 -> deconv1 -> deconv2; y and the input of the
+        // last (CUDA-core) layer of g_s stay float32
+        cd->ga[0].out_bf16 = 1;
+        for (int i = 1; i < 4; ++i) {
+            cd->ga[i].in_bf16 = 1;
+            cd->ga[i].out_bf16 = i < 3;
+        }
+        for (int i = 0; i < 3; ++i) {
+            cd->gs[i].in_bf16 = 1;
+            cd->gs[i].out_bf16 = i < 2;
+        }
+        for (int i = 1; i < 4; ++i)
+            for (auto &op : cd->ga[i].ops)
+                if (!op->tcw.bvalid) return LIC_E_UNSUPPORTED;
+        for (int i = 0; i < 3; ++i)
+            for (auto &op : cd->gs[i].ops)
+                if (!op->tcw.bvalid) return LIC_E_UNSUPPORTED;
+        for (int i = 0; i < 3; ++i)
+            if (!cd->gdn[i].tcw.valid || !cd->igdn[i].tcw.valid || N != 128) return LIC_E_UNSUPPORTED;
+        if (!cd->ga[0].ops[0]->tcw.valid) return LIC_E_UNSUPPORTED;
     }
     // entropy models: the bottleneck codes y (factorized) or z (hyperprior)
     const int C = kind == LIC_FACTORIZED ? M : N;

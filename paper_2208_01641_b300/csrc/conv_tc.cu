@@ -38,6 +38,7 @@
 // Every wait on an mbarrier is bounded; a wait that runs out latches
 // ST_TIMEOUT in the codec status word and the CTA winds down.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include <cstring>
 #include <mutex>
@@ -76,6 +77,7 @@ struct Params {
     const float *in;              // MODE_IM2COL: NHWC input
     int Hi, Wi, s;                // MODE_IM2COL: input size, stride
     int fuse_gdn;                 // 0, 1 (GDN) or 2 (IGDN) applied after bias
+    int out_bf16;                 // store the output as bf16
     const float *gdn_beta;
     int kchunks;
     uint32_t tmem_cols;
@@ -225,6 +227,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16_f(float a, float b) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
 }
 
 // Round to TF32 (10 stored mantissa bits), to nearest, ties away from zero:
@@ -694,7 +701,15 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 valid = gi < p.Gh && gj < p.Gw;
                 opix = ((int64_t)b * p.Ho + p.oym * gi + p.oyo) * p.Wo + p.oxm * gj + p.oxo;
             }
-            if (valid && p.fuse_gdn) {
+            if (valid && p.fuse_gdn && p.out_bf16) {
+                uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(p.out) + opix * COUT + cbase);
+#pragma unroll
+                for (int q = 0; q < HALF * 4; ++q)
+                    dst[q] = make_uint4(pack_bf16_f(master[8 * q], master[8 * q + 1]),
+                                        pack_bf16_f(master[8 * q + 2], master[8 * q + 3]),
+                                        pack_bf16_f(master[8 * q + 4], master[8 * q + 5]),
+                                        pack_bf16_f(master[8 * q + 6], master[8 * q + 7]));
+            } else if (valid && p.fuse_gdn) {
                 float4 *dst = reinterpret_cast<float4 *>(p.out + opix * COUT + cbase);
 #pragma unroll
                 for (int q = 0; q < HALF * 8; ++q)
@@ -731,6 +746,291 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
     }
 }
 
+
+// ------------------------------------------------------------------ BF16 kernel
+//
+// The BF16 precision form: activations between BF16 layers are bf16 NHWC in
+// HBM, weights bf16, the MMA is kind::f16 (BF16 x BF16 -> FP32 in TMEM).  A
+// K chunk is 64 channels (one 128-byte swizzle row), so TMA feeds the MMA
+// directly and the eight epilogue warps only fold partial sums.  Anything
+// that decides an integer or normalises stays FP32: the fused GDN / IGDN
+// norm is the same 3xTF32 GEMM on the FP32 sum as in the FP32 kernel.
+
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4)                       // D: f32
+           | (1u << 7) | (1u << 10)        // A, B: bf16
+           | ((uint32_t)(N >> 3) << 17)
+           | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+    const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+    return lo | (hi << 16);
+}
+
+constexpr int KCB = 64;                        // bf16 per K chunk
+constexpr int AB_BYTES = BLOCK_M * KCB * 2;    // 16 KB
+
+template <int STAGES, int HALF>
+__global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                        const __grid_constant__ CUtensorMap tmB,
+                                                                        const __grid_constant__ CUtensorMap tmGh,
+                                                                        const __grid_constant__ CUtensorMap tmGl,
+                                                                        const __grid_constant__ Params p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int COUT = 64 * HALF;
+    constexpr int BB_BYTES = COUT * KCB * 2;
+    constexpr int STAGE_BYTES = AB_BYTES + BB_BYTES;
+    constexpr int GCH = COUT / KCH;            // tf32 chunks of the fused norm (COUT = 128 only)
+    constexpr int GB = COUT * KCH * 4;         // bytes of one gamma chunk (hi or lo)
+    static_assert(HALF != 2 || (GCH <= STAGES && GB <= AB_BYTES && GB <= BB_BYTES), "norm operands fit the stages");
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *full = bars, *empty = bars + STAGES;
+    uint64_t *pfull = bars + 2 * STAGES, *pempty = pfull + 2;
+    uint64_t *gdn_full = pempty + 2, *gdn_ready = gdn_full + 1, *mma_done = gdn_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gdn_full + 3);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int groups = (p.kchunks + FOLD - 1) / FOLD;
+    int b = 0, i0 = 0, j0 = 0;
+    {
+        int t = blockIdx.x;
+        const int tx = t % p.tiles_x;
+        t /= p.tiles_x;
+        const int ty = t % p.tiles_y;
+        b = t / p.tiles_y;
+        i0 = ty * p.R;
+        j0 = tx * p.Wt;
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&pfull[q], 1);
+            mbar_init(&pempty[q], EPI_THREADS);
+        }
+        mbar_init(gdn_full, 1);
+        mbar_init(gdn_ready, EPI_THREADS);
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, p.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    auto stage_a = [&](int s) { return smem + s * STAGE_BYTES; };
+    auto stage_b = [&](int s) { return smem + s * STAGE_BYTES + AB_BYTES; };
+    // norm A operand (y^2 hi / lo) in TMEM after the two partial buffers
+    auto slot_hi = [&](int c) { return tmem + (uint32_t)(2 * COUT + c * 2 * KCH); };
+    auto slot_lo = [&](int c) { return tmem + (uint32_t)(2 * COUT + c * 2 * KCH + KCH); };
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(p.status, ST_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kc = 0; kc < p.kchunks && !*abort_flag; ++kc) {
+                const int s = kc % STAGES;
+                if (!mbar_wait(&empty[s], ((kc / STAGES) & 1) ^ 1)) {
+                    fail();
+                    break;
+                }
+                const int t = kc / p.cpt;
+                const int c0 = (kc % p.cpt) * KCB;
+                mbar_expect_tx(&full[s], AB_BYTES + BB_BYTES);
+                if (p.mode == MODE_S2) {
+                    const int du = p.du[t], dv = p.dv[t];
+                    tma_load_5d(stage_a(s), &tmA, &full[s], (dv & 1) * p.Cin + c0, j0 + (dv >> 1), du & 1,
+                                i0 + (du >> 1), b);
+                } else {
+                    tma_load_4d(stage_a(s), &tmA, &full[s], c0, j0 + p.dv[t], i0 + p.du[t], b);
+                }
+                tma_load_2d(stage_b(s), &tmB, &full[s], kc * KCB, 0);
+                issued = kc + 1;
+            }
+            if (HALF == 2 && p.fuse_gdn && !*abort_flag) {
+                if (!mbar_wait(mma_done, 0)) {
+                    fail();
+                } else {
+                    mbar_expect_tx(gdn_full, 2 * GCH * GB);
+                    for (int c = 0; c < GCH; ++c) {
+                        tma_load_2d(stage_a(c), &tmGh, gdn_full, c * KCH, 0);
+                        tma_load_2d(stage_b(c), &tmGl, gdn_full, c * KCH, 0);
+                    }
+                }
+            }
+            if (*abort_flag) {
+                for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc)
+                    mbar_wait(&full[kc % STAGES], (kc / STAGES) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(BLOCK_M, COUT);
+            for (int kc = 0; kc < p.kchunks; ++kc) {
+                const int s = kc % STAGES;
+                const int g = kc / FOLD, q = g & 1;
+                const uint32_t dt = tmem + (uint32_t)(q * COUT);
+                if (kc % FOLD == 0 && g >= 2) {
+                    if (*abort_flag || !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1)) {
+                        fail();
+                        break;
+                    }
+                }
+                if (*abort_flag || !mbar_wait(&full[s], (kc / STAGES) & 1)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a = smem_u32(stage_a(s)), bb = smem_u32(stage_b(s));
+#pragma unroll
+                for (int kk = 0; kk < KCB / 16; ++kk)   // 16 bf16 = 32 bytes per MMA
+                    mma_bf16(dt, sdesc(a + kk * 32), sdesc(bb + kk * 32), idesc,
+                             (kc % FOLD != 0 || kk > 0) ? 1u : 0u);
+                mma_commit(&empty[s]);
+                if (kc % FOLD == FOLD - 1 || kc == p.kchunks - 1) mma_commit(&pfull[q]);
+            }
+            mma_commit(mma_done);
+            if (HALF == 2 && p.fuse_gdn) {
+                const uint32_t idt = idesc_tf32(BLOCK_M, COUT);
+                if (*abort_flag || !mbar_wait(gdn_ready, 0) || !mbar_wait(gdn_full, 0)) {
+                    fail();
+                } else {
+                    tc_fence_after();
+#pragma unroll
+                    for (int c = 0; c < GCH; ++c) {
+                        const uint32_t gh = smem_u32(stage_a(c)), gl = smem_u32(stage_b(c));
+#pragma unroll
+                        for (int kk = 0; kk < KCH / 8; ++kk) {
+                            const uint64_t dgh = sdesc(gh + kk * 32), dgl = sdesc(gl + kk * 32);
+                            mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dgh, idt, (c > 0 || kk > 0) ? 1u : 0u);
+                            mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dgl, idt, 1u);
+                            mma_tf32_ts(tmem, slot_lo(c) + 8 * kk, dgh, idt, 1u);
+                        }
+                    }
+                    mma_commit(mma_done);
+                }
+            }
+        }
+    } else {
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const uint32_t lane_base = tmem + lane_off + (uint32_t)(half * HALF * 32);
+        const int cbase = half * HALF * 32;
+        float master[HALF * 32];
+#pragma unroll
+        for (int i = 0; i < HALF * 32; ++i) master[i] = 0.f;
+        bool ok = true;
+        for (int g = 0; g < groups && ok; ++g) {
+            if (*abort_flag || !mbar_wait(&pfull[g & 1], (g >> 1) & 1)) {
+                fail();
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int h = 0; h < HALF; ++h) {
+                float v[32];
+                tmem_ld32(lane_base + (uint32_t)((g & 1) * COUT + h * 32), v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) master[h * 32 + i] += v[i];
+            }
+            tc_fence_before();
+            mbar_arrive(&pempty[g & 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < HALF * 32; ++i) master[i] += __ldg(p.bias + cbase + i);
+        if (ok && HALF == 2 && p.fuse_gdn) {
+#pragma unroll
+            for (int h = 0; h < HALF; ++h) {
+                float hv[32], lv[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const float sq = master[h * 32 + i] * master[h * 32 + i];
+                    hv[i] = tf32_rna(sq);
+                    lv[i] = tf32_rna(sq - hv[i]);
+                }
+                const int slot = HALF * half + h;
+                tmem_st16(slot_hi(slot) + lane_off, hv);
+                tmem_st16(slot_hi(slot) + lane_off + 16, hv + 16);
+                tmem_st16(slot_lo(slot) + lane_off, lv);
+                tmem_st16(slot_lo(slot) + lane_off + 16, lv + 16);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            mbar_arrive(gdn_ready);
+            if (*abort_flag || !mbar_wait(mma_done, 1)) {
+                fail();
+                ok = false;
+            } else {
+                tc_fence_after();
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    float v[32];
+                    tmem_ld32(lane_base + (uint32_t)(h * 32), v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float n = v[i] + __ldg(p.gdn_beta + cbase + h * 32 + i);
+                        const float y = master[h * 32 + i];
+                        master[h * 32 + i] = p.fuse_gdn == 1 ? y * rsqrtf(n) : y * sqrtf(n);
+                    }
+                }
+            }
+        }
+        if (ok && !*abort_flag) {
+            const int m = quarter * 32 + lane;
+            const int r = m / p.Wt, w = m % p.Wt;
+            const int gi = i0 + r, gj = j0 + w;
+            if (gi < p.Gh && gj < p.Gw) {
+                const int64_t opix = ((int64_t)b * p.Ho + p.oym * gi + p.oyo) * p.Wo + p.oxm * gj + p.oxo;
+                if (p.epi == EPI_RELU) {
+#pragma unroll
+                    for (int i = 0; i < HALF * 32; ++i) master[i] = fmaxf(master[i], 0.f);
+                }
+                if (p.out_bf16) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(p.out) + opix * COUT + cbase);
+#pragma unroll
+                    for (int q = 0; q < HALF * 4; ++q)
+                        dst[q] = make_uint4(pack_bf16(master[8 * q], master[8 * q + 1]),
+                                            pack_bf16(master[8 * q + 2], master[8 * q + 3]),
+                                            pack_bf16(master[8 * q + 4], master[8 * q + 5]),
+                                            pack_bf16(master[8 * q + 6], master[8 * q + 7]));
+                } else {
+                    float4 *dst = reinterpret_cast<float4 *>(p.out + opix * COUT + cbase);
+#pragma unroll
+                    for (int q = 0; q < HALF * 8; ++q)
+                        dst[q] = make_float4(master[4 * q], master[4 * q + 1], master[4 * q + 2], master[4 * q + 3]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, p.tmem_cols);
+    }
+}
+
 // ------------------------------------------------------------------ host
 
 using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -752,7 +1052,7 @@ EncodeFn encode_fn() {
 }
 
 bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
-              const uint32_t *box) {
+              const uint32_t *box, CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32) {
     EncodeFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t gd[5], gs[4];
@@ -763,7 +1063,7 @@ bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, 
         es[i] = 1;
         if (i > 0) gs[i - 1] = strides_bytes[i - 1];
     }
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void *>(base), gd, gs, bx, es,
+    CUresult r = fn(m, dt, rank, const_cast<void *>(base), gd, gs, bx, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -818,14 +1118,46 @@ void pick_tile(int Gh, int Gw, int *R, int *Wt) {
 TcWeights::~TcWeights() {
     if (hi) cudaFree(hi);
     if (lo) cudaFree(lo);
+    if (wb) cudaFree(wb);
     delete[] reinterpret_cast<CUtensorMap *>(maps);
+    delete reinterpret_cast<CUtensorMap *>(bmap);
 }
+
+namespace {
+uint16_t bf16_rne_host(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+void build_weights_bf16(const float *w, int Cout, int T, int Cin, TcWeights *out) {
+    if (Cin % KCB || (Cout != 128 && Cout != 192) || !encode_fn()) return;
+    const int64_t K = (int64_t)T * Cin;
+    std::vector<uint16_t> v((size_t)Cout * K);
+    for (size_t e = 0; e < v.size(); ++e) v[e] = bf16_rne_host(w[e]);
+    if (cudaMalloc(&out->wb, v.size() * 2) != cudaSuccess) return;
+    if (cudaMemcpy(out->wb, v.data(), v.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return;
+    CUtensorMap *m = new CUtensorMap;
+    const uint64_t dims[2] = {(uint64_t)K, (uint64_t)Cout};
+    const uint64_t strides[1] = {(uint64_t)K * 2};
+    const uint32_t box[2] = {KCB, (uint32_t)Cout};
+    if (!make_map(m, out->wb, 2, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16)) {
+        delete m;
+        return;
+    }
+    out->bmap = m;
+    out->bvalid = true;
+}
+}  // namespace
 
 void build_weights(const float *w, int Cout, int T, int Cin, TcWeights *out) {
     out->Cout = Cout;
     out->T = T;
     out->Cin = Cin;
     out->valid = false;
+    build_weights_bf16(w, Cout, T, Cin, out);
     if ((Cout != 128 && Cout != 192) || stages_for(Cout) < 2) return;
     // Cin % 32 != 0: the im2col path, K = T * Cin zero-padded to a chunk multiple
     out->im2col = Cin % KCH != 0;
@@ -865,6 +1197,7 @@ bool can_run(const ConvDesc &d, const TcWeights &w) {
     if (!w.valid || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout || !d.bias || !d.status) return false;
     if ((reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15)) return false;
     if ((d.epi == EPI_GDN || d.epi == EPI_IGDN) && !d.gdn_x) return false;
+    if (d.in_bf16 || (d.out_bf16 && !d.fuse_gdn)) return false;
     if (d.fuse_gdn) {
         const TcWeights *g = static_cast<const TcWeights *>(d.gdn_w);
         if (!g || !g->valid || g->T != 1 || g->Cin != d.Cout || g->Cout != d.Cout || !d.gdn_beta) return false;
@@ -905,6 +1238,7 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.in_xform = d.in_xform;
     p.fuse_gdn = d.fuse_gdn;
     p.gdn_beta = d.gdn_beta;
+    p.out_bf16 = d.out_bf16;
     p.tmem_cols = 512;  // partial sums (+ A slots when Cout = 128)
     for (int t = 0; t < d.T; ++t) {
         p.du[t] = d.du[t];
@@ -961,6 +1295,88 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
         launch_kernel<4, 2>(grid, smem, st, tmA, maps[0], maps[1], gmaps[0], gmaps[1], p);
     else
         launch_kernel<2, 3>(grid, smem, st, tmA, maps[0], maps[1], gmaps[0], gmaps[1], p);
+    return true;
+}
+
+bool can_run_bf16(const ConvDesc &d, const TcWeights &w) {
+    if (!w.bvalid || !d.in_bf16 || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout || !d.bias || !d.status)
+        return false;
+    if ((reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15)) return false;
+    if (d.epi != EPI_NONE && d.epi != EPI_RELU) return false;
+    if (d.in_xform != IN_NONE) return false;
+    if (d.fuse_gdn) {
+        const TcWeights *g = static_cast<const TcWeights *>(d.gdn_w);
+        if (d.Cout != 128 || !g || !g->valid || g->T != 1 || g->Cin != d.Cout || g->Cout != d.Cout || !d.gdn_beta)
+            return false;
+    }
+    if (d.s == 2) return (d.Hi % 2 == 0) && (d.Wi % 2 == 0) && d.oym == 1 && d.oxm == 1;
+    return d.s == 1;
+}
+
+bool launch_bf16(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
+    Params p{};
+    p.out = d.out;
+    p.bias = d.bias;
+    p.status = d.status;
+    p.T = d.T;
+    p.Cin = d.Cin;
+    p.cpt = d.Cin / KCB;
+    p.kchunks = d.T * p.cpt;
+    p.Gh = d.Gh;
+    p.Gw = d.Gw;
+    p.B = d.B;
+    p.Ho = d.Ho;
+    p.Wo = d.Wo;
+    p.Cout = d.Cout;
+    p.oym = d.oym;
+    p.oyo = d.oyo;
+    p.oxm = d.oxm;
+    p.oxo = d.oxo;
+    p.epi = d.epi;
+    p.fuse_gdn = d.fuse_gdn;
+    p.gdn_beta = d.gdn_beta;
+    p.out_bf16 = d.out_bf16;
+    p.tmem_cols = 512;
+    for (int t = 0; t < d.T; ++t) {
+        p.du[t] = d.du[t];
+        p.dv[t] = d.dv[t];
+    }
+    pick_tile(d.Gh, d.Gw, &p.R, &p.Wt);
+    p.tiles_x = (d.Gw + p.Wt - 1) / p.Wt;
+    p.tiles_y = (d.Gh + p.R - 1) / p.R;
+    const unsigned grid = (unsigned)(p.tiles_x * p.tiles_y * d.B);
+    const uint64_t C = (uint64_t)d.Cin;
+    CUtensorMap tmA;
+    if (d.s == 2) {
+        p.mode = MODE_S2;
+        const uint64_t dims[5] = {2 * C, (uint64_t)d.Wi / 2, 2, (uint64_t)d.Hi / 2, (uint64_t)d.B};
+        const uint64_t strides[4] = {2 * C * 2, (uint64_t)d.Wi * C * 2, 2ull * d.Wi * C * 2,
+                                     (uint64_t)d.Hi * d.Wi * C * 2};
+        const uint32_t box[5] = {KCB, (uint32_t)p.Wt, 1, (uint32_t)p.R, 1};
+        if (!make_map(&tmA, d.in, 5, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16)) return false;
+    } else {
+        p.mode = MODE_S1;
+        const uint64_t dims[4] = {C, (uint64_t)d.Wi, (uint64_t)d.Hi, (uint64_t)d.B};
+        const uint64_t strides[3] = {C * 2, (uint64_t)d.Wi * C * 2, (uint64_t)d.Hi * d.Wi * C * 2};
+        const uint32_t box[4] = {KCB, (uint32_t)p.Wt, (uint32_t)p.R, 1};
+        if (!make_map(&tmA, d.in, 4, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16)) return false;
+    }
+    if (grid == 0) return true;
+    const CUtensorMap &bm = *reinterpret_cast<const CUtensorMap *>(w.bmap);
+    const CUtensorMap *g = d.fuse_gdn ? reinterpret_cast<const CUtensorMap *>(
+                                            static_cast<const TcWeights *>(d.gdn_w)->maps)
+                                      : reinterpret_cast<const CUtensorMap *>(w.bmap);
+    const CUtensorMap &gh = g[0];
+    const CUtensorMap &gl = d.fuse_gdn ? g[1] : g[0];
+    if (d.Cout == 128) {
+        const int smem = 6 * (AB_BYTES + 128 * KCB * 2) + 256 + 1024;
+        cudaFuncSetAttribute(conv_bf16_kernel<6, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        conv_bf16_kernel<6, 2><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
+    } else {
+        const int smem = 5 * (AB_BYTES + 192 * KCB * 2) + 256 + 1024;
+        cudaFuncSetAttribute(conv_bf16_kernel<5, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        conv_bf16_kernel<5, 3><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
+    }
     return true;
 }
 

@@ -12,6 +12,9 @@ namespace tc {
 struct TcWeights {
     void *hi = nullptr, *lo = nullptr;
     void *maps = nullptr;   // two CUtensorMap (hi, lo), host copies passed as kernel parameters
+    void *wb = nullptr;     // bf16 copy [Cout][K] for the BF16 form
+    void *bmap = nullptr;   // its CUtensorMap
+    bool bvalid = false;
     int Cout = 0, T = 0, Cin = 0, Npad = 0, Kpad = 0;
     bool im2col = false;    // few input channels: A gathered by the kernel, K zero-padded
     bool valid = false;
@@ -31,6 +34,10 @@ bool can_run(const ConvDesc &d, const TcWeights &w);
 // Launches the kernel; false (nothing launched) if a tensor map could not be
 // encoded, in which case the caller runs the CUDA-core kernel instead.
 bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
+
+// BF16 form: bf16 activations in, bf16 or float32 out (d.in_bf16 / out_bf16).
+bool can_run_bf16(const ConvDesc &d, const TcWeights &w);
+bool launch_bf16(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
 
 }  // namespace tc
 }  // namespace lic

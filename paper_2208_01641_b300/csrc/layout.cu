@@ -8,6 +8,8 @@
 //    s = rint(fl32(y - mu_c)), round half to even, in float32.
 //  * scale index (the Gaussian conditional of [2]): the smallest of the 64
 //    table scales that is >= max(sigma, 0.11).
+#include <cuda_bf16.h>
+
 #include "lic_internal.h"
 
 namespace lic {
@@ -162,6 +164,15 @@ cudaError_t upload_scale_table() {
     float T[64];
     scale_table(T);
     return cudaMemcpyToSymbol(c_scales, T, sizeof(T));
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ in, int64_t n, __nv_bfloat16 *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(in[i]);
+}
+
+void launch_to_bf16(const float *in, int64_t n, void *out, cudaStream_t st) {
+    to_bf16_kernel<<<grid_for(n), 256, 0, st>>>(in, n, static_cast<__nv_bfloat16 *>(out));
 }
 
 void launch_pad_pack(const float *frames, int B, int H, int W, int Hp, int Wp, float *out, cudaStream_t st) {

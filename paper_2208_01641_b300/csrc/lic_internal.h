@@ -81,6 +81,8 @@ struct ConvDesc {
     int fuse_gdn;
     const float *gdn_beta;
     const void *gdn_w;
+    // BF16 form: activations stored as bf16 (in is bf16 / out is written bf16)
+    int in_bf16, out_bf16;
     int B, Hi, Wi, Cin;
     int Gh, Gw, s;
     int Ho, Wo, Cout;
@@ -120,6 +122,8 @@ void launch_quantize(const float *y, int B, int HW, int C, const float *mu, int3
                      float *yhat, cudaStream_t st);
 // idx = smallest k with T[k] >= max(sigma, T[0]); NaN / > T[63] -> 63.
 // sigma NHWC [B][HW][C] -> idx NCHW [B][C][HW]; sigma_nchw (optional) copy.
+// float32 -> bf16 (round to nearest even), n elements.
+void launch_to_bf16(const float *in, int64_t n, void *out, cudaStream_t st);
 // Copies the 64 scales into the constant bank of the current device (once
 // per device, at codec creation).
 cudaError_t upload_scale_table();
