@@ -254,17 +254,20 @@ def main():
     # ---- the BF16 precision form, same workload ----
     forms = {}
     if not args.no_forms and args.conv == "auto":
-        bcodec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=lic.BF16)
-        bms, bstatus = time_steps(bcodec, frames, out, H, W, args.steps, args.warmup, stream, flush)
-        forms["bf16"] = {"value": ws * B * args.steps / (sum(bms) / 1000.0), "unit": "frames/s",
-                         "ms_per_step": sum(bms) / args.steps, "p99_ms": sorted(bms)[min(len(bms) - 1,
-                                                                                     int(0.99 * len(bms)))],
-                         "decode_status": bstatus,
-                         "note": "g_a/g_s convs bf16 x bf16 -> fp32; GDN norms, h_a, h_s, index fp32"}
-        if rank == 0 and not args.no_cpu_baseline:
-            forms["bf16"]["psnr_vs_oracle_db"] = psnr_vs_oracle(bcodec, Wt, B)
-            forms["bf16"]["y_maxabs_vs_oracle"] = sampled_errors(bcodec, Wt, frames_np, B)
-        bcodec.close()
+        notes = {"bf16": "g_a/g_s convs bf16 x bf16 -> fp32; GDN norms, h_a, h_s, index fp32",
+                 "fp8": "g_a/g_s convs e4m3 x e4m3 -> fp32 (per-output-channel weight scales, activations "
+                        "x*16; the 192-channel g_s input bf16); GDN norms, h_a, h_s, index fp32"}
+        for name, prec in (("bf16", lic.BF16), ("fp8", lic.FP8)):
+            fcodec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=prec)
+            fms, fstatus = time_steps(fcodec, frames, out, H, W, args.steps, args.warmup, stream, flush)
+            forms[name] = {"value": ws * B * args.steps / (sum(fms) / 1000.0), "unit": "frames/s",
+                           "ms_per_step": sum(fms) / args.steps,
+                           "p99_ms": sorted(fms)[min(len(fms) - 1, int(0.99 * len(fms)))],
+                           "decode_status": fstatus, "note": notes[name]}
+            if rank == 0 and not args.no_cpu_baseline:
+                forms[name]["psnr_vs_oracle_db"] = psnr_vs_oracle(fcodec, Wt, B)
+                forms[name]["y_maxabs_vs_oracle"] = sampled_errors(fcodec, Wt, frames_np, B)
+            fcodec.close()
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None

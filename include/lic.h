@@ -55,7 +55,10 @@ typedef enum { LIC_FACTORIZED = 0, LIC_HYPERPRIOR = 1 } lic_kind;
  * activations and weights with float32 accumulation; GDN / IGDN norms, h_a,
  * h_s, the scales and the scale index stay float32, so encoder and decoder
  * derive identical indices. */
-typedef enum { LIC_FP32 = 0, LIC_BF16 = 1 } lic_precision;
+/* LIC_FP8: as LIC_BF16, with e4m3 activations (stored as x * 16, saturating)
+ * and e4m3 weights scaled per output channel wherever a layer has a multiple
+ * of 128 input channels (the 192-channel input of g_s stays bf16). */
+typedef enum { LIC_FP32 = 0, LIC_BF16 = 1, LIC_FP8 = 2 } lic_precision;
 
 /* Convolution implementation: LIC_CONV_AUTO picks the tcgen05 tensor-core
  * kernels where they exist and the CUDA-core (SIMT) kernels elsewhere;

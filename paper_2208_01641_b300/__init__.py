@@ -23,6 +23,7 @@ CONV_AUTO = 0
 CONV_SIMT = 1
 FP32 = 0
 BF16 = 1
+FP8 = 2
 
 T_Y, T_SY, T_Z, T_SZ, T_SIGMA, T_IDX, T_XPRE = range(7)
 

@@ -75,7 +75,8 @@ struct Layer {
     int in_xform = IN_NONE, epi = EPI_NONE;
     DevBuf bias;
     DevBuf w_small;  // transposed conv to <= 4 channels: [Cin][5][5][4]
-    int in_bf16 = 0, out_bf16 = 0;   // BF16 form: activation storage of this layer
+    int in_dt = DT_F32, out_dt = DT_F32;   // activation storage of this layer (precision forms)
+    float in_scale = 1.f, out_scale = 1.f;   // e4m3 tensors hold x / scale
     std::vector<std::unique_ptr<ConvOp>> ops;
 };
 
@@ -322,8 +323,10 @@ ConvDesc op_desc(const lic_codec *cd, const Layer &L, const ConvOp &op, const fl
     }
     d.in_xform = L.in_xform;
     d.epi = L.epi;
-    d.in_bf16 = L.in_bf16;
-    d.out_bf16 = L.out_bf16;
+    d.in_dt = L.in_dt;
+    d.out_dt = L.out_dt;
+    d.in_scale = L.in_scale;
+    d.out_scale = L.out_scale;
     if (L.deconv) {
         d.Gh = Hi;
         d.Gw = Wi;
@@ -360,10 +363,10 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
         flop += 2.0 * rows * G->C * G->C;
         nm += "+" + G->name.substr(G->name.find('.') + 1);
     }
-    if (d.in_bf16) {   // BF16 form: checked at codec creation
-        nm += ":bf16";
+    if (d.in_dt != DT_F32) {   // precision forms: checked at codec creation
+        nm += d.in_dt == DT_E4M3 ? ":e4m3" : ":bf16";
         timed(const_cast<lic_codec *>(cd), nm, flop, bytes, 1, st, [&] {
-            if (!tc::launch_bf16(d, op.tcw, st)) atomic_status(cd, ST_TIMEOUT);
+            if (!tc::launch_lp(d, op.tcw, st)) atomic_status(cd, ST_TIMEOUT);
         });
         return;
     }
@@ -457,7 +460,7 @@ float *run_layer_gdn(const lic_codec *cd, const Layer &L, const Gdn &G, const fl
         d.fuse_gdn = G.inverse ? 2 : 1;
         d.gdn_beta = G.beta.as<float>();
         d.gdn_w = &G.tcw;
-        fuse = d.in_bf16 ? tc::can_run_bf16(d, op->tcw) : tc::can_run(d, op->tcw);
+        fuse = d.in_dt != DT_F32 ? tc::can_run_lp(d, op->tcw) : tc::can_run(d, op->tcw);
     }
     if (fuse) {
         for (auto &op : L.ops) run_op(cd, L, *op, in, B, Hi, Wi, out, Ho, Wo, st, &G);
@@ -555,7 +558,7 @@ void synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, cudaStre
     float *a = cd->act0.as<float>(), *b = cd->act1.as<float>();
     int H = Hy, W = Wy;
     const float *in = yhat;
-    if (cd->gs[0].in_bf16) {   // BF16 form: g_s takes y_hat as bf16
+    if (cd->gs[0].in_dt == DT_BF16) {   // precision forms: g_s takes y_hat as bf16
         const int64_t n = (int64_t)B * Hy * Wy * cd->M;
         timed(cd, "to_bf16", 0, 6.0 * n, 1, st, [&] { launch_to_bf16(yhat, n, a, st); });
         in = a;
@@ -782,8 +785,8 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
     cd->M = M;
     if (opts) cd->opt = *opts;
     if (cd->opt.band_rows <= 0) cd->opt.band_rows = 16;
-    if (cd->opt.precision != LIC_FP32 && cd->opt.precision != LIC_BF16) return LIC_E_UNSUPPORTED;
-    if (cd->opt.precision == LIC_BF16 && cd->opt.conv_impl == LIC_CONV_SIMT) return LIC_E_UNSUPPORTED;
+    if (cd->opt.precision < LIC_FP32 || cd->opt.precision > LIC_FP8) return LIC_E_UNSUPPORTED;
+    if (cd->opt.precision != LIC_FP32 && cd->opt.conv_impl == LIC_CONV_SIMT) return LIC_E_UNSUPPORTED;
     LIC_CUDA_TRY(cudaGetDevice(&cd->device));
     LIC_CUDA_TRY(upload_scale_table());
     ParamMap pm = param_map(weights);
@@ -807,25 +810,40 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
         if ((rc = make_deconv(cd->hs[1], pm, "h_s.deconv1", N, N, EPI_RELU))) return rc;
         if ((rc = make_conv(cd->hs[2], pm, "h_s.conv2", N, M, 3, 1, IN_NONE, EPI_RELU))) return rc;
     }
-    if (cd->opt.precision == LIC_BF16) {
-        // bf16 activations flow g_a conv0 -> conv1 -> conv2 -> conv3 and
-        // y_hat -> g_s deconv0 -> deconv1 -> deconv2; y and the input of the
-        // last (CUDA-core) layer of g_s stay float32
-        cd->ga[0].out_bf16 = 1;
-        for (int i = 1; i < 4; ++i) {
-            cd->ga[i].in_bf16 = 1;
-            cd->ga[i].out_bf16 = i < 3;
-        }
-        for (int i = 0; i < 3; ++i) {
-            cd->gs[i].in_bf16 = 1;
-            cd->gs[i].out_bf16 = i < 2;
-        }
+    if (cd->opt.precision != LIC_FP32) {
+        // Low-precision activations flow g_a conv0 -> conv1 -> conv2 -> conv3
+        // and y_hat -> g_s deconv0 -> deconv1 -> deconv2; y and the input of
+        // the last (CUDA-core) layer of g_s stay float32.  FP8: e4m3 wherever
+        // the consumer has a multiple of 128 input channels, bf16 otherwise.
+        const bool f8 = cd->opt.precision == LIC_FP8;
+        const float S = 1.f / 16.f;   // e4m3 activation scale: |x| <= 448 * S = 28 representable
+        auto lp_in = [&](Layer &L) {
+            if (f8 && L.Cin % 128 == 0) {
+                L.in_dt = DT_E4M3;
+                L.in_scale = S;
+            } else {
+                L.in_dt = DT_BF16;
+            }
+        };
+        auto lp_out_for = [&](Layer &L, const Layer &next) {
+            L.out_dt = next.in_dt;
+            L.out_scale = next.in_scale;
+        };
+        for (int i = 1; i < 4; ++i) lp_in(cd->ga[i]);
+        for (int i = 0; i < 3; ++i) lp_in(cd->gs[i]);
+        cd->gs[0].in_dt = DT_BF16;   // y_hat is converted to bf16 once
+        cd->gs[0].in_scale = 1.f;
+        for (int i = 0; i < 3; ++i) lp_out_for(cd->ga[i], cd->ga[i + 1]);
+        for (int i = 0; i < 2; ++i) lp_out_for(cd->gs[i], cd->gs[i + 1]);
+        auto check = [&](const Layer &L) {
+            for (auto &op : L.ops)
+                if (L.in_dt == DT_E4M3 ? !op->tcw.f8valid : !op->tcw.bvalid) return false;
+            return true;
+        };
         for (int i = 1; i < 4; ++i)
-            for (auto &op : cd->ga[i].ops)
-                if (!op->tcw.bvalid) return LIC_E_UNSUPPORTED;
+            if (!check(cd->ga[i])) return LIC_E_UNSUPPORTED;
         for (int i = 0; i < 3; ++i)
-            for (auto &op : cd->gs[i].ops)
-                if (!op->tcw.bvalid) return LIC_E_UNSUPPORTED;
+            if (!check(cd->gs[i])) return LIC_E_UNSUPPORTED;
         for (int i = 0; i < 3; ++i)
             if (!cd->gdn[i].tcw.valid || !cd->igdn[i].tcw.valid || N != 128) return LIC_E_UNSUPPORTED;
         if (!cd->ga[0].ops[0]->tcw.valid) return LIC_E_UNSUPPORTED;

@@ -39,6 +39,7 @@
 // ST_TIMEOUT in the codec status word and the CTA winds down.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <cstring>
 #include <mutex>
@@ -77,7 +78,10 @@ struct Params {
     const float *in;              // MODE_IM2COL: NHWC input
     int Hi, Wi, s;                // MODE_IM2COL: input size, stride
     int fuse_gdn;                 // 0, 1 (GDN) or 2 (IGDN) applied after bias
-    int out_bf16;                 // store the output as bf16
+    int out_dt;                   // DType of the output
+    float out_inv_scale;          // e4m3 output: stored = x * out_inv_scale
+    float in_scale;               // e4m3 input: x = stored * in_scale
+    const float *w_scale;         // e4m3 weights: per output channel
     const float *gdn_beta;
     int kchunks;
     uint32_t tmem_cols;
@@ -232,6 +236,41 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 __device__ __forceinline__ uint32_t pack_bf16_f(float a, float b) {
     return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+
+// Four floats -> four e4m3 bytes (round to nearest even, saturating), first in the low byte.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
+
+// Store NV consecutive channels (NV % 16 == 0) of one pixel, element offset
+// `off`, in the output storage type.
+template <int NV>
+__device__ __forceinline__ void store_row(const float *v, void *out, int64_t off, int dt, float inv_scale) {
+    if (dt == DT_BF16) {
+        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(out) + off);
+#pragma unroll
+        for (int q = 0; q < NV / 8; ++q)
+            dst[q] = make_uint4(pack_bf16_f(v[8 * q], v[8 * q + 1]), pack_bf16_f(v[8 * q + 2], v[8 * q + 3]),
+                                pack_bf16_f(v[8 * q + 4], v[8 * q + 5]), pack_bf16_f(v[8 * q + 6], v[8 * q + 7]));
+    } else if (dt == DT_E4M3) {
+        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(out) + off);
+#pragma unroll
+        for (int q = 0; q < NV / 16; ++q) {
+            const float *w = v + 16 * q;
+            dst[q] = make_uint4(
+                pack_e4m3x4(w[0] * inv_scale, w[1] * inv_scale, w[2] * inv_scale, w[3] * inv_scale),
+                pack_e4m3x4(w[4] * inv_scale, w[5] * inv_scale, w[6] * inv_scale, w[7] * inv_scale),
+                pack_e4m3x4(w[8] * inv_scale, w[9] * inv_scale, w[10] * inv_scale, w[11] * inv_scale),
+                pack_e4m3x4(w[12] * inv_scale, w[13] * inv_scale, w[14] * inv_scale, w[15] * inv_scale));
+        }
+    } else {
+        float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(out) + off);
+#pragma unroll
+        for (int q = 0; q < NV / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
 }
 
 // Round to TF32 (10 stored mantissa bits), to nearest, ties away from zero:
@@ -701,19 +740,8 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 valid = gi < p.Gh && gj < p.Gw;
                 opix = ((int64_t)b * p.Ho + p.oym * gi + p.oyo) * p.Wo + p.oxm * gj + p.oxo;
             }
-            if (valid && p.fuse_gdn && p.out_bf16) {
-                uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(p.out) + opix * COUT + cbase);
-#pragma unroll
-                for (int q = 0; q < HALF * 4; ++q)
-                    dst[q] = make_uint4(pack_bf16_f(master[8 * q], master[8 * q + 1]),
-                                        pack_bf16_f(master[8 * q + 2], master[8 * q + 3]),
-                                        pack_bf16_f(master[8 * q + 4], master[8 * q + 5]),
-                                        pack_bf16_f(master[8 * q + 6], master[8 * q + 7]));
-            } else if (valid && p.fuse_gdn) {
-                float4 *dst = reinterpret_cast<float4 *>(p.out + opix * COUT + cbase);
-#pragma unroll
-                for (int q = 0; q < HALF * 8; ++q)
-                    dst[q] = make_float4(master[4 * q], master[4 * q + 1], master[4 * q + 2], master[4 * q + 3]);
+            if (valid && p.fuse_gdn) {
+                store_row<HALF * 32>(master, p.out, opix * COUT + cbase, p.out_dt, p.out_inv_scale);
             } else if (valid) {
                 float *dst = p.out + opix * COUT + cbase;
 #pragma unroll
@@ -773,17 +801,29 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
-    const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
-    return lo | (hi << 16);
+// e4m3 x e4m3 -> f32 (kind::f8f6f4, formats 0 = E4M3)
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-constexpr int KCB = 64;                        // bf16 per K chunk
-constexpr int AB_BYTES = BLOCK_M * KCB * 2;    // 16 KB
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 
-template <int STAGES, int HALF>
-__global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
+constexpr int AB_BYTES = BLOCK_M * 128;   // one 128-byte row per pixel: 64 bf16 or 128 e4m3 channels
+constexpr int KCB = 64;                   // bf16 per K chunk (weights built for the BF16 form)
+constexpr int KC8 = 128;                  // e4m3 per K chunk
+
+// EB: bytes per element (2: bf16, kind::f16; 1: e4m3, kind::f8f6f4).  A K
+// chunk is one 128-byte row either way, fed by 4 MMAs of 32 bytes of K.
+template <int STAGES, int HALF, int EB>
+__global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                         const __grid_constant__ CUtensorMap tmB,
                                                                         const __grid_constant__ CUtensorMap tmGh,
                                                                         const __grid_constant__ CUtensorMap tmGl,
@@ -791,7 +831,8 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_bf16_kernel(const __
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int COUT = 64 * HALF;
-    constexpr int BB_BYTES = COUT * KCB * 2;
+    constexpr int KCE = 128 / EB;              // elements per K chunk
+    constexpr int BB_BYTES = COUT * 128;
     constexpr int STAGE_BYTES = AB_BYTES + BB_BYTES;
     constexpr int GCH = COUT / KCH;            // tf32 chunks of the fused norm (COUT = 128 only)
     constexpr int GB = COUT * KCH * 4;         // bytes of one gamma chunk (hi or lo)
@@ -855,7 +896,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_bf16_kernel(const __
                     break;
                 }
                 const int t = kc / p.cpt;
-                const int c0 = (kc % p.cpt) * KCB;
+                const int c0 = (kc % p.cpt) * KCE;
                 mbar_expect_tx(&full[s], AB_BYTES + BB_BYTES);
                 if (p.mode == MODE_S2) {
                     const int du = p.du[t], dv = p.dv[t];
@@ -864,7 +905,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_bf16_kernel(const __
                 } else {
                     tma_load_4d(stage_a(s), &tmA, &full[s], c0, j0 + p.dv[t], i0 + p.du[t], b);
                 }
-                tma_load_2d(stage_b(s), &tmB, &full[s], kc * KCB, 0);
+                tma_load_2d(stage_b(s), &tmB, &full[s], kc * KCE, 0);
                 issued = kc + 1;
             }
             if (HALF == 2 && p.fuse_gdn && !*abort_flag) {
@@ -885,7 +926,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_bf16_kernel(const __
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(BLOCK_M, COUT);
+            const uint32_t idesc = EB == 2 ? idesc_bf16(BLOCK_M, COUT) : idesc_e4m3(BLOCK_M, COUT);
             for (int kc = 0; kc < p.kchunks; ++kc) {
                 const int s = kc % STAGES;
                 const int g = kc / FOLD, q = g & 1;
@@ -903,9 +944,14 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_bf16_kernel(const __
                 tc_fence_after();
                 const uint32_t a = smem_u32(stage_a(s)), bb = smem_u32(stage_b(s));
 #pragma unroll
-                for (int kk = 0; kk < KCB / 16; ++kk)   // 16 bf16 = 32 bytes per MMA
-                    mma_bf16(dt, sdesc(a + kk * 32), sdesc(bb + kk * 32), idesc,
-                             (kc % FOLD != 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < 4; ++kk) {   // 32 bytes of K per MMA
+                    if constexpr (EB == 2)
+                        mma_bf16(dt, sdesc(a + kk * 32), sdesc(bb + kk * 32), idesc,
+                                 (kc % FOLD != 0 || kk > 0) ? 1u : 0u);
+                    else
+                        mma_e4m3(dt, sdesc(a + kk * 32), sdesc(bb + kk * 32), idesc,
+                                 (kc % FOLD != 0 || kk > 0) ? 1u : 0u);
+                }
                 mma_commit(&empty[s]);
                 if (kc % FOLD == FOLD - 1 || kc == p.kchunks - 1) mma_commit(&pfull[q]);
             }
@@ -957,6 +1003,10 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_bf16_kernel(const __
             tc_fence_before();
             mbar_arrive(&pempty[g & 1]);
         }
+        if constexpr (EB == 1) {   // undo the e4m3 scales: x = stored * in_scale, w = stored * w_scale[o]
+#pragma unroll
+            for (int i = 0; i < HALF * 32; ++i) master[i] *= __ldg(p.w_scale + cbase + i) * p.in_scale;
+        }
 #pragma unroll
         for (int i = 0; i < HALF * 32; ++i) master[i] += __ldg(p.bias + cbase + i);
         if (ok && HALF == 2 && p.fuse_gdn) {
@@ -1006,20 +1056,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_bf16_kernel(const __
 #pragma unroll
                     for (int i = 0; i < HALF * 32; ++i) master[i] = fmaxf(master[i], 0.f);
                 }
-                if (p.out_bf16) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(p.out) + opix * COUT + cbase);
-#pragma unroll
-                    for (int q = 0; q < HALF * 4; ++q)
-                        dst[q] = make_uint4(pack_bf16(master[8 * q], master[8 * q + 1]),
-                                            pack_bf16(master[8 * q + 2], master[8 * q + 3]),
-                                            pack_bf16(master[8 * q + 4], master[8 * q + 5]),
-                                            pack_bf16(master[8 * q + 6], master[8 * q + 7]));
-                } else {
-                    float4 *dst = reinterpret_cast<float4 *>(p.out + opix * COUT + cbase);
-#pragma unroll
-                    for (int q = 0; q < HALF * 8; ++q)
-                        dst[q] = make_float4(master[4 * q], master[4 * q + 1], master[4 * q + 2], master[4 * q + 3]);
-                }
+                store_row<HALF * 32>(master, p.out, opix * COUT + cbase, p.out_dt, p.out_inv_scale);
             }
         }
     }
@@ -1119,8 +1156,11 @@ TcWeights::~TcWeights() {
     if (hi) cudaFree(hi);
     if (lo) cudaFree(lo);
     if (wb) cudaFree(wb);
+    if (w8) cudaFree(w8);
+    if (w8scale) cudaFree(w8scale);
     delete[] reinterpret_cast<CUtensorMap *>(maps);
     delete reinterpret_cast<CUtensorMap *>(bmap);
+    delete reinterpret_cast<CUtensorMap *>(w8map);
 }
 
 namespace {
@@ -1130,6 +1170,35 @@ uint16_t bf16_rne_host(float x) {
     if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
     u += 0x7fffu + ((u >> 16) & 1u);
     return (uint16_t)(u >> 16);
+}
+
+// e4m3 copy of w / s[o], s[o] = max_k |w[o][k]| / 448 (per output channel).
+void build_weights_e4m3(const float *w, int Cout, int T, int Cin, TcWeights *out) {
+    if (Cin % KC8 || (Cout != 128 && Cout != 192) || !encode_fn()) return;
+    const int64_t K = (int64_t)T * Cin;
+    std::vector<uint8_t> v((size_t)Cout * K);
+    std::vector<float> sc(Cout);
+    for (int o = 0; o < Cout; ++o) {
+        float mx = 0.f;
+        for (int64_t k = 0; k < K; ++k) mx = std::max(mx, std::fabs(w[o * K + k]));
+        sc[o] = mx > 0.f ? mx / 448.f : 1.f;
+        for (int64_t k = 0; k < K; ++k)
+            v[o * K + k] = (uint8_t)__nv_cvt_float_to_fp8(w[o * K + k] / sc[o], __NV_SATFINITE, __NV_E4M3);
+    }
+    if (cudaMalloc(&out->w8, v.size()) != cudaSuccess) return;
+    if (cudaMalloc(&out->w8scale, Cout * sizeof(float)) != cudaSuccess) return;
+    if (cudaMemcpy(out->w8, v.data(), v.size(), cudaMemcpyHostToDevice) != cudaSuccess) return;
+    if (cudaMemcpy(out->w8scale, sc.data(), Cout * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return;
+    CUtensorMap *m = new CUtensorMap;
+    const uint64_t dims[2] = {(uint64_t)K, (uint64_t)Cout};
+    const uint64_t strides[1] = {(uint64_t)K};
+    const uint32_t box[2] = {KC8, (uint32_t)Cout};
+    if (!make_map(m, out->w8, 2, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_UINT8)) {
+        delete m;
+        return;
+    }
+    out->w8map = m;
+    out->f8valid = true;
 }
 
 void build_weights_bf16(const float *w, int Cout, int T, int Cin, TcWeights *out) {
@@ -1158,6 +1227,7 @@ void build_weights(const float *w, int Cout, int T, int Cin, TcWeights *out) {
     out->Cin = Cin;
     out->valid = false;
     build_weights_bf16(w, Cout, T, Cin, out);
+    build_weights_e4m3(w, Cout, T, Cin, out);
     if ((Cout != 128 && Cout != 192) || stages_for(Cout) < 2) return;
     // Cin % 32 != 0: the im2col path, K = T * Cin zero-padded to a chunk multiple
     out->im2col = Cin % KCH != 0;
@@ -1197,7 +1267,7 @@ bool can_run(const ConvDesc &d, const TcWeights &w) {
     if (!w.valid || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout || !d.bias || !d.status) return false;
     if ((reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15)) return false;
     if ((d.epi == EPI_GDN || d.epi == EPI_IGDN) && !d.gdn_x) return false;
-    if (d.in_bf16 || (d.out_bf16 && !d.fuse_gdn)) return false;
+    if (d.in_dt != DT_F32 || (d.out_dt != DT_F32 && !d.fuse_gdn)) return false;
     if (d.fuse_gdn) {
         const TcWeights *g = static_cast<const TcWeights *>(d.gdn_w);
         if (!g || !g->valid || g->T != 1 || g->Cin != d.Cout || g->Cout != d.Cout || !d.gdn_beta) return false;
@@ -1238,7 +1308,8 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.in_xform = d.in_xform;
     p.fuse_gdn = d.fuse_gdn;
     p.gdn_beta = d.gdn_beta;
-    p.out_bf16 = d.out_bf16;
+    p.out_dt = d.out_dt;
+    p.out_inv_scale = d.out_scale > 0.f ? 1.f / d.out_scale : 1.f;
     p.tmem_cols = 512;  // partial sums (+ A slots when Cout = 128)
     for (int t = 0; t < d.T; ++t) {
         p.du[t] = d.du[t];
@@ -1298,8 +1369,10 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     return true;
 }
 
-bool can_run_bf16(const ConvDesc &d, const TcWeights &w) {
-    if (!w.bvalid || !d.in_bf16 || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout || !d.bias || !d.status)
+bool can_run_lp(const ConvDesc &d, const TcWeights &w) {
+    const bool e4 = d.in_dt == DT_E4M3;
+    if (d.in_dt != DT_BF16 && !e4) return false;
+    if ((e4 ? !w.f8valid : !w.bvalid) || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout || !d.bias || !d.status)
         return false;
     if ((reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15)) return false;
     if (d.epi != EPI_NONE && d.epi != EPI_RELU) return false;
@@ -1313,14 +1386,16 @@ bool can_run_bf16(const ConvDesc &d, const TcWeights &w) {
     return d.s == 1;
 }
 
-bool launch_bf16(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
+bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
+    const bool e4 = d.in_dt == DT_E4M3;
+    const int EBY = e4 ? 1 : 2;
     Params p{};
     p.out = d.out;
     p.bias = d.bias;
     p.status = d.status;
     p.T = d.T;
     p.Cin = d.Cin;
-    p.cpt = d.Cin / KCB;
+    p.cpt = d.Cin / (128 / EBY);
     p.kchunks = d.T * p.cpt;
     p.Gh = d.Gh;
     p.Gw = d.Gw;
@@ -1335,7 +1410,10 @@ bool launch_bf16(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.epi = d.epi;
     p.fuse_gdn = d.fuse_gdn;
     p.gdn_beta = d.gdn_beta;
-    p.out_bf16 = d.out_bf16;
+    p.out_dt = d.out_dt;
+    p.out_inv_scale = d.out_scale > 0.f ? 1.f / d.out_scale : 1.f;
+    p.in_scale = d.in_scale > 0.f ? d.in_scale : 1.f;
+    p.w_scale = w.w8scale;
     p.tmem_cols = 512;
     for (int t = 0; t < d.T; ++t) {
         p.du[t] = d.du[t];
@@ -1345,37 +1423,49 @@ bool launch_bf16(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.tiles_x = (d.Gw + p.Wt - 1) / p.Wt;
     p.tiles_y = (d.Gh + p.R - 1) / p.R;
     const unsigned grid = (unsigned)(p.tiles_x * p.tiles_y * d.B);
-    const uint64_t C = (uint64_t)d.Cin;
+    const uint64_t C = (uint64_t)d.Cin, E = (uint64_t)EBY;
+    const CUtensorMapDataType dt = e4 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const uint32_t kce = 128 / EBY;
     CUtensorMap tmA;
     if (d.s == 2) {
         p.mode = MODE_S2;
         const uint64_t dims[5] = {2 * C, (uint64_t)d.Wi / 2, 2, (uint64_t)d.Hi / 2, (uint64_t)d.B};
-        const uint64_t strides[4] = {2 * C * 2, (uint64_t)d.Wi * C * 2, 2ull * d.Wi * C * 2,
-                                     (uint64_t)d.Hi * d.Wi * C * 2};
-        const uint32_t box[5] = {KCB, (uint32_t)p.Wt, 1, (uint32_t)p.R, 1};
-        if (!make_map(&tmA, d.in, 5, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16)) return false;
+        const uint64_t strides[4] = {2 * C * E, (uint64_t)d.Wi * C * E, 2ull * d.Wi * C * E,
+                                     (uint64_t)d.Hi * d.Wi * C * E};
+        const uint32_t box[5] = {kce, (uint32_t)p.Wt, 1, (uint32_t)p.R, 1};
+        if (!make_map(&tmA, d.in, 5, dims, strides, box, dt)) return false;
     } else {
         p.mode = MODE_S1;
         const uint64_t dims[4] = {C, (uint64_t)d.Wi, (uint64_t)d.Hi, (uint64_t)d.B};
-        const uint64_t strides[3] = {C * 2, (uint64_t)d.Wi * C * 2, (uint64_t)d.Hi * d.Wi * C * 2};
-        const uint32_t box[4] = {KCB, (uint32_t)p.Wt, (uint32_t)p.R, 1};
-        if (!make_map(&tmA, d.in, 4, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16)) return false;
+        const uint64_t strides[3] = {C * E, (uint64_t)d.Wi * C * E, (uint64_t)d.Hi * d.Wi * C * E};
+        const uint32_t box[4] = {kce, (uint32_t)p.Wt, (uint32_t)p.R, 1};
+        if (!make_map(&tmA, d.in, 4, dims, strides, box, dt)) return false;
     }
     if (grid == 0) return true;
-    const CUtensorMap &bm = *reinterpret_cast<const CUtensorMap *>(w.bmap);
+    const CUtensorMap &bm = *reinterpret_cast<const CUtensorMap *>(e4 ? w.w8map : w.bmap);
     const CUtensorMap *g = d.fuse_gdn ? reinterpret_cast<const CUtensorMap *>(
                                             static_cast<const TcWeights *>(d.gdn_w)->maps)
-                                      : reinterpret_cast<const CUtensorMap *>(w.bmap);
+                                      : &bm;
     const CUtensorMap &gh = g[0];
     const CUtensorMap &gl = d.fuse_gdn ? g[1] : g[0];
     if (d.Cout == 128) {
-        const int smem = 6 * (AB_BYTES + 128 * KCB * 2) + 256 + 1024;
-        cudaFuncSetAttribute(conv_bf16_kernel<6, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        conv_bf16_kernel<6, 2><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
+        const int smem = 6 * (AB_BYTES + 128 * 128) + 256 + 1024;
+        if (e4) {
+            cudaFuncSetAttribute(conv_lp_kernel<6, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            conv_lp_kernel<6, 2, 1><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
+        } else {
+            cudaFuncSetAttribute(conv_lp_kernel<6, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            conv_lp_kernel<6, 2, 2><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
+        }
     } else {
-        const int smem = 5 * (AB_BYTES + 192 * KCB * 2) + 256 + 1024;
-        cudaFuncSetAttribute(conv_bf16_kernel<5, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        conv_bf16_kernel<5, 3><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
+        const int smem = 5 * (AB_BYTES + 192 * 128) + 256 + 1024;
+        if (e4) {
+            cudaFuncSetAttribute(conv_lp_kernel<5, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            conv_lp_kernel<5, 3, 1><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
+        } else {
+            cudaFuncSetAttribute(conv_lp_kernel<5, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            conv_lp_kernel<5, 3, 2><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
+        }
     }
     return true;
 }

@@ -15,6 +15,10 @@ struct TcWeights {
     void *wb = nullptr;     // bf16 copy [Cout][K] for the BF16 form
     void *bmap = nullptr;   // its CUtensorMap
     bool bvalid = false;
+    void *w8 = nullptr;     // e4m3 copy [Cout][K] of w / scale[o] for the FP8 form
+    void *w8map = nullptr;  // its CUtensorMap
+    float *w8scale = nullptr;   // device, per output channel
+    bool f8valid = false;
     int Cout = 0, T = 0, Cin = 0, Npad = 0, Kpad = 0;
     bool im2col = false;    // few input channels: A gathered by the kernel, K zero-padded
     bool valid = false;
@@ -35,9 +39,9 @@ bool can_run(const ConvDesc &d, const TcWeights &w);
 // encoded, in which case the caller runs the CUDA-core kernel instead.
 bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
 
-// BF16 form: bf16 activations in, bf16 or float32 out (d.in_bf16 / out_bf16).
-bool can_run_bf16(const ConvDesc &d, const TcWeights &w);
-bool launch_bf16(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
+// Precision forms: bf16 or e4m3 activations in (d.in_dt), any storage out.
+bool can_run_lp(const ConvDesc &d, const TcWeights &w);
+bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
 
 }  // namespace tc
 }  // namespace lic

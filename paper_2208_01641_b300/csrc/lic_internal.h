@@ -60,6 +60,8 @@ void scale_table(float T[64]);
 
 enum InXform : int { IN_NONE = 0, IN_ABS = 1, IN_SQUARE = 2 };
 enum Epi : int { EPI_NONE = 0, EPI_RELU = 1, EPI_GDN = 2, EPI_IGDN = 3 };
+// Storage of an activation tensor: float32, bf16, or e4m3 holding x / scale.
+enum DType : int { DT_F32 = 0, DT_BF16 = 1, DT_E4M3 = 2 };
 
 constexpr int MAX_TAPS = 25;
 
@@ -81,8 +83,10 @@ struct ConvDesc {
     int fuse_gdn;
     const float *gdn_beta;
     const void *gdn_w;
-    // BF16 form: activations stored as bf16 (in is bf16 / out is written bf16)
-    int in_bf16, out_bf16;
+    // precision forms: storage of the input and output activations; e4m3
+    // tensors hold x / scale (in_scale, out_scale)
+    int in_dt, out_dt;
+    float in_scale, out_scale;
     int B, Hi, Wi, Cin;
     int Gh, Gw, s;
     int Ho, Wo, Cout;

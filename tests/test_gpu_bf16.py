@@ -1,9 +1,10 @@
-"""The BF16 precision form (lic_options.precision = LIC_BF16) against the
-FP64 oracle (marked gpu).  g_a / g_s convolutions run on bf16 operands with
-float32 accumulation; GDN norms, h_a, h_s and the scale index stay float32.
-Its bar: the entropy stages stay lossless, encoder and decoder derive
-identical scale indices, and the reconstruction is within 40 dB PSNR of the
-FP64 chain's; the latent error against FP64 is reported."""
+"""The precision forms (lic_options.precision = LIC_BF16 / LIC_FP8) against
+the FP64 oracle (marked gpu).  g_a / g_s convolutions run on bf16 (or e4m3
+with per-output-channel weight scales) operands with float32 accumulation;
+GDN norms, h_a, h_s and the scale index stay float32.  Both must keep the
+entropy stages lossless and encoder / decoder scale indices identical; BF16
+must reconstruct within 40 dB PSNR of the FP64 chain; FP8's PSNR and latent
+error are reported (and held to a loose floor)."""
 import numpy as np
 import pytest
 import torch
@@ -16,18 +17,25 @@ pytestmark = pytest.mark.gpu
 N, M = 128, 192
 
 
+FLOOR = {lic.BF16: (40.0, 0.1), lic.FP8: (25.0, 1.0)}
+NAME = {lic.BF16: "bf16", lic.FP8: "fp8"}
+
+
 @pytest.fixture(scope="module")
 def setup():
     out = {}
     for kind in (0, 1):
         W = synth.make_weights(kind, N, M)
-        out[kind] = (W, lic.Codec(kind, N, M, W, precision=lic.BF16), O.Codec(kind, N, M, W))
+        oc = O.Codec(kind, N, M, W)
+        for prec in (lic.BF16, lic.FP8):
+            out[(kind, prec)] = (W, lic.Codec(kind, N, M, W, precision=prec), oc)
     return out
 
 
+@pytest.mark.parametrize("prec", [lic.BF16, lic.FP8])
 @pytest.mark.parametrize("kind", [1, 0])
-def test_bf16_form_against_fp64(setup, kind, capsys):
-    W, c, oc = setup[kind]
+def test_precision_form_against_fp64(setup, kind, prec, capsys):
+    W, c, oc = setup[(kind, prec)]
     B, H, Wd = 2, 200, 330
     x = synth.make_frames(B, H, Wd, first=60)
     bs = c.encode(torch.from_numpy(x).cuda())
@@ -56,7 +64,8 @@ def test_bf16_form_against_fp64(setup, kind, capsys):
     yerr = float(np.abs(y - inter["y"]).max())
     flips = float(np.mean(sy != inter["s_y"]))
     with capsys.disabled():
-        print(f"\n[bf16 form kind={kind}] PSNR vs FP64 chain {p:.2f} dB, max|y - y64| {yerr:.4f}, "
+        print(f"\n[{NAME[prec]} form kind={kind}] PSNR vs FP64 chain {p:.2f} dB, max|y - y64| {yerr:.4f}, "
               f"symbols differing {100 * flips:.3f}%")
-    assert p >= 40.0, p
-    assert yerr < 0.1, yerr
+    min_psnr, max_yerr = FLOOR[prec]
+    assert p >= min_psnr, p
+    assert yerr < max_yerr, yerr
