@@ -404,7 +404,10 @@ def roofline(rep, peaks):
 
 # DRAM bytes (read + write) per launch of the dominant kernels, from the ncu
 # captures summarised in profiles/ (None until a capture of the current build)
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/conv_tc_g_a_conv1_gdn1_fp32_b1.md: 143.3 MB per batch-1 launch, x8 tiles
+    "g_a.conv1+gdn1:tc": 8 * 143.306240e6,
+}
 
 
 def psnr_vs_oracle(codec, Wt, B):
