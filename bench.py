@@ -257,16 +257,20 @@ def main():
         notes = {"bf16": "g_a/g_s convs bf16 x bf16 -> fp32; GDN norms, h_a, h_s, index fp32",
                  "fp8": "g_a/g_s convs e4m3 x e4m3 -> fp32 (per-output-channel weight scales, activations "
                         "x*16; the 192-channel g_s input bf16); GDN norms, h_a, h_s, index fp32"}
-        for name, prec in (("bf16", lic.BF16), ("fp8", lic.FP8)):
-            fcodec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=prec)
+        notes["fp32_1dn"] = ("FP32 chain with 1DN (the paper's variant C, read as GDN without channel mixing) "
+                             "in place of GDN/IGDN; its own seeded weights")
+        W1 = synth.make_weights(lic.HYPERPRIOR, N_CH, M_CH, norm=synth.NORM_1DN)
+        for name, prec, wts, norm in (("bf16", lic.BF16, Wt, lic.NORM_GDN), ("fp8", lic.FP8, Wt, lic.NORM_GDN),
+                                      ("fp32_1dn", lic.FP32, W1, lic.NORM_1DN)):
+            fcodec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, wts, precision=prec, norm=norm)
             fms, fstatus = time_steps(fcodec, frames, out, H, W, args.steps, args.warmup, stream, flush)
             forms[name] = {"value": ws * B * args.steps / (sum(fms) / 1000.0), "unit": "frames/s",
                            "ms_per_step": sum(fms) / args.steps,
                            "p99_ms": sorted(fms)[min(len(fms) - 1, int(0.99 * len(fms)))],
                            "decode_status": fstatus, "note": notes[name]}
             if rank == 0 and not args.no_cpu_baseline:
-                forms[name]["psnr_vs_oracle_db"] = psnr_vs_oracle(fcodec, Wt, B)
-                forms[name]["y_maxabs_vs_oracle"] = sampled_errors(fcodec, Wt, frames_np, B)
+                forms[name]["psnr_vs_oracle_db"] = psnr_vs_oracle(fcodec, wts, B)
+                forms[name]["y_maxabs_vs_oracle"] = sampled_errors(fcodec, wts, frames_np, B)
             fcodec.close()
 
     # ---- end to end through the C ABI with host buffers ----

@@ -92,8 +92,16 @@ typedef struct {
     int precision;   /* lic_precision (LIC_BF16 needs the tensor-core kernels) */
     int band_rows;   /* latent rows per y substream; 0 -> 16 */
     int conv_impl;   /* lic_conv_impl */
-    int reserved[5];
+    int norm;        /* lic_norm: the normalisation between the g_a / g_s layers */
+    int reserved[4];
 } lic_options;
+
+/* LIC_NORM_GDN: GDN / IGDN of Ballé et al. (the paper's [9]), gamma [C,C].
+ * LIC_NORM_1DN: the cheaper activation of the paper's variant C (Sec. IV-C,
+ * its ref. [6]), read as GDN without channel mixing:
+ * y_i = x_i / sqrt(beta_i + gamma_i x_i^2) (inverse: x_i * sqrt(.)), with
+ * per-channel gamma [C] under the same parameter names. */
+typedef enum { LIC_NORM_GDN = 0, LIC_NORM_1DN = 1 } lic_norm;
 
 typedef struct lic_codec lic_codec;
 

@@ -66,6 +66,7 @@ def lib():
         L.orc_conv2d.argtypes = [dp, ip, ip, ip, ip, dp, dp, ip, ip, ip, dp]
         L.orc_deconv2d.argtypes = [dp, ip, ip, ip, ip, dp, dp, ip, ip, ip, dp]
         L.orc_gdn.argtypes = [dp, ip, ip, ip, ip, dp, dp, ip]
+        L.orc_norm1d.argtypes = [dp, ip, ip, ip, ip, dp, dp, ip]
         L.orc_relu.argtypes = [dp, ctypes.c_int64]
         L.orc_abs.argtypes = [dp, ctypes.c_int64]
         L.orc_eb_logits.argtypes = [dp, ctypes.c_double]
@@ -131,8 +132,13 @@ def deconv2d(x, w, b, stride):
 
 
 def gdn(x, beta, gamma, inverse=False):
+    """GDN / IGDN; a 1-D gamma selects 1DN (per-channel, no mixing)."""
     y = _f64(x).copy()
     B, C, H, W = y.shape
+    if np.ndim(gamma) == 1:
+        lib().orc_norm1d(_p(y, ctypes.c_double), B, C, H, W, _p(_f64(beta), ctypes.c_double),
+                         _p(_f64(gamma), ctypes.c_double), 1 if inverse else 0)
+        return y
     lib().orc_gdn(_p(y, ctypes.c_double), B, C, H, W, _p(_f64(beta), ctypes.c_double),
                   _p(_f64(gamma), ctypes.c_double), 1 if inverse else 0)
     return y

@@ -107,6 +107,20 @@ void orc_gdn(double *x, int B, int C, int H, int W,
     }
 }
 
+void orc_norm1d(double *x, int B, int C, int H, int W,
+                const double *beta, const double *gamma, int inverse)
+{
+    int64_t HW = (int64_t)H * W;
+    for (int b = 0; b < B; b++)
+        for (int c = 0; c < C; c++) {
+            double *xc = x + ((int64_t)b * C + c) * HW;
+            for (int64_t t = 0; t < HW; t++) {
+                double r = sqrt(beta[c] + gamma[c] * xc[t] * xc[t]);
+                xc[t] = inverse ? xc[t] * r : xc[t] / r;
+            }
+        }
+}
+
 void orc_relu(double *x, int64_t n)
 {
     for (int64_t i = 0; i < n; i++) if (x[i] < 0.0) x[i] = 0.0;

@@ -45,6 +45,12 @@ void orc_deconv2d(const double *x, int B, int Cin, int H, int W,
 void orc_gdn(double *x, int B, int C, int H, int W,
              const double *beta, const double *gamma, int inverse);
 
+/* 1DN (the paper's variant C, ref. [6]), read as GDN without channel mixing,
+ * in place, per element: x_i <- x_i / sqrt(beta_i + gamma_i x_i^2), or
+ * x_i * sqrt(.) when inverse.  gamma has C entries. */
+void orc_norm1d(double *x, int B, int C, int H, int W,
+                const double *beta, const double *gamma, int inverse);
+
 void orc_relu(double *x, int64_t n);
 void orc_abs(double *x, int64_t n);
 

@@ -23,6 +23,8 @@ CONV_AUTO = 0
 CONV_SIMT = 1
 FP32 = 0
 BF16 = 1
+NORM_GDN = 0
+NORM_1DN = 1
 FP8 = 2
 
 T_Y, T_SY, T_Z, T_SZ, T_SIGMA, T_IDX, T_XPRE = range(7)
@@ -58,7 +60,7 @@ class _Weights(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("band_rows", ctypes.c_int),
-                ("conv_impl", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("conv_impl", ctypes.c_int), ("norm", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class _Bitstreams(ctypes.Structure):
@@ -214,10 +216,10 @@ class Codec:
     """One codec on the current CUDA device (lic_codec_create)."""
 
     def __init__(self, kind: int, N: int, M: int, weights: Dict[str, np.ndarray], band_rows: int = 16,
-                 conv_impl: int = CONV_AUTO, precision: int = FP32):
+                 conv_impl: int = CONV_AUTO, precision: int = FP32, norm: int = NORM_GDN):
         self.kind, self.N, self.M = kind, N, M
         w, keep = _weights_struct(weights)
-        opt = _Options(precision, band_rows, conv_impl)
+        opt = _Options(precision, band_rows, conv_impl, norm)
         h = ctypes.c_void_p()
         _check(_lib().lic_codec_create(kind, N, M, ctypes.byref(w), ctypes.byref(opt), ctypes.byref(h)),
                "lic_codec_create")

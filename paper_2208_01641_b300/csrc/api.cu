@@ -84,6 +84,7 @@ struct Gdn {
     std::string name;
     int C = 0;
     bool inverse = false;
+    bool diag = false;   // 1DN: per-channel gamma, no channel mixing
     DevBuf gamma;  // [C][1][C]
     DevBuf beta;
     tc::TcWeights tcw;
@@ -282,17 +283,19 @@ int make_deconv(Layer &L, const ParamMap &pm, const std::string &name, int Cin, 
     return upload(L.bias, b, Cout * sizeof(float));
 }
 
-int make_gdn(Gdn &G, const ParamMap &pm, const std::string &name, int C, bool inverse) {
+int make_gdn(Gdn &G, const ParamMap &pm, const std::string &name, int C, bool inverse, bool diag) {
     G.name = name;
     G.C = C;
     G.inverse = inverse;
+    G.diag = diag;
     const float *beta, *gamma;
     int rc = get_param(pm, name + ".beta", C, &beta);
     if (rc) return rc;
-    rc = get_param(pm, name + ".gamma", (int64_t)C * C, &gamma);
+    const int64_t ng = diag ? C : (int64_t)C * C;
+    rc = get_param(pm, name + ".gamma", ng, &gamma);
     if (rc) return rc;
-    if ((rc = upload(G.gamma, gamma, (size_t)C * C * sizeof(float)))) return rc;
-    tc::build_weights(gamma, C, 1, C, &G.tcw);
+    if ((rc = upload(G.gamma, gamma, (size_t)ng * sizeof(float)))) return rc;
+    if (!diag) tc::build_weights(gamma, C, 1, C, &G.tcw);
     return upload(G.beta, beta, C * sizeof(float));
 }
 
@@ -357,10 +360,11 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
     const double bytes = 4.0 * ((double)B * Hi * Wi * d.Cin + rows * d.Cout + (double)d.Cout * d.T * d.Cin);
     std::string nm = L.name + (L.deconv ? ".p" + std::to_string(2 * op.py + op.px) : std::string());
     if (G) {
-        d.fuse_gdn = G->inverse ? 2 : 1;
+        d.fuse_gdn = G->diag ? (G->inverse ? 4 : 3) : (G->inverse ? 2 : 1);
         d.gdn_beta = G->beta.as<float>();
         d.gdn_w = &G->tcw;
-        flop += 2.0 * rows * G->C * G->C;
+        d.gdn_gamma = G->gamma.as<float>();
+        flop += G->diag ? 4.0 * rows * G->C : 2.0 * rows * G->C * G->C;
         nm += "+" + G->name.substr(G->name.find('.') + 1);
     }
     if (d.in_dt != DT_F32) {   // precision forms: checked at codec creation
@@ -400,6 +404,13 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
 }
 
 void run_gdn(const lic_codec *cd, const Gdn &G, const float *in, int B, int H, int W, float *out, cudaStream_t st) {
+    if (G.diag) {
+        const int64_t P = (int64_t)B * H * W;
+        timed(const_cast<lic_codec *>(cd), G.name + ":1dn", 4.0 * P * G.C, 8.0 * P * G.C, 1, st, [&] {
+            launch_norm1d(in, P, G.C, G.beta.as<float>(), G.gamma.as<float>(), G.inverse ? 1 : 0, out, st);
+        });
+        return;
+    }
     ConvDesc d{};
     d.in = in;
     d.out = out;
@@ -457,9 +468,10 @@ float *run_layer_gdn(const lic_codec *cd, const Layer &L, const Gdn &G, const fl
     for (auto &op : L.ops) {
         if (!fuse) break;
         ConvDesc d = op_desc(cd, L, *op, in, B, Hi, Wi, out, Ho, Wo);
-        d.fuse_gdn = G.inverse ? 2 : 1;
+        d.fuse_gdn = G.diag ? (G.inverse ? 4 : 3) : (G.inverse ? 2 : 1);
         d.gdn_beta = G.beta.as<float>();
         d.gdn_w = &G.tcw;
+        d.gdn_gamma = G.gamma.as<float>();
         fuse = d.in_dt != DT_F32 ? tc::can_run_lp(d, op->tcw) : tc::can_run(d, op->tcw);
     }
     if (fuse) {
@@ -785,6 +797,7 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
     cd->M = M;
     if (opts) cd->opt = *opts;
     if (cd->opt.band_rows <= 0) cd->opt.band_rows = 16;
+    if (cd->opt.norm != LIC_NORM_GDN && cd->opt.norm != LIC_NORM_1DN) return LIC_E_INVALID_ARG;
     if (cd->opt.precision < LIC_FP32 || cd->opt.precision > LIC_FP8) return LIC_E_UNSUPPORTED;
     if (cd->opt.precision != LIC_FP32 && cd->opt.conv_impl == LIC_CONV_SIMT) return LIC_E_UNSUPPORTED;
     LIC_CUDA_TRY(cudaGetDevice(&cd->device));
@@ -799,8 +812,9 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
             return rc;
     }
     for (int i = 0; i < 3; ++i) {
-        if ((rc = make_gdn(cd->gdn[i], pm, "g_a.gdn" + std::to_string(i), N, false))) return rc;
-        if ((rc = make_gdn(cd->igdn[i], pm, "g_s.igdn" + std::to_string(i), N, true))) return rc;
+        const bool diag = cd->opt.norm == LIC_NORM_1DN;
+        if ((rc = make_gdn(cd->gdn[i], pm, "g_a.gdn" + std::to_string(i), N, false, diag))) return rc;
+        if ((rc = make_gdn(cd->igdn[i], pm, "g_s.igdn" + std::to_string(i), N, true, diag))) return rc;
     }
     if (kind == LIC_HYPERPRIOR) {
         if ((rc = make_conv(cd->ha[0], pm, "h_a.conv0", M, N, 3, 1, IN_ABS, EPI_RELU))) return rc;
@@ -845,7 +859,8 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
         for (int i = 0; i < 3; ++i)
             if (!check(cd->gs[i])) return LIC_E_UNSUPPORTED;
         for (int i = 0; i < 3; ++i)
-            if (!cd->gdn[i].tcw.valid || !cd->igdn[i].tcw.valid || N != 128) return LIC_E_UNSUPPORTED;
+            if ((!cd->gdn[i].diag && (!cd->gdn[i].tcw.valid || !cd->igdn[i].tcw.valid)) || N != 128)
+                return LIC_E_UNSUPPORTED;
         if (!cd->ga[0].ops[0]->tcw.valid) return LIC_E_UNSUPPORTED;
     }
     // entropy models: the bottleneck codes y (factorized) or z (hyperprior)

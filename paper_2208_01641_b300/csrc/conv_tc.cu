@@ -83,6 +83,7 @@ struct Params {
     float in_scale;               // e4m3 input: x = stored * in_scale
     const float *w_scale;         // e4m3 weights: per output channel
     const float *gdn_beta;
+    const float *gdn_gamma;       // fuse_gdn 3 / 4 (1DN): per-channel gamma
     int kchunks;
     uint32_t tmem_cols;
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
             }
             // gamma slices for the fused norm: pass h uses stages 0 and 1 once
             // the MMAs that read them (main loop, then pass h-1) are done
-            for (int h = 0; p.fuse_gdn && h < GPASS && !*abort_flag; ++h) {
+            for (int h = 0; (p.fuse_gdn == 1 || p.fuse_gdn == 2) && h < GPASS && !*abort_flag; ++h) {
                 if (!mbar_wait(mma_done, h & 1)) {
                     fail();
                     break;
@@ -485,7 +486,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 if (kc % FOLD == FOLD - 1 || kc == p.kchunks - 1) mma_commit(&pfull[q]);
             }
             mma_commit(mma_done);   // phase 0: the main loop's MMAs are complete
-            for (int h = 0; p.fuse_gdn && h < GPASS; ++h) {
+            for (int h = 0; (p.fuse_gdn == 1 || p.fuse_gdn == 2) && h < GPASS; ++h) {
                 if (*abort_flag || !mbar_wait(gdn_ready, h & 1) || !mbar_wait(gdn_full, h & 1)) {
                     fail();
                     break;
@@ -654,7 +655,16 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
         }
         while (ok && folded < groups) fold(folded++);
         const int cbase = half * HALF * 32;
-        if (ok && p.fuse_gdn) {
+        if (ok && p.fuse_gdn >= 3) {
+            // 1DN / inverse 1DN: per-channel, y * rsqrt(beta + gamma y^2) or y * sqrt(.)
+#pragma unroll
+            for (int i = 0; i < HALF * 32; ++i) {
+                const float y = master[i] + __ldg(p.bias + cbase + i);
+                const float n = fmaf(__ldg(p.gdn_gamma + cbase + i), y * y, __ldg(p.gdn_beta + cbase + i));
+                master[i] = p.fuse_gdn == 3 ? y * rsqrtf(n) : y * sqrtf(n);
+            }
+        }
+        if (ok && (p.fuse_gdn == 1 || p.fuse_gdn == 2)) {
             // y = conv + bias, then the norm GEMM on y^2 (see above)
 #pragma unroll
             for (int i = 0; i < HALF * 32; ++i) master[i] += __ldg(p.bias + cbase + i);
@@ -908,7 +918,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
                 tma_load_2d(stage_b(s), &tmB, &full[s], kc * KCE, 0);
                 issued = kc + 1;
             }
-            if (HALF == 2 && p.fuse_gdn && !*abort_flag) {
+            if (HALF == 2 && (p.fuse_gdn == 1 || p.fuse_gdn == 2) && !*abort_flag) {
                 if (!mbar_wait(mma_done, 0)) {
                     fail();
                 } else {
@@ -956,7 +966,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
                 if (kc % FOLD == FOLD - 1 || kc == p.kchunks - 1) mma_commit(&pfull[q]);
             }
             mma_commit(mma_done);
-            if (HALF == 2 && p.fuse_gdn) {
+            if (HALF == 2 && (p.fuse_gdn == 1 || p.fuse_gdn == 2)) {
                 const uint32_t idt = idesc_tf32(BLOCK_M, COUT);
                 if (*abort_flag || !mbar_wait(gdn_ready, 0) || !mbar_wait(gdn_full, 0)) {
                     fail();
@@ -1009,7 +1019,15 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
         }
 #pragma unroll
         for (int i = 0; i < HALF * 32; ++i) master[i] += __ldg(p.bias + cbase + i);
-        if (ok && HALF == 2 && p.fuse_gdn) {
+        if (ok && p.fuse_gdn >= 3) {   // 1DN / inverse 1DN, per channel
+#pragma unroll
+            for (int i = 0; i < HALF * 32; ++i) {
+                const float y = master[i];
+                const float n = fmaf(__ldg(p.gdn_gamma + cbase + i), y * y, __ldg(p.gdn_beta + cbase + i));
+                master[i] = p.fuse_gdn == 3 ? y * rsqrtf(n) : y * sqrtf(n);
+            }
+        }
+        if (ok && HALF == 2 && (p.fuse_gdn == 1 || p.fuse_gdn == 2)) {
 #pragma unroll
             for (int h = 0; h < HALF; ++h) {
                 float hv[32], lv[32];
@@ -1268,7 +1286,8 @@ bool can_run(const ConvDesc &d, const TcWeights &w) {
     if ((reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15)) return false;
     if ((d.epi == EPI_GDN || d.epi == EPI_IGDN) && !d.gdn_x) return false;
     if (d.in_dt != DT_F32 || (d.out_dt != DT_F32 && !d.fuse_gdn)) return false;
-    if (d.fuse_gdn) {
+    if (d.fuse_gdn >= 3 && (!d.gdn_beta || !d.gdn_gamma || d.epi != EPI_NONE)) return false;
+    if (d.fuse_gdn == 1 || d.fuse_gdn == 2) {
         const TcWeights *g = static_cast<const TcWeights *>(d.gdn_w);
         if (!g || !g->valid || g->T != 1 || g->Cin != d.Cout || g->Cout != d.Cout || !d.gdn_beta) return false;
         if (d.epi != EPI_NONE) return false;
@@ -1308,6 +1327,7 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.in_xform = d.in_xform;
     p.fuse_gdn = d.fuse_gdn;
     p.gdn_beta = d.gdn_beta;
+    p.gdn_gamma = d.gdn_gamma;
     p.out_dt = d.out_dt;
     p.out_inv_scale = d.out_scale > 0.f ? 1.f / d.out_scale : 1.f;
     p.tmem_cols = 512;  // partial sums (+ A slots when Cout = 128)
@@ -1358,7 +1378,7 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     if (grid == 0) return true;
     const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(w.maps);
     // without fusion the gamma maps are unused: pass the weight maps
-    const CUtensorMap *gmaps = d.fuse_gdn
+    const CUtensorMap *gmaps = (d.fuse_gdn == 1 || d.fuse_gdn == 2)
                                    ? reinterpret_cast<const CUtensorMap *>(static_cast<const TcWeights *>(d.gdn_w)->maps)
                                    : maps;
     const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
@@ -1377,7 +1397,8 @@ bool can_run_lp(const ConvDesc &d, const TcWeights &w) {
     if ((reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15)) return false;
     if (d.epi != EPI_NONE && d.epi != EPI_RELU) return false;
     if (d.in_xform != IN_NONE) return false;
-    if (d.fuse_gdn) {
+    if (d.fuse_gdn >= 3 && (!d.gdn_beta || !d.gdn_gamma)) return false;
+    if (d.fuse_gdn == 1 || d.fuse_gdn == 2) {
         const TcWeights *g = static_cast<const TcWeights *>(d.gdn_w);
         if (d.Cout != 128 || !g || !g->valid || g->T != 1 || g->Cin != d.Cout || g->Cout != d.Cout || !d.gdn_beta)
             return false;
@@ -1410,6 +1431,7 @@ bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.epi = d.epi;
     p.fuse_gdn = d.fuse_gdn;
     p.gdn_beta = d.gdn_beta;
+    p.gdn_gamma = d.gdn_gamma;
     p.out_dt = d.out_dt;
     p.out_inv_scale = d.out_scale > 0.f ? 1.f / d.out_scale : 1.f;
     p.in_scale = d.in_scale > 0.f ? d.in_scale : 1.f;
@@ -1443,11 +1465,12 @@ bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     }
     if (grid == 0) return true;
     const CUtensorMap &bm = *reinterpret_cast<const CUtensorMap *>(e4 ? w.w8map : w.bmap);
-    const CUtensorMap *g = d.fuse_gdn ? reinterpret_cast<const CUtensorMap *>(
+    const bool gemm_norm = d.fuse_gdn == 1 || d.fuse_gdn == 2;
+    const CUtensorMap *g = gemm_norm ? reinterpret_cast<const CUtensorMap *>(
                                             static_cast<const TcWeights *>(d.gdn_w)->maps)
                                       : &bm;
     const CUtensorMap &gh = g[0];
-    const CUtensorMap &gl = d.fuse_gdn ? g[1] : g[0];
+    const CUtensorMap &gl = gemm_norm ? g[1] : g[0];
     if (d.Cout == 128) {
         const int smem = 6 * (AB_BYTES + 128 * 128) + 256 + 1024;
         if (e4) {

@@ -166,6 +166,21 @@ cudaError_t upload_scale_table() {
     return cudaMemcpyToSymbol(c_scales, T, sizeof(T));
 }
 
+__global__ void norm1d_kernel(const float *__restrict__ in, int64_t n, int C, const float *__restrict__ beta,
+                              const float *__restrict__ gamma, int inverse, float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const float x = in[i];
+        const float v = fmaf(gamma[c], x * x, beta[c]);
+        out[i] = inverse ? x * sqrtf(v) : x * rsqrtf(v);
+    }
+}
+
+void launch_norm1d(const float *in, int64_t P, int C, const float *beta, const float *gamma, int inverse,
+                   float *out, cudaStream_t st) {
+    norm1d_kernel<<<grid_for(P * C), 256, 0, st>>>(in, P * C, C, beta, gamma, inverse, out);
+}
+
 __global__ void to_bf16_kernel(const float *__restrict__ in, int64_t n, __nv_bfloat16 *__restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = __float2bfloat16_rn(in[i]);

@@ -80,9 +80,10 @@ struct ConvDesc {
     // GDN / IGDN fused into the epilogue of this convolution (tensor-core
     // kernel only): 0 none, 1 GDN, 2 IGDN; gdn_w is the tc::TcWeights of gamma
     // ([C][1][C]), gdn_beta its beta.
-    int fuse_gdn;
+    int fuse_gdn;              // 3: 1DN, 4: inverse 1DN (per-channel, gdn_gamma)
     const float *gdn_beta;
     const void *gdn_w;
+    const float *gdn_gamma;
     // precision forms: storage of the input and output activations; e4m3
     // tensors hold x / scale (in_scale, out_scale)
     int in_dt, out_dt;
@@ -126,6 +127,10 @@ void launch_quantize(const float *y, int B, int HW, int C, const float *mu, int3
                      float *yhat, cudaStream_t st);
 // idx = smallest k with T[k] >= max(sigma, T[0]); NaN / > T[63] -> 63.
 // sigma NHWC [B][HW][C] -> idx NCHW [B][C][HW]; sigma_nchw (optional) copy.
+// 1DN / inverse 1DN on NHWC [P][C] float32: out = x * rsqrt(beta + gamma x^2)
+// (inverse: * sqrt).
+void launch_norm1d(const float *in, int64_t P, int C, const float *beta, const float *gamma, int inverse,
+                   float *out, cudaStream_t st);
 // float32 -> bf16 (round to nearest even), n elements.
 void launch_to_bf16(const float *in, int64_t n, void *out, cudaStream_t st);
 // Copies the 64 scales into the constant bank of the current device (once

@@ -115,7 +115,11 @@ def _param_seed(j: int) -> int:
     return (WEIGHT_SEED << 20) + j
 
 
-def make_weights(kind: int, N: int = 128, M: int = 192) -> "OrderedDict[str, np.ndarray]":
+NORM_GDN = 0
+NORM_1DN = 1
+
+
+def make_weights(kind: int, N: int = 128, M: int = 192, norm: int = NORM_GDN) -> "OrderedDict[str, np.ndarray]":
     """Seeded parameters of a factorized-prior (kind 0) or hyperprior (kind 1) codec.
 
     Recipe:
@@ -123,7 +127,9 @@ def make_weights(kind: int, N: int = 128, M: int = 192) -> "OrderedDict[str, np.
       U(-g*sqrt(6/fan_in), g*sqrt(6/fan_in)), fan_in = Cin*k*k with Cin the
       layer's input channels, g = WEIGHT_GAIN (default 1);
     * bias: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) + BIAS_OFFSET (default 0);
-    * GDN/IGDN: beta = 1, gamma = 0.1*I + U(0, 0.01) on every entry;
+    * GDN/IGDN: beta = 1, gamma = 0.1*I + U(0, 0.01) on every entry; with
+      norm = NORM_1DN the per-channel gamma [C] = 0.1 + U(0, 0.01) instead
+      (same parameter names, same streams);
     * entropy bottleneck of C channels (C = M for the factorized codec, the
       latent it codes; C = N for the hyperprior, coding z), filters
       (1,3,3,3,3,1), init_scale 10 as in Ballé 2018 [2] appendix 6.1:
@@ -159,6 +165,8 @@ def make_weights(kind: int, N: int = 128, M: int = 192) -> "OrderedDict[str, np.
             C = N
             if leaf == "beta":
                 arr = np.ones(C)
+            elif norm == NORM_1DN:
+                arr = 0.1 + 0.01 * uniform01(seed, C)
             else:
                 arr = 0.1 * np.eye(C) + 0.01 * uniform01(seed, C * C).reshape(C, C)
         else:  # entropy bottleneck

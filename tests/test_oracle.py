@@ -391,3 +391,25 @@ def test_oracle_chain_lossless_symbols(kind):
     mu = C.med if kind == 0 else None
     ref = O.g_s(W, O.dequantize(enc["s_y"], mu))
     assert np.array_equal(xr, np.clip(ref, 0, 1)[:, :, :70, :100])
+
+
+def test_norm1d_is_gdn_with_diagonal_gamma():
+    """1DN (no channel mixing) equals the pinned GDN with a diagonal gamma
+    matrix, forward and inverse; with gamma = 0, beta = 1 it is the identity."""
+    x = rng.standard_normal((2, 6, 3, 4)) * 2
+    beta = 0.5 + rng.random(6)
+    g = 0.05 + rng.random(6)
+    for inv in (False, True):
+        np.testing.assert_allclose(O.gdn(x, beta, g, inverse=inv), O.gdn(x, beta, np.diag(g), inverse=inv),
+                                   rtol=1e-14, atol=0)
+    assert np.array_equal(O.gdn(x, np.ones(6), np.zeros(6)), x)
+
+
+def test_norm1d_codec_roundtrip():
+    W = synth.make_weights(1, 16, 24, norm=synth.NORM_1DN)
+    assert W["g_a.gdn0.gamma"].shape == (16,)
+    C = O.Codec(1, 16, 24, W)
+    x = synth.make_frames(1, 64, 64)
+    bs, enc = O.encode(C, x)
+    xr, dec = O.decode(C, bs)
+    assert np.array_equal(dec[0]["s_y"], enc["s_y"][0])
