@@ -12,6 +12,12 @@ strings them together in the order of the paper's Fig. 1 / Sec. III:
   encoder  x -> g_a -> y -> Q -> E       (+ h_a -> z -> Q -> E, h_s -> scales)
   decoder  E^-1 -> Q^-1 -> g_s -> x_hat  (+ z first, then h_s, then y)
 
+The learned form's distilled student synthesis net (4 transposed convs,
+ReLU, MSE against the teacher's g_s output) has its forward pass, its
+backward pass by the chain rule, and Adam (Kingma & Ba 2015, Algorithm 1)
+here too; they are pinned by finite differences, torch float64 autograd
+and the constant-gradient closed form of Adam.
+
 The bitstream container is the project's own format (the paper integrates
 CompressAI's coder and defines no format); it is written out below
 byte by byte.
@@ -67,6 +73,7 @@ def lib():
         L.orc_deconv2d.argtypes = [dp, ip, ip, ip, ip, dp, dp, ip, ip, ip, dp]
         L.orc_gdn.argtypes = [dp, ip, ip, ip, ip, dp, dp, ip]
         L.orc_norm1d.argtypes = [dp, ip, ip, ip, ip, dp, dp, ip]
+        L.orc_deconv2d_wgrad.argtypes = [dp, ip, ip, ip, ip, dp, ip, ip, ip, dp]
         L.orc_relu.argtypes = [dp, ctypes.c_int64]
         L.orc_abs.argtypes = [dp, ctypes.c_int64]
         L.orc_eb_logits.argtypes = [dp, ctypes.c_double]
@@ -507,6 +514,77 @@ def decode(codec: Codec, bitstreams):
         outs.append(np.clip(xr[0], 0.0, 1.0)[:, :hdr["H"], :hdr["W"]])
         inter.append(lat)
     return np.stack(outs), inter
+
+
+# --------------------------------------------------------------------------
+# distilled student synthesis net (learned form): 4 x deconv5x5/2, ReLU
+# after the first three, no IGDN; trained by MSE against the teacher's x_hat
+# --------------------------------------------------------------------------
+
+def deconv2d_wgrad(x, g, k=5, stride=2):
+    x, g = _f64(x), _f64(g)
+    B, Cin, H, W = x.shape
+    Cout = g.shape[1]
+    dw = np.zeros((Cin, Cout, k, k))
+    lib().orc_deconv2d_wgrad(_p(x, ctypes.c_double), B, Cin, H, W, _p(g, ctypes.c_double), Cout, k, stride,
+                             _p(dw, ctypes.c_double))
+    return dw
+
+
+def student_forward(P, yhat):
+    """Activations [h0 = y_hat, h1, h2, h3] (post-ReLU) and the output."""
+    hs = [_f64(yhat)]
+    for l in range(4):
+        z = deconv2d(hs[-1], P[f"student.deconv{l}.weight"], P[f"student.deconv{l}.bias"], 2)
+        if l < 3:
+            hs.append(relu(z))
+        else:
+            return hs, z
+
+
+def student_loss_grads(P, yhat, target):
+    """MSE loss mean((out - target)^2) and its gradients with respect to every
+    student parameter, by the chain rule: output gradient 2 (out - t) / n; per
+    layer, the weight gradient of the transposed conv, the bias gradient
+    (sum over positions), and the input gradient (the strided conv with the
+    same weights -- the transposed conv's adjoint) masked by ReLU."""
+    hs, out = student_forward(P, yhat)
+    t = _f64(target)
+    n = out.size
+    loss = float(np.mean((out - t) ** 2))
+    g = 2.0 * (out - t) / n
+    grads = {}
+    for l in range(3, -1, -1):
+        w = _f64(P[f"student.deconv{l}.weight"])
+        grads[f"student.deconv{l}.weight"] = deconv2d_wgrad(hs[l], g)
+        grads[f"student.deconv{l}.bias"] = g.sum(axis=(0, 2, 3))
+        if l > 0:
+            g = conv2d(g, w, None, 2) * (hs[l] > 0)
+    return loss, grads
+
+
+def adam_step(P, G, m, v, t, lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) of every tensor in P,
+    in place: m <- b1 m + (1 - b1) g; v <- b2 v + (1 - b2) g^2;
+    m_hat = m / (1 - b1^t); v_hat = v / (1 - b2^t);
+    theta <- theta - lr m_hat / (sqrt(v_hat) + eps).  t counts from 1."""
+    for k in P:
+        g = _f64(G[k])
+        m[k] = beta1 * m[k] + (1.0 - beta1) * g
+        v[k] = beta2 * v[k] + (1.0 - beta2) * g * g
+        mh = m[k] / (1.0 - beta1 ** t)
+        vh = v[k] / (1.0 - beta2 ** t)
+        P[k] = _f64(P[k]) - lr * mh / (np.sqrt(vh) + eps)
+
+
+def student_crops(yhat_pool, xhat_pool, crops, crop):
+    """A training batch: for each (frame, row, col) in latent units, the
+    crop/16-square latent window of y_hat and the crop-square window of x_hat
+    at 16x those coordinates."""
+    lc = crop // 16
+    ys = np.stack([yhat_pool[f, :, r:r + lc, c:c + lc] for f, r, c in crops])
+    xs = np.stack([xhat_pool[f, :, 16 * r:16 * r + crop, 16 * c:16 * c + crop] for f, r, c in crops])
+    return ys, xs
 
 
 def psnr(a, b):

@@ -84,6 +84,37 @@ void orc_deconv2d(const double *x, int B, int Cin, int H, int W,
     }
 }
 
+/* The derivative of the transposed convolution's scatter with respect to
+ * each weight: every (input sample, tap) pair that the forward pass added
+ * contributes x * g at the same output position. */
+void orc_deconv2d_wgrad(const double *x, int B, int Cin, int H, int W, const double *g, int Cout,
+                        int k, int s, double *dw)
+{
+    int p = k / 2;
+    int Ho = s * H, Wo = s * W;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < Cin; i++)
+        for (int o = 0; o < Cout; o++)
+            for (int u = 0; u < k; u++)
+                for (int v = 0; v < k; v++) {
+                    double acc = 0.0;
+                    for (int b = 0; b < B; b++) {
+                        const double *xi = x + ((int64_t)b * Cin + i) * H * W;
+                        const double *go = g + ((int64_t)b * Cout + o) * Ho * Wo;
+                        for (int a = 0; a < H; a++) {
+                            int r = s * a + u - p;
+                            if (r < 0 || r >= Ho) continue;
+                            for (int c = 0; c < W; c++) {
+                                int q = s * c + v - p;
+                                if (q < 0 || q >= Wo) continue;
+                                acc += xi[a * W + c] * go[r * Wo + q];
+                            }
+                        }
+                    }
+                    dw[(((int64_t)i * Cout + o) * k + u) * k + v] = acc;
+                }
+}
+
 /* GDN / IGDN, Ballé, Laparra, Simoncelli [9]: a per-pixel divisive
  * normalisation over channels. */
 void orc_gdn(double *x, int B, int C, int H, int W,

@@ -39,6 +39,13 @@ void orc_deconv2d(const double *x, int B, int Cin, int H, int W,
                   const double *w, const double *bias, int Cout, int k, int s,
                   double *y);
 
+/* Weight gradient of the transposed convolution orc_deconv2d (same k, s,
+ * pad k/2): dw[i,o,u,v] = sum_{b,a,c} x[b,i,a,c] * g[b,o, s*a+u-k/2, s*c+v-k/2]
+ * over output positions inside the s*H x s*W output.  x: B x Cin x H x W,
+ * g: B x Cout x sH x sW, dw: Cin x Cout x k x k (overwritten). */
+void orc_deconv2d_wgrad(const double *x, int B, int Cin, int H, int W, const double *g, int Cout,
+                        int k, int s, double *dw);
+
 /* GDN (Ballé et al. [9]) in place, per pixel:
  *   inverse == 0: x_i <- x_i / sqrt(beta_i + sum_j gamma[i,j] x_j^2)
  *   inverse == 1: x_i <- x_i * sqrt(beta_i + sum_j gamma[i,j] x_j^2)   (IGDN) */

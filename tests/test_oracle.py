@@ -413,3 +413,80 @@ def test_norm1d_codec_roundtrip():
     bs, enc = O.encode(C, x)
     xr, dec = O.decode(C, bs)
     assert np.array_equal(dec[0]["s_y"], enc["s_y"][0])
+
+
+def _tiny_student(seed=3, ch=(5, 4, 3, 4, 3)):
+    r = np.random.default_rng(seed)
+    P = {}
+    for l in range(4):
+        P[f"student.deconv{l}.weight"] = r.standard_normal((ch[l], ch[l + 1], 5, 5)) * 0.3
+        P[f"student.deconv{l}.bias"] = r.standard_normal(ch[l + 1]) * 0.1
+    return P
+
+
+def test_student_gradients_match_finite_differences():
+    """The oracle's backward pass (chain rule through 4 transposed convs and
+    ReLUs, MSE) against central finite differences of the loss at sampled
+    coordinates of every parameter tensor."""
+    P = _tiny_student()
+    r = np.random.default_rng(4)
+    yhat = r.standard_normal((2, 5, 3, 4))
+    target = r.standard_normal((2, 3, 48, 64))
+    loss, grads = O.student_loss_grads(P, yhat, target)
+    eps = 1e-6
+    for name, gval in grads.items():
+        for _ in range(4):
+            idx = tuple(r.integers(0, s) for s in P[name].shape)
+            Pp = {k: v.copy() for k, v in P.items()}
+            Pm = {k: v.copy() for k, v in P.items()}
+            Pp[name][idx] += eps
+            Pm[name][idx] -= eps
+            fd = (O.student_loss_grads(Pp, yhat, target)[0] - O.student_loss_grads(Pm, yhat, target)[0]) / (2 * eps)
+            assert abs(fd - gval[idx]) <= 1e-6 * max(1.0, abs(fd)), (name, idx, fd, gval[idx])
+
+
+def test_deconv_wgrad_matches_torch_autograd():
+    """Weight gradient of the transposed conv against torch's float64 autograd
+    of conv_transpose2d (a library routine)."""
+    r = np.random.default_rng(6)
+    x = r.standard_normal((2, 4, 5, 6))
+    g = r.standard_normal((2, 3, 10, 12))
+    w = torch.zeros((4, 3, 5, 5), dtype=torch.float64, requires_grad=True)
+    y = torch.nn.functional.conv_transpose2d(torch.from_numpy(x), w, stride=2, padding=2, output_padding=1)
+    (y * torch.from_numpy(g)).sum().backward()
+    np.testing.assert_allclose(O.deconv2d_wgrad(x, g), w.grad.numpy(), rtol=0, atol=1e-12)
+
+
+def test_adam_constant_gradient_closed_form():
+    """Adam with a constant gradient g has m_hat = g and v_hat = g^2 at every
+    step (the bias corrections cancel the geometric sums exactly), so each
+    step moves theta by -lr g / (|g| + eps); a zero gradient moves nothing."""
+    r = np.random.default_rng(9)
+    g = r.standard_normal(50) * 10.0 ** r.uniform(-4, 1, 50)
+    g[:3] = 0.0
+    P = {"w": r.standard_normal(50)}
+    start = P["w"].copy()
+    m = {"w": np.zeros(50)}
+    v = {"w": np.zeros(50)}
+    lr, eps = 1e-3, 1e-8
+    for t in range(1, 6):
+        O.adam_step(P, {"w": g}, m, v, t, lr=lr, eps=eps)
+        want = start - t * lr * g / (np.abs(g) + eps)
+        np.testing.assert_allclose(P["w"], want, rtol=0, atol=1e-12)
+    assert np.array_equal(P["w"][:3], start[:3])
+
+
+def test_student_training_decreases_loss():
+    """A few oracle Adam steps on a fixed tiny batch lower the student's MSE
+    (a consistency check of gradient sign and update direction together)."""
+    P = _tiny_student(seed=11)
+    r = np.random.default_rng(12)
+    yhat = r.standard_normal((2, 5, 3, 4))
+    target = r.standard_normal((2, 3, 48, 64)) * 0.1
+    m = {k: np.zeros_like(v) for k, v in P.items()}
+    v = {k: np.zeros_like(x) for k, x in P.items()}
+    l0 = O.student_loss_grads(P, yhat, target)[0]
+    for t in range(1, 21):
+        loss, grads = O.student_loss_grads(P, yhat, target)
+        O.adam_step(P, grads, m, v, t, lr=1e-2)
+    assert O.student_loss_grads(P, yhat, target)[0] < 0.5 * l0
