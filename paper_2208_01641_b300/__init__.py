@@ -38,7 +38,14 @@ EXPORTED = [
     "lic_synthesis", "lic_hyper_analysis", "lic_hyper_synthesis", "lic_encode_latents",
     "lic_decode_latents", "lic_build_tables", "lic_scale_table", "lic_strerror",
     "lic_profile_enable", "lic_profile_report", "lic_launch_count", "lic_encode_latents_noalloc",
+    # include/lic_student.h (learned form)
+    "lic_student_create", "lic_student_destroy", "lic_student_grad", "lic_student_step", "lic_student_read",
+    "lic_student_read_activation", "lic_student_steps", "lic_student_forward", "lic_student_profile_enable", "lic_student_profile_report",
+    "lic_student_launch_count", "lic_codec_set_student", "lic_codec_student_report",
 ]
+
+STUDENT_PARAM, STUDENT_GRAD, STUDENT_ADAM_M, STUDENT_ADAM_V = range(4)
+STUDENT_MAX_BATCH = 64
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -61,6 +68,12 @@ class _Weights(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("band_rows", ctypes.c_int),
                 ("conv_impl", ctypes.c_int), ("norm", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+class _StudentOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_batch", ctypes.c_int), ("crop", ctypes.c_int),
+                ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("reserved", ctypes.c_int * 4)]
 
 
 class _Bitstreams(ctypes.Structure):
@@ -105,6 +118,23 @@ def _lib():
         L.lic_profile_report.argtypes = [vp, ctypes.c_char_p, i]
         L.lic_launch_count.argtypes = [vp]
         L.lic_launch_count.restype = i64
+        L.lic_student_create.argtypes = [ctypes.POINTER(_Weights), i, i, ctypes.POINTER(_StudentOptions),
+                                         ctypes.POINTER(vp)]
+        L.lic_student_destroy.argtypes = [vp]
+        L.lic_student_destroy.restype = None
+        L.lic_student_grad.argtypes = [vp, vp, vp, i, i, i, vp, i, ctypes.POINTER(ctypes.c_float), vp]
+        L.lic_student_step.argtypes = [vp, vp, vp, i, i, i, vp, i, ctypes.POINTER(ctypes.c_float), vp]
+        L.lic_student_read.argtypes = [vp, ctypes.c_char_p, i, vp, i64]
+        L.lic_student_read_activation.argtypes = [vp, i, vp, i64]
+        L.lic_student_steps.argtypes = [vp]
+        L.lic_student_steps.restype = i64
+        L.lic_student_forward.argtypes = [vp, vp, i, i, i, vp, vp]
+        L.lic_student_profile_enable.argtypes = [vp, i]
+        L.lic_student_profile_report.argtypes = [vp, ctypes.c_char_p, i]
+        L.lic_student_launch_count.argtypes = [vp]
+        L.lic_student_launch_count.restype = i64
+        L.lic_codec_set_student.argtypes = [vp, vp, ctypes.c_float, i]
+        L.lic_codec_student_report.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), vp, i]
         L.lic_strerror.argtypes = [i]
         L.lic_strerror.restype = ctypes.c_char_p
         _LIB = L
@@ -256,6 +286,20 @@ class Codec:
     def launch_count(self) -> int:
         return int(_lib().lic_launch_count(self.h))
 
+    def set_student(self, student: Optional["Student"], min_psnr_db: float = 35.0, checked: bool = False):
+        """Decode with ``student`` in place of g_s (None restores g_s)."""
+        self._student = student
+        _check(_lib().lic_codec_set_student(self.h, student.h if student else None, float(min_psnr_db),
+                                            1 if checked else 0), "lic_codec_set_student")
+
+    def student_report(self, cap: int = 1024):
+        """(frames checked, fallbacks, per-frame PSNR of the last checked decode)."""
+        fr, fb = ctypes.c_int64(), ctypes.c_int64()
+        ps = np.zeros(cap, np.float32)
+        n = _check(_lib().lic_codec_student_report(self.h, ctypes.byref(fr), ctypes.byref(fb), _ptr(ps), cap),
+                   "lic_codec_student_report")
+        return fr.value, fb.value, ps[:min(n, cap)]
+
     def encode(self, frames, stream=None) -> Bitstreams:
         B, C, H, W = frames.shape
         assert C == 3
@@ -343,3 +387,89 @@ def decoded_shape(frame: bytes):
     _check(_lib().lic_decoded_shape(_ptr(buf), len(frame), ctypes.byref(k), ctypes.byref(h), ctypes.byref(w)),
            "lic_decoded_shape")
     return k.value, h.value, w.value
+
+
+def _profile_json(fn, h):
+    import json
+    n = _check(fn(h, None, 0), "profile_report")
+    buf = ctypes.create_string_buffer(n + 1)
+    _check(fn(h, buf, n + 1), "profile_report")
+    return json.loads(buf.value.decode())
+
+
+class Student:
+    """The learned form's student synthesis net (include/lic_student.h)."""
+
+    def __init__(self, weights: Dict[str, np.ndarray], M: int = 192, C: int = 64, max_batch: int = 16,
+                 crop: int = 256, lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                 precision: int = FP32):
+        self.M, self.C, self.crop = M, C, crop
+        self.shapes = {k: tuple(np.shape(v)) for k, v in weights.items() if k.startswith("student.")}
+        w, keep = _weights_struct(weights)
+        opt = _StudentOptions(precision, max_batch, crop, lr, beta1, beta2, eps)
+        h = ctypes.c_void_p()
+        _check(_lib().lic_student_create(ctypes.byref(w), M, C, ctypes.byref(opt), ctypes.byref(h)),
+               "lic_student_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().lic_student_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, fn, name, yhat_pool, xhat_pool, crops, want_loss, stream):
+        P, M, Hy, Wy = yhat_pool.shape
+        crops = np.ascontiguousarray(crops, dtype=np.int32)
+        loss = ctypes.c_float()
+        _check(fn(self.h, _ptr(yhat_pool), _ptr(xhat_pool), P, Hy, Wy, _ptr(crops), crops.shape[0],
+                  ctypes.byref(loss) if want_loss else None, _stream(stream)), name)
+        return loss.value if want_loss else None
+
+    def grad(self, yhat_pool, xhat_pool, crops, want_loss=True, stream=None):
+        """Loss and gradients of one batch (lic_student_grad)."""
+        return self._call(_lib().lic_student_grad, "lic_student_grad", yhat_pool, xhat_pool, crops, want_loss,
+                          stream)
+
+    def step(self, yhat_pool, xhat_pool, crops, want_loss=False, stream=None):
+        """Gradients and one Adam step (lic_student_step)."""
+        return self._call(_lib().lic_student_step, "lic_student_step", yhat_pool, xhat_pool, crops, want_loss,
+                          stream)
+
+    def read(self, name: str, what: int = STUDENT_PARAM) -> np.ndarray:
+        out = np.zeros(self.shapes[name], np.float32)
+        _check(_lib().lic_student_read(self.h, name.encode(), what, _ptr(out), out.size), "lic_student_read")
+        return out
+
+    def activation(self, layer: int, B: int) -> np.ndarray:
+        """Post-ReLU h_layer of the last training batch, NHWC."""
+        side = self.crop >> (4 - layer)
+        out = np.zeros((B, side, side, self.C), np.float32)
+        _check(_lib().lic_student_read_activation(self.h, layer, _ptr(out), out.size),
+               "lic_student_read_activation")
+        return out
+
+    def params(self) -> "Dict[str, np.ndarray]":
+        return {k: self.read(k) for k in self.shapes}
+
+    def steps(self) -> int:
+        return int(_lib().lic_student_steps(self.h))
+
+    def forward(self, yhat, x, stream=None):
+        B, M, Hy, Wy = yhat.shape
+        _check(_lib().lic_student_forward(self.h, _ptr(yhat), B, Hy, Wy, _ptr(x), _stream(stream)),
+               "lic_student_forward")
+
+    def profile(self, enable: bool):
+        _check(_lib().lic_student_profile_enable(self.h, 1 if enable else 0), "lic_student_profile_enable")
+
+    def profile_report(self):
+        return _profile_json(_lib().lic_student_profile_report, self.h)
+
+    def launch_count(self) -> int:
+        return int(_lib().lic_student_launch_count(self.h))

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/lic_student.h"
 #include "conv_tc.h"
 #include "lic_internal.h"
 
@@ -22,41 +23,6 @@ void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int 
 
 namespace {
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    ~DevBuf() { release(); }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    cudaError_t ensure(size_t n) {
-        if (n <= bytes) return cudaSuccess;
-        release();
-        cudaError_t e = cudaMalloc(&p, n);
-        if (e == cudaSuccess) bytes = n;
-        else p = nullptr;
-        return e;
-    }
-    template <typename T>
-    T *as() const { return static_cast<T *>(p); }
-};
-
-struct HostPinned {
-    void *p = nullptr;
-    size_t bytes = 0;
-    ~HostPinned() { if (p) cudaFreeHost(p); }
-    cudaError_t ensure(size_t n) {
-        if (n <= bytes) return cudaSuccess;
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        bytes = 0;
-        cudaError_t e = cudaMallocHost(&p, n);
-        if (e == cudaSuccess) bytes = n;
-        return e;
-    }
-};
 
 // One GEMM launch of a layer: a full convolution, or one sub-pixel phase of
 // a transposed convolution.
@@ -110,20 +76,12 @@ struct lic_codec {
     lic::DevBuf scratch, counts, sub_off, frame_bytes, offs, data, stage_in, stage_out, in_data, in_offs;
     lic::HostPinned h_offs;
     // measurement
-    struct ProfRec {
-        std::string name;
-        cudaEvent_t a, b;
-        double flop, bytes;
-        int launches;
-    };
-    bool prof_on = false;
-    std::vector<ProfRec> prof;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
-    int64_t launches = 0;
-    ~lic_codec() {
-        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-    }
+    lic::Profiler pf;
+    // learned form: the student that replaces g_s (not owned)
+    lic_student *student = nullptr;
+    float stu_thr = 0.f;
+    int stu_checked = 0, stu_lastB = 0;
+    lic::DevBuf xstu, stu_part, stu_psnr, stu_pass, stu_counts;
     // last call (for lic_read_tensor)
     int last_B = 0, last_Hp = 0, last_Wp = 0;
     bool have_y = false, have_sy = false, have_z = false, have_sz = false, have_sigma = false, have_idx = false,
@@ -133,14 +91,6 @@ struct lic_codec {
 namespace lic {
 namespace {
 
-bool is_device_ptr(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 void atomic_status(const lic_codec *cd, uint32_t bits) {
     // a launch that could not be made (host side): latch it like a kernel would
@@ -150,29 +100,11 @@ void atomic_status(const lic_codec *cd, uint32_t bits) {
     cudaMemcpy(cd->status.p, &cur, 4, cudaMemcpyHostToDevice);
 }
 
-cudaEvent_t next_event(lic_codec *cd) {
-    if (cd->ev_used == cd->ev_pool.size()) {
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        cd->ev_pool.push_back(e);
-    }
-    return cd->ev_pool[cd->ev_used++];
-}
-
 // Every kernel launch goes through here: counts it and, when profiling is
 // on, brackets it with CUDA events on its stream.
 template <typename F>
 void timed(lic_codec *cd, const std::string &name, double flop, double bytes, int nlaunch, cudaStream_t st, F &&f) {
-    cd->launches += nlaunch;
-    if (!cd->prof_on) {
-        f();
-        return;
-    }
-    cudaEvent_t a = next_event(cd), b = next_event(cd);
-    cudaEventRecord(a, st);
-    f();
-    cudaEventRecord(b, st);
-    cd->prof.push_back({name, a, b, flop, bytes, nlaunch});
+    cd->pf.run(name, flop, bytes, nlaunch, st, f);
 }
 
 using ParamMap = std::map<std::string, std::pair<const float *, int64_t>>;
@@ -566,7 +498,7 @@ void hyper_synthesis(lic_codec *cd, const float *zhat, int B, int Hz, int Wz, cu
 }
 
 // g_s: y_hat (NHWC) -> xpre (NHWC, 3 channels); deconvs with IGDN between
-void synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, cudaStream_t st) {
+void teacher_synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, cudaStream_t st) {
     float *a = cd->act0.as<float>(), *b = cd->act1.as<float>();
     int H = Hy, W = Wy;
     const float *in = yhat;
@@ -581,6 +513,34 @@ void synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, cudaStre
         W *= 2;
     }
     run_layer(cd, cd->gs[3], in, B, H, W, cd->xpre.as<float>(), st);
+}
+
+// g_s, or the student in its place when one is set
+int synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, cudaStream_t st) {
+    if (cd->student) return student_forward_nhwc(cd->student, yhat, B, Hy, Wy, cd->xpre.as<float>(), st);
+    teacher_synthesis(cd, yhat, B, Hy, Wy, st);
+    return LIC_OK;
+}
+
+// checked decoding: both nets, per-frame PSNR of the student against the
+// teacher, the teacher's frame wherever the student falls below the bar
+int checked_synthesis(lic_codec *cd, int B, int Hp, int Wp, int H, int W, cudaStream_t st) {
+    if (B > 1024) return LIC_E_INVALID_ARG;
+    teacher_synthesis(cd, cd->yhat.as<float>(), B, Hp / 16, Wp / 16, st);
+    LIC_CUDA_TRY(cd->xstu.ensure((size_t)B * Hp * Wp * 3 * sizeof(float)));
+    LIC_CUDA_TRY(cd->stu_part.ensure((size_t)B * 64 * sizeof(double)));
+    LIC_CUDA_TRY(cd->stu_psnr.ensure((size_t)B * sizeof(float)));
+    LIC_CUDA_TRY(cd->stu_pass.ensure((size_t)B * sizeof(int)));
+    int rc = student_forward_nhwc(cd->student, cd->yhat.as<float>(), B, Hp / 16, Wp / 16, cd->xstu.as<float>(), st);
+    if (rc) return rc;
+    timed(cd, "student_check", 0, 24.0 * B * Hp * Wp, 3, st, [&] {
+        launch_student_check(cd->xstu.as<float>(), cd->xpre.as<float>(), B, Hp, Wp, H, W, cd->stu_thr,
+                             cd->stu_part.as<double>(), cd->stu_psnr.as<float>(), cd->stu_pass.as<int>(),
+                             cd->stu_counts.as<long long>(), st);
+    });
+    cd->stu_lastB = B;
+    LIC_CUDA_TRY(cudaGetLastError());
+    return LIC_OK;
 }
 
 void fill_out(lic_codec *cd, int B, lic_bitstreams *out) {
@@ -975,7 +935,9 @@ int lic_decode(lic_codec *cd, const lic_bitstreams *in, int H, int W, float *fra
     int rc = entropy_decode(cd, in, H, W, st);
     if (rc) return rc;
     const int B = in->count, Hp = pad64(H), Wp = pad64(W);
-    synthesis(cd, cd->yhat.as<float>(), B, Hp / 16, Wp / 16, st);
+    rc = (cd->student && cd->stu_checked) ? checked_synthesis(cd, B, Hp, Wp, H, W, st)
+                                          : synthesis(cd, cd->yhat.as<float>(), B, Hp / 16, Wp / 16, st);
+    if (rc) return rc;
     cd->have_xpre = true;
     const size_t bytes = (size_t)B * 3 * H * W * sizeof(float);
     if (is_device_ptr(frames)) {
@@ -1003,51 +965,40 @@ int64_t lic_bitstreams_download(const lic_bitstreams *in, uint8_t *dst, int64_t 
 
 int lic_profile_enable(lic_codec *cd, int enable) {
     if (!cd) return LIC_E_INVALID_ARG;
-    if (enable) {
-        cd->prof.clear();
-        cd->ev_used = 0;
-    }
-    cd->prof_on = enable != 0;
+    cd->pf.enable(enable != 0);
     return LIC_OK;
 }
 
-int lic_profile_report(lic_codec *cd, char *buf, int cap) {
-    if (!cd) return LIC_E_INVALID_ARG;
-    struct Agg {
-        int launches = 0;
-        double ms = 0, flop = 0, bytes = 0;
-    };
-    std::vector<std::string> order;
-    std::map<std::string, Agg> agg;
-    for (auto &r : cd->prof) {
-        LIC_CUDA_TRY(cudaEventSynchronize(r.b));
-        float ms = 0;
-        LIC_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
-        if (!agg.count(r.name)) order.push_back(r.name);
-        Agg &a = agg[r.name];
-        a.launches += r.launches;
-        a.ms += ms;
-        a.flop += r.flop;
-        a.bytes += r.bytes;
-    }
-    std::string js = "[";
-    char tmp[512];
-    for (size_t i = 0; i < order.size(); ++i) {
-        const Agg &a = agg[order[i]];
-        snprintf(tmp, sizeof(tmp), "%s{\"name\": \"%s\", \"launches\": %d, \"ms\": %.6f, \"flop\": %.6e, \"bytes\": %.6e}",
-                 i ? ", " : "", order[i].c_str(), a.launches, a.ms, a.flop, a.bytes);
-        js += tmp;
-    }
-    js += "]";
-    if (buf && cap > 0) {
-        size_t n = std::min((size_t)cap - 1, js.size());
-        memcpy(buf, js.data(), n);
-        buf[n] = 0;
-    }
-    return (int)js.size();
+int lic_profile_report(lic_codec *cd, char *buf, int cap) { return cd ? cd->pf.report(buf, cap) : LIC_E_INVALID_ARG; }
+
+int64_t lic_launch_count(lic_codec *cd) { return cd ? cd->pf.launches : LIC_E_INVALID_ARG; }
+
+int lic_codec_set_student(lic_codec *cd, lic_student *student, float min_psnr_db, int checked) {
+    if (!cd || (student && student_channels(student) != cd->M) || (checked != 0 && checked != 1))
+        return LIC_E_INVALID_ARG;
+    if (student && checked && !(min_psnr_db == min_psnr_db)) return LIC_E_INVALID_ARG;
+    LIC_CUDA_TRY(cudaDeviceSynchronize());
+    LIC_CUDA_TRY(cd->stu_counts.ensure(2 * sizeof(long long)));
+    LIC_CUDA_TRY(cudaMemset(cd->stu_counts.p, 0, 2 * sizeof(long long)));
+    cd->student = student;
+    cd->stu_thr = min_psnr_db;
+    cd->stu_checked = student ? checked : 0;
+    cd->stu_lastB = 0;
+    cd->have_xpre = false;
+    return LIC_OK;
 }
 
-int64_t lic_launch_count(lic_codec *cd) { return cd ? cd->launches : LIC_E_INVALID_ARG; }
+int lic_codec_student_report(lic_codec *cd, int64_t *frames, int64_t *fallbacks, float *last_psnr, int cap) {
+    if (!cd || cap < 0) return LIC_E_INVALID_ARG;
+    LIC_CUDA_TRY(cudaDeviceSynchronize());
+    long long c[2] = {0, 0};
+    if (cd->stu_counts.p) LIC_CUDA_TRY(cudaMemcpy(c, cd->stu_counts.p, sizeof(c), cudaMemcpyDeviceToHost));
+    if (frames) *frames = c[0];
+    if (fallbacks) *fallbacks = c[1];
+    const int n = std::min(cap, cd->stu_lastB);
+    if (last_psnr && n > 0) LIC_CUDA_TRY(cudaMemcpy(last_psnr, cd->stu_psnr.p, n * sizeof(float), cudaMemcpyDeviceToHost));
+    return cd->stu_lastB;
+}
 
 int lic_decoded_shape(const uint8_t *f, int64_t size, int *kind, int *H, int *W) {
     if (!f || size < 36) return LIC_E_INVALID_ARG;
@@ -1114,7 +1065,7 @@ int lic_synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, float
     int rc = ensure_workspace(cd, B, 16 * Hy, 16 * Wy);
     if (rc) return rc;
     if ((rc = ingest_nchw(cd, yhat, B, cd->M, Hy, Wy, cd->yhat.as<float>(), st))) return rc;
-    synthesis(cd, cd->yhat.as<float>(), B, Hy, Wy, st);
+    if ((rc = synthesis(cd, cd->yhat.as<float>(), B, Hy, Wy, st))) return rc;
     return emit_nchw(cd, cd->xpre.as<float>(), B, 16 * Hy, 16 * Wy, 3, x, st);
 }
 

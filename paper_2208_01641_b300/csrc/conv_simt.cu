@@ -147,6 +147,8 @@ __global__ void __launch_bounds__(NT) conv_simt_kernel(const ConvDesc d) {
                 v = d.gdn_x[opix * d.Cout + n] * rsqrtf(v);
             } else if (d.epi == EPI_IGDN) {
                 v = d.gdn_x[opix * d.Cout + n] * sqrtf(v);
+            } else if (d.epi == EPI_MASK) {
+                v = d.gdn_x[opix * d.Cout + n] > 0.f ? v : 0.f;
             }
             d.out[opix * d.Cout + n] = v;
         }

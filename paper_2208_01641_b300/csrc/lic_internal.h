@@ -6,6 +6,9 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -36,6 +39,160 @@ enum : uint32_t {
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 
 // ---------------------------------------------------------------------------
+// device / pinned buffers, pointer kinds
+// ---------------------------------------------------------------------------
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        else p = nullptr;
+        return e;
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+struct HostPinned {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~HostPinned() { if (p) cudaFreeHost(p); }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMallocHost(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+};
+
+inline bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// launch counting and optional CUDA-event timing of every launch
+// ---------------------------------------------------------------------------
+
+struct Profiler {
+    struct Rec {
+        std::string name;
+        cudaEvent_t a, b;
+        double flop, bytes;
+        int launches;
+    };
+    bool on = false;
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    int64_t launches = 0;
+    ~Profiler() {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+    cudaEvent_t next_event() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void enable(bool en) {
+        if (en) {
+            recs.clear();
+            used = 0;
+        }
+        on = en;
+    }
+    // count nlaunch launches made by f(); with recording on, bracket them
+    // with an event pair on st
+    template <typename F>
+    void run(const std::string &name, double flop, double bytes, int nlaunch, cudaStream_t st, F &&f) {
+        launches += nlaunch;
+        if (!on) {
+            f();
+            return;
+        }
+        cudaEvent_t a = next_event(), b = next_event();
+        cudaEventRecord(a, st);
+        f();
+        cudaEventRecord(b, st);
+        recs.push_back({name, a, b, flop, bytes, nlaunch});
+    }
+    // JSON list of {"name", "launches", "ms", "flop", "bytes"} aggregated by
+    // name in first-seen order; returns the length or a negative LIC_E_*
+    int report(char *buf, int cap) {
+        struct Agg {
+            int launches = 0;
+            double ms = 0, flop = 0, bytes = 0;
+        };
+        std::vector<std::string> order;
+        std::map<std::string, Agg> agg;
+        for (auto &r : recs) {
+            LIC_CUDA_TRY(cudaEventSynchronize(r.b));
+            float ms = 0;
+            LIC_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+            if (!agg.count(r.name)) order.push_back(r.name);
+            Agg &g = agg[r.name];
+            g.launches += r.launches;
+            g.ms += ms;
+            g.flop += r.flop;
+            g.bytes += r.bytes;
+        }
+        std::string js = "[";
+        char tmp[512];
+        for (size_t i = 0; i < order.size(); ++i) {
+            const Agg &g = agg[order[i]];
+            snprintf(tmp, sizeof(tmp),
+                     "%s{\"name\": \"%s\", \"launches\": %d, \"ms\": %.6f, \"flop\": %.6e, \"bytes\": %.6e}",
+                     i ? ", " : "", order[i].c_str(), g.launches, g.ms, g.flop, g.bytes);
+            js += tmp;
+        }
+        js += "]";
+        if (buf && cap > 0) {
+            size_t n = std::min((size_t)cap - 1, js.size());
+            memcpy(buf, js.data(), n);
+            buf[n] = 0;
+        }
+        return (int)js.size();
+    }
+};
+
+// ---------------------------------------------------------------------------
+// the learned form's student net (student.cu), as the codec uses it
+// ---------------------------------------------------------------------------
+
+}  // namespace lic
+struct lic_student;
+namespace lic {
+// latent channels M of the student
+int student_channels(const lic_student *s);
+// NHWC y_hat [B][Hy][Wy][M] -> NHWC [B][16Hy][16Wy][3], stream-ordered
+int student_forward_nhwc(lic_student *s, const float *yhat, int B, int Hy, int Wy, float *out, cudaStream_t st);
+// per-frame PSNR of clamp(xs) against clamp(xt) over the H x W crop of the
+// Hp x Wp NHWC frames; frames with PSNR >= thr get xs copied into xt;
+// counts[0] += B, counts[1] += frames below thr.  part: B * 64 doubles.
+void launch_student_check(const float *xs, float *xt, int B, int Hp, int Wp, int H, int W, float thr, double *part,
+                          float *psnr, int *pass, long long *counts, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
 // entropy tables (host build, tables.cpp)
 // ---------------------------------------------------------------------------
 
@@ -59,7 +216,9 @@ void scale_table(float T[64]);
 // ---------------------------------------------------------------------------
 
 enum InXform : int { IN_NONE = 0, IN_ABS = 1, IN_SQUARE = 2 };
-enum Epi : int { EPI_NONE = 0, EPI_RELU = 1, EPI_GDN = 2, EPI_IGDN = 3 };
+// EPI_MASK (CUDA-core kernel only): keep the sum where gdn_x (same layout
+// as the output) is positive, else 0 -- the ReLU's backward pass.
+enum Epi : int { EPI_NONE = 0, EPI_RELU = 1, EPI_GDN = 2, EPI_IGDN = 3, EPI_MASK = 4 };
 // Storage of an activation tensor: float32, bf16, or e4m3 holding x / scale.
 enum DType : int { DT_F32 = 0, DT_BF16 = 1, DT_E4M3 = 2 };
 

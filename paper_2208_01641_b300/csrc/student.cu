@@ -1,0 +1,828 @@
+// The learned form (include/lic_student.h): a distilled student synthesis
+// net -- four transposed convolutions 5x5 / stride 2, M -> C -> C -> C -> 3,
+// ReLU after the first three -- trained on the GPU against the teacher's g_s
+// (the decoder transform of the paper's Sec. III-A/B) and run by the
+// decoder in its place.
+//
+// Notation: h_0 = y_hat crop, z_l = deconv_l(h_l) (l = 0..3), h_{l+1} =
+// ReLU(z_l), out = z_3.  Loss L = mean((out - x)^2).  Backward pass, by the
+// chain rule: dz_3 = 2 (out - x) / n; for l = 3..0
+//   dW_l[i][o][u][v] = sum_{b,a,c} h_l[b,a,c,i] dz_l[b, 2a+u-2, 2c+v-2, o]
+//   db_l[o]          = sum over dz_l's positions of dz_l[., o]
+//   dz_{l-1}         = conv5x5/2(dz_l; W_l) * [h_l > 0]     (l > 0)
+// where conv5x5/2 with the transposed conv's own weight array is its
+// adjoint.  Then one Adam step (Kingma & Ba 2015, Algorithm 1).
+//
+// Layout: activations and gradients NHWC float32; the master weights keep
+// the transposed-conv layout [Cin][Cout][5][5] and are re-laid out after
+// every update into (a) the four sub-pixel phase matrices [Cout][T][Cin] of
+// the forward pass, (b) the conv matrix [Cin][25][Cout] of the input
+// gradient, (c) [Cin][25][4] for the 3-channel last layer.
+//
+// Every reduction has a fixed order (split-K partials summed in split
+// order), so results do not depend on timing.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/lic_student.h"
+#include "lic_internal.h"
+
+namespace lic {
+namespace {
+
+constexpr int NL = 4;
+// taps of sub-pixel phase ph = 2 py + px: (0,0) 9, (0,1) 6, (1,0) 6, (1,1) 4;
+// and the first tap of each phase in the forward matrices
+__host__ __device__ constexpr int ph_taps(int ph) { return ph == 0 ? 9 : (ph == 3 ? 4 : 6); }
+__host__ __device__ constexpr int ph_off(int ph) { return ph == 0 ? 0 : (ph == 1 ? 9 : (ph == 2 ? 15 : 21)); }
+
+struct Crops {
+    int n;
+    int f[LIC_STUDENT_MAX_BATCH], r[LIC_STUDENT_MAX_BATCH], c[LIC_STUDENT_MAX_BATCH];
+};
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// y_hat crops: pool NCHW [P][M][Hy][Wy] -> h0 NHWC [B][lc][lc][M]
+__global__ void gather_yhat_kernel(const float *__restrict__ pool, int M, int Hy, int Wy, Crops cr, int lc,
+                                   float *__restrict__ h0) {
+    const int64_t n = (int64_t)cr.n * lc * lc * M;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int ch = (int)(e % M);
+        int64_t pos = e / M;
+        const int c = (int)(pos % lc);
+        pos /= lc;
+        const int r = (int)(pos % lc);
+        const int b = (int)(pos / lc);
+        h0[e] = pool[(((int64_t)cr.f[b] * M + ch) * Hy + cr.r[b] + r) * Wy + cr.c[b] + c];
+    }
+}
+
+constexpr int RED_T = 256;
+
+// out NHWC [B][S][S][3] against the target crops of xpool NCHW
+// [P][3][Hx][Wx]: dz = (2/n) (out - x); per block the float64 sum of
+// (out - x)^2 over its pixels (fixed tree)
+__global__ void __launch_bounds__(RED_T) mse_grad_kernel(const float *__restrict__ out,
+                                                         const float *__restrict__ xpool, int Hx, int Wx, Crops cr,
+                                                         int S, float two_over_n, float *__restrict__ dz,
+                                                         double *__restrict__ part) {
+    __shared__ double red[RED_T];
+    const int64_t npix = (int64_t)cr.n * S * S;
+    double acc = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)RED_T + threadIdx.x; p < npix; p += (int64_t)gridDim.x * RED_T) {
+        const int x = (int)(p % S);
+        const int y = (int)((p / S) % S);
+        const int b = (int)(p / ((int64_t)S * S));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float t =
+                xpool[(((int64_t)cr.f[b] * 3 + k) * Hx + 16 * cr.r[b] + y) * Wx + 16 * cr.c[b] + x];
+            const float d = out[p * 3 + k] - t;
+            dz[p * 3 + k] = two_over_n * d;
+            acc += (double)d * (double)d;
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = RED_T / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// loss = (sum of the block partials, in block order) / n
+__global__ void __launch_bounds__(RED_T) mse_final_kernel(const double *__restrict__ part, int nblk, double n,
+                                                          float *__restrict__ loss) {
+    __shared__ double red[RED_T];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += RED_T) acc += part[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = RED_T / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = (float)(red[0] / n);
+}
+
+// per-channel sums of an NHWC tensor [P][C] (C <= RED_T): block z sums the
+// pixels [z*per, (z+1)*per) into part[z][C]
+__global__ void __launch_bounds__(RED_T) chan_sum_kernel(const float *__restrict__ x, int64_t P, int C, int64_t per,
+                                                         float *__restrict__ part) {
+    __shared__ float red[RED_T];
+    const int G = RED_T / C;          // pixel lanes
+    const int g = threadIdx.x / C, c = threadIdx.x % C;
+    float acc = 0.f;
+    if (g < G) {
+        const int64_t p0 = blockIdx.x * per, p1 = min(P, p0 + per);
+        for (int64_t p = p0 + g; p < p1; p += G) acc += x[p * C + c];
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float s = 0.f;
+        for (int q = 0; q < G; ++q) s += red[q * C + threadIdx.x];
+        part[(int64_t)blockIdx.x * C + threadIdx.x] = s;
+    }
+}
+
+// out[c] = sum over z of part[z][c], in z order
+__global__ void chan_sum_final_kernel(const float *__restrict__ part, int nz, int C, float *__restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (int z = 0; z < nz; ++z) s += part[(int64_t)z * C + c];
+    out[c] = s;
+}
+
+// Weight gradient of a transposed conv 5x5 / 2 as a GEMM: rows i (input
+// channel), columns n = tap * Cout + o, K = the B*H*W input pixels, split
+// over gridDim.z slices of kper pixels.  x: NHWC [B][H][W][Cin] (Cin % 4 == 0);
+// dz: NHWC [B][2H][2W][Cout].  part[z][Cin][25*Cout].
+constexpr int WG_BM = 64, WG_BN = 64, WG_BK = 16, WG_NT = 256;
+
+template <bool VEC>   // VEC: Cout % 64 == 0, one tap per column tile, float4 loads
+__global__ void __launch_bounds__(WG_NT) wgrad_kernel(const float *__restrict__ x, const float *__restrict__ dz, int B,
+                                                      int H, int W, int Cin, int Cout, int64_t kper,
+                                                      float *__restrict__ part) {
+    __shared__ __align__(16) float As[WG_BK][WG_BM];
+    __shared__ __align__(16) float Bs[WG_BK][WG_BN];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int i0 = blockIdx.y * WG_BM, n0 = blockIdx.x * WG_BN;
+    const int N = 25 * Cout;
+    const int64_t HW = (int64_t)H * W, P = (int64_t)B * HW;
+    const int64_t k_begin = blockIdx.z * kper, k_end = min(P, k_begin + kper);
+    const int Ho = 2 * H, Wo = 2 * W;
+    const int lp = tid / 16, lq = tid % 16;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+    for (int64_t k0 = k_begin; k0 < k_end; k0 += WG_BK) {
+        const int64_t p = k0 + lp;
+        const bool pv = p < k_end;
+        int b = 0, a = 0, c = 0;
+        if (pv) {
+            b = (int)(p / HW);
+            const int rem = (int)(p % HW);
+            a = rem / W;
+            c = rem % W;
+        }
+        float4 va = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (pv && i0 + 4 * lq < Cin) va = *reinterpret_cast<const float4 *>(x + p * Cin + i0 + 4 * lq);
+        *reinterpret_cast<float4 *>(&As[lp][4 * lq]) = va;
+        if (VEC) {
+            const int tap = n0 / Cout, o0 = n0 % Cout;
+            const int yo = 2 * a + tap / 5 - 2, xo = 2 * c + tap % 5 - 2;
+            float4 vb = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (pv && yo >= 0 && yo < Ho && xo >= 0 && xo < Wo)
+                vb = *reinterpret_cast<const float4 *>(dz + (((int64_t)b * Ho + yo) * Wo + xo) * Cout + o0 + 4 * lq);
+            *reinterpret_cast<float4 *>(&Bs[lp][4 * lq]) = vb;
+        } else {
+#pragma unroll
+            for (int r = 0; r < (WG_BK * WG_BN) / WG_NT; ++r) {
+                const int e = tid + r * WG_NT;
+                const int kk = e / WG_BN, nn = e % WG_BN;
+                const int64_t pp = k0 + kk;
+                const int n = n0 + nn;
+                float vb = 0.f;
+                if (pp < k_end && n < N) {
+                    const int tap = n / Cout, o = n % Cout;
+                    const int bb = (int)(pp / HW);
+                    const int rem = (int)(pp % HW);
+                    const int yo = 2 * (rem / W) + tap / 5 - 2, xo = 2 * (rem % W) + tap % 5 - 2;
+                    if (yo >= 0 && yo < Ho && xo >= 0 && xo < Wo) vb = dz[(((int64_t)bb * Ho + yo) * Wo + xo) * Cout + o];
+                }
+                Bs[kk][nn] = vb;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < WG_BK; ++kk) {
+            const float4 av = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int ii = i0 + ty * 4 + i;
+        if (ii >= Cin) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx * 4 + j;
+            if (n < N) part[((int64_t)blockIdx.z * Cin + ii) * N + n] = acc[i][j];
+        }
+    }
+}
+
+// dW[i][o][u][v] = sum over z (in order) of part[z][i][(u*5+v)*Cout + o]
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int nz, int Cin, int Cout, float *__restrict__ dw) {
+    const int N = 25 * Cout;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)Cin * N) return;
+    const int i = (int)(e / N), n = (int)(e % N);
+    float s = 0.f;
+    for (int z = 0; z < nz; ++z) s += part[((int64_t)z * Cin + i) * N + n];
+    dw[((int64_t)i * Cout + n % Cout) * 25 + n / Cout] = s;
+}
+
+// Adam over the flat parameter vector; c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+__global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ g, int64_t n, float lr, float b1, float b2, float c1, float c2,
+                            float eps) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+struct RepackArgs {
+    const float *w[NL];
+    float *wf[NL];   // forward phase matrices (layers with > 4 outputs) or null
+    float *wd[NL];   // input-gradient conv matrix (layers 1..3) or null
+    float *ws;       // last layer [Cin][25][4]
+    int cin[NL], cout[NL];
+    int64_t start[NL + 1];
+};
+
+// master [Cin][Cout][5][5] -> the layouts the kernels read.  Output row
+// Y = 2m + py takes tap u of input row m + (py + 2 - u)/2 when u = py mod 2:
+// phase (u & 1, v & 1), tap index (u >> 1) * (3 or 2) + (v >> 1).
+__global__ void repack_kernel(RepackArgs a) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= a.start[NL]) return;
+    int l = 0;
+    while (l < NL - 1 && idx >= a.start[l + 1]) ++l;
+    const int64_t e = idx - a.start[l];
+    const int Cin = a.cin[l], Cout = a.cout[l];
+    const int v = (int)(e % 5), u = (int)((e / 5) % 5);
+    const int o = (int)((e / 25) % Cout);
+    const int i = (int)(e / (25 * (int64_t)Cout));
+    const float wv = a.w[l][e];
+    if (a.wf[l]) {
+        const int ph = (u & 1) * 2 + (v & 1);
+        const int t = (u >> 1) * ((v & 1) ? 2 : 3) + (v >> 1);
+        a.wf[l][(int64_t)ph_off(ph) * Cout * Cin + ((int64_t)o * ph_taps(ph) + t) * Cin + i] = wv;
+    }
+    if (a.wd[l]) a.wd[l][((int64_t)i * 25 + u * 5 + v) * Cout + o] = wv;
+    if (l == NL - 1 && a.ws) a.ws[((int64_t)i * 25 + u * 5 + v) * 4 + o] = wv;
+}
+
+// per frame: float64 sum over its H x W x 3 cropped values of
+// (clamp(xs) - clamp(xt))^2; grid (blocks, B); part[b][block]
+__global__ void __launch_bounds__(RED_T) frame_sse_kernel(const float *__restrict__ xs, const float *__restrict__ xt,
+                                                          int Hp, int Wp, int H, int W, double *__restrict__ part) {
+    __shared__ double red[RED_T];
+    const int b = blockIdx.y;
+    const int64_t n = (int64_t)H * W;
+    double acc = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)RED_T + threadIdx.x; p < n; p += (int64_t)gridDim.x * RED_T) {
+        const int y = (int)(p / W), x = (int)(p % W);
+        const int64_t q = (((int64_t)b * Hp + y) * Wp + x) * 3;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float d = fminf(fmaxf(xs[q + k], 0.f), 1.f) - fminf(fmaxf(xt[q + k], 0.f), 1.f);
+            acc += (double)d * (double)d;
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = RED_T / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)b * gridDim.x + blockIdx.x] = red[0];
+}
+
+// per frame PSNR = 10 log10(1 / mse); pass[b] = PSNR >= thr; the counters
+// (frames, fallbacks) advance
+__global__ void frame_psnr_kernel(const double *__restrict__ part, int nblk, int B, double n, float thr,
+                                  float *__restrict__ psnr, int *__restrict__ pass, long long *__restrict__ counts) {
+    const int b = threadIdx.x;
+    bool fail = false;
+    if (b < B) {
+        double s = 0.0;
+        for (int i = 0; i < nblk; ++i) s += part[(int64_t)b * nblk + i];
+        const double mse = s / n;
+        const float q = mse > 0.0 ? (float)(10.0 * log10(1.0 / mse)) : INFINITY;
+        psnr[b] = q;
+        pass[b] = q >= thr;
+        fail = !(q >= thr);
+    }
+    const int nfail = __syncthreads_count(fail);
+    if (b == 0) {
+        counts[0] += B;
+        counts[1] += nfail;
+    }
+}
+
+// frames that passed take the student's output
+__global__ void frame_select_kernel(const float *__restrict__ xs, float *__restrict__ xt, int64_t per_frame, int B,
+                                    const int *__restrict__ pass) {
+    const int64_t n = per_frame * B;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        if (pass[e / per_frame]) xt[e] = xs[e];
+}
+
+int grid_for(int64_t n, int t) { return (int)std::min<int64_t>((n + t - 1) / t, 148 * 16); }
+
+}  // namespace
+}  // namespace lic
+
+struct lic_student {
+    int M = 0, C = 0;
+    lic_student_options opt{};
+    int device = 0;
+    int cin[4] = {}, cout[4] = {};
+    int64_t woff[4] = {}, boff[4] = {}, nparam = 0;
+    lic::DevBuf param, grad, adam_m, adam_v;
+    lic::DevBuf wf[4], wd[4], ws;
+    // training workspace (max_batch crops)
+    lic::DevBuf h[4], out, dz[4], part, lpart, loss, bpart, status;
+    // inference workspace
+    lic::DevBuf ih[4], iout;
+    int64_t t = 0;
+    int last_B = 0;
+    lic::Profiler pf;
+};
+
+namespace lic {
+namespace {
+
+int64_t wsize(const lic_student *s, int l) { return (int64_t)s->cin[l] * s->cout[l] * 25; }
+
+template <typename F>
+void timed(lic_student *s, const std::string &name, double flop, double bytes, int n, cudaStream_t st, F &&f) {
+    s->pf.run(name, flop, bytes, n, st, f);
+}
+
+int repack(lic_student *s, cudaStream_t st) {
+    RepackArgs a{};
+    a.start[0] = 0;
+    for (int l = 0; l < NL; ++l) {
+        a.w[l] = s->param.as<float>() + s->woff[l];
+        a.wf[l] = s->wf[l].as<float>();
+        a.wd[l] = s->wd[l].as<float>();
+        a.cin[l] = s->cin[l];
+        a.cout[l] = s->cout[l];
+        a.start[l + 1] = a.start[l] + wsize(s, l);
+    }
+    a.ws = s->ws.as<float>();
+    const int64_t n = a.start[NL];
+    timed(s, "student.repack", 0, 12.0 * n, 1, st,
+          [&] { repack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a); });
+    LIC_CUDA_TRY(cudaGetLastError());
+    return LIC_OK;
+}
+
+// one transposed conv (l < 3: four phase launches + ReLU; l == 3: the
+// small-Cout kernel) from h (NHWC, Hi x Wi) into out
+void forward_layer(lic_student *s, int l, const float *in, int B, int Hi, int Wi, float *out, cudaStream_t st) {
+    const int Cin = s->cin[l], Cout = s->cout[l];
+    const double flop = 2.0 * B * Hi * Wi * (double)Cin * Cout * 25;
+    const double bytes = 4.0 * ((double)B * Hi * Wi * Cin + 4.0 * B * Hi * Wi * Cout + wsize(s, l));
+    const float *bias = s->param.as<float>() + s->boff[l];
+    if (l == NL - 1) {
+        timed(s, "student.deconv3", flop, bytes, 1, st,
+              [&] { launch_deconv_small(in, B, Hi, Wi, Cin, s->ws.as<float>(), bias, Cout, out, st); });
+        return;
+    }
+    timed(s, "student.deconv" + std::to_string(l), flop, bytes, 4, st, [&] {
+        for (int ph = 0; ph < 4; ++ph) {
+            const int py = ph >> 1, px = ph & 1;
+            ConvDesc d{};
+            d.in = in;
+            d.out = out;
+            d.w = s->wf[l].as<float>() + (int64_t)ph_off(ph) * Cout * Cin;
+            d.bias = bias;
+            d.status = s->status.as<uint32_t>();
+            d.B = B;
+            d.Hi = Hi;
+            d.Wi = Wi;
+            d.Cin = Cin;
+            d.Gh = Hi;
+            d.Gw = Wi;
+            d.s = 1;
+            d.Ho = 2 * Hi;
+            d.Wo = 2 * Wi;
+            d.Cout = Cout;
+            d.oym = 2;
+            d.oyo = py;
+            d.oxm = 2;
+            d.oxo = px;
+            int t = 0;
+            for (int u = py; u < 5; u += 2)
+                for (int v = px; v < 5; v += 2) {
+                    d.du[t] = (int8_t)((py + 2 - u) / 2);
+                    d.dv[t] = (int8_t)((px + 2 - v) / 2);
+                    ++t;
+                }
+            d.T = t;
+            d.in_xform = IN_NONE;
+            d.epi = EPI_RELU;
+            d.in_dt = d.out_dt = DT_F32;
+            d.in_scale = d.out_scale = 1.f;
+            launch_conv_simt(d, st);
+        }
+    });
+}
+
+// the student on NHWC y_hat [B][Hy][Wy][M] into NHWC out [B][16Hy][16Wy][3],
+// activations in hbuf[1..3]
+void forward_all(lic_student *s, const float *h0, int B, int Hy, int Wy, DevBuf *hbuf, float *out, cudaStream_t st) {
+    const float *in = h0;
+    int H = Hy, W = Wy;
+    for (int l = 0; l < NL; ++l) {
+        float *o = l < NL - 1 ? hbuf[l + 1].as<float>() : out;
+        forward_layer(s, l, in, B, H, W, o, st);
+        in = o;
+        H *= 2;
+        W *= 2;
+    }
+}
+
+int ensure_f(DevBuf &b, int64_t n) {
+    LIC_CUDA_TRY(b.ensure((size_t)std::max<int64_t>(n, 1) * sizeof(float)));
+    return LIC_OK;
+}
+
+int check_crops(const lic_student *s, const float *yp, const float *xp, int P, int Hy, int Wy, const int32_t *crops,
+                int B, Crops *cr) {
+    const int lc = s->opt.crop / 16;
+    if (!yp || !xp || !crops || P < 1 || B < 1 || B > s->opt.max_batch || Hy < lc || Wy < lc) return LIC_E_INVALID_ARG;
+    if (!is_device_ptr(yp) || !is_device_ptr(xp)) return LIC_E_INVALID_ARG;
+    cr->n = B;
+    for (int b = 0; b < B; ++b) {
+        const int f = crops[3 * b], r = crops[3 * b + 1], c = crops[3 * b + 2];
+        if (f < 0 || f >= P || r < 0 || c < 0 || r + lc > Hy || c + lc > Wy) return LIC_E_INVALID_ARG;
+        cr->f[b] = f;
+        cr->r[b] = r;
+        cr->c[b] = c;
+    }
+    return LIC_OK;
+}
+
+// forward, loss and every gradient of one batch
+int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, int Wy, const int32_t *crops, int B,
+              cudaStream_t st) {
+    Crops cr{};
+    int rc = check_crops(s, yp, xp, P, Hy, Wy, crops, B, &cr);
+    if (rc) return rc;
+    s->last_B = B;
+    const int S = s->opt.crop, lc = S / 16, M = s->M;
+    // gather
+    const int64_t ny = (int64_t)B * lc * lc * M;
+    timed(s, "student.gather", 0, 8.0 * ny, 1, st, [&] {
+        gather_yhat_kernel<<<grid_for(ny, 256), 256, 0, st>>>(yp, M, Hy, Wy, cr, lc, s->h[0].as<float>());
+    });
+    // forward
+    forward_all(s, s->h[0].as<float>(), B, lc, lc, s->h, s->out.as<float>(), st);
+    // loss and dz_3
+    const int64_t npix = (int64_t)B * S * S;
+    const int nblk = grid_for(npix, RED_T);
+    const double n = 3.0 * npix;
+    timed(s, "student.mse", 3.0 * n, 12.0 * n, 2, st, [&] {
+        mse_grad_kernel<<<nblk, RED_T, 0, st>>>(s->out.as<float>(), xp, 16 * Hy, 16 * Wy, cr, S, (float)(2.0 / n),
+                                                s->dz[3].as<float>(), s->lpart.as<double>());
+        mse_final_kernel<<<1, RED_T, 0, st>>>(s->lpart.as<double>(), nblk, n, s->loss.as<float>());
+    });
+    // backward, l = 3 .. 0
+    int H = S / 2;   // h_3 resolution
+    for (int l = NL - 1; l >= 0; --l) {
+        const int Cin = s->cin[l], Cout = s->cout[l];
+        const float *hl = s->h[l].as<float>();
+        const float *dzl = s->dz[l].as<float>();
+        const int64_t P_in = (int64_t)B * H * H;      // pixels of h_l
+        const int64_t P_out = 4 * P_in;               // pixels of dz_l
+        // bias gradient
+        {
+            const int64_t per = 4096;
+            const int nz = (int)((P_out + per - 1) / per);
+            timed(s, "student.bgrad" + std::to_string(l), (double)P_out * Cout, 4.0 * P_out * Cout, 2, st, [&] {
+                chan_sum_kernel<<<nz, RED_T, 0, st>>>(dzl, P_out, Cout, per, s->bpart.as<float>());
+                chan_sum_final_kernel<<<1, 256, 0, st>>>(s->bpart.as<float>(), nz, Cout,
+                                                         s->grad.as<float>() + s->boff[l]);
+            });
+        }
+        // weight gradient: split K so that the grid covers the SMs a few times
+        {
+            const int N = 25 * Cout;
+            const int tn = (N + WG_BN - 1) / WG_BN, tm = (Cin + WG_BM - 1) / WG_BM;
+            int64_t splits = std::max<int64_t>(1, (4 * 148) / (tn * tm));
+            int64_t kper = (P_in + splits - 1) / splits;
+            kper = std::max<int64_t>(WG_BK, (kper + WG_BK - 1) / WG_BK * WG_BK);
+            splits = (P_in + kper - 1) / kper;
+            const double flop = 2.0 * P_in * (double)Cin * Cout * 25;
+            const double bytes = 4.0 * (P_in * (double)Cin + P_out * (double)Cout + wsize(s, l));
+            timed(s, "student.wgrad" + std::to_string(l), flop, bytes, 2, st, [&] {
+                dim3 grid(tn, tm, (unsigned)splits);
+                if (Cout % WG_BN == 0)
+                    wgrad_kernel<true><<<grid, WG_NT, 0, st>>>(hl, dzl, B, H, H, Cin, Cout, kper, s->part.as<float>());
+                else
+                    wgrad_kernel<false><<<grid, WG_NT, 0, st>>>(hl, dzl, B, H, H, Cin, Cout, kper, s->part.as<float>());
+                const int64_t ne = (int64_t)Cin * N;
+                wgrad_reduce_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+                    s->part.as<float>(), (int)splits, Cin, Cout, s->grad.as<float>() + s->woff[l]);
+            });
+        }
+        // input gradient through the ReLU: dz_{l-1} = conv5x5/2(dz_l; W_l) * [h_l > 0]
+        if (l > 0) {
+            const double flop = 2.0 * P_in * (double)Cin * Cout * 25;
+            const double bytes = 4.0 * (P_out * (double)Cout + 2.0 * P_in * Cin + wsize(s, l));
+            timed(s, "student.dgrad" + std::to_string(l), flop, bytes, 1, st, [&] {
+                ConvDesc d{};
+                d.in = dzl;
+                d.out = s->dz[l - 1].as<float>();
+                d.w = s->wd[l].as<float>();
+                d.bias = nullptr;
+                d.gdn_x = hl;
+                d.status = s->status.as<uint32_t>();
+                d.B = B;
+                d.Hi = 2 * H;
+                d.Wi = 2 * H;
+                d.Cin = Cout;
+                d.Gh = H;
+                d.Gw = H;
+                d.s = 2;
+                d.Ho = H;
+                d.Wo = H;
+                d.Cout = Cin;
+                d.oym = 1;
+                d.oxm = 1;
+                d.T = 25;
+                for (int u = 0; u < 5; ++u)
+                    for (int v = 0; v < 5; ++v) {
+                        d.du[u * 5 + v] = (int8_t)(u - 2);
+                        d.dv[u * 5 + v] = (int8_t)(v - 2);
+                    }
+                d.in_xform = IN_NONE;
+                d.epi = EPI_MASK;
+                d.in_dt = d.out_dt = DT_F32;
+                d.in_scale = d.out_scale = 1.f;
+                launch_conv_simt(d, st);
+            });
+        }
+        H /= 2;
+    }
+    LIC_CUDA_TRY(cudaGetLastError());
+    return LIC_OK;
+}
+
+int read_loss(lic_student *s, float *loss, cudaStream_t st) {
+    if (!loss) return LIC_OK;
+    LIC_CUDA_TRY(cudaMemcpyAsync(loss, s->loss.p, sizeof(float), cudaMemcpyDeviceToHost, st));
+    LIC_CUDA_TRY(cudaStreamSynchronize(st));
+    return LIC_OK;
+}
+
+cudaStream_t SS(void *p) { return static_cast<cudaStream_t>(p); }
+
+}  // namespace
+
+// used by the codec (api.cu)
+int student_channels(const lic_student *s) { return s ? s->M : 0; }
+
+int student_forward_nhwc(lic_student *s, const float *yhat, int B, int Hy, int Wy, float *out, cudaStream_t st) {
+    const int64_t p1 = (int64_t)B * 2 * Hy * 2 * Wy;
+    int rc;
+    if ((rc = ensure_f(s->ih[1], p1 * s->C)) || (rc = ensure_f(s->ih[2], 4 * p1 * s->C)) ||
+        (rc = ensure_f(s->ih[3], 16 * p1 * s->C)))
+        return rc;
+    forward_all(s, yhat, B, Hy, Wy, s->ih, out, st);
+    LIC_CUDA_TRY(cudaGetLastError());
+    return LIC_OK;
+}
+
+void launch_student_check(const float *xs, float *xt, int B, int Hp, int Wp, int H, int W, float thr, double *part,
+                          float *psnr, int *pass, long long *counts, cudaStream_t st) {
+    const int nblk = 64;
+    frame_sse_kernel<<<dim3(nblk, B), RED_T, 0, st>>>(xs, xt, Hp, Wp, H, W, part);
+    frame_psnr_kernel<<<1, ((B + 31) / 32) * 32, 0, st>>>(part, nblk, B, 3.0 * H * W, thr, psnr, pass, counts);
+    const int64_t per = (int64_t)Hp * Wp * 3;
+    frame_select_kernel<<<grid_for(per * B, 256), 256, 0, st>>>(xs, xt, per, B, pass);
+}
+
+}  // namespace lic
+
+using namespace lic;
+
+int lic_student_create(const lic_weights *init, int M, int C, const lic_student_options *opt, lic_student **out) {
+    if (!init || !opt || !out || M < 16 || C < 16 || M % 16 || C % 16 || C > RED_T) return LIC_E_INVALID_ARG;
+    *out = nullptr;
+    if (opt->precision != LIC_FP32 || opt->max_batch < 1 || opt->max_batch > LIC_STUDENT_MAX_BATCH ||
+        opt->crop < 32 || opt->crop % 16 || !(opt->lr > 0.f) || !(opt->beta1 >= 0.f && opt->beta1 < 1.f) ||
+        !(opt->beta2 >= 0.f && opt->beta2 < 1.f) || !(opt->eps > 0.f))
+        return LIC_E_INVALID_ARG;
+    for (int r : opt->reserved)
+        if (r) return LIC_E_INVALID_ARG;
+    auto s = new (std::nothrow) lic_student();
+    if (!s) return LIC_E_OOM;
+    s->M = M;
+    s->C = C;
+    s->opt = *opt;
+    cudaGetDevice(&s->device);
+    const int ch[5] = {M, C, C, C, 3};
+    std::vector<float> host;
+    for (int l = 0; l < NL; ++l) {
+        s->cin[l] = ch[l];
+        s->cout[l] = ch[l + 1];
+        s->woff[l] = s->nparam;
+        s->nparam += wsize(s, l);
+        s->boff[l] = s->nparam;
+        s->nparam += s->cout[l];
+    }
+    host.assign((size_t)s->nparam, 0.f);
+    auto fail = [&](int rc) {
+        delete s;
+        return rc;
+    };
+    for (int l = 0; l < NL; ++l) {
+        const std::string base = "student.deconv" + std::to_string(l);
+        for (int which = 0; which < 2; ++which) {
+            const std::string name = base + (which ? ".bias" : ".weight");
+            const int64_t want = which ? s->cout[l] : wsize(s, l);
+            const float *src = nullptr;
+            for (int i = 0; i < init->count; ++i)
+                if (init->params[i].name && name == init->params[i].name) {
+                    if (init->params[i].numel != want || !init->params[i].data) return fail(LIC_E_INVALID_ARG);
+                    src = init->params[i].data;
+                }
+            if (!src) return fail(LIC_E_INVALID_ARG);
+            memcpy(host.data() + (which ? s->boff[l] : s->woff[l]), src, (size_t)want * sizeof(float));
+        }
+    }
+    auto alloc = [&](DevBuf &b, int64_t n) { return ensure_f(b, n); };
+    int rc;
+    const int64_t np = s->nparam;
+    if ((rc = alloc(s->param, np)) || (rc = alloc(s->grad, np)) || (rc = alloc(s->adam_m, np)) ||
+        (rc = alloc(s->adam_v, np)))
+        return fail(rc);
+    if (cudaMemcpy(s->param.p, host.data(), np * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(s->grad.p, 0, np * sizeof(float)) != cudaSuccess ||
+        cudaMemset(s->adam_m.p, 0, np * sizeof(float)) != cudaSuccess ||
+        cudaMemset(s->adam_v.p, 0, np * sizeof(float)) != cudaSuccess)
+        return fail(LIC_E_CUDA);
+    for (int l = 0; l < NL - 1; ++l)
+        if ((rc = alloc(s->wf[l], wsize(s, l)))) return fail(rc);
+    for (int l = 1; l < NL; ++l)
+        if ((rc = alloc(s->wd[l], wsize(s, l)))) return fail(rc);
+    if ((rc = alloc(s->ws, (int64_t)s->cin[3] * 25 * 4))) return fail(rc);
+    if (cudaMemset(s->ws.p, 0, s->ws.bytes) != cudaSuccess) return fail(LIC_E_CUDA);
+    // training workspace
+    const int Bm = opt->max_batch, S = opt->crop;
+    int64_t side = S / 16;
+    if ((rc = alloc(s->h[0], Bm * side * side * M))) return fail(rc);
+    for (int l = 1; l < NL; ++l) {
+        side *= 2;
+        if ((rc = alloc(s->h[l], Bm * side * side * C))) return fail(rc);
+    }
+    side = S / 16;
+    int64_t part_max = 0;
+    for (int l = 0; l < NL; ++l) {
+        side *= 2;   // dz_l lives at layer l's output resolution
+        if ((rc = alloc(s->dz[l], Bm * side * side * s->cout[l]))) return fail(rc);
+        const int N = 25 * s->cout[l];
+        const int tiles = ((N + WG_BN - 1) / WG_BN) * ((s->cin[l] + WG_BM - 1) / WG_BM);
+        const int64_t P_in = Bm * (side / 2) * (side / 2);
+        const int64_t splits = std::min<int64_t>(std::max<int64_t>(1, (4 * 148) / tiles), (P_in + WG_BK - 1) / WG_BK);
+        part_max = std::max<int64_t>(part_max, (splits + 1) * (int64_t)s->cin[l] * N);
+    }
+    if ((rc = alloc(s->out, (int64_t)Bm * S * S * 3)) || (rc = alloc(s->part, part_max)) ||
+        (rc = alloc(s->bpart, ((int64_t)Bm * S * S + 4095) / 4096 * RED_T + RED_T)) ||
+        (rc = alloc(s->loss, 1)))
+        return fail(rc);
+    if (s->lpart.ensure(sizeof(double) * 148 * 16) != cudaSuccess || s->status.ensure(16) != cudaSuccess)
+        return fail(LIC_E_OOM);
+    cudaMemset(s->status.p, 0, 16);
+    if ((rc = repack(s, 0))) return fail(rc);
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(LIC_E_CUDA);
+    *out = s;
+    return LIC_OK;
+}
+
+void lic_student_destroy(lic_student *s) {
+    if (!s) return;
+    cudaDeviceSynchronize();
+    delete s;
+}
+
+int lic_student_grad(lic_student *s, const float *yp, const float *xp, int P, int Hy, int Wy, const int32_t *crops,
+                     int B, float *loss, void *stream) {
+    if (!s) return LIC_E_INVALID_ARG;
+    cudaStream_t st = SS(stream);
+    int rc = grad_pass(s, yp, xp, P, Hy, Wy, crops, B, st);
+    if (rc) return rc;
+    return read_loss(s, loss, st);
+}
+
+int lic_student_step(lic_student *s, const float *yp, const float *xp, int P, int Hy, int Wy, const int32_t *crops,
+                     int B, float *loss, void *stream) {
+    if (!s) return LIC_E_INVALID_ARG;
+    cudaStream_t st = SS(stream);
+    int rc = grad_pass(s, yp, xp, P, Hy, Wy, crops, B, st);
+    if (rc) return rc;
+    s->t += 1;
+    const double b1 = s->opt.beta1, b2 = s->opt.beta2;
+    const float c1 = (float)(1.0 / (1.0 - std::pow(b1, (double)s->t)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)s->t)));
+    const int64_t n = s->nparam;
+    timed(s, "student.adam", 12.0 * n, 28.0 * n, 1, st, [&] {
+        adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->param.as<float>(), s->adam_m.as<float>(),
+                                                                 s->adam_v.as<float>(), s->grad.as<float>(), n,
+                                                                 s->opt.lr, s->opt.beta1, s->opt.beta2, c1, c2,
+                                                                 s->opt.eps);
+    });
+    LIC_CUDA_TRY(cudaGetLastError());
+    if ((rc = repack(s, st))) return rc;
+    return read_loss(s, loss, st);
+}
+
+int lic_student_read(lic_student *s, const char *name, int what, float *dst, int64_t numel) {
+    if (!s || !name || !dst || what < 0 || what > 3) return LIC_E_INVALID_ARG;
+    const DevBuf *src[4] = {&s->param, &s->grad, &s->adam_m, &s->adam_v};
+    for (int l = 0; l < NL; ++l) {
+        const std::string base = "student.deconv" + std::to_string(l);
+        int64_t off = -1, n = 0;
+        if (base + ".weight" == name) {
+            off = s->woff[l];
+            n = wsize(s, l);
+        } else if (base + ".bias" == name) {
+            off = s->boff[l];
+            n = s->cout[l];
+        }
+        if (off < 0) continue;
+        if (n != numel) return LIC_E_INVALID_ARG;
+        LIC_CUDA_TRY(cudaDeviceSynchronize());
+        LIC_CUDA_TRY(cudaMemcpy(dst, src[what]->as<float>() + off, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
+        return LIC_OK;
+    }
+    return LIC_E_INVALID_ARG;
+}
+
+int lic_student_read_activation(lic_student *s, int layer, float *dst, int64_t numel) {
+    if (!s || !dst || layer < 1 || layer > 3 || s->last_B < 1) return LIC_E_INVALID_ARG;
+    const int64_t side = (int64_t)(s->opt.crop >> (4 - layer));
+    if (numel != (int64_t)s->last_B * side * side * s->C) return LIC_E_INVALID_ARG;
+    LIC_CUDA_TRY(cudaDeviceSynchronize());
+    LIC_CUDA_TRY(cudaMemcpy(dst, s->h[layer].p, (size_t)numel * sizeof(float), cudaMemcpyDeviceToHost));
+    return LIC_OK;
+}
+
+int64_t lic_student_steps(const lic_student *s) { return s ? s->t : LIC_E_INVALID_ARG; }
+
+int lic_student_forward(lic_student *s, const float *yhat, int B, int Hy, int Wy, float *x, void *stream) {
+    if (!s || !yhat || !x || B < 1 || Hy < 1 || Wy < 1) return LIC_E_INVALID_ARG;
+    cudaStream_t st = SS(stream);
+    const int64_t ny = (int64_t)B * s->M * Hy * Wy, nx = (int64_t)B * 3 * 256 * Hy * Wy;
+    int rc;
+    if ((rc = ensure_f(s->ih[0], ny)) || (rc = ensure_f(s->iout, 2 * nx))) return rc;
+    const bool dy = is_device_ptr(yhat), dx = is_device_ptr(x);
+    const float *ysrc = yhat;
+    float *stage = s->iout.as<float>() + nx;   // NCHW staging next to the NHWC output
+    if (!dy) {
+        LIC_CUDA_TRY(cudaMemcpyAsync(stage, yhat, (size_t)ny * sizeof(float), cudaMemcpyHostToDevice, st));
+        ysrc = stage;
+    }
+    timed(s, "student.nchw_to_nhwc", 0, 8.0 * ny, 1, st,
+          [&] { launch_nchw_to_nhwc(ysrc, B, s->M, Hy, Wy, s->ih[0].as<float>(), st); });
+    if ((rc = student_forward_nhwc(s, s->ih[0].as<float>(), B, Hy, Wy, s->iout.as<float>(), st))) return rc;
+    float *dst = dx ? x : stage;
+    timed(s, "student.nhwc_to_nchw", 0, 8.0 * nx, 1, st,
+          [&] { launch_nhwc_to_nchw(s->iout.as<float>(), B, 16 * Hy, 16 * Wy, 3, dst, st); });
+    if (!dx) {
+        LIC_CUDA_TRY(cudaMemcpyAsync(x, stage, (size_t)nx * sizeof(float), cudaMemcpyDeviceToHost, st));
+        LIC_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    LIC_CUDA_TRY(cudaGetLastError());
+    return LIC_OK;
+}
+
+int lic_student_profile_enable(lic_student *s, int enable) {
+    if (!s) return LIC_E_INVALID_ARG;
+    s->pf.enable(enable != 0);
+    return LIC_OK;
+}
+
+int lic_student_profile_report(lic_student *s, char *buf, int cap) {
+    return s ? s->pf.report(buf, cap) : LIC_E_INVALID_ARG;
+}
+
+int64_t lic_student_launch_count(const lic_student *s) { return s ? s->pf.launches : LIC_E_INVALID_ARG; }

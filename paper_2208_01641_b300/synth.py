@@ -261,3 +261,49 @@ def make_frame(index: int, H: int, W: int) -> np.ndarray:
 def make_frames(B: int, H: int, W: int, first: int = 0) -> np.ndarray:
     """B seeded frames stacked as a B x 3 x H x W float32 array."""
     return np.stack([make_frame(first + i, H, W) for i in range(B)])
+
+
+# --------------------------------------------------------------------------
+# Distilled student synthesis net (learned form)
+# --------------------------------------------------------------------------
+
+STUDENT_SEED = 4321
+CROP_SEED = 7777
+
+
+def student_param_names():
+    return [f"student.deconv{l}.{leaf}" for l in range(4) for leaf in ("weight", "bias")]
+
+
+def make_student_weights(M: int = 192, C: int = 64) -> "OrderedDict[str, np.ndarray]":
+    """Initial parameters of the student g_s: 4 transposed convs 5x5 / 2,
+    M -> C -> C -> C -> 3, weights [Cin, Cout, 5, 5].  Same Kaiming-uniform
+    recipe as the codec (fan_in = Cin*25); the last layer takes the codec's
+    g_s.deconv3 gain (0.25) and bias offset (0.5) so the initial output sits
+    inside [0, 1].  Parameter j draws from SplitMix64 stream (4321 << 20) + j."""
+    chans = (M, C, C, C, 3)
+    out: "OrderedDict[str, np.ndarray]" = OrderedDict()
+    for j, pname in enumerate(student_param_names()):
+        l = int(pname.split(".")[1][len("deconv"):])
+        cin, cout = chans[l], chans[l + 1]
+        fan_in = cin * 25
+        u = uniform01((STUDENT_SEED << 20) + j, cin * cout * 25 if pname.endswith("weight") else cout)
+        if pname.endswith("weight"):
+            bound = (0.25 if l == 3 else 1.0) * math.sqrt(6.0 / fan_in)
+            arr = ((2.0 * u - 1.0) * bound).reshape(cin, cout, 5, 5)
+        else:
+            arr = (2.0 * u - 1.0) / math.sqrt(fan_in) + (0.5 if l == 3 else 0.0)
+        out[pname] = np.ascontiguousarray(arr, dtype=np.float32)
+    return out
+
+
+def draw_crops(step: int, B: int, P: int, Hy: int, Wy: int, lc: int) -> np.ndarray:
+    """Crop positions of training step ``step``: B rows of (frame, row, col)
+    in latent units, frame uniform over the P pool frames and the lc x lc
+    latent window uniform over the Hy x Wy latent plane.  SplitMix64 stream
+    (7777 << 20) + step."""
+    u = uniform01((CROP_SEED << 20) + step, 3 * B).reshape(B, 3)
+    f = np.minimum((u[:, 0] * P).astype(np.int64), P - 1)
+    r = np.minimum((u[:, 1] * (Hy - lc + 1)).astype(np.int64), Hy - lc)
+    c = np.minimum((u[:, 2] * (Wy - lc + 1)).astype(np.int64), Wy - lc)
+    return np.ascontiguousarray(np.stack([f, r, c], axis=1), dtype=np.int32)

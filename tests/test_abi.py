@@ -73,3 +73,24 @@ def test_decoded_shape_reads_oracle_container():
     assert lic.decoded_shape(buf) == (1, 721, 1279)
     with pytest.raises(lic.LicError):
         lic.decoded_shape(b"XXXX" + buf[4:])
+
+
+def test_student_create_validates_arguments_before_device_work():
+    """lic_student_create refuses bad options and missing or mis-sized
+    parameters with LIC_E_INVALID_ARG (no device needed to reach the check)."""
+    W = synth.make_student_weights()
+    bad_opts = (dict(max_batch=0), dict(max_batch=lic.STUDENT_MAX_BATCH + 1), dict(crop=40), dict(crop=16),
+                dict(lr=0.0), dict(beta1=1.0), dict(eps=0.0), dict(precision=lic.BF16))
+    for kw in bad_opts:
+        with pytest.raises(lic.LicError) as e:
+            lic.Student(W, **kw)
+        assert e.value.code == lic.E_INVALID_ARG, kw
+    missing = {k: v for k, v in W.items() if k != "student.deconv2.bias"}
+    wrong = dict(W)
+    wrong["student.deconv1.weight"] = W["student.deconv1.weight"][:32]
+    for w in (missing, wrong):
+        with pytest.raises(lic.LicError) as e:
+            lic.Student(w)
+        assert e.value.code == lic.E_INVALID_ARG
+    with pytest.raises(lic.LicError):
+        lic.Student(W, M=100)

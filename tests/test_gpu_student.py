@@ -1,0 +1,188 @@
+"""The learned form's student synthesis net through the C ABI
+(include/lic_student.h) against the FP64 oracle (marked gpu).
+
+Float bar: the gradients of one batch agree with the oracle's chain-rule
+backward pass to 1e-4 of each tensor's largest magnitude (float32 sums over
+up to B*H*W terms); the forward pass to max-abs 1e-4; Adam, fed the GPU's
+own gradients, to 1e-6 of the learning rate.  Decoding with the student
+returns exactly the student's (or, on fallback, the teacher's) frames."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2208_01641_b300 as lic
+from paper_2208_01641_b300 import synth
+
+pytestmark = pytest.mark.gpu
+M, C = 192, 64
+
+
+@pytest.fixture(scope="module")
+def SW():
+    return synth.make_student_weights(M, C)
+
+
+def pools(P, Hy, Wy, seed):
+    r = np.random.default_rng(seed)
+    yp = np.rint(r.standard_normal((P, M, Hy, Wy)) * 2.0).astype(np.float32)
+    xp = r.uniform(0.0, 1.0, (P, 3, 16 * Hy, 16 * Wy)).astype(np.float32)
+    return yp, xp
+
+
+def test_student_gradients_match_oracle(SW):
+    """Loss and every parameter gradient of a 3-crop batch of 96 x 96 crops
+    (latent windows 6 x 6 out of a 2-frame 8 x 10 pool): split-K slices of
+    the weight gradient end ragged, the 3-channel layer takes the scalar
+    path, and the input-gradient convolutions span several tiles.
+
+    The forward activations match to max-abs 1e-4.  A ReLU decision is a
+    float deciding a bit: a pre-activation within rounding of 0 may fall
+    either way (this case has a few dozen within 1e-5), so the GPU's
+    decisions must equal the oracle's wherever the oracle's pre-activation is
+    farther than 1e-4 from 0, and the oracle's backward pass then takes the
+    GPU's decisions -- the rest of the chain is compared exactly as is."""
+    yp, xp = pools(2, 8, 10, seed=1)
+    crops = np.array([[0, 0, 0], [1, 2, 4], [1, 1, 3]], np.int32)
+    st = lic.Student(SW, M, C, max_batch=4, crop=96)
+    loss = st.grad(torch.from_numpy(yp).cuda(), torch.from_numpy(xp).cuda(), crops)
+    ys, xs = O.student_crops(yp, xp, crops, 96)
+    hs, _ = O.student_forward(SW, ys)
+    masks = {}
+    for l in (1, 2, 3):
+        h = st.activation(l, 3).transpose(0, 3, 1, 2)
+        assert np.abs(h - hs[l]).max() <= 1e-4, l
+        z = O.deconv2d(hs[l - 1], SW[f"student.deconv{l - 1}.weight"], SW[f"student.deconv{l - 1}.bias"], 2)
+        clear = np.abs(z) > 1e-4
+        assert np.array_equal((h > 0)[clear], (z > 0)[clear]), l
+        masks[l] = h > 0
+    oloss, ograds = O.student_loss_grads(SW, ys, xs, masks=masks)
+    assert abs(loss - oloss) <= 1e-5 * oloss
+    for name, og in ograds.items():
+        g = st.read(name, lic.STUDENT_GRAD)
+        err = np.abs(g - og).max()
+        assert err <= 1e-4 * np.abs(og).max() + 1e-9, (name, err, np.abs(og).max())
+    st.close()
+
+
+def test_student_adam_step_matches_oracle(SW):
+    """One lic_student_step: the new weights and both moments equal the
+    oracle's Adam applied to the GPU's own gradients (stage-wise parity)."""
+    yp, xp = pools(1, 6, 6, seed=2)
+    crops = np.array([[0, 0, 0], [0, 1, 2]], np.int32)
+    lr = 1e-3
+    st = lic.Student(SW, M, C, max_batch=2, crop=64, lr=lr)
+    dy, dx = torch.from_numpy(yp).cuda(), torch.from_numpy(xp).cuda()
+    P = {k: v.astype(np.float64) for k, v in SW.items()}
+    m = {k: np.zeros(v.shape) for k, v in SW.items()}
+    v = {k: np.zeros(x.shape) for k, x in SW.items()}
+    for t in (1, 2):
+        st.step(dy, dx, crops)
+        G = {k: st.read(k, lic.STUDENT_GRAD) for k in SW}
+        # the hyper-parameters cross the C ABI as float32: the oracle takes those values
+        f32 = lambda q: float(np.float32(q))
+        O.adam_step(P, G, m, v, t, lr=f32(lr), beta1=f32(0.9), beta2=f32(0.999), eps=f32(1e-8))
+        for k in SW:
+            assert np.abs(st.read(k) - P[k]).max() <= 1e-6 * lr + 1e-7 * np.abs(P[k]).max(), (k, t)
+            assert np.abs(st.read(k, lic.STUDENT_ADAM_M) - m[k]).max() <= 1e-6 * np.abs(m[k]).max() + 1e-12
+            assert np.abs(st.read(k, lic.STUDENT_ADAM_V) - v[k]).max() <= 1e-5 * np.abs(v[k]).max() + 1e-16
+        P = {k: st.read(k).astype(np.float64) for k in SW}   # continue from the GPU's own weights
+    assert st.steps() == 2
+    st.close()
+
+
+def test_student_forward_matches_oracle(SW):
+    """Full-frame inference on a ragged 6 x 9 latent plane (B = 2)."""
+    r = np.random.default_rng(3)
+    yhat = np.rint(r.standard_normal((2, M, 6, 9)) * 2).astype(np.float32)
+    st = lic.Student(SW, M, C, max_batch=1, crop=32)
+    x = torch.empty(2, 3, 96, 144, device="cuda")
+    st.forward(torch.from_numpy(yhat).cuda(), x)
+    torch.cuda.synchronize()
+    _, want = O.student_forward(SW, yhat)
+    assert np.abs(x.cpu().numpy() - want).max() <= 1e-4
+    # host buffers through the same call
+    xh = np.zeros((2, 3, 96, 144), np.float32)
+    st.forward(yhat, xh)
+    assert np.array_equal(xh, x.cpu().numpy())
+    st.close()
+
+
+def test_student_training_lowers_loss(SW):
+    """Thirty Adam steps on one fixed batch lower its loss."""
+    yp, xp = pools(1, 8, 8, seed=4)
+    crops = np.array([[0, 0, 0], [0, 2, 2]], np.int32)
+    st = lic.Student(SW, M, C, max_batch=2, crop=96, lr=1e-3)
+    dy, dx = torch.from_numpy(yp).cuda(), torch.from_numpy(xp).cuda()
+    l0 = st.grad(dy, dx, crops)
+    for _ in range(30):
+        st.step(dy, dx, crops)
+    assert st.grad(dy, dx, crops) < 0.7 * l0
+    st.close()
+
+
+def test_student_rejects_bad_crops(SW):
+    yp, xp = pools(1, 6, 6, seed=5)
+    st = lic.Student(SW, M, C, max_batch=2, crop=64)
+    dy, dx = torch.from_numpy(yp).cuda(), torch.from_numpy(xp).cuda()
+    for bad in ([[1, 0, 0]], [[0, 3, 0]], [[0, 0, -1]], [[0, 0, 0]] * 3):
+        with pytest.raises(lic.LicError) as e:
+            st.grad(dy, dx, np.array(bad, np.int32))
+        assert e.value.code == lic.E_INVALID_ARG
+    with pytest.raises(lic.LicError):   # host pools are refused
+        st.grad(yp, xp, np.array([[0, 0, 0]], np.int32))
+    st.close()
+
+
+def test_decode_with_student(SW):
+    """Factorized 128 x 128 codec (N=128, M=192) decoding with the student:
+    unchecked decode = the student's output on the decoded y_hat (clamped,
+    cropped); checked with an unreachable bar = the teacher's frames exactly,
+    all counted as fallbacks; checked with a bar of -inf dB = the unchecked
+    frames exactly; the reported PSNRs match the oracle's."""
+    W = synth.make_weights(0, 128, M)
+    codec = lic.Codec(0, 128, M, W)
+    st = lic.Student(SW, M, C, max_batch=1, crop=32)
+    x = synth.make_frames(2, 120, 100, first=11)
+    bs = codec.encode(torch.from_numpy(x).cuda())
+    teacher = torch.empty(2, 3, 120, 100, device="cuda")
+    codec.decode(bs, 120, 100, teacher)
+    sy = np.zeros((2, M, 8, 8), np.int32)
+    codec.read_tensor(lic.T_SY, sy)
+    oc = O.Codec(0, 128, M, W)
+    yhat_np = O.dequantize(sy, oc.med)
+    _, xs = O.student_forward(SW, yhat_np)
+    want_s = np.clip(xs, 0, 1)[:, :, :120, :100]
+
+    codec.set_student(st)
+    got_s = torch.empty_like(teacher)
+    codec.decode(bs, 120, 100, got_s)
+    torch.cuda.synchronize()
+    assert np.abs(got_s.cpu().numpy() - want_s).max() <= 1e-4
+
+    codec.set_student(st, min_psnr_db=1000.0, checked=True)
+    fb = torch.empty_like(teacher)
+    codec.decode(bs, 120, 100, fb)
+    torch.cuda.synchronize()
+    assert torch.equal(fb, teacher)
+    frames, falls, ps = codec.student_report()
+    assert (frames, falls) == (2, 2)
+    t = teacher.cpu().numpy().astype(np.float64)
+    for b in range(2):
+        mse = np.mean((np.clip(xs[b, :, :120, :100], 0, 1) - t[b]) ** 2)
+        assert abs(ps[b] - 10 * np.log10(1 / mse)) <= 1e-2
+
+    codec.set_student(st, min_psnr_db=-np.inf, checked=True)
+    ok = torch.empty_like(teacher)
+    codec.decode(bs, 120, 100, ok)
+    torch.cuda.synchronize()
+    assert torch.equal(ok, got_s)
+    assert codec.student_report()[:2] == (2, 0)
+
+    codec.set_student(None)
+    back = torch.empty_like(teacher)
+    codec.decode(bs, 120, 100, back)
+    torch.cuda.synchronize()
+    assert torch.equal(back, teacher)
+    codec.close()
+    st.close()
