@@ -542,12 +542,16 @@ def student_forward(P, yhat):
             return hs, z
 
 
-def student_loss_grads(P, yhat, target):
+def student_loss_grads(P, yhat, target, masks=None):
     """MSE loss mean((out - target)^2) and its gradients with respect to every
     student parameter, by the chain rule: output gradient 2 (out - t) / n; per
     layer, the weight gradient of the transposed conv, the bias gradient
     (sum over positions), and the input gradient (the strided conv with the
-    same weights -- the transposed conv's adjoint) masked by ReLU."""
+    same weights -- the transposed conv's adjoint) masked by ReLU.
+
+    masks: optional {l: boolean array shaped like h_l} for l = 1..3, the ReLU
+    decisions h_l > 0 taken elsewhere (a pre-activation within rounding of 0
+    may fall either way); by default h_l > 0 of this forward pass."""
     hs, out = student_forward(P, yhat)
     t = _f64(target)
     n = out.size
@@ -559,7 +563,8 @@ def student_loss_grads(P, yhat, target):
         grads[f"student.deconv{l}.weight"] = deconv2d_wgrad(hs[l], g)
         grads[f"student.deconv{l}.bias"] = g.sum(axis=(0, 2, 3))
         if l > 0:
-            g = conv2d(g, w, None, 2) * (hs[l] > 0)
+            mask = (hs[l] > 0) if masks is None else masks[l]
+            g = conv2d(g, w, None, 2) * mask
     return loss, grads
 
 
