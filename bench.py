@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--conv", default="auto", choices=["auto", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 precision form")
+    ap.add_argument("--no-forms", action="store_true", help="skip the precision / student / pipelined forms")
+    ap.add_argument("--student-steps", type=int, default=20000, help="training steps of the student form (0: skip)")
     return ap.parse_args()
 
 
@@ -306,6 +307,10 @@ def main():
         for c_ in c2:
             c_.close()
 
+    # ---- the learned form: distilled student g_s, trained here, decoding in place of g_s ----
+    if not args.no_forms and args.student_steps > 0:
+        forms["student"] = student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws, peaks)
+
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -358,6 +363,113 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+STUDENT_C = 64
+STUDENT_POOL = 16            # teacher frames the training crops are drawn from
+STUDENT_POOL_FIRST = 3000    # their frame seeds
+STUDENT_BATCH, STUDENT_CROP = 16, 256
+
+
+def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws, peaks):
+    """Train the student g_s (192->64->64->64->3 transposed convs, ReLU) on
+    (y_hat, x_hat) pairs of the factorized N=128/M=192 codec (16 seeded 720p
+    frames), Adam lr 1e-4, batch 16 random 256x256 crops; then decode the
+    hyperprior codec's 720p batch (same g_s parameters) with the student:
+    per-frame PSNR against the teacher (checked decode, fallback below 35 dB)
+    and enc+dec frames/s with the student in place of g_s."""
+    H, W = frames.shape[2], frames.shape[3]
+    B = frames.shape[0]
+    Hy, Wy = PAD_H // 16, PAD_W // 16
+    teacher = lic.Codec(lic.FACTORIZED, N_CH, M_CH, synth.make_weights(lic.FACTORIZED, N_CH, M_CH))
+    pool_y = torch.empty(STUDENT_POOL, M_CH, Hy, Wy, device="cuda")
+    pool_x = torch.empty(STUDENT_POOL, 3, PAD_H, PAD_W, device="cuda")
+    for i in range(0, STUDENT_POOL, 8):
+        fr = torch.from_numpy(synth.make_frames(8, H, W, first=STUDENT_POOL_FIRST + i)).cuda()
+        o = torch.empty_like(fr)
+        teacher.decode(teacher.encode(fr), H, W, o)
+        teacher.read_tensor(lic.T_YHAT, pool_y[i:i + 8])
+        teacher.read_tensor(lic.T_XPRE, pool_x[i:i + 8])
+    teacher.close()
+    st = lic.Student(synth.make_student_weights(M_CH, STUDENT_C), M_CH, STUDENT_C, max_batch=STUDENT_BATCH,
+                     crop=STUDENT_CROP, lr=1e-4)
+    steps = args.student_steps
+    crops = [synth.draw_crops(k, STUDENT_BATCH, STUDENT_POOL, Hy, Wy, STUDENT_CROP // 16) for k in range(steps)]
+    probe = synth.draw_crops(10 ** 6, STUDENT_BATCH, STUDENT_POOL, Hy, Wy, STUDENT_CROP // 16)
+    sid = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        loss0 = st.grad(pool_y, pool_x, probe, stream=sid)
+        warm = min(5, steps)
+        for k in range(warm):
+            st.step(pool_y, pool_x, crops[k], stream=sid)
+        l0 = st.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(warm, steps):
+            st.step(pool_y, pool_x, crops[k], stream=sid)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        train_ms = e0.elapsed_time(e1)
+        timed_steps = steps - warm
+        launches_per_step = (st.launch_count() - l0) / max(1, timed_steps)
+        loss1 = st.grad(pool_y, pool_x, probe, stream=sid)
+        st.profile(True)
+        st.step(pool_y, pool_x, crops[-1], stream=sid)
+        rep = st.profile_report()
+        st.profile(False)
+    train_flop = sum(r["flop"] for r in rep if r["name"] != "student.adam")
+    top = max(rep, key=lambda r: r["ms"])
+    sm_mhz = peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    top_ach = top["flop"] / top["launches"] / (top["ms"] / top["launches"] * 1e-3) / 1e12
+
+    # the hyperprior codec decoding with the student: checked (per-frame PSNR vs the teacher), then timed
+    codec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt)
+    bs = codec.encode(frames)
+    codec.decode(bs, H, W, out)
+    codec.set_student(st, min_psnr_db=35.0, checked=True)
+    codec.decode(bs, H, W, out)
+    nchk, nfall, psnrs = codec.student_report()
+    codec.set_student(st, checked=False)
+    fms, fstatus = time_steps(codec, frames, out, H, W, args.steps, args.warmup, stream, flush)
+    # decode alone, student vs teacher g_s
+    dec = {}
+    for name, s_ in (("student", st), ("teacher", None)):
+        codec.set_student(s_)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                codec.decode(bs, H, W, out, stream=sid)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                codec.decode(bs, H, W, out, stream=sid)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        dec[name] = B * args.steps / (ev0.elapsed_time(ev1) / 1000.0)
+    codec.close()
+    st.close()
+    return {
+        "value": ws * B * args.steps / (sum(fms) / 1000.0), "unit": "frames/s", "ms_per_step": sum(fms) / args.steps,
+        "p99_ms": sorted(fms)[min(len(fms) - 1, int(0.99 * len(fms)))], "decode_status": fstatus,
+        "psnr_vs_teacher_db": [round(float(p), 3) for p in psnrs], "frames_checked": nchk,
+        "fallbacks_below_35db": nfall,
+        "decode_fps_student": dec["student"], "decode_fps_teacher": dec["teacher"],
+        "train": {"steps": steps, "batch": STUDENT_BATCH, "crop": STUDENT_CROP, "lr": 1e-4,
+                  "ms_per_step": train_ms / max(1, timed_steps),
+                  "crops_per_s": STUDENT_BATCH * timed_steps / (train_ms / 1000.0),
+                  "tflops": train_flop / (train_ms / max(1, timed_steps) * 1e-3) / 1e12,
+                  "launches_per_step": launches_per_step,
+                  "probe_loss_before": loss0, "probe_loss_after": loss1,
+                  "pool": f"{STUDENT_POOL} seeded 1280x720 frames through the factorized N=128 M=192 codec"},
+        "roofline": {"kernel": top["name"], "bound": "alu", "achieved": top_ach, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": top_ach / fp32_peak, "traffic": None,
+                     "note": "CUDA-core FP32 FMA peak: 148 SMs x 128 lanes x 2 x max SM clock"},
+        "kernels": rep,
+        "note": "student g_s (4 transposed convs 192->64->64->64->3, ReLU, no IGDN), FP32 CUDA-core kernels, "
+                "trained on the GPU, decoding the hyperprior codec in place of g_s",
+    }
 
 
 def time_steps(codec, frames, out, H, W, steps, warmup, stream, flush):

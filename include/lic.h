@@ -198,8 +198,11 @@ typedef enum {
     LIC_T_SZ = 3,     /* int32, quantized z symbols                         */
     LIC_T_SIGMA = 4,  /* float32 B x M x Hp/16 x Wp/16, h_s scales          */
     LIC_T_IDX = 5,    /* uint8, scale-table index                           */
-    LIC_T_XPRE = 6    /* float32 B x 3 x Hp x Wp, decoder output before
+    LIC_T_XPRE = 6,   /* float32 B x 3 x Hp x Wp, decoder output before
                          clamp and crop                                     */
+    LIC_T_YHAT = 7    /* float32 B x M x Hp/16 x Wp/16, the decoder's
+                         dequantized y_hat (g_s input; after lic_decode or
+                         lic_decode_latents)                                */
 } lic_tensor;
 
 /* Copy intermediate `which` of the last call into dst (NCHW); `count`

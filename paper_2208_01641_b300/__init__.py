@@ -27,7 +27,7 @@ NORM_GDN = 0
 NORM_1DN = 1
 FP8 = 2
 
-T_Y, T_SY, T_Z, T_SZ, T_SIGMA, T_IDX, T_XPRE = range(7)
+T_Y, T_SY, T_Z, T_SZ, T_SIGMA, T_IDX, T_XPRE, T_YHAT = range(8)
 
 OK = 0
 E_INVALID_ARG, E_UNSUPPORTED, E_OOM, E_CORRUPT_STREAM, E_TIMEOUT, E_CUDA = -1, -2, -3, -4, -5, -6

@@ -85,7 +85,7 @@ struct lic_codec {
     // last call (for lic_read_tensor)
     int last_B = 0, last_Hp = 0, last_Wp = 0;
     bool have_y = false, have_sy = false, have_z = false, have_sz = false, have_sigma = false, have_idx = false,
-         have_xpre = false;
+         have_xpre = false, have_yhat = false;
 };
 
 namespace lic {
@@ -643,6 +643,7 @@ int entropy_decode(lic_codec *cd, const lic_bitstreams *in, int H, int W, cudaSt
     cd->have_sz = cd->kind == LIC_HYPERPRIOR;
     cd->have_sigma = cd->have_idx = cd->kind == LIC_HYPERPRIOR;
     cd->have_xpre = false;
+    cd->have_yhat = true;
     LIC_CUDA_TRY(cudaGetLastError());
     return LIC_OK;
 }
@@ -900,7 +901,7 @@ int lic_encode(lic_codec *cd, const float *frames, int B, int H, int W, lic_bits
     cd->last_Wp = Wp;
     cd->have_y = cd->have_sy = true;
     cd->have_z = cd->have_sz = cd->have_sigma = cd->have_idx = cd->kind == LIC_HYPERPRIOR;
-    cd->have_xpre = false;
+    cd->have_xpre = cd->have_yhat = false;
     return LIC_OK;
 }
 
@@ -1113,6 +1114,7 @@ int lic_read_tensor(lic_codec *cd, int which, void *dst, int64_t *count, void *s
         case LIC_T_SIGMA: n = (int64_t)B * cd->M * Hy * Wy; ok = cd->have_sigma; break;
         case LIC_T_IDX: n = (int64_t)B * cd->M * Hy * Wy; ok = cd->have_idx; break;
         case LIC_T_XPRE: n = (int64_t)B * 3 * Hp * Wp; ok = cd->have_xpre; break;
+        case LIC_T_YHAT: n = (int64_t)B * cd->M * Hy * Wy; ok = cd->have_yhat; break;
         default: return LIC_E_INVALID_ARG;
     }
     if (!ok || B == 0) return LIC_E_INVALID_ARG;
@@ -1123,6 +1125,7 @@ int lic_read_tensor(lic_codec *cd, int which, void *dst, int64_t *count, void *s
         case LIC_T_Z: return emit_nchw(cd, cd->z.as<float>(), B, Hz, Wz, cd->N, dst, st);
         case LIC_T_SIGMA: return emit_nchw(cd, cd->sigma.as<float>(), B, Hy, Wy, cd->M, dst, st);
         case LIC_T_XPRE: return emit_nchw(cd, cd->xpre.as<float>(), B, Hp, Wp, 3, dst, st);
+        case LIC_T_YHAT: return emit_nchw(cd, cd->yhat.as<float>(), B, Hy, Wy, cd->M, dst, st);
         case LIC_T_SY: LIC_CUDA_TRY(cudaMemcpyAsync(dst, cd->s_y.p, n * 4, cudaMemcpyDefault, st)); break;
         case LIC_T_SZ: LIC_CUDA_TRY(cudaMemcpyAsync(dst, cd->s_z.p, n * 4, cudaMemcpyDefault, st)); break;
         case LIC_T_IDX: LIC_CUDA_TRY(cudaMemcpyAsync(dst, cd->idx.p, n, cudaMemcpyDefault, st)); break;

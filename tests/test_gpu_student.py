@@ -151,6 +151,9 @@ def test_decode_with_student(SW):
     codec.read_tensor(lic.T_SY, sy)
     oc = O.Codec(0, 128, M, W)
     yhat_np = O.dequantize(sy, oc.med)
+    yhat_gpu = np.zeros((2, M, 8, 8), np.float32)
+    codec.read_tensor(lic.T_YHAT, yhat_gpu)
+    assert np.array_equal(yhat_gpu, yhat_np.astype(np.float32))
     _, xs = O.student_forward(SW, yhat_np)
     want_s = np.clip(xs, 0, 1)[:, :, :120, :100]
 
