@@ -30,7 +30,7 @@ FP8 = 2
 T_Y, T_SY, T_Z, T_SZ, T_SIGMA, T_IDX, T_XPRE, T_YHAT = range(8)
 
 OK = 0
-E_INVALID_ARG, E_UNSUPPORTED, E_OOM, E_CORRUPT_STREAM, E_TIMEOUT, E_CUDA = -1, -2, -3, -4, -5, -6
+E_INVALID_ARG, E_UNSUPPORTED, E_OOM, E_CORRUPT_STREAM, E_TIMEOUT, E_CUDA, E_BUSY = -1, -2, -3, -4, -5, -6, -7
 
 EXPORTED = [
     "lic_codec_create", "lic_codec_destroy", "lic_sync", "lic_encode", "lic_decode",
@@ -42,6 +42,9 @@ EXPORTED = [
     "lic_student_create", "lic_student_destroy", "lic_student_grad", "lic_student_step", "lic_student_read",
     "lic_student_read_activation", "lic_student_steps", "lic_student_forward", "lic_student_profile_enable", "lic_student_profile_report",
     "lic_student_launch_count", "lic_codec_set_student", "lic_codec_student_report",
+    # include/lic_serve.h (serving form)
+    "lic_server_create", "lic_server_destroy", "lic_server_prepare", "lic_server_submit", "lic_server_poll",
+    "lic_server_drain", "lic_server_stats_get", "lic_server_clock_ms",
 ]
 
 STUDENT_PARAM, STUDENT_GRAD, STUDENT_ADAM_M, STUDENT_ADAM_V = range(4)
@@ -74,6 +77,24 @@ class _StudentOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_batch", ctypes.c_int), ("crop", ctypes.c_int),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("reserved", ctypes.c_int * 4)]
+
+
+class _ServerOptions(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int), ("lanes", ctypes.c_int), ("max_pending", ctypes.c_int),
+                ("graphs", ctypes.c_int), ("max_wait_ms", ctypes.c_double), ("hbm_budget", ctypes.c_int64),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class _ServerResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("stream_id", ctypes.c_int), ("status", ctypes.c_int),
+                ("H", ctypes.c_int), ("W", ctypes.c_int), ("batch", ctypes.c_int), ("bytes", ctypes.c_int64),
+                ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("refused_busy", ctypes.c_int64),
+                ("refused_budget", ctypes.c_int64), ("batches", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("buckets", ctypes.c_int)]
 
 
 class _Bitstreams(ctypes.Structure):
@@ -135,6 +156,17 @@ def _lib():
         L.lic_student_launch_count.restype = i64
         L.lic_codec_set_student.argtypes = [vp, vp, ctypes.c_float, i]
         L.lic_codec_student_report.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), vp, i]
+        L.lic_server_create.argtypes = [i, i, i, ctypes.POINTER(_Weights), ctypes.POINTER(_Options),
+                                        ctypes.POINTER(_ServerOptions), ctypes.POINTER(vp)]
+        L.lic_server_destroy.argtypes = [vp]
+        L.lic_server_destroy.restype = None
+        L.lic_server_prepare.argtypes = [vp, i, i]
+        L.lic_server_submit.argtypes = [vp, i, vp, i, i, vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.lic_server_poll.argtypes = [vp, ctypes.POINTER(_ServerResult), i, ctypes.c_double]
+        L.lic_server_drain.argtypes = [vp, ctypes.c_double]
+        L.lic_server_stats_get.argtypes = [vp, ctypes.POINTER(_ServerStats)]
+        L.lic_server_clock_ms.argtypes = [vp]
+        L.lic_server_clock_ms.restype = ctypes.c_double
         L.lic_strerror.argtypes = [i]
         L.lic_strerror.restype = ctypes.c_char_p
         _LIB = L
@@ -473,3 +505,69 @@ class Student:
 
     def launch_count(self) -> int:
         return int(_lib().lic_student_launch_count(self.h))
+
+
+class Server:
+    """The serving form (include/lic_serve.h): frames of many streams and
+    resolutions, batched per resolution, encoded and decoded on lanes of
+    codecs running concurrently.  Keeps each submitted frame (and output
+    buffer) alive until its result has been polled."""
+
+    def __init__(self, kind: int, N: int, M: int, weights: Dict[str, np.ndarray], precision: int = FP32,
+                 max_batch: int = 8, lanes: int = 2, max_pending: int = 256, graphs: bool = True,
+                 max_wait_ms: float = 2.0, hbm_budget: int = 40 << 30, band_rows: int = 16):
+        w, keep = _weights_struct(weights)
+        copt = _Options(precision, band_rows, CONV_AUTO, NORM_GDN)
+        opt = _ServerOptions(max_batch, lanes, max_pending, 1 if graphs else 0, max_wait_ms, hbm_budget)
+        h = ctypes.c_void_p()
+        _check(_lib().lic_server_create(kind, N, M, ctypes.byref(w), ctypes.byref(copt), ctypes.byref(opt),
+                                        ctypes.byref(h)), "lic_server_create")
+        self.h = h
+        self._live = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().lic_server_destroy(self.h)
+            self.h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def prepare(self, H: int, W: int):
+        _check(_lib().lic_server_prepare(self.h, H, W), "lic_server_prepare")
+
+    def submit(self, stream_id: int, frame, decoded=None) -> int:
+        """Queue one 3 x H x W frame; returns its ticket.  Raises LicError
+        (code E_BUSY / E_OOM) when admission refuses it."""
+        H, W = frame.shape[-2], frame.shape[-1]
+        t = ctypes.c_uint64()
+        _check(_lib().lic_server_submit(self.h, stream_id, _ptr(frame), H, W,
+                                        _ptr(decoded) if decoded is not None else None, ctypes.byref(t)),
+               "lic_server_submit")
+        self._live[t.value] = (frame, decoded)
+        return t.value
+
+    def poll(self, cap: int = 256, wait_ms: float = 0.0):
+        buf = (_ServerResult * cap)()
+        n = _check(_lib().lic_server_poll(self.h, buf, cap, wait_ms), "lic_server_poll")
+        out = []
+        for k in range(n):
+            r = buf[k]
+            self._live.pop(r.ticket, None)
+            out.append({f: getattr(r, f) for f, _ in _ServerResult._fields_})
+        return out
+
+    def drain(self, timeout_ms: float = 60000.0):
+        _check(_lib().lic_server_drain(self.h, timeout_ms), "lic_server_drain")
+
+    def stats(self):
+        s = _ServerStats()
+        _check(_lib().lic_server_stats_get(self.h, ctypes.byref(s)), "lic_server_stats_get")
+        return {f: getattr(s, f) for f, _ in _ServerStats._fields_}
+
+    def clock_ms(self) -> float:
+        return float(_lib().lic_server_clock_ms(self.h))

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/lic_serve.h"
 #include "../../include/lic_student.h"
 #include "conv_tc.h"
 #include "lic_internal.h"
@@ -687,6 +688,7 @@ const char *lic_strerror(int code) {
         case LIC_E_CORRUPT_STREAM: return "corrupt bitstream";
         case LIC_E_TIMEOUT: return "device wait timed out";
         case LIC_E_CUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+        case LIC_E_BUSY: return "busy: too many requests in flight";
         default: return "unknown error";
     }
 }
@@ -973,6 +975,14 @@ int lic_profile_enable(lic_codec *cd, int enable) {
 int lic_profile_report(lic_codec *cd, char *buf, int cap) { return cd ? cd->pf.report(buf, cap) : LIC_E_INVALID_ARG; }
 
 int64_t lic_launch_count(lic_codec *cd) { return cd ? cd->pf.launches : LIC_E_INVALID_ARG; }
+
+}  // extern "C"
+
+namespace lic {
+uint32_t *codec_status_ptr(lic_codec *cd) { return cd->status.as<uint32_t>(); }
+}  // namespace lic
+
+extern "C" {
 
 int lic_codec_set_student(lic_codec *cd, lic_student *student, float min_psnr_db, int checked) {
     if (!cd || (student && student_channels(student) != cd->M) || (checked != 0 && checked != 1))

@@ -182,6 +182,8 @@ struct Profiler {
 }  // namespace lic
 struct lic_student;
 namespace lic {
+// the codec's device status word (ST_* bits; api.cu)
+uint32_t *codec_status_ptr(lic_codec *cd);
 // latent channels M of the student
 int student_channels(const lic_student *s);
 // NHWC y_hat [B][Hy][Wy][M] -> NHWC [B][16Hy][16Wy][3], stream-ordered

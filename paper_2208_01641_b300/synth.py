@@ -307,3 +307,29 @@ def draw_crops(step: int, B: int, P: int, Hy: int, Wy: int, lc: int) -> np.ndarr
     r = np.minimum((u[:, 1] * (Hy - lc + 1)).astype(np.int64), Hy - lc)
     c = np.minimum((u[:, 2] * (Wy - lc + 1)).astype(np.int64), Wy - lc)
     return np.ascontiguousarray(np.stack([f, r, c], axis=1), dtype=np.int32)
+
+
+# --------------------------------------------------------------------------
+# Serving workload
+# --------------------------------------------------------------------------
+
+SERVE_SEED = 7
+SERVE_STREAMS = ((6, 480, 640), (6, 720, 1280), (4, 1080, 1920))   # (streams, H, W)
+
+
+def poisson_arrivals(seconds: float, rate: float = 30.0, streams=SERVE_STREAMS, seed: int = SERVE_SEED):
+    """Arrival times of every stream's frames over [0, seconds): each stream
+    a Poisson process of ``rate`` frames/s (exponential gaps -ln(1-u)/rate,
+    u from SplitMix64 stream (seed << 20) + stream index).  Returns a list of
+    (t_seconds, stream_id, H, W) sorted by time."""
+    out = []
+    sid = 0
+    for count, H, W in streams:
+        for _ in range(count):
+            n = int(seconds * rate * 3 + 64)
+            gaps = -np.log1p(-uniform01((seed << 20) + sid, n)) / rate
+            t = np.cumsum(gaps)
+            out += [(float(x), sid, H, W) for x in t[t < seconds]]
+            sid += 1
+    out.sort()
+    return out

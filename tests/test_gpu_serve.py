@@ -1,0 +1,99 @@
+"""The serving form through the C ABI (include/lic_serve.h), marked gpu.
+
+A frame served in a mix -- batched with other frames of its resolution, on
+one of several lanes, while other resolutions run concurrently, replayed
+from a CUDA graph -- gives the same bitstream size and the same
+reconstruction, bit for bit, as the same frame encoded and decoded alone by
+a plain codec; the codec's results are per frame."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2208_01641_b300 as lic
+from paper_2208_01641_b300 import synth
+
+pytestmark = pytest.mark.gpu
+N, M = 64, 96
+
+
+@pytest.fixture(scope="module")
+def W():
+    return synth.make_weights(lic.HYPERPRIOR, N, M)
+
+
+def alone(W, frame, precision, n=N, m=M):
+    c = lic.Codec(lic.HYPERPRIOR, n, m, W, precision=precision)
+    x = torch.from_numpy(frame[None]).cuda()
+    bs = c.encode(x)
+    out = torch.empty_like(x)
+    c.decode(bs, x.shape[2], x.shape[3], out)
+    size = bs.sizes()[0]
+    c.close()
+    return size, out[0].cpu()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_served_frames_equal_frames_coded_alone(W, graphs):
+    shapes = [(64, 96)] * 5 + [(128, 128)] * 3 + [(64, 96)] * 2
+    frames = [synth.make_frame(40 + i, h, w) for i, (h, w) in enumerate(shapes)]
+    srv = lic.Server(lic.HYPERPRIOR, N, M, W, max_batch=3, lanes=2, graphs=graphs, max_wait_ms=1.0)
+    srv.prepare(64, 96)
+    srv.prepare(128, 128)
+    dev = [torch.from_numpy(f).cuda() for f in frames]
+    outs = [torch.empty_like(d) for d in dev]
+    tickets = [srv.submit(i % 4, d, o) for i, (d, o) in enumerate(zip(dev, outs))]
+    assert tickets == list(range(len(frames)))
+    srv.drain(60000)
+    res = {r["ticket"]: r for r in srv.poll(64)}
+    assert sorted(res) == tickets
+    st = srv.stats()
+    assert st["completed"] == len(frames) and st["buckets"] == 2 and st["device_bytes"] > 0
+    if graphs:
+        assert st["graph_replays"] >= 1
+    else:
+        assert st["graph_replays"] == 0
+    for i, f in enumerate(frames):
+        r = res[i]
+        assert r["status"] == 0 and (r["H"], r["W"]) == shapes[i] and r["stream_id"] == i % 4
+        assert r["t_submit_ms"] <= r["t_start_ms"] <= r["t_done_ms"]
+        size, x = alone(W, f, lic.FP32)
+        assert r["bytes"] == size, i
+        assert torch.equal(outs[i].cpu(), x), i
+    srv.close()
+
+
+def test_served_bf16_frames_equal_alone():
+    """The BF16 precision form (N=128, M=192), pinned host frames in and out."""
+    W = synth.make_weights(lic.HYPERPRIOR, 128, 192)
+    frames = [synth.make_frame(60 + i, 64, 128) for i in range(4)]
+    srv = lic.Server(lic.HYPERPRIOR, 128, 192, W, precision=lic.BF16, max_batch=4, lanes=1, max_wait_ms=50.0)
+    hosts = [torch.from_numpy(f).pin_memory() for f in frames]
+    outs = [torch.empty(f.shape).pin_memory() for f in frames]
+    for i, (h, o) in enumerate(zip(hosts, outs)):
+        srv.submit(0, h, o)
+    srv.drain(60000)
+    res = {r["ticket"]: r for r in srv.poll(16)}
+    assert all(r["batch"] == 4 for r in res.values())
+    for i, f in enumerate(frames):
+        size, x = alone(W, f, lic.BF16, 128, 192)
+        assert res[i]["bytes"] == size
+        assert torch.equal(outs[i], x)
+    srv.close()
+
+
+def test_server_admission(W):
+    f = torch.from_numpy(synth.make_frame(80, 64, 64)).cuda()
+    tiny = lic.Server(lic.HYPERPRIOR, N, M, W, hbm_budget=1)
+    with pytest.raises(lic.LicError) as e:
+        tiny.submit(0, f)
+    assert e.value.code == lic.E_OOM
+    assert tiny.stats()["refused_budget"] == 1 and tiny.stats()["buckets"] == 0
+    tiny.close()
+    # one request admitted (it waits in its bucket for a second frame), the next refused
+    srv = lic.Server(lic.HYPERPRIOR, N, M, W, max_batch=2, max_pending=1, max_wait_ms=1e7)
+    srv.submit(0, f)
+    with pytest.raises(lic.LicError) as e:
+        srv.submit(1, f)
+    assert e.value.code == lic.E_BUSY
+    assert srv.stats()["refused_busy"] == 1
+    srv.close()   # the queued partial batch runs at shutdown
