@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / student / pipelined forms")
     ap.add_argument("--student-steps", type=int, default=20000, help="training steps of the student form (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the serving form's workload (0: skip)")
     return ap.parse_args()
 
 
@@ -64,10 +65,11 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, tag="main"):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(tempfile.gettempdir(), f"lic_bench_clocks_gpu{gpu_index}_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(),
+                                 f"lic_bench_clocks_gpu{gpu_index}_{os.getpid()}_{tag}.csv")
 
     def __enter__(self):
         try:
@@ -311,6 +313,10 @@ def main():
     if not args.no_forms and args.student_steps > 0:
         forms["student"] = student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws, peaks)
 
+    # ---- the serving form: 16 Poisson streams of mixed resolutions through the BF16 codec ----
+    if not args.no_forms and args.serve_seconds > 0:
+        forms["serving"] = serving_form(args, lic, synth, torch, np, Wt)
+
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -469,6 +475,76 @@ def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws
         "kernels": rep,
         "note": "student g_s (4 transposed convs 192->64->64->64->3, ReLU, no IGDN), FP32 CUDA-core kernels, "
                 "trained on the GPU, decoding the hyperprior codec in place of g_s",
+    }
+
+
+def serving_form(args, lic, synth, torch, np, Wt):
+    """16 streams at 30 frames/s each, Poisson arrivals (seed 7): 6 x 640x480,
+    6 x 1280x720, 4 x 1920x1080, submitted in real time to the serving
+    runtime (hyperprior N=128 M=192, BF16 form, batches of up to 8 per
+    resolution, 2 lanes per resolution, CUDA-graph replays, 40 GB budget);
+    frames come from pinned host memory, bitstreams and reconstructions stay
+    on the device.  Latency = completion callback - submit, per frame."""
+    arrivals = synth.poisson_arrivals(args.serve_seconds)
+    shapes = sorted({(a[2], a[3]) for a in arrivals})
+    pool = {s: [torch.from_numpy(synth.make_frame(5000 + 10 * k + j, *s)).pin_memory() for j in range(2)]
+            for k, s in enumerate(shapes)}
+    srv = lic.Server(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=lic.BF16, max_batch=8, lanes=2, max_pending=1 << 16,
+                     graphs=True, max_wait_ms=4.0, hbm_budget=40 << 30)
+    for s in shapes:
+        srv.prepare(*s)
+    # warm every lane once outside the measured workload
+    for s in shapes:
+        for j in range(16):
+            srv.submit(0, pool[s][j % 2])
+    srv.drain(120000)
+    srv.poll(4096)
+    base = srv.stats()
+    results, refused = [], 0
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), tag="serving")
+    with sampler:
+        t0 = time.perf_counter()
+        for i, (t, sid, H, W) in enumerate(arrivals):
+            d = t0 + t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            try:
+                srv.submit(sid, pool[(H, W)][i % 2])
+            except lic.LicError:
+                refused += 1
+            if i % 64 == 0:
+                results += srv.poll(4096)
+        srv.drain(120000)
+        results += srv.poll(1 << 16)
+    st = srv.stats()
+    # capacity: the same frames submitted all at once (full batches, every lane busy)
+    sat = []
+    c0 = srv.clock_ms()
+    for i, (t, sid, H, W) in enumerate(arrivals):
+        srv.submit(sid, pool[(H, W)][i % 2])
+    srv.drain(300000)
+    sat = srv.poll(1 << 16)
+    sat_span_s = (max(r["t_done_ms"] for r in sat) - c0) / 1000.0
+    srv.close()
+    lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in results])
+    span_s = (max(r["t_done_ms"] for r in results) - min(r["t_submit_ms"] for r in results)) / 1000.0
+    per_res = {}
+    for s in shapes:
+        ls = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in results if (r["H"], r["W"]) == s])
+        per_res[f"{s[1]}x{s[0]}"] = {"frames": int(ls.size), "p50_ms": float(np.percentile(ls, 50)),
+                                    "p99_ms": float(np.percentile(ls, 99))}
+    return {
+        "value": len(results) / span_s, "unit": "frames/s", "offered_fps": len(arrivals) / args.serve_seconds,
+        "capacity_fps": len(sat) / sat_span_s,
+        "capacity_mp_per_s": sum(r["H"] * r["W"] for r in sat) / sat_span_s / 1e6,
+        "frames": len(results), "refused": refused, "errors": int(sum(r["status"] != 0 for r in results)),
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)), "per_resolution": per_res,
+        "batches": st["batches"] - base["batches"], "graph_replays": st["graph_replays"] - base["graph_replays"],
+        "mean_batch": len(results) / max(1, st["batches"] - base["batches"]), "device_bytes": st["device_bytes"],
+        "clocks": sampler.summary(),
+        "note": "hyperprior N=128 M=192 BF16 form; 16 Poisson(30/s) streams for %.0f s, seed 7; frames from pinned "
+                "host memory, bitstreams and reconstructions device-resident; latency = submit -> completion"
+                % args.serve_seconds,
     }
 
 
