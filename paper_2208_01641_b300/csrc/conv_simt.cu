@@ -14,6 +14,8 @@
 // (taps, then channels), so results do not depend on the batch position or
 // the launch.  This is the exact FP32 path the tensor-core kernels are
 // measured against, and it runs the layers those kernels do not cover.
+#include <cuda_bf16.h>
+
 #include "lic_internal.h"
 
 namespace lic {
@@ -150,7 +152,10 @@ __global__ void __launch_bounds__(NT) conv_simt_kernel(const ConvDesc d) {
             } else if (d.epi == EPI_MASK) {
                 v = d.gdn_x[opix * d.Cout + n] > 0.f ? v : 0.f;
             }
-            d.out[opix * d.Cout + n] = v;
+            if (d.out_dt == DT_BF16)
+                reinterpret_cast<__nv_bfloat16 *>(d.out)[opix * d.Cout + n] = __float2bfloat16_rn(v);
+            else
+                d.out[opix * d.Cout + n] = v;
         }
     }
 }

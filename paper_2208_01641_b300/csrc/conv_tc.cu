@@ -274,6 +274,35 @@ __device__ __forceinline__ void store_row(const float *v, void *out, int64_t off
     }
 }
 
+// The ReLU's backward pass: zero v[i] wherever the activation m (same layout
+// and storage type as the output, dt) is not positive.
+template <int NV>
+__device__ __forceinline__ void mask_row(float *v, const void *m, int64_t off, int dt) {
+    if (dt == DT_BF16) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(m) + off);
+#pragma unroll
+        for (int q = 0; q < NV / 8; ++q) {
+            const uint4 u = __ldg(src + q);
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t h = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+                if ((h & 0x8000u) || !(h & 0x7fffu)) v[8 * q + j] = 0.f;
+            }
+        }
+    } else {
+        const float4 *src = reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(m) + off);
+#pragma unroll
+        for (int q = 0; q < NV / 4; ++q) {
+            const float4 u = __ldg(src + q);
+            if (!(u.x > 0.f)) v[4 * q] = 0.f;
+            if (!(u.y > 0.f)) v[4 * q + 1] = 0.f;
+            if (!(u.z > 0.f)) v[4 * q + 2] = 0.f;
+            if (!(u.w > 0.f)) v[4 * q + 3] = 0.f;
+        }
+    }
+}
+
 // Round to TF32 (10 stored mantissa bits), to nearest, ties away from zero:
 // add half of the 13 dropped bits to the magnitude, then clear them.  Same
 // result as cvt.rna.tf32.f32 for finite values, at integer-ALU rate.
@@ -1017,8 +1046,10 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
 #pragma unroll
             for (int i = 0; i < HALF * 32; ++i) master[i] *= __ldg(p.w_scale + cbase + i) * p.in_scale;
         }
+        if (p.bias) {
 #pragma unroll
-        for (int i = 0; i < HALF * 32; ++i) master[i] += __ldg(p.bias + cbase + i);
+            for (int i = 0; i < HALF * 32; ++i) master[i] += __ldg(p.bias + cbase + i);
+        }
         if (ok && p.fuse_gdn >= 3) {   // 1DN / inverse 1DN, per channel
 #pragma unroll
             for (int i = 0; i < HALF * 32; ++i) {
@@ -1073,6 +1104,8 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
                 if (p.epi == EPI_RELU) {
 #pragma unroll
                     for (int i = 0; i < HALF * 32; ++i) master[i] = fmaxf(master[i], 0.f);
+                } else if (p.epi == EPI_MASK) {
+                    mask_row<HALF * 32>(master, p.gdn_x, opix * COUT + cbase, p.out_dt);
                 }
                 store_row<HALF * 32>(master, p.out, opix * COUT + cbase, p.out_dt, p.out_inv_scale);
             }
@@ -1389,14 +1422,21 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     return true;
 }
 
-bool can_run_lp(const ConvDesc &d, const TcWeights &w) {
+namespace {
+// launch shapes the low-precision kernel handles (weights aside)
+bool lp_shape_ok(const ConvDesc &d) {
     const bool e4 = d.in_dt == DT_E4M3;
     if (d.in_dt != DT_BF16 && !e4) return false;
-    if ((e4 ? !w.f8valid : !w.bvalid) || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout || !d.bias || !d.status)
+    if (d.Cout != 64 && d.Cout != 128 && d.Cout != 192) return false;
+    if (d.Cout == 64 && e4) return false;
+    if (!d.status || (reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15))
         return false;
-    if ((reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15)) return false;
-    if (d.epi != EPI_NONE && d.epi != EPI_RELU) return false;
+    if (d.epi != EPI_NONE && d.epi != EPI_RELU && d.epi != EPI_MASK) return false;
+    if (d.epi == EPI_MASK && (!d.gdn_x || (reinterpret_cast<uintptr_t>(d.gdn_x) & 15) ||
+                              (d.out_dt != DT_BF16 && d.out_dt != DT_F32)))
+        return false;
     if (d.in_xform != IN_NONE) return false;
+    if (d.Cin % (e4 ? KC8 : KCB)) return false;
     if (d.fuse_gdn >= 3 && (!d.gdn_beta || !d.gdn_gamma)) return false;
     if (d.fuse_gdn == 1 || d.fuse_gdn == 2) {
         const TcWeights *g = static_cast<const TcWeights *>(d.gdn_w);
@@ -1407,12 +1447,42 @@ bool can_run_lp(const ConvDesc &d, const TcWeights &w) {
     return d.s == 1;
 }
 
-bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
+template <int STAGES, int HALF, int EB>
+void launch_lp_kernel(unsigned grid, cudaStream_t st, const CUtensorMap &a, const CUtensorMap &b,
+                      const CUtensorMap &gh, const CUtensorMap &gl, const Params &p) {
+    const int smem = STAGES * (AB_BYTES + 64 * HALF * 128) + 256 + 1024;
+    cudaFuncSetAttribute(conv_lp_kernel<STAGES, HALF, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    conv_lp_kernel<STAGES, HALF, EB><<<grid, 64 + EPI_THREADS, smem, st>>>(a, b, gh, gl, p);
+}
+}  // namespace
+
+bool can_run_lp(const ConvDesc &d, const TcWeights &w) {
+    const bool e4 = d.in_dt == DT_E4M3;
+    if (!lp_shape_ok(d) || (e4 ? !w.f8valid : !w.bvalid) || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout)
+        return false;
+    return d.bias != nullptr;
+}
+
+bool can_run_lp_map(const ConvDesc &d) { return d.in_dt == DT_BF16 && lp_shape_ok(d); }
+
+bool make_bf16_weight_map(TmaMap *m, const void *w, int Cout, int K) {
+    if (!m || !w || K % KCB || (reinterpret_cast<uintptr_t>(w) & 15) || !encode_fn()) return false;
+    if (Cout != 64 && Cout != 128 && Cout != 192) return false;
+    const uint64_t dims[2] = {(uint64_t)K, (uint64_t)Cout};
+    const uint64_t strides[1] = {(uint64_t)K * 2};
+    const uint32_t box[2] = {KCB, (uint32_t)Cout};
+    static_assert(sizeof(TmaMap) == sizeof(CUtensorMap), "TmaMap holds one CUtensorMap");
+    return make_map(reinterpret_cast<CUtensorMap *>(m), w, 2, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+}
+
+namespace {
+bool launch_lp_impl(const ConvDesc &d, const CUtensorMap &bm, const float *w_scale, cudaStream_t st) {
     const bool e4 = d.in_dt == DT_E4M3;
     const int EBY = e4 ? 1 : 2;
     Params p{};
     p.out = d.out;
     p.bias = d.bias;
+    p.gdn_x = d.gdn_x;
     p.status = d.status;
     p.T = d.T;
     p.Cin = d.Cin;
@@ -1435,8 +1505,8 @@ bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.out_dt = d.out_dt;
     p.out_inv_scale = d.out_scale > 0.f ? 1.f / d.out_scale : 1.f;
     p.in_scale = d.in_scale > 0.f ? d.in_scale : 1.f;
-    p.w_scale = w.w8scale;
-    p.tmem_cols = 512;
+    p.w_scale = w_scale;
+    p.tmem_cols = d.Cout == 64 ? 128 : 512;   // two partial buffers (+ norm operands when Cout = 128)
     for (int t = 0; t < d.T; ++t) {
         p.du[t] = d.du[t];
         p.dv[t] = d.dv[t];
@@ -1464,33 +1534,39 @@ bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
         if (!make_map(&tmA, d.in, 4, dims, strides, box, dt)) return false;
     }
     if (grid == 0) return true;
-    const CUtensorMap &bm = *reinterpret_cast<const CUtensorMap *>(e4 ? w.w8map : w.bmap);
     const bool gemm_norm = d.fuse_gdn == 1 || d.fuse_gdn == 2;
     const CUtensorMap *g = gemm_norm ? reinterpret_cast<const CUtensorMap *>(
                                             static_cast<const TcWeights *>(d.gdn_w)->maps)
                                       : &bm;
     const CUtensorMap &gh = g[0];
     const CUtensorMap &gl = gemm_norm ? g[1] : g[0];
-    if (d.Cout == 128) {
-        const int smem = 6 * (AB_BYTES + 128 * 128) + 256 + 1024;
-        if (e4) {
-            cudaFuncSetAttribute(conv_lp_kernel<6, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            conv_lp_kernel<6, 2, 1><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
-        } else {
-            cudaFuncSetAttribute(conv_lp_kernel<6, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            conv_lp_kernel<6, 2, 2><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
-        }
+    if (d.Cout == 64) {
+        // 4 stages (99.6 KB of shared memory, 128 TMEM columns): two CTAs share an SM, so one
+        // CTA's epilogue overlaps the other's main loop on these short-K launches
+        launch_lp_kernel<4, 1, 2>(grid, st, tmA, bm, gh, gl, p);
+    } else if (d.Cout == 128) {
+        if (e4)
+            launch_lp_kernel<6, 2, 1>(grid, st, tmA, bm, gh, gl, p);
+        else
+            launch_lp_kernel<6, 2, 2>(grid, st, tmA, bm, gh, gl, p);
     } else {
-        const int smem = 5 * (AB_BYTES + 192 * 128) + 256 + 1024;
-        if (e4) {
-            cudaFuncSetAttribute(conv_lp_kernel<5, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            conv_lp_kernel<5, 3, 1><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
-        } else {
-            cudaFuncSetAttribute(conv_lp_kernel<5, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            conv_lp_kernel<5, 3, 2><<<grid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, p);
-        }
+        if (e4)
+            launch_lp_kernel<5, 3, 1>(grid, st, tmA, bm, gh, gl, p);
+        else
+            launch_lp_kernel<5, 3, 2>(grid, st, tmA, bm, gh, gl, p);
     }
     return true;
+}
+}  // namespace
+
+bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
+    const bool e4 = d.in_dt == DT_E4M3;
+    return launch_lp_impl(d, *reinterpret_cast<const CUtensorMap *>(e4 ? w.w8map : w.bmap), w.w8scale, st);
+}
+
+bool launch_lp_map(const ConvDesc &d, const TmaMap &bmap, cudaStream_t st) {
+    if (!can_run_lp_map(d)) return false;
+    return launch_lp_impl(d, *reinterpret_cast<const CUtensorMap *>(&bmap), nullptr, st);
 }
 
 }  // namespace tc

@@ -43,5 +43,21 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
 bool can_run_lp(const ConvDesc &d, const TcWeights &w);
 bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
 
+// Storage of one tensor map (a CUtensorMap, passed to kernels by value).
+struct alignas(64) TmaMap {
+    unsigned char raw[128];
+};
+
+// bf16 weights [Cout][K] in device memory (Cout 64, 128 or 192; K a multiple
+// of 64; 16-byte aligned) -> the kernel's B-operand tensor map.
+bool make_bf16_weight_map(TmaMap *m, const void *w, int Cout, int K);
+
+// The bf16 kernel with caller-made weight maps (weights that change on the
+// device, e.g. during training): Cout 64, 128 or 192; epilogues none, ReLU
+// or EPI_MASK (d.gdn_x = the activation, stored like the output); d.bias
+// may be null.  false = not launched.
+bool can_run_lp_map(const ConvDesc &d);
+bool launch_lp_map(const ConvDesc &d, const TmaMap &bmap, cudaStream_t st);
+
 }  // namespace tc
 }  // namespace lic

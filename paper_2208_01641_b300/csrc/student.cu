@@ -21,12 +21,22 @@
 //
 // Every reduction has a fixed order (split-K partials summed in split
 // order), so results do not depend on timing.
+//
+// Precision LIC_BF16 (the training form the task configures): the three
+// 64-channel transposed convs and the input gradients through them run on
+// the tcgen05 bf16 kernel (bf16 operands, float32 accumulation); y_hat,
+// h_1, h_2 and dz_0..dz_2 are stored in bf16, h_3, the output and dz_3 in
+// float32; the 3-channel layer, the weight and bias gradients and Adam stay
+// float32 on CUDA cores (reading the bf16 tensors), master weights float32.
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
 
 #include "../../include/lic_student.h"
+#include "conv_tc.h"
 #include "lic_internal.h"
 
 namespace lic {
@@ -47,9 +57,22 @@ struct Crops {
 // kernels
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ float ld(const float *p, int64_t i) { return p[i]; }
+__device__ __forceinline__ float ld(const __nv_bfloat16 *p, int64_t i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ void st(float *p, int64_t i, float v) { p[i] = v; }
+__device__ __forceinline__ void st(__nv_bfloat16 *p, int64_t i, float v) { p[i] = __float2bfloat16_rn(v); }
+// four consecutive values starting at a 4-aligned index
+__device__ __forceinline__ float4 ld4(const float *p, int64_t i) { return *reinterpret_cast<const float4 *>(p + i); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p, int64_t i) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p + i);
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                       __uint_as_float(u.y & 0xffff0000u));
+}
+
 // y_hat crops: pool NCHW [P][M][Hy][Wy] -> h0 NHWC [B][lc][lc][M]
+template <typename TO>
 __global__ void gather_yhat_kernel(const float *__restrict__ pool, int M, int Hy, int Wy, Crops cr, int lc,
-                                   float *__restrict__ h0) {
+                                   TO *__restrict__ h0) {
     const int64_t n = (int64_t)cr.n * lc * lc * M;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int ch = (int)(e % M);
@@ -58,7 +81,7 @@ __global__ void gather_yhat_kernel(const float *__restrict__ pool, int M, int Hy
         pos /= lc;
         const int r = (int)(pos % lc);
         const int b = (int)(pos / lc);
-        h0[e] = pool[(((int64_t)cr.f[b] * M + ch) * Hy + cr.r[b] + r) * Wy + cr.c[b] + c];
+        st(h0, e, pool[(((int64_t)cr.f[b] * M + ch) * Hy + cr.r[b] + r) * Wy + cr.c[b] + c]);
     }
 }
 
@@ -113,7 +136,8 @@ __global__ void __launch_bounds__(RED_T) mse_final_kernel(const double *__restri
 
 // per-channel sums of an NHWC tensor [P][C] (C <= RED_T): block z sums the
 // pixels [z*per, (z+1)*per) into part[z][C]
-__global__ void __launch_bounds__(RED_T) chan_sum_kernel(const float *__restrict__ x, int64_t P, int C, int64_t per,
+template <typename TX>
+__global__ void __launch_bounds__(RED_T) chan_sum_kernel(const TX *__restrict__ x, int64_t P, int C, int64_t per,
                                                          float *__restrict__ part) {
     __shared__ float red[RED_T];
     const int G = RED_T / C;          // pixel lanes
@@ -121,7 +145,7 @@ __global__ void __launch_bounds__(RED_T) chan_sum_kernel(const float *__restrict
     float acc = 0.f;
     if (g < G) {
         const int64_t p0 = blockIdx.x * per, p1 = min(P, p0 + per);
-        for (int64_t p = p0 + g; p < p1; p += G) acc += x[p * C + c];
+        for (int64_t p = p0 + g; p < p1; p += G) acc += ld(x, p * C + c);
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -147,8 +171,8 @@ __global__ void chan_sum_final_kernel(const float *__restrict__ part, int nz, in
 // dz: NHWC [B][2H][2W][Cout].  part[z][Cin][25*Cout].
 constexpr int WG_BM = 64, WG_BN = 64, WG_BK = 16, WG_NT = 256;
 
-template <bool VEC>   // VEC: Cout % 64 == 0, one tap per column tile, float4 loads
-__global__ void __launch_bounds__(WG_NT) wgrad_kernel(const float *__restrict__ x, const float *__restrict__ dz, int B,
+template <bool VEC, typename TX, typename TD>   // VEC: Cout % 64 == 0, one tap per column tile, 4-wide loads
+__global__ void __launch_bounds__(WG_NT) wgrad_kernel(const TX *__restrict__ x, const TD *__restrict__ dz, int B,
                                                       int H, int W, int Cin, int Cout, int64_t kper,
                                                       float *__restrict__ part) {
     __shared__ __align__(16) float As[WG_BK][WG_BM];
@@ -177,14 +201,14 @@ __global__ void __launch_bounds__(WG_NT) wgrad_kernel(const float *__restrict__ 
             c = rem % W;
         }
         float4 va = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (pv && i0 + 4 * lq < Cin) va = *reinterpret_cast<const float4 *>(x + p * Cin + i0 + 4 * lq);
+        if (pv && i0 + 4 * lq < Cin) va = ld4(x, p * Cin + i0 + 4 * lq);
         *reinterpret_cast<float4 *>(&As[lp][4 * lq]) = va;
         if (VEC) {
             const int tap = n0 / Cout, o0 = n0 % Cout;
             const int yo = 2 * a + tap / 5 - 2, xo = 2 * c + tap % 5 - 2;
             float4 vb = make_float4(0.f, 0.f, 0.f, 0.f);
             if (pv && yo >= 0 && yo < Ho && xo >= 0 && xo < Wo)
-                vb = *reinterpret_cast<const float4 *>(dz + (((int64_t)b * Ho + yo) * Wo + xo) * Cout + o0 + 4 * lq);
+                vb = ld4(dz, (((int64_t)b * Ho + yo) * Wo + xo) * Cout + o0 + 4 * lq);
             *reinterpret_cast<float4 *>(&Bs[lp][4 * lq]) = vb;
         } else {
 #pragma unroll
@@ -199,7 +223,7 @@ __global__ void __launch_bounds__(WG_NT) wgrad_kernel(const float *__restrict__ 
                     const int bb = (int)(pp / HW);
                     const int rem = (int)(pp % HW);
                     const int yo = 2 * (rem / W) + tap / 5 - 2, xo = 2 * (rem % W) + tap % 5 - 2;
-                    if (yo >= 0 && yo < Ho && xo >= 0 && xo < Wo) vb = dz[(((int64_t)bb * Ho + yo) * Wo + xo) * Cout + o];
+                    if (yo >= 0 && yo < Ho && xo >= 0 && xo < Wo) vb = ld(dz, (((int64_t)bb * Ho + yo) * Wo + xo) * Cout + o);
                 }
                 Bs[kk][nn] = vb;
             }
@@ -258,6 +282,7 @@ struct RepackArgs {
     const float *w[NL];
     float *wf[NL];   // forward phase matrices (layers with > 4 outputs) or null
     float *wd[NL];   // input-gradient conv matrix (layers 1..3) or null
+    __nv_bfloat16 *wfb[NL], *wdb[NL];   // bf16 copies of the same (precision LIC_BF16) or null
     float *ws;       // last layer [Cin][25][4]
     int cin[NL], cout[NL];
     int64_t start[NL + 1];
@@ -277,12 +302,14 @@ __global__ void repack_kernel(RepackArgs a) {
     const int o = (int)((e / 25) % Cout);
     const int i = (int)(e / (25 * (int64_t)Cout));
     const float wv = a.w[l][e];
-    if (a.wf[l]) {
-        const int ph = (u & 1) * 2 + (v & 1);
-        const int t = (u >> 1) * ((v & 1) ? 2 : 3) + (v >> 1);
-        a.wf[l][(int64_t)ph_off(ph) * Cout * Cin + ((int64_t)o * ph_taps(ph) + t) * Cin + i] = wv;
-    }
-    if (a.wd[l]) a.wd[l][((int64_t)i * 25 + u * 5 + v) * Cout + o] = wv;
+    const int ph = (u & 1) * 2 + (v & 1);
+    const int t = (u >> 1) * ((v & 1) ? 2 : 3) + (v >> 1);
+    const int64_t fi = (int64_t)ph_off(ph) * Cout * Cin + ((int64_t)o * ph_taps(ph) + t) * Cin + i;
+    const int64_t di = ((int64_t)i * 25 + u * 5 + v) * Cout + o;
+    if (a.wf[l]) a.wf[l][fi] = wv;
+    if (a.wfb[l]) a.wfb[l][fi] = __float2bfloat16_rn(wv);
+    if (a.wd[l]) a.wd[l][di] = wv;
+    if (a.wdb[l]) a.wdb[l][di] = __float2bfloat16_rn(wv);
     if (l == NL - 1 && a.ws) a.ws[((int64_t)i * 25 + u * 5 + v) * 4 + o] = wv;
 }
 
@@ -350,17 +377,21 @@ int grid_for(int64_t n, int t) { return (int)std::min<int64_t>((n + t - 1) / t, 
 struct lic_student {
     int M = 0, C = 0;
     lic_student_options opt{};
+    bool bf16 = false;
     int device = 0;
     int cin[4] = {}, cout[4] = {};
     int64_t woff[4] = {}, boff[4] = {}, nparam = 0;
     lic::DevBuf param, grad, adam_m, adam_v;
-    lic::DevBuf wf[4], wd[4], ws;
+    // float32 re-layouts (CUDA-core kernels) and bf16 ones with their tensor maps (tcgen05 kernel)
+    lic::DevBuf wf[4], wd[4], ws, wfb[4], wdb[4];
+    lic::tc::TmaMap fmap[4][4], dmap[4];
     // training workspace (max_batch crops)
     lic::DevBuf h[4], out, dz[4], part, lpart, loss, bpart, status;
     // inference workspace
     lic::DevBuf ih[4], iout;
     int64_t t = 0;
     int last_B = 0;
+    bool launch_failed = false;
     lic::Profiler pf;
 };
 
@@ -369,10 +400,20 @@ namespace {
 
 int64_t wsize(const lic_student *s, int l) { return (int64_t)s->cin[l] * s->cout[l] * 25; }
 
+// storage bytes per element of h_l / dz_l (l = 0..3)
+int act_bytes(const lic_student *s, int l) { return (s->bf16 && l < NL - 1) ? 2 : 4; }
+
 template <typename F>
 void timed(lic_student *s, const std::string &name, double flop, double bytes, int n, cudaStream_t st, F &&f) {
     s->pf.run(name, flop, bytes, n, st, f);
 }
+
+int ensure_e(DevBuf &b, int64_t n, int elem) {
+    LIC_CUDA_TRY(b.ensure((size_t)std::max<int64_t>(n, 1) * elem));
+    return LIC_OK;
+}
+
+int ensure_f(DevBuf &b, int64_t n) { return ensure_e(b, n, 4); }
 
 int repack(lic_student *s, cudaStream_t st) {
     RepackArgs a{};
@@ -381,6 +422,8 @@ int repack(lic_student *s, cudaStream_t st) {
         a.w[l] = s->param.as<float>() + s->woff[l];
         a.wf[l] = s->wf[l].as<float>();
         a.wd[l] = s->wd[l].as<float>();
+        a.wfb[l] = s->wfb[l].as<__nv_bfloat16>();
+        a.wdb[l] = s->wdb[l].as<__nv_bfloat16>();
         a.cin[l] = s->cin[l];
         a.cout[l] = s->cout[l];
         a.start[l + 1] = a.start[l] + wsize(s, l);
@@ -393,25 +436,42 @@ int repack(lic_student *s, cudaStream_t st) {
     return LIC_OK;
 }
 
-// one transposed conv (l < 3: four phase launches + ReLU; l == 3: the
-// small-Cout kernel) from h (NHWC, Hi x Wi) into out
-void forward_layer(lic_student *s, int l, const float *in, int B, int Hi, int Wi, float *out, cudaStream_t st) {
+// taps of sub-pixel phase (py, px) of a transposed conv 5x5 / 2 into d
+void phase_taps(ConvDesc &d, int py, int px) {
+    int t = 0;
+    for (int u = py; u < 5; u += 2)
+        for (int v = px; v < 5; v += 2) {
+            d.du[t] = (int8_t)((py + 2 - u) / 2);
+            d.dv[t] = (int8_t)((px + 2 - v) / 2);
+            ++t;
+        }
+    d.T = t;
+}
+
+// one transposed conv (l < 3: four phase launches + ReLU, on the bf16
+// tensor-core kernel or the CUDA-core kernel; l == 3: the small-Cout
+// kernel) from h (NHWC, Hi x Wi) into out
+void forward_layer(lic_student *s, int l, const void *in, int B, int Hi, int Wi, void *out, cudaStream_t st) {
     const int Cin = s->cin[l], Cout = s->cout[l];
     const double flop = 2.0 * B * Hi * Wi * (double)Cin * Cout * 25;
-    const double bytes = 4.0 * ((double)B * Hi * Wi * Cin + 4.0 * B * Hi * Wi * Cout + wsize(s, l));
+    const double bytes = (double)B * Hi * Wi * Cin * act_bytes(s, l) +
+                         4.0 * B * Hi * Wi * Cout * act_bytes(s, l + 1 < NL ? l + 1 : NL - 1) +
+                         4.0 * wsize(s, l) * (s->bf16 ? 2 : 4) / 4.0;
     const float *bias = s->param.as<float>() + s->boff[l];
     if (l == NL - 1) {
-        timed(s, "student.deconv3", flop, bytes, 1, st,
-              [&] { launch_deconv_small(in, B, Hi, Wi, Cin, s->ws.as<float>(), bias, Cout, out, st); });
+        timed(s, "student.deconv3", flop, bytes, 1, st, [&] {
+            launch_deconv_small(static_cast<const float *>(in), B, Hi, Wi, Cin, s->ws.as<float>(), bias, Cout,
+                                static_cast<float *>(out), st);
+        });
         return;
     }
-    timed(s, "student.deconv" + std::to_string(l), flop, bytes, 4, st, [&] {
+    const bool tc = s->bf16;
+    timed(s, "student.deconv" + std::to_string(l) + (tc ? ":tc" : ""), flop, bytes, 4, st, [&] {
         for (int ph = 0; ph < 4; ++ph) {
             const int py = ph >> 1, px = ph & 1;
             ConvDesc d{};
-            d.in = in;
-            d.out = out;
-            d.w = s->wf[l].as<float>() + (int64_t)ph_off(ph) * Cout * Cin;
+            d.in = static_cast<const float *>(in);
+            d.out = static_cast<float *>(out);
             d.bias = bias;
             d.status = s->status.as<uint32_t>();
             d.B = B;
@@ -428,40 +488,35 @@ void forward_layer(lic_student *s, int l, const float *in, int B, int Hi, int Wi
             d.oyo = py;
             d.oxm = 2;
             d.oxo = px;
-            int t = 0;
-            for (int u = py; u < 5; u += 2)
-                for (int v = px; v < 5; v += 2) {
-                    d.du[t] = (int8_t)((py + 2 - u) / 2);
-                    d.dv[t] = (int8_t)((px + 2 - v) / 2);
-                    ++t;
-                }
-            d.T = t;
+            phase_taps(d, py, px);
             d.in_xform = IN_NONE;
             d.epi = EPI_RELU;
-            d.in_dt = d.out_dt = DT_F32;
             d.in_scale = d.out_scale = 1.f;
-            launch_conv_simt(d, st);
+            if (tc) {
+                d.in_dt = DT_BF16;
+                d.out_dt = (l == NL - 2) ? DT_F32 : DT_BF16;
+                if (!tc::launch_lp_map(d, s->fmap[l][ph], st)) s->launch_failed = true;
+            } else {
+                d.w = s->wf[l].as<float>() + (int64_t)ph_off(ph) * Cout * Cin;
+                d.in_dt = d.out_dt = DT_F32;
+                launch_conv_simt(d, st);
+            }
         }
     });
 }
 
-// the student on NHWC y_hat [B][Hy][Wy][M] into NHWC out [B][16Hy][16Wy][3],
-// activations in hbuf[1..3]
-void forward_all(lic_student *s, const float *h0, int B, int Hy, int Wy, DevBuf *hbuf, float *out, cudaStream_t st) {
-    const float *in = h0;
+// the student on NHWC y_hat [B][Hy][Wy][M] (stored as h_0) into NHWC out
+// [B][16Hy][16Wy][3], activations in hbuf[1..3]
+void forward_all(lic_student *s, const void *h0, int B, int Hy, int Wy, DevBuf *hbuf, float *out, cudaStream_t st) {
+    const void *in = h0;
     int H = Hy, W = Wy;
     for (int l = 0; l < NL; ++l) {
-        float *o = l < NL - 1 ? hbuf[l + 1].as<float>() : out;
+        void *o = l < NL - 1 ? hbuf[l + 1].p : out;
         forward_layer(s, l, in, B, H, W, o, st);
         in = o;
         H *= 2;
         W *= 2;
     }
-}
-
-int ensure_f(DevBuf &b, int64_t n) {
-    LIC_CUDA_TRY(b.ensure((size_t)std::max<int64_t>(n, 1) * sizeof(float)));
-    return LIC_OK;
 }
 
 int check_crops(const lic_student *s, const float *yp, const float *xp, int P, int Hy, int Wy, const int32_t *crops,
@@ -480,6 +535,17 @@ int check_crops(const lic_student *s, const float *yp, const float *xp, int P, i
     return LIC_OK;
 }
 
+template <typename TX, typename TD>
+void launch_wgrad(bool vec, dim3 grid, cudaStream_t st, const void *x, const void *dz, int B, int H, int Cin,
+                  int Cout, int64_t kper, float *part) {
+    if (vec)
+        wgrad_kernel<true, TX, TD><<<grid, WG_NT, 0, st>>>(static_cast<const TX *>(x), static_cast<const TD *>(dz), B,
+                                                           H, H, Cin, Cout, kper, part);
+    else
+        wgrad_kernel<false, TX, TD><<<grid, WG_NT, 0, st>>>(static_cast<const TX *>(x), static_cast<const TD *>(dz),
+                                                            B, H, H, Cin, Cout, kper, part);
+}
+
 // forward, loss and every gradient of one batch
 int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, int Wy, const int32_t *crops, int B,
               cudaStream_t st) {
@@ -487,14 +553,18 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
     int rc = check_crops(s, yp, xp, P, Hy, Wy, crops, B, &cr);
     if (rc) return rc;
     s->last_B = B;
+    s->launch_failed = false;
     const int S = s->opt.crop, lc = S / 16, M = s->M;
     // gather
     const int64_t ny = (int64_t)B * lc * lc * M;
-    timed(s, "student.gather", 0, 8.0 * ny, 1, st, [&] {
-        gather_yhat_kernel<<<grid_for(ny, 256), 256, 0, st>>>(yp, M, Hy, Wy, cr, lc, s->h[0].as<float>());
+    timed(s, "student.gather", 0, (4.0 + act_bytes(s, 0)) * ny, 1, st, [&] {
+        if (s->bf16)
+            gather_yhat_kernel<<<grid_for(ny, 256), 256, 0, st>>>(yp, M, Hy, Wy, cr, lc, s->h[0].as<__nv_bfloat16>());
+        else
+            gather_yhat_kernel<<<grid_for(ny, 256), 256, 0, st>>>(yp, M, Hy, Wy, cr, lc, s->h[0].as<float>());
     });
     // forward
-    forward_all(s, s->h[0].as<float>(), B, lc, lc, s->h, s->out.as<float>(), st);
+    forward_all(s, s->h[0].p, B, lc, lc, s->h, s->out.as<float>(), st);
     // loss and dz_3
     const int64_t npix = (int64_t)B * S * S;
     const int nblk = grid_for(npix, RED_T);
@@ -508,8 +578,9 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
     int H = S / 2;   // h_3 resolution
     for (int l = NL - 1; l >= 0; --l) {
         const int Cin = s->cin[l], Cout = s->cout[l];
-        const float *hl = s->h[l].as<float>();
-        const float *dzl = s->dz[l].as<float>();
+        const bool xb = act_bytes(s, l) == 2, db = act_bytes(s, l) == 2 && l < NL - 1;
+        const void *hl = s->h[l].p;
+        const void *dzl = s->dz[l].p;
         const int64_t P_in = (int64_t)B * H * H;      // pixels of h_l
         const int64_t P_out = 4 * P_in;               // pixels of dz_l
         // bias gradient
@@ -517,7 +588,12 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
             const int64_t per = 4096;
             const int nz = (int)((P_out + per - 1) / per);
             timed(s, "student.bgrad" + std::to_string(l), (double)P_out * Cout, 4.0 * P_out * Cout, 2, st, [&] {
-                chan_sum_kernel<<<nz, RED_T, 0, st>>>(dzl, P_out, Cout, per, s->bpart.as<float>());
+                if (db)
+                    chan_sum_kernel<<<nz, RED_T, 0, st>>>(static_cast<const __nv_bfloat16 *>(dzl), P_out, Cout, per,
+                                                          s->bpart.as<float>());
+                else
+                    chan_sum_kernel<<<nz, RED_T, 0, st>>>(static_cast<const float *>(dzl), P_out, Cout, per,
+                                                          s->bpart.as<float>());
                 chan_sum_final_kernel<<<1, 256, 0, st>>>(s->bpart.as<float>(), nz, Cout,
                                                          s->grad.as<float>() + s->boff[l]);
             });
@@ -531,29 +607,35 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
             kper = std::max<int64_t>(WG_BK, (kper + WG_BK - 1) / WG_BK * WG_BK);
             splits = (P_in + kper - 1) / kper;
             const double flop = 2.0 * P_in * (double)Cin * Cout * 25;
-            const double bytes = 4.0 * (P_in * (double)Cin + P_out * (double)Cout + wsize(s, l));
+            const double bytes = P_in * (double)Cin * act_bytes(s, l) + P_out * (double)Cout * act_bytes(s, l) +
+                                 4.0 * wsize(s, l);
             timed(s, "student.wgrad" + std::to_string(l), flop, bytes, 2, st, [&] {
                 dim3 grid(tn, tm, (unsigned)splits);
-                if (Cout % WG_BN == 0)
-                    wgrad_kernel<true><<<grid, WG_NT, 0, st>>>(hl, dzl, B, H, H, Cin, Cout, kper, s->part.as<float>());
+                const bool vec = Cout % WG_BN == 0;
+                float *part = s->part.as<float>();
+                if (xb && db)
+                    launch_wgrad<__nv_bfloat16, __nv_bfloat16>(vec, grid, st, hl, dzl, B, H, Cin, Cout, kper, part);
+                else if (!xb && !db)
+                    launch_wgrad<float, float>(vec, grid, st, hl, dzl, B, H, Cin, Cout, kper, part);
                 else
-                    wgrad_kernel<false><<<grid, WG_NT, 0, st>>>(hl, dzl, B, H, H, Cin, Cout, kper, s->part.as<float>());
+                    s->launch_failed = true;
                 const int64_t ne = (int64_t)Cin * N;
                 wgrad_reduce_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-                    s->part.as<float>(), (int)splits, Cin, Cout, s->grad.as<float>() + s->woff[l]);
+                    part, (int)splits, Cin, Cout, s->grad.as<float>() + s->woff[l]);
             });
         }
         // input gradient through the ReLU: dz_{l-1} = conv5x5/2(dz_l; W_l) * [h_l > 0]
         if (l > 0) {
             const double flop = 2.0 * P_in * (double)Cin * Cout * 25;
-            const double bytes = 4.0 * (P_out * (double)Cout + 2.0 * P_in * Cin + wsize(s, l));
-            timed(s, "student.dgrad" + std::to_string(l), flop, bytes, 1, st, [&] {
+            const double bytes = P_out * (double)Cout * act_bytes(s, l) + 2.0 * P_in * Cin * act_bytes(s, l - 1) +
+                                 4.0 * wsize(s, l);
+            const bool tc = s->bf16 && l < NL - 1;
+            timed(s, "student.dgrad" + std::to_string(l) + (tc ? ":tc" : ""), flop, bytes, 1, st, [&] {
                 ConvDesc d{};
-                d.in = dzl;
-                d.out = s->dz[l - 1].as<float>();
-                d.w = s->wd[l].as<float>();
+                d.in = static_cast<const float *>(dzl);
+                d.out = static_cast<float *>(s->dz[l - 1].p);
                 d.bias = nullptr;
-                d.gdn_x = hl;
+                d.gdn_x = static_cast<const float *>(hl);
                 d.status = s->status.as<uint32_t>();
                 d.B = B;
                 d.Hi = 2 * H;
@@ -575,14 +657,31 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
                     }
                 d.in_xform = IN_NONE;
                 d.epi = EPI_MASK;
-                d.in_dt = d.out_dt = DT_F32;
                 d.in_scale = d.out_scale = 1.f;
-                launch_conv_simt(d, st);
+                d.out_dt = act_bytes(s, l - 1) == 2 ? DT_BF16 : DT_F32;
+                if (tc) {
+                    d.in_dt = DT_BF16;
+                    if (!tc::launch_lp_map(d, s->dmap[l], st)) s->launch_failed = true;
+                } else {
+                    d.in_dt = DT_F32;
+                    d.w = s->wd[l].as<float>();
+                    launch_conv_simt(d, st);
+                }
             });
         }
         H /= 2;
     }
     LIC_CUDA_TRY(cudaGetLastError());
+    return s->launch_failed ? LIC_E_UNSUPPORTED : LIC_OK;
+}
+
+int check_status(lic_student *s) {
+    uint32_t v = 0;
+    LIC_CUDA_TRY(cudaMemcpy(&v, s->status.p, 4, cudaMemcpyDeviceToHost));
+    if (v) {
+        LIC_CUDA_TRY(cudaMemset(s->status.p, 0, 4));
+        return LIC_E_TIMEOUT;
+    }
     return LIC_OK;
 }
 
@@ -590,7 +689,7 @@ int read_loss(lic_student *s, float *loss, cudaStream_t st) {
     if (!loss) return LIC_OK;
     LIC_CUDA_TRY(cudaMemcpyAsync(loss, s->loss.p, sizeof(float), cudaMemcpyDeviceToHost, st));
     LIC_CUDA_TRY(cudaStreamSynchronize(st));
-    return LIC_OK;
+    return check_status(s);
 }
 
 cudaStream_t SS(void *p) { return static_cast<cudaStream_t>(p); }
@@ -603,12 +702,20 @@ int student_channels(const lic_student *s) { return s ? s->M : 0; }
 int student_forward_nhwc(lic_student *s, const float *yhat, int B, int Hy, int Wy, float *out, cudaStream_t st) {
     const int64_t p1 = (int64_t)B * 2 * Hy * 2 * Wy;
     int rc;
-    if ((rc = ensure_f(s->ih[1], p1 * s->C)) || (rc = ensure_f(s->ih[2], 4 * p1 * s->C)) ||
-        (rc = ensure_f(s->ih[3], 16 * p1 * s->C)))
+    if ((rc = ensure_e(s->ih[1], p1 * s->C, act_bytes(s, 1))) || (rc = ensure_e(s->ih[2], 4 * p1 * s->C, act_bytes(s, 2))) ||
+        (rc = ensure_e(s->ih[3], 16 * p1 * s->C, act_bytes(s, 3))))
         return rc;
-    forward_all(s, yhat, B, Hy, Wy, s->ih, out, st);
+    const void *h0 = yhat;
+    if (s->bf16) {
+        const int64_t ny = (int64_t)B * Hy * Wy * s->M;
+        if ((rc = ensure_e(s->ih[0], ny, 2))) return rc;
+        timed(s, "student.to_bf16", 0, 6.0 * ny, 1, st, [&] { launch_to_bf16(yhat, ny, s->ih[0].p, st); });
+        h0 = s->ih[0].p;
+    }
+    s->launch_failed = false;
+    forward_all(s, h0, B, Hy, Wy, s->ih, out, st);
     LIC_CUDA_TRY(cudaGetLastError());
-    return LIC_OK;
+    return s->launch_failed ? LIC_E_UNSUPPORTED : LIC_OK;
 }
 
 void launch_student_check(const float *xs, float *xt, int B, int Hp, int Wp, int H, int W, float thr, double *part,
@@ -627,10 +734,12 @@ using namespace lic;
 int lic_student_create(const lic_weights *init, int M, int C, const lic_student_options *opt, lic_student **out) {
     if (!init || !opt || !out || M < 16 || C < 16 || M % 16 || C % 16 || C > RED_T) return LIC_E_INVALID_ARG;
     *out = nullptr;
-    if (opt->precision != LIC_FP32 || opt->max_batch < 1 || opt->max_batch > LIC_STUDENT_MAX_BATCH ||
-        opt->crop < 32 || opt->crop % 16 || !(opt->lr > 0.f) || !(opt->beta1 >= 0.f && opt->beta1 < 1.f) ||
-        !(opt->beta2 >= 0.f && opt->beta2 < 1.f) || !(opt->eps > 0.f))
+    if ((opt->precision != LIC_FP32 && opt->precision != LIC_BF16) || opt->max_batch < 1 ||
+        opt->max_batch > LIC_STUDENT_MAX_BATCH || opt->crop < 32 || opt->crop % 16 || !(opt->lr > 0.f) ||
+        !(opt->beta1 >= 0.f && opt->beta1 < 1.f) || !(opt->beta2 >= 0.f && opt->beta2 < 1.f) || !(opt->eps > 0.f))
         return LIC_E_INVALID_ARG;
+    // the bf16 tensor-core kernel takes 64-channel chunks and 64 outputs
+    if (opt->precision == LIC_BF16 && (C != 64 || M % 64)) return LIC_E_UNSUPPORTED;
     for (int r : opt->reserved)
         if (r) return LIC_E_INVALID_ARG;
     auto s = new (std::nothrow) lic_student();
@@ -638,6 +747,7 @@ int lic_student_create(const lic_weights *init, int M, int C, const lic_student_
     s->M = M;
     s->C = C;
     s->opt = *opt;
+    s->bf16 = opt->precision == LIC_BF16;
     cudaGetDevice(&s->device);
     const int ch[5] = {M, C, C, C, 3};
     std::vector<float> host;
@@ -669,45 +779,61 @@ int lic_student_create(const lic_weights *init, int M, int C, const lic_student_
             memcpy(host.data() + (which ? s->boff[l] : s->woff[l]), src, (size_t)want * sizeof(float));
         }
     }
-    auto alloc = [&](DevBuf &b, int64_t n) { return ensure_f(b, n); };
     int rc;
     const int64_t np = s->nparam;
-    if ((rc = alloc(s->param, np)) || (rc = alloc(s->grad, np)) || (rc = alloc(s->adam_m, np)) ||
-        (rc = alloc(s->adam_v, np)))
+    if ((rc = ensure_f(s->param, np)) || (rc = ensure_f(s->grad, np)) || (rc = ensure_f(s->adam_m, np)) ||
+        (rc = ensure_f(s->adam_v, np)))
         return fail(rc);
     if (cudaMemcpy(s->param.p, host.data(), np * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(s->grad.p, 0, np * sizeof(float)) != cudaSuccess ||
         cudaMemset(s->adam_m.p, 0, np * sizeof(float)) != cudaSuccess ||
         cudaMemset(s->adam_v.p, 0, np * sizeof(float)) != cudaSuccess)
         return fail(LIC_E_CUDA);
-    for (int l = 0; l < NL - 1; ++l)
-        if ((rc = alloc(s->wf[l], wsize(s, l)))) return fail(rc);
-    for (int l = 1; l < NL; ++l)
-        if ((rc = alloc(s->wd[l], wsize(s, l)))) return fail(rc);
-    if ((rc = alloc(s->ws, (int64_t)s->cin[3] * 25 * 4))) return fail(rc);
+    for (int l = 0; l < NL - 1; ++l) {
+        if (!s->bf16) {
+            if ((rc = ensure_f(s->wf[l], wsize(s, l)))) return fail(rc);
+            continue;
+        }
+        if ((rc = ensure_e(s->wfb[l], wsize(s, l), 2))) return fail(rc);
+        for (int ph = 0; ph < 4; ++ph) {
+            const void *base = s->wfb[l].as<__nv_bfloat16>() + (int64_t)ph_off(ph) * s->cout[l] * s->cin[l];
+            if (!tc::make_bf16_weight_map(&s->fmap[l][ph], base, s->cout[l], ph_taps(ph) * s->cin[l]))
+                return fail(LIC_E_UNSUPPORTED);
+        }
+    }
+    for (int l = 1; l < NL; ++l) {
+        if (s->bf16 && l < NL - 1) {
+            if ((rc = ensure_e(s->wdb[l], wsize(s, l), 2))) return fail(rc);
+            if (!tc::make_bf16_weight_map(&s->dmap[l], s->wdb[l].p, s->cin[l], 25 * s->cout[l]))
+                return fail(LIC_E_UNSUPPORTED);
+        } else if ((rc = ensure_f(s->wd[l], wsize(s, l)))) {
+            return fail(rc);
+        }
+    }
+    if ((rc = ensure_f(s->ws, (int64_t)s->cin[3] * 25 * 4))) return fail(rc);
     if (cudaMemset(s->ws.p, 0, s->ws.bytes) != cudaSuccess) return fail(LIC_E_CUDA);
     // training workspace
     const int Bm = opt->max_batch, S = opt->crop;
     int64_t side = S / 16;
-    if ((rc = alloc(s->h[0], Bm * side * side * M))) return fail(rc);
+    if ((rc = ensure_e(s->h[0], Bm * side * side * M, act_bytes(s, 0)))) return fail(rc);
     for (int l = 1; l < NL; ++l) {
         side *= 2;
-        if ((rc = alloc(s->h[l], Bm * side * side * C))) return fail(rc);
+        if ((rc = ensure_e(s->h[l], Bm * side * side * C, act_bytes(s, l)))) return fail(rc);
     }
     side = S / 16;
     int64_t part_max = 0;
     for (int l = 0; l < NL; ++l) {
         side *= 2;   // dz_l lives at layer l's output resolution
-        if ((rc = alloc(s->dz[l], Bm * side * side * s->cout[l]))) return fail(rc);
+        if ((rc = ensure_e(s->dz[l], Bm * side * side * s->cout[l], act_bytes(s, l)))) return fail(rc);
         const int N = 25 * s->cout[l];
         const int tiles = ((N + WG_BN - 1) / WG_BN) * ((s->cin[l] + WG_BM - 1) / WG_BM);
         const int64_t P_in = Bm * (side / 2) * (side / 2);
         const int64_t splits = std::min<int64_t>(std::max<int64_t>(1, (4 * 148) / tiles), (P_in + WG_BK - 1) / WG_BK);
         part_max = std::max<int64_t>(part_max, (splits + 1) * (int64_t)s->cin[l] * N);
     }
-    if ((rc = alloc(s->out, (int64_t)Bm * S * S * 3)) || (rc = alloc(s->part, part_max)) ||
-        (rc = alloc(s->bpart, ((int64_t)Bm * S * S + 4095) / 4096 * RED_T + RED_T)) ||
-        (rc = alloc(s->loss, 1)))
+    if ((rc = ensure_f(s->out, (int64_t)Bm * S * S * 3)) || (rc = ensure_f(s->part, part_max)) ||
+        (rc = ensure_f(s->bpart, ((int64_t)Bm * S * S + 4095) / 4096 * RED_T + RED_T)) ||
+        (rc = ensure_f(s->loss, 1)))
         return fail(rc);
     if (s->lpart.ensure(sizeof(double) * 148 * 16) != cudaSuccess || s->status.ensure(16) != cudaSuccess)
         return fail(LIC_E_OOM);
@@ -782,7 +908,16 @@ int lic_student_read_activation(lic_student *s, int layer, float *dst, int64_t n
     const int64_t side = (int64_t)(s->opt.crop >> (4 - layer));
     if (numel != (int64_t)s->last_B * side * side * s->C) return LIC_E_INVALID_ARG;
     LIC_CUDA_TRY(cudaDeviceSynchronize());
-    LIC_CUDA_TRY(cudaMemcpy(dst, s->h[layer].p, (size_t)numel * sizeof(float), cudaMemcpyDeviceToHost));
+    if (act_bytes(s, layer) == 4) {
+        LIC_CUDA_TRY(cudaMemcpy(dst, s->h[layer].p, (size_t)numel * sizeof(float), cudaMemcpyDeviceToHost));
+        return LIC_OK;
+    }
+    std::vector<uint16_t> raw((size_t)numel);
+    LIC_CUDA_TRY(cudaMemcpy(raw.data(), s->h[layer].p, (size_t)numel * 2, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < numel; ++i) {
+        const uint32_t u = (uint32_t)raw[i] << 16;
+        memcpy(dst + i, &u, 4);
+    }
     return LIC_OK;
 }
 
@@ -793,23 +928,25 @@ int lic_student_forward(lic_student *s, const float *yhat, int B, int Hy, int Wy
     cudaStream_t st = SS(stream);
     const int64_t ny = (int64_t)B * s->M * Hy * Wy, nx = (int64_t)B * 3 * 256 * Hy * Wy;
     int rc;
-    if ((rc = ensure_f(s->ih[0], ny)) || (rc = ensure_f(s->iout, 2 * nx))) return rc;
+    if ((rc = ensure_f(s->iout, 2 * nx + ny))) return rc;
     const bool dy = is_device_ptr(yhat), dx = is_device_ptr(x);
+    float *nhwc_y = s->iout.as<float>() + 2 * nx;   // y_hat NHWC
     const float *ysrc = yhat;
-    float *stage = s->iout.as<float>() + nx;   // NCHW staging next to the NHWC output
+    float *stage = s->iout.as<float>() + nx;        // NCHW staging next to the NHWC output
     if (!dy) {
         LIC_CUDA_TRY(cudaMemcpyAsync(stage, yhat, (size_t)ny * sizeof(float), cudaMemcpyHostToDevice, st));
         ysrc = stage;
     }
     timed(s, "student.nchw_to_nhwc", 0, 8.0 * ny, 1, st,
-          [&] { launch_nchw_to_nhwc(ysrc, B, s->M, Hy, Wy, s->ih[0].as<float>(), st); });
-    if ((rc = student_forward_nhwc(s, s->ih[0].as<float>(), B, Hy, Wy, s->iout.as<float>(), st))) return rc;
+          [&] { launch_nchw_to_nhwc(ysrc, B, s->M, Hy, Wy, nhwc_y, st); });
+    if ((rc = student_forward_nhwc(s, nhwc_y, B, Hy, Wy, s->iout.as<float>(), st))) return rc;
     float *dst = dx ? x : stage;
     timed(s, "student.nhwc_to_nchw", 0, 8.0 * nx, 1, st,
           [&] { launch_nhwc_to_nchw(s->iout.as<float>(), B, 16 * Hy, 16 * Wy, 3, dst, st); });
     if (!dx) {
         LIC_CUDA_TRY(cudaMemcpyAsync(x, stage, (size_t)nx * sizeof(float), cudaMemcpyDeviceToHost, st));
         LIC_CUDA_TRY(cudaStreamSynchronize(st));
+        if ((rc = check_status(s))) return rc;
     }
     LIC_CUDA_TRY(cudaGetLastError());
     return LIC_OK;

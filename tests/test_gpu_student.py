@@ -189,3 +189,92 @@ def test_decode_with_student(SW):
     assert torch.equal(back, teacher)
     codec.close()
     st.close()
+
+
+# ---------------------------------------------------------------------------
+# BF16 form: the 64-channel transposed convs and their input gradients on the
+# tcgen05 bf16 kernel, bf16 storage of y_hat, h_1, h_2, dz_0..dz_2
+# ---------------------------------------------------------------------------
+
+def bf16(a):
+    """Round float values to bfloat16 (nearest even), returned as float64."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_student_forward(P, yhat):
+    """The BF16 form's forward pass as defined: bf16 y_hat, bf16 weights of the
+    three 64-channel layers, bf16 storage of h_1 and h_2, float h_3 and a
+    float 3-channel layer (the oracle's float64 arithmetic in between)."""
+    h = bf16(yhat)
+    for l in range(4):
+        w = P[f"student.deconv{l}.weight"]
+        z = O.deconv2d(h, bf16(w) if l < 3 else w, P[f"student.deconv{l}.bias"], 2)
+        if l == 3:
+            return z
+        h = O.relu(z)
+        if l < 2:
+            h = bf16(h)
+
+
+def test_bf16_student_forward_matches_its_definition(SW):
+    r = np.random.default_rng(13)
+    yhat = np.rint(r.standard_normal((2, M, 6, 9)) * 2).astype(np.float32)
+    st = lic.Student(SW, M, C, max_batch=1, crop=32, precision=lic.BF16)
+    x = torch.empty(2, 3, 96, 144, device="cuda")
+    st.forward(torch.from_numpy(yhat).cuda(), x)
+    torch.cuda.synchronize()
+    got = x.cpu().numpy()
+    want = bf16_student_forward(SW, yhat)
+    assert np.abs(got - want).max() <= 2e-3
+    # against the float64 student: the error bf16 storage costs
+    _, exact = O.student_forward(SW, yhat)
+    assert np.abs(got - exact).max() <= 5e-2
+    st.close()
+
+
+def test_bf16_student_gradients_close_to_oracle(SW):
+    """BF16 gradients against the float64 chain rule (taking the GPU's ReLU
+    decisions): relative L2 error of every tensor below 3e-2, loss within
+    1e-2; an index or sign mistake anywhere gives O(1)."""
+    yp, xp = pools(2, 8, 10, seed=1)
+    crops = np.array([[0, 0, 0], [1, 2, 4], [1, 1, 3]], np.int32)
+    st = lic.Student(SW, M, C, max_batch=4, crop=96, precision=lic.BF16)
+    loss = st.grad(torch.from_numpy(yp).cuda(), torch.from_numpy(xp).cuda(), crops)
+    ys, xs = O.student_crops(yp, xp, crops, 96)
+    masks = {l: st.activation(l, 3).transpose(0, 3, 1, 2) > 0 for l in (1, 2, 3)}
+    oloss, ograds = O.student_loss_grads(SW, ys, xs, masks=masks)
+    assert abs(loss - oloss) <= 1e-2 * oloss
+    for name, og in ograds.items():
+        g = st.read(name, lic.STUDENT_GRAD)
+        rel = np.linalg.norm(g - og) / np.linalg.norm(og)
+        assert rel <= 3e-2, (name, rel)
+    st.close()
+
+
+def test_bf16_student_training_and_decode(SW):
+    yp, xp = pools(1, 8, 8, seed=4)
+    crops = np.array([[0, 0, 0], [0, 2, 2]], np.int32)
+    st = lic.Student(SW, M, C, max_batch=2, crop=96, lr=1e-3, precision=lic.BF16)
+    dy, dx = torch.from_numpy(yp).cuda(), torch.from_numpy(xp).cuda()
+    l0 = st.grad(dy, dx, crops)
+    for _ in range(30):
+        st.step(dy, dx, crops)
+    assert st.grad(dy, dx, crops) < 0.7 * l0
+    # the decoder running this student returns its forward pass, clamped and cropped
+    W = synth.make_weights(0, 128, M)
+    codec = lic.Codec(0, 128, M, W)
+    x = synth.make_frames(2, 120, 100, first=21)
+    bs = codec.encode(torch.from_numpy(x).cuda())
+    codec.set_student(st)
+    got = torch.empty(2, 3, 120, 100, device="cuda")
+    codec.decode(bs, 120, 100, got)
+    yhat = torch.empty(2, M, 8, 8, device="cuda")
+    codec.read_tensor(lic.T_YHAT, yhat)
+    ref = torch.empty(2, 3, 128, 128, device="cuda")
+    st.forward(yhat, ref)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref.clamp(0, 1)[:, :, :120, :100])
+    codec.close()
+    st.close()
