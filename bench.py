@@ -398,7 +398,7 @@ def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws
         teacher.read_tensor(lic.T_XPRE, pool_x[i:i + 8])
     teacher.close()
     st = lic.Student(synth.make_student_weights(M_CH, STUDENT_C), M_CH, STUDENT_C, max_batch=STUDENT_BATCH,
-                     crop=STUDENT_CROP, lr=1e-4)
+                     crop=STUDENT_CROP, lr=1e-4, precision=lic.BF16)
     steps = args.student_steps
     crops = [synth.draw_crops(k, STUDENT_BATCH, STUDENT_POOL, Hy, Wy, STUDENT_CROP // 16) for k in range(steps)]
     probe = synth.draw_crops(10 ** 6, STUDENT_BATCH, STUDENT_POOL, Hy, Wy, STUDENT_CROP // 16)
@@ -427,8 +427,13 @@ def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws
     train_flop = sum(r["flop"] for r in rep if r["name"] != "student.adam")
     top = max(rep, key=lambda r: r["ms"])
     sm_mhz = peaks.get("sm_max_mhz", 2032.0)
-    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
     top_ach = top["flop"] / top["launches"] / (top["ms"] / top["launches"] * 1e-3) / 1e12
+    if top["name"].endswith(":tc"):
+        top_peak, top_bound = peaks.get("bf16_tflops", 1800.0), "tensor"
+        top_note = "bf16 tcgen05 kernel against the measured dense BF16 peak"
+    else:
+        top_peak, top_bound = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12, "alu"
+        top_note = "CUDA-core FP32 FMA peak: 148 SMs x 128 lanes x 2 x max SM clock"
 
     # the hyperprior codec decoding with the student: checked (per-frame PSNR vs the teacher), then timed
     codec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt)
@@ -469,12 +474,13 @@ def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws
                   "launches_per_step": launches_per_step,
                   "probe_loss_before": loss0, "probe_loss_after": loss1,
                   "pool": f"{STUDENT_POOL} seeded 1280x720 frames through the factorized N=128 M=192 codec"},
-        "roofline": {"kernel": top["name"], "bound": "alu", "achieved": top_ach, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": top_ach / fp32_peak, "traffic": None,
-                     "note": "CUDA-core FP32 FMA peak: 148 SMs x 128 lanes x 2 x max SM clock"},
+        "roofline": {"kernel": top["name"], "bound": top_bound, "achieved": top_ach, "peak": top_peak,
+                     "unit": "TFLOP/s", "frac": top_ach / top_peak, "traffic": None, "note": top_note},
         "kernels": rep,
-        "note": "student g_s (4 transposed convs 192->64->64->64->3, ReLU, no IGDN), FP32 CUDA-core kernels, "
-                "trained on the GPU, decoding the hyperprior codec in place of g_s",
+        "note": "student g_s (4 transposed convs 192->64->64->64->3, ReLU, no IGDN), BF16 form: the 64-channel "
+                "convs and their input gradients on tcgen05 (bf16 x bf16 -> fp32), weight/bias gradients, the "
+                "3-channel layer and Adam in fp32 on CUDA cores; trained on the GPU, decoding the hyperprior "
+                "codec in place of g_s",
     }
 
 

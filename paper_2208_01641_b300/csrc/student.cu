@@ -86,6 +86,7 @@ __global__ void gather_yhat_kernel(const float *__restrict__ pool, int M, int Hy
 }
 
 constexpr int RED_T = 256;
+constexpr int BG_BLOCKS = 4 * 148;   // blocks of a bias-gradient reduction
 
 // out NHWC [B][S][S][3] against the target crops of xpool NCHW
 // [P][3][Hx][Wx]: dz = (2/n) (out - x); per block the float64 sum of
@@ -583,9 +584,9 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
         const void *dzl = s->dz[l].p;
         const int64_t P_in = (int64_t)B * H * H;      // pixels of h_l
         const int64_t P_out = 4 * P_in;               // pixels of dz_l
-        // bias gradient
+        // bias gradient: pixel slices sized so that about 4 x 148 blocks run
         {
-            const int64_t per = 4096;
+            const int64_t per = std::max<int64_t>(64, (P_out + BG_BLOCKS - 1) / BG_BLOCKS);
             const int nz = (int)((P_out + per - 1) / per);
             timed(s, "student.bgrad" + std::to_string(l), (double)P_out * Cout, 4.0 * P_out * Cout, 2, st, [&] {
                 if (db)
@@ -832,7 +833,7 @@ int lic_student_create(const lic_weights *init, int M, int C, const lic_student_
         part_max = std::max<int64_t>(part_max, (splits + 1) * (int64_t)s->cin[l] * N);
     }
     if ((rc = ensure_f(s->out, (int64_t)Bm * S * S * 3)) || (rc = ensure_f(s->part, part_max)) ||
-        (rc = ensure_f(s->bpart, ((int64_t)Bm * S * S + 4095) / 4096 * RED_T + RED_T)) ||
+        (rc = ensure_f(s->bpart, (int64_t)(BG_BLOCKS + 1) * RED_T)) ||
         (rc = ensure_f(s->loss, 1)))
         return fail(rc);
     if (s->lpart.ensure(sizeof(double) * 148 * 16) != cudaSuccess || s->status.ensure(16) != cudaSuccess)
