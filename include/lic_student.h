@@ -43,7 +43,8 @@ typedef struct {
     int max_batch;   /* crops per training step, 1 .. LIC_STUDENT_MAX_BATCH */
     int crop;        /* crop side in output pixels, a multiple of 16, >= 32 */
     float lr, beta1, beta2, eps;   /* Adam hyper-parameters */
-    int reserved[4];               /* must be 0 */
+    int halo;        /* latent rows/columns of context around each crop, 0 .. 8 */
+    int reserved[3];               /* must be 0 */
 } lic_student_options;
 
 /* Create a student with M latent channels and C hidden channels from the
@@ -60,13 +61,15 @@ void lic_student_destroy(lic_student *student);
  * yhat_pool: device NCHW [P, M, Hy, Wy]; xhat_pool: device NCHW
  * [P, 3, 16 Hy, 16 Wy], the teacher's g_s output for that pool (both
  * caller-owned, read only).  crops: host int32 [B, 3] of (frame, row, col)
- * in latent units; crop b takes the (crop/16)-square latent window at
- * (row, col) of frame `frame` and the crop-square target window at
- * (16 row, 16 col); every window must lie inside the pool (else
- * LIC_E_INVALID_ARG, nothing launched).  B <= max_batch.
- * The loss is mean((student(y) - x)^2) over the B x 3 x crop x crop target
- * values; when `loss` is non-null the call waits for the stream and writes
- * it there (host float). */
+ * in latent units.  Crop b runs the student on the L-square latent window
+ * at (row, col) of frame `frame`, L = crop/16 + 2 halo, and compares the
+ * central crop-square of its output with the target window at
+ * (16 (row + halo), 16 (col + halo)): with halo > 0 the student sees the
+ * latents around the crop that the teacher's output there depends on.
+ * Every window must lie inside the pool (else LIC_E_INVALID_ARG, nothing
+ * launched).  B <= max_batch.  The loss is mean((student(y) - x)^2) over
+ * the B x 3 x crop x crop target values; when `loss` is non-null the call
+ * waits for the stream and writes it there (host float). */
 int lic_student_grad(lic_student *student, const float *yhat_pool, const float *xhat_pool, int P, int Hy, int Wy,
                      const int32_t *crops, int B, float *loss, void *stream);
 
@@ -90,7 +93,7 @@ typedef enum {
 int lic_student_read(lic_student *student, const char *name, int what, float *dst, int64_t numel);
 
 /* Diagnostics: the post-ReLU activation h_layer (layer 1..3) of the last
- * lic_student_grad/step batch, NHWC [B, crop/2^(4-layer), same, C] float32,
+ * lic_student_grad/step batch, NHWC [B, 16 L/2^(4-layer), same, C] float32,
  * copied to the host buffer dst of numel elements (must equal that size for
  * the batch's B).  Synchronous. */
 int lic_student_read_activation(lic_student *student, int layer, float *dst, int64_t numel);

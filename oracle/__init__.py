@@ -554,9 +554,14 @@ def student_loss_grads(P, yhat, target, masks=None):
     may fall either way); by default h_l > 0 of this forward pass."""
     hs, out = student_forward(P, yhat)
     t = _f64(target)
-    n = out.size
-    loss = float(np.mean((out - t) ** 2))
-    g = 2.0 * (out - t) / n
+    # the loss covers the central target-sized square of the output (all of
+    # it when the sizes agree); the gradient is zero outside it
+    o = (out.shape[-1] - t.shape[-1]) // 2
+    core = out[:, :, o:o + t.shape[-2], o:o + t.shape[-1]]
+    n = t.size
+    loss = float(np.mean((core - t) ** 2))
+    g = np.zeros_like(out)
+    g[:, :, o:o + t.shape[-2], o:o + t.shape[-1]] = 2.0 * (core - t) / n
     grads = {}
     for l in range(3, -1, -1):
         w = _f64(P[f"student.deconv{l}.weight"])
@@ -582,13 +587,15 @@ def adam_step(P, G, m, v, t, lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8):
         P[k] = _f64(P[k]) - lr * mh / (np.sqrt(vh) + eps)
 
 
-def student_crops(yhat_pool, xhat_pool, crops, crop):
+def student_crops(yhat_pool, xhat_pool, crops, crop, halo=0):
     """A training batch: for each (frame, row, col) in latent units, the
-    crop/16-square latent window of y_hat and the crop-square window of x_hat
-    at 16x those coordinates."""
-    lc = crop // 16
+    latent window of side crop/16 + 2 halo at (row, col) of y_hat, and the
+    crop-square window of x_hat at 16 (row + halo), 16 (col + halo) -- the
+    pixels the central crop of the window's output covers."""
+    lc = crop // 16 + 2 * halo
     ys = np.stack([yhat_pool[f, :, r:r + lc, c:c + lc] for f, r, c in crops])
-    xs = np.stack([xhat_pool[f, :, 16 * r:16 * r + crop, 16 * c:16 * c + crop] for f, r, c in crops])
+    xs = np.stack([xhat_pool[f, :, 16 * (r + halo):16 * (r + halo) + crop, 16 * (c + halo):16 * (c + halo) + crop]
+                   for f, r, c in crops])
     return ys, xs
 
 

@@ -76,7 +76,7 @@ class _Options(ctypes.Structure):
 class _StudentOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_batch", ctypes.c_int), ("crop", ctypes.c_int),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
-                ("eps", ctypes.c_float), ("reserved", ctypes.c_int * 4)]
+                ("eps", ctypes.c_float), ("halo", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class _ServerOptions(ctypes.Structure):
@@ -434,11 +434,11 @@ class Student:
 
     def __init__(self, weights: Dict[str, np.ndarray], M: int = 192, C: int = 64, max_batch: int = 16,
                  crop: int = 256, lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
-                 precision: int = FP32):
-        self.M, self.C, self.crop = M, C, crop
+                 precision: int = FP32, halo: int = 0):
+        self.M, self.C, self.crop, self.halo = M, C, crop, halo
         self.shapes = {k: tuple(np.shape(v)) for k, v in weights.items() if k.startswith("student.")}
         w, keep = _weights_struct(weights)
-        opt = _StudentOptions(precision, max_batch, crop, lr, beta1, beta2, eps)
+        opt = _StudentOptions(precision, max_batch, crop, lr, beta1, beta2, eps, halo)
         h = ctypes.c_void_p()
         _check(_lib().lic_student_create(ctypes.byref(w), M, C, ctypes.byref(opt), ctypes.byref(h)),
                "lic_student_create")
@@ -480,7 +480,7 @@ class Student:
 
     def activation(self, layer: int, B: int) -> np.ndarray:
         """Post-ReLU h_layer of the last training batch, NHWC."""
-        side = self.crop >> (4 - layer)
+        side = (self.crop + 32 * self.halo) >> (4 - layer)
         out = np.zeros((B, side, side, self.C), np.float32)
         _check(_lib().lic_student_read_activation(self.h, layer, _ptr(out), out.size),
                "lic_student_read_activation")

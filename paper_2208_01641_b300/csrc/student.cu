@@ -88,13 +88,14 @@ __global__ void gather_yhat_kernel(const float *__restrict__ pool, int M, int Hy
 constexpr int RED_T = 256;
 constexpr int BG_BLOCKS = 4 * 148;   // blocks of a bias-gradient reduction
 
-// out NHWC [B][S][S][3] against the target crops of xpool NCHW
-// [P][3][Hx][Wx]: dz = (2/n) (out - x); per block the float64 sum of
-// (out - x)^2 over its pixels (fixed tree)
+// out NHWC [B][S][S][3] (the net's output on the latent windows) against
+// the target crops of xpool NCHW [P][3][Hx][Wx]: inside the loss square
+// [o, o + crop)^2, dz = (2/n) (out - x), outside dz = 0; per block the
+// float64 sum of (out - x)^2 over its loss pixels (fixed tree)
 __global__ void __launch_bounds__(RED_T) mse_grad_kernel(const float *__restrict__ out,
                                                          const float *__restrict__ xpool, int Hx, int Wx, Crops cr,
-                                                         int S, float two_over_n, float *__restrict__ dz,
-                                                         double *__restrict__ part) {
+                                                         int S, int o, int crop, float two_over_n,
+                                                         float *__restrict__ dz, double *__restrict__ part) {
     __shared__ double red[RED_T];
     const int64_t npix = (int64_t)cr.n * S * S;
     double acc = 0.0;
@@ -102,11 +103,15 @@ __global__ void __launch_bounds__(RED_T) mse_grad_kernel(const float *__restrict
         const int x = (int)(p % S);
         const int y = (int)((p / S) % S);
         const int b = (int)(p / ((int64_t)S * S));
+        const bool in = y >= o && y < o + crop && x >= o && x < o + crop;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float t =
-                xpool[(((int64_t)cr.f[b] * 3 + k) * Hx + 16 * cr.r[b] + y) * Wx + 16 * cr.c[b] + x];
-            const float d = out[p * 3 + k] - t;
+            float d = 0.f;
+            if (in) {
+                const float t =
+                    xpool[(((int64_t)cr.f[b] * 3 + k) * Hx + 16 * cr.r[b] + y) * Wx + 16 * cr.c[b] + x];
+                d = out[p * 3 + k] - t;
+            }
             dz[p * 3 + k] = two_over_n * d;
             acc += (double)d * (double)d;
         }
@@ -520,9 +525,12 @@ void forward_all(lic_student *s, const void *h0, int B, int Hy, int Wy, DevBuf *
     }
 }
 
+// latent side of one training window: the crop's latents plus the halo
+int window_lat(const lic_student *s) { return s->opt.crop / 16 + 2 * s->opt.halo; }
+
 int check_crops(const lic_student *s, const float *yp, const float *xp, int P, int Hy, int Wy, const int32_t *crops,
                 int B, Crops *cr) {
-    const int lc = s->opt.crop / 16;
+    const int lc = window_lat(s);
     if (!yp || !xp || !crops || P < 1 || B < 1 || B > s->opt.max_batch || Hy < lc || Wy < lc) return LIC_E_INVALID_ARG;
     if (!is_device_ptr(yp) || !is_device_ptr(xp)) return LIC_E_INVALID_ARG;
     cr->n = B;
@@ -555,7 +563,7 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
     if (rc) return rc;
     s->last_B = B;
     s->launch_failed = false;
-    const int S = s->opt.crop, lc = S / 16, M = s->M;
+    const int lc = window_lat(s), S = 16 * lc, M = s->M;
     // gather
     const int64_t ny = (int64_t)B * lc * lc * M;
     timed(s, "student.gather", 0, (4.0 + act_bytes(s, 0)) * ny, 1, st, [&] {
@@ -569,10 +577,11 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
     // loss and dz_3
     const int64_t npix = (int64_t)B * S * S;
     const int nblk = grid_for(npix, RED_T);
-    const double n = 3.0 * npix;
+    const double n = 3.0 * B * s->opt.crop * s->opt.crop;   // values inside the loss squares
     timed(s, "student.mse", 3.0 * n, 12.0 * n, 2, st, [&] {
-        mse_grad_kernel<<<nblk, RED_T, 0, st>>>(s->out.as<float>(), xp, 16 * Hy, 16 * Wy, cr, S, (float)(2.0 / n),
-                                                s->dz[3].as<float>(), s->lpart.as<double>());
+        mse_grad_kernel<<<nblk, RED_T, 0, st>>>(s->out.as<float>(), xp, 16 * Hy, 16 * Wy, cr, S, 16 * s->opt.halo,
+                                                s->opt.crop, (float)(2.0 / n), s->dz[3].as<float>(),
+                                                s->lpart.as<double>());
         mse_final_kernel<<<1, RED_T, 0, st>>>(s->lpart.as<double>(), nblk, n, s->loss.as<float>());
     });
     // backward, l = 3 .. 0
@@ -736,7 +745,8 @@ int lic_student_create(const lic_weights *init, int M, int C, const lic_student_
     if (!init || !opt || !out || M < 16 || C < 16 || M % 16 || C % 16 || C > RED_T) return LIC_E_INVALID_ARG;
     *out = nullptr;
     if ((opt->precision != LIC_FP32 && opt->precision != LIC_BF16) || opt->max_batch < 1 ||
-        opt->max_batch > LIC_STUDENT_MAX_BATCH || opt->crop < 32 || opt->crop % 16 || !(opt->lr > 0.f) ||
+        opt->max_batch > LIC_STUDENT_MAX_BATCH || opt->crop < 32 || opt->crop % 16 || opt->halo < 0 ||
+        opt->halo > 8 || !(opt->lr > 0.f) ||
         !(opt->beta1 >= 0.f && opt->beta1 < 1.f) || !(opt->beta2 >= 0.f && opt->beta2 < 1.f) || !(opt->eps > 0.f))
         return LIC_E_INVALID_ARG;
     // the bf16 tensor-core kernel takes 64-channel chunks and 64 outputs
@@ -814,7 +824,7 @@ int lic_student_create(const lic_weights *init, int M, int C, const lic_student_
     if ((rc = ensure_f(s->ws, (int64_t)s->cin[3] * 25 * 4))) return fail(rc);
     if (cudaMemset(s->ws.p, 0, s->ws.bytes) != cudaSuccess) return fail(LIC_E_CUDA);
     // training workspace
-    const int Bm = opt->max_batch, S = opt->crop;
+    const int Bm = opt->max_batch, S = 16 * window_lat(s);
     int64_t side = S / 16;
     if ((rc = ensure_e(s->h[0], Bm * side * side * M, act_bytes(s, 0)))) return fail(rc);
     for (int l = 1; l < NL; ++l) {
@@ -906,7 +916,7 @@ int lic_student_read(lic_student *s, const char *name, int what, float *dst, int
 
 int lic_student_read_activation(lic_student *s, int layer, float *dst, int64_t numel) {
     if (!s || !dst || layer < 1 || layer > 3 || s->last_B < 1) return LIC_E_INVALID_ARG;
-    const int64_t side = (int64_t)(s->opt.crop >> (4 - layer));
+    const int64_t side = (int64_t)((16 * window_lat(s)) >> (4 - layer));
     if (numel != (int64_t)s->last_B * side * side * s->C) return LIC_E_INVALID_ARG;
     LIC_CUDA_TRY(cudaDeviceSynchronize());
     if (act_bytes(s, layer) == 4) {

@@ -80,7 +80,8 @@ def test_student_create_validates_arguments_before_device_work():
     parameters with LIC_E_INVALID_ARG (no device needed to reach the check)."""
     W = synth.make_student_weights()
     bad_opts = (dict(max_batch=0), dict(max_batch=lic.STUDENT_MAX_BATCH + 1), dict(crop=40), dict(crop=16),
-                dict(lr=0.0), dict(beta1=1.0), dict(eps=0.0), dict(precision=lic.BF16))
+                dict(lr=0.0), dict(beta1=1.0), dict(eps=0.0), dict(precision=lic.FP8), dict(halo=-1),
+                dict(halo=9))
     for kw in bad_opts:
         with pytest.raises(lic.LicError) as e:
             lic.Student(W, **kw)

@@ -278,3 +278,28 @@ def test_bf16_student_training_and_decode(SW):
     assert torch.equal(got, ref.clamp(0, 1)[:, :, :120, :100])
     codec.close()
     st.close()
+
+
+@pytest.mark.parametrize("precision", [lic.FP32, lic.BF16])
+def test_student_halo_window_gradients(SW, precision):
+    """halo = 1: the student runs on 8 x 8 latent windows, the loss covers the
+    central 96 x 96 output pixels (zero gradient outside)."""
+    yp, xp = pools(2, 9, 10, seed=8)
+    crops = np.array([[0, 0, 0], [1, 1, 2]], np.int32)
+    st = lic.Student(SW, M, C, max_batch=2, crop=96, halo=1, precision=precision)
+    loss = st.grad(torch.from_numpy(yp).cuda(), torch.from_numpy(xp).cuda(), crops)
+    ys, xs = O.student_crops(yp, xp, crops, 96, halo=1)
+    assert ys.shape[-1] == 8 and xs.shape[-1] == 96
+    masks = {l: st.activation(l, 2).transpose(0, 3, 1, 2) > 0 for l in (1, 2, 3)}
+    oloss, ograds = O.student_loss_grads(SW, ys, xs, masks=masks)
+    tol = 1e-5 if precision == lic.FP32 else 1e-2
+    assert abs(loss - oloss) <= tol * oloss
+    for name, og in ograds.items():
+        g = st.read(name, lic.STUDENT_GRAD)
+        if precision == lic.FP32:
+            assert np.abs(g - og).max() <= 1e-4 * np.abs(og).max() + 1e-9, name
+        else:
+            assert np.linalg.norm(g - og) / np.linalg.norm(og) <= 3e-2, name
+    with pytest.raises(lic.LicError):   # the window must fit: 2 + 8 > 9 rows
+        st.grad(torch.from_numpy(yp).cuda(), torch.from_numpy(xp).cuda(), np.array([[0, 2, 0]], np.int32))
+    st.close()

@@ -490,3 +490,26 @@ def test_student_training_decreases_loss():
         loss, grads = O.student_loss_grads(P, yhat, target)
         O.adam_step(P, grads, m, v, t, lr=1e-2)
     assert O.student_loss_grads(P, yhat, target)[0] < 0.5 * l0
+
+
+def test_student_loss_window_matches_finite_differences():
+    """With a latent halo the output (80 x 80 here) is larger than the target
+    (48 x 48): the loss covers the central square only, and its gradient --
+    zero outside that square -- still matches central differences."""
+    P = _tiny_student(seed=5)
+    r = np.random.default_rng(6)
+    yhat = r.standard_normal((2, 5, 5, 5))
+    target = r.standard_normal((2, 3, 48, 48))
+    loss, grads = O.student_loss_grads(P, yhat, target)
+    _, out = O.student_forward(P, yhat)
+    assert abs(loss - np.mean((out[:, :, 16:64, 16:64] - target) ** 2)) < 1e-12
+    eps = 1e-6
+    for name, gval in grads.items():
+        for _ in range(3):
+            idx = tuple(r.integers(0, s) for s in P[name].shape)
+            Pp = {k: v.copy() for k, v in P.items()}
+            Pm = {k: v.copy() for k, v in P.items()}
+            Pp[name][idx] += eps
+            Pm[name][idx] -= eps
+            fd = (O.student_loss_grads(Pp, yhat, target)[0] - O.student_loss_grads(Pm, yhat, target)[0]) / (2 * eps)
+            assert abs(fd - gval[idx]) <= 1e-6 * max(1.0, abs(fd)), (name, idx)
