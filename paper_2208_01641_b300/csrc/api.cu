@@ -66,6 +66,10 @@ struct lic_codec {
     int device = 0;
     // transforms
     lic::Layer ga[4], gs[4], ha[3], hs[3];
+    // g_a conv0 as a GEMM over packed 5x5 patches (tensor-core path): the
+    // kernel then loads its A operand with TMA instead of gathering it
+    lic::Layer ga0p;
+    bool use_patch = false;
     lic::Gdn gdn[3], igdn[3];
     // entropy models
     lic::HostTables ht;
@@ -73,7 +77,7 @@ struct lic_codec {
     lic::DevTables dt{};
     lic::DevBuf status;
     // workspace
-    lic::DevBuf xin, act0, act1, y, s_y, h1, h2, z, s_z, zhat, g1, g2, sigma, idx, yhat, xpre;
+    lic::DevBuf xin, patches, act0, act1, y, s_y, h1, h2, z, s_z, zhat, g1, g2, sigma, idx, yhat, xpre;
     lic::DevBuf scratch, counts, sub_off, frame_bytes, offs, data, stage_in, stage_out, in_data, in_offs;
     lic::HostPinned h_offs;
     // measurement
@@ -214,6 +218,45 @@ int make_deconv(Layer &L, const ParamMap &pm, const std::string &name, int Cin, 
             L.ops.push_back(std::move(op));
         }
     return upload(L.bias, b, Cout * sizeof(float));
+}
+
+// g_a conv0 (Cin * 25 <= PATCH_K) as a 1x1 convolution over its packed
+// patches: weights [Cout][PATCH_K], the conv's [Cout][25][Cin] order
+// flattened and zero-padded, the same K order the gathering kernel uses, so
+// results are unchanged
+int make_patch_layer(Layer &P, const Layer &L, const ParamMap &pm) {
+    const int Cout = L.Cout, Cin = L.Cin, k = L.k;
+    if (L.deconv || Cin * k * k > PATCH_K || L.stride != 2 || k != 5) return LIC_E_UNSUPPORTED;
+    const float *w, *b;
+    int rc = get_param(pm, L.name + ".weight", (int64_t)Cout * Cin * k * k, &w);
+    if (rc) return rc;
+    if ((rc = get_param(pm, L.name + ".bias", Cout, &b))) return rc;
+    P.name = L.name;
+    P.deconv = false;
+    P.Cin = PATCH_K;
+    P.Cout = Cout;
+    P.k = 1;
+    P.stride = 1;
+    P.in_xform = IN_NONE;
+    P.epi = L.epi;
+    P.in_dt = DT_F32;
+    P.out_dt = L.out_dt;
+    P.in_scale = 1.f;
+    P.out_scale = L.out_scale;
+    auto op = std::make_unique<ConvOp>();
+    op->T = 1;
+    std::vector<float> r((size_t)Cout * PATCH_K, 0.f);
+    for (int o = 0; o < Cout; ++o)
+        for (int u = 0; u < k; ++u)
+            for (int v = 0; v < k; ++v)
+                for (int c = 0; c < Cin; ++c)
+                    r[(size_t)o * PATCH_K + (u * k + v) * Cin + c] = w[(((size_t)o * Cin + c) * k + u) * k + v];
+    if ((rc = upload(op->w, r.data(), r.size() * sizeof(float)))) return rc;
+    tc::build_weights(r.data(), Cout, 1, PATCH_K, &op->tcw);
+    if (!op->tcw.valid) return LIC_E_UNSUPPORTED;
+    P.ops.clear();
+    P.ops.push_back(std::move(op));
+    return upload(P.bias, b, Cout * sizeof(float));
 }
 
 int make_gdn(Gdn &G, const ParamMap &pm, const std::string &name, int C, bool inverse, bool diag) {
@@ -430,6 +473,7 @@ int ensure_workspace(lic_codec *cd, int B, int Hp, int Wp) {
     const int64_t Hy = Hp / 16, Wy = Wp / 16, Hz = Hp / 64, Wz = Wp / 64;
     const int64_t big = (int64_t)B * (Hp / 2) * (Wp / 2) * N;
     LIC_CUDA_TRY(ensure_n<float>(cd->xin, (int64_t)B * Hp * Wp * 3));
+    if (cd->use_patch) LIC_CUDA_TRY(ensure_n<float>(cd->patches, (int64_t)B * (Hp / 2) * (Wp / 2) * PATCH_K));
     LIC_CUDA_TRY(ensure_n<float>(cd->act0, big));
     LIC_CUDA_TRY(ensure_n<float>(cd->act1, big));
     LIC_CUDA_TRY(ensure_n<float>(cd->y, (int64_t)B * Hy * Wy * M));
@@ -472,7 +516,17 @@ void analysis(lic_codec *cd, int B, int Hp, int Wp, cudaStream_t st) {
     float *a = cd->act0.as<float>(), *b = cd->act1.as<float>();
     int H = Hp, W = Wp;
     const float *in = cd->xin.as<float>();
-    for (int i = 0; i < 3; ++i) {
+    int first = 0;
+    if (cd->use_patch) {
+        const double rows = (double)B * (Hp / 2) * (Wp / 2);
+        timed(cd, "patch_pack", 0, 12.0 * B * Hp * Wp + 4.0 * rows * PATCH_K, 1, st,
+              [&] { launch_patch_pack(cd->xin.as<float>(), B, Hp, Wp, cd->patches.as<float>(), st); });
+        in = run_layer_gdn(cd, cd->ga0p, cd->gdn[0], cd->patches.as<float>(), B, Hp / 2, Wp / 2, a, b, st);
+        H /= 2;
+        W /= 2;
+        first = 1;
+    }
+    for (int i = first; i < 3; ++i) {
         in = run_layer_gdn(cd, cd->ga[i], cd->gdn[i], in, B, H, W, a, b, st);
         H /= 2;
         W /= 2;
@@ -826,6 +880,8 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
                 return LIC_E_UNSUPPORTED;
         if (!cd->ga[0].ops[0]->tcw.valid) return LIC_E_UNSUPPORTED;
     }
+    // tensor-core path: g_a conv0 over packed patches (same arithmetic, TMA-fed)
+    if (cd->opt.conv_impl != LIC_CONV_SIMT) cd->use_patch = make_patch_layer(cd->ga0p, cd->ga[0], pm) == LIC_OK;
     // entropy models: the bottleneck codes y (factorized) or z (hyperprior)
     const int C = kind == LIC_FACTORIZED ? M : N;
     std::vector<double> P;

@@ -33,6 +33,42 @@ __global__ void pad_pack_kernel(const float *__restrict__ f, int B, int H, int W
     }
 }
 
+// Patches of a 5x5 / stride-2 convolution of a 3-channel NHWC image:
+// row (b, i, j) of the output holds, at K index k = (5u + v) * 3 + c, the
+// input value x[b][2i + u - 2][2j + v - 2][c] (0 outside the image), and 0
+// for k >= 75.  A block makes PP_COLS consecutive rows of one output image
+// row: it stages the 5 input rows they read (zero-filled outside the
+// image) in shared memory, then writes the rows as contiguous float4s.
+constexpr int PP_COLS = 64, PP_T = 256;
+constexpr int PP_IN_COLS = 2 * PP_COLS + 3;   // input columns 2 j0 - 2 .. 2 j0 + 2 PP_COLS
+
+__global__ void __launch_bounds__(PP_T) patch_pack_kernel(const float *__restrict__ x, int Hp, int Wp,
+                                                          float *__restrict__ out) {
+    __shared__ float tile[5][PP_IN_COLS * 3];
+    const int Ho = Hp / 2, Wo = Wp / 2;
+    const int j0 = blockIdx.x * PP_COLS, i = blockIdx.y, b = blockIdx.z;
+    for (int e = threadIdx.x; e < 5 * PP_IN_COLS * 3; e += PP_T) {
+        const int r = e / (PP_IN_COLS * 3), rem = e % (PP_IN_COLS * 3);
+        const int y = 2 * i - 2 + r, xx = 2 * j0 - 2 + rem / 3;
+        tile[r][rem] = (y >= 0 && y < Hp && xx >= 0 && xx < Wp) ? x[(((int64_t)b * Hp + y) * Wp + xx) * 3 + rem % 3]
+                                                                 : 0.f;
+    }
+    __syncthreads();
+    const int cols = min(PP_COLS, Wo - j0);
+    float4 *dst = reinterpret_cast<float4 *>(out + (((int64_t)b * Ho + i) * Wo + j0) * PATCH_K);
+    for (int f = threadIdx.x; f < cols * (PATCH_K / 4); f += PP_T) {
+        const int jr = f / (PATCH_K / 4), q = f % (PATCH_K / 4);
+        float v[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int k = 4 * q + m;
+            const int t = k / 3, c = k % 3;
+            v[m] = k < 75 ? tile[t / 5][(2 * jr + t % 5) * 3 + c] : 0.f;
+        }
+        dst[f] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
 __global__ void crop_unpack_kernel(const float *__restrict__ x, int B, int Hp, int Wp, int H, int W,
                                    float *__restrict__ f) {
     int64_t n = (int64_t)B * 3 * H * W;
@@ -192,6 +228,11 @@ void launch_to_bf16(const float *in, int64_t n, void *out, cudaStream_t st) {
 
 void launch_pad_pack(const float *frames, int B, int H, int W, int Hp, int Wp, float *out, cudaStream_t st) {
     pad_pack_kernel<<<grid_for((int64_t)B * Hp * Wp), 256, 0, st>>>(frames, B, H, W, Hp, Wp, out);
+}
+
+void launch_patch_pack(const float *x, int B, int Hp, int Wp, float *out, cudaStream_t st) {
+    const dim3 grid((unsigned)((Wp / 2 + PP_COLS - 1) / PP_COLS), (unsigned)(Hp / 2), (unsigned)B);
+    patch_pack_kernel<<<grid, PP_T, 0, st>>>(x, Hp, Wp, out);
 }
 
 void launch_crop_unpack(const float *x, int B, int Hp, int Wp, int H, int W, float *frames, cudaStream_t st) {

@@ -294,6 +294,12 @@ void launch_norm1d(const float *in, int64_t P, int C, const float *beta, const f
                    float *out, cudaStream_t st);
 // float32 -> bf16 (round to nearest even), n elements.
 void launch_to_bf16(const float *in, int64_t n, void *out, cudaStream_t st);
+
+// The first layer of g_a as a plain GEMM: NHWC 3-channel [B][Hp][Wp][3] ->
+// the rows of its 5x5 / stride-2 patches [B][Hp/2][Wp/2][PATCH_K], K index
+// (5u + v) * 3 + c, zero-padded from 75 to PATCH_K.
+constexpr int PATCH_K = 96;
+void launch_patch_pack(const float *x, int B, int Hp, int Wp, float *out, cudaStream_t st);
 // Copies the 64 scales into the constant bank of the current device (once
 // per device, at codec creation).
 cudaError_t upload_scale_table();
