@@ -303,3 +303,52 @@ def test_student_halo_window_gradients(SW, precision):
     with pytest.raises(lic.LicError):   # the window must fit: 2 + 8 > 9 rows
         st.grad(torch.from_numpy(yp).cuda(), torch.from_numpy(xp).cuda(), np.array([[0, 2, 0]], np.int32))
     st.close()
+
+
+def test_trained_student_gain_over_teacher_and_untrained(SW):
+    """What the trained network gains: after 400 Adam steps on pairs the
+    factorized codec generates, the student reconstructs the teacher's frames
+    far better than before training (>= 8 dB), and decoding with it costs
+    less than a third of g_s's multiply-adds per frame."""
+    W = synth.make_weights(0, 128, M)
+    codec = lic.Codec(0, 128, M, W)
+    P, H, Wd = 4, 256, 256
+    pool_y = torch.empty(P, M, H // 16, Wd // 16, device="cuda")
+    pool_x = torch.empty(P, 3, H, Wd, device="cuda")
+    for i in range(P):
+        fr = torch.from_numpy(synth.make_frames(1, H, Wd, first=600 + i)).cuda()
+        out = torch.empty_like(fr)
+        codec.decode(codec.encode(fr), H, Wd, out)
+        codec.read_tensor(lic.T_YHAT, pool_y[i:i + 1])
+        codec.read_tensor(lic.T_XPRE, pool_x[i:i + 1])
+    val = torch.from_numpy(synth.make_frames(2, H, Wd, first=700)).cuda()
+    bs = codec.encode(val)
+    teacher = torch.empty_like(val)
+    codec.profile(True)
+    codec.decode(bs, H, Wd, teacher)
+    gs_flop = sum(r["flop"] for r in codec.profile_report() if r["name"].startswith("g_s."))
+    codec.profile(False)
+
+    st = lic.Student(SW, M, C, max_batch=8, crop=128, lr=1e-3, precision=lic.BF16)
+
+    def psnr_vs_teacher():
+        codec.set_student(st, min_psnr_db=99.0, checked=True)
+        codec.decode(bs, H, Wd, torch.empty_like(val))
+        ps = codec.student_report()[2]
+        codec.set_student(None)
+        return float(np.mean(ps))
+
+    before = psnr_vs_teacher()
+    for k in range(400):
+        st.step(pool_y, pool_x, synth.draw_crops(k, 8, P, H // 16, Wd // 16, 8))
+    after = psnr_vs_teacher()
+    print(f"[student gain] PSNR vs teacher {before:.2f} dB untrained -> {after:.2f} dB after 400 steps")
+    assert after >= before + 8.0, (before, after)
+    st.profile(True)
+    st.forward(torch.empty(2, M, H // 16, Wd // 16, device="cuda"), torch.empty(2, 3, H, Wd, device="cuda"))
+    stu_flop = sum(r["flop"] for r in st.profile_report())
+    st.profile(False)
+    print(f"[student gain] decoder synthesis work {stu_flop / 1e9:.2f} GFLOP (student) vs {gs_flop / 1e9:.2f} (g_s)")
+    assert stu_flop < gs_flop / 3, (stu_flop, gs_flop)
+    codec.close()
+    st.close()
