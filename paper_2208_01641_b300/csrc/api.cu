@@ -73,7 +73,7 @@ struct lic_codec {
     lic::Gdn gdn[3], igdn[3];
     // entropy models
     lic::HostTables ht;
-    lic::DevBuf cdf, start, lo, hi, med;
+    lic::DevBuf cdf, start, lo, hi, med, lut;
     lic::DevTables dt{};
     lic::DevBuf status;
     // workspace
@@ -892,6 +892,24 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
     if ((rc = upload(cd->lo, cd->ht.lo.data(), cd->ht.lo.size() * 4))) return rc;
     if ((rc = upload(cd->hi, cd->ht.hi.data(), cd->ht.hi.size() * 4))) return rc;
     if ((rc = upload(cd->med, cd->ht.medians.data(), cd->ht.medians.size() * 4))) return rc;
+    {
+        // slot lookup of every table (see LUT_N)
+        const size_t nt = cd->ht.lo.size();
+        std::vector<uint16_t> lut(nt * LUT_N);
+        for (size_t t = 0; t < nt; ++t) {
+            const int n = cd->ht.lo[t] + cd->ht.hi[t] + 2;
+            const uint32_t *c = cd->ht.cdf.data() + cd->ht.start[t];
+            int s = 0;
+            for (int j = 0; j < LUT_N - 1; ++j) {
+                const uint32_t slot = 256u * (uint32_t)j;
+                while (s < n - 1 && c[s + 1] <= slot) ++s;
+                lut[t * LUT_N + j] = (uint16_t)s;
+            }
+            lut[t * LUT_N + LUT_N - 1] = (uint16_t)(n - 1);
+        }
+        if ((rc = upload(cd->lut, lut.data(), lut.size() * sizeof(uint16_t)))) return rc;
+    }
+    cd->dt.lut = cd->lut.as<uint16_t>();
     cd->dt.cdf = cd->cdf.as<uint32_t>();
     cd->dt.start = cd->start.as<int64_t>();
     cd->dt.lo = cd->lo.as<int32_t>();

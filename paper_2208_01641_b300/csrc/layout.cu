@@ -39,7 +39,7 @@ __global__ void pad_pack_kernel(const float *__restrict__ f, int B, int H, int W
 // for k >= 75.  A block makes PP_COLS consecutive rows of one output image
 // row: it stages the 5 input rows they read (zero-filled outside the
 // image) in shared memory, then writes the rows as contiguous float4s.
-constexpr int PP_COLS = 64, PP_T = 256;
+constexpr int PP_COLS = 64, PP_T = 240;   // 10 rows x 24 float4 columns per pass
 constexpr int PP_IN_COLS = 2 * PP_COLS + 3;   // input columns 2 j0 - 2 .. 2 j0 + 2 PP_COLS
 
 __global__ void __launch_bounds__(PP_T) patch_pack_kernel(const float *__restrict__ x, int Hp, int Wp,
@@ -56,30 +56,38 @@ __global__ void __launch_bounds__(PP_T) patch_pack_kernel(const float *__restric
     __syncthreads();
     const int cols = min(PP_COLS, Wo - j0);
     float4 *dst = reinterpret_cast<float4 *>(out + (((int64_t)b * Ho + i) * Wo + j0) * PATCH_K);
-    for (int f = threadIdx.x; f < cols * (PATCH_K / 4); f += PP_T) {
-        const int jr = f / (PATCH_K / 4), q = f % (PATCH_K / 4);
+    // this thread's four K indices, fixed: their offsets in the tile (output column 0)
+    constexpr int Q = PATCH_K / 4;
+    const int q = threadIdx.x % Q, r0 = threadIdx.x / Q;
+    int off[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int k = 4 * q + m, t = k / 3, c = k % 3;
+        off[m] = k < 75 ? (t / 5) * (PP_IN_COLS * 3) + (t % 5) * 3 + c : -1;
+    }
+    const float *tf = &tile[0][0];
+    for (int jr = r0; jr < cols; jr += PP_T / Q) {
         float v[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int k = 4 * q + m;
-            const int t = k / 3, c = k % 3;
-            v[m] = k < 75 ? tile[t / 5][(2 * jr + t % 5) * 3 + c] : 0.f;
-        }
-        dst[f] = make_float4(v[0], v[1], v[2], v[3]);
+        for (int m = 0; m < 4; ++m) v[m] = off[m] >= 0 ? tf[off[m] + 6 * jr] : 0.f;
+        dst[jr * Q + q] = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
 
 __global__ void crop_unpack_kernel(const float *__restrict__ x, int B, int Hp, int Wp, int H, int W,
                                    float *__restrict__ f) {
-    int64_t n = (int64_t)B * 3 * H * W;
+    // one thread per pixel: its 3 channels are one 12-byte read, and each
+    // channel plane is written coalesced across the warp
+    const int64_t n = (int64_t)B * H * W, HW = (int64_t)H * W;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int xx = (int)(e % W);
-        int yy = (int)((e / W) % H);
-        int c = (int)((e / ((int64_t)W * H)) % 3);
-        int b = (int)(e / ((int64_t)W * H * 3));
-        float v = x[(((int64_t)b * Hp + yy) * Wp + xx) * 3 + c];
-        f[e] = fminf(fmaxf(v, 0.f), 1.f);
+        const int xx = (int)(e % W);
+        const int yy = (int)((e / W) % H);
+        const int64_t b = e / HW;
+        const float *src = x + ((b * Hp + yy) * Wp + xx) * 3;
+        float *dst = f + b * 3 * HW + (int64_t)yy * W + xx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dst[c * HW] = fminf(fmaxf(src[c], 0.f), 1.f);
     }
 }
 
@@ -236,7 +244,7 @@ void launch_patch_pack(const float *x, int B, int Hp, int Wp, float *out, cudaSt
 }
 
 void launch_crop_unpack(const float *x, int B, int Hp, int Wp, int H, int W, float *frames, cudaStream_t st) {
-    crop_unpack_kernel<<<grid_for((int64_t)B * 3 * H * W), 256, 0, st>>>(x, B, Hp, Wp, H, W, frames);
+    crop_unpack_kernel<<<grid_for((int64_t)B * H * W), 256, 0, st>>>(x, B, Hp, Wp, H, W, frames);
 }
 
 void launch_nhwc_to_nchw(const float *in, int B, int H, int W, int C, float *out, cudaStream_t st) {

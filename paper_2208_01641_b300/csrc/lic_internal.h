@@ -310,10 +310,16 @@ void launch_scale_index(const float *sigma, int B, int HW, int C, uint8_t *idx,
 // entropy coder (rans.cu)
 // ---------------------------------------------------------------------------
 
+// Slot lookup: for table t, lut[t * LUT_N + j] (j = 0 .. 256) is the symbol
+// whose CDF interval holds slot 256 j (entry 256: the last symbol), so the
+// symbol of a slot lies in [lut[slot >> 8], lut[(slot >> 8) + 1]].
+constexpr int LUT_N = 257;
+
 struct DevTables {
     const uint32_t *cdf;
     const int64_t *start;
     const int32_t *lo, *hi;
+    const uint16_t *lut;
     int n_eb;        // bottleneck tables: table c for channel c
     int gauss_base;  // first Gaussian table (or -1)
 };

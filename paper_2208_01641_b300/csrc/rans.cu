@@ -255,9 +255,11 @@ __device__ __forceinline__ uint32_t rd_u32(const uint8_t *p) {
     return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
 }
 
-__device__ __forceinline__ int find_symbol(const uint32_t *cdf, int n, uint32_t slot) {
-    // largest s in [0, n) with cdf[s] <= slot (cdf[0] = 0, cdf[n] = 2^16)
-    int lo = 0, hi = n - 1;
+__device__ __forceinline__ int find_symbol(const uint32_t *cdf, int n, uint32_t slot, const uint16_t *lut) {
+    // largest s in [0, n) with cdf[s] <= slot (cdf[0] = 0, cdf[n] = 2^16),
+    // searched between the symbols of the 256-slot bucket's two ends
+    const int j = (int)(slot >> 8);
+    int lo = lut[j], hi = min((int)lut[j + 1], n - 1);
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (cdf[mid] <= slot) lo = mid; else hi = mid - 1;
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(WARPS * 32) rans_decode_kernel(const StreamGeo
             nt = lo + t.hi[tab] + 2;
             const uint32_t *cdf = t.cdf + t.start[tab];
             uint32_t slot = x & 0xffffu;
-            sym = find_symbol(cdf, nt, slot);
+            sym = find_symbol(cdf, nt, slot, t.lut + (int64_t)tab * LUT_N);
             uint32_t st = cdf[sym], f = cdf[sym + 1] - st;
             x = f * (x >> 16) + slot - st;
             need = x < RANS_L;

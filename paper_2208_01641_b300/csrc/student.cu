@@ -162,13 +162,21 @@ __global__ void __launch_bounds__(RED_T) chan_sum_kernel(const TX *__restrict__ 
     }
 }
 
-// out[c] = sum over z of part[z][c], in z order
-__global__ void chan_sum_final_kernel(const float *__restrict__ part, int nz, int C, float *__restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+// out[c] = sum over z of part[z][c]: block c, thread t sums z = t, t + RED_T,
+// ... in order, then a fixed tree over the threads
+__global__ void __launch_bounds__(RED_T) chan_sum_final_kernel(const float *__restrict__ part, int nz, int C,
+                                                               float *__restrict__ out) {
+    __shared__ float red[RED_T];
+    const int c = blockIdx.x;
     float s = 0.f;
-    for (int z = 0; z < nz; ++z) s += part[(int64_t)z * C + c];
-    out[c] = s;
+    for (int z = threadIdx.x; z < nz; z += RED_T) s += part[(int64_t)z * C + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = RED_T / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
 }
 
 // Weight gradient of a transposed conv 5x5 / 2 as a GEMM: rows i (input
@@ -604,8 +612,8 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
                 else
                     chan_sum_kernel<<<nz, RED_T, 0, st>>>(static_cast<const float *>(dzl), P_out, Cout, per,
                                                           s->bpart.as<float>());
-                chan_sum_final_kernel<<<1, 256, 0, st>>>(s->bpart.as<float>(), nz, Cout,
-                                                         s->grad.as<float>() + s->boff[l]);
+                chan_sum_final_kernel<<<Cout, RED_T, 0, st>>>(s->bpart.as<float>(), nz, Cout,
+                                                              s->grad.as<float>() + s->boff[l]);
             });
         }
         // weight gradient: split K so that the grid covers the SMs a few times
