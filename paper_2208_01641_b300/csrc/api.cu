@@ -82,6 +82,17 @@ struct lic_codec {
     lic::HostPinned h_offs;
     // measurement
     lic::Profiler pf;
+    // the four sub-pixel phases of a transposed conv write disjoint pixels:
+    // phases 1..3 run on these streams, forked from and joined to the caller's
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
+    ~lic_codec() {
+        for (int i = 0; i < 3; ++i) {
+            if (aux[i]) cudaStreamDestroy(aux[i]);
+            if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+    }
     // learned form: the student that replaces g_s (not owned)
     lic_student *student = nullptr;
     float stu_thr = 0.f;
@@ -357,6 +368,28 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
     });
 }
 
+// Every GEMM launch of a layer.  The phases of a transposed conv are
+// independent (disjoint output pixels, shared input): phase k > 0 runs on
+// auxiliary stream k - 1, so the small launches of h_s and of the first
+// g_s layers fill the GPU together instead of one after another.
+void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out, int Ho, int Wo,
+             cudaStream_t st, const Gdn *G) {
+    const int n = (int)L.ops.size();
+    const bool fork = n > 1 && n <= 4 && cd->ev_fork && cd->aux[n - 2];
+    if (fork) {
+        cudaEventRecord(cd->ev_fork, st);
+        for (int k = 1; k < n; ++k) cudaStreamWaitEvent(cd->aux[k - 1], cd->ev_fork, 0);
+    }
+    for (int k = 0; k < n; ++k)
+        run_op(cd, L, *L.ops[k], in, B, Hi, Wi, out, Ho, Wo, (fork && k > 0) ? cd->aux[k - 1] : st, G);
+    if (fork) {
+        for (int k = 1; k < n; ++k) {
+            cudaEventRecord(cd->ev_join[k - 1], cd->aux[k - 1]);
+            cudaStreamWaitEvent(st, cd->ev_join[k - 1], 0);
+        }
+    }
+}
+
 void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out,
                cudaStream_t st) {
     int Ho, Wo;
@@ -376,7 +409,7 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
         });
         return;
     }
-    for (auto &op : L.ops) run_op(cd, L, *op, in, B, Hi, Wi, out, Ho, Wo, st);
+    run_ops(cd, L, in, B, Hi, Wi, out, Ho, Wo, st, nullptr);
 }
 
 void run_gdn(const lic_codec *cd, const Gdn &G, const float *in, int B, int H, int W, float *out, cudaStream_t st) {
@@ -451,7 +484,7 @@ float *run_layer_gdn(const lic_codec *cd, const Layer &L, const Gdn &G, const fl
         fuse = d.in_dt != DT_F32 ? tc::can_run_lp(d, op->tcw) : tc::can_run(d, op->tcw);
     }
     if (fuse) {
-        for (auto &op : L.ops) run_op(cd, L, *op, in, B, Hi, Wi, out, Ho, Wo, st, &G);
+        run_ops(cd, L, in, B, Hi, Wi, out, Ho, Wo, st, &G);
         return out;
     }
     float *norm_out = (other == a) ? b : a;
@@ -818,6 +851,11 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
     if (cd->opt.precision < LIC_FP32 || cd->opt.precision > LIC_FP8) return LIC_E_UNSUPPORTED;
     if (cd->opt.precision != LIC_FP32 && cd->opt.conv_impl == LIC_CONV_SIMT) return LIC_E_UNSUPPORTED;
     LIC_CUDA_TRY(cudaGetDevice(&cd->device));
+    for (int i = 0; i < 3; ++i) {
+        LIC_CUDA_TRY(cudaStreamCreateWithFlags(&cd->aux[i], cudaStreamNonBlocking));
+        LIC_CUDA_TRY(cudaEventCreateWithFlags(&cd->ev_join[i], cudaEventDisableTiming));
+    }
+    LIC_CUDA_TRY(cudaEventCreateWithFlags(&cd->ev_fork, cudaEventDisableTiming));
     LIC_CUDA_TRY(upload_scale_table());
     ParamMap pm = param_map(weights);
     int rc;
