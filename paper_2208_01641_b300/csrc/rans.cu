@@ -267,7 +267,16 @@ __device__ __forceinline__ int find_symbol(const uint32_t *cdf, int n, uint32_t 
     return lo;
 }
 
-__global__ void __launch_bounds__(WARPS * 32) rans_decode_kernel(const StreamGeom g, int B, int part,
+// Decoder: DEC_WARPS substreams per block.  The per-symbol table data sits
+// in shared memory: for the Gaussian scale tables (hyperprior y) the slot
+// lookups and (lo, symbol count, CDF start) of all 64 tables, staged once per
+// block; for a substream with one fixed table (z, factorized y) that table's
+// slot lookup in the warp's own row.  The next group's scale indices are
+// loaded a group ahead.
+constexpr int DEC_WARPS = 8;
+constexpr int NGAUSS = 64;
+
+__global__ void __launch_bounds__(DEC_WARPS * 32) rans_decode_kernel(const StreamGeom g, int B, int part,
                                                                  const DevTables t,
                                                                  const uint8_t *__restrict__ data,
                                                                  const int64_t *__restrict__ offsets,
@@ -277,9 +286,25 @@ __global__ void __launch_bounds__(WARPS * 32) rans_decode_kernel(const StreamGeo
                                                                  int32_t *__restrict__ s_out,
                                                                  float *__restrict__ hat_out,
                                                                  uint32_t *__restrict__ status) {
-    const int lane = threadIdx.x & 31;
+    __shared__ uint16_t s_glut[NGAUSS * LUT_N];
+    __shared__ int32_t s_glo[NGAUSS], s_gnt[NGAUSS];
+    __shared__ int64_t s_gstart[NGAUSS];
+    __shared__ uint16_t s_wlut[DEC_WARPS][LUT_N];
+    const bool gauss = part == 1 && g.kind == LIC_HYPERPRIOR && t.gauss_base >= 0;
+    if (gauss) {
+        for (int e = threadIdx.x; e < NGAUSS * LUT_N; e += blockDim.x)
+            s_glut[e] = t.lut[(int64_t)t.gauss_base * LUT_N + e];
+        for (int e = threadIdx.x; e < NGAUSS; e += blockDim.x) {
+            const int tab = t.gauss_base + e;
+            s_glo[e] = t.lo[tab];
+            s_gnt[e] = t.lo[tab] + t.hi[tab] + 2;
+            s_gstart[e] = t.start[tab];
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nq = part == 0 ? g.nz : g.nsub - g.nz;
-    const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    const int64_t warp = (int64_t)blockIdx.x * DEC_WARPS + wib;
     if (warp >= (int64_t)B * nq) return;
     const int b = (int)(warp / nq);
     const int q = (int)(warp % nq) + (part == 0 ? 0 : g.nz);
@@ -317,22 +342,50 @@ __global__ void __launch_bounds__(WARPS * 32) rans_decode_kernel(const StreamGeo
     float *hdst = hat_out ? hat_out + ((int64_t)b * HW + si.p0) * C + si.c : nullptr;
     const float mu = (si.is_z || g.kind == LIC_FACTORIZED) ? med[si.c] : 0.f;
 
+    // a substream with one table: its parameters in registers, its lookup in the warp's row
+    int lo_f = 0, nt_f = 2;
+    const uint32_t *cdf_f = t.cdf;
+    const bool per_symbol = si.idx != nullptr;
+    if ((per_symbol && !gauss) || (!per_symbol && si.table < 0)) {   // no table for these symbols
+        if (lane == 0) atomicOr(status, ST_CORRUPT);
+        return;
+    }
+    if (!per_symbol) {
+        lo_f = t.lo[si.table];
+        nt_f = lo_f + t.hi[si.table] + 2;
+        cdf_f = t.cdf + t.start[si.table];
+        for (int e = lane; e < LUT_N; e += 32) s_wlut[wib][e] = t.lut[(int64_t)si.table * LUT_N + e];
+        __syncwarp();
+    }
+
     uint32_t x = (uint32_t)words[2 * lane] | ((uint32_t)words[2 * lane + 1] << 16);
     int64_t pos = 64;
     bool corrupt = false;
     const int ngroups = (si.n + 31) / 32;
+    int next_k = (per_symbol && lane < si.n) ? si.idx[lane] : 0;
     for (int grp = 0; grp < ngroups; ++grp) {
         const int i = grp * 32 + lane;
         const bool active = i < si.n;
-        int tab = 0, lo = 0, nt = 2, sym = 0;
+        const int k = next_k;
+        if (per_symbol) next_k = (i + 32 < si.n) ? si.idx[i + 32] : 0;   // a group ahead
+        int lo = 0, nt = 2, sym = 0;
         bool need = false;
         if (active) {
-            tab = si.idx ? t.gauss_base + si.idx[i] : si.table;
-            lo = t.lo[tab];
-            nt = lo + t.hi[tab] + 2;
-            const uint32_t *cdf = t.cdf + t.start[tab];
+            const uint32_t *cdf;
+            const uint16_t *lut;
+            if (per_symbol) {
+                lo = s_glo[k];
+                nt = s_gnt[k];
+                cdf = t.cdf + s_gstart[k];
+                lut = s_glut + k * LUT_N;
+            } else {
+                lo = lo_f;
+                nt = nt_f;
+                cdf = cdf_f;
+                lut = s_wlut[wib];
+            }
             uint32_t slot = x & 0xffffu;
-            sym = find_symbol(cdf, nt, slot, t.lut + (int64_t)tab * LUT_N);
+            sym = find_symbol(cdf, nt, slot, lut);
             uint32_t st = cdf[sym], f = cdf[sym + 1] - st;
             x = f * (x >> 16) + slot - st;
             need = x < RANS_L;
@@ -347,38 +400,49 @@ __global__ void __launch_bounds__(WARPS * 32) rans_decode_kernel(const StreamGeo
             }
             pos += __popc(m);
         } else {
-            // serial over lanes: an escape's nibbles sit between its word and
-            // the next lane's word
-            for (int l = 0; l < 32; ++l) {
-                if (lane == l && active) {
-                    if (need) {
-                        if (pos < nw) x = (x << 16) | words[pos]; else corrupt = true;
-                        ++pos;
-                    }
-                    if (is_esc && !corrupt) {
-                        uint32_t v = 0, nn = 0;
-                        for (int j = -1; j < (int)nn && !corrupt; ++j) {
-                            uint32_t slot = x & 0xffffu;
-                            uint32_t nib = slot >> 12;
-                            x = 4096u * (x >> 16) + slot - 4096u * nib;
-                            if (x < RANS_L) {
-                                if (pos < nw) x = (x << 16) | words[pos]; else corrupt = true;
-                                ++pos;
-                            }
-                            if (j < 0) {
-                                nn = nib + 1;
-                                if (nn > 8) corrupt = true;
-                            } else {
-                                v |= nib << (4 * j);
-                            }
-                        }
-                        int64_t r = (v & 1u) ? -(int64_t)lo - 1 - (int64_t)(v >> 1)
-                                             : (int64_t)(nt - 2 - lo) + 1 + (int64_t)(v >> 1);
-                        if (r > 1073741824LL || r < -1073741824LL) corrupt = true;
-                        val = (int32_t)r;
-                    }
+            // an escape's nibbles sit between its own word and the next lane's:
+            // lanes between two escapes read their words in parallel (rank
+            // among the renormalising lanes of the segment), each escape lane
+            // then decodes its nibbles alone and hands on the position
+            const unsigned m_need = __ballot_sync(FULL, need);
+            unsigned m_esc = __ballot_sync(FULL, is_esc);
+            int first = 0;
+            for (;;) {
+                const int e = m_esc ? __ffs(m_esc) - 1 : 31;
+                const unsigned seg = (e == 31 ? FULL : ((2u << e) - 1u)) & ~((1u << first) - 1u);
+                const unsigned seg_need = m_need & seg;
+                if (need && ((seg >> lane) & 1u)) {
+                    const int64_t p = pos + __popc(seg_need & ((1u << lane) - 1u));
+                    if (p < nw) x = (x << 16) | words[p]; else corrupt = true;
                 }
-                pos = __shfl_sync(FULL, pos, l);
+                pos += __popc(seg_need);
+                if (!m_esc) break;
+                if (lane == e && !corrupt) {
+                    uint32_t v = 0, nn = 0;
+                    for (int j = -1; j < (int)nn && !corrupt; ++j) {
+                        uint32_t slot = x & 0xffffu;
+                        uint32_t nib = slot >> 12;
+                        x = 4096u * (x >> 16) + slot - 4096u * nib;
+                        if (x < RANS_L) {
+                            if (pos < nw) x = (x << 16) | words[pos]; else corrupt = true;
+                            ++pos;
+                        }
+                        if (j < 0) {
+                            nn = nib + 1;
+                            if (nn > 8) corrupt = true;
+                        } else {
+                            v |= nib << (4 * j);
+                        }
+                    }
+                    int64_t r = (v & 1u) ? -(int64_t)lo - 1 - (int64_t)(v >> 1)
+                                         : (int64_t)(nt - 2 - lo) + 1 + (int64_t)(v >> 1);
+                    if (r > 1073741824LL || r < -1073741824LL) corrupt = true;
+                    val = (int32_t)r;
+                }
+                pos = __shfl_sync(FULL, pos, e);
+                m_esc &= m_esc - 1u;
+                first = e + 1;
+                if (first == 32) break;
             }
         }
         if (__any_sync(FULL, corrupt)) {
@@ -442,8 +506,9 @@ void launch_rans_decode(const StreamGeom &g, int B, int part, const DevTables &t
     int nq = part == 0 ? g.nz : g.nsub - g.nz;
     int64_t warps = (int64_t)B * nq;
     if (warps == 0) return;
-    rans_decode_kernel<<<(unsigned)blocks_for(warps), WARPS * 32, 0, st>>>(g, B, part, t, data, offsets, sizes, idx,
-                                                                           med, s_out, hat_out, status);
+    const unsigned blocks = (unsigned)((warps + DEC_WARPS - 1) / DEC_WARPS);
+    rans_decode_kernel<<<blocks, DEC_WARPS * 32, 0, st>>>(g, B, part, t, data, offsets, sizes, idx, med, s_out,
+                                                          hat_out, status);
 }
 
 }  // namespace lic
