@@ -133,6 +133,23 @@ def cpu_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+def job_time_ms(local_ms, dist=None):
+    """Time of the whole job: the slowest rank's (MAX over ranks of a NCCL or
+    gloo group; the local time without a group)."""
+    if dist is None:
+        return local_ms
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(frames_per_rank, ws, job_ms):
+    """Whole-job frames/s: every rank's frames over the slowest rank's time."""
+    return ws * frames_per_rank / (job_ms / 1000.0)
+
+
 def reference_arm(args, ws, rank):
     """The oracle, as it stands, on the host cores (rank 0 only)."""
     if rank != 0:
@@ -230,12 +247,8 @@ def main():
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     enc_ms = [a.elapsed_time(b) for a, b, c in ev]
     dec_ms = [b.elapsed_time(c) for a, b, c in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * B * args.steps / (total_ms / 1000.0)
+    total_ms = job_time_ms(sum(step_ms), dist)
+    value = job_value(B * args.steps, ws, total_ms)
     frame_bytes = bs.sizes()
 
     # ---- roofline of the dominant kernel: per-launch CUDA events, live ----
