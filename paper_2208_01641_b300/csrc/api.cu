@@ -30,6 +30,10 @@ namespace {
 struct ConvOp {
     DevBuf w;     // [Cout][T][Cin] float32
     tc::TcWeights tcw;  // tensor-core operand copy (built when the op qualifies)
+    // Cout the tensor-core kernels take only in slices (Cout not 128 or 192,
+    // e.g. M = 320): one operand copy per column slice of 192 or 128 channels
+    std::vector<std::unique_ptr<tc::TcWeights>> parts;
+    std::vector<int> part_off;
     int T = 0;
     int8_t du[MAX_TAPS] = {}, dv[MAX_TAPS] = {};
     int py = 0, px = 0;
@@ -142,6 +146,26 @@ int upload(DevBuf &b, const void *src, size_t bytes) {
     return LIC_OK;
 }
 
+// Column slices of a [Cout][T][Cin] weight matrix for the tensor-core
+// kernels when Cout is not one of their widths: Cout = 192 a + 128 b.
+void build_parts(ConvOp &op, const float *r, int Cout, int Cin) {
+    if (Cout == 128 || Cout == 192 || Cout % 64) return;
+    for (int a = Cout / 192; a >= 0; --a) {
+        if ((Cout - 192 * a) % 128) continue;
+        const int64_t K = (int64_t)op.T * Cin;
+        int off = 0;
+        for (int j = 0; j < a + (Cout - 192 * a) / 128; ++j) {
+            const int w = j < a ? 192 : 128;
+            auto tw = std::make_unique<tc::TcWeights>();
+            tc::build_weights(r + off * K, w, op.T, Cin, tw.get());
+            op.parts.push_back(std::move(tw));
+            op.part_off.push_back(off);
+            off += w;
+        }
+        return;
+    }
+}
+
 // conv weight [Cout][Cin][k][k] -> [Cout][k*k][Cin]; taps (u - k/2, v - k/2)
 int make_conv(Layer &L, const ParamMap &pm, const std::string &name, int Cin, int Cout, int k, int stride,
               int in_xform, int epi) {
@@ -173,6 +197,7 @@ int make_conv(Layer &L, const ParamMap &pm, const std::string &name, int Cin, in
         }
     if ((rc = upload(op->w, r.data(), r.size() * sizeof(float)))) return rc;
     tc::build_weights(r.data(), Cout, op->T, Cin, &op->tcw);
+    build_parts(*op, r.data(), Cout, Cin);
     L.ops.push_back(std::move(op));
     return upload(L.bias, b, Cout * sizeof(float));
 }
@@ -226,6 +251,7 @@ int make_deconv(Layer &L, const ParamMap &pm, const std::string &name, int Cin, 
                 }
             if ((rc = upload(op->w, r.data(), r.size() * sizeof(float)))) return rc;
             tc::build_weights(r.data(), Cout, op->T, Cin, &op->tcw);
+            build_parts(*op, r.data(), Cout, Cin);
             L.ops.push_back(std::move(op));
         }
     return upload(L.bias, b, Cout * sizeof(float));
@@ -340,8 +366,12 @@ ConvDesc op_desc(const lic_codec *cd, const Layer &L, const ConvOp &op, const fl
 // One GEMM launch of a layer; with G, the GDN / IGDN that follows the layer
 // runs in the same launch (the caller has checked that it can).
 void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *in, int B, int Hi, int Wi,
-            float *out, int Ho, int Wo, cudaStream_t st, const Gdn *G = nullptr) {
+            float *out, int Ho, int Wo, cudaStream_t st, const Gdn *G = nullptr, int out_dt = -1) {
     ConvDesc d = op_desc(cd, L, op, in, B, Hi, Wi, out, Ho, Wo);
+    if (out_dt >= 0) {   // the caller wants this storage instead of the layer's own
+        d.out_dt = out_dt;
+        d.out_scale = 1.f;
+    }
     const double rows = (double)B * d.Gh * d.Gw;
     double flop = 2.0 * rows * d.Cout * d.T * d.Cin;
     const double bytes = 4.0 * ((double)B * Hi * Wi * d.Cin + rows * d.Cout + (double)d.Cout * d.T * d.Cin);
@@ -353,6 +383,31 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
         d.gdn_gamma = G->gamma.as<float>();
         flop += G->diag ? 4.0 * rows * G->C : 2.0 * rows * G->C * G->C;
         nm += "+" + G->name.substr(G->name.find('.') + 1);
+    }
+    if (!op.parts.empty() && !G) {
+        // column slices on the tensor cores, each writing its channels of the full-width output
+        std::vector<ConvDesc> ds;
+        bool ok = cd->opt.conv_impl != LIC_CONV_SIMT || d.in_dt != DT_F32;
+        for (size_t j = 0; j < op.parts.size() && ok; ++j) {
+            ConvDesc dp = d;
+            dp.Cout = op.parts[j]->Cout;
+            dp.out_coff = op.part_off[j];
+            dp.out_stride = d.Cout;
+            dp.bias = d.bias + op.part_off[j];
+            ok = d.in_dt != DT_F32 ? tc::can_run_lp(dp, *op.parts[j]) : tc::can_run(dp, *op.parts[j]);
+            ds.push_back(dp);
+        }
+        if (ok) {
+            nm += d.in_dt == DT_F32 ? ":tc" : (d.in_dt == DT_E4M3 ? ":e4m3" : ":bf16");
+            timed(const_cast<lic_codec *>(cd), nm, flop, bytes, (int)ds.size(), st, [&] {
+                for (size_t j = 0; j < ds.size(); ++j) {
+                    const bool done = d.in_dt != DT_F32 ? tc::launch_lp(ds[j], *op.parts[j], st)
+                                                        : tc::launch(ds[j], *op.parts[j], st);
+                    if (!done) atomic_status(cd, ST_TIMEOUT);
+                }
+            });
+            return;
+        }
     }
     if (d.in_dt != DT_F32) {   // precision forms: checked at codec creation
         nm += d.in_dt == DT_E4M3 ? ":e4m3" : ":bf16";
@@ -373,7 +428,7 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
 // auxiliary stream k - 1, so the small launches of h_s and of the first
 // g_s layers fill the GPU together instead of one after another.
 void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out, int Ho, int Wo,
-             cudaStream_t st, const Gdn *G) {
+             cudaStream_t st, const Gdn *G, int out_dt = -1) {
     const int n = (int)L.ops.size();
     const bool fork = n > 1 && n <= 4 && cd->ev_fork && cd->aux[n - 2];
     if (fork) {
@@ -381,7 +436,7 @@ void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi
         for (int k = 1; k < n; ++k) cudaStreamWaitEvent(cd->aux[k - 1], cd->ev_fork, 0);
     }
     for (int k = 0; k < n; ++k)
-        run_op(cd, L, *L.ops[k], in, B, Hi, Wi, out, Ho, Wo, (fork && k > 0) ? cd->aux[k - 1] : st, G);
+        run_op(cd, L, *L.ops[k], in, B, Hi, Wi, out, Ho, Wo, (fork && k > 0) ? cd->aux[k - 1] : st, G, out_dt);
     if (fork) {
         for (int k = 1; k < n; ++k) {
             cudaEventRecord(cd->ev_join[k - 1], cd->aux[k - 1]);
@@ -391,7 +446,7 @@ void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi
 }
 
 void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out,
-               cudaStream_t st) {
+               cudaStream_t st, int out_dt = -1) {
     int Ho, Wo;
     if (L.deconv) {
         Ho = 2 * Hi;
@@ -409,7 +464,7 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
         });
         return;
     }
-    run_ops(cd, L, in, B, Hi, Wi, out, Ho, Wo, st, nullptr);
+    run_ops(cd, L, in, B, Hi, Wi, out, Ho, Wo, st, nullptr, out_dt);
 }
 
 void run_gdn(const lic_codec *cd, const Gdn &G, const float *in, int B, int H, int W, float *out, cudaStream_t st) {
@@ -488,6 +543,16 @@ float *run_layer_gdn(const lic_codec *cd, const Layer &L, const Gdn &G, const fl
         return out;
     }
     float *norm_out = (other == a) ? b : a;
+    if (L.out_dt != DT_F32) {
+        // precision form with a norm the low-precision kernel cannot fuse (Cout 192): the
+        // convolution in float32, the norm in float32, then the next layer's storage
+        run_layer(cd, L, in, B, Hi, Wi, other, st, DT_F32);
+        run_gdn(cd, G, other, B, Ho, Wo, norm_out, st);
+        const int64_t n = (int64_t)B * Ho * Wo * L.Cout;
+        timed(const_cast<lic_codec *>(cd), G.name + ":to_bf16", 0, 6.0 * n, 1, st,
+              [&] { launch_to_bf16(norm_out, n, other, st); });
+        return other;
+    }
     run_layer(cd, L, in, B, Hi, Wi, other, st);
     run_gdn(cd, G, other, B, Ho, Wo, norm_out, st);
     return norm_out;
@@ -905,8 +970,14 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
         for (int i = 0; i < 3; ++i) lp_out_for(cd->ga[i], cd->ga[i + 1]);
         for (int i = 0; i < 2; ++i) lp_out_for(cd->gs[i], cd->gs[i + 1]);
         auto check = [&](const Layer &L) {
-            for (auto &op : L.ops)
-                if (L.in_dt == DT_E4M3 ? !op->tcw.f8valid : !op->tcw.bvalid) return false;
+            for (auto &op : L.ops) {
+                bool ok = L.in_dt == DT_E4M3 ? op->tcw.f8valid : op->tcw.bvalid;
+                if (!ok && !op->parts.empty()) {
+                    ok = true;
+                    for (auto &pt : op->parts) ok = ok && (L.in_dt == DT_E4M3 ? pt->f8valid : pt->bvalid);
+                }
+                if (!ok) return false;
+            }
             return true;
         };
         for (int i = 1; i < 4; ++i)
@@ -914,8 +985,13 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
         for (int i = 0; i < 3; ++i)
             if (!check(cd->gs[i])) return LIC_E_UNSUPPORTED;
         for (int i = 0; i < 3; ++i)
-            if ((!cd->gdn[i].diag && (!cd->gdn[i].tcw.valid || !cd->igdn[i].tcw.valid)) || N != 128)
+            if ((!cd->gdn[i].diag && (!cd->gdn[i].tcw.valid || !cd->igdn[i].tcw.valid)) || (N != 128 && N != 192))
                 return LIC_E_UNSUPPORTED;
+        // N = 192: the low-precision kernel does not fuse the norm; the unfused path hands the next
+        // layer bf16, so no e4m3 input may follow a norm
+        if (N != 128)
+            for (int i = 1; i < 4; ++i)
+                if (cd->ga[i].in_dt == DT_E4M3 || (i < 3 && cd->gs[i].in_dt == DT_E4M3)) return LIC_E_UNSUPPORTED;
         if (!cd->ga[0].ops[0]->tcw.valid) return LIC_E_UNSUPPORTED;
     }
     // tensor-core path: g_a conv0 over packed patches (same arithmetic, TMA-fed)

@@ -79,6 +79,7 @@ struct Params {
     int Hi, Wi, s;                // MODE_IM2COL: input size, stride
     int fuse_gdn;                 // 0, 1 (GDN) or 2 (IGDN) applied after bias
     int out_dt;                   // DType of the output
+    int ostride, ocoff;           // output: elements per pixel, first channel (a column slice of a wider layer)
     float out_inv_scale;          // e4m3 output: stored = x * out_inv_scale
     float in_scale;               // e4m3 input: x = stored * in_scale
     const float *w_scale;         // e4m3 weights: per output channel
@@ -780,16 +781,16 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 opix = ((int64_t)b * p.Ho + p.oym * gi + p.oyo) * p.Wo + p.oxm * gj + p.oxo;
             }
             if (valid && p.fuse_gdn) {
-                store_row<HALF * 32>(master, p.out, opix * COUT + cbase, p.out_dt, p.out_inv_scale);
+                store_row<HALF * 32>(master, p.out, opix * p.ostride + p.ocoff + cbase, p.out_dt, p.out_inv_scale);
             } else if (valid) {
-                float *dst = p.out + opix * COUT + cbase;
+                float *dst = p.out + opix * p.ostride + p.ocoff + cbase;
 #pragma unroll
                 for (int q = 0; q < HALF * 8; ++q) {
                     float4 o;
                     float *op = reinterpret_cast<float *>(&o);
                     float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (p.epi == EPI_GDN || p.epi == EPI_IGDN)
-                        xg = *reinterpret_cast<const float4 *>(p.gdn_x + opix * COUT + cbase + 4 * q);
+                        xg = *reinterpret_cast<const float4 *>(p.gdn_x + opix * p.ostride + p.ocoff + cbase + 4 * q);
                     const float *xp = reinterpret_cast<const float *>(&xg);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
@@ -1105,9 +1106,9 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
 #pragma unroll
                     for (int i = 0; i < HALF * 32; ++i) master[i] = fmaxf(master[i], 0.f);
                 } else if (p.epi == EPI_MASK) {
-                    mask_row<HALF * 32>(master, p.gdn_x, opix * COUT + cbase, p.out_dt);
+                    mask_row<HALF * 32>(master, p.gdn_x, opix * p.ostride + p.ocoff + cbase, p.out_dt);
                 }
-                store_row<HALF * 32>(master, p.out, opix * COUT + cbase, p.out_dt, p.out_inv_scale);
+                store_row<HALF * 32>(master, p.out, opix * p.ostride + p.ocoff + cbase, p.out_dt, p.out_inv_scale);
             }
         }
     }
@@ -1362,6 +1363,8 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.gdn_beta = d.gdn_beta;
     p.gdn_gamma = d.gdn_gamma;
     p.out_dt = d.out_dt;
+    p.ostride = d.out_stride > 0 ? d.out_stride : d.Cout;
+    p.ocoff = d.out_coff;
     p.out_inv_scale = d.out_scale > 0.f ? 1.f / d.out_scale : 1.f;
     p.tmem_cols = 512;  // partial sums (+ A slots when Cout = 128)
     for (int t = 0; t < d.T; ++t) {
@@ -1503,6 +1506,8 @@ bool launch_lp_impl(const ConvDesc &d, const CUtensorMap &bm, const float *w_sca
     p.gdn_beta = d.gdn_beta;
     p.gdn_gamma = d.gdn_gamma;
     p.out_dt = d.out_dt;
+    p.ostride = d.out_stride > 0 ? d.out_stride : d.Cout;
+    p.ocoff = d.out_coff;
     p.out_inv_scale = d.out_scale > 0.f ? 1.f / d.out_scale : 1.f;
     p.in_scale = d.in_scale > 0.f ? d.in_scale : 1.f;
     p.w_scale = w_scale;

@@ -253,6 +253,9 @@ struct ConvDesc {
     int Gh, Gw, s;
     int Ho, Wo, Cout;
     int oym, oyo, oxm, oxo;
+    // output row stride in elements (0: Cout) and first output channel, for
+    // a launch that computes a column slice of a wider layer (tensor cores)
+    int out_stride, out_coff;
     int T;
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
     int in_xform, epi;

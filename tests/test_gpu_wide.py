@@ -1,0 +1,121 @@
+"""The precision form's configuration, N = 192 and M = 320 (marked gpu).
+
+M = 320 is not a width the tensor-core kernels take in one launch: the
+layers with 320 outputs (g_a conv3, h_s conv2) run as column slices of 192
+and 128 channels writing one output.  With N = 192 the low-precision kernel
+does not fuse GDN / IGDN: the BF16 form runs those convolutions with a
+float32 output, the norm in float32, then hands the next layer bf16.
+
+FP32: the same bars as the N = 128 chain (float stages max-abs 1e-4 against
+the FP64 oracle on identical inputs; symbols, indices and bitstream bytes
+identical).  BF16: lossless entropy stages, encoder and decoder indices
+identical, reconstruction within 40 dB PSNR of the FP64 chain."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2208_01641_b300 as lic
+from paper_2208_01641_b300 import synth
+
+pytestmark = pytest.mark.gpu
+N, M = 192, 320
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def W():
+    return synth.make_weights(1, N, M)
+
+
+def pad(x):
+    H, Wd = x.shape[2:]
+    Hp, Wp = O.pad_size(H, Wd)
+    return np.pad(x, ((0, 0), (0, 0), (0, Hp - H), (0, Wp - Wd)), mode="edge")
+
+
+def test_wide_fp32_transforms_match_oracle(W):
+    c = lic.Codec(1, N, M, W)
+    x = synth.make_frames(2, 64, 120, first=90)
+    y = torch.empty(2, M, 4, 8, device="cuda")
+    c.analysis(torch.from_numpy(x).cuda(), y)
+    torch.cuda.synchronize()
+    ry = O.g_a(W, pad(x))
+    assert np.abs(y.cpu().numpy() - ry).max() <= TOL
+    yn = y.cpu().numpy()
+    z = torch.empty(2, N, 1, 2, device="cuda")
+    c.hyper_analysis(torch.from_numpy(yn).cuda(), z)
+    torch.cuda.synchronize()
+    assert np.abs(z.cpu().numpy() - O.h_a(W, yn)).max() <= TOL
+    zhat = np.rint(z.cpu().numpy()).astype(np.float32)
+    sigma = torch.empty(2, M, 4, 8, device="cuda")
+    c.hyper_synthesis(torch.from_numpy(zhat).cuda(), sigma)
+    torch.cuda.synchronize()
+    assert np.abs(sigma.cpu().numpy() - O.h_s(W, zhat)).max() <= TOL
+    yhat = np.rint(yn).astype(np.float32)
+    xr = torch.empty(2, 3, 64, 128, device="cuda")
+    c.synthesis(torch.from_numpy(yhat).cuda(), xr)
+    torch.cuda.synchronize()
+    assert np.abs(xr.cpu().numpy() - O.g_s(W, yhat)).max() <= TOL
+    c.close()
+
+
+def test_wide_fp32_bitstreams_and_roundtrip(W):
+    c = lic.Codec(1, N, M, W)
+    oc = O.Codec(1, N, M, W)
+    x = synth.make_frames(2, 100, 150, first=95)
+    bs = c.encode(torch.from_numpy(x).cuda())
+    got = bs.to_bytes()
+    shp_y, shp_z = (2, M, 8, 12), (2, N, 2, 3)
+    sy, y = np.zeros(shp_y, np.int32), np.zeros(shp_y, np.float32)
+    z, sz = np.zeros(shp_z, np.float32), np.zeros(shp_z, np.int32)
+    sg, idx = np.zeros(shp_y, np.float32), np.zeros(shp_y, np.uint8)
+    for t, a in ((lic.T_SY, sy), (lic.T_Y, y), (lic.T_Z, z), (lic.T_SZ, sz), (lic.T_SIGMA, sg), (lic.T_IDX, idx)):
+        c.read_tensor(t, a)
+    assert np.array_equal(sy, O.quantize(y))
+    assert np.array_equal(sz, O.quantize(z, oc.med))
+    assert np.array_equal(idx, O.scale_index(sg))
+    for b in range(2):
+        subs = O.encode_latents(oc, sy[b], idx[b], sz[b])
+        assert got[b] == O.pack_frame(1, N, M, 100, 150, 128, 192, oc.R, subs)
+    out = torch.empty(2, 3, 100, 150, device="cuda")
+    c.decode(bs, 100, 150, out)
+    assert c.sync_status() == lic.OK
+    ref, _ = O.decode(oc, got)
+    assert np.abs(out.cpu().numpy() - ref).max() <= TOL
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [lic.BF16])
+def test_wide_precision_form(W, prec, capsys):
+    c = lic.Codec(1, N, M, W, precision=prec)
+    oc = O.Codec(1, N, M, W)
+    B, H, Wd = 2, 130, 200
+    x = synth.make_frames(B, H, Wd, first=97)
+    bs = c.encode(torch.from_numpy(x).cuda())
+    c.sync()
+    Hy, Wy = 12, 16
+    sy = np.zeros((B, M, Hy, Wy), np.int32)
+    y = np.zeros((B, M, Hy, Wy), np.float32)
+    idx_enc = np.zeros((B, M, Hy, Wy), np.uint8)
+    c.read_tensor(lic.T_SY, sy)
+    c.read_tensor(lic.T_Y, y)
+    c.read_tensor(lic.T_IDX, idx_enc)
+    out = torch.empty(B, 3, H, Wd, device="cuda")
+    c.decode(bs, H, Wd, out)
+    assert c.sync_status() == lic.OK
+    sy_dec = np.zeros_like(sy)
+    idx_dec = np.zeros_like(idx_enc)
+    c.read_tensor(lic.T_SY, sy_dec)
+    c.read_tensor(lic.T_IDX, idx_dec)
+    assert np.array_equal(sy_dec, sy), "entropy coding must stay lossless"
+    assert np.array_equal(idx_dec, idx_enc), "encoder and decoder indices differ"
+    ref_bs, inter = O.encode(oc, x)
+    ref, _ = O.decode(oc, ref_bs)
+    p = O.psnr(out.cpu().numpy(), ref)
+    yerr = float(np.abs(y - inter["y"]).max())
+    with capsys.disabled():
+        print(f"\n[N=192 M=320 bf16] PSNR vs FP64 chain {p:.2f} dB, max|y - y64| {yerr:.4f}")
+    assert p >= 40.0, p
+    assert yerr < 0.1, yerr
+    c.close()
