@@ -874,9 +874,19 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
     constexpr int KCE = 128 / EB;              // elements per K chunk
     constexpr int BB_BYTES = COUT * 128;
     constexpr int STAGE_BYTES = AB_BYTES + BB_BYTES;
-    constexpr int GCH = COUT / KCH;            // tf32 chunks of the fused norm (COUT = 128 only)
+    // Fused GDN / IGDN: the norm GEMM of y^2 (TF32 hi / lo, A from TMEM slots
+    // after the two partial buffers) with gamma (hi / lo slices by TMA into the
+    // idle stages).  Cout = 128: one pass over its 4 chunks (gamma hi in the A
+    // area, lo in the B area of stages 0..3).  Cout = 192: three passes of two
+    // chunks (two TMEM slot pairs after the 384 partial columns; gamma hi / lo
+    // of chunk j in the B areas of stages 2j / 2j + 1).
+    constexpr bool NORM = HALF >= 2;
+    constexpr int GPASS = HALF == 3 ? 3 : 1;   // norm passes
+    constexpr int GCP = HALF == 3 ? 2 : COUT / KCH;   // tf32 chunks per pass
     constexpr int GB = COUT * KCH * 4;         // bytes of one gamma chunk (hi or lo)
-    static_assert(HALF != 2 || (GCH <= STAGES && GB <= AB_BYTES && GB <= BB_BYTES), "norm operands fit the stages");
+    static_assert(HALF != 2 || (GCP <= STAGES && GB <= AB_BYTES && GB <= BB_BYTES), "norm operands fit the stages");
+    static_assert(HALF != 3 || (2 * GCP <= STAGES && GB <= BB_BYTES && 2 * COUT + GCP * 2 * KCH <= 512),
+                  "norm operands fit the stages and TMEM");
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
     uint64_t *full = bars, *empty = bars + STAGES;
     uint64_t *pfull = bars + 2 * STAGES, *pempty = pfull + 2;
@@ -948,15 +958,19 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
                 tma_load_2d(stage_b(s), &tmB, &full[s], kc * KCE, 0);
                 issued = kc + 1;
             }
-            if (HALF == 2 && (p.fuse_gdn == 1 || p.fuse_gdn == 2) && !*abort_flag) {
-                if (!mbar_wait(mma_done, 0)) {
+            for (int h = 0; NORM && (p.fuse_gdn == 1 || p.fuse_gdn == 2) && h < GPASS && !*abort_flag; ++h) {
+                // pass h's gamma once the MMAs reading the stages (main loop, then pass h-1) are done
+                if (!mbar_wait(mma_done, h & 1)) {
                     fail();
-                } else {
-                    mbar_expect_tx(gdn_full, 2 * GCH * GB);
-                    for (int c = 0; c < GCH; ++c) {
-                        tma_load_2d(stage_a(c), &tmGh, gdn_full, c * KCH, 0);
-                        tma_load_2d(stage_b(c), &tmGl, gdn_full, c * KCH, 0);
-                    }
+                    break;
+                }
+                mbar_expect_tx(gdn_full, 2 * GCP * GB);
+                for (int c = 0; c < GCP; ++c) {
+                    const int chunk = h * GCP + c;
+                    uint8_t *dh = HALF == 3 ? stage_b(2 * c) : stage_a(c);
+                    uint8_t *dl = HALF == 3 ? stage_b(2 * c + 1) : stage_b(c);
+                    tma_load_2d(dh, &tmGh, gdn_full, chunk * KCH, 0);
+                    tma_load_2d(dl, &tmGl, gdn_full, chunk * KCH, 0);
                 }
             }
             if (*abort_flag) {
@@ -995,26 +1009,27 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
                 mma_commit(&empty[s]);
                 if (kc % FOLD == FOLD - 1 || kc == p.kchunks - 1) mma_commit(&pfull[q]);
             }
-            mma_commit(mma_done);
-            if (HALF == 2 && (p.fuse_gdn == 1 || p.fuse_gdn == 2)) {
+            mma_commit(mma_done);   // commit 0: the main loop
+            for (int h = 0; NORM && (p.fuse_gdn == 1 || p.fuse_gdn == 2) && h < GPASS; ++h) {
                 const uint32_t idt = idesc_tf32(BLOCK_M, COUT);
-                if (*abort_flag || !mbar_wait(gdn_ready, 0) || !mbar_wait(gdn_full, 0)) {
+                if (*abort_flag || !mbar_wait(gdn_ready, h & 1) || !mbar_wait(gdn_full, h & 1)) {
                     fail();
-                } else {
-                    tc_fence_after();
-#pragma unroll
-                    for (int c = 0; c < GCH; ++c) {
-                        const uint32_t gh = smem_u32(stage_a(c)), gl = smem_u32(stage_b(c));
-#pragma unroll
-                        for (int kk = 0; kk < KCH / 8; ++kk) {
-                            const uint64_t dgh = sdesc(gh + kk * 32), dgl = sdesc(gl + kk * 32);
-                            mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dgh, idt, (c > 0 || kk > 0) ? 1u : 0u);
-                            mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dgl, idt, 1u);
-                            mma_tf32_ts(tmem, slot_lo(c) + 8 * kk, dgh, idt, 1u);
-                        }
-                    }
-                    mma_commit(mma_done);
+                    break;
                 }
+                tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < GCP; ++c) {
+                    const uint32_t gh = smem_u32(HALF == 3 ? stage_b(2 * c) : stage_a(c));
+                    const uint32_t gl = smem_u32(HALF == 3 ? stage_b(2 * c + 1) : stage_b(c));
+#pragma unroll
+                    for (int kk = 0; kk < KCH / 8; ++kk) {
+                        const uint64_t dgh = sdesc(gh + kk * 32), dgl = sdesc(gl + kk * 32);
+                        mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dgh, idt, (h > 0 || c > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dgl, idt, 1u);
+                        mma_tf32_ts(tmem, slot_lo(c) + 8 * kk, dgh, idt, 1u);
+                    }
+                }
+                mma_commit(mma_done);   // commit h + 1: norm pass h
             }
         }
     } else {
@@ -1059,26 +1074,40 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
                 master[i] = p.fuse_gdn == 3 ? y * rsqrtf(n) : y * sqrtf(n);
             }
         }
-        if (ok && HALF == 2 && (p.fuse_gdn == 1 || p.fuse_gdn == 2)) {
+        if (ok && NORM && (p.fuse_gdn == 1 || p.fuse_gdn == 2)) {
+            // pass g: this thread's chunks among [g GCP, (g+1) GCP) -> slots chunk - g GCP
 #pragma unroll
-            for (int h = 0; h < HALF; ++h) {
-                float hv[32], lv[32];
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const float sq = master[h * 32 + i] * master[h * 32 + i];
-                    hv[i] = tf32_rna(sq);
-                    lv[i] = tf32_rna(sq - hv[i]);
+            for (int g = 0; g < GPASS; ++g) {
+                if (!ok) break;
+                if (g > 0 && (*abort_flag || !mbar_wait(mma_done, g & 1))) {   // pass g-1 read the slots
+                    fail();
+                    ok = false;
+                    break;
                 }
-                const int slot = HALF * half + h;
-                tmem_st16(slot_hi(slot) + lane_off, hv);
-                tmem_st16(slot_hi(slot) + lane_off + 16, hv + 16);
-                tmem_st16(slot_lo(slot) + lane_off, lv);
-                tmem_st16(slot_lo(slot) + lane_off + 16, lv + 16);
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    const int chunk = HALF * half + h;
+                    if (chunk / GCP != g) continue;
+                    const int slot = chunk - g * GCP;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {   // 16 columns at a time
+                        float hv[16], lv[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float y = master[h * 32 + 16 * q + i];
+                            const float sq = y * y;
+                            hv[i] = tf32_rna(sq);
+                            lv[i] = tf32_rna(sq - hv[i]);
+                        }
+                        tmem_st16(slot_hi(slot) + lane_off + 16 * q, hv);
+                        tmem_st16(slot_lo(slot) + lane_off + 16 * q, lv);
+                    }
+                }
+                tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(gdn_ready);
             }
-            tmem_st_wait();
-            tc_fence_before();
-            mbar_arrive(gdn_ready);
-            if (*abort_flag || !mbar_wait(mma_done, 1)) {
+            if (!ok || *abort_flag || !mbar_wait(mma_done, GPASS & 1)) {
                 fail();
                 ok = false;
             } else {
@@ -1443,7 +1472,8 @@ bool lp_shape_ok(const ConvDesc &d) {
     if (d.fuse_gdn >= 3 && (!d.gdn_beta || !d.gdn_gamma)) return false;
     if (d.fuse_gdn == 1 || d.fuse_gdn == 2) {
         const TcWeights *g = static_cast<const TcWeights *>(d.gdn_w);
-        if (d.Cout != 128 || !g || !g->valid || g->T != 1 || g->Cin != d.Cout || g->Cout != d.Cout || !d.gdn_beta)
+        if ((d.Cout != 128 && d.Cout != 192) || !g || !g->valid || g->T != 1 || g->Cin != d.Cout ||
+            g->Cout != d.Cout || !d.gdn_beta)
             return false;
     }
     if (d.s == 2) return (d.Hi % 2 == 0) && (d.Wi % 2 == 0) && d.oym == 1 && d.oxm == 1;
