@@ -301,8 +301,10 @@ void lic_scale_table(float T[64]);
 
 /* enable = 1: start recording a CUDA event pair around every kernel launch
  * the codec issues (on the stream it is given), discarding earlier records;
- * enable = 0: stop recording.  Recording adds a small gap between launches;
- * time the chain without it. */
+ * enable = 0: stop recording.  Recording adds a small gap between launches,
+ * and the sub-pixel phases of a transposed convolution, which otherwise run
+ * side by side on auxiliary streams, run one after another so that each
+ * record times one launch; time the chain without it. */
 int lic_profile_enable(lic_codec *codec, int enable);
 
 /* Write the records as JSON into buf: a list of {"name", "launches", "ms",

@@ -430,7 +430,9 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
 void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out, int Ho, int Wo,
              cudaStream_t st, const Gdn *G, int out_dt = -1) {
     const int n = (int)L.ops.size();
-    const bool fork = n > 1 && n <= 4 && cd->ev_fork && cd->aux[n - 2];
+    // while launches are being timed one by one (lic_profile_enable) the phases run in
+    // sequence, so that each launch's event pair brackets that launch alone
+    const bool fork = n > 1 && n <= 4 && cd->ev_fork && cd->aux[n - 2] && !cd->pf.on;
     if (fork) {
         cudaEventRecord(cd->ev_fork, st);
         for (int k = 1; k < n; ++k) cudaStreamWaitEvent(cd->aux[k - 1], cd->ev_fork, 0);
