@@ -289,6 +289,19 @@ def main():
                 forms[name]["y_maxabs_vs_oracle"] = sampled_errors(fcodec, wts, frames_np, B)
             fcodec.close()
 
+    # ---- the rate cost of interleaving: y substreams of whole latent planes instead of 16-row bands ----
+    if not args.no_forms:
+        cw = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, conv_impl=impl, band_rows=PAD_H // 16)
+        wms, wstatus = time_steps(cw, frames, out, H, W, args.steps, args.warmup, stream, flush)
+        wbytes = cw.encode(frames).sizes()
+        forms["fp32_whole_plane_substreams"] = {
+            "value": ws * B * args.steps / (sum(wms) / 1000.0), "unit": "frames/s", "decode_status": wstatus,
+            "bits_per_pixel": 8.0 * statistics.mean(wbytes) / (H * W),
+            "bits_per_pixel_16_row_bands": 8.0 * statistics.mean(frame_bytes) / (H * W),
+            "note": "one y substream (32 interleaved states) per latent plane instead of per 16-row band: a third "
+                    "of the states to flush (rate), a third of the decoder's warps (parallelism)"}
+        cw.close()
+
     # ---- the precision form's own configuration: N=192 M=320, 8 x 1920x1080 ----
     if not args.no_forms and args.conv == "auto":
         forms["precision_1080p_n192_m320"] = wide_form(args, lic, synth, torch, np, stream, flush, rank)
