@@ -619,9 +619,9 @@ def wide_form(args, lic, synth, torch, np, stream, flush, rank):
     1920x1088): FP32 and BF16 enc+dec frames/s; for BF16 the PSNR of x_hat
     against the FP64 oracle's g_s on sampled windows and max |y - y64| on a
     crop interior; for both, encoder and decoder scale indices compared
-    element by element.  (FP8 needs 128-channel multiples for its e4m3
-    operands; at 192 and 320 channels every layer would take bf16, so it is
-    the BF16 row.)"""
+    element by element; FP8 likewise (e4m3 operands for the 192-channel
+    inputs, weights zero-padded per tap to whole 128-channel chunks; the
+    320-channel g_s input stays bf16)."""
     N3, M3, H3, W3, B3 = 192, 320, 1080, 1920, 8
     Hp3, Wp3 = 1088, 1920
     Wt3 = synth.make_weights(lic.HYPERPRIOR, N3, M3)
@@ -630,7 +630,7 @@ def wide_form(args, lic, synth, torch, np, stream, flush, rank):
     fr = torch.from_numpy(fr_np).cuda()
     out = torch.empty_like(fr)
     res = {}
-    for name, prec in (("fp32", lic.FP32), ("bf16", lic.BF16)):
+    for name, prec in (("fp32", lic.FP32), ("bf16", lic.BF16), ("fp8", lic.FP8)):
         c = lic.Codec(lic.HYPERPRIOR, N3, M3, Wt3, precision=prec)
         fms, status = time_steps(c, fr, out, H3, W3, args.steps, args.warmup, stream, flush)
         bs = c.encode(fr)
@@ -644,7 +644,7 @@ def wide_form(args, lic, synth, torch, np, stream, flush, rank):
         r = {"value": B3 * args.steps / (sum(fms) / 1000.0), "unit": "frames/s",
              "ms_per_step": sum(fms) / args.steps, "p99_ms": sorted(fms)[min(len(fms) - 1, int(0.99 * len(fms)))],
              "decode_status": max(status, st), "indices_identical_enc_dec": bool(torch.equal(idx_e, idx_d))}
-        if prec == lic.BF16 and rank == 0 and not args.no_cpu_baseline:
+        if prec != lic.FP32 and rank == 0 and not args.no_cpu_baseline:
             r["psnr_vs_oracle_db"] = psnr_vs_oracle(c, Wt3, B3, M3, Hp3, Wp3)
             r["y_maxabs_vs_oracle"] = sampled_errors(c, Wt3, fr_np, B3, M3, Hp3, Wp3)
         c.close()

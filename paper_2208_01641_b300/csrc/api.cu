@@ -954,7 +954,7 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
         const bool f8 = cd->opt.precision == LIC_FP8;
         const float S = 1.f / 16.f;   // e4m3 activation scale: |x| <= 448 * S = 28 representable
         auto lp_in = [&](Layer &L) {
-            if (f8 && L.Cin % 128 == 0) {
+            if (f8 && L.Cin % 64 == 0) {
                 L.in_dt = DT_E4M3;
                 L.in_scale = S;
             } else {
@@ -989,11 +989,13 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
         for (int i = 0; i < 3; ++i)
             if ((!cd->gdn[i].diag && (!cd->gdn[i].tcw.valid || !cd->igdn[i].tcw.valid)) || (N != 128 && N != 192))
                 return LIC_E_UNSUPPORTED;
-        // N = 192: the low-precision kernel does not fuse the norm; the unfused path hands the next
-        // layer bf16, so no e4m3 input may follow a norm
-        if (N != 128)
-            for (int i = 1; i < 4; ++i)
-                if (cd->ga[i].in_dt == DT_E4M3 || (i < 3 && cd->gs[i].in_dt == DT_E4M3)) return LIC_E_UNSUPPORTED;
+        // a norm the low-precision kernels cannot fuse runs unfused and hands the next layer
+        // bf16: no e4m3 input may follow one (the kernels fuse at 128 and 192 channels)
+        for (int i = 0; i < 3; ++i) {
+            const bool fusable = cd->gdn[i].diag || N == 128 || N == 192;
+            if (!fusable && (cd->ga[i + 1].in_dt == DT_E4M3 || (i < 2 && cd->gs[i + 1].in_dt == DT_E4M3)))
+                return LIC_E_UNSUPPORTED;
+        }
         if (!cd->ga[0].ops[0]->tcw.valid) return LIC_E_UNSUPPORTED;
     }
     // tensor-core path: g_a conv0 over packed patches (same arithmetic, TMA-fed)

@@ -1253,19 +1253,26 @@ uint16_t bf16_rne_host(float x) {
     return (uint16_t)(u >> 16);
 }
 
-// e4m3 copy of w / s[o], s[o] = max_k |w[o][k]| / 448 (per output channel).
+// e4m3 copy of w / s[o], s[o] = max_k |w[o][k]| / 448 (per output channel),
+// laid out [Cout][T][cin8] with each tap's channels zero-padded to a
+// multiple of 128 (one K chunk): the kernel then reads whole chunks, and
+// whatever the activation box holds past the real channels meets zeros.
 void build_weights_e4m3(const float *w, int Cout, int T, int Cin, TcWeights *out) {
-    if (Cin % KC8 || (Cout != 128 && Cout != 192) || !encode_fn()) return;
-    const int64_t K = (int64_t)T * Cin;
-    std::vector<uint8_t> v((size_t)Cout * K);
+    if (Cin % 16 || (Cout != 128 && Cout != 192) || !encode_fn()) return;
+    const int cin8 = (Cin + KC8 - 1) / KC8 * KC8;
+    const int64_t K0 = (int64_t)T * Cin, K = (int64_t)T * cin8;
+    std::vector<uint8_t> v((size_t)Cout * K, 0);
     std::vector<float> sc(Cout);
     for (int o = 0; o < Cout; ++o) {
         float mx = 0.f;
-        for (int64_t k = 0; k < K; ++k) mx = std::max(mx, std::fabs(w[o * K + k]));
+        for (int64_t k = 0; k < K0; ++k) mx = std::max(mx, std::fabs(w[o * K0 + k]));
         sc[o] = mx > 0.f ? mx / 448.f : 1.f;
-        for (int64_t k = 0; k < K; ++k)
-            v[o * K + k] = (uint8_t)__nv_cvt_float_to_fp8(w[o * K + k] / sc[o], __NV_SATFINITE, __NV_E4M3);
+        for (int t = 0; t < T; ++t)
+            for (int c = 0; c < Cin; ++c)
+                v[o * K + (int64_t)t * cin8 + c] =
+                    (uint8_t)__nv_cvt_float_to_fp8(w[o * K0 + (int64_t)t * Cin + c] / sc[o], __NV_SATFINITE, __NV_E4M3);
     }
+    out->cin8 = cin8;
     if (cudaMalloc(&out->w8, v.size()) != cudaSuccess) return;
     if (cudaMalloc(&out->w8scale, Cout * sizeof(float)) != cudaSuccess) return;
     if (cudaMemcpy(out->w8, v.data(), v.size(), cudaMemcpyHostToDevice) != cudaSuccess) return;
@@ -1468,7 +1475,7 @@ bool lp_shape_ok(const ConvDesc &d) {
                               (d.out_dt != DT_BF16 && d.out_dt != DT_F32)))
         return false;
     if (d.in_xform != IN_NONE) return false;
-    if (d.Cin % (e4 ? KC8 : KCB)) return false;
+    if (d.Cin % (e4 ? 16 : KCB)) return false;   // e4m3: weights padded to whole chunks, see build_weights_e4m3
     if (d.fuse_gdn >= 3 && (!d.gdn_beta || !d.gdn_gamma)) return false;
     if (d.fuse_gdn == 1 || d.fuse_gdn == 2) {
         const TcWeights *g = static_cast<const TcWeights *>(d.gdn_w);
@@ -1509,7 +1516,8 @@ bool make_bf16_weight_map(TmaMap *m, const void *w, int Cout, int K) {
 }
 
 namespace {
-bool launch_lp_impl(const ConvDesc &d, const CUtensorMap &bm, const float *w_scale, cudaStream_t st) {
+// cpt: K chunks per tap (Cin / 64 for bf16; the padded e4m3 width / 128)
+bool launch_lp_impl(const ConvDesc &d, const CUtensorMap &bm, const float *w_scale, int cpt, cudaStream_t st) {
     const bool e4 = d.in_dt == DT_E4M3;
     const int EBY = e4 ? 1 : 2;
     Params p{};
@@ -1519,7 +1527,7 @@ bool launch_lp_impl(const ConvDesc &d, const CUtensorMap &bm, const float *w_sca
     p.status = d.status;
     p.T = d.T;
     p.Cin = d.Cin;
-    p.cpt = d.Cin / (128 / EBY);
+    p.cpt = cpt;
     p.kchunks = d.T * p.cpt;
     p.Gh = d.Gh;
     p.Gw = d.Gw;
@@ -1596,12 +1604,13 @@ bool launch_lp_impl(const ConvDesc &d, const CUtensorMap &bm, const float *w_sca
 
 bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     const bool e4 = d.in_dt == DT_E4M3;
-    return launch_lp_impl(d, *reinterpret_cast<const CUtensorMap *>(e4 ? w.w8map : w.bmap), w.w8scale, st);
+    return launch_lp_impl(d, *reinterpret_cast<const CUtensorMap *>(e4 ? w.w8map : w.bmap), w.w8scale,
+                          e4 ? w.cin8 / KC8 : d.Cin / KCB, st);
 }
 
 bool launch_lp_map(const ConvDesc &d, const TmaMap &bmap, cudaStream_t st) {
     if (!can_run_lp_map(d)) return false;
-    return launch_lp_impl(d, *reinterpret_cast<const CUtensorMap *>(&bmap), nullptr, st);
+    return launch_lp_impl(d, *reinterpret_cast<const CUtensorMap *>(&bmap), nullptr, d.Cin / KCB, st);
 }
 
 }  // namespace tc

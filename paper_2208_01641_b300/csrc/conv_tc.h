@@ -20,6 +20,7 @@ struct TcWeights {
     float *w8scale = nullptr;   // device, per output channel
     bool f8valid = false;
     int Cout = 0, T = 0, Cin = 0, Npad = 0, Kpad = 0;
+    int cin8 = 0;           // e4m3 copy: Cin zero-padded to a multiple of 128 (one K chunk per 128 channels)
     bool im2col = false;    // few input channels: A gathered by the kernel, K zero-padded
     bool valid = false;
     TcWeights() = default;
