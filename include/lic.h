@@ -318,6 +318,14 @@ int lic_profile_report(lic_codec *codec, char *buf, int cap);
 /* Kernel launches issued by this codec since it was created. */
 int64_t lic_launch_count(lic_codec *codec);
 
+/* Diagnostics of the failure path: one GPU thread waits, through the same
+ * bounded wait the tensor-core pipelines use, on a barrier that nothing
+ * arrives at; after limit_cycles (1 .. 4e9 SM clock cycles) it gives up and
+ * latches the codec's timeout status, so the next lic_sync returns
+ * LIC_E_TIMEOUT (and clears it) while the context stays usable.  No hang,
+ * no fault.  Stream-ordered. */
+int lic_test_bounded_wait(lic_codec *codec, int64_t limit_cycles, void *stream);
+
 /* Human-readable message for an error code. */
 const char *lic_strerror(int code);
 

@@ -38,6 +38,7 @@ EXPORTED = [
     "lic_synthesis", "lic_hyper_analysis", "lic_hyper_synthesis", "lic_encode_latents",
     "lic_decode_latents", "lic_build_tables", "lic_scale_table", "lic_strerror",
     "lic_profile_enable", "lic_profile_report", "lic_launch_count", "lic_encode_latents_noalloc",
+    "lic_test_bounded_wait",
     # include/lic_student.h (learned form)
     "lic_student_create", "lic_student_destroy", "lic_student_grad", "lic_student_step", "lic_student_read",
     "lic_student_read_activation", "lic_student_steps", "lic_student_forward", "lic_student_profile_enable", "lic_student_profile_report",
@@ -139,6 +140,7 @@ def _lib():
         L.lic_profile_report.argtypes = [vp, ctypes.c_char_p, i]
         L.lic_launch_count.argtypes = [vp]
         L.lic_launch_count.restype = i64
+        L.lic_test_bounded_wait.argtypes = [vp, i64, vp]
         L.lic_student_create.argtypes = [ctypes.POINTER(_Weights), i, i, ctypes.POINTER(_StudentOptions),
                                          ctypes.POINTER(vp)]
         L.lic_student_destroy.argtypes = [vp]
@@ -317,6 +319,10 @@ class Codec:
 
     def launch_count(self) -> int:
         return int(_lib().lic_launch_count(self.h))
+
+    def test_bounded_wait(self, limit_cycles: int, stream=None):
+        """Diagnostics: a bounded wait that runs out (lic_test_bounded_wait)."""
+        _check(_lib().lic_test_bounded_wait(self.h, limit_cycles, _stream(stream)), "lic_test_bounded_wait")
 
     def set_student(self, student: Optional["Student"], min_psnr_db: float = 35.0, checked: bool = False):
         """Decode with ``student`` in place of g_s (None restores g_s)."""

@@ -1168,6 +1168,14 @@ int lic_profile_report(lic_codec *cd, char *buf, int cap) { return cd ? cd->pf.r
 
 int64_t lic_launch_count(lic_codec *cd) { return cd ? cd->pf.launches : LIC_E_INVALID_ARG; }
 
+int lic_test_bounded_wait(lic_codec *cd, int64_t limit_cycles, void *stream) {
+    if (!cd || limit_cycles < 1 || limit_cycles > 4000000000LL) return LIC_E_INVALID_ARG;
+    timed(cd, "wait_probe", 0, 0, 1, S(stream),
+          [&] { tc::launch_wait_probe(cd->status.as<uint32_t>(), (long long)limit_cycles, S(stream)); });
+    LIC_CUDA_TRY(cudaGetLastError());
+    return LIC_OK;
+}
+
 }  // extern "C"
 
 namespace lic {

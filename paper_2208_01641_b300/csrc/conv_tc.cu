@@ -122,13 +122,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait: false if the phase did not complete within WAIT_CYCLES.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = WAIT_CYCLES) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -321,6 +321,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= (uint64_t)1u << 46;            // descriptor version
     d |= (uint64_t)2u << 61;            // SWIZZLE_128B
     return d;
+}
+
+// One thread waits on a barrier that nothing arrives at, through the same
+// bounded wait as the kernels' pipelines; when it gives up it latches
+// ST_TIMEOUT, as a stalled pipeline would.
+__global__ void wait_probe_kernel(uint32_t *status, long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    if (!mbar_wait(&bar, 0, limit)) atomicOr(status, ST_TIMEOUT);
+    mbar_arrive(&bar);   // complete the phase before the block exits
 }
 
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
@@ -1611,6 +1622,10 @@ bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
 bool launch_lp_map(const ConvDesc &d, const TmaMap &bmap, cudaStream_t st) {
     if (!can_run_lp_map(d)) return false;
     return launch_lp_impl(d, *reinterpret_cast<const CUtensorMap *>(&bmap), nullptr, d.Cin / KCB, st);
+}
+
+void launch_wait_probe(uint32_t *status, long long limit_cycles, cudaStream_t st) {
+    wait_probe_kernel<<<1, 1, 0, st>>>(status, limit_cycles);
 }
 
 }  // namespace tc

@@ -58,6 +58,10 @@ bool make_bf16_weight_map(TmaMap *m, const void *w, int Cout, int K);
 // or EPI_MASK (d.gdn_x = the activation, stored like the output); d.bias
 // may be null.  false = not launched.
 bool can_run_lp_map(const ConvDesc &d);
+
+// The bounded mbarrier wait of the kernels, on a barrier nothing arrives at:
+// gives up after limit_cycles and latches ST_TIMEOUT in *status.
+void launch_wait_probe(uint32_t *status, long long limit_cycles, cudaStream_t st);
 bool launch_lp_map(const ConvDesc &d, const TmaMap &bmap, cudaStream_t st);
 
 }  // namespace tc
