@@ -454,7 +454,6 @@ def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws
         teacher.decode(teacher.encode(fr), H, W, o)
         teacher.read_tensor(lic.T_YHAT, pool_y[i:i + 8])
         teacher.read_tensor(lic.T_XPRE, pool_x[i:i + 8])
-    teacher.close()
     st = lic.Student(synth.make_student_weights(M_CH, STUDENT_C), M_CH, STUDENT_C, max_batch=STUDENT_BATCH,
                      crop=STUDENT_CROP, lr=1e-4, precision=lic.BF16, halo=STUDENT_HALO)
     steps = args.student_steps
@@ -494,6 +493,12 @@ def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws
         top_peak, top_bound = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12, "alu"
         top_note = "CUDA-core FP32 FMA peak: 148 SMs x 128 lanes x 2 x max SM clock"
 
+    # the codec the pairs came from, checked on the held-out batch (the same frames as below)
+    fbs = teacher.encode(frames)
+    teacher.set_student(st, min_psnr_db=35.0, checked=True)
+    teacher.decode(fbs, H, W, out)
+    _, ffall, fpsnrs = teacher.student_report()
+    teacher.close()
     # the hyperprior codec decoding with the student: checked (per-frame PSNR vs the teacher), then timed
     codec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt)
     bs = codec.encode(frames)
@@ -525,6 +530,8 @@ def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws
         "p99_ms": sorted(fms)[min(len(fms) - 1, int(0.99 * len(fms)))], "decode_status": fstatus,
         "psnr_vs_teacher_db": [round(float(p), 3) for p in psnrs], "frames_checked": nchk,
         "fallbacks_below_35db": nfall,
+        "psnr_vs_teacher_factorized_db": [round(float(p), 3) for p in fpsnrs],
+        "fallbacks_below_35db_factorized": ffall,
         "decode_fps_student": dec["student"], "decode_fps_teacher": dec["teacher"],
         "train": {"steps": steps, "batch": STUDENT_BATCH, "crop": STUDENT_CROP, "halo_latents": STUDENT_HALO,
                   "lr": 1e-4,
