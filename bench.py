@@ -365,22 +365,23 @@ def main():
                 codec.decode(bs2, H, W, hout, stream=sid)
             codec.sync(sid)
             serial_fps = ws * B * args.steps / (time.perf_counter() - t0)
-        # pipelined through the serving API: two lanes (codec + stream), a batch's host copies overlap
-        # the other lane's kernels; at most two batches in flight, each frame's output its own pinned buffer
-        srv = lic.Server(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=lic.FP32, max_batch=B, lanes=2,
-                         max_pending=4 * B, graphs=True, max_wait_ms=1e6)
+        # pipelined through the serving API: three lanes (codec + stream), a batch's host copies overlap
+        # the other lanes' kernels; at most three batches in flight, each frame's output its own pinned buffer
+        depth = 3
+        srv = lic.Server(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=lic.FP32, max_batch=B, lanes=depth,
+                         max_pending=(depth + 1) * B, graphs=True, max_wait_ms=1e6)
         srv.prepare(H, W)
-        outs = [torch.empty(hin.shape, dtype=torch.float32).pin_memory() for _ in range(3)]
+        outs = [torch.empty(hin.shape, dtype=torch.float32).pin_memory() for _ in range(depth + 1)]
 
         def run(nsteps):
             done = 0
             for k in range(nsteps):
-                while k - done // B >= 2:
-                    done += len(srv.poll(4 * B, wait_ms=100.0))
+                while k - done // B >= depth:
+                    done += len(srv.poll((depth + 1) * B, wait_ms=100.0))
                 for f in range(B):
-                    srv.submit(f, hin[f], outs[k % 3][f])
+                    srv.submit(f, hin[f], outs[k % (depth + 1)][f])
             srv.drain(600000)
-            srv.poll(4 * B * nsteps)
+            srv.poll((depth + 1) * B * nsteps)
 
         run(2)
         t0 = time.perf_counter()
@@ -391,7 +392,7 @@ def main():
         e2e = {"value": ws * B * args.steps / dt, "unit": "frames/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "serial_value": serial_fps, "graph_replays": est["graph_replays"],
                "note": "pinned host frames in, decoded frames out to pinned host memory, through the serving "
-                       "API (FP32 codec, 2 lanes, batches of 8, at most 2 in flight); serial_value: one codec "
+                       "API (FP32 codec, 3 lanes, batches of 8, at most 3 in flight); serial_value: one codec "
                        "on one stream, copies not overlapped"}
 
     # ---- reconstruction vs the FP64 oracle on sampled windows ----
