@@ -235,6 +235,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16_f(float a, float b) {
     return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
@@ -272,6 +286,60 @@ __device__ __forceinline__ void store_row(const float *v, void *out, int64_t off
         float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(out) + off);
 #pragma unroll
         for (int q = 0; q < NV / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+}
+
+// Four consecutive per-channel parameters (16-byte aligned; the launch checks
+// it) through the read-only path.
+__device__ __forceinline__ float4 ld_param4(const float *src) { return __ldg(reinterpret_cast<const float4 *>(src)); }
+
+// Divisive normalisation of one value: y / sqrt(n) (GDN) or y * sqrt(n)
+// (inverse GDN).  n >= beta > 0, so sqrt(n) = n * rsqrt(n); both forms go
+// through rsqrtf, which keeps the epilogue's loops free of the IEEE square
+// root's slow-path branch.
+template <bool INV>
+__device__ __forceinline__ float norm_apply(float y, float n) {
+    const float r = rsqrtf(n);
+    return INV ? y * (n * r) : y * r;
+}
+
+// master[i] = norm_apply(master[i], n[i] + beta[i]) for NV channels
+template <int NV, bool INV>
+__device__ __forceinline__ void norm_n(float *master, const float *n, const float *beta) {
+#pragma unroll
+    for (int q = 0; q < NV / 4; ++q) {
+        const float4 b = ld_param4(beta + 4 * q);
+        master[4 * q + 0] = norm_apply<INV>(master[4 * q + 0], n[4 * q + 0] + b.x);
+        master[4 * q + 1] = norm_apply<INV>(master[4 * q + 1], n[4 * q + 1] + b.y);
+        master[4 * q + 2] = norm_apply<INV>(master[4 * q + 2], n[4 * q + 2] + b.z);
+        master[4 * q + 3] = norm_apply<INV>(master[4 * q + 3], n[4 * q + 3] + b.w);
+    }
+}
+
+// Per-channel (diagonal) norm of NV channels: y = master + bias (bias may be
+// null), master = norm_apply(y, beta + gamma y^2)
+template <int NV, bool INV>
+__device__ __forceinline__ void norm_diag(float *master, const float *bias, const float *gamma, const float *beta) {
+#pragma unroll
+    for (int q = 0; q < NV / 4; ++q) {
+        const float4 bi = bias ? ld_param4(bias + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 g = ld_param4(gamma + 4 * q), be = ld_param4(beta + 4 * q);
+        const float bb[4] = {bi.x, bi.y, bi.z, bi.w}, gg[4] = {g.x, g.y, g.z, g.w}, ee[4] = {be.x, be.y, be.z, be.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float y = master[4 * q + e] + bb[e];
+            master[4 * q + e] = norm_apply<INV>(y, fmaf(gg[e], y * y, ee[e]));
+        }
+    }
+}
+
+// master[i] += bias[i] for NV channels
+template <int NV>
+__device__ __forceinline__ void add_bias(float *master, const float *bias) {
+#pragma unroll
+    for (int q = 0; q < NV / 4; ++q) {
+        const float4 b = ld_param4(bias + 4 * q);
+        master[4 * q] += b.x; master[4 * q + 1] += b.y; master[4 * q + 2] += b.z; master[4 * q + 3] += b.w;
     }
 }
 
@@ -699,16 +767,16 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
         if (ok && p.fuse_gdn >= 3) {
             // 1DN / inverse 1DN: per-channel, y * rsqrt(beta + gamma y^2) or y * sqrt(.)
 #pragma unroll
-            for (int i = 0; i < HALF * 32; ++i) {
-                const float y = master[i] + __ldg(p.bias + cbase + i);
-                const float n = fmaf(__ldg(p.gdn_gamma + cbase + i), y * y, __ldg(p.gdn_beta + cbase + i));
-                master[i] = p.fuse_gdn == 3 ? y * rsqrtf(n) : y * sqrtf(n);
+            for (int h = 0; h < HALF; ++h) {
+                const int c = cbase + 32 * h;
+                if (p.fuse_gdn == 3) norm_diag<32, false>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
+                else norm_diag<32, true>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
             }
         }
         if (ok && (p.fuse_gdn == 1 || p.fuse_gdn == 2)) {
             // y = conv + bias, then the norm GEMM on y^2 (see above)
 #pragma unroll
-            for (int i = 0; i < HALF * 32; ++i) master[i] += __ldg(p.bias + cbase + i);
+            for (int h = 0; h < HALF; ++h) add_bias<32>(master + 32 * h, p.bias + cbase + 32 * h);
             const int m = quarter * 32 + lane;
             if constexpr (ATM) {
                 // this thread's chunks (HALF of them) -> TMEM A slots HALF*half + h, its lane
@@ -766,15 +834,11 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
             if (ok) {
                 tc_fence_after();
 #pragma unroll
-                for (int h = 0; h < HALF; ++h) {
-                    float v[32];
-                    tmem_ld32(lane_base + (uint32_t)(h * 32), v);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float n = v[i] + __ldg(p.gdn_beta + cbase + h * 32 + i);
-                        const float y = master[h * 32 + i];
-                        master[h * 32 + i] = p.fuse_gdn == 1 ? y * rsqrtf(n) : y * sqrtf(n);
-                    }
+                for (int h = 0; h < 2 * HALF; ++h) {   // 16 columns at a time
+                    float v[16];
+                    tmem_ld16(lane_base + (uint32_t)(h * 16), v);
+                    if (p.fuse_gdn == 1) norm_n<16, false>(master + h * 16, v, p.gdn_beta + cbase + h * 16);
+                    else norm_n<16, true>(master + h * 16, v, p.gdn_beta + cbase + h * 16);
                 }
             }
         }
@@ -803,12 +867,14 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                     if (p.epi == EPI_GDN || p.epi == EPI_IGDN)
                         xg = *reinterpret_cast<const float4 *>(p.gdn_x + opix * p.ostride + p.ocoff + cbase + 4 * q);
                     const float *xp = reinterpret_cast<const float *>(&xg);
+                    const float4 b4 = ld_param4(p.bias + cbase + 4 * q);
+                    const float bb[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        float y = master[4 * q + e] + __ldg(p.bias + cbase + 4 * q + e);
+                        float y = master[4 * q + e] + bb[e];
                         if (p.epi == EPI_RELU) y = fmaxf(y, 0.f);
-                        else if (p.epi == EPI_GDN) y = xp[e] * rsqrtf(y);
-                        else if (p.epi == EPI_IGDN) y = xp[e] * sqrtf(y);
+                        else if (p.epi == EPI_GDN) y = norm_apply<false>(xp[e], y);
+                        else if (p.epi == EPI_IGDN) y = norm_apply<true>(xp[e], y);
                         op[e] = y;
                     }
                     reinterpret_cast<float4 *>(dst)[q] = o;
@@ -1069,20 +1135,25 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
             tc_fence_before();
             mbar_arrive(&pempty[g & 1]);
         }
-        if constexpr (EB == 1) {   // undo the e4m3 scales: x = stored * in_scale, w = stored * w_scale[o]
 #pragma unroll
-            for (int i = 0; i < HALF * 32; ++i) master[i] *= __ldg(p.w_scale + cbase + i) * p.in_scale;
-        }
-        if (p.bias) {
+        for (int h = 0; h < HALF; ++h) {
+            float *mh = master + 32 * h;
+            if constexpr (EB == 1) {   // undo the e4m3 scales: x = stored * in_scale, w = stored * w_scale[o]
 #pragma unroll
-            for (int i = 0; i < HALF * 32; ++i) master[i] += __ldg(p.bias + cbase + i);
+                for (int q = 0; q < 8; ++q) {
+                    const float4 w = ld_param4(p.w_scale + cbase + 32 * h + 4 * q);
+                    mh[4 * q] *= w.x * p.in_scale; mh[4 * q + 1] *= w.y * p.in_scale;
+                    mh[4 * q + 2] *= w.z * p.in_scale; mh[4 * q + 3] *= w.w * p.in_scale;
+                }
+            }
+            if (p.bias) add_bias<32>(mh, p.bias + cbase + 32 * h);
         }
         if (ok && p.fuse_gdn >= 3) {   // 1DN / inverse 1DN, per channel
 #pragma unroll
-            for (int i = 0; i < HALF * 32; ++i) {
-                const float y = master[i];
-                const float n = fmaf(__ldg(p.gdn_gamma + cbase + i), y * y, __ldg(p.gdn_beta + cbase + i));
-                master[i] = p.fuse_gdn == 3 ? y * rsqrtf(n) : y * sqrtf(n);
+            for (int h = 0; h < HALF; ++h) {
+                const int c = cbase + 32 * h;
+                if (p.fuse_gdn == 3) norm_diag<32, false>(master + 32 * h, nullptr, p.gdn_gamma + c, p.gdn_beta + c);
+                else norm_diag<32, true>(master + 32 * h, nullptr, p.gdn_gamma + c, p.gdn_beta + c);
             }
         }
         if (ok && NORM && (p.fuse_gdn == 1 || p.fuse_gdn == 2)) {
@@ -1124,15 +1195,11 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
             } else {
                 tc_fence_after();
 #pragma unroll
-                for (int h = 0; h < HALF; ++h) {
-                    float v[32];
-                    tmem_ld32(lane_base + (uint32_t)(h * 32), v);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float n = v[i] + __ldg(p.gdn_beta + cbase + h * 32 + i);
-                        const float y = master[h * 32 + i];
-                        master[h * 32 + i] = p.fuse_gdn == 1 ? y * rsqrtf(n) : y * sqrtf(n);
-                    }
+                for (int h = 0; h < 2 * HALF; ++h) {   // 16 columns at a time
+                    float v[16];
+                    tmem_ld16(lane_base + (uint32_t)(h * 16), v);
+                    if (p.fuse_gdn == 1) norm_n<16, false>(master + h * 16, v, p.gdn_beta + cbase + h * 16);
+                    else norm_n<16, true>(master + h * 16, v, p.gdn_beta + cbase + h * 16);
                 }
             }
         }
@@ -1362,8 +1429,15 @@ void build_weights(const float *w, int Cout, int T, int Cin, TcWeights *out) {
     out->valid = true;
 }
 
+// The epilogues read per-channel parameters (bias, norm beta / gamma) four at a time.
+bool params_aligned(const ConvDesc &d) {
+    auto a16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    return a16(d.bias) && a16(d.gdn_beta) && a16(d.gdn_gamma);
+}
+
 bool can_run(const ConvDesc &d, const TcWeights &w) {
     if (!w.valid || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout || !d.bias || !d.status) return false;
+    if (!params_aligned(d)) return false;
     if ((reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15)) return false;
     if ((d.epi == EPI_GDN || d.epi == EPI_IGDN) && !d.gdn_x) return false;
     if (d.in_dt != DT_F32 || (d.out_dt != DT_F32 && !d.fuse_gdn)) return false;
@@ -1481,6 +1555,7 @@ bool lp_shape_ok(const ConvDesc &d) {
     if (d.Cout == 64 && e4) return false;
     if (!d.status || (reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15))
         return false;
+    if (!params_aligned(d)) return false;
     if (d.epi != EPI_NONE && d.epi != EPI_RELU && d.epi != EPI_MASK) return false;
     if (d.epi == EPI_MASK && (!d.gdn_x || (reinterpret_cast<uintptr_t>(d.gdn_x) & 15) ||
                               (d.out_dt != DT_BF16 && d.out_dt != DT_F32)))
