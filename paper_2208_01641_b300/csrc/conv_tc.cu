@@ -41,6 +41,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -87,6 +88,7 @@ struct Params {
     const float *gdn_gamma;       // fuse_gdn 3 / 4 (1DN): per-channel gamma
     int kchunks;
     uint32_t tmem_cols;
+    int ntiles;                   // conv_tcp_kernel: tiles of the launch
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
 };
 
@@ -109,14 +111,24 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// n arrivals at once (completes a phase that expects n)
+__device__ __forceinline__ void mbar_arrive_n(uint64_t *bar, uint32_t n) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(n) : "memory");
+}
+
+// A waiting thread is suspended until the phase completes or the hint
+// (nanoseconds) runs out, so idle producer / MMA lanes leave the issue slots
+// to the warps doing the work.
+constexpr uint32_t WAIT_HINT_NS = 20000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(WAIT_HINT_NS)
         : "memory");
     return ok != 0;
 }
@@ -163,6 +175,30 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *tm, ui
         "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
         : "memory");
 }
+
+// Tensor stores from a 128-byte-swizzled shared-memory box (bulk groups of
+// the issuing thread).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *tm, const void *src, int c0, int c1) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(smem_u32(src)), "r"(c0), "r"(c1)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap *tm, const void *src, int c0, int c1, int c2, int c3,
+                                             int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(tm)),
+        "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the committed stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// the committed stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
@@ -892,6 +928,435 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
 }
 
 
+
+// ------------------------------------------------------------------ persistent FP32 kernel
+//
+// conv_tcp_kernel: the Cout = 128 FP32 path (A split into TMEM) as a
+// persistent kernel, one CTA per SM taking tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ...  Timestamps inside conv_tc_kernel showed every 128-pixel tile
+// paying about 2 us of start-up (barrier set-up, TMEM allocation, the first
+// TMA round trip), 1 us between CTAs and 2.4 us of output stores before its
+// SM takes the next tile.  Here these overlap the neighbouring tiles' work:
+//   * one load ring runs across tiles, so the producer fetches the next
+//     tile's first chunks while this tile's epilogue runs;
+//   * the fused norm's gamma (hi / lo slices of its four 32-channel chunks:
+//     eight 16 KB boxes of the stages' A / B layout) rides the ring as three
+//     entries of three boxes each, loaded as soon as the tile's last MMAs
+//     free their stages; y^2 (hi / lo) of the four chunks goes to four fixed
+//     TMEM slots (the ring's three, idle once the tile's last group is
+//     folded, and one more), and the norm GEMM's result is one more group of
+//     the ping-pong partial buffers;
+//   * the finished tile is staged in shared memory as four 128-byte-swizzled
+//     boxes of 32 channels and leaves by TMA store while the warps go on.
+// The arithmetic is conv_tc_kernel's: per-chunk TF32 hi / lo split, 3xTF32
+// products, FOLD-chunk partial sums folded into float32 registers.
+template <int STAGES>
+__global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tcp_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                       const __grid_constant__ CUtensorMap tmBh,
+                                                                       const __grid_constant__ CUtensorMap tmBl,
+                                                                       const __grid_constant__ CUtensorMap tmGh,
+                                                                       const __grid_constant__ CUtensorMap tmGl,
+                                                                       const __grid_constant__ CUtensorMap tmO,
+                                                                       const __grid_constant__ Params p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int COUT = 128, HALF = 2;
+    constexpr int B_BYTES = COUT * KCH * 4;
+    constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;
+    constexpr int BOX_BYTES = BLOCK_M * 128;          // one output box: 128 rows x 32 channels
+    constexpr int GCH = COUT / KCH;                   // gamma slices of the norm GEMM
+    // TMEM: two partial buffers, then 2 x KCH columns (hi, lo) per A slot: one
+    // per stage, and GCH for the norm GEMM's y^2 (the first STAGES shared)
+    static_assert(2 * COUT + (STAGES > GCH ? STAGES : GCH) * 2 * KCH <= 512, "TMEM budget");
+    uint8_t *otile = smem + STAGES * STAGE_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(otile + GCH * BOX_BYTES);
+    uint64_t *full = bars, *conv = bars + STAGES, *empty = bars + 2 * STAGES;
+    uint64_t *pfull = bars + 3 * STAGES, *pempty = pfull + 2, *ebar = pempty + 2, *ready = ebar + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ready + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int groups = (p.kchunks + FOLD - 1) / FOLD;
+    const bool gdn = p.fuse_gdn == 1 || p.fuse_gdn == 2;
+    // gamma boxes: piece P = 2 c + (0: hi, 1: lo) of chunk c, in area P % 3
+    // (0: A, 1: B hi, 2: B lo) of gamma entry P / 3
+    constexpr int NGE = (2 * GCH + 2) / 3;
+    static_assert(NGE <= STAGES, "the gamma entries fit the ring at once");
+    const int entries = p.kchunks + (gdn ? NGE : 0);   // ring entries per tile
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], EPI_THREADS);
+            mbar_init(&empty[s], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&pfull[q], 1);
+            mbar_init(&pempty[q], EPI_THREADS);
+        }
+        mbar_init(ebar, EPI_THREADS);
+        mbar_init(ready, EPI_THREADS);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto stage_a = [&](int s) { return smem + s * STAGE_BYTES; };
+    auto stage_bh = [&](int s) { return smem + s * STAGE_BYTES + A_BYTES; };
+    auto stage_bl = [&](int s) { return smem + s * STAGE_BYTES + A_BYTES + B_BYTES; };
+    auto slot_hi = [&](int s) { return tmem + (uint32_t)(2 * COUT + s * 2 * KCH); };
+    auto slot_lo = [&](int s) { return tmem + (uint32_t)(2 * COUT + s * 2 * KCH + KCH); };
+    auto area = [&](int s, int a) { return smem + s * STAGE_BYTES + a * A_BYTES; };   // A_BYTES == B_BYTES
+    static_assert(A_BYTES == B_BYTES, "gamma boxes fill any area");
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(p.status, ST_TIMEOUT);
+    };
+    // origin of a tile: image b, output-grid row i0 and column j0 (grid
+    // modes), or first pixel p0 (MODE_FLAT)
+    auto origin = [&](int tile, int &b, int &i0, int &j0, int64_t &p0) {
+        b = i0 = j0 = 0;
+        p0 = (int64_t)tile * BLOCK_M;
+        if (p.mode != MODE_FLAT) {
+            const int tx = tile % p.tiles_x, t = tile / p.tiles_x;
+            i0 = (t % p.tiles_y) * p.R;
+            j0 = tx * p.Wt;
+            b = t / p.tiles_y;
+        }
+    };
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            const uint32_t tx_bytes = (p.mode == MODE_IM2COL ? 0 : A_BYTES) + 2 * B_BYTES;
+            uint32_t v = 0;   // ring entry
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+                int b, i0, j0;
+                int64_t p0;
+                origin(tile, b, i0, j0, p0);
+                for (int kc = 0; kc < entries; ++kc, ++v) {
+                    const int s = v % STAGES;
+                    if (*abort_flag || !mbar_wait(&empty[s], ((v / STAGES) & 1) ^ 1)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    if (kc < p.kchunks) {
+                        const int t = kc / p.cpt;
+                        const int c0 = (kc % p.cpt) * KCH;
+                        mbar_expect_tx(&full[s], tx_bytes);
+                        if (p.mode == MODE_S2) {
+                            const int du = p.du[t], dv = p.dv[t];
+                            tma_load_5d(stage_a(s), &tmA, &full[s], (dv & 1) * p.Cin + c0, j0 + (dv >> 1), du & 1,
+                                        i0 + (du >> 1), b);
+                        } else if (p.mode == MODE_S1) {
+                            tma_load_4d(stage_a(s), &tmA, &full[s], c0, j0 + p.dv[t], i0 + p.du[t], b);
+                        } else if (p.mode == MODE_FLAT) {
+                            tma_load_2d(stage_a(s), &tmA, &full[s], c0, (int)p0);
+                        }
+                        tma_load_2d(stage_bh(s), &tmBh, &full[s], kc * KCH, 0);
+                        tma_load_2d(stage_bl(s), &tmBl, &full[s], kc * KCH, 0);
+                    } else {   // gamma entry e of the norm GEMM: pieces 3 e .. 3 e + 2
+                        const int e = kc - p.kchunks;
+                        const int np = min(3, 2 * GCH - 3 * e);
+                        mbar_expect_tx(&full[s], np * B_BYTES);
+                        for (int a = 0; a < np; ++a) {
+                            const int P = 3 * e + a;
+                            tma_load_2d(area(s, a), P % 2 ? &tmGl : &tmGh, &full[s], (P / 2) * KCH, 0);
+                        }
+                    }
+                }
+            }
+            if (!ok) {   // wait (bounded) for loads still in flight
+                for (uint32_t u = v > STAGES ? v - STAGES : 0; u < v; ++u) mbar_wait(&full[u % STAGES], (u / STAGES) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(BLOCK_M, COUT);
+            uint32_t v = 0, g = 0;   // ring entry, partial-buffer group
+            bool ok = true;
+            int tk = 0;              // tiles done
+            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x, ++tk) {
+                for (int kc = 0; kc < p.kchunks; ++kc, ++v) {
+                    const int s = v % STAGES;
+                    const bool first = kc % FOLD == 0;
+                    const bool last = kc % FOLD == FOLD - 1 || kc == p.kchunks - 1;
+                    const uint32_t q = g & 1;
+                    if (first && g >= 2 && (*abort_flag || !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1))) {
+                        fail();   // partial buffer q must have been read
+                        ok = false;
+                        break;
+                    }
+                    if (*abort_flag || !mbar_wait(&conv[s], (v / STAGES) & 1)) {   // A slot s written
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tmem + q * COUT;
+                    const uint32_t bh = smem_u32(stage_bh(s)), bl = smem_u32(stage_bl(s));
+#pragma unroll
+                    for (int kk = 0; kk < KCH / 8; ++kk) {
+                        const uint64_t dbh = sdesc(bh + kk * 32), dbl = sdesc(bl + kk * 32);
+                        mma_tf32_ts(dt, slot_hi(s) + 8 * kk, dbh, idesc, (!first || kk > 0) ? 1u : 0u);
+                        mma_tf32_ts(dt, slot_hi(s) + 8 * kk, dbl, idesc, 1u);
+                        mma_tf32_ts(dt, slot_lo(s) + 8 * kk, dbh, idesc, 1u);
+                    }
+                    mma_commit(&empty[s]);
+                    if (last) {
+                        mma_commit(&pfull[q]);
+                        ++g;
+                    }
+                }
+                if (!ok || !gdn) continue;
+                // the norm GEMM: y^2 (A slots 0 .. GCH-1) x gamma (the NGE entries)
+                const uint32_t q = g & 1;
+                if (*abort_flag || (g >= 2 && !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1)) ||
+                    !mbar_wait(ready, tk & 1)) {
+                    fail();
+                    ok = false;
+                    continue;
+                }
+                const uint32_t dt = tmem + q * COUT;
+                int landed = 0;   // gamma entries waited for
+#pragma unroll
+                for (int c = 0; c < GCH; ++c) {
+                    const int ph = 2 * c, pl = 2 * c + 1;   // pieces of chunk c
+                    while (ok && landed <= pl / 3) {
+                        const uint32_t ve = v + landed;
+                        if (*abort_flag || !mbar_wait(&full[ve % STAGES], (ve / STAGES) & 1)) {
+                            fail();
+                            ok = false;
+                        }
+                        ++landed;
+                    }
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t bh = smem_u32(area((v + ph / 3) % STAGES, ph % 3));
+                    const uint32_t bl = smem_u32(area((v + pl / 3) % STAGES, pl % 3));
+#pragma unroll
+                    for (int kk = 0; kk < KCH / 8; ++kk) {
+                        const uint64_t dbh = sdesc(bh + kk * 32), dbl = sdesc(bl + kk * 32);
+                        mma_tf32_ts(dt, slot_hi(c) + 8 * kk, dbh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32_ts(dt, slot_hi(c) + 8 * kk, dbl, idesc, 1u);
+                        mma_tf32_ts(dt, slot_lo(c) + 8 * kk, dbh, idesc, 1u);
+                    }
+                    // an entry whose last piece belongs to chunk c goes back to the producer;
+                    // conv[s] completes its phase for it here (one phase per ring entry;
+                    // the stage's previous phase is complete: its MMAs were issued above)
+#pragma unroll
+                    for (int e = 0; e < NGE; ++e) {
+                        const int lastp = 3 * e + 2 < 2 * GCH - 1 ? 3 * e + 2 : 2 * GCH - 1;
+                        if (lastp / 2 != c) continue;
+                        const uint32_t ve = v + e;
+                        mbar_arrive_n(&conv[ve % STAGES], EPI_THREADS);
+                        mma_commit(&empty[ve % STAGES]);
+                    }
+                }
+                if (!ok) continue;
+                mma_commit(&pfull[q]);
+                ++g;
+                v += NGE;
+            }
+        }
+    } else {
+        // ---------------- split, fold, epilogue (warps 2..9) ----------------
+        const int et = threadIdx.x - 64;
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        const int m = quarter * 32 + lane;                 // this thread's TMEM lane / tile row
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const uint32_t lane_base = tmem + lane_off + (uint32_t)(half * HALF * 32);
+        const int cbase = half * HALF * 32;                // this thread's output channels
+        uint32_t v = 0, g = 0, eph = 0;                    // ring entry, group, epilogue-barrier phase
+        bool ok = true;
+        float master[HALF * 32];
+        // all epilogue threads (bounded, like every other wait)
+        auto esync = [&]() {
+            if (!ok) return;
+            mbar_arrive(ebar);
+            if (!mbar_wait(ebar, eph & 1)) {
+                fail();
+                ok = false;
+            }
+            ++eph;
+        };
+        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+            int b, i0, j0;
+            int64_t p0;
+            origin(tile, b, i0, j0, p0);
+#pragma unroll
+            for (int i = 0; i < HALF * 32; ++i) master[i] = 0.f;
+            const uint32_t g0 = g;
+            int folded = 0;
+            auto fold = [&](int k) {   // group g0 + k into master
+                const uint32_t gg = g0 + k;
+                if (!ok) return;
+                if (!mbar_wait(&pfull[gg & 1], (gg >> 1) & 1)) {
+                    fail();
+                    ok = false;
+                    return;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    float x[32];
+                    tmem_ld32(lane_base + (uint32_t)((gg & 1) * COUT + h * 32), x);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += x[i];
+                }
+                tc_fence_before();
+                mbar_arrive(&pempty[gg & 1]);
+            };
+            for (int kc = 0; kc < p.kchunks && ok; ++kc, ++v) {
+                const int s = v % STAGES;
+                // row m, columns [16 half, 16 half + 16) of the chunk; MODE_IM2COL gathers
+                // them from global memory first, overlapping the weights' TMA
+                float x[16], hv[16], lv[16];
+                if (p.mode == MODE_IM2COL) {
+                    const int gi = i0 + m / p.Wt, gj = j0 + m % p.Wt;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int k = kc * KCH + 16 * half + e;
+                        const int t = k / p.Cin, c = k - t * p.Cin;
+                        float val = 0.f;
+                        if (t < p.T) {
+                            const int yi = p.s * gi + p.du[t], xi = p.s * gj + p.dv[t];
+                            if (yi >= 0 && yi < p.Hi && xi >= 0 && xi < p.Wi)
+                                val = __ldg(p.in + (((int64_t)b * p.Hi + yi) * p.Wi + xi) * p.Cin + c);
+                        }
+                        x[e] = val;
+                    }
+                }
+                if (*abort_flag || !mbar_wait(&full[s], (v / STAGES) & 1)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                if (p.mode != MODE_IM2COL) {
+                    const uint8_t *row = stage_a(s) + m * 128;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 f = *reinterpret_cast<const float4 *>(row + (((4 * half + q) ^ (m & 7)) << 4));
+                        x[4 * q] = f.x; x[4 * q + 1] = f.y; x[4 * q + 2] = f.z; x[4 * q + 3] = f.w;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    float y = x[e];
+                    if (p.in_xform == IN_ABS) y = fabsf(y);
+                    else if (p.in_xform == IN_SQUARE) y = y * y;
+                    hv[e] = tf32_rna(y);
+                    lv[e] = tf32_rna(y - hv[e]);
+                }
+                tmem_st16(slot_hi(s) + lane_off + 16 * half, hv);
+                tmem_st16(slot_lo(s) + lane_off + 16 * half, lv);
+                tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(&conv[s]);
+                // mid-way through group k, the MMAs of group k-1 are done: fold it
+                if (kc % FOLD == FOLD / 2 && kc / FOLD >= 1 && folded < kc / FOLD) fold(folded++);
+            }
+            while (ok && folded < groups) fold(folded++);
+            g = g0 + groups;
+            if (ok) {
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    const int c = cbase + 32 * h;
+                    if (p.fuse_gdn == 3) norm_diag<32, false>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
+                    else if (p.fuse_gdn == 4) norm_diag<32, true>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
+                    else add_bias<32>(master + 32 * h, p.bias + c);
+                }
+                if (p.epi == EPI_RELU) {
+#pragma unroll
+                    for (int i = 0; i < HALF * 32; ++i) master[i] = fmaxf(master[i], 0.f);
+                }
+            }
+            if (gdn) {
+                // y^2 (hi / lo) of this thread's chunks HALF half + h into A slots of the
+                // same number: every slot is idle (the last group's MMAs are done)
+                if (ok) {
+#pragma unroll
+                    for (int h = 0; h < HALF; ++h) {
+                        const int slot = HALF * half + h;
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            float hv[16], lv[16];
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                const float sq = master[32 * h + 16 * q + i] * master[32 * h + 16 * q + i];
+                                hv[i] = tf32_rna(sq);
+                                lv[i] = tf32_rna(sq - hv[i]);
+                            }
+                            tmem_st16(slot_hi(slot) + lane_off + 16 * q, hv);
+                            tmem_st16(slot_lo(slot) + lane_off + 16 * q, lv);
+                        }
+                    }
+                    tmem_st_wait();
+                    tc_fence_before();
+                    mbar_arrive(ready);
+                }
+                v += NGE;
+                // the norm GEMM's result (group g): y / sqrt(beta + .) or y * sqrt(.)
+                if (ok && (*abort_flag || !mbar_wait(&pfull[g & 1], (g >> 1) & 1))) {
+                    fail();
+                    ok = false;
+                }
+                if (ok) {
+                    tc_fence_after();
+#pragma unroll
+                    for (int h = 0; h < 2 * HALF; ++h) {
+                        float n[16];
+                        tmem_ld16(lane_base + (uint32_t)((g & 1) * COUT + h * 16), n);
+                        if (p.fuse_gdn == 1) norm_n<16, false>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
+                        else norm_n<16, true>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
+                    }
+                    tc_fence_before();
+                    mbar_arrive(&pempty[g & 1]);
+                }
+                ++g;
+            }
+            // stage the tile once the previous tile's store has read the buffer
+            if (et == 0) bulk_wait_read();
+            esync();
+            if (ok) {
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    uint8_t *row = otile + (HALF * half + h) * BOX_BYTES + m * 128;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        *reinterpret_cast<float4 *>(row + ((q ^ (m & 7)) << 4)) =
+                            make_float4(master[32 * h + 4 * q], master[32 * h + 4 * q + 1],
+                                        master[32 * h + 4 * q + 2], master[32 * h + 4 * q + 3]);
+                }
+                fence_proxy_async();
+            }
+            esync();
+            if (ok && et == 0 && !*abort_flag) {
+                for (int bx = 0; bx < GCH; ++bx) {
+                    if (p.mode == MODE_FLAT) tma_store_2d(&tmO, otile + bx * BOX_BYTES, 32 * bx, (int)p0);
+                    else tma_store_5d(&tmO, otile + bx * BOX_BYTES, p.oxo * p.ostride + 32 * bx, j0, p.oyo, i0, b);
+                }
+                bulk_commit();
+            }
+        }
+        if (et == 0) bulk_wait_all();
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 // ------------------------------------------------------------------ BF16 kernel
 //
 // The BF16 precision form: activations between BF16 layers are bf16 NHWC in
@@ -1295,6 +1760,40 @@ bool is_flat(const ConvDesc &d) {
            d.oxm == 1 && d.Ho == d.Hi && d.Wo == d.Wi;
 }
 
+int sm_count() {
+    static int n = 0;
+    if (n <= 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
+// The output of a conv_tcp_kernel launch as a tensor map for its 32-channel
+// boxes.  Grid modes: output pixel (b, oym * gi + oyo, oxm * gj + oxo),
+// channel c, of a row stride of ostride elements from channel ocoff, viewed
+// as (oxm * ostride - ocoff, Gw, oym, Gh, B) -- the x phase merged into the
+// channel dimension -- so a tile is one box at (oxo * ostride + 32 k, j0, oyo,
+// i0, b); boxes past Gw or Gh are clipped by the store.  MODE_FLAT: (ostride
+// - ocoff, rows) at (32 k, p0).
+bool make_out_map(CUtensorMap *m, const ConvDesc &d, const Params &p) {
+    const uint64_t os = (uint64_t)p.ostride;
+    float *base = d.out + p.ocoff;
+    if (p.mode == MODE_FLAT) {
+        const uint64_t dims[2] = {os - p.ocoff, (uint64_t)p.rows};
+        const uint64_t strides[1] = {os * 4};
+        const uint32_t box[2] = {32, BLOCK_M};
+        return make_map(m, base, 2, dims, strides, box);
+    }
+    const uint64_t dims[5] = {(uint64_t)p.oxm * os - p.ocoff, (uint64_t)d.Gw, (uint64_t)p.oym, (uint64_t)d.Gh,
+                              (uint64_t)d.B};
+    const uint64_t strides[4] = {(uint64_t)p.oxm * os * 4, (uint64_t)d.Wo * os * 4, (uint64_t)p.oym * d.Wo * os * 4,
+                                 (uint64_t)d.Ho * d.Wo * os * 4};
+    const uint32_t box[5] = {32, (uint32_t)p.Wt, 1, (uint32_t)p.R, 1};
+    return make_map(m, base, 5, dims, strides, box);
+}
+
 // Choose the R x Wt output block (R * Wt = 128) with the least padding.
 void pick_tile(int Gh, int Gw, int *R, int *Wt) {
     double best = 1e30;
@@ -1538,6 +2037,19 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     const CUtensorMap *gmaps = (d.fuse_gdn == 1 || d.fuse_gdn == 2)
                                    ? reinterpret_cast<const CUtensorMap *>(static_cast<const TcWeights *>(d.gdn_w)->maps)
                                    : maps;
+    CUtensorMap tmO;
+    if (d.Cout == 128 && p.out_dt == DT_F32 && (d.epi == EPI_NONE || d.epi == EPI_RELU) &&
+        make_out_map(&tmO, d, p)) {
+        // persistent: one CTA per SM, 3 stages + the staged output tile
+        constexpr int TCP_STAGES = 3;
+        const int smem = TCP_STAGES * (A_BYTES + 2 * 128 * KCH * 4) + BLOCK_M * 128 * 4 + 256 + 1024;
+        p.ntiles = (int)grid;
+        const unsigned pgrid = std::min<unsigned>(grid, (unsigned)sm_count());
+        cudaFuncSetAttribute(conv_tcp_kernel<TCP_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        conv_tcp_kernel<TCP_STAGES><<<pgrid, 64 + EPI_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1],
+                                                                          tmO, p);
+        return true;
+    }
     const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
     if (d.Cout == 128)
         launch_kernel<4, 2>(grid, smem, st, tmA, maps[0], maps[1], gmaps[0], gmaps[1], p);
