@@ -744,8 +744,9 @@ def roofline(rep, peaks):
 # DRAM bytes (read + write) per launch of the dominant kernels, from the ncu
 # captures summarised in profiles/ (None until a capture of the current build)
 TRAFFIC = {
-    # profiles/conv_tc_g_a_conv1_gdn1_fp32_b1.md: 143.3 MB per batch-1 launch, x8 tiles
-    "g_a.conv1+gdn1:tc": 8 * 144.164864e6,
+    # conv_tcw_kernel, ncu on one batch-1 launch: 131.7 MB read + 13.8 MB written,
+    # x8 for the batch-8 launch (traffic grows with the tiles)
+    "g_a.conv1+gdn1:tc": 8 * 145.513728e6,
 }
 
 
