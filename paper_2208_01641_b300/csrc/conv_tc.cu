@@ -195,6 +195,12 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 // the committed stores are complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// Warpgroup register budgets (every thread of the warpgroup executes these)
+template <int N>
+__device__ __forceinline__ void reg_release() { asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N)); }
+template <int N>
+__device__ __forceinline__ void reg_claim() { asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N)); }
+
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
                  "r"(ncols)
@@ -406,6 +412,10 @@ __device__ __forceinline__ void mask_row(float *v, const void *m, int64_t off, i
 // Round to TF32 (10 stored mantissa bits), to nearest, ties away from zero:
 // add half of the 13 dropped bits to the magnitude, then clear them.  Same
 // result as cvt.rna.tf32.f32 for finite values, at integer-ALU rate.
+// x with its low 13 mantissa bits cleared: the TF32 value the tensor core
+// takes an FP32 operand for
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
 __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
 }
@@ -1775,6 +1785,409 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tcw_kernel(const __g
     }
 }
 
+// ------------------------------------------------------------------ warp-specialised wide-N FP32 kernel
+//
+// conv_tcx_kernel: conv_tcw_kernel's arithmetic, ring and TMEM use with the
+// work spread over 16 warps so that a tile's epilogue runs under the next
+// tile's main loop.  Timestamps in conv_tcw_kernel put its per-tile epilogue
+// (last fold, y^2, norm GEMM, normalisation, output) at about 7.4 us, against
+// 0.7 us per K chunk, with the tensor pipe idle throughout.  Here six warps
+// only split A, and eight epilogue warps fold each partial sum as it
+// completes and finish the tile while the next one streams through the
+// ring: the tensor pipe waits only for a tile's last fold and its y^2.
+// Registers move from the producer / MMA / split warpgroups (72 a thread) to
+// the epilogue warpgroups (184) with setmaxnreg; the shares add up to the
+// 64 K registers the block is launched with.
+//   warp 0       TMA producer            warp 1      TMEM allocation, MMA issue
+//   warps 2..7   split A (hi / lo, in place in shared memory)
+//   warps 8..15  fold, bias / norm, output (TMEM lanes 32 (warp % 4) ..)
+constexpr int TCX_THREADS = 512, TCX_SPLIT = 192, TCX_EPI = 256;
+
+template <int STAGES>
+__global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                       const __grid_constant__ CUtensorMap tmBh,
+                                                                       const __grid_constant__ CUtensorMap tmBl,
+                                                                       const __grid_constant__ CUtensorMap tmGh,
+                                                                       const __grid_constant__ CUtensorMap tmGl,
+                                                                       const __grid_constant__ CUtensorMap tmO,
+                                                                       const __grid_constant__ Params p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int COUT = 128, HALF = 2;
+    constexpr int AREA = A_BYTES;                     // 128 rows x 128 bytes
+    constexpr int STAGE_BYTES = 4 * AREA;             // A (split in place to hi), A lo, B hi, B lo
+    constexpr int GCH = COUT / KCH;                   // gamma chunks of the norm GEMM
+    constexpr int NGE = GCH / 2;                      // gamma entries: two chunks ([hi | lo] each) per stage
+    static_assert(NGE <= STAGES, "the gamma entries fit the ring at once");
+    static_assert(COUT * KCH * 4 == AREA, "a weight slice fills one area");
+    uint8_t *otile = smem + STAGES * STAGE_BYTES;     // two output boxes of 32 channels
+    uint64_t *bars = reinterpret_cast<uint64_t *>(otile + 2 * AREA);
+    uint64_t *full = bars, *conv = bars + STAGES, *empty = bars + 2 * STAGES;
+    uint64_t *pfull = bars + 3 * STAGES, *pempty = pfull + 2, *ebar = pempty + 2, *ready = ebar + 1;
+    uint64_t *done = ready + 1;   // the epilogue warps' last TMEM access is behind them
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int groups = (p.kchunks + FOLD - 1) / FOLD;
+    const bool gdn = p.fuse_gdn == 1 || p.fuse_gdn == 2;
+    const int entries = p.kchunks + (gdn ? NGE : 0);   // ring entries per tile
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], TCX_SPLIT);
+            mbar_init(&empty[s], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&pfull[q], 1);
+            mbar_init(&pempty[q], TCX_EPI);
+        }
+        mbar_init(ebar, TCX_EPI);
+        mbar_init(ready, TCX_EPI);
+        mbar_init(done, TCX_EPI);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto area = [&](int s, int a) { return smem + s * STAGE_BYTES + a * AREA; };
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(p.status, ST_TIMEOUT);
+    };
+    auto origin = [&](int tile, int &b, int &i0, int &j0, int64_t &p0) {
+        b = i0 = j0 = 0;
+        p0 = (int64_t)tile * BLOCK_M;
+        if (p.mode != MODE_FLAT) {
+            const int tx = tile % p.tiles_x, t = tile / p.tiles_x;
+            i0 = (t % p.tiles_y) * p.R;
+            j0 = tx * p.Wt;
+            b = t / p.tiles_y;
+        }
+    };
+
+    if (warp < 8) reg_release<72>();   // warpgroups 0, 1; the epilogue's take the rest
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            const uint32_t tx_bytes = (p.mode == MODE_IM2COL ? 0 : AREA) + 2 * AREA;
+            uint32_t v = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+                int b, i0, j0;
+                int64_t p0;
+                origin(tile, b, i0, j0, p0);
+                for (int kc = 0; kc < entries; ++kc, ++v) {
+                    const int s = v % STAGES;
+                    if (*abort_flag || !mbar_wait(&empty[s], ((v / STAGES) & 1) ^ 1)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    if (kc < p.kchunks) {
+                        const int t = kc / p.cpt;
+                        const int c0 = (kc % p.cpt) * KCH;
+                        mbar_expect_tx(&full[s], tx_bytes);
+                        if (p.mode == MODE_S2) {
+                            const int du = p.du[t], dv = p.dv[t];
+                            tma_load_5d(area(s, 0), &tmA, &full[s], (dv & 1) * p.Cin + c0, j0 + (dv >> 1), du & 1,
+                                        i0 + (du >> 1), b);
+                        } else if (p.mode == MODE_S1) {
+                            tma_load_4d(area(s, 0), &tmA, &full[s], c0, j0 + p.dv[t], i0 + p.du[t], b);
+                        } else if (p.mode == MODE_FLAT) {
+                            tma_load_2d(area(s, 0), &tmA, &full[s], c0, (int)p0);
+                        }
+                        tma_load_2d(area(s, 2), &tmBh, &full[s], kc * KCH, 0);
+                        tma_load_2d(area(s, 3), &tmBl, &full[s], kc * KCH, 0);
+                    } else {   // gamma entry e: chunks 2e, 2e + 1 as [hi | lo] pairs
+                        const int e = kc - p.kchunks;
+                        mbar_expect_tx(&full[s], 4 * AREA);
+                        for (int j = 0; j < 2; ++j) {
+                            tma_load_2d(area(s, 2 * j), &tmGh, &full[s], (2 * e + j) * KCH, 0);
+                            tma_load_2d(area(s, 2 * j + 1), &tmGl, &full[s], (2 * e + j) * KCH, 0);
+                        }
+                    }
+                }
+            }
+            if (!ok) {   // wait (bounded) for loads still in flight
+                for (uint32_t u = v > STAGES ? v - STAGES : 0; u < v; ++u) mbar_wait(&full[u % STAGES], (u / STAGES) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idw = idesc_tf32(BLOCK_M, 2 * COUT), idn = idesc_tf32(BLOCK_M, COUT);
+            uint32_t v = 0, g = 0;   // ring entry, partial-buffer group
+            bool ok = true;
+            int tk = 0;
+            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x, ++tk) {
+                // the previous tile's norm GEMM read its y^2 from the buffer this tile's
+                // first group writes: let it complete first
+                if (gdn && tk > 0 && (*abort_flag || !mbar_wait(&pfull[(g - 1) & 1], ((g - 1) >> 1) & 1))) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                for (int kc = 0; kc < p.kchunks; ++kc, ++v) {
+                    const int s = v % STAGES;
+                    const bool first = kc % FOLD == 0;
+                    const bool last = kc % FOLD == FOLD - 1 || kc == p.kchunks - 1;
+                    const uint32_t q = g & 1;
+                    if (first && g >= 2 && (*abort_flag || !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1))) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    if (*abort_flag || !mbar_wait(&conv[s], (v / STAGES) & 1)) {   // A split into hi / lo
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tmem + q * 2 * COUT;
+                    const uint32_t ah = smem_u32(area(s, 0)), al = smem_u32(area(s, 1)), bh = smem_u32(area(s, 2));
+#pragma unroll
+                    for (int kk = 0; kk < KCH / 8; ++kk) {
+                        const uint64_t db = sdesc(bh + kk * 32);
+                        mma_tf32(dt, sdesc(ah + kk * 32), db, idw, (!first || kk > 0) ? 1u : 0u);   // [hi | lo]
+                        mma_tf32(dt, sdesc(al + kk * 32), db, idn, 1u);                             // A lo x B hi
+                    }
+                    mma_commit(&empty[s]);
+                    if (last) {
+                        mma_commit(&pfull[q]);
+                        ++g;
+                    }
+                }
+                if (!ok || !gdn) continue;
+                // the norm GEMM into buffer g & 1; y^2 sits in the other (the tile's last group's)
+                const uint32_t q = g & 1;
+                if (*abort_flag || (g >= 2 && !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1)) ||
+                    !mbar_wait(ready, tk & 1)) {
+                    fail();
+                    ok = false;
+                    continue;
+                }
+                const uint32_t dt = tmem + q * 2 * COUT, ysl = tmem + (q ^ 1) * 2 * COUT;
+#pragma unroll
+                for (int c = 0; c < GCH; ++c) {
+                    const uint32_t ve = v + c / 2;
+                    const int s = ve % STAGES;
+                    if (c % 2 == 0) {
+                        if (*abort_flag || !mbar_wait(&full[s], (ve / STAGES) & 1)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    const uint32_t bh = smem_u32(area(s, 2 * (c % 2)));
+#pragma unroll
+                    for (int kk = 0; kk < KCH / 8; ++kk) {
+                        const uint64_t db = sdesc(bh + kk * 32);
+                        mma_tf32_ts(dt, ysl + KCH * c + 8 * kk, db, idw, (c > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32_ts(dt, ysl + COUT + KCH * c + 8 * kk, db, idn, 1u);
+                    }
+                    if (c % 2 == 1) {   // the entry's two chunks are issued: back to the producer
+                        mbar_arrive_n(&conv[s], TCX_SPLIT);   // one conv phase per ring entry
+                        mma_commit(&empty[s]);
+                    }
+                }
+                if (!ok) continue;
+                mma_commit(&pfull[q]);
+                ++g;
+                v += NGE;
+            }
+        }
+    } else if (warp < 8) {
+        // ---------------- split (warps 2..7) ----------------
+        const int st = threadIdx.x - 64;   // 0 .. TCX_SPLIT - 1
+        uint32_t v = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+            for (int kc = 0; kc < p.kchunks; ++kc, ++v) {
+                const int s = v % STAGES;
+                if (*abort_flag || !mbar_wait(&full[s], (v / STAGES) & 1)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                // The MMA reads an FP32 operand as TF32 by dropping its low 13 mantissa
+                // bits (checked on this part), so the raw activation serves as A_hi and
+                // only A_lo = x - trunc(x), exact in FP32, is written (elementwise, the
+                // swizzled layout kept); a transformed input (|x|, x^2) is written back
+                float4 *ah = reinterpret_cast<float4 *>(area(s, 0)), *al = reinterpret_cast<float4 *>(area(s, 1));
+                for (int idx = st; idx < AREA / 16; idx += TCX_SPLIT) {
+                    float4 f = ah[idx];
+                    if (p.in_xform != IN_NONE) {
+                        if (p.in_xform == IN_ABS) {
+                            f.x = fabsf(f.x); f.y = fabsf(f.y); f.z = fabsf(f.z); f.w = fabsf(f.w);
+                        } else {
+                            f.x *= f.x; f.y *= f.y; f.z *= f.z; f.w *= f.w;
+                        }
+                        ah[idx] = f;
+                    }
+                    al[idx] = make_float4(f.x - tf32_trunc(f.x), f.y - tf32_trunc(f.y), f.z - tf32_trunc(f.z),
+                                          f.w - tf32_trunc(f.w));
+                }
+                fence_proxy_async();
+                mbar_arrive(&conv[s]);
+            }
+            if (gdn) v += NGE;
+        }
+    } else {
+        // ---------------- fold, bias / norm, output (warps 8..15) ----------------
+        reg_claim<184>();
+        const int et = threadIdx.x - 256;
+        const int quarter = warp & 3, half = (warp - 8) >> 2;
+        const int m = quarter * 32 + lane;                 // this thread's TMEM lane / tile row
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const int cbase = half * HALF * 32;                // this thread's output channels
+        uint32_t g = 0, eph = 0;
+        bool ok = true;
+        float master[HALF * 32];
+        auto esync = [&]() {
+            if (!ok) return;
+            mbar_arrive(ebar);
+            if (!mbar_wait(ebar, eph & 1)) {
+                fail();
+                ok = false;
+            }
+            ++eph;
+        };
+        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+            int b, i0, j0;
+            int64_t p0;
+            origin(tile, b, i0, j0, p0);
+#pragma unroll
+            for (int i = 0; i < HALF * 32; ++i) master[i] = 0.f;
+            // every partial sum of the tile into master, as its group completes
+            for (int k = 0; k < groups && ok; ++k, ++g) {
+                if (*abort_flag || !mbar_wait(&pfull[g & 1], (g >> 1) & 1)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem + lane_off + (g & 1) * 2 * COUT + cbase;
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    float x[32];
+                    tmem_ld32(base + 32 * h, x);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += x[i];
+                    tmem_ld32(base + COUT + 32 * h, x);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += x[i];
+                }
+                tc_fence_before();
+                mbar_arrive(&pempty[g & 1]);
+            }
+            if (!ok) break;
+#pragma unroll
+            for (int h = 0; h < HALF; ++h) {
+                const int c = cbase + 32 * h;
+                if (p.fuse_gdn == 3) norm_diag<32, false>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
+                else if (p.fuse_gdn == 4) norm_diag<32, true>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
+                else add_bias<32>(master + 32 * h, p.bias + c);
+            }
+            if (p.epi == EPI_RELU) {
+#pragma unroll
+                for (int i = 0; i < HALF * 32; ++i) master[i] = fmaxf(master[i], 0.f);
+            }
+            if (gdn) {
+                // y^2 of this thread's chunks c = HALF half + h into the buffer of the
+                // tile's last group (folded above; the MMA warp writes it again only
+                // after the norm GEMM has completed): hi at column 32 c, lo at COUT + 32 c,
+                // the columns this thread has read
+                const uint32_t ysl = tmem + lane_off + ((g - 1) & 1) * 2 * COUT;
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    const uint32_t slot = ysl + KCH * (HALF * half + h);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        float hv[16], lv[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float sq = master[32 * h + 16 * q + i] * master[32 * h + 16 * q + i];
+                            hv[i] = tf32_rna(sq);
+                            lv[i] = tf32_rna(sq - hv[i]);
+                        }
+                        tmem_st16(slot + 16 * q, hv);
+                        tmem_st16(slot + COUT + 16 * q, lv);
+                    }
+                }
+                tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(ready);
+                if (*abort_flag || !mbar_wait(&pfull[g & 1], (g >> 1) & 1)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem + lane_off + (g & 1) * 2 * COUT + cbase;
+#pragma unroll
+                for (int h = 0; h < 2 * HALF; ++h) {
+                    float n[16], nl[16];
+                    tmem_ld16(base + 16 * h, n);
+                    tmem_ld16(base + COUT + 16 * h, nl);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) n[i] += nl[i];
+                    if (p.fuse_gdn == 1) norm_n<16, false>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
+                    else norm_n<16, true>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
+                }
+                tc_fence_before();
+                mbar_arrive(&pempty[g & 1]);
+                ++g;
+            }
+            // the output in two halves of 64 channels (threads of half 0, then 1)
+#pragma unroll
+            for (int ph = 0; ph < 2; ++ph) {
+                if (et == 0) bulk_wait_read();   // the previous store has read the staging boxes
+                esync();
+                if (ok && half == ph) {
+#pragma unroll
+                    for (int h = 0; h < HALF; ++h) {
+                        uint8_t *row = otile + h * AREA + m * 128;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            *reinterpret_cast<float4 *>(row + ((q ^ (m & 7)) << 4)) =
+                                make_float4(master[32 * h + 4 * q], master[32 * h + 4 * q + 1],
+                                            master[32 * h + 4 * q + 2], master[32 * h + 4 * q + 3]);
+                    }
+                    fence_proxy_async();
+                }
+                esync();
+                if (ok && et == 0 && !*abort_flag) {
+                    for (int bx = 0; bx < HALF; ++bx) {
+                        const int co = HALF * 32 * ph + 32 * bx;
+                        if (p.mode == MODE_FLAT) tma_store_2d(&tmO, otile + bx * AREA, co, (int)p0);
+                        else tma_store_5d(&tmO, otile + bx * AREA, p.oxo * p.ostride + co, j0, p.oyo, i0, b);
+                    }
+                    bulk_commit();
+                }
+            }
+        }
+        if (et == 0) bulk_wait_all();
+        tc_fence_before();
+        mbar_arrive(done);
+    }
+
+    // TMEM is released once the epilogue warps are past their last access
+    // (bounded: a stalled pipeline has latched its status already)
+    if (warp == 1) {
+        __syncwarp();
+        mbar_wait(done, 0);
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 // ------------------------------------------------------------------ BF16 kernel
 //
 // The BF16 precision form: activations between BF16 layers are bf16 NHWC in
@@ -2464,7 +2877,12 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
         constexpr int STAGES = 3;
         p.ntiles = (int)grid;
         const unsigned pgrid = std::min<unsigned>(grid, (unsigned)sm_count());
-        if (p.kchunks >= 8) {
+        if (p.kchunks >= 8 && p.mode != MODE_IM2COL) {
+            const int smem = STAGES * 4 * A_BYTES + 2 * A_BYTES + 256 + 1024;
+            cudaFuncSetAttribute(conv_tcx_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            conv_tcx_kernel<STAGES><<<pgrid, TCX_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1], tmO,
+                                                                      p);
+        } else if (p.kchunks >= 8) {
             const int smem = STAGES * 4 * A_BYTES + 2 * A_BYTES + 256 + 1024;
             cudaFuncSetAttribute(conv_tcw_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             conv_tcw_kernel<STAGES><<<pgrid, 64 + EPI_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1],
