@@ -88,7 +88,7 @@ struct Params {
     const float *gdn_gamma;       // fuse_gdn 3 / 4 (1DN): per-channel gamma
     int kchunks;
     uint32_t tmem_cols;
-    int ntiles;                   // conv_tcp_kernel: tiles of the launch
+    int ntiles;                   // conv_tcx_kernel: tiles of the launch
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
 };
 
@@ -934,873 +934,48 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
 
 
 
-// ------------------------------------------------------------------ persistent FP32 kernel
+// ------------------------------------------------------------------ persistent FP32 kernel (Cout = 128)
 //
-// conv_tcp_kernel: the Cout = 128 FP32 path (A split into TMEM) as a
-// persistent kernel, one CTA per SM taking tiles blockIdx.x, blockIdx.x +
-// gridDim.x, ...  Timestamps inside conv_tc_kernel showed every 128-pixel tile
-// paying about 2 us of start-up (barrier set-up, TMEM allocation, the first
-// TMA round trip), 1 us between CTAs and 2.4 us of output stores before its
-// SM takes the next tile.  Here these overlap the neighbouring tiles' work:
-//   * one load ring runs across tiles, so the producer fetches the next
-//     tile's first chunks while this tile's epilogue runs;
-//   * the fused norm's gamma (hi / lo slices of its four 32-channel chunks:
-//     eight 16 KB boxes of the stages' A / B layout) rides the ring as three
-//     entries of three boxes each, loaded as soon as the tile's last MMAs
-//     free their stages; y^2 (hi / lo) of the four chunks goes to four fixed
-//     TMEM slots (the ring's three, idle once the tile's last group is
-//     folded, and one more), and the norm GEMM's result is one more group of
-//     the ping-pong partial buffers;
-//   * the finished tile is staged in shared memory as four 128-byte-swizzled
-//     boxes of 32 channels and leaves by TMA store while the warps go on.
-// The arithmetic is conv_tc_kernel's: per-chunk TF32 hi / lo split, 3xTF32
-// products, FOLD-chunk partial sums folded into float32 registers.
-template <int STAGES>
-__global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tcp_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                                       const __grid_constant__ CUtensorMap tmBh,
-                                                                       const __grid_constant__ CUtensorMap tmBl,
-                                                                       const __grid_constant__ CUtensorMap tmGh,
-                                                                       const __grid_constant__ CUtensorMap tmGl,
-                                                                       const __grid_constant__ CUtensorMap tmO,
-                                                                       const __grid_constant__ Params p) {
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    constexpr int COUT = 128, HALF = 2;
-    constexpr int B_BYTES = COUT * KCH * 4;
-    constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;
-    constexpr int BOX_BYTES = BLOCK_M * 128;          // one output box: 128 rows x 32 channels
-    constexpr int GCH = COUT / KCH;                   // gamma slices of the norm GEMM
-    // TMEM: two partial buffers, then 2 x KCH columns (hi, lo) per A slot: one
-    // per stage, and GCH for the norm GEMM's y^2 (the first STAGES shared)
-    static_assert(2 * COUT + (STAGES > GCH ? STAGES : GCH) * 2 * KCH <= 512, "TMEM budget");
-    uint8_t *otile = smem + STAGES * STAGE_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(otile + GCH * BOX_BYTES);
-    uint64_t *full = bars, *conv = bars + STAGES, *empty = bars + 2 * STAGES;
-    uint64_t *pfull = bars + 3 * STAGES, *pempty = pfull + 2, *ebar = pempty + 2, *ready = ebar + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ready + 1);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int groups = (p.kchunks + FOLD - 1) / FOLD;
-    const bool gdn = p.fuse_gdn == 1 || p.fuse_gdn == 2;
-    // gamma boxes: piece P = 2 c + (0: hi, 1: lo) of chunk c, in area P % 3
-    // (0: A, 1: B hi, 2: B lo) of gamma entry P / 3
-    constexpr int NGE = (2 * GCH + 2) / 3;
-    static_assert(NGE <= STAGES, "the gamma entries fit the ring at once");
-    const int entries = p.kchunks + (gdn ? NGE : 0);   // ring entries per tile
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&conv[s], EPI_THREADS);
-            mbar_init(&empty[s], 1);
-        }
-        for (int q = 0; q < 2; ++q) {
-            mbar_init(&pfull[q], 1);
-            mbar_init(&pempty[q], EPI_THREADS);
-        }
-        mbar_init(ebar, EPI_THREADS);
-        mbar_init(ready, EPI_THREADS);
-        *abort_flag = 0;
-        fence_barrier_init();
-    }
-    if (warp == 1) tmem_alloc(tmem_slot, 512);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-
-    auto stage_a = [&](int s) { return smem + s * STAGE_BYTES; };
-    auto stage_bh = [&](int s) { return smem + s * STAGE_BYTES + A_BYTES; };
-    auto stage_bl = [&](int s) { return smem + s * STAGE_BYTES + A_BYTES + B_BYTES; };
-    auto slot_hi = [&](int s) { return tmem + (uint32_t)(2 * COUT + s * 2 * KCH); };
-    auto slot_lo = [&](int s) { return tmem + (uint32_t)(2 * COUT + s * 2 * KCH + KCH); };
-    auto area = [&](int s, int a) { return smem + s * STAGE_BYTES + a * A_BYTES; };   // A_BYTES == B_BYTES
-    static_assert(A_BYTES == B_BYTES, "gamma boxes fill any area");
-    auto fail = [&]() {
-        *abort_flag = 1;
-        atomicOr(p.status, ST_TIMEOUT);
-    };
-    // origin of a tile: image b, output-grid row i0 and column j0 (grid
-    // modes), or first pixel p0 (MODE_FLAT)
-    auto origin = [&](int tile, int &b, int &i0, int &j0, int64_t &p0) {
-        b = i0 = j0 = 0;
-        p0 = (int64_t)tile * BLOCK_M;
-        if (p.mode != MODE_FLAT) {
-            const int tx = tile % p.tiles_x, t = tile / p.tiles_x;
-            i0 = (t % p.tiles_y) * p.R;
-            j0 = tx * p.Wt;
-            b = t / p.tiles_y;
-        }
-    };
-
-    if (warp == 0) {
-        // ---------------- TMA producer ----------------
-        if (lane == 0) {
-            const uint32_t tx_bytes = (p.mode == MODE_IM2COL ? 0 : A_BYTES) + 2 * B_BYTES;
-            uint32_t v = 0;   // ring entry
-            bool ok = true;
-            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-                int b, i0, j0;
-                int64_t p0;
-                origin(tile, b, i0, j0, p0);
-                for (int kc = 0; kc < entries; ++kc, ++v) {
-                    const int s = v % STAGES;
-                    if (*abort_flag || !mbar_wait(&empty[s], ((v / STAGES) & 1) ^ 1)) {
-                        fail();
-                        ok = false;
-                        break;
-                    }
-                    if (kc < p.kchunks) {
-                        const int t = kc / p.cpt;
-                        const int c0 = (kc % p.cpt) * KCH;
-                        mbar_expect_tx(&full[s], tx_bytes);
-                        if (p.mode == MODE_S2) {
-                            const int du = p.du[t], dv = p.dv[t];
-                            tma_load_5d(stage_a(s), &tmA, &full[s], (dv & 1) * p.Cin + c0, j0 + (dv >> 1), du & 1,
-                                        i0 + (du >> 1), b);
-                        } else if (p.mode == MODE_S1) {
-                            tma_load_4d(stage_a(s), &tmA, &full[s], c0, j0 + p.dv[t], i0 + p.du[t], b);
-                        } else if (p.mode == MODE_FLAT) {
-                            tma_load_2d(stage_a(s), &tmA, &full[s], c0, (int)p0);
-                        }
-                        tma_load_2d(stage_bh(s), &tmBh, &full[s], kc * KCH, 0);
-                        tma_load_2d(stage_bl(s), &tmBl, &full[s], kc * KCH, 0);
-                    } else {   // gamma entry e of the norm GEMM: pieces 3 e .. 3 e + 2
-                        const int e = kc - p.kchunks;
-                        const int np = min(3, 2 * GCH - 3 * e);
-                        mbar_expect_tx(&full[s], np * B_BYTES);
-                        for (int a = 0; a < np; ++a) {
-                            const int P = 3 * e + a;
-                            tma_load_2d(area(s, a), P % 2 ? &tmGl : &tmGh, &full[s], (P / 2) * KCH, 0);
-                        }
-                    }
-                }
-            }
-            if (!ok) {   // wait (bounded) for loads still in flight
-                for (uint32_t u = v > STAGES ? v - STAGES : 0; u < v; ++u) mbar_wait(&full[u % STAGES], (u / STAGES) & 1);
-            }
-        }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(BLOCK_M, COUT);
-            uint32_t v = 0, g = 0;   // ring entry, partial-buffer group
-            bool ok = true;
-            int tk = 0;              // tiles done
-            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x, ++tk) {
-                for (int kc = 0; kc < p.kchunks; ++kc, ++v) {
-                    const int s = v % STAGES;
-                    const bool first = kc % FOLD == 0;
-                    const bool last = kc % FOLD == FOLD - 1 || kc == p.kchunks - 1;
-                    const uint32_t q = g & 1;
-                    if (first && g >= 2 && (*abort_flag || !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1))) {
-                        fail();   // partial buffer q must have been read
-                        ok = false;
-                        break;
-                    }
-                    if (*abort_flag || !mbar_wait(&conv[s], (v / STAGES) & 1)) {   // A slot s written
-                        fail();
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t dt = tmem + q * COUT;
-                    const uint32_t bh = smem_u32(stage_bh(s)), bl = smem_u32(stage_bl(s));
-#pragma unroll
-                    for (int kk = 0; kk < KCH / 8; ++kk) {
-                        const uint64_t dbh = sdesc(bh + kk * 32), dbl = sdesc(bl + kk * 32);
-                        mma_tf32_ts(dt, slot_hi(s) + 8 * kk, dbh, idesc, (!first || kk > 0) ? 1u : 0u);
-                        mma_tf32_ts(dt, slot_hi(s) + 8 * kk, dbl, idesc, 1u);
-                        mma_tf32_ts(dt, slot_lo(s) + 8 * kk, dbh, idesc, 1u);
-                    }
-                    mma_commit(&empty[s]);
-                    if (last) {
-                        mma_commit(&pfull[q]);
-                        ++g;
-                    }
-                }
-                if (!ok || !gdn) continue;
-                // the norm GEMM: y^2 (A slots 0 .. GCH-1) x gamma (the NGE entries)
-                const uint32_t q = g & 1;
-                if (*abort_flag || (g >= 2 && !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1)) ||
-                    !mbar_wait(ready, tk & 1)) {
-                    fail();
-                    ok = false;
-                    continue;
-                }
-                const uint32_t dt = tmem + q * COUT;
-                int landed = 0;   // gamma entries waited for
-#pragma unroll
-                for (int c = 0; c < GCH; ++c) {
-                    const int ph = 2 * c, pl = 2 * c + 1;   // pieces of chunk c
-                    while (ok && landed <= pl / 3) {
-                        const uint32_t ve = v + landed;
-                        if (*abort_flag || !mbar_wait(&full[ve % STAGES], (ve / STAGES) & 1)) {
-                            fail();
-                            ok = false;
-                        }
-                        ++landed;
-                    }
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint32_t bh = smem_u32(area((v + ph / 3) % STAGES, ph % 3));
-                    const uint32_t bl = smem_u32(area((v + pl / 3) % STAGES, pl % 3));
-#pragma unroll
-                    for (int kk = 0; kk < KCH / 8; ++kk) {
-                        const uint64_t dbh = sdesc(bh + kk * 32), dbl = sdesc(bl + kk * 32);
-                        mma_tf32_ts(dt, slot_hi(c) + 8 * kk, dbh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-                        mma_tf32_ts(dt, slot_hi(c) + 8 * kk, dbl, idesc, 1u);
-                        mma_tf32_ts(dt, slot_lo(c) + 8 * kk, dbh, idesc, 1u);
-                    }
-                    // an entry whose last piece belongs to chunk c goes back to the producer;
-                    // conv[s] completes its phase for it here (one phase per ring entry;
-                    // the stage's previous phase is complete: its MMAs were issued above)
-#pragma unroll
-                    for (int e = 0; e < NGE; ++e) {
-                        const int lastp = 3 * e + 2 < 2 * GCH - 1 ? 3 * e + 2 : 2 * GCH - 1;
-                        if (lastp / 2 != c) continue;
-                        const uint32_t ve = v + e;
-                        mbar_arrive_n(&conv[ve % STAGES], EPI_THREADS);
-                        mma_commit(&empty[ve % STAGES]);
-                    }
-                }
-                if (!ok) continue;
-                mma_commit(&pfull[q]);
-                ++g;
-                v += NGE;
-            }
-        }
-    } else {
-        // ---------------- split, fold, epilogue (warps 2..9) ----------------
-        const int et = threadIdx.x - 64;
-        const int quarter = warp & 3, half = (warp - 2) >> 2;
-        const int m = quarter * 32 + lane;                 // this thread's TMEM lane / tile row
-        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const uint32_t lane_base = tmem + lane_off + (uint32_t)(half * HALF * 32);
-        const int cbase = half * HALF * 32;                // this thread's output channels
-        uint32_t v = 0, g = 0, eph = 0;                    // ring entry, group, epilogue-barrier phase
-        bool ok = true;
-        float master[HALF * 32];
-        // all epilogue threads (bounded, like every other wait)
-        auto esync = [&]() {
-            if (!ok) return;
-            mbar_arrive(ebar);
-            if (!mbar_wait(ebar, eph & 1)) {
-                fail();
-                ok = false;
-            }
-            ++eph;
-        };
-        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-            int b, i0, j0;
-            int64_t p0;
-            origin(tile, b, i0, j0, p0);
-#pragma unroll
-            for (int i = 0; i < HALF * 32; ++i) master[i] = 0.f;
-            const uint32_t g0 = g;
-            int folded = 0;
-            auto fold = [&](int k) {   // group g0 + k into master
-                const uint32_t gg = g0 + k;
-                if (!ok) return;
-                if (!mbar_wait(&pfull[gg & 1], (gg >> 1) & 1)) {
-                    fail();
-                    ok = false;
-                    return;
-                }
-                tc_fence_after();
-#pragma unroll
-                for (int h = 0; h < HALF; ++h) {
-                    float x[32];
-                    tmem_ld32(lane_base + (uint32_t)((gg & 1) * COUT + h * 32), x);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += x[i];
-                }
-                tc_fence_before();
-                mbar_arrive(&pempty[gg & 1]);
-            };
-            for (int kc = 0; kc < p.kchunks && ok; ++kc, ++v) {
-                const int s = v % STAGES;
-                // row m, columns [16 half, 16 half + 16) of the chunk; MODE_IM2COL gathers
-                // them from global memory first, overlapping the weights' TMA
-                float x[16], hv[16], lv[16];
-                if (p.mode == MODE_IM2COL) {
-                    const int gi = i0 + m / p.Wt, gj = j0 + m % p.Wt;
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int k = kc * KCH + 16 * half + e;
-                        const int t = k / p.Cin, c = k - t * p.Cin;
-                        float val = 0.f;
-                        if (t < p.T) {
-                            const int yi = p.s * gi + p.du[t], xi = p.s * gj + p.dv[t];
-                            if (yi >= 0 && yi < p.Hi && xi >= 0 && xi < p.Wi)
-                                val = __ldg(p.in + (((int64_t)b * p.Hi + yi) * p.Wi + xi) * p.Cin + c);
-                        }
-                        x[e] = val;
-                    }
-                }
-                if (*abort_flag || !mbar_wait(&full[s], (v / STAGES) & 1)) {
-                    fail();
-                    ok = false;
-                    break;
-                }
-                if (p.mode != MODE_IM2COL) {
-                    const uint8_t *row = stage_a(s) + m * 128;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 f = *reinterpret_cast<const float4 *>(row + (((4 * half + q) ^ (m & 7)) << 4));
-                        x[4 * q] = f.x; x[4 * q + 1] = f.y; x[4 * q + 2] = f.z; x[4 * q + 3] = f.w;
-                    }
-                }
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    float y = x[e];
-                    if (p.in_xform == IN_ABS) y = fabsf(y);
-                    else if (p.in_xform == IN_SQUARE) y = y * y;
-                    hv[e] = tf32_rna(y);
-                    lv[e] = tf32_rna(y - hv[e]);
-                }
-                tmem_st16(slot_hi(s) + lane_off + 16 * half, hv);
-                tmem_st16(slot_lo(s) + lane_off + 16 * half, lv);
-                tmem_st_wait();
-                tc_fence_before();
-                mbar_arrive(&conv[s]);
-                // mid-way through group k, the MMAs of group k-1 are done: fold it
-                if (kc % FOLD == FOLD / 2 && kc / FOLD >= 1 && folded < kc / FOLD) fold(folded++);
-            }
-            while (ok && folded < groups) fold(folded++);
-            g = g0 + groups;
-            if (ok) {
-#pragma unroll
-                for (int h = 0; h < HALF; ++h) {
-                    const int c = cbase + 32 * h;
-                    if (p.fuse_gdn == 3) norm_diag<32, false>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
-                    else if (p.fuse_gdn == 4) norm_diag<32, true>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
-                    else add_bias<32>(master + 32 * h, p.bias + c);
-                }
-                if (p.epi == EPI_RELU) {
-#pragma unroll
-                    for (int i = 0; i < HALF * 32; ++i) master[i] = fmaxf(master[i], 0.f);
-                }
-            }
-            if (gdn) {
-                // y^2 (hi / lo) of this thread's chunks HALF half + h into A slots of the
-                // same number: every slot is idle (the last group's MMAs are done)
-                if (ok) {
-#pragma unroll
-                    for (int h = 0; h < HALF; ++h) {
-                        const int slot = HALF * half + h;
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            float hv[16], lv[16];
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                const float sq = master[32 * h + 16 * q + i] * master[32 * h + 16 * q + i];
-                                hv[i] = tf32_rna(sq);
-                                lv[i] = tf32_rna(sq - hv[i]);
-                            }
-                            tmem_st16(slot_hi(slot) + lane_off + 16 * q, hv);
-                            tmem_st16(slot_lo(slot) + lane_off + 16 * q, lv);
-                        }
-                    }
-                    tmem_st_wait();
-                    tc_fence_before();
-                    mbar_arrive(ready);
-                }
-                v += NGE;
-                // the norm GEMM's result (group g): y / sqrt(beta + .) or y * sqrt(.)
-                if (ok && (*abort_flag || !mbar_wait(&pfull[g & 1], (g >> 1) & 1))) {
-                    fail();
-                    ok = false;
-                }
-                if (ok) {
-                    tc_fence_after();
-#pragma unroll
-                    for (int h = 0; h < 2 * HALF; ++h) {
-                        float n[16];
-                        tmem_ld16(lane_base + (uint32_t)((g & 1) * COUT + h * 16), n);
-                        if (p.fuse_gdn == 1) norm_n<16, false>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
-                        else norm_n<16, true>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
-                    }
-                    tc_fence_before();
-                    mbar_arrive(&pempty[g & 1]);
-                }
-                ++g;
-            }
-            // stage the tile once the previous tile's store has read the buffer
-            if (et == 0) bulk_wait_read();
-            esync();
-            if (ok) {
-#pragma unroll
-                for (int h = 0; h < HALF; ++h) {
-                    uint8_t *row = otile + (HALF * half + h) * BOX_BYTES + m * 128;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        *reinterpret_cast<float4 *>(row + ((q ^ (m & 7)) << 4)) =
-                            make_float4(master[32 * h + 4 * q], master[32 * h + 4 * q + 1],
-                                        master[32 * h + 4 * q + 2], master[32 * h + 4 * q + 3]);
-                }
-                fence_proxy_async();
-            }
-            esync();
-            if (ok && et == 0 && !*abort_flag) {
-                for (int bx = 0; bx < GCH; ++bx) {
-                    if (p.mode == MODE_FLAT) tma_store_2d(&tmO, otile + bx * BOX_BYTES, 32 * bx, (int)p0);
-                    else tma_store_5d(&tmO, otile + bx * BOX_BYTES, p.oxo * p.ostride + 32 * bx, j0, p.oyo, i0, b);
-                }
-                bulk_commit();
-            }
-        }
-        if (et == 0) bulk_wait_all();
-    }
-
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tmem, 512);
-    }
-}
-
-
-// ------------------------------------------------------------------ wide-N persistent FP32 kernel
-//
-// conv_tcw_kernel: conv_tcp_kernel with the weights' hi and lo slices stacked
-// into one N = 256 operand.  On this part a tcgen05 TF32 MMA of 128 x 128 x 8
-// takes nearly as long as one of 128 x 256 x 8 (about 63 against 73 ns,
-// measured back to back), so the three products of a K step, A_hi B_hi +
-// A_hi B_lo + A_lo B_hi, go out as two instructions: A_hi x [B_hi | B_lo]
-// (N = 256, the halves of the partial sum accumulating apart) and A_lo x B_hi
-// (N = 128, into the first half); the fold adds the halves.  The fused norm's
-// GEMM does the same with y^2 and [gamma_hi | gamma_lo].  With 256-column
-// partial sums the two ping-pong buffers take all of TMEM, so A (split hi /
-// lo in place) is read from shared memory, and y^2 is written into the
-// buffer of the tile's last (already folded) group.  The output tile leaves
-// in two halves of 64 channels through a 32 KB staging buffer.
-template <int STAGES>
-__global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tcw_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                                       const __grid_constant__ CUtensorMap tmBh,
-                                                                       const __grid_constant__ CUtensorMap tmBl,
-                                                                       const __grid_constant__ CUtensorMap tmGh,
-                                                                       const __grid_constant__ CUtensorMap tmGl,
-                                                                       const __grid_constant__ CUtensorMap tmO,
-                                                                       const __grid_constant__ Params p) {
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    constexpr int COUT = 128, HALF = 2;
-    constexpr int AREA = A_BYTES;                     // 128 rows x 128 bytes
-    constexpr int STAGE_BYTES = 4 * AREA;             // A (split in place to hi), A lo, B hi, B lo
-    constexpr int GCH = COUT / KCH;                   // gamma chunks of the norm GEMM
-    constexpr int NGE = GCH / 2;                      // gamma entries: two chunks ([hi | lo] each) per stage
-    static_assert(NGE <= STAGES, "the gamma entries fit the ring at once");
-    static_assert(COUT * KCH * 4 == AREA, "a weight slice fills one area");
-    uint8_t *otile = smem + STAGES * STAGE_BYTES;     // two output boxes of 32 channels
-    uint64_t *bars = reinterpret_cast<uint64_t *>(otile + 2 * AREA);
-    uint64_t *full = bars, *conv = bars + STAGES, *empty = bars + 2 * STAGES;
-    uint64_t *pfull = bars + 3 * STAGES, *pempty = pfull + 2, *ebar = pempty + 2, *ready = ebar + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ready + 1);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int groups = (p.kchunks + FOLD - 1) / FOLD;
-    const bool gdn = p.fuse_gdn == 1 || p.fuse_gdn == 2;
-    const int entries = p.kchunks + (gdn ? NGE : 0);   // ring entries per tile
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&conv[s], EPI_THREADS);
-            mbar_init(&empty[s], 1);
-        }
-        for (int q = 0; q < 2; ++q) {
-            mbar_init(&pfull[q], 1);
-            mbar_init(&pempty[q], EPI_THREADS);
-        }
-        mbar_init(ebar, EPI_THREADS);
-        mbar_init(ready, EPI_THREADS);
-        *abort_flag = 0;
-        fence_barrier_init();
-    }
-    if (warp == 1) tmem_alloc(tmem_slot, 512);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-
-    auto area = [&](int s, int a) { return smem + s * STAGE_BYTES + a * AREA; };
-    auto fail = [&]() {
-        *abort_flag = 1;
-        atomicOr(p.status, ST_TIMEOUT);
-    };
-    auto origin = [&](int tile, int &b, int &i0, int &j0, int64_t &p0) {
-        b = i0 = j0 = 0;
-        p0 = (int64_t)tile * BLOCK_M;
-        if (p.mode != MODE_FLAT) {
-            const int tx = tile % p.tiles_x, t = tile / p.tiles_x;
-            i0 = (t % p.tiles_y) * p.R;
-            j0 = tx * p.Wt;
-            b = t / p.tiles_y;
-        }
-    };
-
-    if (warp == 0) {
-        // ---------------- TMA producer ----------------
-        if (lane == 0) {
-            const uint32_t tx_bytes = (p.mode == MODE_IM2COL ? 0 : AREA) + 2 * AREA;
-            uint32_t v = 0;
-            bool ok = true;
-            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-                int b, i0, j0;
-                int64_t p0;
-                origin(tile, b, i0, j0, p0);
-                for (int kc = 0; kc < entries; ++kc, ++v) {
-                    const int s = v % STAGES;
-                    if (*abort_flag || !mbar_wait(&empty[s], ((v / STAGES) & 1) ^ 1)) {
-                        fail();
-                        ok = false;
-                        break;
-                    }
-                    if (kc < p.kchunks) {
-                        const int t = kc / p.cpt;
-                        const int c0 = (kc % p.cpt) * KCH;
-                        mbar_expect_tx(&full[s], tx_bytes);
-                        if (p.mode == MODE_S2) {
-                            const int du = p.du[t], dv = p.dv[t];
-                            tma_load_5d(area(s, 0), &tmA, &full[s], (dv & 1) * p.Cin + c0, j0 + (dv >> 1), du & 1,
-                                        i0 + (du >> 1), b);
-                        } else if (p.mode == MODE_S1) {
-                            tma_load_4d(area(s, 0), &tmA, &full[s], c0, j0 + p.dv[t], i0 + p.du[t], b);
-                        } else if (p.mode == MODE_FLAT) {
-                            tma_load_2d(area(s, 0), &tmA, &full[s], c0, (int)p0);
-                        }
-                        tma_load_2d(area(s, 2), &tmBh, &full[s], kc * KCH, 0);
-                        tma_load_2d(area(s, 3), &tmBl, &full[s], kc * KCH, 0);
-                    } else {   // gamma entry e: chunks 2e, 2e + 1 as [hi | lo] pairs
-                        const int e = kc - p.kchunks;
-                        mbar_expect_tx(&full[s], 4 * AREA);
-                        for (int j = 0; j < 2; ++j) {
-                            tma_load_2d(area(s, 2 * j), &tmGh, &full[s], (2 * e + j) * KCH, 0);
-                            tma_load_2d(area(s, 2 * j + 1), &tmGl, &full[s], (2 * e + j) * KCH, 0);
-                        }
-                    }
-                }
-            }
-            if (!ok) {   // wait (bounded) for loads still in flight
-                for (uint32_t u = v > STAGES ? v - STAGES : 0; u < v; ++u) mbar_wait(&full[u % STAGES], (u / STAGES) & 1);
-            }
-        }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
-            const uint32_t idw = idesc_tf32(BLOCK_M, 2 * COUT), idn = idesc_tf32(BLOCK_M, COUT);
-            uint32_t v = 0, g = 0;   // ring entry, partial-buffer group
-            bool ok = true;
-            int tk = 0;
-            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x, ++tk) {
-                for (int kc = 0; kc < p.kchunks; ++kc, ++v) {
-                    const int s = v % STAGES;
-                    const bool first = kc % FOLD == 0;
-                    const bool last = kc % FOLD == FOLD - 1 || kc == p.kchunks - 1;
-                    const uint32_t q = g & 1;
-                    if (first && g >= 2 && (*abort_flag || !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1))) {
-                        fail();
-                        ok = false;
-                        break;
-                    }
-                    if (*abort_flag || !mbar_wait(&conv[s], (v / STAGES) & 1)) {   // A split into hi / lo
-                        fail();
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t dt = tmem + q * 2 * COUT;
-                    const uint32_t ah = smem_u32(area(s, 0)), al = smem_u32(area(s, 1)), bh = smem_u32(area(s, 2));
-#pragma unroll
-                    for (int kk = 0; kk < KCH / 8; ++kk) {
-                        const uint64_t db = sdesc(bh + kk * 32);
-                        mma_tf32(dt, sdesc(ah + kk * 32), db, idw, (!first || kk > 0) ? 1u : 0u);   // [hi | lo]
-                        mma_tf32(dt, sdesc(al + kk * 32), db, idn, 1u);                             // A lo x B hi
-                    }
-                    mma_commit(&empty[s]);
-                    if (last) {
-                        mma_commit(&pfull[q]);
-                        ++g;
-                    }
-                }
-                if (!ok || !gdn) continue;
-                // the norm GEMM into buffer g & 1; y^2 sits in the other (the tile's last group's)
-                const uint32_t q = g & 1;
-                if (*abort_flag || (g >= 2 && !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1)) ||
-                    !mbar_wait(ready, tk & 1)) {
-                    fail();
-                    ok = false;
-                    continue;
-                }
-                const uint32_t dt = tmem + q * 2 * COUT, ysl = tmem + (q ^ 1) * 2 * COUT;
-#pragma unroll
-                for (int c = 0; c < GCH; ++c) {
-                    const uint32_t ve = v + c / 2;
-                    const int s = ve % STAGES;
-                    if (c % 2 == 0) {
-                        if (*abort_flag || !mbar_wait(&full[s], (ve / STAGES) & 1)) {
-                            fail();
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                    }
-                    const uint32_t bh = smem_u32(area(s, 2 * (c % 2)));
-#pragma unroll
-                    for (int kk = 0; kk < KCH / 8; ++kk) {
-                        const uint64_t db = sdesc(bh + kk * 32);
-                        mma_tf32_ts(dt, ysl + KCH * c + 8 * kk, db, idw, (c > 0 || kk > 0) ? 1u : 0u);
-                        mma_tf32_ts(dt, ysl + COUT + KCH * c + 8 * kk, db, idn, 1u);
-                    }
-                    if (c % 2 == 1) {   // the entry's two chunks are issued: back to the producer
-                        mbar_arrive_n(&conv[s], EPI_THREADS);   // one conv phase per ring entry
-                        mma_commit(&empty[s]);
-                    }
-                }
-                if (!ok) continue;
-                mma_commit(&pfull[q]);
-                ++g;
-                v += NGE;
-            }
-        }
-    } else {
-        // ---------------- split, fold, epilogue (warps 2..9) ----------------
-        const int et = threadIdx.x - 64;
-        const int quarter = warp & 3, half = (warp - 2) >> 2;
-        const int m = quarter * 32 + lane;                 // this thread's TMEM lane / tile row
-        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const int cbase = half * HALF * 32;                // this thread's output channels
-        uint32_t v = 0, g = 0, eph = 0;
-        bool ok = true;
-        float master[HALF * 32];
-        auto esync = [&]() {
-            if (!ok) return;
-            mbar_arrive(ebar);
-            if (!mbar_wait(ebar, eph & 1)) {
-                fail();
-                ok = false;
-            }
-            ++eph;
-        };
-        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-            int b, i0, j0;
-            int64_t p0;
-            origin(tile, b, i0, j0, p0);
-#pragma unroll
-            for (int i = 0; i < HALF * 32; ++i) master[i] = 0.f;
-            const uint32_t g0 = g;
-            int folded = 0;
-            // group g0 + k into master (its two halves); the tile's last group keeps
-            // its buffer when the norm GEMM follows (y^2 goes there)
-            auto fold = [&](int k) {
-                const uint32_t gg = g0 + k;
-                if (!ok) return;
-                if (!mbar_wait(&pfull[gg & 1], (gg >> 1) & 1)) {
-                    fail();
-                    ok = false;
-                    return;
-                }
-                tc_fence_after();
-                const uint32_t base = tmem + lane_off + (gg & 1) * 2 * COUT + cbase;
-#pragma unroll
-                for (int h = 0; h < HALF; ++h) {
-                    float x[32];
-                    tmem_ld32(base + 32 * h, x);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += x[i];
-                    tmem_ld32(base + COUT + 32 * h, x);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += x[i];
-                }
-                tc_fence_before();
-                if (!(gdn && k == groups - 1)) mbar_arrive(&pempty[gg & 1]);
-            };
-            for (int kc = 0; kc < p.kchunks && ok; ++kc, ++v) {
-                const int s = v % STAGES;
-                float x[16];
-                const int mi = et >> 1, kh = et & 1;   // MODE_IM2COL: row mi, K entries [16 kh, 16 kh + 16)
-                if (p.mode == MODE_IM2COL) {
-                    const int gi = i0 + mi / p.Wt, gj = j0 + mi % p.Wt;
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int k = kc * KCH + 16 * kh + e;
-                        const int t = k / p.Cin, c = k - t * p.Cin;
-                        float val = 0.f;
-                        if (t < p.T) {
-                            const int yi = p.s * gi + p.du[t], xi = p.s * gj + p.dv[t];
-                            if (yi >= 0 && yi < p.Hi && xi >= 0 && xi < p.Wi)
-                                val = __ldg(p.in + (((int64_t)b * p.Hi + yi) * p.Wi + xi) * p.Cin + c);
-                        }
-                        x[e] = val;
-                    }
-                }
-                if (*abort_flag || !mbar_wait(&full[s], (v / STAGES) & 1)) {
-                    fail();
-                    ok = false;
-                    break;
-                }
-                uint8_t *ah = area(s, 0), *al = area(s, 1);
-                if (p.mode == MODE_IM2COL) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float4 hv, lv;
-                        hv.x = tf32_rna(x[4 * q + 0]); lv.x = tf32_rna(x[4 * q + 0] - hv.x);
-                        hv.y = tf32_rna(x[4 * q + 1]); lv.y = tf32_rna(x[4 * q + 1] - hv.y);
-                        hv.z = tf32_rna(x[4 * q + 2]); lv.z = tf32_rna(x[4 * q + 2] - hv.z);
-                        hv.w = tf32_rna(x[4 * q + 3]); lv.w = tf32_rna(x[4 * q + 3] - hv.w);
-                        const int off = mi * 128 + (((4 * kh + q) ^ (mi & 7)) << 4);
-                        *reinterpret_cast<float4 *>(ah + off) = hv;
-                        *reinterpret_cast<float4 *>(al + off) = lv;
-                    }
-                } else {
-                    // elementwise, in place: the swizzled layout is kept
-#pragma unroll
-                    for (int q = 0; q < AREA / 16 / EPI_THREADS; ++q) {
-                        const int idx = et + q * EPI_THREADS;
-                        float4 f = reinterpret_cast<float4 *>(ah)[idx];
-                        if (p.in_xform == IN_ABS) {
-                            f.x = fabsf(f.x); f.y = fabsf(f.y); f.z = fabsf(f.z); f.w = fabsf(f.w);
-                        } else if (p.in_xform == IN_SQUARE) {
-                            f.x *= f.x; f.y *= f.y; f.z *= f.z; f.w *= f.w;
-                        }
-                        float4 hv, lv;
-                        hv.x = tf32_rna(f.x); lv.x = tf32_rna(f.x - hv.x);
-                        hv.y = tf32_rna(f.y); lv.y = tf32_rna(f.y - hv.y);
-                        hv.z = tf32_rna(f.z); lv.z = tf32_rna(f.z - hv.z);
-                        hv.w = tf32_rna(f.w); lv.w = tf32_rna(f.w - hv.w);
-                        reinterpret_cast<float4 *>(ah)[idx] = hv;
-                        reinterpret_cast<float4 *>(al)[idx] = lv;
-                    }
-                }
-                fence_proxy_async();
-                mbar_arrive(&conv[s]);
-                if (kc % FOLD == FOLD / 2 && kc / FOLD >= 1 && folded < kc / FOLD) fold(folded++);
-            }
-            while (ok && folded < groups) fold(folded++);
-            g = g0 + groups;
-            if (ok) {
-#pragma unroll
-                for (int h = 0; h < HALF; ++h) {
-                    const int c = cbase + 32 * h;
-                    if (p.fuse_gdn == 3) norm_diag<32, false>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
-                    else if (p.fuse_gdn == 4) norm_diag<32, true>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
-                    else add_bias<32>(master + 32 * h, p.bias + c);
-                }
-                if (p.epi == EPI_RELU) {
-#pragma unroll
-                    for (int i = 0; i < HALF * 32; ++i) master[i] = fmaxf(master[i], 0.f);
-                }
-            }
-            if (gdn) {
-                // y^2 of this thread's chunks c = HALF half + h into the buffer of group
-                // g - 1 (folded above, its MMAs complete): hi at column 32 c, lo at
-                // COUT + 32 c -- exactly the columns this thread has read, so no other
-                // thread's fold can still need them
-                const uint32_t ysl = tmem + lane_off + ((g - 1) & 1) * 2 * COUT;
-                if (ok) {
-#pragma unroll
-                    for (int h = 0; h < HALF; ++h) {
-                        const uint32_t slot = ysl + KCH * (HALF * half + h);
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            float hv[16], lv[16];
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                const float sq = master[32 * h + 16 * q + i] * master[32 * h + 16 * q + i];
-                                hv[i] = tf32_rna(sq);
-                                lv[i] = tf32_rna(sq - hv[i]);
-                            }
-                            tmem_st16(slot + 16 * q, hv);
-                            tmem_st16(slot + COUT + 16 * q, lv);
-                        }
-                    }
-                    tmem_st_wait();
-                    tc_fence_before();
-                    mbar_arrive(ready);
-                }
-                v += NGE;
-                if (ok && (*abort_flag || !mbar_wait(&pfull[g & 1], (g >> 1) & 1))) {
-                    fail();
-                    ok = false;
-                }
-                if (ok) {
-                    tc_fence_after();
-                    const uint32_t base = tmem + lane_off + (g & 1) * 2 * COUT + cbase;
-#pragma unroll
-                    for (int h = 0; h < 2 * HALF; ++h) {
-                        float n[16], nl[16];
-                        tmem_ld16(base + 16 * h, n);
-                        tmem_ld16(base + COUT + 16 * h, nl);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) n[i] += nl[i];
-                        if (p.fuse_gdn == 1) norm_n<16, false>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
-                        else norm_n<16, true>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
-                    }
-                    tc_fence_before();
-                    mbar_arrive(&pempty[g & 1]);         // the norm GEMM's group
-                    mbar_arrive(&pempty[(g - 1) & 1]);   // the last conv group's buffer, now free of y^2
-                }
-                ++g;
-            }
-            // the output in two halves of 64 channels (threads of half 0, then 1)
-#pragma unroll
-            for (int ph = 0; ph < 2; ++ph) {
-                if (et == 0) bulk_wait_read();   // the previous store has read the staging boxes
-                esync();
-                if (ok && half == ph) {
-#pragma unroll
-                    for (int h = 0; h < HALF; ++h) {
-                        uint8_t *row = otile + h * AREA + m * 128;
-#pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            *reinterpret_cast<float4 *>(row + ((q ^ (m & 7)) << 4)) =
-                                make_float4(master[32 * h + 4 * q], master[32 * h + 4 * q + 1],
-                                            master[32 * h + 4 * q + 2], master[32 * h + 4 * q + 3]);
-                    }
-                    fence_proxy_async();
-                }
-                esync();
-                if (ok && et == 0 && !*abort_flag) {
-                    for (int bx = 0; bx < HALF; ++bx) {
-                        const int co = HALF * 32 * ph + 32 * bx;
-                        if (p.mode == MODE_FLAT) tma_store_2d(&tmO, otile + bx * AREA, co, (int)p0);
-                        else tma_store_5d(&tmO, otile + bx * AREA, p.oxo * p.ostride + co, j0, p.oyo, i0, b);
-                    }
-                    bulk_commit();
-                }
-            }
-        }
-        if (et == 0) bulk_wait_all();
-    }
-
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tmem, 512);
-    }
-}
-
-// ------------------------------------------------------------------ warp-specialised wide-N FP32 kernel
-//
-// conv_tcx_kernel: conv_tcw_kernel's arithmetic, ring and TMEM use with the
-// work spread over 16 warps so that a tile's epilogue runs under the next
-// tile's main loop.  Timestamps in conv_tcw_kernel put its per-tile epilogue
-// (last fold, y^2, norm GEMM, normalisation, output) at about 7.4 us, against
-// 0.7 us per K chunk, with the tensor pipe idle throughout.  Here six warps
-// only split A, and eight epilogue warps fold each partial sum as it
-// completes and finish the tile while the next one streams through the
-// ring: the tensor pipe waits only for a tile's last fold and its y^2.
-// Registers move from the producer / MMA / split warpgroups (72 a thread) to
-// the epilogue warpgroups (184) with setmaxnreg; the shares add up to the
-// 64 K registers the block is launched with.
+// conv_tcx_kernel: the Cout = 128 FP32 convolutions (fused GDN / IGDN, 1DN,
+// bias, ReLU) as a persistent, warp-specialised kernel: one CTA per SM over
+// tiles blockIdx.x + k gridDim.x, the same arithmetic as conv_tc_kernel
+// (3xTF32, FOLD-chunk partial sums folded into float32 registers), organised
+// around four measurements on this part (timestamps and micro-benchmarks):
+//   * a one-tile-per-CTA schedule paid ~2 us of start-up, ~1 us between CTAs
+//     and ~2.4 us of output stores per 128-pixel tile, and its epilogue
+//     (last fold, y^2, norm GEMM, normalisation, output: ~7.4 us) left the
+//     tensor pipe idle;
+//   * a TF32 MMA of 128 x 128 x 8 takes ~63 ns and one of 128 x 256 x 8 ~73
+//     ns: the instruction, not the multiply-adds, sets the pace at N = 128;
+//   * the MMA takes an FP32 operand as TF32 by clearing its low 13 mantissa
+//     bits;
+//   * with A split by eight epilogue warps between their other work, the
+//     split paced the main loop.
+// Hence:
+//   * one 3-stage load ring runs across tiles; a stage holds A (raw, serving
+//     as A_hi), A_lo, B_hi, B_lo (16 KB each, 128-byte swizzled);
+//   * per 8-wide K step two MMAs: A_hi x [B_hi | B_lo] (N = 256: one
+//     descriptor spans the adjacent B areas; the two halves of the partial
+//     sum accumulate apart and the fold adds them) and A_lo x B_hi (N = 128,
+//     into the first half); with 256-column partials the two ping-pong
+//     buffers fill TMEM, so A is read from shared memory;
+//   * the split only writes A_lo = x - trunc(x), exact in FP32 (the MMA's
+//     own truncation of it costs at most 2^-20 of a product);
+//   * the fused norm's gamma rides the ring as two entries of two
+//     [gamma_hi | gamma_lo] chunks; y^2 goes into the columns of the tile's
+//     last (already folded) partial, each thread writing exactly the columns
+//     it read; the norm result is one more ping-pong group;
+//   * six warps only split, eight epilogue warps fold each partial as it
+//     completes and finish a tile while the next one streams through the
+//     ring, so the tensor pipe waits only for a tile's last fold and y^2;
+//     the output leaves through a 32 KB staging buffer as two TMA stores of
+//     64 channels;
+//   * registers move from the producer / MMA / split warpgroups (72 a
+//     thread) to the epilogue warpgroups (184) with setmaxnreg; the shares
+//     add up to the 64 K registers the block is launched with.
 //   warp 0       TMA producer            warp 1      TMEM allocation, MMA issue
-//   warps 2..7   split A (hi / lo, in place in shared memory)
-//   warps 8..15  fold, bias / norm, output (TMEM lanes 32 (warp % 4) ..)
+//   warps 2..7   split A                 warps 8..15 fold, bias / norm, output
+//                                                    (TMEM lanes 32 (warp % 4) ..)
 constexpr int TCX_THREADS = 512, TCX_SPLIT = 192, TCX_EPI = 256;
 
 template <int STAGES>
@@ -2601,7 +1776,7 @@ int sm_count() {
     return n;
 }
 
-// The output of a conv_tcp_kernel launch as a tensor map for its 32-channel
+// The output of a conv_tcx_kernel launch as a tensor map for its 32-channel
 // boxes.  Grid modes: output pixel (b, oym * gi + oyo, oxm * gj + oxo),
 // channel c, of a row stride of ostride elements from channel ocoff, viewed
 // as (oxm * ostride - ocoff, Gw, oym, Gh, B) -- the x phase merged into the
@@ -2869,33 +2044,17 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
                                    ? reinterpret_cast<const CUtensorMap *>(static_cast<const TcWeights *>(d.gdn_w)->maps)
                                    : maps;
     CUtensorMap tmO;
-    if (d.Cout == 128 && p.out_dt == DT_F32 && (d.epi == EPI_NONE || d.epi == EPI_RELU) &&
+    if (d.Cout == 128 && p.out_dt == DT_F32 && (d.epi == EPI_NONE || d.epi == EPI_RELU) && p.mode != MODE_IM2COL &&
         make_out_map(&tmO, d, p)) {
-        // persistent, one CTA per SM.  Long reductions take the wide-N kernel (fewer,
-        // wider MMAs; A from shared memory); short ones, where the per-tile epilogue
-        // dominates, the TMEM-A kernel with the whole output tile staged at once.
+        // persistent, one CTA per SM (conv_tcx_kernel)
         constexpr int STAGES = 3;
         p.ntiles = (int)grid;
         const unsigned pgrid = std::min<unsigned>(grid, (unsigned)sm_count());
-        if (p.kchunks >= 8 && p.mode != MODE_IM2COL) {
-            const int smem = STAGES * 4 * A_BYTES + 2 * A_BYTES + 256 + 1024;
-            cudaFuncSetAttribute(conv_tcx_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            conv_tcx_kernel<STAGES><<<pgrid, TCX_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1], tmO,
-                                                                      p);
-        } else if (p.kchunks >= 8) {
-            const int smem = STAGES * 4 * A_BYTES + 2 * A_BYTES + 256 + 1024;
-            cudaFuncSetAttribute(conv_tcw_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            conv_tcw_kernel<STAGES><<<pgrid, 64 + EPI_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1],
-                                                                          tmO, p);
-        } else {
-            const int smem = STAGES * (A_BYTES + 2 * 128 * KCH * 4) + BLOCK_M * 128 * 4 + 256 + 1024;
-            cudaFuncSetAttribute(conv_tcp_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            conv_tcp_kernel<STAGES><<<pgrid, 64 + EPI_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1],
-                                                                          tmO, p);
-        }
+        const int smem = STAGES * 4 * A_BYTES + 2 * A_BYTES + 256 + 1024;
+        cudaFuncSetAttribute(conv_tcx_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        conv_tcx_kernel<STAGES><<<pgrid, TCX_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1], tmO, p);
         return true;
-    }
-    const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
+    }    const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
     if (d.Cout == 128)
         launch_kernel<4, 2>(grid, smem, st, tmA, maps[0], maps[1], gmaps[0], gmaps[1], p);
     else
