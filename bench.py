@@ -365,9 +365,9 @@ def main():
                 codec.decode(bs2, H, W, hout, stream=sid)
             codec.sync(sid)
             serial_fps = ws * B * args.steps / (time.perf_counter() - t0)
-        # pipelined through the serving API: three lanes (codec + stream), a batch's host copies overlap
-        # the other lanes' kernels; at most three batches in flight, each frame's output its own pinned buffer
-        depth = 3
+        # pipelined through the serving API: four lanes (codec + stream), a batch's host copies overlap
+        # the other lanes' kernels; at most four batches in flight, each frame's output its own pinned buffer
+        depth = 4
         srv = lic.Server(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=lic.FP32, max_batch=B, lanes=depth,
                          max_pending=(depth + 1) * B, graphs=True, max_wait_ms=1e6)
         srv.prepare(H, W)
@@ -392,7 +392,7 @@ def main():
         e2e = {"value": ws * B * args.steps / dt, "unit": "frames/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "serial_value": serial_fps, "graph_replays": est["graph_replays"],
                "note": "pinned host frames in, decoded frames out to pinned host memory, through the serving "
-                       "API (FP32 codec, 3 lanes, batches of 8, at most 3 in flight); serial_value: one codec "
+                       "API (FP32 codec, 4 lanes, batches of 8, at most 4 in flight); serial_value: one codec "
                        "on one stream, copies not overlapped"}
 
     # ---- reconstruction vs the FP64 oracle on sampled windows ----

@@ -46,6 +46,11 @@ struct Layer {
     int in_xform = IN_NONE, epi = EPI_NONE;
     DevBuf bias;
     DevBuf w_small;  // transposed conv to <= 4 channels: [Cin][5][5][4]
+    // ... and as a 1x1 GEMM from Cin channels to 128 columns: the 25 * Cout tap
+    // contributions of an input position (column (u * 5 + v) * Cout + o, zero
+    // beyond), summed per output pixel by launch_deconv_gather
+    tc::TcWeights w_scatter;
+    DevBuf zero_bias;
     int in_dt = DT_F32, out_dt = DT_F32;   // activation storage of this layer (precision forms)
     float in_scale = 1.f, out_scale = 1.f;   // e4m3 tensors hold x / scale
     std::vector<std::unique_ptr<ConvOp>> ops;
@@ -228,6 +233,20 @@ int make_deconv(Layer &L, const ParamMap &pm, const std::string &name, int Cin, 
                     for (int v = 0; v < k; ++v)
                         r[(((size_t)c * 25) + u * 5 + v) * 4 + o] = w[(((size_t)c * Cout + o) * k + u) * k + v];
         if ((rc = upload(L.w_small, r.data(), r.size() * sizeof(float)))) return rc;
+        // the two-pass form needs 128 floats of scratch a position, which the
+        // codec's activation buffers hold when Cin >= 128; the choice depends on
+        // the model only, so every batch size decodes through the same arithmetic
+        if (Cin >= 128) {
+            std::vector<float> ws((size_t)128 * Cin, 0.f), zb(128, 0.f);
+            for (int c = 0; c < Cin; ++c)
+                for (int o = 0; o < Cout; ++o)
+                    for (int u = 0; u < k; ++u)
+                        for (int v = 0; v < k; ++v)
+                            ws[((size_t)(u * 5 + v) * Cout + o) * Cin + c] =
+                                w[(((size_t)c * Cout + o) * k + u) * k + v];
+            tc::build_weights(ws.data(), 128, 1, Cin, &L.w_scatter);
+            if ((rc = upload(L.zero_bias, zb.data(), zb.size() * sizeof(float)))) return rc;
+        }
     }
     for (int py = 0; py < 2; ++py)
         for (int px = 0; px < 2; ++px) {
@@ -448,7 +467,7 @@ void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi
 }
 
 void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out,
-               cudaStream_t st, int out_dt = -1) {
+               cudaStream_t st, int out_dt = -1, const DevBuf *scratch = nullptr) {
     int Ho, Wo;
     if (L.deconv) {
         Ho = 2 * Hi;
@@ -461,6 +480,46 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
     if (L.deconv && L.w_small.p) {
         const double flop = 2.0 * B * Ho * Wo * L.Cout * L.Cin * 6.25;
         const double bytes = 4.0 * ((double)B * Hi * Wi * L.Cin + (double)B * Ho * Wo * L.Cout + 100.0 * L.Cin);
+        // two passes (the layer's tensor-core weights exist when Cin >= 128): the tap
+        // contributions of every input position by a tensor-core 1x1 GEMM into the
+        // scratch buffer (128 floats a position; an activation buffer of Cin >= 128
+        // channels), then their per-pixel sums
+        const size_t need = (size_t)B * Hi * Wi * 128 * sizeof(float);
+        if (scratch && L.w_scatter.valid && cd->opt.conv_impl != LIC_CONV_SIMT && L.in_dt == DT_F32) {
+            if (!scratch->p || scratch->bytes < need) {   // not reached: the buffers hold Cin >= 128 channels
+                atomic_status(cd, ST_TIMEOUT);
+                return;
+            }
+            float *cbuf = scratch->as<float>();
+            ConvDesc d{};
+            d.in = in;
+            d.out = cbuf;
+            d.bias = L.zero_bias.as<float>();
+            d.status = cd->status.as<uint32_t>();
+            d.B = B;
+            d.Hi = d.Gh = d.Ho = Hi;
+            d.Wi = d.Gw = d.Wo = Wi;
+            d.Cin = L.Cin;
+            d.Cout = 128;
+            d.T = 1;
+            d.s = 1;
+            d.oym = d.oxm = 1;
+            d.in_xform = IN_NONE;
+            d.epi = EPI_NONE;
+            d.in_dt = d.out_dt = DT_F32;
+            d.in_scale = d.out_scale = 1.f;
+            d.out_stream = 1;
+            if (tc::can_run(d, L.w_scatter)) {
+                const double rows = (double)B * Hi * Wi;
+                timed(const_cast<lic_codec *>(cd), L.name + ":tc", flop, 4.0 * rows * (L.Cin + 128), 1, st, [&] {
+                    if (!tc::launch(d, L.w_scatter, st)) atomic_status(cd, ST_TIMEOUT);
+                });
+                timed(const_cast<lic_codec *>(cd), L.name + ".gather", 0.0,
+                      4.0 * (rows * 25 * L.Cout + (double)B * Ho * Wo * L.Cout), 1, st,
+                      [&] { launch_deconv_gather(cbuf, B, Hi, Wi, L.Cout, L.bias.as<float>(), out, st); });
+                return;
+            }
+        }
         timed(const_cast<lic_codec *>(cd), L.name + ":small", flop, bytes, 1, st, [&] {
             launch_deconv_small(in, B, Hi, Wi, L.Cin, L.w_small.as<float>(), L.bias.as<float>(), L.Cout, out, st);
         });
@@ -667,7 +726,9 @@ void teacher_synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, 
         H *= 2;
         W *= 2;
     }
-    run_layer(cd, cd->gs[3], in, B, H, W, cd->xpre.as<float>(), st);
+    // the contributions of g_s's last layer go to the activation buffer its input is not in
+    // (when it is large enough: 128 floats a position)
+    run_layer(cd, cd->gs[3], in, B, H, W, cd->xpre.as<float>(), st, -1, in == a ? &cd->act1 : &cd->act0);
 }
 
 // g_s, or the student in its place when one is set

@@ -259,7 +259,54 @@ __global__ void __launch_bounds__(DS_THREADS) deconv_small_kernel(const float *_
         }
 }
 
+
+// Second pass of the two-pass form (see launch_deconv_gather): one thread per
+// output pixel (2m + py, 2n + px) adds, for du, dv in {-1, 0, 1} with taps
+// u = py + 2 - 2 du and v = px + 2 - 2 dv in [0, 4], the contribution of
+// input position (m + du, n + dv) through (u, v).
+constexpr int DG_STRIDE = 128;   // C row: 25 * Cout contributions, padded
+template <int COUT>
+__global__ void __launch_bounds__(256) deconv_gather_kernel(const float *__restrict__ C, int B, int Hi, int Wi,
+                                                            const float *__restrict__ bias, float *__restrict__ out) {
+    const int Ho = 2 * Hi, Wo = 2 * Wi;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)B * Ho * Wo) return;
+    const int X = (int)(idx % Wo), Y = (int)((idx / Wo) % Ho);
+    const int b = (int)(idx / ((int64_t)Wo * Ho));
+    const int m = Y >> 1, py = Y & 1, n = X >> 1, px = X & 1;
+    float acc[COUT];
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) acc[o] = __ldg(bias + o);
+#pragma unroll
+    for (int du = -1; du <= 1; ++du) {
+        const int u = py + 2 - 2 * du, mi = m + du;
+        if (u < 0 || u > 4 || mi < 0 || mi >= Hi) continue;
+#pragma unroll
+        for (int dv = -1; dv <= 1; ++dv) {
+            const int v = px + 2 - 2 * dv, ni = n + dv;
+            if (v < 0 || v > 4 || ni < 0 || ni >= Wi) continue;
+            const float *c = C + (((int64_t)b * Hi + mi) * Wi + ni) * DG_STRIDE + (u * 5 + v) * COUT;
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) acc[o] += __ldcs(c + o);   // read once: streaming
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) out[idx * COUT + o] = acc[o];
+}
 }  // namespace
+
+void launch_deconv_gather(const float *C, int B, int Hi, int Wi, int Cout, const float *bias, float *out,
+                          cudaStream_t st) {
+    const int64_t n = (int64_t)B * 4 * Hi * Wi;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (n == 0) return;
+    switch (Cout) {
+        case 1: deconv_gather_kernel<1><<<grid, 256, 0, st>>>(C, B, Hi, Wi, bias, out); break;
+        case 2: deconv_gather_kernel<2><<<grid, 256, 0, st>>>(C, B, Hi, Wi, bias, out); break;
+        case 3: deconv_gather_kernel<3><<<grid, 256, 0, st>>>(C, B, Hi, Wi, bias, out); break;
+        default: deconv_gather_kernel<4><<<grid, 256, 0, st>>>(C, B, Hi, Wi, bias, out); break;
+    }
+}
 
 void launch_deconv_small(const float *in, int B, int Hi, int Wi, int Cin, const float *w, const float *bias, int Cout,
                          float *out, cudaStream_t st) {

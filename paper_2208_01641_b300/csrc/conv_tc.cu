@@ -89,6 +89,7 @@ struct Params {
     int kchunks;
     uint32_t tmem_cols;
     int ntiles;                   // conv_tcx_kernel: tiles of the launch
+    int out_stream;               // conv_tcx_kernel: output read once soon after; evict it from L2 first
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
 };
 
@@ -187,6 +188,21 @@ __device__ __forceinline__ void tma_store_5d(const CUtensorMap *tm, const void *
             reinterpret_cast<uint64_t>(tm)),
         "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
         : "memory");
+}
+
+// The same with an L2 cache policy (createpolicy: evict-first for output that
+// is read once, so it does not displace weights and activations other
+// launches reuse)
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void tma_store_2d_hint(const CUtensorMap *tm, const void *src, int c0, int c1, uint64_t pol) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%2, %3}], [%1], %4;" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(smem_u32(src)), "r"(c0), "r"(c1), "l"(pol)
+                 : "memory");
 }
 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -1341,7 +1357,9 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                 if (ok && et == 0 && !*abort_flag) {
                     for (int bx = 0; bx < HALF; ++bx) {
                         const int co = HALF * 32 * ph + 32 * bx;
-                        if (p.mode == MODE_FLAT) tma_store_2d(&tmO, otile + bx * AREA, co, (int)p0);
+                        if (p.mode == MODE_FLAT && p.out_stream)
+                            tma_store_2d_hint(&tmO, otile + bx * AREA, co, (int)p0, policy_evict_first());
+                        else if (p.mode == MODE_FLAT) tma_store_2d(&tmO, otile + bx * AREA, co, (int)p0);
                         else tma_store_5d(&tmO, otile + bx * AREA, p.oxo * p.ostride + co, j0, p.oyo, i0, b);
                     }
                     bulk_commit();
@@ -1990,6 +2008,7 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.gdn_gamma = d.gdn_gamma;
     p.out_dt = d.out_dt;
     p.ostride = d.out_stride > 0 ? d.out_stride : d.Cout;
+    p.out_stream = d.out_stream;
     p.ocoff = d.out_coff;
     p.out_inv_scale = d.out_scale > 0.f ? 1.f / d.out_scale : 1.f;
     p.tmem_cols = 512;  // partial sums (+ A slots when Cout = 128)

@@ -256,6 +256,8 @@ struct ConvDesc {
     // output row stride in elements (0: Cout) and first output channel, for
     // a launch that computes a column slice of a wider layer (tensor cores)
     int out_stride, out_coff;
+    // the output is read once, soon (tensor-core kernels store it evict-first in L2)
+    int out_stream;
     int T;
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
     int in_xform, epi;
@@ -269,6 +271,14 @@ void launch_conv_simt(const ConvDesc &d, cudaStream_t st);
 // (output channel padded to 4); out: NHWC [B][2Hi][2Wi][Cout].
 void launch_deconv_small(const float *in, int B, int Hi, int Wi, int Cin, const float *w, const float *bias,
                          int Cout, float *out, cudaStream_t st);
+
+// The same transposed conv in two passes, the first on the tensor cores: C
+// ([B][Hi][Wi][128], from a 1x1 GEMM) holds every input position's 25 * Cout
+// tap contributions (column (u * 5 + v) * Cout + o); this sums them into
+// out (NHWC [B][2Hi][2Wi][Cout]) and adds the bias.  Each C entry lands in
+// exactly one output pixel; the sum order per pixel is fixed.
+void launch_deconv_gather(const float *C, int B, int Hi, int Wi, int Cout, const float *bias, float *out,
+                          cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // elementwise / layout kernels (layout.cu)
