@@ -1301,12 +1301,13 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                     const uint32_t slot = ysl + KCH * (HALF * half + h);
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
+                        // hi is y^2 itself (the MMA takes it as trunc(y^2)), lo the exact rest
                         float hv[16], lv[16];
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const float sq = master[32 * h + 16 * q + i] * master[32 * h + 16 * q + i];
-                            hv[i] = tf32_rna(sq);
-                            lv[i] = tf32_rna(sq - hv[i]);
+                            hv[i] = sq;
+                            lv[i] = sq - tf32_trunc(sq);
                         }
                         tmem_st16(slot + 16 * q, hv);
                         tmem_st16(slot + COUT + 16 * q, lv);
