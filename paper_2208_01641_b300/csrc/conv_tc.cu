@@ -1337,30 +1337,71 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                 mbar_arrive(&pempty[g & 1]);
                 ++g;
             }
-            // the output in two halves of 64 channels (threads of half 0, then 1)
+            if (p.out_dt == DT_F32) {
+                // the output in two halves of 64 channels (threads of half 0, then 1)
 #pragma unroll
-            for (int ph = 0; ph < 2; ++ph) {
-                if (et == 0) bulk_wait_read();   // the previous store has read the staging boxes
+                for (int ph = 0; ph < 2; ++ph) {
+                    if (et == 0) bulk_wait_read();   // the previous store has read the staging boxes
+                    esync();
+                    if (ok && half == ph) {
+#pragma unroll
+                        for (int h = 0; h < HALF; ++h) {
+                            uint8_t *row = otile + h * AREA + m * 128;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                *reinterpret_cast<float4 *>(row + ((q ^ (m & 7)) << 4)) =
+                                    make_float4(master[32 * h + 4 * q], master[32 * h + 4 * q + 1],
+                                                master[32 * h + 4 * q + 2], master[32 * h + 4 * q + 3]);
+                        }
+                        fence_proxy_async();
+                    }
+                    esync();
+                    if (ok && et == 0 && !*abort_flag) {
+                        for (int bx = 0; bx < HALF; ++bx) {
+                            const int co = HALF * 32 * ph + 32 * bx;
+                            if (p.mode == MODE_FLAT && p.out_stream)
+                                tma_store_2d_hint(&tmO, otile + bx * AREA, co, (int)p0, policy_evict_first());
+                            else if (p.mode == MODE_FLAT) tma_store_2d(&tmO, otile + bx * AREA, co, (int)p0);
+                            else tma_store_5d(&tmO, otile + bx * AREA, p.oxo * p.ostride + co, j0, p.oyo, i0, b);
+                        }
+                        bulk_commit();
+                    }
+                }
+            } else {
+                // bf16: one 128-byte box row of 64 channels per half; e4m3: one box row
+                // of all 128 channels (the halves write its two 64-byte parts)
+                const bool e4 = p.out_dt == DT_E4M3;
+                if (et == 0) bulk_wait_read();
                 esync();
-                if (ok && half == ph) {
-#pragma unroll
-                    for (int h = 0; h < HALF; ++h) {
-                        uint8_t *row = otile + h * AREA + m * 128;
+                if (ok) {
+                    uint8_t *row = otile + (e4 ? 0 : half) * AREA + m * 128;
+                    if (!e4) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q)
-                            *reinterpret_cast<float4 *>(row + ((q ^ (m & 7)) << 4)) =
-                                make_float4(master[32 * h + 4 * q], master[32 * h + 4 * q + 1],
-                                            master[32 * h + 4 * q + 2], master[32 * h + 4 * q + 3]);
+                            *reinterpret_cast<uint4 *>(row + ((q ^ (m & 7)) << 4)) = make_uint4(
+                                pack_bf16_f(master[8 * q], master[8 * q + 1]),
+                                pack_bf16_f(master[8 * q + 2], master[8 * q + 3]),
+                                pack_bf16_f(master[8 * q + 4], master[8 * q + 5]),
+                                pack_bf16_f(master[8 * q + 6], master[8 * q + 7]));
+                    } else {
+                        const float sc = p.out_inv_scale;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float *w = master + 16 * q;
+                            *reinterpret_cast<uint4 *>(row + (((4 * half + q) ^ (m & 7)) << 4)) = make_uint4(
+                                pack_e4m3x4(w[0] * sc, w[1] * sc, w[2] * sc, w[3] * sc),
+                                pack_e4m3x4(w[4] * sc, w[5] * sc, w[6] * sc, w[7] * sc),
+                                pack_e4m3x4(w[8] * sc, w[9] * sc, w[10] * sc, w[11] * sc),
+                                pack_e4m3x4(w[12] * sc, w[13] * sc, w[14] * sc, w[15] * sc));
+                        }
                     }
                     fence_proxy_async();
                 }
                 esync();
                 if (ok && et == 0 && !*abort_flag) {
-                    for (int bx = 0; bx < HALF; ++bx) {
-                        const int co = HALF * 32 * ph + 32 * bx;
-                        if (p.mode == MODE_FLAT && p.out_stream)
-                            tma_store_2d_hint(&tmO, otile + bx * AREA, co, (int)p0, policy_evict_first());
-                        else if (p.mode == MODE_FLAT) tma_store_2d(&tmO, otile + bx * AREA, co, (int)p0);
+                    for (int bx = 0; bx < (e4 ? 1 : 2); ++bx) {
+                        const int co = 64 * bx;
+                        if (p.mode == MODE_FLAT) tma_store_2d(&tmO, otile + bx * AREA, co, (int)p0);
                         else tma_store_5d(&tmO, otile + bx * AREA, p.oxo * p.ostride + co, j0, p.oyo, i0, b);
                     }
                     bulk_commit();
@@ -1803,20 +1844,26 @@ int sm_count() {
 // i0, b); boxes past Gw or Gh are clipped by the store.  MODE_FLAT: (ostride
 // - ocoff, rows) at (32 k, p0).
 bool make_out_map(CUtensorMap *m, const ConvDesc &d, const Params &p) {
+    // a box row is 128 bytes: 32 floats, 64 bf16 or 128 e4m3 channels
+    const uint64_t es = p.out_dt == DT_BF16 ? 2 : (p.out_dt == DT_E4M3 ? 1 : 4);
+    const CUtensorMapDataType dt = p.out_dt == DT_BF16   ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                   : p.out_dt == DT_E4M3 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const uint32_t inner = (uint32_t)(128 / es);
     const uint64_t os = (uint64_t)p.ostride;
-    float *base = d.out + p.ocoff;
+    void *base = reinterpret_cast<uint8_t *>(d.out) + (uint64_t)p.ocoff * es;
     if (p.mode == MODE_FLAT) {
         const uint64_t dims[2] = {os - p.ocoff, (uint64_t)p.rows};
-        const uint64_t strides[1] = {os * 4};
-        const uint32_t box[2] = {32, BLOCK_M};
-        return make_map(m, base, 2, dims, strides, box);
+        const uint64_t strides[1] = {os * es};
+        const uint32_t box[2] = {inner, BLOCK_M};
+        return make_map(m, base, 2, dims, strides, box, dt);
     }
     const uint64_t dims[5] = {(uint64_t)p.oxm * os - p.ocoff, (uint64_t)d.Gw, (uint64_t)p.oym, (uint64_t)d.Gh,
                               (uint64_t)d.B};
-    const uint64_t strides[4] = {(uint64_t)p.oxm * os * 4, (uint64_t)d.Wo * os * 4, (uint64_t)p.oym * d.Wo * os * 4,
-                                 (uint64_t)d.Ho * d.Wo * os * 4};
-    const uint32_t box[5] = {32, (uint32_t)p.Wt, 1, (uint32_t)p.R, 1};
-    return make_map(m, base, 5, dims, strides, box);
+    const uint64_t strides[4] = {(uint64_t)p.oxm * os * es, (uint64_t)d.Wo * os * es, (uint64_t)p.oym * d.Wo * os * es,
+                                 (uint64_t)d.Ho * d.Wo * os * es};
+    const uint32_t box[5] = {inner, (uint32_t)p.Wt, 1, (uint32_t)p.R, 1};
+    return make_map(m, base, 5, dims, strides, box, dt);
 }
 
 // Choose the R x Wt output block (R * Wt = 128) with the least padding.
@@ -2064,7 +2111,7 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
                                    ? reinterpret_cast<const CUtensorMap *>(static_cast<const TcWeights *>(d.gdn_w)->maps)
                                    : maps;
     CUtensorMap tmO;
-    if (d.Cout == 128 && p.out_dt == DT_F32 && (d.epi == EPI_NONE || d.epi == EPI_RELU) && p.mode != MODE_IM2COL &&
+    if (d.Cout == 128 && (d.epi == EPI_NONE || d.epi == EPI_RELU) && p.mode != MODE_IM2COL &&
         make_out_map(&tmO, d, p)) {
         // persistent, one CTA per SM (conv_tcx_kernel)
         constexpr int STAGES = 3;
