@@ -1821,6 +1821,359 @@ void launch_kernel(unsigned grid, int smem, cudaStream_t st, const CUtensorMap &
     conv_tc_kernel<STAGES, HALF><<<grid, 64 + EPI_THREADS, smem, st>>>(a, bh, bl, gh, gl, p);
 }
 
+
+// ------------------------------------------------------------------ persistent low-precision kernel (Cout = 128)
+//
+// conv_lpx_kernel: conv_lp_kernel's Cout = 128 arithmetic (bf16 or e4m3
+// operands by TMA straight into the MMA, FOLD-chunk partial sums folded into
+// float32 registers, the fused norm as a 3xTF32 GEMM on the FP32 sum) with
+// conv_tcx_kernel's schedule: one CTA per SM over tiles blockIdx.x + k
+// gridDim.x, one load ring across tiles (six 32 KB stages: A, B), gamma hi /
+// lo of the norm's four 32-channel chunks as four more ring entries, y^2 in
+// four TMEM slots of its own (so the next tile's first group never waits for
+// the norm GEMM), the norm result as one more ping-pong group, and eight
+// epilogue warps that finish a tile -- scales, bias or norm, output through a
+// 32 KB staging buffer by TMA store -- while the next one streams through.
+//   warp 0  TMA producer     warp 1  TMEM allocation, MMA issue
+//   warps 2..9  fold, scales / bias / norm, output (TMEM lanes 32 (warp % 4) ..)
+template <int STAGES, int EB>
+__global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lpx_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                       const __grid_constant__ CUtensorMap tmB,
+                                                                       const __grid_constant__ CUtensorMap tmGh,
+                                                                       const __grid_constant__ CUtensorMap tmGl,
+                                                                       const __grid_constant__ CUtensorMap tmO,
+                                                                       const __grid_constant__ Params p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int COUT = 128, HALF = 2;
+    constexpr int AREA = AB_BYTES;                 // 128 rows x 128 bytes
+    constexpr int STAGE_BYTES = 2 * AREA;          // A, B (or gamma hi, lo)
+    constexpr int GCH = COUT / KCH;                // gamma chunks of the norm GEMM
+    static_assert(COUT * 128 == AREA && COUT * KCH * 4 == AREA, "weight slices and gamma chunks fill an area");
+    uint8_t *otile = smem + STAGES * STAGE_BYTES;  // two output boxes
+    uint64_t *bars = reinterpret_cast<uint64_t *>(otile + 2 * AREA);
+    uint64_t *full = bars, *empty = bars + STAGES;
+    uint64_t *pfull = bars + 2 * STAGES, *pempty = pfull + 2, *ebar = pempty + 2, *ready = ebar + 1, *done = ready + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int groups = (p.kchunks + FOLD - 1) / FOLD;
+    const bool gdn = p.fuse_gdn == 1 || p.fuse_gdn == 2;
+    const int entries = p.kchunks + (gdn ? GCH : 0);
+    constexpr int KCE = 128 / EB;                  // elements per K chunk
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&pfull[q], 1);
+            mbar_init(&pempty[q], EPI_THREADS);
+        }
+        mbar_init(ebar, EPI_THREADS);
+        mbar_init(ready, EPI_THREADS);
+        mbar_init(done, EPI_THREADS);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto area = [&](int s, int a) { return smem + s * STAGE_BYTES + a * AREA; };
+    // y^2 of norm chunk c (hi, lo) in TMEM after the two partial buffers
+    auto slot_hi = [&](int c) { return tmem + (uint32_t)(2 * COUT + c * 2 * KCH); };
+    auto slot_lo = [&](int c) { return tmem + (uint32_t)(2 * COUT + c * 2 * KCH + KCH); };
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(p.status, ST_TIMEOUT);
+    };
+    auto origin = [&](int tile, int &b, int &i0, int &j0) {
+        const int tx = tile % p.tiles_x, t = tile / p.tiles_x;
+        i0 = (t % p.tiles_y) * p.R;
+        j0 = tx * p.Wt;
+        b = t / p.tiles_y;
+    };
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            uint32_t v = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+                int b, i0, j0;
+                origin(tile, b, i0, j0);
+                for (int kc = 0; kc < entries; ++kc, ++v) {
+                    const int s = v % STAGES;
+                    if (*abort_flag || !mbar_wait(&empty[s], ((v / STAGES) & 1) ^ 1)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], 2 * AREA);
+                    if (kc < p.kchunks) {
+                        const int t = kc / p.cpt;
+                        const int c0 = (kc % p.cpt) * KCE;
+                        if (p.mode == MODE_S2) {
+                            const int du = p.du[t], dv = p.dv[t];
+                            tma_load_5d(area(s, 0), &tmA, &full[s], (dv & 1) * p.Cin + c0, j0 + (dv >> 1), du & 1,
+                                        i0 + (du >> 1), b);
+                        } else {
+                            tma_load_4d(area(s, 0), &tmA, &full[s], c0, j0 + p.dv[t], i0 + p.du[t], b);
+                        }
+                        tma_load_2d(area(s, 1), &tmB, &full[s], kc * KCE, 0);
+                    } else {   // gamma chunk kc - kchunks: hi, lo
+                        tma_load_2d(area(s, 0), &tmGh, &full[s], (kc - p.kchunks) * KCH, 0);
+                        tma_load_2d(area(s, 1), &tmGl, &full[s], (kc - p.kchunks) * KCH, 0);
+                    }
+                }
+            }
+            if (!ok) {
+                for (uint32_t u = v > STAGES ? v - STAGES : 0; u < v; ++u) mbar_wait(&full[u % STAGES], (u / STAGES) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = EB == 2 ? idesc_bf16(BLOCK_M, COUT) : idesc_e4m3(BLOCK_M, COUT);
+            const uint32_t idt = idesc_tf32(BLOCK_M, COUT);
+            uint32_t v = 0, g = 0;
+            bool ok = true;
+            int tk = 0;
+            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x, ++tk) {
+                for (int kc = 0; kc < entries; ++kc, ++v) {
+                    const int s = v % STAGES;
+                    const bool norm = kc >= p.kchunks;
+                    const bool first = norm ? kc == p.kchunks : kc % FOLD == 0;
+                    const bool last = norm ? kc == entries - 1 : (kc % FOLD == FOLD - 1 || kc == p.kchunks - 1);
+                    const uint32_t q = g & 1;
+                    if (first && g >= 2 && (*abort_flag || !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1))) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    if (first && norm && (*abort_flag || !mbar_wait(ready, tk & 1))) {   // y^2 written
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    if (*abort_flag || !mbar_wait(&full[s], (v / STAGES) & 1)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tmem + q * COUT;
+                    const uint32_t a = smem_u32(area(s, 0)), bb = smem_u32(area(s, 1));
+                    if (!norm) {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {   // 32 bytes of K per MMA
+                            if constexpr (EB == 2)
+                                mma_bf16(dt, sdesc(a + kk * 32), sdesc(bb + kk * 32), idesc, (!first || kk > 0) ? 1u : 0u);
+                            else
+                                mma_e4m3(dt, sdesc(a + kk * 32), sdesc(bb + kk * 32), idesc, (!first || kk > 0) ? 1u : 0u);
+                        }
+                    } else {
+                        const int c = kc - p.kchunks;
+#pragma unroll
+                        for (int kk = 0; kk < KCH / 8; ++kk) {
+                            const uint64_t dgh = sdesc(a + kk * 32), dgl = sdesc(bb + kk * 32);
+                            mma_tf32_ts(dt, slot_hi(c) + 8 * kk, dgh, idt, (!first || kk > 0) ? 1u : 0u);
+                            mma_tf32_ts(dt, slot_hi(c) + 8 * kk, dgl, idt, 1u);
+                            mma_tf32_ts(dt, slot_lo(c) + 8 * kk, dgh, idt, 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                    if (last) {
+                        mma_commit(&pfull[q]);
+                        ++g;
+                    }
+                }
+            }
+        }
+    } else {
+        // ---------------- fold, scales / bias / norm, output (warps 2..9) ----------------
+        const int et = threadIdx.x - 64;
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        const int m = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const int cbase = half * HALF * 32;
+        uint32_t g = 0, eph = 0;
+        bool ok = true;
+        float master[HALF * 32];
+        auto esync = [&]() {
+            if (!ok) return;
+            mbar_arrive(ebar);
+            if (!mbar_wait(ebar, eph & 1)) {
+                fail();
+                ok = false;
+            }
+            ++eph;
+        };
+        int tk = 0;
+        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x, ++tk) {
+            int b, i0, j0;
+            origin(tile, b, i0, j0);
+#pragma unroll
+            for (int i = 0; i < HALF * 32; ++i) master[i] = 0.f;
+            for (int k = 0; k < groups && ok; ++k, ++g) {
+                if (*abort_flag || !mbar_wait(&pfull[g & 1], (g >> 1) & 1)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem + lane_off + (g & 1) * COUT + cbase;
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    float x[32];
+                    tmem_ld32(base + 32 * h, x);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += x[i];
+                }
+                tc_fence_before();
+                mbar_arrive(&pempty[g & 1]);
+            }
+            if (!ok) break;
+#pragma unroll
+            for (int h = 0; h < HALF; ++h) {
+                float *mh = master + 32 * h;
+                const int c = cbase + 32 * h;
+                if constexpr (EB == 1) {   // undo the e4m3 scales: x = stored * in_scale, w = stored * w_scale[o]
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 w = ld_param4(p.w_scale + c + 4 * q);
+                        mh[4 * q] *= w.x * p.in_scale; mh[4 * q + 1] *= w.y * p.in_scale;
+                        mh[4 * q + 2] *= w.z * p.in_scale; mh[4 * q + 3] *= w.w * p.in_scale;
+                    }
+                }
+                if (p.bias) add_bias<32>(mh, p.bias + c);
+                if (p.fuse_gdn == 3) norm_diag<32, false>(mh, nullptr, p.gdn_gamma + c, p.gdn_beta + c);
+                else if (p.fuse_gdn == 4) norm_diag<32, true>(mh, nullptr, p.gdn_gamma + c, p.gdn_beta + c);
+            }
+            if (p.epi == EPI_RELU) {
+#pragma unroll
+                for (int i = 0; i < HALF * 32; ++i) master[i] = fmaxf(master[i], 0.f);
+            }
+            if (gdn) {
+                // y^2 of this thread's chunks c = HALF half + h into their slots (hi is y^2
+                // itself, the MMA taking it as trunc(y^2); lo the exact rest)
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    const int c = HALF * half + h;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        float hv[16], lv[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float sq = master[32 * h + 16 * q + i] * master[32 * h + 16 * q + i];
+                            hv[i] = sq;
+                            lv[i] = sq - tf32_trunc(sq);
+                        }
+                        tmem_st16(slot_hi(c) + lane_off + 16 * q, hv);
+                        tmem_st16(slot_lo(c) + lane_off + 16 * q, lv);
+                    }
+                }
+                tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(ready);
+                if (*abort_flag || !mbar_wait(&pfull[g & 1], (g >> 1) & 1)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem + lane_off + (g & 1) * COUT + cbase;
+#pragma unroll
+                for (int h = 0; h < 2 * HALF; ++h) {
+                    float n[16];
+                    tmem_ld16(base + 16 * h, n);
+                    if (p.fuse_gdn == 1) norm_n<16, false>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
+                    else norm_n<16, true>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
+                }
+                tc_fence_before();
+                mbar_arrive(&pempty[g & 1]);
+                ++g;
+            }
+            if (p.out_dt == DT_F32) {
+                // two halves of 64 channels (threads of half 0, then 1)
+#pragma unroll
+                for (int ph = 0; ph < 2; ++ph) {
+                    if (et == 0) bulk_wait_read();
+                    esync();
+                    if (ok && half == ph) {
+#pragma unroll
+                        for (int h = 0; h < HALF; ++h) {
+                            uint8_t *row = otile + h * AREA + m * 128;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                *reinterpret_cast<float4 *>(row + ((q ^ (m & 7)) << 4)) =
+                                    make_float4(master[32 * h + 4 * q], master[32 * h + 4 * q + 1],
+                                                master[32 * h + 4 * q + 2], master[32 * h + 4 * q + 3]);
+                        }
+                        fence_proxy_async();
+                    }
+                    esync();
+                    if (ok && et == 0 && !*abort_flag) {
+                        for (int bx = 0; bx < HALF; ++bx)
+                            tma_store_5d(&tmO, otile + bx * AREA, p.oxo * p.ostride + HALF * 32 * ph + 32 * bx, j0,
+                                         p.oyo, i0, b);
+                        bulk_commit();
+                    }
+                }
+            } else {
+                const bool e4 = p.out_dt == DT_E4M3;
+                if (et == 0) bulk_wait_read();
+                esync();
+                if (ok) {
+                    uint8_t *row = otile + (e4 ? 0 : half) * AREA + m * 128;
+                    if (!e4) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            *reinterpret_cast<uint4 *>(row + ((q ^ (m & 7)) << 4)) = make_uint4(
+                                pack_bf16_f(master[8 * q], master[8 * q + 1]),
+                                pack_bf16_f(master[8 * q + 2], master[8 * q + 3]),
+                                pack_bf16_f(master[8 * q + 4], master[8 * q + 5]),
+                                pack_bf16_f(master[8 * q + 6], master[8 * q + 7]));
+                    } else {
+                        const float sc = p.out_inv_scale;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float *w = master + 16 * q;
+                            *reinterpret_cast<uint4 *>(row + (((4 * half + q) ^ (m & 7)) << 4)) = make_uint4(
+                                pack_e4m3x4(w[0] * sc, w[1] * sc, w[2] * sc, w[3] * sc),
+                                pack_e4m3x4(w[4] * sc, w[5] * sc, w[6] * sc, w[7] * sc),
+                                pack_e4m3x4(w[8] * sc, w[9] * sc, w[10] * sc, w[11] * sc),
+                                pack_e4m3x4(w[12] * sc, w[13] * sc, w[14] * sc, w[15] * sc));
+                        }
+                    }
+                    fence_proxy_async();
+                }
+                esync();
+                if (ok && et == 0 && !*abort_flag) {
+                    for (int bx = 0; bx < (e4 ? 1 : 2); ++bx)
+                        tma_store_5d(&tmO, otile + bx * AREA, p.oxo * p.ostride + 64 * bx, j0, p.oyo, i0, b);
+                    bulk_commit();
+                }
+            }
+        }
+        if (et == 0) bulk_wait_all();
+        tc_fence_before();
+        mbar_arrive(done);
+    }
+
+    if (warp == 1) {
+        __syncwarp();
+        mbar_wait(done, 0);
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 bool is_flat(const ConvDesc &d) {
     return d.T == 1 && d.du[0] == 0 && d.dv[0] == 0 && d.s == 1 && d.Gh == d.Hi && d.Gw == d.Wi && d.oym == 1 &&
            d.oxm == 1 && d.Ho == d.Hi && d.Wo == d.Wi;
@@ -2257,10 +2610,25 @@ bool launch_lp_impl(const ConvDesc &d, const CUtensorMap &bm, const float *w_sca
         // CTA's epilogue overlaps the other's main loop on these short-K launches
         launch_lp_kernel<4, 1, 2>(grid, st, tmA, bm, gh, gl, p);
     } else if (d.Cout == 128) {
-        if (e4)
+        CUtensorMap tmO;
+        if ((d.epi == EPI_NONE || d.epi == EPI_RELU) && make_out_map(&tmO, d, p)) {
+            // persistent, one CTA per SM: six stages of 32 KB + half the output tile
+            constexpr int ST = 6;
+            const int smem = ST * 2 * AB_BYTES + 2 * AB_BYTES + 256 + 1024;
+            p.ntiles = (int)grid;
+            const unsigned pgrid = std::min<unsigned>(grid, (unsigned)sm_count());
+            if (e4) {
+                cudaFuncSetAttribute(conv_lpx_kernel<ST, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                conv_lpx_kernel<ST, 1><<<pgrid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, tmO, p);
+            } else {
+                cudaFuncSetAttribute(conv_lpx_kernel<ST, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                conv_lpx_kernel<ST, 2><<<pgrid, 64 + EPI_THREADS, smem, st>>>(tmA, bm, gh, gl, tmO, p);
+            }
+        } else if (e4) {
             launch_lp_kernel<6, 2, 1>(grid, st, tmA, bm, gh, gl, p);
-        else
+        } else {
             launch_lp_kernel<6, 2, 2>(grid, st, tmA, bm, gh, gl, p);
+        }
     } else {
         if (e4)
             launch_lp_kernel<5, 3, 1>(grid, st, tmA, bm, gh, gl, p);
