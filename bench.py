@@ -744,9 +744,9 @@ def roofline(rep, peaks):
 # DRAM bytes (read + write) per launch of the dominant kernels, from the ncu
 # captures summarised in profiles/ (None until a capture of the current build)
 TRAFFIC = {
-    # conv_tcx_kernel, ncu on one batch-1 launch: 131.7 MB read + 14.4 MB written,
+    # conv_tcx_kernel, ncu on one batch-1 launch: 131.6 MB read + 14.3 MB written,
     # x8 for the batch-8 launch (traffic grows with the tiles)
-    "g_a.conv1+gdn1:tc": 8 * 146.041856e6,
+    "g_a.conv1+gdn1:tc": 8 * 145.89824e6,
 }
 
 
