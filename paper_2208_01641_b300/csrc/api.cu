@@ -233,7 +233,7 @@ int make_deconv(Layer &L, const ParamMap &pm, const std::string &name, int Cin, 
                     for (int v = 0; v < k; ++v)
                         r[(((size_t)c * 25) + u * 5 + v) * 4 + o] = w[(((size_t)c * Cout + o) * k + u) * k + v];
         if ((rc = upload(L.w_small, r.data(), r.size() * sizeof(float)))) return rc;
-        // the two-pass form needs 128 floats of scratch a position, which the
+        // the two-pass form needs 25 * Cout floats of scratch a position, which the
         // codec's activation buffers hold when Cin >= 128; the choice depends on
         // the model only, so every batch size decodes through the same arithmetic
         if (Cin >= 128) {
@@ -481,10 +481,11 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
         const double flop = 2.0 * B * Ho * Wo * L.Cout * L.Cin * 6.25;
         const double bytes = 4.0 * ((double)B * Hi * Wi * L.Cin + (double)B * Ho * Wo * L.Cout + 100.0 * L.Cin);
         // two passes (the layer's tensor-core weights exist when Cin >= 128): the tap
-        // contributions of every input position by a tensor-core 1x1 GEMM into the
-        // scratch buffer (128 floats a position; an activation buffer of Cin >= 128
-        // channels), then their per-pixel sums
-        const size_t need = (size_t)B * Hi * Wi * 128 * sizeof(float);
+        // contributions of every input position by a tensor-core 1x1 GEMM (128 columns,
+        // the leading 25 * Cout stored) into the scratch buffer (an activation buffer
+        // of Cin >= 128 channels), then their per-pixel sums
+        const int cs = deconv_scatter_stride(L.Cout);
+        const size_t need = (size_t)B * Hi * Wi * cs * sizeof(float);
         if (scratch && L.w_scatter.valid && cd->opt.conv_impl != LIC_CONV_SIMT && L.in_dt == DT_F32) {
             if (!scratch->p || scratch->bytes < need) {   // not reached: the buffers hold Cin >= 128 channels
                 atomic_status(cd, ST_TIMEOUT);
@@ -509,9 +510,10 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
             d.in_dt = d.out_dt = DT_F32;
             d.in_scale = d.out_scale = 1.f;
             d.out_stream = 1;
+            d.out_stride = cs;
             if (tc::can_run(d, L.w_scatter)) {
                 const double rows = (double)B * Hi * Wi;
-                timed(const_cast<lic_codec *>(cd), L.name + ":tc", flop, 4.0 * rows * (L.Cin + 128), 1, st, [&] {
+                timed(const_cast<lic_codec *>(cd), L.name + ":tc", flop, 4.0 * rows * (L.Cin + cs), 1, st, [&] {
                     if (!tc::launch(d, L.w_scatter, st)) atomic_status(cd, ST_TIMEOUT);
                 });
                 timed(const_cast<lic_codec *>(cd), L.name + ".gather", 0.0,

@@ -264,7 +264,6 @@ __global__ void __launch_bounds__(DS_THREADS) deconv_small_kernel(const float *_
 // output pixel (2m + py, 2n + px) adds, for du, dv in {-1, 0, 1} with taps
 // u = py + 2 - 2 du and v = px + 2 - 2 dv in [0, 4], the contribution of
 // input position (m + du, n + dv) through (u, v).
-constexpr int DG_STRIDE = 128;   // C row: 25 * Cout contributions, padded
 template <int COUT>
 __global__ void __launch_bounds__(256) deconv_gather_kernel(const float *__restrict__ C, int B, int Hi, int Wi,
                                                             const float *__restrict__ bias, float *__restrict__ out) {
@@ -285,7 +284,7 @@ __global__ void __launch_bounds__(256) deconv_gather_kernel(const float *__restr
         for (int dv = -1; dv <= 1; ++dv) {
             const int v = px + 2 - 2 * dv, ni = n + dv;
             if (v < 0 || v > 4 || ni < 0 || ni >= Wi) continue;
-            const float *c = C + (((int64_t)b * Hi + mi) * Wi + ni) * DG_STRIDE + (u * 5 + v) * COUT;
+            const float *c = C + (((int64_t)b * Hi + mi) * Wi + ni) * deconv_scatter_stride(COUT) + (u * 5 + v) * COUT;
 #pragma unroll
             for (int o = 0; o < COUT; ++o) acc[o] += __ldcs(c + o);   // read once: streaming
         }

@@ -799,20 +799,20 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
             } else
 #pragma unroll
             for (int q = 0; q < A_BYTES / 16 / EPI_THREADS; ++q) {
+                // the raw value serves as A_hi (the MMA takes it as trunc(x)); only
+                // A_lo = x - trunc(x), exact, is written, and a transformed input back
                 const int idx = et + q * EPI_THREADS;
                 float4 v = a[idx];
-                if (p.in_xform == IN_ABS) {
-                    v.x = fabsf(v.x); v.y = fabsf(v.y); v.z = fabsf(v.z); v.w = fabsf(v.w);
-                } else if (p.in_xform == IN_SQUARE) {
-                    v.x *= v.x; v.y *= v.y; v.z *= v.z; v.w *= v.w;
+                if (p.in_xform != IN_NONE) {
+                    if (p.in_xform == IN_ABS) {
+                        v.x = fabsf(v.x); v.y = fabsf(v.y); v.z = fabsf(v.z); v.w = fabsf(v.w);
+                    } else {
+                        v.x *= v.x; v.y *= v.y; v.z *= v.z; v.w *= v.w;
+                    }
+                    a[idx] = v;
                 }
-                float4 h, l;
-                h.x = tf32_rna(v.x); l.x = tf32_rna(v.x - h.x);
-                h.y = tf32_rna(v.y); l.y = tf32_rna(v.y - h.y);
-                h.z = tf32_rna(v.z); l.z = tf32_rna(v.z - h.z);
-                h.w = tf32_rna(v.w); l.w = tf32_rna(v.w - h.w);
-                a[idx] = h;
-                alo[idx] = l;
+                alo[idx] = make_float4(v.x - tf32_trunc(v.x), v.y - tf32_trunc(v.y), v.z - tf32_trunc(v.z),
+                                       v.w - tf32_trunc(v.w));
             }
             fence_proxy_async();
             mbar_arrive(&conv[s]);
@@ -872,10 +872,10 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                     v.x = master[h * 32 + 4 * u + 0]; v.y = master[h * 32 + 4 * u + 1];
                     v.z = master[h * 32 + 4 * u + 2]; v.w = master[h * 32 + 4 * u + 3];
                     v.x *= v.x; v.y *= v.y; v.z *= v.z; v.w *= v.w;
-                    hv.x = tf32_rna(v.x); lv.x = tf32_rna(v.x - hv.x);
-                    hv.y = tf32_rna(v.y); lv.y = tf32_rna(v.y - hv.y);
-                    hv.z = tf32_rna(v.z); lv.z = tf32_rna(v.z - hv.z);
-                    hv.w = tf32_rna(v.w); lv.w = tf32_rna(v.w - hv.w);
+                    // truncation split, as for the activations: y^2 itself is the hi operand
+                    hv = v;
+                    lv.x = v.x - tf32_trunc(v.x); lv.y = v.y - tf32_trunc(v.y);
+                    lv.z = v.z - tf32_trunc(v.z); lv.w = v.w - tf32_trunc(v.w);
                     const int off = m * 128 + ((u ^ (m & 7)) << 4);
                     *reinterpret_cast<float4 *>(ahi + off) = hv;
                     *reinterpret_cast<float4 *>(alo + off) = lv;
@@ -1359,6 +1359,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                     if (ok && et == 0 && !*abort_flag) {
                         for (int bx = 0; bx < HALF; ++bx) {
                             const int co = HALF * 32 * ph + 32 * bx;
+                            if (p.mode == MODE_FLAT && co >= p.ostride - p.ocoff) continue;   // narrow output
                             if (p.mode == MODE_FLAT && p.out_stream)
                                 tma_store_2d_hint(&tmO, otile + bx * AREA, co, (int)p0, policy_evict_first());
                             else if (p.mode == MODE_FLAT) tma_store_2d(&tmO, otile + bx * AREA, co, (int)p0);
@@ -2371,6 +2372,13 @@ bool can_run(const ConvDesc &d, const TcWeights &w) {
         if (!g || !g->valid || g->T != 1 || g->Cin != d.Cout || g->Cout != d.Cout || !d.gdn_beta) return false;
         if (d.epi != EPI_NONE) return false;
     }
+    if (d.out_stride > 0 && d.out_stride - d.out_coff < d.Cout) {
+        // a narrow output (the leading out_stride - out_coff channels of each row are
+        // stored): the persistent kernel's clipped FLAT store only
+        if (d.Cout != 128 || !is_flat(d) || w.im2col || d.fuse_gdn || d.out_dt != DT_F32) return false;
+        if (d.epi != EPI_NONE && d.epi != EPI_RELU) return false;
+        if (d.out_stride - d.out_coff <= 0 || (d.out_stride * 4) % 16 || (d.out_coff * 4) % 16) return false;
+    }
     if (w.im2col) return d.epi != EPI_GDN && d.epi != EPI_IGDN && d.in_xform == IN_NONE && d.oym == 1 && d.oxm == 1;
 
     if (is_flat(d)) return true;
@@ -2474,7 +2482,9 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
         cudaFuncSetAttribute(conv_tcx_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         conv_tcx_kernel<STAGES><<<pgrid, TCX_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1], tmO, p);
         return true;
-    }    const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
+    }
+    if (p.ostride - p.ocoff < d.Cout) return false;   // a narrow output needs the clipped TMA store
+    const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
     if (d.Cout == 128)
         launch_kernel<4, 2>(grid, smem, st, tmA, maps[0], maps[1], gmaps[0], gmaps[1], p);
     else

@@ -273,10 +273,11 @@ void launch_deconv_small(const float *in, int B, int Hi, int Wi, int Cin, const 
                          int Cout, float *out, cudaStream_t st);
 
 // The same transposed conv in two passes, the first on the tensor cores: C
-// ([B][Hi][Wi][128], from a 1x1 GEMM) holds every input position's 25 * Cout
-// tap contributions (column (u * 5 + v) * Cout + o); this sums them into
-// out (NHWC [B][2Hi][2Wi][Cout]) and adds the bias.  Each C entry lands in
-// exactly one output pixel; the sum order per pixel is fixed.
+// ([B][Hi][Wi][deconv_scatter_stride(Cout)], from a 1x1 GEMM) holds every input
+// position's 25 * Cout tap contributions (column (u * 5 + v) * Cout + o); this
+// sums them into out (NHWC [B][2Hi][2Wi][Cout]) and adds the bias.  Each C
+// entry lands in exactly one output pixel; the sum order per pixel is fixed.
+constexpr int deconv_scatter_stride(int cout) { return (25 * cout + 3) / 4 * 4; }   // 16-byte rows
 void launch_deconv_gather(const float *C, int B, int Hi, int Wi, int Cout, const float *bias, float *out,
                           cudaStream_t st);
 
