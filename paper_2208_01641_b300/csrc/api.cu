@@ -384,9 +384,19 @@ ConvDesc op_desc(const lic_codec *cd, const Layer &L, const ConvOp &op, const fl
 
 // One GEMM launch of a layer; with G, the GDN / IGDN that follows the layer
 // runs in the same launch (the caller has checked that it can).
+// Split-K scratch a layer's launches may use: B * frame_floats floats at p,
+// frame_floats fixed by the frame size (never by the buffer's capacity)
+struct SplitScratch {
+    float *p = nullptr;
+    int64_t frame_floats = 0;
+};
+
 void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *in, int B, int Hi, int Wi,
-            float *out, int Ho, int Wo, cudaStream_t st, const Gdn *G = nullptr, int out_dt = -1) {
+            float *out, int Ho, int Wo, cudaStream_t st, const Gdn *G = nullptr, int out_dt = -1,
+            SplitScratch sk = {}) {
     ConvDesc d = op_desc(cd, L, op, in, B, Hi, Wi, out, Ho, Wo);
+    d.part = sk.p;
+    d.part_frame_floats = sk.p ? sk.frame_floats : 0;
     if (out_dt >= 0) {   // the caller wants this storage instead of the layer's own
         d.out_dt = out_dt;
         d.out_scale = 1.f;
@@ -409,6 +419,7 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
         bool ok = cd->opt.conv_impl != LIC_CONV_SIMT || d.in_dt != DT_F32;
         for (size_t j = 0; j < op.parts.size() && ok; ++j) {
             ConvDesc dp = d;
+            dp.part = nullptr;
             dp.Cout = op.parts[j]->Cout;
             dp.out_coff = op.part_off[j];
             dp.out_stride = d.Cout;
@@ -437,7 +448,8 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
     }
     const bool use_tc = cd->opt.conv_impl != LIC_CONV_SIMT && tc::can_run(d, op.tcw);
     nm += use_tc ? ":tc" : ":simt";
-    timed(const_cast<lic_codec *>(cd), nm, flop, bytes, 1, st, [&] {
+    const int nl = use_tc && tc::split_k(d, op.tcw) > 1 ? 2 : 1;   // split K: + the sum of the slices
+    timed(const_cast<lic_codec *>(cd), nm, flop, bytes, nl, st, [&] {
         if (!use_tc || !tc::launch(d, op.tcw, st)) launch_conv_simt(d, st);
     });
 }
@@ -447,7 +459,7 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
 // auxiliary stream k - 1, so the small launches of h_s and of the first
 // g_s layers fill the GPU together instead of one after another.
 void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out, int Ho, int Wo,
-             cudaStream_t st, const Gdn *G, int out_dt = -1) {
+             cudaStream_t st, const Gdn *G, int out_dt = -1, SplitScratch sk = {}) {
     const int n = (int)L.ops.size();
     // while launches are being timed one by one (lic_profile_enable) the phases run in
     // sequence, so that each launch's event pair brackets that launch alone
@@ -456,8 +468,11 @@ void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi
         cudaEventRecord(cd->ev_fork, st);
         for (int k = 1; k < n; ++k) cudaStreamWaitEvent(cd->aux[k - 1], cd->ev_fork, 0);
     }
+    // split K only for a single launch: the phases of a transposed conv already
+    // fill the GPU together (slicing them measured slower)
     for (int k = 0; k < n; ++k)
-        run_op(cd, L, *L.ops[k], in, B, Hi, Wi, out, Ho, Wo, (fork && k > 0) ? cd->aux[k - 1] : st, G, out_dt);
+        run_op(cd, L, *L.ops[k], in, B, Hi, Wi, out, Ho, Wo, (fork && k > 0) ? cd->aux[k - 1] : st, G, out_dt,
+               n == 1 ? sk : SplitScratch{});
     if (fork) {
         for (int k = 1; k < n; ++k) {
             cudaEventRecord(cd->ev_join[k - 1], cd->aux[k - 1]);
@@ -467,7 +482,7 @@ void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi
 }
 
 void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out,
-               cudaStream_t st, int out_dt = -1, const DevBuf *scratch = nullptr) {
+               cudaStream_t st, int out_dt = -1, const DevBuf *scratch = nullptr, SplitScratch sk = {}) {
     int Ho, Wo;
     if (L.deconv) {
         Ho = 2 * Hi;
@@ -527,7 +542,7 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
         });
         return;
     }
-    run_ops(cd, L, in, B, Hi, Wi, out, Ho, Wo, st, nullptr, out_dt);
+    run_ops(cd, L, in, B, Hi, Wi, out, Ho, Wo, st, nullptr, out_dt, sk);
 }
 
 void run_gdn(const lic_codec *cd, const Gdn &G, const float *in, int B, int H, int W, float *out, cudaStream_t st) {
@@ -695,18 +710,30 @@ void analysis(lic_codec *cd, int B, int Hp, int Wp, cudaStream_t st) {
     run_layer(cd, cd->ga[3], in, B, H, W, cd->y.as<float>(), st);
 }
 
+// Split-K scratch of the hyper transforms: act0, free while they run, holds
+// (Hp / 2) (Wp / 2) N floats a frame for frames of Hp x Wp = 16 Hy x 16 Wy
+SplitScratch hyper_scratch(lic_codec *cd, int B, int Hy, int Wy) {
+    SplitScratch sk;
+    sk.frame_floats = 64LL * Hy * Wy * cd->N;
+    if (cd->act0.p && cd->act0.bytes >= (size_t)B * sk.frame_floats * sizeof(float)) sk.p = cd->act0.as<float>();
+    else atomic_status(cd, ST_TIMEOUT);   // not reached: ensure_workspace sized act0 for these frames
+    return sk;
+}
+
 // h_a: y -> z; conv3x3/1 on |y| + ReLU, conv5x5/2 + ReLU, conv5x5/2
 void hyper_analysis(lic_codec *cd, const float *y, int B, int Hy, int Wy, cudaStream_t st) {
-    run_layer(cd, cd->ha[0], y, B, Hy, Wy, cd->h1.as<float>(), st);
-    run_layer(cd, cd->ha[1], cd->h1.as<float>(), B, Hy, Wy, cd->h2.as<float>(), st);
-    run_layer(cd, cd->ha[2], cd->h2.as<float>(), B, Hy / 2, Wy / 2, cd->z.as<float>(), st);
+    const SplitScratch sk = hyper_scratch(cd, B, Hy, Wy);
+    run_layer(cd, cd->ha[0], y, B, Hy, Wy, cd->h1.as<float>(), st, -1, nullptr, sk);
+    run_layer(cd, cd->ha[1], cd->h1.as<float>(), B, Hy, Wy, cd->h2.as<float>(), st, -1, nullptr, sk);
+    run_layer(cd, cd->ha[2], cd->h2.as<float>(), B, Hy / 2, Wy / 2, cd->z.as<float>(), st, -1, nullptr, sk);
 }
 
 // h_s: z_hat -> sigma; deconv+ReLU, deconv+ReLU, conv3x3+ReLU; then the index
 void hyper_synthesis(lic_codec *cd, const float *zhat, int B, int Hz, int Wz, cudaStream_t st) {
-    run_layer(cd, cd->hs[0], zhat, B, Hz, Wz, cd->g1.as<float>(), st);
-    run_layer(cd, cd->hs[1], cd->g1.as<float>(), B, 2 * Hz, 2 * Wz, cd->g2.as<float>(), st);
-    run_layer(cd, cd->hs[2], cd->g2.as<float>(), B, 4 * Hz, 4 * Wz, cd->sigma.as<float>(), st);
+    const SplitScratch sk = hyper_scratch(cd, B, 4 * Hz, 4 * Wz);
+    run_layer(cd, cd->hs[0], zhat, B, Hz, Wz, cd->g1.as<float>(), st, -1, nullptr, sk);
+    run_layer(cd, cd->hs[1], cd->g1.as<float>(), B, 2 * Hz, 2 * Wz, cd->g2.as<float>(), st, -1, nullptr, sk);
+    run_layer(cd, cd->hs[2], cd->g2.as<float>(), B, 4 * Hz, 4 * Wz, cd->sigma.as<float>(), st, -1, nullptr, sk);
     const double n = 16.0 * B * Hz * Wz * cd->M;
     timed(cd, "scale_index", 0, 5 * n, 1, st, [&] {
         launch_scale_index(cd->sigma.as<float>(), B, 16 * Hz * Wz, cd->M, cd->idx.as<uint8_t>(), nullptr, st);

@@ -89,6 +89,7 @@ struct Params {
     int kchunks;
     uint32_t tmem_cols;
     int ntiles;                   // conv_tcx_kernel: tiles of the launch
+    int ksplit;                   // conv_tcx_kernel: K slices a tile is cut into (1: none)
     int out_stream;               // conv_tcx_kernel: output read once soon after; evict it from L2 first
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
 };
@@ -1020,9 +1021,10 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int groups = (p.kchunks + FOLD - 1) / FOLD;
-    const bool gdn = p.fuse_gdn == 1 || p.fuse_gdn == 2;
-    const int entries = p.kchunks + (gdn ? NGE : 0);   // ring entries per tile
+    const bool gdn = p.fuse_gdn == 1 || p.fuse_gdn == 2;   // (never with ksplit > 1)
+    // work units u = tile * ksplit + slice; slice q covers K chunks [kbegin(q), kbegin(q + 1))
+    const int nunits = p.ntiles * p.ksplit;
+    auto kbegin = [&](int q) { return (int)((int64_t)q * p.kchunks / p.ksplit); };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -1069,18 +1071,20 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
             const uint32_t tx_bytes = (p.mode == MODE_IM2COL ? 0 : AREA) + 2 * AREA;
             uint32_t v = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+            for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const int tile = u / p.ksplit, kc0 = kbegin(u % p.ksplit), nk = kbegin(u % p.ksplit + 1) - kc0;
                 int b, i0, j0;
                 int64_t p0;
                 origin(tile, b, i0, j0, p0);
-                for (int kc = 0; kc < entries; ++kc, ++v) {
+                for (int e = 0; e < nk + (gdn ? NGE : 0); ++e, ++v) {   // ring entries of the unit
                     const int s = v % STAGES;
                     if (*abort_flag || !mbar_wait(&empty[s], ((v / STAGES) & 1) ^ 1)) {
                         fail();
                         ok = false;
                         break;
                     }
-                    if (kc < p.kchunks) {
+                    if (e < nk) {
+                        const int kc = kc0 + e;
                         const int t = kc / p.cpt;
                         const int c0 = (kc % p.cpt) * KCH;
                         mbar_expect_tx(&full[s], tx_bytes);
@@ -1095,12 +1099,12 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                         }
                         tma_load_2d(area(s, 2), &tmBh, &full[s], kc * KCH, 0);
                         tma_load_2d(area(s, 3), &tmBl, &full[s], kc * KCH, 0);
-                    } else {   // gamma entry e: chunks 2e, 2e + 1 as [hi | lo] pairs
-                        const int e = kc - p.kchunks;
+                    } else {   // gamma entry ge: chunks 2 ge, 2 ge + 1 as [hi | lo] pairs
+                        const int ge = e - nk;
                         mbar_expect_tx(&full[s], 4 * AREA);
                         for (int j = 0; j < 2; ++j) {
-                            tma_load_2d(area(s, 2 * j), &tmGh, &full[s], (2 * e + j) * KCH, 0);
-                            tma_load_2d(area(s, 2 * j + 1), &tmGl, &full[s], (2 * e + j) * KCH, 0);
+                            tma_load_2d(area(s, 2 * j), &tmGh, &full[s], (2 * ge + j) * KCH, 0);
+                            tma_load_2d(area(s, 2 * j + 1), &tmGl, &full[s], (2 * ge + j) * KCH, 0);
                         }
                     }
                 }
@@ -1116,7 +1120,8 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
             uint32_t v = 0, g = 0;   // ring entry, partial-buffer group
             bool ok = true;
             int tk = 0;
-            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x, ++tk) {
+            for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++tk) {
+                const int kc0 = kbegin(u % p.ksplit), kc1 = kbegin(u % p.ksplit + 1);
                 // the previous tile's norm GEMM read its y^2 from the buffer this tile's
                 // first group writes: let it complete first
                 if (gdn && tk > 0 && (*abort_flag || !mbar_wait(&pfull[(g - 1) & 1], ((g - 1) >> 1) & 1))) {
@@ -1124,10 +1129,10 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                     ok = false;
                     break;
                 }
-                for (int kc = 0; kc < p.kchunks; ++kc, ++v) {
+                for (int kc = kc0; kc < kc1; ++kc, ++v) {
                     const int s = v % STAGES;
-                    const bool first = kc % FOLD == 0;
-                    const bool last = kc % FOLD == FOLD - 1 || kc == p.kchunks - 1;
+                    const bool first = (kc - kc0) % FOLD == 0;
+                    const bool last = (kc - kc0) % FOLD == FOLD - 1 || kc == kc1 - 1;
                     const uint32_t q = g & 1;
                     if (first && g >= 2 && (*abort_flag || !mbar_wait(&pempty[q], ((g >> 1) - 1) & 1))) {
                         fail();
@@ -1199,8 +1204,9 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
         const int st = threadIdx.x - 64;   // 0 .. TCX_SPLIT - 1
         uint32_t v = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-            for (int kc = 0; kc < p.kchunks; ++kc, ++v) {
+        for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            const int nk = kbegin(u % p.ksplit + 1) - kbegin(u % p.ksplit);
+            for (int kc = 0; kc < nk; ++kc, ++v) {
                 const int s = v % STAGES;
                 if (*abort_flag || !mbar_wait(&full[s], (v / STAGES) & 1)) {
                     fail();
@@ -1250,13 +1256,15 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
             }
             ++eph;
         };
-        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+        for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            const int tile = u / p.ksplit, sl = u % p.ksplit;
+            const int groups = (kbegin(sl + 1) - kbegin(sl) + FOLD - 1) / FOLD;
             int b, i0, j0;
             int64_t p0;
             origin(tile, b, i0, j0, p0);
 #pragma unroll
             for (int i = 0; i < HALF * 32; ++i) master[i] = 0.f;
-            // every partial sum of the tile into master, as its group completes
+            // every partial sum of the unit into master, as its group completes
             for (int k = 0; k < groups && ok; ++k, ++g) {
                 if (*abort_flag || !mbar_wait(&pfull[g & 1], (g >> 1) & 1)) {
                     fail();
@@ -1280,13 +1288,13 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
             }
             if (!ok) break;
 #pragma unroll
-            for (int h = 0; h < HALF; ++h) {
+            for (int h = 0; h < (p.ksplit > 1 ? 0 : HALF); ++h) {   // a K slice leaves bias and ReLU to the sum
                 const int c = cbase + 32 * h;
                 if (p.fuse_gdn == 3) norm_diag<32, false>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
                 else if (p.fuse_gdn == 4) norm_diag<32, true>(master + 32 * h, p.bias + c, p.gdn_gamma + c, p.gdn_beta + c);
                 else add_bias<32>(master + 32 * h, p.bias + c);
             }
-            if (p.epi == EPI_RELU) {
+            if (p.epi == EPI_RELU && p.ksplit == 1) {
 #pragma unroll
                 for (int i = 0; i < HALF * 32; ++i) master[i] = fmaxf(master[i], 0.f);
             }
@@ -1359,6 +1367,10 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                     if (ok && et == 0 && !*abort_flag) {
                         for (int bx = 0; bx < HALF; ++bx) {
                             const int co = HALF * 32 * ph + 32 * bx;
+                            if (p.ksplit > 1) {   // partial sums: rows (slice * ntiles + tile) * 128 ..
+                                tma_store_2d(&tmO, otile + bx * AREA, co, (sl * p.ntiles + tile) * BLOCK_M);
+                                continue;
+                            }
                             if (p.mode == MODE_FLAT && co >= p.ostride - p.ocoff) continue;   // narrow output
                             if (p.mode == MODE_FLAT && p.out_stream)
                                 tma_store_2d_hint(&tmO, otile + bx * AREA, co, (int)p0, policy_evict_first());
@@ -1822,6 +1834,50 @@ void launch_kernel(unsigned grid, int smem, cudaStream_t st, const CUtensorMap &
     conv_tc_kernel<STAGES, HALF><<<grid, 64 + EPI_THREADS, smem, st>>>(a, bh, bl, gh, gl, p);
 }
 
+
+// Split-K sums of conv_tcx_kernel (ksplit > 1): slice q of tile t left its
+// 128 x 128 partial sums at rows (q * ntiles + t) * 128 .. of part; one thread
+// adds the slices of four channels of one tile row in slice order, then the
+// bias and ReLU, and writes them where the fused store would have (FLAT rows,
+// or pixel (i, j) of the tile's R x Wt block at output (i oym + oyo, j oxm + oxo)).
+__global__ void __launch_bounds__(256) tcx_splitk_sum_kernel(const float4 *__restrict__ part, const Params p) {
+    const int64_t rows = (int64_t)p.ntiles * BLOCK_M;
+    const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (idx >= rows * 32) return;
+    const int c4 = (int)(idx % 32);
+    const int64_t row = idx / 32;
+    const int tile = (int)(row / BLOCK_M), m = (int)(row % BLOCK_M);
+    int64_t o;
+    if (p.mode == MODE_FLAT) {
+        if (row >= p.rows) return;
+        o = row * p.ostride;
+    } else {
+        const int tx = tile % p.tiles_x, t = tile / p.tiles_x;
+        const int i = (t % p.tiles_y) * p.R + m / p.Wt, j = tx * p.Wt + m % p.Wt, b = t / p.tiles_y;
+        if (i >= p.Gh || j >= p.Gw) return;
+        o = (((int64_t)b * p.Ho + (int64_t)i * p.oym + p.oyo) * p.Wo + (int64_t)j * p.oxm + p.oxo) * p.ostride;
+    }
+    float4 acc = part[idx];
+    for (int q = 1; q < p.ksplit; ++q) {
+        const float4 x = part[q * rows * 32 + idx];
+        acc.x += x.x;
+        acc.y += x.y;
+        acc.z += x.z;
+        acc.w += x.w;
+    }
+    const float4 bb = __ldg(reinterpret_cast<const float4 *>(p.bias) + c4);
+    acc.x += bb.x;
+    acc.y += bb.y;
+    acc.z += bb.z;
+    acc.w += bb.w;
+    if (p.epi == EPI_RELU) {
+        acc.x = fmaxf(acc.x, 0.f);
+        acc.y = fmaxf(acc.y, 0.f);
+        acc.z = fmaxf(acc.z, 0.f);
+        acc.w = fmaxf(acc.w, 0.f);
+    }
+    *reinterpret_cast<float4 *>(p.out + o + p.ocoff + 4 * c4) = acc;
+}
 
 // ------------------------------------------------------------------ persistent low-precision kernel (Cout = 128)
 //
@@ -2360,6 +2416,30 @@ bool params_aligned(const ConvDesc &d) {
     return a16(d.bias) && a16(d.gdn_beta) && a16(d.gdn_gamma);
 }
 
+int split_k(const ConvDesc &d, const TcWeights &w) {
+    // Only the small grids of the hyper transforms profit: a tile walks its K
+    // chunks one after another, so a layer of a few tiles a frame leaves most SMs
+    // idle.  The slice count fills 148 SMs for a batch of 8 frames (fixed numbers,
+    // not the device's: the arithmetic must not depend on where it runs), keeps
+    // six or more K chunks a slice, and keeps the partial sums within the
+    // scratch the caller gives a frame.
+    if (!d.part || d.part_frame_floats <= 0 || !w.valid || w.im2col) return 1;
+    if (d.Cout != 128 || d.fuse_gdn || d.in_dt != DT_F32 || d.out_dt != DT_F32) return 1;
+    if (d.epi != EPI_NONE && d.epi != EPI_RELU) return 1;
+    const int ostride = d.out_stride > 0 ? d.out_stride : d.Cout;
+    if (ostride - d.out_coff < d.Cout || ostride % 4 || d.out_coff % 4) return 1;
+    if (is_flat(d) || (d.s != 1 && d.s != 2)) return 1;
+    int R, Wt;
+    pick_tile(d.Gh, d.Gw, &R, &Wt);
+    const int64_t tpf = (int64_t)((d.Gw + Wt - 1) / Wt) * ((d.Gh + R - 1) / R);
+    const int nk = d.T * (d.Cin / KCH);
+    int64_t q = 148 / (8 * tpf);
+    q = std::min<int64_t>(q, nk / 6);
+    q = std::min<int64_t>(q, 8);
+    q = std::min<int64_t>(q, d.part_frame_floats / (tpf * BLOCK_M * 128));
+    return (int)std::max<int64_t>(q, 1);
+}
+
 bool can_run(const ConvDesc &d, const TcWeights &w) {
     if (!w.valid || d.Cin != w.Cin || d.T != w.T || d.Cout != w.Cout || !d.bias || !d.status) return false;
     if (!params_aligned(d)) return false;
@@ -2388,6 +2468,7 @@ bool can_run(const ConvDesc &d, const TcWeights &w) {
 
 bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     Params p{};
+    p.ksplit = 1;
     p.out = d.out;
     p.bias = d.bias;
     p.gdn_x = d.gdn_x;
@@ -2472,17 +2553,34 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
                                    ? reinterpret_cast<const CUtensorMap *>(static_cast<const TcWeights *>(d.gdn_w)->maps)
                                    : maps;
     CUtensorMap tmO;
-    if (d.Cout == 128 && (d.epi == EPI_NONE || d.epi == EPI_RELU) && p.mode != MODE_IM2COL &&
-        make_out_map(&tmO, d, p)) {
+    const int ks = split_k(d, w);
+    bool omap;
+    if (ks > 1) {
+        // the slices' partial sums: [ks][grid * 128][128] floats at d.part
+        const uint64_t dims[2] = {128, (uint64_t)ks * grid * BLOCK_M};
+        const uint64_t strides[1] = {128 * 4};
+        const uint32_t box[2] = {32, BLOCK_M};
+        omap = make_map(&tmO, d.part, 2, dims, strides, box);
+    } else {
+        omap = make_out_map(&tmO, d, p);
+    }
+    if (d.Cout == 128 && (d.epi == EPI_NONE || d.epi == EPI_RELU) && p.mode != MODE_IM2COL && omap) {
         // persistent, one CTA per SM (conv_tcx_kernel)
         constexpr int STAGES = 3;
         p.ntiles = (int)grid;
-        const unsigned pgrid = std::min<unsigned>(grid, (unsigned)sm_count());
+        p.ksplit = ks;
+        const unsigned pgrid = std::min<unsigned>(grid * ks, (unsigned)sm_count());
         const int smem = STAGES * 4 * A_BYTES + 2 * A_BYTES + 256 + 1024;
         cudaFuncSetAttribute(conv_tcx_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         conv_tcx_kernel<STAGES><<<pgrid, TCX_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1], tmO, p);
+        if (ks > 1) {
+            const int64_t n = (int64_t)grid * BLOCK_M * 32;
+            tcx_splitk_sum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const float4 *>(d.part),
+                                                                               p);
+        }
         return true;
     }
+    if (ks > 1) return false;   // not reached: split_k admits only launches of the persistent kernel
     if (p.ostride - p.ocoff < d.Cout) return false;   // a narrow output needs the clipped TMA store
     const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
     if (d.Cout == 128)
@@ -2553,6 +2651,7 @@ bool launch_lp_impl(const ConvDesc &d, const CUtensorMap &bm, const float *w_sca
     const bool e4 = d.in_dt == DT_E4M3;
     const int EBY = e4 ? 1 : 2;
     Params p{};
+    p.ksplit = 1;
     p.out = d.out;
     p.bias = d.bias;
     p.gdn_x = d.gdn_x;

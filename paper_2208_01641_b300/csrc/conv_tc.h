@@ -40,6 +40,12 @@ bool can_run(const ConvDesc &d, const TcWeights &w);
 // encoded, in which case the caller runs the CUDA-core kernel instead.
 bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
 
+// The K slices launch() cuts each 128-pixel tile into (1: none).  Above 1 it
+// runs a second kernel that adds the slices' partial sums in slice order.  The
+// count depends on the layer and the frame size only (never on the batch, the
+// buffers or the device), so a frame gets the same arithmetic in any batch.
+int split_k(const ConvDesc &d, const TcWeights &w);
+
 // Precision forms: bf16 or e4m3 activations in (d.in_dt), any storage out.
 bool can_run_lp(const ConvDesc &d, const TcWeights &w);
 bool launch_lp(const ConvDesc &d, const TcWeights &w, cudaStream_t st);

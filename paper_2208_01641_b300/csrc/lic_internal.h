@@ -258,6 +258,10 @@ struct ConvDesc {
     int out_stride, out_coff;
     // the output is read once, soon (tensor-core kernels store it evict-first in L2)
     int out_stream;
+    // split-K scratch (FP32 tensor-core kernel, Cout = 128, no fused norm): part
+    // holds B * part_frame_floats floats; null: no split
+    float *part;
+    int64_t part_frame_floats;
     int T;
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
     int in_xform, epi;
