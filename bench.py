@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--height", type=int, default=720)
     ap.add_argument("--width", type=int, default=1280)
     ap.add_argument("--conv", default="auto", choices=["auto", "simt"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"],
+                    help="arithmetic of the timed chain (the precision forms run in any case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / student / pipelined forms")
@@ -205,7 +207,8 @@ def main():
     B, H, W = args.batch, args.height, args.width
     impl = lic.CONV_SIMT if args.conv == "simt" else lic.CONV_AUTO
     Wt = synth.make_weights(lic.HYPERPRIOR, N_CH, M_CH)
-    codec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, conv_impl=impl)
+    prec = {"fp32": lic.FP32, "bf16": lic.BF16, "fp8": lic.FP8}[args.precision]
+    codec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, conv_impl=impl, precision=prec)
     frames_np = synth.make_frames(B, H, W, first=8 * rank)
     frames = torch.from_numpy(frames_np).cuda()
     out = torch.empty_like(frames)
@@ -368,7 +371,7 @@ def main():
         # pipelined through the serving API: four lanes (codec + stream), a batch's host copies overlap
         # the other lanes' kernels; at most four batches in flight, each frame's output its own pinned buffer
         depth = 4
-        srv = lic.Server(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=lic.FP32, max_batch=B, lanes=depth,
+        srv = lic.Server(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=prec, max_batch=B, lanes=depth,
                          max_pending=(depth + 1) * B, graphs=True, max_wait_ms=1e6)
         srv.prepare(H, W)
         outs = [torch.empty(hin.shape, dtype=torch.float32).pin_memory() for _ in range(depth + 1)]
@@ -413,10 +416,12 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision], "data": "synthetic",
             "config": {"workload": "hyperprior N=128 M=192, 8 x 1280x720 frames padded to 1280x768, enc+dec",
                        "global_batch": B * ws, "seq_len": None, "parallelism": f"replicas{ws}",
-                       "conv": args.conv, "l2": "512 MB write before every step, outside the timed events"},
+                       "conv": args.conv, "precision": args.precision,
+                       "l2": "512 MB write before every step, outside the timed events"},
             "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
             "enc_fps": B * args.steps / (sum(enc_ms) / 1000), "dec_fps": B * args.steps / (sum(dec_ms) / 1000),
             "bits_per_pixel": 8.0 * statistics.mean(frame_bytes) / (H * W),
@@ -723,6 +728,12 @@ def roofline(rep, peaks):
         note = ("FP32-accurate 3xTF32 on tcgen05: algorithmic FP32 flops over the TF32 peak (measured BF16 "
                 "x 1.1/2.25); three TF32 MMAs per product bound the algorithmic rate at a third of it")
         extra = {"ceiling_3xtf32": peak / 3, "frac_of_3xtf32_ceiling": ach / (peak / 3)}
+    elif name.endswith((":bf16", ":e4m3")):
+        # BF16: the measured dense BF16 peak; e4m3: that x the nominal FP8/BF16 ratio (4.5/2.25)
+        peak = bf16 * (2.0 if name.endswith(":e4m3") else 1.0)
+        ach = top["flop"] / top["launches"] / (per_ms * 1e-3) / 1e12
+        bound, unit = "tensor", "TFLOP/s"
+        note = "low-precision tcgen05 MMA with FP32 accumulation; algorithmic flops over the dense peak of its type"
     elif top["flop"] > 0:
         # FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock
         peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
