@@ -648,7 +648,7 @@ int ensure_workspace(lic_codec *cd, int B, int Hp, int Wp) {
     const int N = cd->N, M = cd->M;
     const int64_t Hy = Hp / 16, Wy = Wp / 16, Hz = Hp / 64, Wz = Wp / 64;
     const int64_t big = (int64_t)B * (Hp / 2) * (Wp / 2) * N;
-    LIC_CUDA_TRY(ensure_n<float>(cd->xin, (int64_t)B * Hp * Wp * 3));
+    if (!cd->use_patch) LIC_CUDA_TRY(ensure_n<float>(cd->xin, (int64_t)B * Hp * Wp * 3));   // else unused
     if (cd->use_patch) LIC_CUDA_TRY(ensure_n<float>(cd->patches, (int64_t)B * (Hp / 2) * (Wp / 2) * PATCH_K));
     LIC_CUDA_TRY(ensure_n<float>(cd->act0, big));
     LIC_CUDA_TRY(ensure_n<float>(cd->act1, big));
@@ -687,20 +687,25 @@ cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
 
 // ---- the transforms ----
 
-// g_a: x (NHWC, xin) -> y (NHWC); 4 x conv5x5/2 with GDN after the first three
-void analysis(lic_codec *cd, int B, int Hp, int Wp, cudaStream_t st) {
+// g_a: frames (device [B][3][Hf][Wf], replicate-padded to Hp x Wp) -> y (NHWC);
+// 4 x conv5x5/2 with GDN after the first three
+void analysis(lic_codec *cd, const float *frames, int B, int Hf, int Wf, int Hp, int Wp, cudaStream_t st) {
     float *a = cd->act0.as<float>(), *b = cd->act1.as<float>();
     int H = Hp, W = Wp;
     const float *in = cd->xin.as<float>();
     int first = 0;
     if (cd->use_patch) {
+        // the first layer's patches straight from the frames (no padded copy)
         const double rows = (double)B * (Hp / 2) * (Wp / 2);
-        timed(cd, "patch_pack", 0, 12.0 * B * Hp * Wp + 4.0 * rows * PATCH_K, 1, st,
-              [&] { launch_patch_pack(cd->xin.as<float>(), B, Hp, Wp, cd->patches.as<float>(), st); });
+        timed(cd, "patch_pack", 0, 12.0 * B * Hf * Wf + 4.0 * rows * PATCH_K, 1, st,
+              [&] { launch_frame_patch(frames, B, Hf, Wf, Hp, Wp, cd->patches.as<float>(), st); });
         in = run_layer_gdn(cd, cd->ga0p, cd->gdn[0], cd->patches.as<float>(), B, Hp / 2, Wp / 2, a, b, st);
         H /= 2;
         W /= 2;
         first = 1;
+    } else {
+        timed(cd, "pad_pack", 0, 12.0 * B * ((double)Hf * Wf + (double)Hp * Wp), 1, st,
+              [&] { launch_pad_pack(frames, B, Hf, Wf, Hp, Wp, cd->xin.as<float>(), st); });
     }
     for (int i = first; i < 3; ++i) {
         in = run_layer_gdn(cd, cd->ga[i], cd->gdn[i], in, B, H, W, a, b, st);
@@ -1156,10 +1161,7 @@ int lic_encode(lic_codec *cd, const float *frames, int B, int H, int W, lic_bits
     if (rc) return rc;
     const void *src;
     if ((rc = copy_in(cd, cd->stage_in, frames, (size_t)B * 3 * H * W * sizeof(float), &src, st))) return rc;
-    timed(cd, "pad_pack", 0, 12.0 * B * ((double)H * W + (double)Hp * Wp), 1, st, [&] {
-        launch_pad_pack(static_cast<const float *>(src), B, H, W, Hp, Wp, cd->xin.as<float>(), st);
-    });
-    analysis(cd, B, Hp, Wp, st);
+    analysis(cd, static_cast<const float *>(src), B, H, W, Hp, Wp, st);
     const int Hy = Hp / 16, Wy = Wp / 16;
     StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows);
     if (cd->kind == LIC_HYPERPRIOR) {
@@ -1353,10 +1355,7 @@ int lic_analysis(lic_codec *cd, const float *frames, int B, int H, int W, float 
     if (rc) return rc;
     const void *src;
     if ((rc = copy_in(cd, cd->stage_in, frames, (size_t)B * 3 * H * W * sizeof(float), &src, st))) return rc;
-    timed(cd, "pad_pack", 0, 12.0 * B * ((double)H * W + (double)Hp * Wp), 1, st, [&] {
-        launch_pad_pack(static_cast<const float *>(src), B, H, W, Hp, Wp, cd->xin.as<float>(), st);
-    });
-    analysis(cd, B, Hp, Wp, st);
+    analysis(cd, static_cast<const float *>(src), B, H, W, Hp, Wp, st);
     return emit_nchw(cd, cd->y.as<float>(), B, Hp / 16, Wp / 16, cd->M, y, st);
 }
 

@@ -33,25 +33,38 @@ __global__ void pad_pack_kernel(const float *__restrict__ f, int B, int H, int W
     }
 }
 
-// Patches of a 5x5 / stride-2 convolution of a 3-channel NHWC image:
+// Patches of a 5x5 / stride-2 convolution of a 3-channel Hp x Wp image:
 // row (b, i, j) of the output holds, at K index k = (5u + v) * 3 + c, the
 // input value x[b][2i + u - 2][2j + v - 2][c] (0 outside the image), and 0
 // for k >= 75.  A block makes PP_COLS consecutive rows of one output image
 // row: it stages the 5 input rows they read (zero-filled outside the
 // image) in shared memory, then writes the rows as contiguous float4s.
+// PLANAR: x is the caller's frames [B][3][H][W], replicate-padded to Hp x Wp
+// on the fly (the padded value at (y, x) is frame[min(y, H-1)][min(x, W-1)]);
+// otherwise x is the padded NHWC image [B][Hp][Wp][3].
 constexpr int PP_COLS = 64, PP_T = 240;   // 10 rows x 24 float4 columns per pass
 constexpr int PP_IN_COLS = 2 * PP_COLS + 3;   // input columns 2 j0 - 2 .. 2 j0 + 2 PP_COLS
 
-__global__ void __launch_bounds__(PP_T) patch_pack_kernel(const float *__restrict__ x, int Hp, int Wp,
+template <bool PLANAR>
+__global__ void __launch_bounds__(PP_T) patch_pack_kernel(const float *__restrict__ x, int H, int W, int Hp, int Wp,
                                                           float *__restrict__ out) {
     __shared__ float tile[5][PP_IN_COLS * 3];
     const int Ho = Hp / 2, Wo = Wp / 2;
     const int j0 = blockIdx.x * PP_COLS, i = blockIdx.y, b = blockIdx.z;
     for (int e = threadIdx.x; e < 5 * PP_IN_COLS * 3; e += PP_T) {
-        const int r = e / (PP_IN_COLS * 3), rem = e % (PP_IN_COLS * 3);
-        const int y = 2 * i - 2 + r, xx = 2 * j0 - 2 + rem / 3;
-        tile[r][rem] = (y >= 0 && y < Hp && xx >= 0 && xx < Wp) ? x[(((int64_t)b * Hp + y) * Wp + xx) * 3 + rem % 3]
-                                                                 : 0.f;
+        if (PLANAR) {   // consecutive threads read consecutive columns of one plane
+            const int r = e / (PP_IN_COLS * 3), c = (e / PP_IN_COLS) % 3, col = e % PP_IN_COLS;
+            const int y = 2 * i - 2 + r, xx = 2 * j0 - 2 + col;
+            tile[r][col * 3 + c] = (y >= 0 && y < Hp && xx >= 0 && xx < Wp)
+                                       ? x[(((int64_t)b * 3 + c) * H + min(y, H - 1)) * W + min(xx, W - 1)]
+                                       : 0.f;
+        } else {
+            const int r = e / (PP_IN_COLS * 3), rem = e % (PP_IN_COLS * 3);
+            const int y = 2 * i - 2 + r, xx = 2 * j0 - 2 + rem / 3;
+            tile[r][rem] = (y >= 0 && y < Hp && xx >= 0 && xx < Wp)
+                               ? x[(((int64_t)b * Hp + y) * Wp + xx) * 3 + rem % 3]
+                               : 0.f;
+        }
     }
     __syncthreads();
     const int cols = min(PP_COLS, Wo - j0);
@@ -240,7 +253,12 @@ void launch_pad_pack(const float *frames, int B, int H, int W, int Hp, int Wp, f
 
 void launch_patch_pack(const float *x, int B, int Hp, int Wp, float *out, cudaStream_t st) {
     const dim3 grid((unsigned)((Wp / 2 + PP_COLS - 1) / PP_COLS), (unsigned)(Hp / 2), (unsigned)B);
-    patch_pack_kernel<<<grid, PP_T, 0, st>>>(x, Hp, Wp, out);
+    patch_pack_kernel<false><<<grid, PP_T, 0, st>>>(x, Hp, Wp, Hp, Wp, out);
+}
+
+void launch_frame_patch(const float *frames, int B, int H, int W, int Hp, int Wp, float *out, cudaStream_t st) {
+    const dim3 grid((unsigned)((Wp / 2 + PP_COLS - 1) / PP_COLS), (unsigned)(Hp / 2), (unsigned)B);
+    patch_pack_kernel<true><<<grid, PP_T, 0, st>>>(frames, H, W, Hp, Wp, out);
 }
 
 void launch_crop_unpack(const float *x, int B, int Hp, int Wp, int H, int W, float *frames, cudaStream_t st) {

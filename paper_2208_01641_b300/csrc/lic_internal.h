@@ -318,6 +318,9 @@ void launch_to_bf16(const float *in, int64_t n, void *out, cudaStream_t st);
 // (5u + v) * 3 + c, zero-padded from 75 to PATCH_K.
 constexpr int PATCH_K = 96;
 void launch_patch_pack(const float *x, int B, int Hp, int Wp, float *out, cudaStream_t st);
+// The same patches straight from the caller's frames [B][3][H][W] (device),
+// replicate-padded to Hp x Wp on the fly (as launch_pad_pack pads).
+void launch_frame_patch(const float *frames, int B, int H, int W, int Hp, int Wp, float *out, cudaStream_t st);
 // Copies the 64 scales into the constant bank of the current device (once
 // per device, at codec creation).
 cudaError_t upload_scale_table();

@@ -105,6 +105,27 @@ def test_hyper_transforms_match_oracle(codecs, weights, impl):
     assert np.array_equal(idx.cpu().numpy(), O.scale_index(s_gpu))
 
 
+def test_batch_does_not_change_a_frames_arithmetic(codecs):
+    """A frame coded in a batch of three and coded alone gives the same
+    bitstream and the same reconstruction, bit for bit.  At N = 128 the
+    hyper transforms' small grids are cut into K slices whose count depends
+    on the layer and the frame size only; this pins that."""
+    c = codecs[(1, lic.CONV_AUTO)]
+    x = synth.make_frames(3, 128, 192, first=60)
+    bs = c.encode(dev(x))
+    out3 = torch.empty(3, 3, 128, 192, device="cuda")
+    c.decode(bs, 128, 192, out3)
+    assert c.sync_status() == lic.OK
+    b3 = bs.to_bytes()
+    for i in range(3):
+        bi = c.encode(dev(x[i:i + 1]))
+        out1 = torch.empty(1, 3, 128, 192, device="cuda")
+        c.decode(bi, 128, 192, out1)
+        assert c.sync_status() == lic.OK
+        assert bi.to_bytes()[0] == b3[i], i
+        assert torch.equal(out1[0], out3[i]), i
+
+
 # --------------------------------------------------- integer stages, strict
 
 def encode_and_read(c, x):
