@@ -2437,6 +2437,8 @@ int split_k(const ConvDesc &d, const TcWeights &w) {
     q = std::min<int64_t>(q, nk / 6);
     q = std::min<int64_t>(q, 8);
     q = std::min<int64_t>(q, d.part_frame_floats / (tpf * BLOCK_M * 128));
+    // partial-sum rows are 32-bit TMA coordinates (2^31 rows would be a terabyte of scratch)
+    if (q > 1 && q * tpf * d.B * BLOCK_M >= ((int64_t)1 << 31)) return 1;
     return (int)std::max<int64_t>(q, 1);
 }
 

@@ -179,14 +179,16 @@ struct QuantF {
 
 __global__ void quantize_kernel(QuantF fn, int B) { tile_nhwc_to_nchw(B, fn.P, fn.C, fn); }
 
-__device__ __forceinline__ uint8_t index_one(float sg) {
+// tab: the 64 scales, in shared memory (the threads of a warp probe different
+// entries; constant memory would serialise those reads)
+__device__ __forceinline__ uint8_t index_one(float sg, const float *tab) {
     if (sg != sg) return 63;
-    sg = fmaxf(sg, c_scales[0]);
+    sg = fmaxf(sg, tab[0]);
     // smallest k with scales[k] >= sg (scales increasing), else 63
     int lo = 0, hi = 63;
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        if (c_scales[mid] >= sg) hi = mid; else lo = mid + 1;
+        if (tab[mid] >= sg) hi = mid; else lo = mid + 1;
     }
     return (uint8_t)lo;
 }
@@ -196,17 +198,25 @@ struct IndexF {
     uint8_t *idx;
     float *sig_nchw;
     int P, C;
+    const float *tab;   // shared-memory copy of the scales
     __device__ void load(int b, int p, int c, bool ok, float &v) const {
         v = ok ? sigma[((int64_t)b * P + p) * C + c] : 0.f;
     }
     __device__ void store(int b, int p, int c, float v) const {
         int64_t o = ((int64_t)b * C + c) * P + p;
-        idx[o] = index_one(v);
+        idx[o] = index_one(v, tab);
         if (sig_nchw) sig_nchw[o] = v;
     }
 };
 
-__global__ void index_kernel(IndexF fn, int B) { tile_nhwc_to_nchw(B, fn.P, fn.C, fn); }
+__global__ void index_kernel(IndexF fn, int B) {
+    __shared__ float tab[64];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if (t < 64) tab[t] = c_scales[t];
+    __syncthreads();
+    fn.tab = tab;
+    tile_nhwc_to_nchw(B, fn.P, fn.C, fn);
+}
 
 int grid_for(int64_t n) {
     int64_t g = (n + 255) / 256;
@@ -282,7 +292,7 @@ void launch_quantize(const float *y, int B, int HW, int C, const float *mu, int3
 
 void launch_scale_index(const float *sigma, int B, int HW, int C, uint8_t *idx, float *sigma_nchw,
                         cudaStream_t st) {
-    IndexF fn{sigma, idx, sigma_nchw, HW, C};
+    IndexF fn{sigma, idx, sigma_nchw, HW, C, nullptr};
     index_kernel<<<tile_grid(B, HW, C), dim3(32, 8), 0, st>>>(fn, B);
 }
 
