@@ -369,9 +369,10 @@ def main():
                 codec.decode(bs2, H, W, hout, stream=sid)
             codec.sync(sid)
             serial_fps = ws * B * args.steps / (time.perf_counter() - t0)
-        # pipelined through the serving API: four lanes (codec + stream), a batch's host copies overlap
-        # the other lanes' kernels; at most four batches in flight, each frame's output its own pinned buffer
-        depth = 4
+        # pipelined through the serving API: eight lanes (codec + stream, the server's maximum), a
+        # batch's host copies and latency-bound stages overlap the other lanes' kernels; at most eight
+        # batches in flight, each frame's output its own pinned buffer
+        depth = 8
         srv = lic.Server(lic.HYPERPRIOR, N_CH, M_CH, Wt, precision=prec, max_batch=B, lanes=depth,
                          max_pending=(depth + 1) * B, graphs=True, max_wait_ms=1e6)
         srv.prepare(H, W)
@@ -399,7 +400,7 @@ def main():
                "d2h_bytes_per_step": nbytes, "serial_value": serial_fps, "graph_replays": est["graph_replays"],
                "batches": n_e2e,
                "note": f"pinned host frames in, decoded frames out to pinned host memory, through the serving "
-                       f"API ({args.precision.upper()} codec, 4 lanes, batches of {B}, at most 4 in flight, "
+                       f"API ({args.precision.upper()} codec, {depth} lanes, batches of {B}, at most {depth} in flight, "
                        f"{n_e2e} batches timed from the first submit to the last result); serial_value: one "
                        f"codec on one stream, copies not overlapped"}
 
