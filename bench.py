@@ -269,7 +269,12 @@ def main():
     except Exception:
         pass
     roof = roofline(rep, peaks)
-    chain = chain_roofline(rep, peaks, total_ms / args.steps, steps=3)
+    # the I/O floor, as context: per frame the frame in and out, the bitstream out (encoder) and
+    # in (decoder), and the latents y and z written once and read once, all float32
+    Hp, Wp = -(-H // 64) * 64, -(-W // 64) * 64
+    lat = M_CH * (Hp // 16) * (Wp // 16) + N_CH * (Hp // 64) * (Wp // 64)
+    floor_bytes = sum(2 * 12.0 * H * W + 2.0 * fb + 2 * 4.0 * lat for fb in frame_bytes)
+    chain = chain_roofline(rep, peaks, total_ms / args.steps, steps=3, floor_bytes=floor_bytes)
 
     # ---- the BF16 precision form, same workload ----
     forms = {}
@@ -758,7 +763,7 @@ def roofline(rep, peaks):
     return out
 
 
-def chain_roofline(rep, peaks, measured_ms, steps):
+def chain_roofline(rep, peaks, measured_ms, steps, floor_bytes=None):
     """The whole step against its roofline: T_roof = sum over launches of
     max(algorithmic FLOP / the launch's peak, algorithmic bytes / HBM), per
     step (rep covers `steps` steps, timed launch by launch); frac = T_roof /
@@ -783,6 +788,7 @@ def chain_roofline(rep, peaks, measured_ms, steps):
     t_roof_ms = t_roof * 1e3 / steps
     return {"t_roof_ms": t_roof_ms, "t_measured_ms": measured_ms, "frac": t_roof_ms / measured_ms,
             "t_compute_ms": t_flop * 1e3 / steps, "t_hbm_ms": t_mem * 1e3 / steps,
+            "t_io_floor_ms": None if floor_bytes is None else floor_bytes / hbm * 1e3,
             "note": "sum over the step's launches of max(FLOP / peak of the launch's arithmetic, bytes / "
                     "measured HBM); algorithmic FLOP and bytes as the library counts them; FP32 convs "
                     "against the 3xTF32 ceiling (a third of the TF32 peak)",

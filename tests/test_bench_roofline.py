@@ -49,6 +49,10 @@ def test_chain_roofline():
     # (the layout kernel's FLOP time counts against the CUDA-core peak and is zero)
     assert c["t_compute_ms"] == pytest.approx((t_conv1 + 1.0) / 3)
     assert c["t_hbm_ms"] == pytest.approx((0.2 + 1.0 + 0.1) / 3)
+    assert c["t_io_floor_ms"] is None
+    # the I/O floor: bytes of one step over the measured HBM bandwidth
+    c = bench.chain_roofline(REP, PEAKS, measured_ms=10.0, steps=3, floor_bytes=6e9)
+    assert c["t_io_floor_ms"] == pytest.approx(1.0)
 
 
 def test_e4m3_peak_is_twice_bf16():
