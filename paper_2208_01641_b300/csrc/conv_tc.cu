@@ -289,6 +289,56 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 columns at each of two TMEM addresses of this thread's lane, one wait for both
+__device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float *va, float *vb) {
+    uint32_t r[32], q[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+          "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15]),
+          "=r"(q[16]), "=r"(q[17]), "=r"(q[18]), "=r"(q[19]), "=r"(q[20]), "=r"(q[21]), "=r"(q[22]), "=r"(q[23]),
+          "=r"(q[24]), "=r"(q[25]), "=r"(q[26]), "=r"(q[27]), "=r"(q[28]), "=r"(q[29]), "=r"(q[30]), "=r"(q[31])
+        : "r"(tb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        va[i] = __uint_as_float(r[i]);
+        vb[i] = __uint_as_float(q[i]);
+    }
+}
+
+// 16 columns at each of two TMEM addresses of this thread's lane, one wait for both
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float *va, float *vb) {
+    uint32_t r[16], q[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+          "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+        : "r"(tb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        va[i] = __uint_as_float(r[i]);
+        vb[i] = __uint_as_float(q[i]);
+    }
+}
+
 // 16 consecutive 32-bit TMEM columns of this thread's lane
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     uint32_t r[16];
@@ -702,12 +752,21 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 return;
             }
             tc_fence_after();
+            if constexpr (HALF == 2) {   // both 32-column slices in one TMEM round trip
+                float v[32], w[32];
+                tmem_ld32x2(lane_base + (uint32_t)((g & 1) * COUT), lane_base + (uint32_t)((g & 1) * COUT + 32), v, w);
 #pragma unroll
-            for (int h = 0; h < HALF; ++h) {
-                float v[32];
-                tmem_ld32(lane_base + (uint32_t)((g & 1) * COUT + h * 32), v);
+                for (int i = 0; i < 32; ++i) master[i] += v[i];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) master[h * 32 + i] += v[i];
+                for (int i = 0; i < 32; ++i) master[32 + i] += w[i];
+            } else {   // (three slices: one at a time, the registers are short)
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    float v[32];
+                    tmem_ld32(lane_base + (uint32_t)((g & 1) * COUT + h * 32), v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += v[i];
+                }
             }
             tc_fence_before();
             mbar_arrive(&pempty[g & 1]);
@@ -1274,14 +1333,13 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                 tc_fence_after();
                 const uint32_t base = tmem + lane_off + (g & 1) * 2 * COUT + cbase;
 #pragma unroll
-                for (int h = 0; h < HALF; ++h) {
-                    float x[32];
-                    tmem_ld32(base + 32 * h, x);
+                for (int h = 0; h < HALF; ++h) {   // both halves of the partial, one TMEM round trip
+                    float x[32], xl[32];
+                    tmem_ld32x2(base + 32 * h, base + COUT + 32 * h, x, xl);
 #pragma unroll
                     for (int i = 0; i < 32; ++i) master[h * 32 + i] += x[i];
-                    tmem_ld32(base + COUT + 32 * h, x);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += x[i];
+                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += xl[i];
                 }
                 tc_fence_before();
                 mbar_arrive(&pempty[g & 1]);
@@ -1334,8 +1392,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
 #pragma unroll
                 for (int h = 0; h < 2 * HALF; ++h) {
                     float n[16], nl[16];
-                    tmem_ld16(base + 16 * h, n);
-                    tmem_ld16(base + COUT + 16 * h, nl);
+                    tmem_ld16x2(base + 16 * h, base + COUT + 16 * h, n, nl);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) n[i] += nl[i];
                     if (p.fuse_gdn == 1) norm_n<16, false>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
@@ -1669,12 +1726,21 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lp_kernel(const __gr
                 break;
             }
             tc_fence_after();
+            if constexpr (HALF == 2) {   // both 32-column slices in one TMEM round trip
+                float v[32], w[32];
+                tmem_ld32x2(lane_base + (uint32_t)((g & 1) * COUT), lane_base + (uint32_t)((g & 1) * COUT + 32), v, w);
 #pragma unroll
-            for (int h = 0; h < HALF; ++h) {
-                float v[32];
-                tmem_ld32(lane_base + (uint32_t)((g & 1) * COUT + h * 32), v);
+                for (int i = 0; i < 32; ++i) master[i] += v[i];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) master[h * 32 + i] += v[i];
+                for (int i = 0; i < 32; ++i) master[32 + i] += w[i];
+            } else {   // (three slices: one at a time, the registers are short)
+#pragma unroll
+                for (int h = 0; h < HALF; ++h) {
+                    float v[32];
+                    tmem_ld32(lane_base + (uint32_t)((g & 1) * COUT + h * 32), v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += v[i];
+                }
             }
             tc_fence_before();
             mbar_arrive(&pempty[g & 1]);
@@ -2085,12 +2151,14 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lpx_kernel(const __g
                 }
                 tc_fence_after();
                 const uint32_t base = tmem + lane_off + (g & 1) * COUT + cbase;
+                static_assert(HALF == 2, "one TMEM round trip per partial");
+                {
+                    float x[32], w[32];
+                    tmem_ld32x2(base, base + 32, x, w);
 #pragma unroll
-                for (int h = 0; h < HALF; ++h) {
-                    float x[32];
-                    tmem_ld32(base + 32 * h, x);
+                    for (int i = 0; i < 32; ++i) master[i] += x[i];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) master[h * 32 + i] += x[i];
+                    for (int i = 0; i < 32; ++i) master[32 + i] += w[i];
                 }
                 tc_fence_before();
                 mbar_arrive(&pempty[g & 1]);
