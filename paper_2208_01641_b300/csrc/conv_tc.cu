@@ -2214,11 +2214,16 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_lpx_kernel(const __g
                 tc_fence_after();
                 const uint32_t base = tmem + lane_off + (g & 1) * COUT + cbase;
 #pragma unroll
-                for (int h = 0; h < 2 * HALF; ++h) {
-                    float n[16];
-                    tmem_ld16(base + 16 * h, n);
-                    if (p.fuse_gdn == 1) norm_n<16, false>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
-                    else norm_n<16, true>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
+                for (int h = 0; h < 2 * HALF; h += 2) {   // two 16-column slices per TMEM round trip
+                    float n[16], n2[16];
+                    tmem_ld16x2(base + 16 * h, base + 16 * (h + 1), n, n2);
+                    if (p.fuse_gdn == 1) {
+                        norm_n<16, false>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
+                        norm_n<16, false>(master + (h + 1) * 16, n2, p.gdn_beta + cbase + (h + 1) * 16);
+                    } else {
+                        norm_n<16, true>(master + h * 16, n, p.gdn_beta + cbase + h * 16);
+                        norm_n<16, true>(master + (h + 1) * 16, n2, p.gdn_beta + cbase + (h + 1) * 16);
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive(&pempty[g & 1]);
