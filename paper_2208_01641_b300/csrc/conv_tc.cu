@@ -1048,7 +1048,12 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
 //     64 channels;
 //   * registers move from the producer / MMA / split warpgroups (72 a
 //     thread) to the epilogue warpgroups (184) with setmaxnreg; the shares
-//     add up to the 64 K registers the block is launched with.
+//     add up to the 64 K registers the block is launched with;
+//   * the fold reads a partial's two halves with one TMEM round trip (the
+//     tile's last fold is on the tensor pipe's critical path);
+//   * split K (ksplit > 1, launches without a fused norm): the work units are
+//     (tile, K slice) pairs; a slice stores its folded partial sums raw and
+//     tcx_splitk_sum_kernel adds the slices, the bias and ReLU.
 //   warp 0       TMA producer            warp 1      TMEM allocation, MMA issue
 //   warps 2..7   split A                 warps 8..15 fold, bias / norm, output
 //                                                    (TMEM lanes 32 (warp % 4) ..)
