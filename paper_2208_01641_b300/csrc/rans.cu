@@ -402,11 +402,20 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) rans_decode_kernel(const Strea
         } else {
             // an escape's nibbles sit between its own word and the next lane's:
             // lanes between two escapes read their words in parallel (rank
-            // among the renormalising lanes of the segment), each escape lane
-            // then decodes its nibbles alone and hands on the position
+            // among the renormalising lanes of the segment).  The nibbles are
+            // uniform 4-bit symbols, and decoding one leaves the renormalisation
+            // test (state < 2^16) to the state's high half h alone: h >> 4 without
+            // a renormalisation; after one, the next three steps cannot
+            // renormalise and the fourth sees the same h.  So the words an escape
+            // consumes follow from its state when it starts (its count nibble
+            // gives the number of steps): the walk over the escapes only adds
+            // those counts, and the escape lanes then decode their nibbles at
+            // once, each checking the count it predicted.
             const unsigned m_need = __ballot_sync(FULL, need);
             unsigned m_esc = __ballot_sync(FULL, is_esc);
             int first = 0;
+            int64_t epos = 0;   // escape lanes: the first word of their nibbles
+            int ewords = 0;     // escape lanes: the words their nibbles consume
             for (;;) {
                 const int e = m_esc ? __ffs(m_esc) - 1 : 31;
                 const unsigned seg = (e == 31 ? FULL : ((2u << e) - 1u)) & ~((1u << first) - 1u);
@@ -417,32 +426,47 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) rans_decode_kernel(const Strea
                 }
                 pos += __popc(seg_need);
                 if (!m_esc) break;
-                if (lane == e && !corrupt) {
-                    uint32_t v = 0, nn = 0;
-                    for (int j = -1; j < (int)nn && !corrupt; ++j) {
-                        uint32_t slot = x & 0xffffu;
-                        uint32_t nib = slot >> 12;
-                        x = 4096u * (x >> 16) + slot - 4096u * nib;
-                        if (x < RANS_L) {
-                            if (pos < nw) x = (x << 16) | words[pos]; else corrupt = true;
-                            ++pos;
-                        }
-                        if (j < 0) {
-                            nn = nib + 1;
-                            if (nn > 8) corrupt = true;
-                        } else {
-                            v |= nib << (4 * j);
-                        }
-                    }
-                    int64_t r = (v & 1u) ? -(int64_t)lo - 1 - (int64_t)(v >> 1)
-                                         : (int64_t)(nt - 2 - lo) + 1 + (int64_t)(v >> 1);
-                    if (r > 1073741824LL || r < -1073741824LL) corrupt = true;
-                    val = (int32_t)r;
+                int w = 0;
+                if (lane == e) {
+                    epos = pos;
+                    // steps: the count nibble, then count + 1 nibbles; the first
+                    // renormalisation comes after j0 shifts of h by 4 bits (h < 2^16),
+                    // then every fourth step
+                    const int steps = (int)((x & 0xffffu) >> 12) + 2;
+                    const uint32_t h = x >> 16;
+                    const int j0 = (h >= 16u) + (h >= 256u) + (h >= 4096u);
+                    w = steps > j0 ? (steps - 1 - j0) / 4 + 1 : 0;
+                    ewords = w;
                 }
-                pos = __shfl_sync(FULL, pos, e);
+                pos += __shfl_sync(FULL, w, e);
                 m_esc &= m_esc - 1u;
                 first = e + 1;
                 if (first == 32) break;
+            }
+            if (is_esc && !corrupt) {
+                int64_t p = epos;
+                uint32_t v = 0, nn = 0;
+                for (int j = -1; j < (int)nn && !corrupt; ++j) {
+                    uint32_t slot = x & 0xffffu;
+                    uint32_t nib = slot >> 12;
+                    x = 4096u * (x >> 16) + slot - 4096u * nib;
+                    if (x < RANS_L) {
+                        if (p < nw) x = (x << 16) | words[p]; else corrupt = true;
+                        ++p;
+                    }
+                    if (j < 0) {
+                        nn = nib + 1;
+                        if (nn > 8) corrupt = true;
+                    } else {
+                        v |= nib << (4 * j);
+                    }
+                }
+                // a state below 2^16 here (no stream this coder wrote) breaks the count
+                if (p - epos != ewords) corrupt = true;
+                int64_t r = (v & 1u) ? -(int64_t)lo - 1 - (int64_t)(v >> 1)
+                                     : (int64_t)(nt - 2 - lo) + 1 + (int64_t)(v >> 1);
+                if (r > 1073741824LL || r < -1073741824LL) corrupt = true;
+                val = (int32_t)r;
             }
         }
         if (__any_sync(FULL, corrupt)) {
