@@ -290,6 +290,10 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) rans_decode_kernel(const Strea
     __shared__ int32_t s_glo[NGAUSS], s_gnt[NGAUSS];
     __shared__ int64_t s_gstart[NGAUSS];
     __shared__ uint16_t s_wlut[DEC_WARPS][LUT_N];
+    // escape walk of a group: the lanes' states in, each escape's nibble words
+    // before it (ew) and its own count (ec) out
+    __shared__ uint32_t s_ex[DEC_WARPS][32];
+    __shared__ int32_t s_ew[DEC_WARPS][32], s_ec[DEC_WARPS][32], s_wt[DEC_WARPS];
     const bool gauss = part == 1 && g.kind == LIC_HYPERPRIOR && t.gauss_base >= 0;
     if (gauss) {
         for (int e = threadIdx.x; e < NGAUSS * LUT_N; e += blockDim.x)
@@ -412,37 +416,56 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) rans_decode_kernel(const Strea
             // those counts, and the escape lanes then decode their nibbles at
             // once, each checking the count it predicted.
             const unsigned m_need = __ballot_sync(FULL, need);
-            unsigned m_esc = __ballot_sync(FULL, is_esc);
-            int first = 0;
-            int64_t epos = 0;   // escape lanes: the first word of their nibbles
-            int ewords = 0;     // escape lanes: the words their nibbles consume
-            for (;;) {
-                const int e = m_esc ? __ffs(m_esc) - 1 : 31;
-                const unsigned seg = (e == 31 ? FULL : ((2u << e) - 1u)) & ~((1u << first) - 1u);
-                const unsigned seg_need = m_need & seg;
-                if (need && ((seg >> lane) & 1u)) {
-                    const int64_t p = pos + __popc(seg_need & ((1u << lane) - 1u));
-                    if (p < nw) x = (x << 16) | words[p]; else corrupt = true;
-                }
-                pos += __popc(seg_need);
-                if (!m_esc) break;
-                int w = 0;
-                if (lane == e) {
-                    epos = pos;
-                    // steps: the count nibble, then count + 1 nibbles; the first
-                    // renormalisation comes after j0 shifts of h by 4 bits (h < 2^16),
-                    // then every fourth step
-                    const int steps = (int)((x & 0xffffu) >> 12) + 2;
-                    const uint32_t h = x >> 16;
+            const unsigned m_esc = __ballot_sync(FULL, is_esc);
+            // one lane walks the escapes in order: lane e's symbol word sits after the
+            // renormalising lanes below it and the nibble words of the escapes below it
+            s_ex[wib][lane] = x;
+            __syncwarp();
+            if (lane == 0) {
+                int32_t W = 0;
+                for (unsigned m = m_esc; m; m &= m - 1u) {
+                    const int e = __ffs(m) - 1;
+                    const uint32_t xe = s_ex[wib][e];
+                    uint32_t h, low;
+                    if ((m_need >> e) & 1u) {   // its word becomes the state's low half
+                        const int64_t P = pos + __popc(m_need & ((1u << e) - 1u)) + W;
+                        low = P < nw ? words[P] : 0u;
+                        if (P >= nw) corrupt = true;
+                        h = xe;
+                    } else {
+                        low = xe & 0xffffu;
+                        h = xe >> 16;
+                    }
+                    const int steps = (int)(low >> 12) + 2;
                     const int j0 = (h >= 16u) + (h >= 256u) + (h >= 4096u);
-                    w = steps > j0 ? (steps - 1 - j0) / 4 + 1 : 0;
-                    ewords = w;
+                    const int w = steps > j0 ? (steps - 1 - j0) / 4 + 1 : 0;
+                    s_ew[wib][e] = W;
+                    s_ec[wib][e] = w;
+                    W += w;
                 }
-                pos += __shfl_sync(FULL, w, e);
-                m_esc &= m_esc - 1u;
-                first = e + 1;
-                if (first == 32) break;
+                s_wt[wib] = W;   // the group's nibble words in all
             }
+            __syncwarp();
+            // this lane's nibble words before it: the walk's running total at the
+            // last escape below it (for an escape lane, before its own)
+            int32_t wb = 0;
+            if (is_esc) {
+                wb = s_ew[wib][lane];
+            } else {
+                const unsigned below = m_esc & ((1u << lane) - 1u);
+                if (below) {
+                    const int k = 31 - __clz(below);
+                    wb = s_ew[wib][k] + s_ec[wib][k];
+                }
+            }
+            const int64_t psym = pos + __popc(m_need & ((1u << lane) - 1u)) + wb;
+            if (need) {
+                if (psym < nw) x = (x << 16) | words[psym]; else corrupt = true;
+            }
+            const int64_t epos = psym + (need ? 1 : 0);   // escape lanes: their nibbles' first word
+            const int ewords = is_esc ? s_ec[wib][lane] : 0;
+            pos += __popc(m_need) + s_wt[wib];
+            __syncwarp();   // s_ex / s_ew / s_ec / s_wt are rewritten by the next group
             if (is_esc && !corrupt) {
                 int64_t p = epos;
                 uint32_t v = 0, nn = 0;
