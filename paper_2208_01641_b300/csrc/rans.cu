@@ -290,10 +290,8 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) rans_decode_kernel(const Strea
     __shared__ int32_t s_glo[NGAUSS], s_gnt[NGAUSS];
     __shared__ int64_t s_gstart[NGAUSS];
     __shared__ uint16_t s_wlut[DEC_WARPS][LUT_N];
-    // escape walk of a group: the lanes' states in, each escape's nibble words
-    // before it (ew) and its own count (ec) out
+    // escape walk of a group: every lane's state after its symbol, read by all lanes
     __shared__ uint32_t s_ex[DEC_WARPS][32];
-    __shared__ int32_t s_ew[DEC_WARPS][32], s_ec[DEC_WARPS][32], s_wt[DEC_WARPS];
     const bool gauss = part == 1 && g.kind == LIC_HYPERPRIOR && t.gauss_base >= 0;
     if (gauss) {
         for (int e = threadIdx.x; e < NGAUSS * LUT_N; e += blockDim.x)
@@ -421,51 +419,41 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) rans_decode_kernel(const Strea
             // renormalising lanes below it and the nibble words of the escapes below it
             s_ex[wib][lane] = x;
             __syncwarp();
-            if (lane == 0) {
-                int32_t W = 0;
-                for (unsigned m = m_esc; m; m &= m - 1u) {
-                    const int e = __ffs(m) - 1;
-                    const uint32_t xe = s_ex[wib][e];
-                    uint32_t h, low;
-                    if ((m_need >> e) & 1u) {   // its word becomes the state's low half
-                        const int64_t P = pos + __popc(m_need & ((1u << e) - 1u)) + W;
-                        low = P < nw ? words[P] : 0u;
-                        if (P >= nw) corrupt = true;
-                        h = xe;
-                    } else {
-                        low = xe & 0xffffu;
-                        h = xe >> 16;
-                    }
-                    const int steps = (int)(low >> 12) + 2;
-                    const int j0 = (h >= 16u) + (h >= 256u) + (h >= 4096u);
-                    const int w = steps > j0 ? (steps - 1 - j0) / 4 + 1 : 0;
-                    s_ew[wib][e] = W;
-                    s_ec[wib][e] = w;
-                    W += w;
+            // every lane runs the same walk (no divergence): escape e's symbol word sits
+            // after the renormalising lanes below it and the nibble words of the escapes
+            // below it; each lane keeps what it needs
+            int32_t W = 0, wb = 0, ewords = 0;
+            for (unsigned m = m_esc; m; m &= m - 1u) {
+                const int e = __ffs(m) - 1;
+                const uint32_t xe = s_ex[wib][e];
+                uint32_t h, low;
+                if ((m_need >> e) & 1u) {   // its word becomes the state's low half
+                    const int64_t P = pos + __popc(m_need & ((1u << e) - 1u)) + W;
+                    low = P < nw ? words[P] : 0u;
+                    if (P >= nw) corrupt = true;
+                    h = xe;
+                } else {
+                    low = xe & 0xffffu;
+                    h = xe >> 16;
                 }
-                s_wt[wib] = W;   // the group's nibble words in all
-            }
-            __syncwarp();
-            // this lane's nibble words before it: the walk's running total at the
-            // last escape below it (for an escape lane, before its own)
-            int32_t wb = 0;
-            if (is_esc) {
-                wb = s_ew[wib][lane];
-            } else {
-                const unsigned below = m_esc & ((1u << lane) - 1u);
-                if (below) {
-                    const int k = 31 - __clz(below);
-                    wb = s_ew[wib][k] + s_ec[wib][k];
+                const int steps = (int)(low >> 12) + 2;
+                const int j0 = (h >= 16u) + (h >= 256u) + (h >= 4096u);
+                const int w = steps > j0 ? (steps - 1 - j0) / 4 + 1 : 0;
+                if (e == lane) {
+                    wb = W;   // an escape lane: the nibble words before its own
+                    ewords = w;
+                } else if (e < lane) {
+                    wb = W + w;   // a lane above escape e
                 }
+                W += w;
             }
             const int64_t psym = pos + __popc(m_need & ((1u << lane) - 1u)) + wb;
             if (need) {
                 if (psym < nw) x = (x << 16) | words[psym]; else corrupt = true;
             }
             const int64_t epos = psym + (need ? 1 : 0);   // escape lanes: their nibbles' first word
-            const int ewords = is_esc ? s_ec[wib][lane] : 0;
-            pos += __popc(m_need) + s_wt[wib];
-            __syncwarp();   // s_ex / s_ew / s_ec / s_wt are rewritten by the next group
+            pos += __popc(m_need) + W;
+            __syncwarp();   // s_ex is rewritten by the next group
             if (is_esc && !corrupt) {
                 int64_t p = epos;
                 uint32_t v = 0, nn = 0;
