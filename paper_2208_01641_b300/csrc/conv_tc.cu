@@ -55,7 +55,7 @@ constexpr int BLOCK_M = 128;
 constexpr int KCH = 32;                          // K chunk: 32 float32 = one 128-byte swizzle row
 constexpr int A_BYTES = BLOCK_M * KCH * 4;       // 16 KB
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
-constexpr int FOLD = 4;                          // K chunks per TMEM partial sum
+constexpr int FOLD = 8;                          // K chunks per TMEM partial sum
 constexpr int EPI_WARPS = 8;
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 
