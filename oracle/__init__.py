@@ -80,6 +80,7 @@ def lib():
         L.orc_eb_logits.restype = ctypes.c_double
         L.orc_eb_table.argtypes = [dp, fp, ctypes.POINTER(ip), ctypes.POINTER(ip),
                                    ctypes.POINTER(ctypes.c_uint32)]
+        L.orc_eb_pmf.argtypes = [dp, fp, ctypes.POINTER(ip), ctypes.POINTER(ip), dp, ip]
         L.orc_quantize_pmf.argtypes = [dp, ip, ctypes.POINTER(ctypes.c_uint32)]
         L.orc_scale_table.argtypes = [fp]
         L.orc_gauss_table.argtypes = [ip, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_uint32)]
@@ -239,6 +240,21 @@ def eb_tables(Wt):
         med[c] = m.value
         tabs.append(Table(lo.value, hi.value, cdf[:lo.value + hi.value + 3].copy()))
     return med, tabs
+
+
+def eb_pmf(Wt, c):
+    """(median float32, lo, hi, pmf float64[lo+hi+2]) of channel c of the
+    entropy bottleneck before frequency quantization (C7): the unit-bin
+    likelihoods of s in [-lo, hi] around the median, then the escape mass."""
+    row = np.ascontiguousarray(eb_pack(Wt)[c])
+    pm = np.zeros(4096, dtype=np.float64)
+    m = ctypes.c_float()
+    lo, hi = ctypes.c_int(), ctypes.c_int()
+    n = lib().orc_eb_pmf(_p(row, ctypes.c_double), ctypes.byref(m), ctypes.byref(lo),
+                         ctypes.byref(hi), _p(pm, ctypes.c_double), 4096)
+    if n < 0:
+        raise ValueError(f"entropy bottleneck channel {c}: support above 4096 symbols")
+    return np.float32(m.value), lo.value, hi.value, pm[:n].copy()
 
 
 def eb_logits(Wt, c, x):

@@ -212,7 +212,7 @@ static double eb_solve(const double *p, double target)
 
 #define TAIL_MASS 1e-9
 
-int orc_eb_table(const double *p, float *median, int *lo, int *hi, uint32_t *cdf)
+int orc_eb_pmf(const double *p, float *median, int *lo, int *hi, double *pm, int cap)
 {
     double tq = log((TAIL_MASS / 2) / (1.0 - TAIL_MASS / 2)); /* logit(tau/2) */
     float med = (float)eb_solve(p, 0.0);
@@ -223,7 +223,7 @@ int orc_eb_table(const double *p, float *median, int *lo, int *hi, uint32_t *cdf
     if (h < 0) h = 0;
     if (l + h + 2 > 4096) return -1;
     int L = (int)l, Hh = (int)h, n = L + Hh + 2;
-    double *pm = (double *)malloc(sizeof(double) * n);
+    if (n > cap) return -1;
     for (int s = -L; s <= Hh; s++) {
         /* likelihood of the unit bin around m+s, with the sign flip that
          * evaluates the difference on the side where the sigmoid is small */
@@ -234,9 +234,16 @@ int orc_eb_table(const double *p, float *median, int *lo, int *hi, uint32_t *cdf
     }
     pm[n - 1] = sigmoid(orc_eb_logits(p, m - L - 0.5))
               + sigmoid(-orc_eb_logits(p, m + Hh + 0.5));
-    int rc = orc_quantize_pmf(pm, n, cdf);
-    free(pm);
     *median = med; *lo = L; *hi = Hh;
+    return n;
+}
+
+int orc_eb_table(const double *p, float *median, int *lo, int *hi, uint32_t *cdf)
+{
+    double *pm = (double *)malloc(sizeof(double) * 4096);
+    int n = orc_eb_pmf(p, median, lo, hi, pm, 4096);
+    int rc = n < 0 ? -1 : orc_quantize_pmf(pm, n, cdf);
+    free(pm);
     return rc;
 }
 

@@ -82,6 +82,13 @@ typedef struct {
 /* Quantized 16-bit CDF from a pmf over n symbols (escape last). */
 int orc_quantize_pmf(const double *p, int n, uint32_t *cdf);
 
+/* Median (float), tails and likelihoods of one channel of the entropy
+ * bottleneck before frequency quantization: pm[s + lo] = c(m+s+1/2) -
+ * c(m+s-1/2) for s in [-lo, hi], and pm[lo+hi+1] = c(m-lo-1/2) + 1 -
+ * c(m+hi+1/2), the escape mass of both tails.  cap = capacity of pm.
+ * Returns n = lo+hi+2, or -1 (support above 4096 symbols, or above cap). */
+int orc_eb_pmf(const double *p, float *median, int *lo, int *hi, double *pm, int cap);
+
 /* Median (float) and tails of channel c of the entropy bottleneck, and its
  * quantized table.  cdf must hold 4097 entries.  Returns 0 or -1 if the
  * support exceeds 4096 symbols. */
