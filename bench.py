@@ -218,7 +218,7 @@ def main():
 
     def step():
         bs = codec.encode(frames, stream=sid)
-        codec.decode(bs, H, W, out, stream=sid)
+        codec.decode(bs, out, stream=sid)
         return bs
 
     with torch.cuda.stream(stream):
@@ -240,7 +240,7 @@ def main():
             ev[k][0].record(stream)
             bs = codec.encode(frames, stream=sid)
             ev[k][1].record(stream)
-            codec.decode(bs, H, W, out, stream=sid)
+            codec.decode(bs, out, stream=sid)
             ev[k][2].record(stream)
         torch.cuda.synchronize()
     status = codec.sync_status(sid)
@@ -323,7 +323,7 @@ def main():
         for _ in range(max(args.warmup, 3)):
             for c_, s_, o_ in zip(c2, st2, outs):
                 with torch.cuda.stream(s_):
-                    c_.decode(c_.encode(frames, stream=s_.cuda_stream), H, W, o_, stream=s_.cuda_stream)
+                    c_.decode(c_.encode(frames, stream=s_.cuda_stream), o_, stream=s_.cuda_stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.zero_()
@@ -333,7 +333,7 @@ def main():
         for _ in range(args.steps):
             for c_, s_, o_ in zip(c2, st2, outs):
                 with torch.cuda.stream(s_):
-                    c_.decode(c_.encode(frames, stream=s_.cuda_stream), H, W, o_, stream=s_.cuda_stream)
+                    c_.decode(c_.encode(frames, stream=s_.cuda_stream), o_, stream=s_.cuda_stream)
         done = torch.cuda.Event()
         done.record(st2[1])
         st2[0].wait_event(done)
@@ -366,12 +366,12 @@ def main():
         with torch.cuda.stream(stream):
             for _ in range(2):
                 bs2 = codec.encode(hin, stream=sid)
-                codec.decode(bs2, H, W, hout, stream=sid)
+                codec.decode(bs2, hout, stream=sid)
             codec.sync(sid)
             t0 = time.perf_counter()
             for _ in range(args.steps):
                 bs2 = codec.encode(hin, stream=sid)
-                codec.decode(bs2, H, W, hout, stream=sid)
+                codec.decode(bs2, hout, stream=sid)
             codec.sync(sid)
             serial_fps = ws * B * args.steps / (time.perf_counter() - t0)
         # pipelined through the serving API: eight lanes (codec + stream, the server's maximum), a
@@ -468,7 +468,7 @@ def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws
     for i in range(0, STUDENT_POOL, 8):
         fr = torch.from_numpy(synth.make_frames(8, H, W, first=STUDENT_POOL_FIRST + i)).cuda()
         o = torch.empty_like(fr)
-        teacher.decode(teacher.encode(fr), H, W, o)
+        teacher.decode(teacher.encode(fr), o)
         teacher.read_tensor(lic.T_YHAT, pool_y[i:i + 8])
         teacher.read_tensor(lic.T_XPRE, pool_x[i:i + 8])
     st = lic.Student(synth.make_student_weights(M_CH, STUDENT_C), M_CH, STUDENT_C, max_batch=STUDENT_BATCH,
@@ -513,15 +513,15 @@ def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws
     # the codec the pairs came from, checked on the held-out batch (the same frames as below)
     fbs = teacher.encode(frames)
     teacher.set_student(st, min_psnr_db=35.0, checked=True)
-    teacher.decode(fbs, H, W, out)
+    teacher.decode(fbs, out)
     _, ffall, fpsnrs = teacher.student_report()
     teacher.close()
     # the hyperprior codec decoding with the student: checked (per-frame PSNR vs the teacher), then timed
     codec = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt)
     bs = codec.encode(frames)
-    codec.decode(bs, H, W, out)
+    codec.decode(bs, out)
     codec.set_student(st, min_psnr_db=35.0, checked=True)
-    codec.decode(bs, H, W, out)
+    codec.decode(bs, out)
     nchk, nfall, psnrs = codec.student_report()
     codec.set_student(st, checked=False)
     fms, fstatus = time_steps(codec, frames, out, H, W, args.steps, args.warmup, stream, flush)
@@ -531,12 +531,12 @@ def student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws
         codec.set_student(s_)
         with torch.cuda.stream(stream):
             for _ in range(3):
-                codec.decode(bs, H, W, out, stream=sid)
+                codec.decode(bs, out, stream=sid)
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.zero_()
             ev0.record(stream)
             for _ in range(args.steps):
-                codec.decode(bs, H, W, out, stream=sid)
+                codec.decode(bs, out, stream=sid)
             ev1.record(stream)
             torch.cuda.synchronize()
         dec[name] = B * args.steps / (ev0.elapsed_time(ev1) / 1000.0)
@@ -662,7 +662,7 @@ def wide_form(args, lic, synth, torch, np, stream, flush, rank):
         idx_e = torch.empty(B3, M3, Hp3 // 16, Wp3 // 16, dtype=torch.uint8, device="cuda")
         idx_d = torch.empty_like(idx_e)
         c.read_tensor(lic.T_IDX, idx_e)
-        c.decode(bs, H3, W3, out)
+        c.decode(bs, out)
         st = c.sync_status()
         c.read_tensor(lic.T_IDX, idx_d)
         r = {"value": B3 * args.steps / (sum(fms) / 1000.0), "unit": "frames/s",
@@ -686,14 +686,14 @@ def time_steps(codec, frames, out, H, W, steps, warmup, stream, flush):
     with torch.cuda.stream(stream):
         for _ in range(max(warmup, 3)):
             bs = codec.encode(frames, stream=sid)
-            codec.decode(bs, H, W, out, stream=sid)
+            codec.decode(bs, out, stream=sid)
         codec.sync(sid)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for k in range(steps):
             flush.zero_()
             ev[k][0].record(stream)
             bs = codec.encode(frames, stream=sid)
-            codec.decode(bs, H, W, out, stream=sid)
+            codec.decode(bs, out, stream=sid)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in ev], codec.sync_status(sid)

@@ -48,6 +48,7 @@ extern "C" {
 #define LIC_E_CORRUPT_STREAM (-4)
 #define LIC_E_TIMEOUT (-5)
 #define LIC_E_CUDA (-6)
+#define LIC_E_BUSY (-7)   /* too many requests / batches outstanding */
 
 typedef enum { LIC_FACTORIZED = 0, LIC_HYPERPRIOR = 1 } lic_kind;
 /* LIC_FP32: every step float32-accurate (tensor-core convs in 3xTF32).
@@ -105,12 +106,18 @@ typedef enum { LIC_NORM_GDN = 0, LIC_NORM_1DN = 1 } lic_norm;
 
 typedef struct lic_codec lic_codec;
 
-/* A batch of frame bitstreams laid out back to back.  Frame i occupies
- * bytes [offsets[i], offsets[i] + sizes[i]) of `data`.  Each frame is one
- * self-describing container (magic "LIC1", see the design notes):
+/* A batch of frame bitstreams laid out back to back -- the strings the
+ * paper's encoder hands to its decoder (Sec. III-B: the z string, then the
+ * y string, per frame).  Frame i occupies bytes [offsets[i], offsets[i] +
+ * sizes[i]) of `data`.  Each frame is one self-describing container (magic
+ * "LIC1", see the design notes):
  *   'LIC1' u16 version=1, u16 kind, u16 N, u16 M, u32 H, u32 W, u32 Hp,
  *   u32 Wp, u16 R, u16 0, u32 nsub, u32 off[nsub+1] (16-bit word offsets),
- *   u16 payload[off[nsub]]                               (little endian)  */
+ *   u16 payload[off[nsub]]                               (little endian)
+ * A batch made by lic_encode is library-owned (owner != NULL) and stays
+ * valid until lic_bitstreams_release; a batch a caller assembles from its
+ * own memory has owner = NULL and is never touched by the library beyond
+ * the call it is passed to.  Every frame of a batch has the same size. */
 typedef struct {
     int count;                 /* frames */
     int on_device;             /* 1: data and d_offsets are device pointers */
@@ -121,6 +128,9 @@ typedef struct {
     const int64_t *sizes;      /* host, count sizes in bytes */
     const int64_t *d_offsets;  /* device copy of offsets (on_device only) */
     const int64_t *d_sizes;    /* device copy of sizes (on_device only) */
+    int H, W;                  /* original frame size of every frame; 0, 0:
+                                  lic_decode reads it from frame 0's header */
+    void *owner;               /* library batch this view belongs to, or NULL */
 } lic_bitstreams;
 
 /* ---------------------------------------------------------------------- */
@@ -128,53 +138,79 @@ typedef struct {
 /* ---------------------------------------------------------------------- */
 
 /* Create a codec of `kind` with N transform channels and M latent channels
- * on the current CUDA device.  The weights are validated (every name above
- * present with the right numel), copied, re-laid-out for the kernels, and
- * the entropy-model CDF tables are built once on the host in FP64 (the
- * factorized entropy bottleneck of [2] app. 6.1 and the 64-scale Gaussian
- * conditional of [2]) and uploaded.  opts may be NULL (defaults).
+ * on the current CUDA device -- the factorized-prior codec of the paper's
+ * [1] (Sec. III-A, the "factorized" rows of Tables 2-4) or the scale
+ * hyperprior of [2] (Sec. III-B, the "hyper" rows).  The weights are
+ * validated (every name above present with the right numel), copied,
+ * re-laid-out for the kernels, and the entropy-model CDF tables are built
+ * once on the host in FP64 (the factorized entropy bottleneck of [2] app.
+ * 6.1 and the 64-scale Gaussian conditional of [2]) and uploaded.  opts may
+ * be NULL (defaults).  *out is owned by the caller (lic_codec_destroy).
  * Errors: INVALID_ARG (bad kind/N/M/weights), UNSUPPORTED (table support
  * above 4096 symbols, N or M not a multiple of 32, N > 256), OOM, CUDA. */
 int lic_codec_create(int kind, int N, int M, const lic_weights *weights,
                      const lic_options *opts, lic_codec **out);
 
 /* Free every device and host resource of the codec (synchronizes the
- * device first).  NULL is accepted. */
+ * device first), including every bitstream batch it still owns.  NULL is
+ * accepted. */
 void lic_codec_destroy(lic_codec *codec);
 
 /* Wait for `stream`, then return and clear the status latched by kernels
  * since the previous lic_sync: LIC_OK, LIC_E_CORRUPT_STREAM or
- * LIC_E_TIMEOUT (or LIC_E_CUDA if the stream itself failed). */
+ * LIC_E_TIMEOUT (or LIC_E_CUDA if the stream itself failed).  (No
+ * counterpart in the paper, whose stages report nothing back.) */
 int lic_sync(lic_codec *codec, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Encode / decode                                                         */
 /* ---------------------------------------------------------------------- */
 
-/* Encode B frames (B x 3 x H x W float32, device or host memory).  The
- * frames are replicate-padded on the bottom/right to multiples of 64
- * internally.  On return *out describes library-owned buffers: data,
- * d_offsets and d_sizes on the device (valid in stream order), offsets and
- * sizes on the host (pinned; valid once the stream has synchronized).  They
- * stay valid until the next lic_encode/lic_encode_latents on this codec or
- * lic_codec_destroy.  Errors: INVALID_ARG (B < 1, H or W < 1, null
- * pointers), OOM, CUDA. */
+/* Encode B frames (B x 3 x H x W float32, device or host memory): the
+ * encoder of the paper's Fig. 1 / Sec. III-A (x -> g_a -> y -> Q -> rANS)
+ * and, for the hyperprior, Sec. III-B (y -> h_a -> z -> Q -> rANS, z_hat ->
+ * h_s -> scales -> index).  The frames are replicate-padded on the
+ * bottom/right to multiples of 64 internally.  On return *out describes a
+ * library-owned batch: data, d_offsets and d_sizes on the device (valid in
+ * stream order), offsets and sizes on the host (pinned; valid once the
+ * stream has synchronized), H and W, and the owner handle.  The batch stays
+ * valid until lic_bitstreams_release (or lic_codec_destroy), whatever is
+ * encoded meanwhile; released batches' buffers are pooled and reused by
+ * later encodes (the paper's memory pooling, Sec. III-D).  At most 64
+ * batches may be unreleased at once.  Errors: INVALID_ARG (B < 1, H or W <
+ * 1, null pointers), BUSY (64 batches unreleased), OOM, CUDA. */
 int lic_encode(lic_codec *codec, const float *frames, int B, int H, int W,
                lic_bitstreams *out, void *stream);
 
-/* Decode in->count frames of size H x W into `frames` (count x 3 x H x W
- * float32, device or host memory; a host destination makes the call wait
- * for the stream).  in may live on the device (on_device = 1, e.g. the
- * output of lic_encode) or on the host.  Headers are validated on the
- * device against (kind, N, M, H, W); a mismatch or a corrupt substream is
- * latched as LIC_E_CORRUPT_STREAM (read it with lic_sync) and the frames of
- * a corrupt stream are left unspecified.  The entropy decoder bounds every
- * read; a corrupt stream never faults the device. */
-int lic_decode(lic_codec *codec, const lic_bitstreams *in, int H, int W,
-               float *frames, void *stream);
+/* Return a batch made by lic_encode or lic_encode_latents to the codec's
+ * pool and clear *bs (owner = NULL, count = 0).  The buffers may be
+ * overwritten by the next encode on this codec, on any stream: release a
+ * batch once every call that reads it has been enqueued on the stream the
+ * next encode will use, or has completed.  Host-only, never waits.  Errors:
+ * INVALID_ARG (not a live batch of this codec; releasing twice is an
+ * error, and a cleared struct is accepted as a no-op). */
+int lic_bitstreams_release(lic_codec *codec, lic_bitstreams *bs);
+
+/* Decode in->count frames into `frames` (count x 3 x H x W float32, device
+ * or host memory; a host destination makes the call wait for the stream):
+ * the decoder of Sec. III-B in the order of its 4-stage pipeline -- z
+ * first, then h_s -> scales -> index, then y, then g_s (Fig. 1) -- or, for
+ * the factorized codec, rANS^-1 -> Q^-1 -> g_s (Sec. III-A).  H x W is the
+ * batch's frame size: in->H, in->W, or, when those are 0, frame 0's header
+ * (a device-resident batch then costs one small synchronous copy).  in may
+ * live on the device (on_device = 1, e.g. the output of lic_encode) or on
+ * the host.  Headers are validated on the device against (kind, N, M, H,
+ * W); a mismatch or a corrupt substream is latched as LIC_E_CORRUPT_STREAM
+ * (read it with lic_sync) and the frames of a corrupt stream are left
+ * unspecified.  The entropy decoder bounds every read; a corrupt stream
+ * never faults the device.  Errors: INVALID_ARG (null pointers, count < 1),
+ * CORRUPT_STREAM returned at once (nothing launched) when H, W are taken
+ * from a frame-0 header that is not a valid container header, OOM, CUDA. */
+int lic_decode(lic_codec *codec, const lic_bitstreams *in, float *frames, void *stream);
 
 /* Copy a device-resident batch (in->on_device = 1, e.g. from lic_encode)
- * to host memory after waiting for `stream`: bytes [0, offsets[count]) of
+ * to host memory after waiting for `stream` (the strings leave the GPU, as
+ * the paper's encoder sends them, Sec. III-B and V-B): bytes [0, offsets[count]) of
  * in->data, so frame i starts at dst + offsets[i] and is sizes[i] bytes.
  * dst_cap is the capacity of dst.  Returns the bytes copied (>= 0) or
  * INVALID_ARG (capacity too small, not a device batch) / CUDA. */
@@ -182,7 +218,8 @@ int64_t lic_bitstreams_download(const lic_bitstreams *in, uint8_t *dst, int64_t 
                                 void *stream);
 
 /* Parse the header of one host-resident frame container: original size
- * and kind.  Returns INVALID_ARG / CORRUPT_STREAM on a bad header. */
+ * and kind (the project's container; the paper defines no format).
+ * Returns INVALID_ARG / CORRUPT_STREAM on a bad header. */
 int lic_decoded_shape(const uint8_t *frame, int64_t size, int *kind, int *H, int *W);
 
 /* ---------------------------------------------------------------------- */
@@ -211,25 +248,33 @@ typedef enum {
 int lic_read_tensor(lic_codec *codec, int which, void *dst, int64_t *count,
                     void *stream);
 
-/* y = g_a(pad(frames)): B x M x Hp/16 x Wp/16 float32. */
+/* y = g_a(pad(frames)): B x M x Hp/16 x Wp/16 float32 (the analysis
+ * transform of [1], Sec. III-A).  Errors: INVALID_ARG, OOM, CUDA. */
 int lic_analysis(lic_codec *codec, const float *frames, int B, int H, int W,
                  float *y, void *stream);
-/* x = g_s(y_hat), unclamped: B x 3 x 16Hy x 16Wy float32. */
+/* x = g_s(y_hat), unclamped: B x 3 x 16Hy x 16Wy float32 (the synthesis
+ * transform of [1], Sec. III-A; the student replaces it when one is set).
+ * Errors: INVALID_ARG, OOM, CUDA. */
 int lic_synthesis(lic_codec *codec, const float *yhat, int B, int Hy, int Wy,
                   float *x, void *stream);
-/* z = h_a(y) (hyperprior): B x N x Hy/4 x Wy/4. */
+/* z = h_a(y) (hyperprior): B x N x Hy/4 x Wy/4 (the hyper analysis of
+ * [2], Sec. III-B).  Errors: INVALID_ARG (factorized codec), OOM, CUDA. */
 int lic_hyper_analysis(lic_codec *codec, const float *y, int B, int Hy, int Wy,
                        float *z, void *stream);
 /* sigma = h_s(z_hat) and idx = scale index of sigma (hyperprior):
- * B x M x 4Hz x 4Wz float32 and uint8 (idx may be NULL). */
+ * B x M x 4Hz x 4Wz float32 and uint8 (idx may be NULL) -- the hyper
+ * synthesis of [2] that both encoder and decoder run (Sec. III-B), and the
+ * index into the 64-scale Gaussian table.  Errors: INVALID_ARG, OOM, CUDA. */
 int lic_hyper_synthesis(lic_codec *codec, const float *zhat, int B, int Hz, int Wz,
                         float *sigma, uint8_t *idx, void *stream);
 
 /* Entropy-code given integer symbols (device int32/uint8, NCHW) into frame
- * containers, exactly as lic_encode does after quantization: s_y is
+ * containers, exactly as lic_encode does after quantization (the rANS
+ * stage of Sec. III-A/B, which the paper runs on CPU threads): s_y is
  * B x M x Hy x Wy; idx (hyperprior) the same shape; s_z (hyperprior)
  * B x N x Hy/4 x Wy/4.  H, W are the original frame size recorded in the
- * headers (Hp = 16 Hy, Wp = 16 Wy).  Output as for lic_encode. */
+ * headers (Hp = 16 Hy, Wp = 16 Wy).  Output, ownership and errors as for
+ * lic_encode; INVALID_ARG also for a symbol pointer not in device memory. */
 int lic_encode_latents(lic_codec *codec, const int32_t *s_y, const uint8_t *idx,
                        const int32_t *s_z, int B, int H, int W, int Hy, int Wy,
                        lic_bitstreams *out, void *stream);
@@ -269,18 +314,21 @@ int lic_encode_latents_noalloc(lic_codec *codec, const int32_t *s_y, const uint8
                                uint8_t *data, int64_t data_cap, int64_t *d_layout,
                                void *stream);
 
-/* Entropy-decode the symbols of in->count frames of size H x W (device
- * int32 outputs; s_z ignored for the factorized codec).  The hyperprior
- * path runs h_s on the decoded z to obtain the indices of y, as the
- * decoder must. */
-int lic_decode_latents(lic_codec *codec, const lic_bitstreams *in, int H, int W,
+/* Entropy-decode the symbols of in->count frames (device int32 outputs,
+ * NCHW; s_z ignored for the factorized codec); the frame size comes from in
+ * as for lic_decode.  The hyperprior path runs h_s on the decoded z to
+ * obtain the indices of y, as the decoder must (stages 1-3 of the 4-stage
+ * decoder, Sec. III-B).  Errors as for lic_decode. */
+int lic_decode_latents(lic_codec *codec, const lic_bitstreams *in,
                        int32_t *s_y, int32_t *s_z, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Host-only: entropy-model tables (no GPU needed)                         */
 /* ---------------------------------------------------------------------- */
 
-/* Build the quantized 16-bit CDF tables exactly as lic_codec_create does.
+/* Build the quantized 16-bit CDF tables exactly as lic_codec_create does
+ * (the entropy models of [2]: app. 6.1 for the bottleneck, Sec. 3 for the
+ * Gaussian conditional; the paper's codecs use them through CompressAI).
  * Factorized entropy bottleneck over C channels from the eb.* parameters
  * (pass weights with the eb.* entries; C from eb.H0's numel / 3), then, if
  * gauss != 0, the 64 Gaussian tables.  Table t has support [-lo[t], hi[t]]
@@ -292,14 +340,17 @@ int lic_build_tables(const lic_weights *weights, int gauss, int max_tables,
                      int64_t cdf_cap, float *medians, int32_t *lo, int32_t *hi,
                      int64_t *start, uint32_t *cdf);
 
-/* The 64 scales of the Gaussian conditional (0.11 .. 256, log-spaced). */
+/* The 64 scales of the Gaussian conditional (0.11 .. 256, log-spaced; the
+ * scale table of [2] as the hyperprior codec of Sec. III-B indexes it). */
 void lic_scale_table(float T[64]);
 
 /* ---------------------------------------------------------------------- */
 /* Measurement                                                             */
 /* ---------------------------------------------------------------------- */
 
-/* enable = 1: start recording a CUDA event pair around every kernel launch
+/* Measurement hooks (no counterpart in the paper; they time the chain the
+ * way its Tables 2-4 report fps, per stage).
+ * enable = 1: start recording a CUDA event pair around every kernel launch
  * the codec issues (on the stream it is given), discarding earlier records;
  * enable = 0: stop recording.  Recording adds a small gap between launches,
  * and the sub-pixel phases of a transposed convolution, which otherwise run
@@ -318,7 +369,22 @@ int lic_profile_report(lic_codec *codec, char *buf, int cap);
 /* Kernel launches issued by this codec since it was created. */
 int64_t lic_launch_count(lic_codec *codec);
 
-/* Diagnostics of the failure path: one GPU thread waits, through the same
+/* Device memory the codec holds now, in bytes: weights, tables, grow-only
+ * workspaces and pooled bitstream batches, counted at each allocation the
+ * codec makes (not from the device's free memory, which other users of the
+ * GPU move).  Returns the byte count or INVALID_ARG. */
+int64_t lic_codec_device_bytes(const lic_codec *codec);
+
+/* Device memory, in bytes, that lic_encode + lic_decode of B frames of
+ * H x W (device frames, no student) make the codec's workspaces and one
+ * bitstream batch reach, computed from the geometry without allocating
+ * (the weights and tables, already held, are not included).  For
+ * admission decisions before a workload is first run.  Returns the byte
+ * count or INVALID_ARG. */
+int64_t lic_codec_workspace_bytes(const lic_codec *codec, int B, int H, int W);
+
+/* Diagnostics of the failure path (no counterpart in the paper): one GPU
+ * thread waits, through the same
  * bounded wait the tensor-core pipelines use, on a barrier that nothing
  * arrives at; after limit_cycles (1 .. 4e9 SM clock cycles) it gives up and
  * latches the codec's timeout status, so the next lic_sync returns

@@ -18,6 +18,11 @@
  * Admission: a request is refused with LIC_E_BUSY when max_pending requests
  * are in flight, and a new resolution is refused with LIC_E_OOM when its
  * lanes would take the device memory the server holds above hbm_budget.
+ * That memory is what the lanes' codecs count at each allocation they make
+ * (lic_codec_device_bytes) plus the frame slabs, never the device's free
+ * memory (which other users of the GPU move); a resolution's cost is
+ * estimated from its geometry (lic_codec_workspace_bytes) and checked before
+ * its workspaces are allocated, then charged as counted.
  *
  * Each request is one frame encoded and decoded again (the round trip the
  * paper's demo makes); its bitstream and decoded frame stay in device memory
@@ -38,7 +43,9 @@ extern "C" {
 #endif
 
 /* too many requests in flight (lic_server_submit) */
+#ifndef LIC_E_BUSY
 #define LIC_E_BUSY (-7)
+#endif
 
 typedef struct lic_server lic_server;
 
@@ -64,7 +71,9 @@ void lic_server_destroy(lic_server *server);
 
 /* Make the bucket of H x W frames ready (its lanes' codecs, workspaces and
  * graphs for every batch size) so that the first request does not pay for
- * it.  LIC_E_OOM when it would exceed hbm_budget.  Idempotent. */
+ * it.  LIC_E_OOM when it would exceed hbm_budget (refused before any
+ * workspace is allocated when the estimate already exceeds it; only the
+ * first lane's weights are created to make the estimate).  Idempotent. */
 int lic_server_prepare(lic_server *server, int H, int W);
 
 /* Queue one frame (float32 3 x H x W in [0, 1], host memory -- pinned for

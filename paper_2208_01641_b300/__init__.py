@@ -38,7 +38,7 @@ EXPORTED = [
     "lic_synthesis", "lic_hyper_analysis", "lic_hyper_synthesis", "lic_encode_latents",
     "lic_decode_latents", "lic_build_tables", "lic_scale_table", "lic_strerror",
     "lic_profile_enable", "lic_profile_report", "lic_launch_count", "lic_encode_latents_noalloc",
-    "lic_test_bounded_wait",
+    "lic_test_bounded_wait", "lic_bitstreams_release", "lic_codec_device_bytes", "lic_codec_workspace_bytes",
     # include/lic_student.h (learned form)
     "lic_student_create", "lic_student_destroy", "lic_student_grad", "lic_student_step", "lic_student_read",
     "lic_student_read_activation", "lic_student_steps", "lic_student_forward", "lic_student_profile_enable", "lic_student_profile_report",
@@ -102,7 +102,8 @@ class _Bitstreams(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int), ("on_device", ctypes.c_int),
                 ("data", ctypes.c_void_p), ("offsets", ctypes.POINTER(ctypes.c_int64)),
                 ("sizes", ctypes.POINTER(ctypes.c_int64)), ("d_offsets", ctypes.c_void_p),
-                ("d_sizes", ctypes.c_void_p)]
+                ("d_sizes", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("owner", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -121,7 +122,12 @@ def _lib():
         L.lic_codec_destroy.restype = None
         L.lic_sync.argtypes = [vp, vp]
         L.lic_encode.argtypes = [vp, vp, i, i, i, ctypes.POINTER(_Bitstreams), vp]
-        L.lic_decode.argtypes = [vp, ctypes.POINTER(_Bitstreams), i, i, vp, vp]
+        L.lic_decode.argtypes = [vp, ctypes.POINTER(_Bitstreams), vp, vp]
+        L.lic_bitstreams_release.argtypes = [vp, ctypes.POINTER(_Bitstreams)]
+        L.lic_codec_device_bytes.argtypes = [vp]
+        L.lic_codec_device_bytes.restype = i64
+        L.lic_codec_workspace_bytes.argtypes = [vp, i, i, i]
+        L.lic_codec_workspace_bytes.restype = i64
         L.lic_bitstreams_download.argtypes = [ctypes.POINTER(_Bitstreams), vp, i64, vp]
         L.lic_bitstreams_download.restype = i64
         L.lic_decoded_shape.argtypes = [vp, i64, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
@@ -131,7 +137,7 @@ def _lib():
         L.lic_hyper_analysis.argtypes = [vp, vp, i, i, i, vp, vp]
         L.lic_hyper_synthesis.argtypes = [vp, vp, i, i, i, vp, vp, vp]
         L.lic_encode_latents.argtypes = [vp, vp, vp, vp, i, i, i, i, i, ctypes.POINTER(_Bitstreams), vp]
-        L.lic_decode_latents.argtypes = [vp, ctypes.POINTER(_Bitstreams), i, i, vp, vp, vp]
+        L.lic_decode_latents.argtypes = [vp, ctypes.POINTER(_Bitstreams), vp, vp, vp]
         L.lic_encode_latents_noalloc.argtypes = [vp, vp, vp, vp, i, i, i, i, i, vp, i64, vp, vp]
         L.lic_build_tables.argtypes = [ctypes.POINTER(_Weights), i, i, i64, vp, vp, vp, vp, vp]
         L.lic_scale_table.argtypes = [vp]
@@ -238,8 +244,11 @@ def scale_table():
 
 
 class Bitstreams:
-    """A batch of frame containers returned by encode (library-owned buffers,
-    valid until the codec's next encode)."""
+    """A batch of frame containers returned by encode: library-owned
+    buffers, valid until release() (called when the object is collected).
+    The codec may reuse released buffers in its next encode on any stream,
+    so release a batch (or drop the last reference) only once the calls that
+    read it are enqueued on the stream of that next encode."""
 
     def __init__(self, codec: "Codec", s: _Bitstreams, stream):
         self.codec, self.s, self.stream = codec, s, stream
@@ -247,6 +256,11 @@ class Bitstreams:
     @property
     def count(self):
         return self.s.count
+
+    @property
+    def shape(self):
+        """(H, W): the frame size of every frame of the batch."""
+        return self.s.H, self.s.W
 
     def sizes(self):
         """Frame sizes in bytes (synchronizes the stream)."""
@@ -263,15 +277,29 @@ class Bitstreams:
         return [buf[self.s.offsets[i]:self.s.offsets[i] + self.s.sizes[i]].tobytes()
                 for i in range(self.s.count)]
 
+    def release(self):
+        """Return the buffers to the codec's pool (lic_bitstreams_release)."""
+        c = self.codec
+        if self.s.owner and c is not None and getattr(c, "h", None):
+            _check(_lib().lic_bitstreams_release(c.h, ctypes.byref(self.s)), "lic_bitstreams_release")
+        self.codec = None
 
-def host_bitstreams(frames):
-    """A lic_bitstreams view of host bytes objects (for lic_decode)."""
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def host_bitstreams(frames, H: int = 0, W: int = 0):
+    """A lic_bitstreams view of host bytes objects (for lic_decode).  With
+    H = W = 0 the library reads the frame size from frame 0's header."""
     sizes = np.array([len(f) for f in frames], np.int64)
     offs = np.zeros(len(frames) + 1, np.int64)
     offs[1:] = np.cumsum(sizes)
     data = np.frombuffer(b"".join(frames) or b"\0", np.uint8).copy()
     s = _Bitstreams(len(frames), 0, data.ctypes.data, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                    sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), None, None)
+                    sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), None, None, H, W, None)
     s._keep = (data, offs, sizes)
     return s
 
@@ -346,16 +374,26 @@ class Codec:
         _check(_lib().lic_encode(self.h, _ptr(frames), B, H, W, ctypes.byref(s), st), "lic_encode")
         return Bitstreams(self, s, st)
 
-    def decode(self, bs, H: int, W: int, out, stream=None):
+    def decode(self, bs, out, stream=None):
+        """Decode a batch into out (B x 3 x H x W float32, device or host);
+        the frame size comes from the batch."""
         st = _stream(stream)
         s = bs.s if isinstance(bs, Bitstreams) else bs
-        _check(_lib().lic_decode(self.h, ctypes.byref(s), H, W, _ptr(out), st), "lic_decode")
+        _check(_lib().lic_decode(self.h, ctypes.byref(s), _ptr(out), st), "lic_decode")
         return out
 
-    def decode_status(self, bs, H: int, W: int, out, stream=None) -> int:
+    def decode_status(self, bs, out, stream=None) -> int:
         st = _stream(stream)
         s = bs.s if isinstance(bs, Bitstreams) else bs
-        return _lib().lic_decode(self.h, ctypes.byref(s), H, W, _ptr(out), st)
+        return _lib().lic_decode(self.h, ctypes.byref(s), _ptr(out), st)
+
+    def device_bytes(self) -> int:
+        """Device memory the codec holds (lic_codec_device_bytes)."""
+        return _check(_lib().lic_codec_device_bytes(self.h), "lic_codec_device_bytes")
+
+    def workspace_bytes(self, B: int, H: int, W: int) -> int:
+        """Workspace + one batch that B frames of H x W need (lic_codec_workspace_bytes)."""
+        return _check(_lib().lic_codec_workspace_bytes(self.h, B, H, W), "lic_codec_workspace_bytes")
 
     def read_tensor(self, which: int, dst, stream=None):
         n = ctypes.c_int64()
@@ -412,9 +450,9 @@ class Codec:
             self.h, _ptr(s_y), _ptr(idx) if idx is not None else None, _ptr(s_z) if s_z is not None else None,
             B, H, W, Hy, Wy, _ptr(data), data.numel(), _ptr(layout), _stream(stream))
 
-    def decode_latents(self, bs, H: int, W: int, s_y, s_z=None, stream=None):
+    def decode_latents(self, bs, s_y, s_z=None, stream=None):
         s = bs.s if isinstance(bs, Bitstreams) else bs
-        _check(_lib().lic_decode_latents(self.h, ctypes.byref(s), H, W, _ptr(s_y),
+        _check(_lib().lic_decode_latents(self.h, ctypes.byref(s), _ptr(s_y),
                                          _ptr(s_z) if s_z is not None else None, _stream(stream)),
                "lic_decode_latents")
 

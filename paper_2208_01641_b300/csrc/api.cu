@@ -17,6 +17,7 @@
 namespace lic {
 
 static thread_local char g_last_error[512];
+thread_local int64_t *g_alloc_sink = nullptr;
 
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
@@ -87,8 +88,17 @@ struct lic_codec {
     lic::DevBuf status;
     // workspace
     lic::DevBuf xin, patches, act0, act1, y, s_y, h1, h2, z, s_z, zhat, g1, g2, sigma, idx, yhat, xpre;
-    lic::DevBuf scratch, counts, sub_off, frame_bytes, offs, data, stage_in, stage_out, in_data, in_offs;
-    lic::HostPinned h_offs;
+    lic::DevBuf scratch, counts, sub_off, frame_bytes, stage_in, stage_out, in_data, in_offs;
+    // encoded batches: containers + offsets/sizes (device and pinned host),
+    // handed out by encode, pooled on release (grow-only buffers)
+    struct Batch {
+        lic::DevBuf data, offs;
+        lic::HostPinned h_offs;
+        bool live = false;
+    };
+    std::vector<std::unique_ptr<Batch>> batches;
+    // device bytes this codec holds (lic::AllocScope of every entry point)
+    int64_t device_bytes = 0;
     // measurement
     lic::Profiler pf;
     // the four sub-pixel phases of a transposed conv write disjoint pixels:
@@ -638,49 +648,94 @@ float *run_layer_gdn(const lic_codec *cd, const Layer &L, const Gdn &G, const fl
 
 int pad64(int v) { return (v + 63) / 64 * 64; }
 
-template <typename T>
-cudaError_t ensure_n(DevBuf &b, int64_t n) {
-    return b.ensure((size_t)n * sizeof(T) + 256);
-}
-
-// Workspace for a batch of B frames padded to Hp x Wp.
-int ensure_workspace(lic_codec *cd, int B, int Hp, int Wp) {
+// The grow-only workspace of a batch of B frames padded to Hp x Wp, as a
+// list of (buffer, bytes) handed to need(): ensure_workspace allocates it,
+// lic_codec_workspace_bytes adds it up without allocating.
+template <typename F>
+int workspace_plan(lic_codec *cd, int B, int Hp, int Wp, F &&need) {
     const int N = cd->N, M = cd->M;
     const int64_t Hy = Hp / 16, Wy = Wp / 16, Hz = Hp / 64, Wz = Wp / 64;
     const int64_t big = (int64_t)B * (Hp / 2) * (Wp / 2) * N;
-    if (!cd->use_patch) LIC_CUDA_TRY(ensure_n<float>(cd->xin, (int64_t)B * Hp * Wp * 3));   // else unused
-    if (cd->use_patch) LIC_CUDA_TRY(ensure_n<float>(cd->patches, (int64_t)B * (Hp / 2) * (Wp / 2) * PATCH_K));
-    LIC_CUDA_TRY(ensure_n<float>(cd->act0, big));
-    LIC_CUDA_TRY(ensure_n<float>(cd->act1, big));
-    LIC_CUDA_TRY(ensure_n<float>(cd->y, (int64_t)B * Hy * Wy * M));
-    LIC_CUDA_TRY(ensure_n<int32_t>(cd->s_y, (int64_t)B * Hy * Wy * M));
-    LIC_CUDA_TRY(ensure_n<float>(cd->yhat, (int64_t)B * Hy * Wy * M));
-    LIC_CUDA_TRY(ensure_n<float>(cd->xpre, (int64_t)B * Hp * Wp * 3));
+    int rc = 0;
+    auto f = [&](DevBuf &b, int64_t n, int64_t elem) {
+        if (!rc) rc = need(b, n * elem + 256);
+    };
+    if (!cd->use_patch) f(cd->xin, (int64_t)B * Hp * Wp * 3, 4);   // else unused
+    if (cd->use_patch) f(cd->patches, (int64_t)B * (Hp / 2) * (Wp / 2) * PATCH_K, 4);
+    f(cd->act0, big, 4);
+    f(cd->act1, big, 4);
+    f(cd->y, (int64_t)B * Hy * Wy * M, 4);
+    f(cd->s_y, (int64_t)B * Hy * Wy * M, 4);
+    f(cd->yhat, (int64_t)B * Hy * Wy * M, 4);
+    f(cd->xpre, (int64_t)B * Hp * Wp * 3, 4);
     if (cd->kind == LIC_HYPERPRIOR) {
-        LIC_CUDA_TRY(ensure_n<float>(cd->h1, (int64_t)B * Hy * Wy * N));
-        LIC_CUDA_TRY(ensure_n<float>(cd->h2, (int64_t)B * (Hy / 2) * (Wy / 2) * N));
-        LIC_CUDA_TRY(ensure_n<float>(cd->z, (int64_t)B * Hz * Wz * N));
-        LIC_CUDA_TRY(ensure_n<int32_t>(cd->s_z, (int64_t)B * Hz * Wz * N));
-        LIC_CUDA_TRY(ensure_n<float>(cd->zhat, (int64_t)B * Hz * Wz * N));
-        LIC_CUDA_TRY(ensure_n<float>(cd->g1, (int64_t)B * (Hy / 2) * (Wy / 2) * N));
-        LIC_CUDA_TRY(ensure_n<float>(cd->g2, (int64_t)B * Hy * Wy * N));
-        LIC_CUDA_TRY(ensure_n<float>(cd->sigma, (int64_t)B * Hy * Wy * M));
-        LIC_CUDA_TRY(ensure_n<uint8_t>(cd->idx, (int64_t)B * Hy * Wy * M));
+        f(cd->h1, (int64_t)B * Hy * Wy * N, 4);
+        f(cd->h2, (int64_t)B * (Hy / 2) * (Wy / 2) * N, 4);
+        f(cd->z, (int64_t)B * Hz * Wz * N, 4);
+        f(cd->s_z, (int64_t)B * Hz * Wz * N, 4);
+        f(cd->zhat, (int64_t)B * Hz * Wz * N, 4);
+        f(cd->g1, (int64_t)B * (Hy / 2) * (Wy / 2) * N, 4);
+        f(cd->g2, (int64_t)B * Hy * Wy * N, 4);
+        f(cd->sigma, (int64_t)B * Hy * Wy * M, 4);
+        f(cd->idx, (int64_t)B * Hy * Wy * M, 1);
     }
+    return rc;
+}
+
+// Working memory of the entropy encoder, then the batch's own buffers
+// (bb: the pooled batch being filled; its data holds worst-case containers).
+template <typename F>
+int entropy_plan(lic_codec *cd, const StreamGeom &g, int B, lic_codec::Batch *bb, F &&need) {
+    const int64_t subs = (int64_t)B * g.nsub;
+    int rc = 0;
+    auto f = [&](DevBuf &b, int64_t n, int64_t elem) {
+        if (!rc) rc = need(b, n * elem + 256);
+    };
+    f(cd->scratch, subs * g.cap_words, 2);
+    f(cd->counts, subs, 8);
+    f(cd->sub_off, subs, 8);
+    f(cd->frame_bytes, B, 8);
+    const int64_t frame_cap = g.header_bytes + 2 * (int64_t)g.nsub * g.cap_words + 16;
+    f(bb->offs, 2 * (int64_t)B + 1, 8);
+    f(bb->data, (int64_t)B * frame_cap, 1);
+    return rc;
+}
+
+int ensure_buf(DevBuf &b, int64_t n) {
+    LIC_CUDA_TRY(b.ensure((size_t)n));
     return LIC_OK;
 }
 
-int ensure_entropy(lic_codec *cd, const StreamGeom &g, int B) {
-    const int64_t subs = (int64_t)B * g.nsub;
-    LIC_CUDA_TRY(ensure_n<uint16_t>(cd->scratch, subs * g.cap_words));
-    LIC_CUDA_TRY(ensure_n<int64_t>(cd->counts, subs));
-    LIC_CUDA_TRY(ensure_n<int64_t>(cd->sub_off, subs));
-    LIC_CUDA_TRY(ensure_n<int64_t>(cd->frame_bytes, B));
-    LIC_CUDA_TRY(ensure_n<int64_t>(cd->offs, 2 * (int64_t)B + 1));
-    const int64_t frame_cap = g.header_bytes + 2 * (int64_t)g.nsub * g.cap_words + 16;
-    LIC_CUDA_TRY(ensure_n<uint8_t>(cd->data, (int64_t)B * frame_cap));
-    LIC_CUDA_TRY(cd->h_offs.ensure((2 * (size_t)B + 1) * sizeof(int64_t)));
-    return LIC_OK;
+int ensure_workspace(lic_codec *cd, int B, int Hp, int Wp) {
+    return workspace_plan(cd, B, Hp, Wp, ensure_buf);
+}
+
+// At most this many encoded batches may be unreleased at once per codec.
+constexpr int kMaxLiveBatches = 64;
+
+// A free pooled batch sized for B frames of geometry g (not yet marked
+// live), or null with *rc set.
+lic_codec::Batch *acquire_batch(lic_codec *cd, const StreamGeom &g, int B, int *rc) {
+    lic_codec::Batch *bb = nullptr;
+    int live = 0;
+    for (auto &p : cd->batches) {
+        if (p->live) ++live;
+        else if (!bb) bb = p.get();
+    }
+    if (!bb) {
+        if (live >= kMaxLiveBatches) {
+            *rc = LIC_E_BUSY;
+            return nullptr;
+        }
+        cd->batches.push_back(std::make_unique<lic_codec::Batch>());
+        bb = cd->batches.back().get();
+    }
+    if ((*rc = entropy_plan(cd, g, B, bb, ensure_buf))) return nullptr;
+    if (bb->h_offs.ensure((2 * (size_t)B + 1) * sizeof(int64_t)) != cudaSuccess) {
+        *rc = LIC_E_OOM;
+        return nullptr;
+    }
+    return bb;
 }
 
 cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
@@ -767,7 +822,10 @@ void teacher_synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, 
 
 // g_s, or the student in its place when one is set
 int synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, cudaStream_t st) {
-    if (cd->student) return student_forward_nhwc(cd->student, yhat, B, Hy, Wy, cd->xpre.as<float>(), st);
+    if (cd->student) {
+        AllocScope not_ours(nullptr);   // the student's buffers are its own
+        return student_forward_nhwc(cd->student, yhat, B, Hy, Wy, cd->xpre.as<float>(), st);
+    }
     teacher_synthesis(cd, yhat, B, Hy, Wy, st);
     return LIC_OK;
 }
@@ -781,7 +839,11 @@ int checked_synthesis(lic_codec *cd, int B, int Hp, int Wp, int H, int W, cudaSt
     LIC_CUDA_TRY(cd->stu_part.ensure((size_t)B * 64 * sizeof(double)));
     LIC_CUDA_TRY(cd->stu_psnr.ensure((size_t)B * sizeof(float)));
     LIC_CUDA_TRY(cd->stu_pass.ensure((size_t)B * sizeof(int)));
-    int rc = student_forward_nhwc(cd->student, cd->yhat.as<float>(), B, Hp / 16, Wp / 16, cd->xstu.as<float>(), st);
+    int rc;
+    {
+        AllocScope not_ours(nullptr);   // the student's buffers are its own
+        rc = student_forward_nhwc(cd->student, cd->yhat.as<float>(), B, Hp / 16, Wp / 16, cd->xstu.as<float>(), st);
+    }
     if (rc) return rc;
     timed(cd, "student_check", 0, 24.0 * B * Hp * Wp, 3, st, [&] {
         launch_student_check(cd->xstu.as<float>(), cd->xpre.as<float>(), B, Hp, Wp, H, W, cd->stu_thr,
@@ -793,34 +855,71 @@ int checked_synthesis(lic_codec *cd, int B, int Hp, int Wp, int H, int W, cudaSt
     return LIC_OK;
 }
 
-void fill_out(lic_codec *cd, int B, lic_bitstreams *out) {
-    int64_t *h = static_cast<int64_t *>(cd->h_offs.p);
-    const int64_t *d = cd->offs.as<int64_t>();
+void fill_out(lic_codec::Batch *bb, int B, int H, int W, lic_bitstreams *out) {
+    int64_t *h = static_cast<int64_t *>(bb->h_offs.p);
+    const int64_t *d = bb->offs.as<int64_t>();
     out->count = B;
     out->on_device = 1;
-    out->data = cd->data.as<uint8_t>();
+    out->data = bb->data.as<uint8_t>();
     out->offsets = h;
     out->sizes = h + B + 1;
     out->d_offsets = d;
     out->d_sizes = d + B + 1;
+    out->H = H;
+    out->W = W;
+    out->owner = bb;
 }
 
 int entropy_encode(lic_codec *cd, const StreamGeom &g, int B, const int32_t *s_y, const uint8_t *idx,
                    const int32_t *s_z, lic_bitstreams *out, cudaStream_t st) {
-    int rc = ensure_entropy(cd, g, B);
-    if (rc) return rc;
+    int rc = LIC_OK;
+    lic_codec::Batch *bb = acquire_batch(cd, g, B, &rc);
+    if (!bb) return rc;
     const double nsym = (double)B * ((double)g.M * g.Hy * g.Wy + (double)g.nz * g.Hz * g.Wz);
     timed(cd, "rans_encode", 0, 5 * nsym, 1, st, [&] {
         launch_rans_encode(g, B, cd->dt, s_y, idx, s_z, cd->scratch.as<uint16_t>(), cd->counts.as<int64_t>(), st);
     });
     timed(cd, "rans_compact", 0, 0, 3, st, [&] {
         launch_rans_compact(g, B, cd->scratch.as<uint16_t>(), cd->counts.as<int64_t>(), cd->sub_off.as<int64_t>(),
-                            cd->frame_bytes.as<int64_t>(), cd->offs.as<int64_t>(), cd->data.as<uint8_t>(), st);
+                            cd->frame_bytes.as<int64_t>(), bb->offs.as<int64_t>(), bb->data.as<uint8_t>(), st);
     });
-    LIC_CUDA_TRY(cudaMemcpyAsync(cd->h_offs.p, cd->offs.p, (2 * (size_t)B + 1) * sizeof(int64_t),
+    LIC_CUDA_TRY(cudaMemcpyAsync(bb->h_offs.p, bb->offs.p, (2 * (size_t)B + 1) * sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, st));
-    fill_out(cd, B, out);
     LIC_CUDA_TRY(cudaGetLastError());
+    bb->live = true;
+    fill_out(bb, B, g.H, g.W, out);
+    return LIC_OK;
+}
+
+// The frame size of a batch: in->H, in->W, else frame 0's header (copied
+// from the device when the batch lives there).
+int batch_frame_size(const lic_bitstreams *in, int *H, int *W, cudaStream_t st) {
+    if (in->H > 0 && in->W > 0) {
+        *H = in->H;
+        *W = in->W;
+        return LIC_OK;
+    }
+    if (in->H != 0 || in->W != 0 || !in->data) return LIC_E_INVALID_ARG;
+    uint8_t head[36];
+    int64_t off = 0, size = 0;
+    if (in->on_device) {
+        if (!in->d_offsets || !in->d_sizes) return LIC_E_INVALID_ARG;
+        LIC_CUDA_TRY(cudaStreamSynchronize(st));
+        LIC_CUDA_TRY(cudaMemcpy(&off, in->d_offsets, 8, cudaMemcpyDeviceToHost));
+        LIC_CUDA_TRY(cudaMemcpy(&size, in->d_sizes, 8, cudaMemcpyDeviceToHost));
+        if (off < 0) return LIC_E_INVALID_ARG;
+        if (size < 36) return LIC_E_CORRUPT_STREAM;
+        LIC_CUDA_TRY(cudaMemcpy(head, in->data + off, 36, cudaMemcpyDeviceToHost));
+    } else {
+        if (!in->offsets || !in->sizes) return LIC_E_INVALID_ARG;
+        off = in->offsets[0];
+        size = in->sizes[0];
+        if (off < 0) return LIC_E_INVALID_ARG;
+        if (size < 36) return LIC_E_CORRUPT_STREAM;
+        memcpy(head, in->data + off, 36);
+    }
+    int kind = 0;
+    if (lic_decoded_shape(head, 36, &kind, H, W) != LIC_OK || *H < 1 || *W < 1) return LIC_E_CORRUPT_STREAM;
     return LIC_OK;
 }
 
@@ -919,6 +1018,7 @@ int codec_entropy_view(const lic_codec *cd, CodecEntropyView *out) {
     out->N = cd->N;
     out->M = cd->M;
     out->R = cd->opt.band_rows;
+    out->device = cd->device;
     out->tables = cd->dt;
     return LIC_OK;
 }
@@ -1012,6 +1112,7 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
     if (cd->opt.norm != LIC_NORM_GDN && cd->opt.norm != LIC_NORM_1DN) return LIC_E_INVALID_ARG;
     if (cd->opt.precision < LIC_FP32 || cd->opt.precision > LIC_FP8) return LIC_E_UNSUPPORTED;
     if (cd->opt.precision != LIC_FP32 && cd->opt.conv_impl == LIC_CONV_SIMT) return LIC_E_UNSUPPORTED;
+    AllocScope scope(&cd->device_bytes);
     LIC_CUDA_TRY(cudaGetDevice(&cd->device));
     for (int i = 0; i < 3; ++i) {
         LIC_CUDA_TRY(cudaStreamCreateWithFlags(&cd->aux[i], cudaStreamNonBlocking));
@@ -1155,6 +1256,7 @@ int lic_sync(lic_codec *cd, void *stream) {
 
 int lic_encode(lic_codec *cd, const float *frames, int B, int H, int W, lic_bitstreams *out, void *stream) {
     if (!cd || !frames || !out || B < 1 || H < 1 || W < 1) return LIC_E_INVALID_ARG;
+    AllocScope scope(&cd->device_bytes);
     cudaStream_t st = S(stream);
     const int Hp = pad64(H), Wp = pad64(W);
     int rc = ensure_workspace(cd, B, Hp, Wp);
@@ -1193,19 +1295,35 @@ int lic_encode(lic_codec *cd, const float *frames, int B, int H, int W, lic_bits
 
 int lic_encode_latents(lic_codec *cd, const int32_t *s_y, const uint8_t *idx, const int32_t *s_z, int B, int H, int W,
                        int Hy, int Wy, lic_bitstreams *out, void *stream) {
-    if (!cd || !s_y || !out || B < 1 || Hy < 1 || Wy < 1) return LIC_E_INVALID_ARG;
+    if (!cd || !s_y || !out || B < 1 || H < 1 || W < 1 || Hy < 1 || Wy < 1) return LIC_E_INVALID_ARG;
     if (cd->kind == LIC_HYPERPRIOR && (!idx || !s_z || Hy % 4 || Wy % 4)) return LIC_E_INVALID_ARG;
     if (!is_device_ptr(s_y) || (idx && !is_device_ptr(idx)) || (s_z && !is_device_ptr(s_z))) return LIC_E_INVALID_ARG;
+    AllocScope scope(&cd->device_bytes);
     StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, 16 * Hy, 16 * Wy, cd->opt.band_rows);
     return entropy_encode(cd, g, B, s_y, idx, s_z, out, S(stream));
 }
 
-int lic_decode_latents(lic_codec *cd, const lic_bitstreams *in, int H, int W, int32_t *s_y, int32_t *s_z,
-                       void *stream) {
-    if (!cd || !in || !s_y || in->count < 1 || H < 1 || W < 1) return LIC_E_INVALID_ARG;
+int lic_bitstreams_release(lic_codec *cd, lic_bitstreams *bs) {
+    if (!cd || !bs) return LIC_E_INVALID_ARG;
+    if (!bs->owner) return bs->count == 0 ? LIC_OK : LIC_E_INVALID_ARG;
+    for (auto &p : cd->batches)
+        if (p.get() == bs->owner) {
+            if (!p->live) return LIC_E_INVALID_ARG;
+            p->live = false;
+            *bs = lic_bitstreams{};
+            return LIC_OK;
+        }
+    return LIC_E_INVALID_ARG;
+}
+
+int lic_decode_latents(lic_codec *cd, const lic_bitstreams *in, int32_t *s_y, int32_t *s_z, void *stream) {
+    if (!cd || !in || !s_y || in->count < 1) return LIC_E_INVALID_ARG;
+    AllocScope scope(&cd->device_bytes);
     cudaStream_t st = S(stream);
-    int rc = entropy_decode(cd, in, H, W, st);
+    int H = 0, W = 0;
+    int rc = batch_frame_size(in, &H, &W, st);
     if (rc) return rc;
+    if ((rc = entropy_decode(cd, in, H, W, st))) return rc;
     const int B = in->count, Hp = pad64(H), Wp = pad64(W);
     const int64_t ny = (int64_t)B * cd->M * (Hp / 16) * (Wp / 16);
     LIC_CUDA_TRY(cudaMemcpyAsync(s_y, cd->s_y.p, ny * 4, cudaMemcpyDefault, st));
@@ -1216,11 +1334,14 @@ int lic_decode_latents(lic_codec *cd, const lic_bitstreams *in, int H, int W, in
     return LIC_OK;
 }
 
-int lic_decode(lic_codec *cd, const lic_bitstreams *in, int H, int W, float *frames, void *stream) {
-    if (!cd || !in || !frames || in->count < 1 || H < 1 || W < 1) return LIC_E_INVALID_ARG;
+int lic_decode(lic_codec *cd, const lic_bitstreams *in, float *frames, void *stream) {
+    if (!cd || !in || !frames || in->count < 1) return LIC_E_INVALID_ARG;
+    AllocScope scope(&cd->device_bytes);
     cudaStream_t st = S(stream);
-    int rc = entropy_decode(cd, in, H, W, st);
+    int H = 0, W = 0;
+    int rc = batch_frame_size(in, &H, &W, st);
     if (rc) return rc;
+    if ((rc = entropy_decode(cd, in, H, W, st))) return rc;
     const int B = in->count, Hp = pad64(H), Wp = pad64(W);
     rc = (cd->student && cd->stu_checked) ? checked_synthesis(cd, B, Hp, Wp, H, W, st)
                                           : synthesis(cd, cd->yhat.as<float>(), B, Hp / 16, Wp / 16, st);
@@ -1239,6 +1360,23 @@ int lic_decode(lic_codec *cd, const lic_bitstreams *in, int H, int W, float *fra
     }
     LIC_CUDA_TRY(cudaGetLastError());
     return LIC_OK;
+}
+
+int64_t lic_codec_device_bytes(const lic_codec *cd) { return cd ? cd->device_bytes : LIC_E_INVALID_ARG; }
+
+int64_t lic_codec_workspace_bytes(const lic_codec *cd, int B, int H, int W) {
+    if (!cd || B < 1 || H < 1 || W < 1) return LIC_E_INVALID_ARG;
+    lic_codec *c = const_cast<lic_codec *>(cd);   // the plans only name the buffers
+    const int Hp = pad64(H), Wp = pad64(W);
+    int64_t total = 0;
+    auto add = [&](DevBuf &, int64_t n) {
+        total += n;
+        return 0;
+    };
+    workspace_plan(c, B, Hp, Wp, add);
+    lic_codec::Batch probe;
+    entropy_plan(c, make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows), B, &probe, add);
+    return total;
 }
 
 int64_t lic_bitstreams_download(const lic_bitstreams *in, uint8_t *dst, int64_t dst_cap, void *stream) {
@@ -1279,6 +1417,7 @@ extern "C" {
 int lic_codec_set_student(lic_codec *cd, lic_student *student, float min_psnr_db, int checked) {
     if (!cd || (student && student_channels(student) != cd->M) || (checked != 0 && checked != 1))
         return LIC_E_INVALID_ARG;
+    AllocScope scope(&cd->device_bytes);
     if (student && checked && !(min_psnr_db == min_psnr_db)) return LIC_E_INVALID_ARG;
     LIC_CUDA_TRY(cudaDeviceSynchronize());
     LIC_CUDA_TRY(cd->stu_counts.ensure(2 * sizeof(long long)));
@@ -1349,6 +1488,7 @@ static int ingest_nchw(lic_codec *cd, const float *src, int B, int C, int H, int
 
 int lic_analysis(lic_codec *cd, const float *frames, int B, int H, int W, float *y, void *stream) {
     if (!cd || !frames || !y || B < 1 || H < 1 || W < 1) return LIC_E_INVALID_ARG;
+    AllocScope scope(&cd->device_bytes);
     cudaStream_t st = S(stream);
     const int Hp = pad64(H), Wp = pad64(W);
     int rc = ensure_workspace(cd, B, Hp, Wp);
@@ -1361,6 +1501,7 @@ int lic_analysis(lic_codec *cd, const float *frames, int B, int H, int W, float 
 
 int lic_synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, float *x, void *stream) {
     if (!cd || !yhat || !x || B < 1 || Hy < 1 || Wy < 1) return LIC_E_INVALID_ARG;
+    AllocScope scope(&cd->device_bytes);
     cudaStream_t st = S(stream);
     int rc = ensure_workspace(cd, B, 16 * Hy, 16 * Wy);
     if (rc) return rc;
@@ -1371,6 +1512,7 @@ int lic_synthesis(lic_codec *cd, const float *yhat, int B, int Hy, int Wy, float
 
 int lic_hyper_analysis(lic_codec *cd, const float *y, int B, int Hy, int Wy, float *z, void *stream) {
     if (!cd || !y || !z || B < 1 || Hy < 4 || Wy < 4 || Hy % 4 || Wy % 4) return LIC_E_INVALID_ARG;
+    AllocScope scope(&cd->device_bytes);
     if (cd->kind != LIC_HYPERPRIOR) return LIC_E_INVALID_ARG;
     cudaStream_t st = S(stream);
     int rc = ensure_workspace(cd, B, 16 * Hy, 16 * Wy);
@@ -1383,6 +1525,7 @@ int lic_hyper_analysis(lic_codec *cd, const float *y, int B, int Hy, int Wy, flo
 int lic_hyper_synthesis(lic_codec *cd, const float *zhat, int B, int Hz, int Wz, float *sigma, uint8_t *idx,
                         void *stream) {
     if (!cd || !zhat || !sigma || B < 1 || Hz < 1 || Wz < 1) return LIC_E_INVALID_ARG;
+    AllocScope scope(&cd->device_bytes);
     if (cd->kind != LIC_HYPERPRIOR) return LIC_E_INVALID_ARG;
     cudaStream_t st = S(stream);
     int rc = ensure_workspace(cd, B, 64 * Hz, 64 * Wz);
@@ -1400,6 +1543,7 @@ int lic_hyper_synthesis(lic_codec *cd, const float *zhat, int B, int Hz, int Wz,
 
 int lic_read_tensor(lic_codec *cd, int which, void *dst, int64_t *count, void *stream) {
     if (!cd) return LIC_E_INVALID_ARG;
+    AllocScope scope(&cd->device_bytes);
     cudaStream_t st = S(stream);
     const int B = cd->last_B, Hp = cd->last_Hp, Wp = cd->last_Wp;
     const int Hy = Hp / 16, Wy = Wp / 16, Hz = Hp / 64, Wz = Wp / 64;

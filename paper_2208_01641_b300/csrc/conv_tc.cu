@@ -2410,8 +2410,8 @@ void build_weights_e4m3(const float *w, int Cout, int T, int Cin, TcWeights *out
                     (uint8_t)__nv_cvt_float_to_fp8(w[o * K0 + (int64_t)t * Cin + c] / sc[o], __NV_SATFINITE, __NV_E4M3);
     }
     out->cin8 = cin8;
-    if (cudaMalloc(&out->w8, v.size()) != cudaSuccess) return;
-    if (cudaMalloc(&out->w8scale, Cout * sizeof(float)) != cudaSuccess) return;
+    if (dev_malloc(&out->w8, v.size()) != cudaSuccess) return;
+    if (dev_malloc((void **)&out->w8scale, Cout * sizeof(float)) != cudaSuccess) return;
     if (cudaMemcpy(out->w8, v.data(), v.size(), cudaMemcpyHostToDevice) != cudaSuccess) return;
     if (cudaMemcpy(out->w8scale, sc.data(), Cout * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return;
     CUtensorMap *m = new CUtensorMap;
@@ -2431,7 +2431,7 @@ void build_weights_bf16(const float *w, int Cout, int T, int Cin, TcWeights *out
     const int64_t K = (int64_t)T * Cin;
     std::vector<uint16_t> v((size_t)Cout * K);
     for (size_t e = 0; e < v.size(); ++e) v[e] = bf16_rne_host(w[e]);
-    if (cudaMalloc(&out->wb, v.size() * 2) != cudaSuccess) return;
+    if (dev_malloc(&out->wb, v.size() * 2) != cudaSuccess) return;
     if (cudaMemcpy(out->wb, v.data(), v.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return;
     CUtensorMap *m = new CUtensorMap;
     const uint64_t dims[2] = {(uint64_t)K, (uint64_t)Cout};
@@ -2470,8 +2470,8 @@ void build_weights(const float *w, int Cout, int T, int Cin, TcWeights *out) {
             hi[o * K + k] = h;
             lo[o * K + k] = tf32_rna_host(x - hf);
         }
-    if (cudaMalloc(&out->hi, hi.size() * 4) != cudaSuccess) return;
-    if (cudaMalloc(&out->lo, lo.size() * 4) != cudaSuccess) return;
+    if (dev_malloc(&out->hi, hi.size() * 4) != cudaSuccess) return;
+    if (dev_malloc(&out->lo, lo.size() * 4) != cudaSuccess) return;
     if (cudaMemcpy(out->hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return;
     if (cudaMemcpy(out->lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return;
     CUtensorMap *maps = new CUtensorMap[2];

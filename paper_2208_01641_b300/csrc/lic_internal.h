@@ -42,19 +42,41 @@ void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int 
 // device / pinned buffers, pointer kinds
 // ---------------------------------------------------------------------------
 
+// Device bytes allocated through dev_malloc / DevBuf while an AllocScope is
+// active on this thread are added to (and bytes freed subtracted from) its
+// counter: every public entry point of a codec opens one on the codec's own
+// counter, so a codec knows what it holds without asking the device (whose
+// free memory other users of the GPU move).
+extern thread_local int64_t *g_alloc_sink;
+struct AllocScope {
+    int64_t *prev;
+    explicit AllocScope(int64_t *sink) : prev(g_alloc_sink) { g_alloc_sink = sink; }
+    ~AllocScope() { g_alloc_sink = prev; }
+    AllocScope(const AllocScope &) = delete;
+    AllocScope &operator=(const AllocScope &) = delete;
+};
+inline cudaError_t dev_malloc(void **p, size_t n) {
+    cudaError_t e = cudaMalloc(p, n);
+    if (e == cudaSuccess && g_alloc_sink) *g_alloc_sink += (int64_t)n;
+    return e;
+}
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
     ~DevBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            cudaFree(p);
+            if (g_alloc_sink) *g_alloc_sink -= (int64_t)bytes;
+        }
         p = nullptr;
         bytes = 0;
     }
     cudaError_t ensure(size_t n) {
         if (n <= bytes) return cudaSuccess;
         release();
-        cudaError_t e = cudaMalloc(&p, n);
+        cudaError_t e = dev_malloc(&p, n);
         if (e == cudaSuccess) bytes = n;
         else p = nullptr;
         return e;
@@ -384,6 +406,7 @@ void launch_rans_decode(const StreamGeom &g, int B, int part, const DevTables &t
 // live outside api.cu.
 struct CodecEntropyView {
     int kind, N, M, R;
+    int device;      // the CUDA device the codec (and its tables) lives on
     DevTables tables;
 };
 int codec_entropy_view(const lic_codec *codec, CodecEntropyView *out);

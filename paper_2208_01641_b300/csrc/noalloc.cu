@@ -13,6 +13,8 @@
 // would allocate.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "lic_internal.h"
 
 // The working memory of every call on a device: LIC_NOALLOC_SCRATCH_BYTES,
@@ -23,24 +25,27 @@ namespace lic {
 namespace {
 
 constexpr int kMaxDevices = 64;
-void *g_scratch_ptr[kMaxDevices] = {};
+// Per device, the array's device address, published once found.  Two host
+// threads may both look it up the first time; they store the same value.
+// The cache assumes the module stays loaded: after cudaDeviceReset the
+// library's device code is loaded afresh and these addresses are stale.
+std::atomic<void *> g_scratch_ptr[kMaxDevices];
 
 // Device address of the scratch array on the current device, looked up once
 // per device (host code cannot use the array's name as a device address).
-int scratch_address(void **ptr) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return LIC_E_CUDA;
+int scratch_address(int dev, void **ptr) {
     if (dev < 0 || dev >= kMaxDevices) return LIC_E_UNSUPPORTED;
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    void *p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return LIC_E_CUDA;
-        g_scratch_ptr[dev] = p;
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
     }
-    *ptr = g_scratch_ptr[dev];
+    *ptr = p;
     return LIC_OK;
 }
+
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 int64_t align256(int64_t v) { return (v + 255) / 256 * 256; }
 
@@ -56,6 +61,19 @@ extern "C" int lic_encode_latents_noalloc(lic_codec *codec, const int32_t *s_y, 
     if (codec_entropy_view(codec, &v) != LIC_OK) return LIC_E_INVALID_ARG;
     if (!s_y || !data || !d_layout || B < 1 || H < 1 || W < 1 || Hy < 1 || Wy < 1) return LIC_E_INVALID_ARG;
     if (v.kind == LIC_HYPERPRIOR && (!idx || !s_z || Hy % 4 || Wy % 4)) return LIC_E_INVALID_ARG;
+    // The kernels store 32-bit container words into data and 64-bit offsets
+    // into d_layout, and read every input on the device: a host pointer or a
+    // misaligned output is refused here rather than faulting a kernel.
+    if (!is_device_ptr(s_y) || !is_device_ptr(data) || !is_device_ptr(d_layout) ||
+        (v.kind == LIC_HYPERPRIOR && (!is_device_ptr(idx) || !is_device_ptr(s_z))))
+        return LIC_E_INVALID_ARG;
+    if (!aligned(s_y, 4) || !aligned(data, 16) || !aligned(d_layout, 8) ||
+        (v.kind == LIC_HYPERPRIOR && !aligned(s_z, 4)))
+        return LIC_E_INVALID_ARG;
+    // the codec's tables live on its own device: the call must run there
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LIC_E_CUDA;
+    if (dev != v.device) return LIC_E_INVALID_ARG;
     const StreamGeom g = make_geom(v.kind, v.N, v.M, H, W, 16 * Hy, 16 * Wy, v.R);
     const int64_t subs = (int64_t)B * g.nsub;
     // scratch carve-up: words | counts | sub_off | frame_bytes
@@ -68,7 +86,7 @@ extern "C" int lic_encode_latents_noalloc(lic_codec *codec, const int32_t *s_y, 
     const int64_t frame_cap = g.header_bytes + 2 * (int64_t)g.nsub * g.cap_words + 16;
     if (data_cap < (int64_t)B * frame_cap) return LIC_E_INVALID_ARG;
     void *base = nullptr;
-    int rc = scratch_address(&base);
+    int rc = scratch_address(dev, &base);
     if (rc != LIC_OK) return rc;
     unsigned char *p = static_cast<unsigned char *>(base);
     uint16_t *words = reinterpret_cast<uint16_t *>(p);

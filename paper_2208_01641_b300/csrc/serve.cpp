@@ -42,7 +42,7 @@ struct Lane {
     float *in = nullptr, *out = nullptr;     // device slabs, max_batch frames each
     uint32_t *status_host = nullptr;         // pinned: the codec's status word after each batch
     std::vector<cudaGraphExec_t> graphs;     // [b - 1]: encode+decode of b frames
-    lic_bitstreams bs{};                     // sizes of the last batch (pinned, written by the chain)
+    lic_bitstreams last{};                   // view of the last batch: its sizes (pinned, written by the chain)
     bool busy = false;
     std::vector<Request> batch;
     double t_start = 0;
@@ -103,12 +103,21 @@ void destroy_lane(Lane *L) {
 }
 
 // The device part of one batch of b frames: encode, decode, then the codec's
-// status word to the host and cleared (so each batch reports its own).
+// status word to the host and cleared (so each batch reports its own).  The
+// batch goes back to the codec's pool once its decode is enqueued: the next
+// chain on this lane (same stream) reuses the same buffers, so every graph
+// of the lane is captured over one batch buffer.  The view stays in
+// L->last for the sizes the completion callback reads.
 int chain(Lane *L, int b) {
     const Bucket *B = L->bucket;
-    int rc = lic_encode(L->codec, L->in, b, B->H, B->W, &L->bs, L->stream);
+    lic_bitstreams bs{};
+    int rc = lic_encode(L->codec, L->in, b, B->H, B->W, &bs, L->stream);
     if (rc) return rc;
-    if ((rc = lic_decode(L->codec, &L->bs, B->H, B->W, L->out, L->stream))) return rc;
+    L->last = bs;
+    rc = lic_decode(L->codec, &bs, L->out, L->stream);
+    const int rr = lic_bitstreams_release(L->codec, &bs);
+    if (rc) return rc;
+    if (rr) return rr;
     uint32_t *dev_status = lic::codec_status_ptr(L->codec);
     if (cudaMemcpyAsync(L->status_host, dev_status, 4, cudaMemcpyDeviceToHost, L->stream) != cudaSuccess ||
         cudaMemsetAsync(dev_status, 0, 4, L->stream) != cudaSuccess)
@@ -136,7 +145,7 @@ void finish(lic_server *s, Lane *L, int status) {
         x.W = L->bucket->W;
         x.batch = n;
         // the chain's offsets land in the codec's pinned array: b + 1 offsets, then b sizes
-        x.bytes = (status == LIC_OK && L->bs.offsets) ? L->bs.offsets[n + 1 + i] : 0;
+        x.bytes = (status == LIC_OK && L->last.offsets) ? L->last.offsets[n + 1 + i] : 0;
         x.t_submit_ms = r.t_submit;
         x.t_start_ms = L->t_start;
         x.t_done_ms = t;
@@ -241,7 +250,8 @@ void dispatch_loop(lic_server *s) {
     }
 }
 
-int make_lane(lic_server *s, Bucket *B, Lane *L) {
+// Create the lane's codec only (weights and tables, no workspace yet).
+int make_lane_codec(lic_server *s, Bucket *B, Lane *L) {
     L->srv = s;
     L->bucket = B;
     std::vector<lic_param> ps(s->names.size());
@@ -251,15 +261,30 @@ int make_lane(lic_server *s, Bucket *B, Lane *L) {
         ps[i].numel = (int64_t)s->data[i].size();
     }
     lic_weights w{ps.data(), (int)ps.size()};
-    int rc = lic_codec_create((lic_kind)s->kind, s->N, s->M, &w, s->has_copt ? &s->copt : nullptr, &L->codec);
-    if (rc) return rc;
-    const size_t bytes = (size_t)s->opt.max_batch * frame_floats(B) * sizeof(float);
+    return lic_codec_create((lic_kind)s->kind, s->N, s->M, &w, s->has_copt ? &s->copt : nullptr, &L->codec);
+}
+
+size_t slab_bytes(const lic_server *s, const Bucket *B) {
+    return (size_t)s->opt.max_batch * frame_floats(B) * sizeof(float);
+}
+
+// Device bytes the lane holds: its codec's own count and its two slabs.
+int64_t lane_bytes(const lic_server *s, const Lane *L) {
+    const int64_t c = L->codec ? lic_codec_device_bytes(L->codec) : 0;
+    return (c > 0 ? c : 0) + (L->in ? 2 * (int64_t)slab_bytes(s, L->bucket) : 0);
+}
+
+// Slabs, a first pass at the largest batch (every workspace reaches its
+// final size), then one graph per batch size.
+int make_lane(lic_server *s, Bucket *B, Lane *L) {
+    int rc = LIC_OK;
+    if (!L->codec && (rc = make_lane_codec(s, B, L))) return rc;
+    const size_t bytes = slab_bytes(s, B);
     LIC_CUDA_TRY(cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking));
     LIC_CUDA_TRY(cudaMalloc(&L->in, bytes));
     LIC_CUDA_TRY(cudaMalloc(&L->out, bytes));
     LIC_CUDA_TRY(cudaMallocHost(&L->status_host, 16));
     LIC_CUDA_TRY(cudaMemsetAsync(L->in, 0, bytes, L->stream));
-    // first pass at the largest batch: every workspace reaches its final size
     if ((rc = chain(L, s->opt.max_batch))) return rc;
     LIC_CUDA_TRY(cudaStreamSynchronize(L->stream));
     if ((rc = status_code(*L->status_host))) return rc;
@@ -290,37 +315,49 @@ int make_lane(lic_server *s, Bucket *B, Lane *L) {
     return LIC_OK;
 }
 
-// create the bucket of H x W frames (outside the server lock; prep_mu held)
+// Create the bucket of H x W frames (outside the server lock; prep_mu held).
+// Admission by HBM budget: the first lane's codec is created (weights and
+// tables), then the bucket's cost is estimated from the geometry -- per
+// lane, those weights, the workspaces and one bitstream batch that
+// encode + decode of max_batch frames reach (lic_codec_workspace_bytes), and
+// the two frame slabs -- and checked against the budget before any
+// workspace is allocated.  Once built, the bucket is charged what its lanes'
+// codecs counted at each allocation plus the slabs: the device's free
+// memory, which other users of the GPU move, enters neither figure.
 int prepare_locked(lic_server *s, int H, int W) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->buckets.count({H, W})) return LIC_OK;
     }
-    size_t free0 = 0, total = 0;
-    LIC_CUDA_TRY(cudaMemGetInfo(&free0, &total));
     auto B = std::make_unique<Bucket>();
     B->H = H;
     B->W = W;
-    int rc = LIC_OK;
-    for (int l = 0; l < s->opt.lanes && !rc; ++l) {
-        B->lanes.push_back(std::make_unique<Lane>());
-        rc = make_lane(s, B.get(), B->lanes.back().get());
-    }
-    size_t free1 = 0;
-    if (!rc && cudaMemGetInfo(&free1, &total) != cudaSuccess) rc = LIC_E_CUDA;
     int64_t held = 0;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         held = s->st.device_bytes;
     }
-    B->bytes = free0 > free1 ? (int64_t)(free0 - free1) : 0;
-    if (!rc && held + B->bytes > s->opt.hbm_budget) rc = LIC_E_OOM;
-    if (rc) {
+    auto refuse = [&](int rc) {
         for (auto &L : B->lanes) destroy_lane(L.get());
         std::lock_guard<std::mutex> lk(s->mu);
         if (rc == LIC_E_OOM) s->st.refused_budget += 1;
         return rc;
+    };
+    B->lanes.push_back(std::make_unique<Lane>());
+    int rc = make_lane_codec(s, B.get(), B->lanes[0].get());
+    if (rc) return refuse(rc);
+    const int64_t ws = lic_codec_workspace_bytes(B->lanes[0]->codec, s->opt.max_batch, H, W);
+    if (ws < 0) return refuse((int)ws);
+    const int64_t per_lane = lic_codec_device_bytes(B->lanes[0]->codec) + ws + 2 * (int64_t)slab_bytes(s, B.get());
+    if (held + (int64_t)s->opt.lanes * per_lane > s->opt.hbm_budget) return refuse(LIC_E_OOM);
+    for (int l = 0; l < s->opt.lanes && !rc; ++l) {
+        if (l > 0) B->lanes.push_back(std::make_unique<Lane>());
+        rc = make_lane(s, B.get(), B->lanes[l].get());
     }
+    if (rc) return refuse(rc);
+    B->bytes = 0;
+    for (auto &L : B->lanes) B->bytes += lane_bytes(s, L.get());
+    if (held + B->bytes > s->opt.hbm_budget) return refuse(LIC_E_OOM);
     std::lock_guard<std::mutex> lk(s->mu);
     s->st.device_bytes += B->bytes;
     s->st.buckets += 1;

@@ -63,7 +63,7 @@ def test_1dn_codec_bitstreams_and_roundtrip(W1):
         subs = O.encode_latents(oc, sy[b], idx[b], sz[b])
         assert got[b] == O.pack_frame(1, N, M, 100, 150, 128, 192, oc.R, subs)
     out = torch.empty(2, 3, 100, 150, device="cuda")
-    c.decode(bs, 100, 150, out)
+    c.decode(bs, out)
     assert c.sync_status() == lic.OK
     ref, inter = O.decode(oc, got)
     assert np.abs(out.cpu().numpy() - ref).max() <= TOL

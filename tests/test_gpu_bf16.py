@@ -49,7 +49,7 @@ def test_precision_form_against_fp64(setup, kind, prec, capsys):
     if kind == 1:
         idx_enc = np.zeros((B, M, Hy, Wy), np.uint8)
         c.read_tensor(lic.T_IDX, idx_enc)
-    c.decode(bs, H, Wd, out)
+    c.decode(bs, out)
     assert c.sync_status() == lic.OK
     sy_dec = np.zeros_like(sy)
     c.read_tensor(lic.T_SY, sy_dec)

@@ -18,13 +18,13 @@ def test_bounded_wait_runs_out_and_the_context_survives():
     c = lic.Codec(lic.HYPERPRIOR, 64, 96, W)
     x = torch.from_numpy(synth.make_frames(2, 64, 64, first=3)).cuda()
     out = torch.empty_like(x)
-    c.decode(c.encode(x), 64, 64, out)
+    c.decode(c.encode(x), out)
     assert c.sync_status() == lic.OK
     ref = out.clone()
     c.test_bounded_wait(2_000_000)   # about a millisecond of SM clock
     assert c.sync_status() == lic.E_TIMEOUT
     assert c.sync_status() == lic.OK   # reported once, then cleared
-    c.decode(c.encode(x), 64, 64, out)
+    c.decode(c.encode(x), out)
     assert c.sync_status() == lic.OK
     assert torch.equal(out, ref)
     with pytest.raises(lic.LicError):

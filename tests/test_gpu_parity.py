@@ -114,13 +114,13 @@ def test_batch_does_not_change_a_frames_arithmetic(codecs):
     x = synth.make_frames(3, 128, 192, first=60)
     bs = c.encode(dev(x))
     out3 = torch.empty(3, 3, 128, 192, device="cuda")
-    c.decode(bs, 128, 192, out3)
+    c.decode(bs, out3)
     assert c.sync_status() == lic.OK
     b3 = bs.to_bytes()
     for i in range(3):
         bi = c.encode(dev(x[i:i + 1]))
         out1 = torch.empty(1, 3, 128, 192, device="cuda")
-        c.decode(bi, 128, 192, out1)
+        c.decode(bi, out1)
         assert c.sync_status() == lic.OK
         assert bi.to_bytes()[0] == b3[i], i
         assert torch.equal(out1[0], out3[i]), i
@@ -176,7 +176,7 @@ def test_roundtrip_lossless_and_decoder_matches_oracle(codecs, ocodecs, weights,
     c, oc = codecs[(kind, lic.CONV_AUTO)], ocodecs[kind]
     bs, g = encode_and_read(c, x)
     out = torch.empty(2, 3, 70, 130, device="cuda")
-    c.decode(bs, 70, 130, out)
+    c.decode(bs, out)
     assert c.sync_status() == lic.OK
     sy = np.zeros_like(g["s_y"])
     c.read_tensor(lic.T_SY, sy)
@@ -192,7 +192,7 @@ def test_roundtrip_lossless_and_decoder_matches_oracle(codecs, ocodecs, weights,
     assert np.abs(out.cpu().numpy() - ref).max() <= TOL
     # host-resident input bitstreams and host output frames
     host_out = np.zeros((2, 3, 70, 130), np.float32)
-    c.decode(lic.host_bitstreams(g["bytes"]), 70, 130, host_out)
+    c.decode(lic.host_bitstreams(g["bytes"]), host_out)
     assert c.sync_status() == lic.OK
     assert np.array_equal(host_out, out.cpu().numpy())
 
@@ -245,7 +245,7 @@ def test_entropy_adversarial_factorized(codecs, ocodecs):
         subs = O.encode_latents(oc, sy[b])
         assert got[b] == O.pack_frame(0, N, M, 320, 192, 16 * Hy, 16 * Wy, oc.R, subs)
     out_y = torch.empty(B, M, Hy, Wy, dtype=torch.int32, device="cuda")
-    c.decode_latents(bs, 320, 192, out_y)
+    c.decode_latents(bs, out_y)
     assert c.sync_status() == lic.OK
     assert np.array_equal(out_y.cpu().numpy(), sy)
 
@@ -275,7 +275,7 @@ def test_entropy_adversarial_hyperprior(codecs, ocodecs):
         assert got[b] == O.pack_frame(1, N, M, 320, 192, 16 * Hy, 16 * Wy, oc.R, subs)
     out_y = torch.empty(B, M, Hy, Wy, dtype=torch.int32, device="cuda")
     out_z = torch.empty(B, N, Hy // 4, Wy // 4, dtype=torch.int32, device="cuda")
-    c.decode_latents(bs, 320, 192, out_y, out_z)
+    c.decode_latents(bs, out_y, out_z)
     assert c.sync_status() == lic.OK
     assert np.array_equal(out_z.cpu().numpy(), sz)
     assert np.array_equal(out_y.cpu().numpy(), sy)
@@ -288,24 +288,27 @@ def test_corrupt_and_truncated_streams_are_reported(codecs):
     good = bs.to_bytes()[0]
     out = torch.empty(1, 3, 64, 64, device="cuda")
     # truncated payload
-    c.decode(lic.host_bitstreams([good[: len(good) // 2]]), 64, 64, out)
+    c.decode(lic.host_bitstreams([good[: len(good) // 2]]), out)
     assert c.sync_status() == lic.E_CORRUPT_STREAM
-    # wrong magic
-    c.decode(lic.host_bitstreams([b"XXXX" + good[4:]]), 64, 64, out)
+    # wrong magic: with the frame size given, the device's header check latches it ...
+    c.decode(lic.host_bitstreams([b"XXXX" + good[4:]], 64, 64), out)
     assert c.sync_status() == lic.E_CORRUPT_STREAM
+    # ... and with the size to be read from that header, the call refuses it at once
+    assert c.decode_status(lic.host_bitstreams([b"XXXX" + good[4:]]), out) == lic.E_CORRUPT_STREAM
+    assert c.sync_status() == lic.OK
     # offset table pointing past the payload
     bad = bytearray(good)
     bad[36 + 4:36 + 8] = (0xFFFFFF).to_bytes(4, "little")
-    c.decode(lic.host_bitstreams([bytes(bad)]), 64, 64, out)
+    c.decode(lic.host_bitstreams([bytes(bad)]), out)
     assert c.sync_status() == lic.E_CORRUPT_STREAM
     # random payload bytes: decoding ends (either way) and the context stays usable
     rng = np.random.default_rng(0)
     noisy = bytearray(good)
     hdr = 36 + 4 * (N + M * 1 + 1)
     noisy[hdr:] = rng.integers(0, 256, len(good) - hdr, dtype=np.uint8).tobytes()
-    c.decode(lic.host_bitstreams([bytes(noisy)]), 64, 64, out)
+    c.decode(lic.host_bitstreams([bytes(noisy)]), out)
     assert c.sync_status() in (lic.OK, lic.E_CORRUPT_STREAM)
-    c.decode(lic.host_bitstreams([good]), 64, 64, out)
+    c.decode(lic.host_bitstreams([good]), out)
     assert c.sync_status() == lic.OK
 
 
@@ -321,7 +324,7 @@ def test_full_size_720p_batch8_sampled(codecs, ocodecs, weights):
     xd = dev(x)
     bs = c.encode(xd)
     out = torch.empty(B, 3, H, W, device="cuda")
-    c.decode(bs, H, W, out)
+    c.decode(bs, out)
     assert c.sync_status() == lic.OK
     Hy, Wy = 48, 80
     y = np.zeros((B, M, Hy, Wy), np.float32)

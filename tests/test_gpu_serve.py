@@ -4,16 +4,22 @@ A frame served in a mix -- batched with other frames of its resolution, on
 one of several lanes, while other resolutions run concurrently, replayed
 from a CUDA graph -- gives the same bitstream size and the same
 reconstruction, bit for bit, as the same frame encoded and decoded alone by
-a plain codec; the codec's results are per frame."""
+a plain codec; the codec's results are per frame.  For the FP32 chain at the
+configured width (N=128, M=192), the bitstream of one frame per resolution
+is also decoded by the FP64 oracle: its symbols must equal the GPU
+decoder's and its reconstruction must lie within 1e-4 of the served frame,
+so the served results are pinned to the oracle, not only to the library."""
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import paper_2208_01641_b300 as lic
 from paper_2208_01641_b300 import synth
 
 pytestmark = pytest.mark.gpu
-N, M = 64, 96
+N, M = 128, 192
+TOL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -21,19 +27,31 @@ def W():
     return synth.make_weights(lic.HYPERPRIOR, N, M)
 
 
-def alone(W, frame, precision, n=N, m=M):
+def alone(W, frame, precision, n=N, m=M, oracle=None):
+    """(bitstream size, reconstruction) of the frame coded by a plain codec;
+    with oracle = an O.Codec, also checks that bitstream against the oracle."""
     c = lic.Codec(lic.HYPERPRIOR, n, m, W, precision=precision)
     x = torch.from_numpy(frame[None]).cuda()
     bs = c.encode(x)
     out = torch.empty_like(x)
-    c.decode(bs, x.shape[2], x.shape[3], out)
+    c.decode(bs, out)
     size = bs.sizes()[0]
+    if oracle is not None:
+        H, Wd = frame.shape[1:]
+        Hy, Wy = (H + 63) // 64 * 4, (Wd + 63) // 64 * 4
+        sy = np.zeros((1, m, Hy, Wy), np.int32)
+        c.read_tensor(lic.T_SY, sy)
+        ref, inter = O.decode(oracle, bs.to_bytes())
+        assert np.array_equal(inter[0]["s_y"], sy[0]), "oracle decodes other symbols"
+        err = float(np.abs(out.cpu().numpy() - ref).max())
+        assert err <= TOL, f"served frame {frame.shape} vs oracle: {err}"
     c.close()
     return size, out[0].cpu()
 
 
 @pytest.mark.parametrize("graphs", [True, False])
 def test_served_frames_equal_frames_coded_alone(W, graphs):
+    oc = O.Codec(lic.HYPERPRIOR, N, M, W) if graphs else None
     shapes = [(64, 96)] * 5 + [(128, 128)] * 3 + [(64, 96)] * 2
     frames = [synth.make_frame(40 + i, h, w) for i, (h, w) in enumerate(shapes)]
     srv = lic.Server(lic.HYPERPRIOR, N, M, W, max_batch=3, lanes=2, graphs=graphs, max_wait_ms=1.0)
@@ -52,11 +70,14 @@ def test_served_frames_equal_frames_coded_alone(W, graphs):
         assert st["graph_replays"] >= 1
     else:
         assert st["graph_replays"] == 0
+    checked = set()
     for i, f in enumerate(frames):
         r = res[i]
         assert r["status"] == 0 and (r["H"], r["W"]) == shapes[i] and r["stream_id"] == i % 4
         assert r["t_submit_ms"] <= r["t_start_ms"] <= r["t_done_ms"]
-        size, x = alone(W, f, lic.FP32)
+        first_of_shape = oc is not None and shapes[i] not in checked
+        checked.add(shapes[i])
+        size, x = alone(W, f, lic.FP32, oracle=oc if first_of_shape else None)
         assert r["bytes"] == size, i
         assert torch.equal(outs[i].cpu(), x), i
     srv.close()
@@ -89,6 +110,23 @@ def test_server_admission(W):
     assert e.value.code == lic.E_OOM
     assert tiny.stats()["refused_budget"] == 1 and tiny.stats()["buckets"] == 0
     tiny.close()
+    # the budget is charged what the lanes' codecs count, not the device's
+    # free memory: two lanes of one resolution hold at least the estimate of
+    # their workspaces, and a budget just below that sum is refused before
+    # the workspaces are made
+    probe = lic.Codec(lic.HYPERPRIOR, N, M, W)
+    per_lane = probe.device_bytes() + probe.workspace_bytes(2, 64, 64) + 2 * 2 * 3 * 64 * 64 * 4
+    probe.close()
+    srv = lic.Server(lic.HYPERPRIOR, N, M, W, max_batch=2, lanes=2, hbm_budget=2 * per_lane - 1)
+    with pytest.raises(lic.LicError) as e:
+        srv.prepare(64, 64)
+    assert e.value.code == lic.E_OOM
+    srv.close()
+    srv = lic.Server(lic.HYPERPRIOR, N, M, W, max_batch=2, lanes=2, hbm_budget=4 * per_lane)
+    srv.prepare(64, 64)
+    held = srv.stats()["device_bytes"]
+    assert 2 * per_lane <= held <= 4 * per_lane, (held, per_lane)
+    srv.close()
     # one request admitted (it waits in its bucket for a second frame), the next refused
     srv = lic.Server(lic.HYPERPRIOR, N, M, W, max_batch=2, max_pending=1, max_wait_ms=1e7)
     srv.submit(0, f)

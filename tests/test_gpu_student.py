@@ -146,7 +146,7 @@ def test_decode_with_student(SW):
     x = synth.make_frames(2, 120, 100, first=11)
     bs = codec.encode(torch.from_numpy(x).cuda())
     teacher = torch.empty(2, 3, 120, 100, device="cuda")
-    codec.decode(bs, 120, 100, teacher)
+    codec.decode(bs, teacher)
     sy = np.zeros((2, M, 8, 8), np.int32)
     codec.read_tensor(lic.T_SY, sy)
     oc = O.Codec(0, 128, M, W)
@@ -159,13 +159,13 @@ def test_decode_with_student(SW):
 
     codec.set_student(st)
     got_s = torch.empty_like(teacher)
-    codec.decode(bs, 120, 100, got_s)
+    codec.decode(bs, got_s)
     torch.cuda.synchronize()
     assert np.abs(got_s.cpu().numpy() - want_s).max() <= 1e-4
 
     codec.set_student(st, min_psnr_db=1000.0, checked=True)
     fb = torch.empty_like(teacher)
-    codec.decode(bs, 120, 100, fb)
+    codec.decode(bs, fb)
     torch.cuda.synchronize()
     assert torch.equal(fb, teacher)
     frames, falls, ps = codec.student_report()
@@ -177,14 +177,14 @@ def test_decode_with_student(SW):
 
     codec.set_student(st, min_psnr_db=-np.inf, checked=True)
     ok = torch.empty_like(teacher)
-    codec.decode(bs, 120, 100, ok)
+    codec.decode(bs, ok)
     torch.cuda.synchronize()
     assert torch.equal(ok, got_s)
     assert codec.student_report()[:2] == (2, 0)
 
     codec.set_student(None)
     back = torch.empty_like(teacher)
-    codec.decode(bs, 120, 100, back)
+    codec.decode(bs, back)
     torch.cuda.synchronize()
     assert torch.equal(back, teacher)
     codec.close()
@@ -269,7 +269,7 @@ def test_bf16_student_training_and_decode(SW):
     bs = codec.encode(torch.from_numpy(x).cuda())
     codec.set_student(st)
     got = torch.empty(2, 3, 120, 100, device="cuda")
-    codec.decode(bs, 120, 100, got)
+    codec.decode(bs, got)
     yhat = torch.empty(2, M, 8, 8, device="cuda")
     codec.read_tensor(lic.T_YHAT, yhat)
     ref = torch.empty(2, 3, 128, 128, device="cuda")
@@ -318,14 +318,14 @@ def test_trained_student_gain_over_teacher_and_untrained(SW):
     for i in range(P):
         fr = torch.from_numpy(synth.make_frames(1, H, Wd, first=600 + i)).cuda()
         out = torch.empty_like(fr)
-        codec.decode(codec.encode(fr), H, Wd, out)
+        codec.decode(codec.encode(fr), out)
         codec.read_tensor(lic.T_YHAT, pool_y[i:i + 1])
         codec.read_tensor(lic.T_XPRE, pool_x[i:i + 1])
     val = torch.from_numpy(synth.make_frames(2, H, Wd, first=700)).cuda()
     bs = codec.encode(val)
     teacher = torch.empty_like(val)
     codec.profile(True)
-    codec.decode(bs, H, Wd, teacher)
+    codec.decode(bs, teacher)
     gs_flop = sum(r["flop"] for r in codec.profile_report() if r["name"].startswith("g_s."))
     codec.profile(False)
 
@@ -333,7 +333,7 @@ def test_trained_student_gain_over_teacher_and_untrained(SW):
 
     def psnr_vs_teacher():
         codec.set_student(st, min_psnr_db=99.0, checked=True)
-        codec.decode(bs, H, Wd, torch.empty_like(val))
+        codec.decode(bs, torch.empty_like(val))
         ps = codec.student_report()[2]
         codec.set_student(None)
         return float(np.mean(ps))

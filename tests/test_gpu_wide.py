@@ -80,7 +80,7 @@ def test_wide_fp32_bitstreams_and_roundtrip(W):
         subs = O.encode_latents(oc, sy[b], idx[b], sz[b])
         assert got[b] == O.pack_frame(1, N, M, 100, 150, 128, 192, oc.R, subs)
     out = torch.empty(2, 3, 100, 150, device="cuda")
-    c.decode(bs, 100, 150, out)
+    c.decode(bs, out)
     assert c.sync_status() == lic.OK
     ref, _ = O.decode(oc, got)
     assert np.abs(out.cpu().numpy() - ref).max() <= TOL
@@ -106,7 +106,7 @@ def test_wide_precision_form(W, prec, capsys):
     c.read_tensor(lic.T_Y, y)
     c.read_tensor(lic.T_IDX, idx_enc)
     out = torch.empty(B, 3, H, Wd, device="cuda")
-    c.decode(bs, H, Wd, out)
+    c.decode(bs, out)
     assert c.sync_status() == lic.OK
     sy_dec = np.zeros_like(sy)
     idx_dec = np.zeros_like(idx_enc)

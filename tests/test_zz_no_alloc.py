@@ -81,3 +81,59 @@ def test_noalloc_refuses_oversized_and_short_buffers():
         == lic.E_INVALID_ARG
     assert codec.sync_status() == lic.OK
     codec.close()
+
+
+def test_noalloc_refuses_host_and_misaligned_buffers():
+    """Pointers the kernels could not use are refused before any launch: a
+    host output buffer, a container buffer not 16-byte aligned, an offset
+    table not 8-byte aligned, and host symbols."""
+    Wt = synth.make_weights(1, N, M)
+    codec = lic.Codec(1, N, M, Wt)
+    B, H, W, Hy, Wy = 1, 64, 64, 4, 4
+    sy = torch.zeros(B, M, Hy, Wy, dtype=torch.int32, device="cuda")
+    idx = torch.zeros(B, M, Hy, Wy, dtype=torch.uint8, device="cuda")
+    sz = torch.zeros(B, N, 1, 1, dtype=torch.int32, device="cuda")
+    cap = B * frame_cap(1, Hy, Wy)
+    data = torch.zeros(cap + 64, dtype=torch.uint8, device="cuda")
+    layout = torch.zeros(2 * B + 2, dtype=torch.int64, device="cuda")
+    L = lic.lib()
+
+    def call(sy_p, data_p, cap_, lay_p):
+        return L.lic_encode_latents_noalloc(codec.h, sy_p, idx.data_ptr(), sz.data_ptr(), B, H, W, Hy, Wy,
+                                            data_p, cap_, lay_p, torch.cuda.current_stream().cuda_stream)
+
+    host_data = np.zeros(cap + 64, np.uint8)
+    host_sy = np.zeros(B * M * Hy * Wy, np.int32)
+    assert call(sy.data_ptr(), host_data.ctypes.data, cap, layout.data_ptr()) == lic.E_INVALID_ARG
+    assert call(sy.data_ptr(), data.data_ptr() + 1, cap, layout.data_ptr()) == lic.E_INVALID_ARG
+    assert call(sy.data_ptr(), data.data_ptr(), cap, layout.data_ptr() + 4) == lic.E_INVALID_ARG
+    assert call(host_sy.ctypes.data, data.data_ptr(), cap, layout.data_ptr()) == lic.E_INVALID_ARG
+    assert call(sy.data_ptr(), data.data_ptr(), cap, layout.data_ptr()) == lic.OK
+    assert codec.sync_status() == lic.OK
+    codec.close()
+
+
+def test_noalloc_at_a_new_larger_batch_allocates_nothing():
+    """After one call, a call at a batch size the codec has never coded
+    leaves the device's free memory and the codec's own count unchanged."""
+    Wt = synth.make_weights(1, N, M)
+    codec = lic.Codec(1, N, M, Wt)
+    H, W, Hy, Wy = 128, 192, 8, 12
+    bufs = {}
+    for B in (1, 3):
+        bufs[B] = (torch.zeros(B, M, Hy, Wy, dtype=torch.int32, device="cuda"),
+                   torch.zeros(B, M, Hy, Wy, dtype=torch.uint8, device="cuda"),
+                   torch.zeros(B, N, Hy // 4, Wy // 4, dtype=torch.int32, device="cuda"),
+                   torch.zeros(B * frame_cap(1, Hy, Wy), dtype=torch.uint8, device="cuda"),
+                   torch.zeros(2 * B + 1, dtype=torch.int64, device="cuda"))
+    sy, idx, sz, data, layout = bufs[1]
+    assert codec.encode_latents_noalloc(sy, idx, sz, H, W, data, layout) == lic.OK
+    torch.cuda.synchronize()
+    free0, held0 = torch.cuda.mem_get_info()[0], codec.device_bytes()
+    sy, idx, sz, data, layout = bufs[3]
+    assert codec.encode_latents_noalloc(sy, idx, sz, H, W, data, layout) == lic.OK
+    torch.cuda.synchronize()
+    assert codec.sync_status() == lic.OK
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert codec.device_bytes() == held0
+    codec.close()
