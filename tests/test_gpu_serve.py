@@ -27,6 +27,44 @@ def W():
     return synth.make_weights(lic.HYPERPRIOR, N, M)
 
 
+def oracle_check(c, oc, blob, out, H, Wd):
+    """The parity rules on one frame's bitstream and reconstruction: the
+    oracle decodes the bytes with the GPU decoder's own indices to the GPU
+    decoder's symbols (integer stages, exact); those indices differ from the
+    FP64 chain's only beside a scale-table edge; the oracle's g_s of the same
+    y_hat is within TOL of the served frame (float stage)."""
+    hdr = O.unpack_frame(blob)
+    n, m, R = hdr["N"], hdr["M"], hdr["R"]
+    Hy, Wy = hdr["Hp"] // 16, hdr["Wp"] // 16
+    Hz, Wz = Hy // 4, Wy // 4
+    sy_g = np.zeros((1, m, Hy, Wy), np.int32)
+    sz_g = np.zeros((1, n, Hz, Wz), np.int32)
+    idx_g = np.zeros((1, m, Hy, Wy), np.uint8)
+    c.read_tensor(lic.T_SY, sy_g)
+    c.read_tensor(lic.T_SZ, sz_g)
+    c.read_tensor(lic.T_IDX, idx_g)
+    subs = hdr["subs"]
+    s_z = np.stack([O.rans_decode(subs[ch], Hz * Wz, np.full(Hz * Wz, ch), oc.eb).reshape(Hz, Wz)
+                    for ch in range(n)])
+    assert np.array_equal(s_z, sz_g[0])
+    s_y = np.zeros((m, Hy, Wy), np.int32)
+    k = n
+    for ch in range(m):
+        for r0, r1 in O._bands(Hy, R):
+            t = idx_g[0, ch, r0:r1].ravel().astype(np.int32)
+            s_y[ch, r0:r1] = O.rans_decode(subs[k], t.size, t, oc.gauss).reshape(r1 - r0, Wy)
+            k += 1
+    assert np.array_equal(s_y, sy_g[0])
+    sig = O.h_s(oc.W, O.dequantize(s_z[None], oc.med))
+    bad = O.scale_index(sig.astype(np.float32)) != idx_g
+    T = O.scale_table().astype(np.float64)
+    sg = sig[bad]
+    assert np.all(np.min(np.abs(sg[:, None] - T[None, :]), axis=1) <= TOL * np.maximum(1.0, sg)), int(bad.sum())
+    ref = np.clip(O.g_s(oc.W, s_y[None].astype(np.float32)), 0.0, 1.0)[:, :, :H, :Wd]
+    err = float(np.abs(out - ref).max())
+    assert err <= TOL, f"served frame {H}x{Wd} vs oracle: {err}"
+
+
 def alone(W, frame, precision, n=N, m=M, oracle=None):
     """(bitstream size, reconstruction) of the frame coded by a plain codec;
     with oracle = an O.Codec, also checks that bitstream against the oracle."""
@@ -37,14 +75,7 @@ def alone(W, frame, precision, n=N, m=M, oracle=None):
     c.decode(bs, out)
     size = bs.sizes()[0]
     if oracle is not None:
-        H, Wd = frame.shape[1:]
-        Hy, Wy = (H + 63) // 64 * 4, (Wd + 63) // 64 * 4
-        sy = np.zeros((1, m, Hy, Wy), np.int32)
-        c.read_tensor(lic.T_SY, sy)
-        ref, inter = O.decode(oracle, bs.to_bytes())
-        assert np.array_equal(inter[0]["s_y"], sy[0]), "oracle decodes other symbols"
-        err = float(np.abs(out.cpu().numpy() - ref).max())
-        assert err <= TOL, f"served frame {frame.shape} vs oracle: {err}"
+        oracle_check(c, oracle, bs.to_bytes()[0], out.cpu().numpy(), *frame.shape[1:])
     c.close()
     return size, out[0].cpu()
 
