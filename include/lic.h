@@ -383,6 +383,16 @@ int64_t lic_codec_device_bytes(const lic_codec *codec);
  * count or INVALID_ARG. */
 int64_t lic_codec_workspace_bytes(const lic_codec *codec, int B, int H, int W);
 
+/* The dense rate of the current device's tensor pipe, measured (no
+ * counterpart in the paper; the roofline context of the convolution
+ * kernels): every SM issues `iters` (1 .. 1e6) tcgen05 MMAs of M = 128,
+ * N = 256 back to back into one tensor-memory accumulator, operands resident
+ * in shared memory; kind 0 = tf32 (K = 8 per MMA), 1 = bf16 (K = 16), 2 =
+ * e4m3 (K = 32).  *tflops = 2 M N K iters SMs / the launch's CUDA-event
+ * time.  Allocates a 4-byte status word and a stream, synchronizes.  Errors:
+ * INVALID_ARG, TIMEOUT (a bounded wait ran out), CUDA. */
+int lic_probe_mma_rate(int kind, int iters, double *tflops);
+
 /* Diagnostics of the failure path (no counterpart in the paper): one GPU
  * thread waits, through the same
  * bounded wait the tensor-core pipelines use, on a barrier that nothing

@@ -39,6 +39,7 @@ EXPORTED = [
     "lic_decode_latents", "lic_build_tables", "lic_scale_table", "lic_strerror",
     "lic_profile_enable", "lic_profile_report", "lic_launch_count", "lic_encode_latents_noalloc",
     "lic_test_bounded_wait", "lic_bitstreams_release", "lic_codec_device_bytes", "lic_codec_workspace_bytes",
+    "lic_probe_mma_rate",
     # include/lic_student.h (learned form)
     "lic_student_create", "lic_student_destroy", "lic_student_grad", "lic_student_step", "lic_student_read",
     "lic_student_read_activation", "lic_student_steps", "lic_student_forward", "lic_student_profile_enable", "lic_student_profile_report",
@@ -147,6 +148,7 @@ def _lib():
         L.lic_launch_count.argtypes = [vp]
         L.lic_launch_count.restype = i64
         L.lic_test_bounded_wait.argtypes = [vp, i64, vp]
+        L.lic_probe_mma_rate.argtypes = [i, i, ctypes.POINTER(ctypes.c_double)]
         L.lic_student_create.argtypes = [ctypes.POINTER(_Weights), i, i, ctypes.POINTER(_StudentOptions),
                                          ctypes.POINTER(vp)]
         L.lic_student_destroy.argtypes = [vp]
@@ -455,6 +457,14 @@ class Codec:
         _check(_lib().lic_decode_latents(self.h, ctypes.byref(s), _ptr(s_y),
                                          _ptr(s_z) if s_z is not None else None, _stream(stream)),
                "lic_decode_latents")
+
+
+def mma_rate(kind: int, iters: int = 20000) -> float:
+    """Measured dense tensor-pipe rate in TFLOP/s (lic_probe_mma_rate):
+    kind 0 tf32, 1 bf16, 2 e4m3."""
+    t = ctypes.c_double()
+    _check(_lib().lic_probe_mma_rate(kind, iters, ctypes.byref(t)), "lic_probe_mma_rate")
+    return t.value
 
 
 def decoded_shape(frame: bytes):

@@ -55,6 +55,10 @@ struct Layer {
     int in_dt = DT_F32, out_dt = DT_F32;   // activation storage of this layer (precision forms)
     float in_scale = 1.f, out_scale = 1.f;   // e4m3 tensors hold x / scale
     std::vector<std::unique_ptr<ConvOp>> ops;
+    // a 1x1 GEMM over packed patches standing for a k x k conv of def_cin
+    // channels: its algorithmic work is that conv's (K = k * k * def_cin), and
+    // the input it reads is the frame, whose bytes the packing launch counts
+    int def_cin = 0, def_k = 0;
 };
 
 struct Gdn {
@@ -309,6 +313,8 @@ int make_patch_layer(Layer &P, const Layer &L, const ParamMap &pm) {
     P.out_dt = L.out_dt;
     P.in_scale = 1.f;
     P.out_scale = L.out_scale;
+    P.def_cin = Cin;
+    P.def_k = k;
     auto op = std::make_unique<ConvOp>();
     op->T = 1;
     std::vector<float> r((size_t)Cout * PATCH_K, 0.f);
@@ -411,9 +417,21 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
         d.out_dt = out_dt;
         d.out_scale = 1.f;
     }
+    // algorithmic work of the definition: 2 x multiply-adds; bytes = the
+    // input read once (a transposed conv's phases share it), the output
+    // written once, the weights, at the storage size of each
     const double rows = (double)B * d.Gh * d.Gw;
-    double flop = 2.0 * rows * d.Cout * d.T * d.Cin;
-    const double bytes = 4.0 * ((double)B * Hi * Wi * d.Cin + rows * d.Cout + (double)d.Cout * d.T * d.Cin);
+    const double esz_in = d.in_dt == DT_F32 ? 4.0 : (d.in_dt == DT_BF16 ? 2.0 : 1.0);
+    const int odt = out_dt >= 0 ? out_dt : d.out_dt;
+    const double esz_out = odt == DT_F32 ? 4.0 : (odt == DT_BF16 ? 2.0 : 1.0);
+    double kdef = (double)d.T * d.Cin;
+    double in_bytes = esz_in * B * Hi * Wi * d.Cin / (L.deconv ? (double)L.ops.size() : 1.0);
+    if (L.def_cin > 0) {   // patch GEMM: the k x k conv it stands for; the frame read is the packing's
+        kdef = (double)L.def_k * L.def_k * L.def_cin;
+        in_bytes = 0.0;
+    }
+    double flop = 2.0 * rows * d.Cout * kdef;
+    const double bytes = in_bytes + esz_out * rows * d.Cout + esz_in * d.Cout * kdef;
     std::string nm = L.name + (L.deconv ? ".p" + std::to_string(2 * op.py + op.px) : std::string());
     if (G) {
         d.fuse_gdn = G->diag ? (G->inverse ? 4 : 3) : (G->inverse ? 2 : 1);
@@ -504,7 +522,7 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
     }
     if (L.deconv && L.w_small.p) {
         const double flop = 2.0 * B * Ho * Wo * L.Cout * L.Cin * 6.25;
-        const double bytes = 4.0 * ((double)B * Hi * Wi * L.Cin + (double)B * Ho * Wo * L.Cout + 100.0 * L.Cin);
+        const double bytes = 4.0 * ((double)B * Hi * Wi * L.Cin + (double)B * Ho * Wo * L.Cout + 25.0 * L.Cout * L.Cin);
         // two passes (the layer's tensor-core weights exist when Cin >= 128): the tap
         // contributions of every input position by a tensor-core 1x1 GEMM (128 columns,
         // the leading 25 * Cout stored) into the scratch buffer (an activation buffer
@@ -538,11 +556,13 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
             d.out_stride = cs;
             if (tc::can_run(d, L.w_scatter)) {
                 const double rows = (double)B * Hi * Wi;
-                timed(const_cast<lic_codec *>(cd), L.name + ":tc", flop, 4.0 * rows * (L.Cin + cs), 1, st, [&] {
-                    if (!tc::launch(d, L.w_scatter, st)) atomic_status(cd, ST_TIMEOUT);
-                });
-                timed(const_cast<lic_codec *>(cd), L.name + ".gather", 0.0,
-                      4.0 * (rows * 25 * L.Cout + (double)B * Ho * Wo * L.Cout), 1, st,
+                // algorithmic bytes: the input and weights for the GEMM, the output for
+                // the gather (the tap contributions in between are this build's staging)
+                timed(const_cast<lic_codec *>(cd), L.name + ":tc", flop, 4.0 * (rows * L.Cin + 25.0 * L.Cout * L.Cin),
+                      1, st, [&] {
+                          if (!tc::launch(d, L.w_scatter, st)) atomic_status(cd, ST_TIMEOUT);
+                      });
+                timed(const_cast<lic_codec *>(cd), L.name + ".gather", 0.0, 4.0 * (double)B * Ho * Wo * L.Cout, 1, st,
                       [&] { launch_deconv_gather(cbuf, B, Hi, Wi, L.Cout, L.bias.as<float>(), out, st); });
                 return;
             }
@@ -751,8 +771,8 @@ void analysis(lic_codec *cd, const float *frames, int B, int Hf, int Wf, int Hp,
     int first = 0;
     if (cd->use_patch) {
         // the first layer's patches straight from the frames (no padded copy)
-        const double rows = (double)B * (Hp / 2) * (Wp / 2);
-        timed(cd, "patch_pack", 0, 12.0 * B * Hf * Wf + 4.0 * rows * PATCH_K, 1, st,
+        // algorithmic bytes: the frame read once (the patch rows are this build's staging)
+        timed(cd, "patch_pack", 0, 12.0 * B * Hf * Wf, 1, st,
               [&] { launch_frame_patch(frames, B, Hf, Wf, Hp, Wp, cd->patches.as<float>(), st); });
         in = run_layer_gdn(cd, cd->ga0p, cd->gdn[0], cd->patches.as<float>(), B, Hp / 2, Wp / 2, a, b, st);
         H /= 2;
@@ -1397,6 +1417,8 @@ int lic_profile_enable(lic_codec *cd, int enable) {
 int lic_profile_report(lic_codec *cd, char *buf, int cap) { return cd ? cd->pf.report(buf, cap) : LIC_E_INVALID_ARG; }
 
 int64_t lic_launch_count(lic_codec *cd) { return cd ? cd->pf.launches : LIC_E_INVALID_ARG; }
+
+int lic_probe_mma_rate(int kind, int iters, double *tflops) { return tc::mma_rate(kind, iters, tflops); }
 
 int lic_test_bounded_wait(lic_codec *cd, int64_t limit_cycles, void *stream) {
     if (!cd || limit_cycles < 1 || limit_cycles > 4000000000LL) return LIC_E_INVALID_ARG;

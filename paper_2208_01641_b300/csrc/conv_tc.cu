@@ -2843,5 +2843,95 @@ void launch_wait_probe(uint32_t *status, long long limit_cycles, cudaStream_t st
     wait_probe_kernel<<<1, 1, 0, st>>>(status, limit_cycles);
 }
 
+// ------------------------------------------------------------------ MMA rate probe
+//
+// The dense rate of the tensor pipe, measured: every CTA (one per SM) issues
+// `iters` tcgen05 MMAs of M = 128, N = 256 back to back into one TMEM
+// accumulator, A (128 x 128 B) and B (256 x 128 B) resident in shared memory,
+// the K step cycling over the four 32-byte quarters of the swizzled row.
+// KIND 0: kind::tf32 (K = 8 per MMA), 1: kind::f16 with bf16 (K = 16),
+// 2: kind::f8f6f4 with e4m3 (K = 32).  The operands hold 1.0 in their format.
+template <int KIND>
+__global__ void __launch_bounds__(128, 1) mma_rate_kernel(int iters, uint32_t *status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint32_t tslot;
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t one = KIND == 0 ? 0x3f800000u : (KIND == 1 ? 0x3f803f80u : 0x38383838u);
+    uint32_t *w = reinterpret_cast<uint32_t *>(smem);
+    for (int i = threadIdx.x; i < (128 + 256) * 128 / 4; i += blockDim.x) w[i] = one;
+    fence_proxy_async();
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    if (threadIdx.x < 32) tmem_alloc(&tslot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t dt = tslot;
+    if (threadIdx.x == 0) {
+        const uint32_t a = smem_u32(smem), b = a + 128 * 128;
+        const uint32_t idesc = KIND == 0 ? idesc_tf32(128, 256) : (KIND == 1 ? idesc_bf16(128, 256) : idesc_e4m3(128, 256));
+        for (int i = 0; i < iters; ++i) {
+            const uint32_t kk = (uint32_t)(i & 3) * 32;
+            if (KIND == 0) mma_tf32(dt, sdesc(a + kk), sdesc(b + kk), idesc, i > 0 ? 1u : 0u);
+            else if (KIND == 1) mma_bf16(dt, sdesc(a + kk), sdesc(b + kk), idesc, i > 0 ? 1u : 0u);
+            else mma_e4m3(dt, sdesc(a + kk), sdesc(b + kk), idesc, i > 0 ? 1u : 0u);
+        }
+        mma_commit(&bar);
+        // the MMAs must have finished before TMEM is released: one more bounded
+        // wait after a first one that ran out
+        if (!mbar_wait(&bar, 0)) {
+            atomicOr(status, ST_TIMEOUT);
+            mbar_wait(&bar, 0);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(dt, 256);
+}
+
+int mma_rate(int kind, int iters, double *tflops) {
+    if (kind < 0 || kind > 2 || iters < 1 || iters > 1000000 || !tflops) return LIC_E_INVALID_ARG;
+    int dev = 0, sms = 0;
+    LIC_CUDA_TRY(cudaGetDevice(&dev));
+    LIC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // more shared memory than two CTAs could share: one CTA per SM
+    const int smem = 160 * 1024;
+    auto kern = kind == 0 ? mma_rate_kernel<0> : (kind == 1 ? mma_rate_kernel<1> : mma_rate_kernel<2>);
+    LIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    uint32_t *status = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = LIC_OK;
+    float ms = 0.f;
+    uint32_t hs = 0;
+    if (cudaMalloc(&status, 4) != cudaSuccess || cudaMemset(status, 0, 4) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        rc = LIC_E_CUDA;
+    } else {
+        kern<<<sms, 128, smem, st>>>(iters / 10 + 1, status);   // warm-up
+        cudaEventRecord(e0, st);
+        kern<<<sms, 128, smem, st>>>(iters, status);
+        cudaEventRecord(e1, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+            cudaMemcpy(&hs, status, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = LIC_E_CUDA;
+        else if (hs)
+            rc = LIC_E_TIMEOUT;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (status) cudaFree(status);
+    if (rc) return rc;
+    const double k = kind == 0 ? 8.0 : (kind == 1 ? 16.0 : 32.0);
+    *tflops = 2.0 * 128.0 * 256.0 * k * (double)iters * sms / (ms * 1e-3) / 1e12;
+    return LIC_OK;
+}
+
 }  // namespace tc
 }  // namespace lic

@@ -68,6 +68,10 @@ bool can_run_lp_map(const ConvDesc &d);
 // The bounded mbarrier wait of the kernels, on a barrier nothing arrives at:
 // gives up after limit_cycles and latches ST_TIMEOUT in *status.
 void launch_wait_probe(uint32_t *status, long long limit_cycles, cudaStream_t st);
+
+// Dense tensor-pipe rate (TFLOP/s) of back-to-back MMAs of M = 128, N = 256
+// on every SM: kind 0 tf32, 1 bf16, 2 e4m3.  Synchronizes; LIC_OK or LIC_E_*.
+int mma_rate(int kind, int iters, double *tflops);
 bool launch_lp_map(const ConvDesc &d, const TmaMap &bmap, cudaStream_t st);
 
 }  // namespace tc

@@ -115,3 +115,13 @@ def test_workspace_estimate_equals_what_encode_and_decode_allocate(W):
     assert c.sync_status() == lic.OK
     assert c.device_bytes() - before == est
     c.close()
+
+
+def test_mma_rate_probe_orders_the_types():
+    """The tensor-pipe probe: dense rates are positive, and per MMA the
+    narrower types do more work in the same time (tf32 < bf16 < e4m3)."""
+    r = [lic.mma_rate(k, 4000) for k in range(3)]
+    assert all(x > 50.0 for x in r), r
+    assert r[0] < r[1] < r[2], r
+    with pytest.raises(lic.LicError):
+        lic.mma_rate(3)
