@@ -95,6 +95,14 @@ def lib():
         L.orc_rans_decode.argtypes = [ctypes.POINTER(ctypes.c_uint16), ctypes.c_int64, ip,
                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_Table),
                                       ctypes.POINTER(ctypes.c_int32)]
+        u16p, u32p, i64p = (ctypes.POINTER(ctypes.c_uint16), ctypes.POINTER(ctypes.c_uint32),
+                            ctypes.POINTER(ctypes.c_int64))
+        L.orc_rans2_encode.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ip,
+                                       ctypes.POINTER(_Table), ip, u16p, ctypes.c_int64, i64p, u32p,
+                                       ctypes.c_int64, i64p, i64p, dp]
+        L.orc_rans2_decode_range.argtypes = [u16p, ctypes.c_int64, ip, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(_Table), u32p, ip, ip,
+                                             ctypes.POINTER(ctypes.c_int32)]
         _lib = L
     return _lib
 
@@ -376,6 +384,49 @@ def rans_decode(words, n, tab_of, tabs):
     return s
 
 
+def rans2_encode(s, tab_of, tabs, S=0, with_stats=False):
+    """One format-2 substream (escape payloads outside the rANS words) and,
+    with S > 0, its resume records (an array of shape (nrec, 35), uint32)."""
+    s = np.ascontiguousarray(s, dtype=np.int32).ravel()
+    t = np.ascontiguousarray(tab_of, dtype=np.int32).ravel()
+    n = len(s)
+    cap = 4 * n + 80
+    out = np.zeros(cap, dtype=np.uint16)
+    ng = (n + 31) // 32
+    nr_max = (ng - 1) // S if (S > 0 and ng > 0) else 0
+    rec = np.zeros(max(1, 35 * nr_max), dtype=np.uint32)
+    ln, nrec = ctypes.c_int64(), ctypes.c_int64()
+    lw = np.zeros(32, dtype=np.int64)
+    lb = np.zeros(32, dtype=np.float64)
+    arr, keep = _ctables(tabs)
+    rc = lib().orc_rans2_encode(_p(s, ctypes.c_int32), _p(t, ctypes.c_int32), n, arr, int(S),
+                                _p(out, ctypes.c_uint16), cap, ctypes.byref(ln), _p(rec, ctypes.c_uint32),
+                                rec.size, ctypes.byref(nrec), _p(lw, ctypes.c_int64), _p(lb, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("rans2 encode failed")
+    words = out[:ln.value].copy()
+    recs = rec[:35 * nrec.value].reshape(nrec.value, 35).copy()
+    return (words, recs, lw, lb) if with_stats else (words, recs)
+
+
+def rans2_decode(words, n, tab_of, tabs, rec=None, g0=0, g1=None):
+    """Symbols of groups [g0, g1) of a format-2 substream (all of them by
+    default), from its start or from the resume record of group g0; the
+    returned array has n entries, those outside the range left 0."""
+    w = np.ascontiguousarray(words, dtype=np.uint16)
+    t = np.ascontiguousarray(tab_of, dtype=np.int32).ravel()
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    g1 = (n + 31) // 32 if g1 is None else g1
+    arr, keep = _ctables(tabs)
+    r = None if rec is None else np.ascontiguousarray(rec, dtype=np.uint32)
+    rc = lib().orc_rans2_decode_range(_p(w, ctypes.c_uint16), len(w), n, _p(t, ctypes.c_int32), arr,
+                                      _p(r, ctypes.c_uint32) if r is not None else None, int(g0), int(g1),
+                                      _p(out, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError("corrupt substream")
+    return out[:n]
+
+
 # --------------------------------------------------------------------------
 # frame container (project-defined; little endian)
 #   'LIC1' | u16 version=1 | u16 kind | u16 N | u16 M | u32 H | u32 W |
@@ -386,32 +437,53 @@ def rans_decode(words, n, tab_of, tabs):
 # --------------------------------------------------------------------------
 
 HEADER = struct.Struct("<4sHHHHIIIIHHI")
+REC_U32 = 35   # u32 per resume record (format 2)
 
 
 def pad_size(H, W):
     return (H + 63) // 64 * 64, (W + 63) // 64 * 64
 
 
-def pack_frame(kind, N, M, H, W, Hp, Wp, R, subs):
+def pack_frame(kind, N, M, H, W, Hp, Wp, R, subs, version=1, S=0, recs=None):
+    """Format 1: header, u32 word offsets, substreams.  Format 2 adds the
+    resume-record spacing S in the header's last u16 and, when S > 0, a
+    trailer with every substream's records in order (35 u32 each)."""
     offs = [0]
     for s in subs:
         offs.append(offs[-1] + len(s))
-    head = HEADER.pack(b"LIC1", 1, kind, N, M, H, W, Hp, Wp, R, 0, len(subs))
+    head = HEADER.pack(b"LIC1", version, kind, N, M, H, W, Hp, Wp, R, S if version == 2 else 0, len(subs))
     body = np.concatenate(subs).astype("<u2").tobytes() if subs else b""
-    return head + np.asarray(offs, dtype="<u4").tobytes() + body
+    tail = b""
+    if version == 2 and S > 0 and recs:
+        tail = np.concatenate([np.asarray(r, np.uint32).ravel() for r in recs]).astype("<u4").tobytes()
+    return head + np.asarray(offs, dtype="<u4").tobytes() + body + tail
 
 
 def unpack_frame(buf):
-    (magic, ver, kind, N, M, H, W, Hp, Wp, R, _r, nsub) = HEADER.unpack_from(buf, 0)
-    if magic != b"LIC1" or ver != 1:
+    (magic, ver, kind, N, M, H, W, Hp, Wp, R, S, nsub) = HEADER.unpack_from(buf, 0)
+    if magic != b"LIC1" or ver not in (1, 2) or (ver == 1 and S != 0):
         raise ValueError("bad header")
     offs = np.frombuffer(buf, dtype="<u4", count=nsub + 1, offset=HEADER.size)
     base = HEADER.size + 4 * (nsub + 1)
-    words = np.frombuffer(buf, dtype="<u2", offset=base)
-    if len(words) < offs[-1]:
+    if len(buf) < base + 2 * int(offs[-1]):
         raise ValueError("truncated")
+    words = np.frombuffer(buf, dtype="<u2", count=int(offs[-1]), offset=base)
     subs = [words[offs[i]:offs[i + 1]] for i in range(nsub)]
-    return dict(kind=kind, N=N, M=M, H=H, W=W, Hp=Hp, Wp=Wp, R=R, subs=subs)
+    tail = np.frombuffer(buf, dtype="<u4", offset=base + 2 * int(offs[-1]))
+    return dict(kind=kind, N=N, M=M, H=H, W=W, Hp=Hp, Wp=Wp, R=R, S=S, version=ver, subs=subs, trailer=tail)
+
+
+def strip_records(buf):
+    """A format-2 frame without its resume records: the trailer dropped and
+    S set to 0 (the substreams are unchanged; a decoder then reads each
+    substream from its start)."""
+    h = unpack_frame(buf)
+    if h["version"] != 2 or h["S"] == 0:
+        return bytes(buf)
+    end = HEADER.size + 4 * (len(h["subs"]) + 1) + 2 * sum(len(x) for x in h["subs"])
+    out = bytearray(buf[:end])
+    struct.pack_into("<H", out, 30, 0)
+    return bytes(out)
 
 
 def _bands(Hy, R):
@@ -425,6 +497,8 @@ class Codec:
     M: int
     W: dict
     R: int = BAND_ROWS
+    version: int = 1        # substream format: 1 escape nibbles in the rANS words, 2 outside them
+    S: int = 0              # format 2: resume record every S groups of 32 symbols (0: none)
     med: np.ndarray = field(default=None)
     eb: list = field(default=None)
     gauss: list = field(default=None)
@@ -435,23 +509,48 @@ class Codec:
             self.gauss = gauss_tables()
 
 
+def _substream_plan(codec: Codec, Hy, Wy, R=None):
+    """(kind, channel, row0, row1) of every substream of a frame, in order:
+    hyperprior z channels first, then each y channel's bands of R rows."""
+    plan = []
+    if codec.kind == KIND_HYPERPRIOR:
+        plan += [("z", c, 0, Hy // 4) for c in range(codec.N)]
+    for c in range(codec.M):
+        plan += [("y", c, r0, r1) for r0, r1 in _bands(Hy, codec.R if R is None else R)]
+    return plan
+
+
 def encode_latents(codec: Codec, s_y, idx=None, s_z=None):
     """Substreams of one frame from its integer symbols.
-    s_y: M x Hy x Wy int32; idx: M x Hy x Wy uint8 (hyper); s_z: N x Hz x Wz."""
-    subs = []
-    if codec.kind == KIND_HYPERPRIOR:
-        for c in range(codec.N):
-            plane = s_z[c].ravel()
-            subs.append(rans_encode(plane, np.full(plane.size, c), codec.eb))
+    s_y: M x Hy x Wy int32; idx: M x Hy x Wy uint8 (hyper); s_z: N x Hz x Wz.
+    Format 1 returns the list of substreams; format 2 returns (substreams,
+    resume records per substream)."""
+    subs, recs = [], []
     M, Hy, Wy = s_y.shape
-    for c in range(M):
-        for r0, r1 in _bands(Hy, codec.R):
+    for part, c, r0, r1 in _substream_plan(codec, Hy, Wy):
+        if part == "z":
+            sym = s_z[c].ravel()
+            tab, tabs = np.full(sym.size, c), codec.eb
+        else:
             sym = s_y[c, r0:r1].ravel()
             if codec.kind == KIND_HYPERPRIOR:
-                subs.append(rans_encode(sym, idx[c, r0:r1].ravel().astype(np.int32), codec.gauss))
+                tab, tabs = idx[c, r0:r1].ravel().astype(np.int32), codec.gauss
             else:
-                subs.append(rans_encode(sym, np.full(sym.size, c), codec.eb))
-    return subs
+                tab, tabs = np.full(sym.size, c), codec.eb
+        if codec.version == 2:
+            w, r = rans2_encode(sym, tab, tabs, codec.S)
+            subs.append(w)
+            recs.append(r)
+        else:
+            subs.append(rans_encode(sym, tab, tabs))
+    return (subs, recs) if codec.version == 2 else subs
+
+
+def _pack(codec: Codec, H, W, Hp, Wp, enc):
+    if codec.version == 2:
+        subs, recs = enc
+        return pack_frame(codec.kind, codec.N, codec.M, H, W, Hp, Wp, codec.R, subs, 2, codec.S, recs)
+    return pack_frame(codec.kind, codec.N, codec.M, H, W, Hp, Wp, codec.R, enc)
 
 
 def encode(codec: Codec, frames):
@@ -474,15 +573,32 @@ def encode(codec: Codec, frames):
         s_y = quantize(y.astype(np.float32))
         inter.update(z=z, s_z=s_z, zhat=zhat, sigma=sigma, idx=idx, s_y=s_y)
         for b in range(B):
-            subs = encode_latents(codec, s_y[b], idx[b], s_z[b])
-            out.append(pack_frame(codec.kind, codec.N, codec.M, H, W, Hp, Wp, codec.R, subs))
+            out.append(_pack(codec, H, W, Hp, Wp, encode_latents(codec, s_y[b], idx[b], s_z[b])))
     else:
         s_y = quantize(y.astype(np.float32), codec.med)
         inter.update(s_y=s_y)
         for b in range(B):
-            subs = encode_latents(codec, s_y[b])
-            out.append(pack_frame(codec.kind, codec.N, codec.M, H, W, Hp, Wp, codec.R, subs))
+            out.append(_pack(codec, H, W, Hp, Wp, encode_latents(codec, s_y[b])))
     return out, inter
+
+
+def _decode_sub(hdr, words, n, tab, tabs, recs):
+    """One substream of either format; format 2 with records decodes each
+    segment between records from its own record (as a parallel decoder
+    would), and the whole substream must then also decode from its start."""
+    if hdr["version"] == 1:
+        return rans_decode(words, n, tab, tabs)
+    whole = rans2_decode(words, n, tab, tabs)
+    if len(recs):
+        S, ng = hdr["S"], (n + 31) // 32
+        seg = np.zeros(n, np.int32)
+        bounds = [0] + [S * (r + 1) for r in range(len(recs))] + [ng]
+        for r in range(len(recs) + 1):
+            part = rans2_decode(words, n, tab, tabs, None if r == 0 else recs[r - 1], bounds[r], bounds[r + 1])
+            seg[32 * bounds[r]:32 * bounds[r + 1]] = part[32 * bounds[r]:32 * bounds[r + 1]]
+        if not np.array_equal(seg, whole):
+            raise ValueError("resume records disagree with the substream")
+    return whole
 
 
 def decode_latents(codec: Codec, hdr):
@@ -490,13 +606,28 @@ def decode_latents(codec: Codec, hdr):
     Hp, Wp, R = hdr["Hp"], hdr["Wp"], hdr["R"]
     Hy, Wy = Hp // 16, Wp // 16
     subs = hdr["subs"]
+    S = hdr.get("S", 0) if hdr.get("version", 1) == 2 else 0
+    plan = _substream_plan(codec, Hy, Wy, R)
+    # resume records: per substream ((groups - 1) // S of them), in order
+    trailer = hdr.get("trailer", np.zeros(0, np.uint32))
+    nrec = []
+    for part, c, r0, r1 in plan:
+        n = (Hy // 4) * (Wy // 4) if part == "z" else (r1 - r0) * Wy
+        ng = (n + 31) // 32
+        nrec.append((ng - 1) // S if (S > 0 and ng > 0) else 0)
+    if len(trailer) != REC_U32 * sum(nrec):
+        raise ValueError("resume trailer size")
+    recs, o = [], 0
+    for k in nrec:
+        recs.append(trailer[o:o + REC_U32 * k].reshape(k, REC_U32))
+        o += REC_U32 * k
     k = 0
     res = {}
     if codec.kind == KIND_HYPERPRIOR:
         Hz, Wz = Hp // 64, Wp // 64
         s_z = np.zeros((codec.N, Hz, Wz), dtype=np.int32)
         for c in range(codec.N):
-            s_z[c] = rans_decode(subs[k], Hz * Wz, np.full(Hz * Wz, c), codec.eb).reshape(Hz, Wz)
+            s_z[c] = _decode_sub(hdr, subs[k], Hz * Wz, np.full(Hz * Wz, c), codec.eb, recs[k]).reshape(Hz, Wz)
             k += 1
         zhat = dequantize(s_z[None], codec.med)
         sigma = h_s(codec.W, zhat)
@@ -508,9 +639,9 @@ def decode_latents(codec: Codec, hdr):
             n = (r1 - r0) * Wy
             if codec.kind == KIND_HYPERPRIOR:
                 t = idx[c, r0:r1].ravel().astype(np.int32)
-                s_y[c, r0:r1] = rans_decode(subs[k], n, t, codec.gauss).reshape(r1 - r0, Wy)
+                s_y[c, r0:r1] = _decode_sub(hdr, subs[k], n, t, codec.gauss, recs[k]).reshape(r1 - r0, Wy)
             else:
-                s_y[c, r0:r1] = rans_decode(subs[k], n, np.full(n, c), codec.eb).reshape(r1 - r0, Wy)
+                s_y[c, r0:r1] = _decode_sub(hdr, subs[k], n, np.full(n, c), codec.eb, recs[k]).reshape(r1 - r0, Wy)
             k += 1
     res["s_y"] = s_y
     return res

@@ -553,3 +553,186 @@ int orc_rans_decode(const uint16_t *words, int64_t nwords, int n,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* rANS substreams, format 2: escape payloads outside the rANS words and     */
+/* optional resume records (the decoder-adaptive form)                       */
+/* ------------------------------------------------------------------------ */
+
+/* Substream layout (16-bit words, little endian), L words in all:
+ *   w[0], w[1]          nw, the number of rANS words (low half first)
+ *   w[2 .. 2+nw)        the rANS words exactly as format 1 would order them
+ *                       (32 initial states, then renormalisation words in
+ *                       symbol order), except that an escape is the escape
+ *                       symbol alone: its payload is not in this section
+ *   payload nibbles     from w[2+nw] on: escape k's n_k nibbles of v (the
+ *                       zigzag overflow, least significant first) at nibble
+ *                       positions Q_k .. Q_k+n_k-1, Q_k = sum of n_i, i < k;
+ *                       nibble j sits in word j/4 at bits 4 (j mod 4)
+ *   count nibbles       from the last word backwards: n_k - 1 for escape k is
+ *                       nibble k, in word L-1-k/4 at bits 4 (k mod 4)
+ *   with 2 + nw + ceil(np/4) + ceil(ne/4) = L (ne escapes, np payload nibbles).
+ * Resume record for group G (symbols 32G .. 32G+31), 35 u32: the index P of
+ * the next rANS word at the start of group G (relative to w[2]), the escapes
+ * E and payload nibbles Q before group G, and the 32 lane states then.  With
+ * spacing S > 0 there is one record for each G = S, 2S, ... below the group
+ * count. */
+
+static void put_nibble(uint16_t *base, int64_t j, uint32_t v)
+{
+    base[j >> 2] = (uint16_t)(base[j >> 2] | ((v & 15u) << (4 * (j & 3))));
+}
+
+static uint32_t get_nibble(const uint16_t *base, int64_t j)
+{
+    return ((uint32_t)base[j >> 2] >> (4 * (j & 3))) & 15u;
+}
+
+int orc_rans2_encode(const int32_t *s, const int32_t *tab_of, int n, const orc_table *tabs, int S,
+                     uint16_t *out, int64_t cap, int64_t *len, uint32_t *rec, int64_t rec_cap,
+                     int64_t *nrec, int64_t lane_words[32], double lane_bits[32])
+{
+    int ngroups = (n + 31) / 32;
+    int64_t nr = (S > 0 && ngroups > 0) ? (ngroups - 1) / S : 0;
+    if (nr * 35 > rec_cap) return -1;
+    /* symbols, escapes and their payloads in symbol order */
+    int *sym = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
+    uint32_t *pay = (uint32_t *)malloc(sizeof(uint32_t) * (n > 0 ? n : 1));
+    int *nib = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
+    int64_t ne = 0, np = 0;
+    for (int i = 0; i < n; i++) {
+        const orc_table *t = &tabs[tab_of[i]];
+        nib[i] = 0;
+        if (s[i] >= -t->lo && s[i] <= t->hi) {
+            sym[i] = s[i] + t->lo;
+        } else {
+            sym[i] = t->lo + t->hi + 1;
+            pay[i] = s[i] > t->hi ? 2u * (uint32_t)(s[i] - t->hi - 1) : 2u * (uint32_t)(-s[i] - t->lo - 1) + 1u;
+            nib[i] = nibbles_of(pay[i]);
+            ne++;
+            np += nib[i];
+        }
+    }
+    /* the rANS words: symbols from last to first, state i mod 32; records
+     * keep each lane's state after its group G was encoded */
+    uint16_t *tmp = (uint16_t *)malloc(sizeof(uint16_t) * ((int64_t)n + 64));
+    wbuf b = {tmp, 0, (int64_t)n + 64, 0};
+    uint32_t x[32];
+    int64_t dummy[32];
+    int64_t *lw = lane_words ? lane_words : dummy;
+    for (int l = 0; l < 32; l++) {
+        x[l] = RANS_L;
+        lw[l] = 0;
+        if (lane_bits) lane_bits[l] = 0.0;
+    }
+    int64_t esc_after = 0, nib_after = 0;   /* escapes / nibbles in the groups encoded so far */
+    for (int i = n - 1; i >= 0; i--) {
+        int l = i % 32;
+        const orc_table *t = &tabs[tab_of[i]];
+        uint32_t st = t->cdf[sym[i]], f = t->cdf[sym[i] + 1] - t->cdf[sym[i]];
+        rans_put(&x[l], st, f, &b, &lw[l]);
+        if (lane_bits) lane_bits[l] += -log2((double)f / 65536.0) + (nib[i] ? 4.0 * (nib[i] + 1) : 0.0);
+        if (nib[i]) {
+            esc_after++;
+            nib_after += nib[i];
+        }
+        if (l == 0 && S > 0 && i / 32 > 0 && (i / 32) % S == 0) {
+            int64_t r = (i / 32) / S - 1;   /* record of group G = i / 32 */
+            uint32_t *R = rec + 35 * r;
+            R[0] = (uint32_t)b.n;           /* words emitted for groups >= G; made relative below */
+            R[1] = (uint32_t)(ne - esc_after);
+            R[2] = (uint32_t)(np - nib_after);
+            for (int k = 0; k < 32; k++) R[3 + k] = x[k];
+        }
+    }
+    for (int l = 31; l >= 0; l--) {
+        put_word(&b, (uint16_t)(x[l] >> 16));
+        put_word(&b, (uint16_t)(x[l] & 0xFFFF));
+    }
+    int64_t nw = b.n;
+    int64_t L = 2 + nw + (np + 3) / 4 + (ne + 3) / 4;
+    int rc = 0;
+    if (b.overflow || L > cap) {
+        rc = -1;
+    } else {
+        memset(out, 0, sizeof(uint16_t) * L);
+        out[0] = (uint16_t)(nw & 0xFFFF);
+        out[1] = (uint16_t)(nw >> 16);
+        for (int64_t k = 0; k < nw; k++) out[2 + k] = tmp[nw - 1 - k];   /* decoder order */
+        uint16_t *pw = out + 2 + nw;
+        int64_t q = 0, e = 0;
+        for (int i = 0; i < n; i++) {
+            if (!nib[i]) continue;
+            for (int j = 0; j < nib[i]; j++) put_nibble(pw, q++, pay[i] >> (4 * j));
+            /* count nibbles grow from the last word backwards */
+            out[L - 1 - (e >> 2)] = (uint16_t)(out[L - 1 - (e >> 2)] | ((uint32_t)(nib[i] - 1) << (4 * (e & 3))));
+            e++;
+        }
+        for (int64_t r = 0; r < nr; r++) rec[35 * r] = (uint32_t)(nw - rec[35 * r]);   /* P: words before G */
+        *len = L;
+        *nrec = nr;
+    }
+    free(tmp);
+    free(sym);
+    free(pay);
+    free(nib);
+    return rc;
+}
+
+/* Decode groups [g0, g1) of a format-2 substream of n symbols.  rec = NULL
+ * starts at group 0 from the stream's initial states; otherwise from that
+ * record (g0 is its group).  Every read is bounded; returns 0, or -1 for a
+ * stream this coder cannot have written.  When the decode reaches the last
+ * symbol, the section sizes must add up to the substream length exactly. */
+int orc_rans2_decode_range(const uint16_t *w, int64_t L, int n, const int32_t *tab_of, const orc_table *tabs,
+                           const uint32_t *rec, int g0, int g1, int32_t *s)
+{
+    if (L < 2) return -1;
+    int64_t nw = (int64_t)w[0] | ((int64_t)w[1] << 16);
+    if (nw < 64 || 2 + nw > L) return -1;
+    rbuf r = {w + 2, nw, 0, 0};
+    uint32_t x[32];
+    int64_t e = 0, q = 0;
+    if (!rec) {
+        if (g0 != 0) return -1;
+        for (int l = 0; l < 32; l++) {
+            uint32_t lo = take_word(&r);
+            uint32_t hi = take_word(&r);
+            x[l] = lo | (hi << 16);
+        }
+    } else {
+        r.pos = rec[0];
+        e = rec[1];
+        q = rec[2];
+        for (int l = 0; l < 32; l++) x[l] = rec[3 + l];
+        if (r.pos < 64 || r.pos > nw) return -1;
+    }
+    if (r.bad) return -1;
+    const uint16_t *pw = w + 2 + nw;
+    int64_t wa = L - 2 - nw;   /* words after the rANS section: payload, then counts from the end */
+    int i_end = 32 * g1 < n ? 32 * g1 : n;
+    for (int i = 32 * g0; i < i_end; i++) {
+        int l = i % 32;
+        const orc_table *t = &tabs[tab_of[i]];
+        int esc = t->lo + t->hi + 1;
+        int sym = rans_get(&x[l], t->cdf, t->n, &r);
+        if (r.bad) return -1;
+        if (sym < esc) {
+            s[i] = sym - t->lo;
+            continue;
+        }
+        /* count nibble e from the end, then its payload nibbles from q on */
+        if (e / 4 >= wa) return -1;
+        uint32_t nn = ((uint32_t)w[L - 1 - e / 4] >> (4 * (e % 4)) & 15u) + 1;
+        e++;
+        if ((q + (int64_t)nn - 1) / 4 >= wa) return -1;
+        uint32_t v = 0;
+        for (uint32_t j = 0; j < nn; j++) v |= get_nibble(pw, q + j) << (4 * j);
+        q += nn;
+        int64_t val = (v & 1u) ? -(int64_t)t->lo - 1 - (int64_t)(v >> 1) : (int64_t)t->hi + 1 + (int64_t)(v >> 1);
+        if (val > 1073741824LL || val < -1073741824LL) return -1;
+        s[i] = (int32_t)val;
+    }
+    if (i_end == n && (r.pos != nw || 2 + nw + (q + 3) / 4 + (e + 3) / 4 != L)) return -1;
+    return 0;
+}

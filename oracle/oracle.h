@@ -122,6 +122,23 @@ int orc_rans_encode(const int32_t *s, const int32_t *tab_of, int n,
 int orc_rans_decode(const uint16_t *words, int64_t nwords, int n,
                     const int32_t *tab_of, const orc_table *tabs, int32_t *s);
 
+/* ---- format 2: escape payloads outside the rANS words, resume records ---- */
+
+/* Encode n symbols into one format-2 substream (layout in oracle.c) of
+ * *len words (cap = capacity of out), and, with S > 0, its resume records
+ * (35 u32 each, rec_cap u32 of room) every S groups of 32 symbols.  The
+ * lane statistics are as for orc_rans_encode (escape nibbles counted as
+ * bits of their lane).  Returns 0 or -1. */
+int orc_rans2_encode(const int32_t *s, const int32_t *tab_of, int n, const orc_table *tabs, int S,
+                     uint16_t *out, int64_t cap, int64_t *len, uint32_t *rec, int64_t rec_cap,
+                     int64_t *nrec, int64_t lane_words[32], double lane_bits[32]);
+
+/* Decode groups [g0, g1) of a format-2 substream of L words: from its
+ * initial states (rec NULL, g0 = 0) or from the resume record of group g0.
+ * Returns 0 or -1 (corrupt). */
+int orc_rans2_decode_range(const uint16_t *w, int64_t L, int n, const int32_t *tab_of, const orc_table *tabs,
+                           const uint32_t *rec, int g0, int g1, int32_t *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -513,3 +513,151 @@ def test_student_loss_window_matches_finite_differences():
             Pm[name][idx] -= eps
             fd = (O.student_loss_grads(Pp, yhat, target)[0] - O.student_loss_grads(Pm, yhat, target)[0]) / (2 * eps)
             assert abs(fd - gval[idx]) <= 1e-6 * max(1.0, abs(fd)), (name, idx)
+
+
+# ------------------------------------------- rANS substream format 2 (escapes outside)
+
+def test_rans2_hand_computed():
+    g = json.load(open(os.path.join(GOLD, "rans2_hand.json")))
+    for key in ("escape3", "resume33"):
+        case = g[key]
+        t = _tab(case["lo"], case["hi"], case["cdf"])
+        sy = np.array(case["symbols"], np.int32)
+        tab = np.zeros(len(sy), np.int32)
+        words, recs = O.rans2_encode(sy, tab, [t], case["S"])
+        assert words.tolist() == case["words"], key
+        assert recs.tolist() == case["records"], key
+        assert O.rans2_decode(words, len(sy), tab, [t]).tolist() == case["symbols"]
+        for r, rec in enumerate(recs):
+            G = case["S"] * (r + 1)
+            got = O.rans2_decode(words, len(sy), tab, [t], rec, G, (len(sy) + 31) // 32)
+            assert got[32 * G:].tolist() == case["symbols"][32 * G:]
+
+
+def _v2_roundtrip(s, idx, tabs, S):
+    n = len(s)
+    w, recs = O.rans2_encode(s, idx, tabs, S)
+    assert O.rans2_decode(w, n, idx, tabs).tolist() == s.tolist()
+    ng = (n + 31) // 32
+    bounds = [0] + [S * (r + 1) for r in range(len(recs))] + [ng]
+    assert len(recs) == ((ng - 1) // S if S and ng else 0)
+    for r in range(len(recs) + 1):
+        part = O.rans2_decode(w, n, idx, tabs, None if r == 0 else recs[r - 1], bounds[r], bounds[r + 1])
+        sl = slice(32 * bounds[r], 32 * bounds[r + 1])
+        assert part[sl].tolist() == s[sl].tolist(), r
+    return w
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 1000])
+@pytest.mark.parametrize("S", [0, 1, 3])
+def test_rans2_roundtrip_and_resume_records(n, S):
+    tabs = _random_tables()
+    idx = rng.integers(0, 64, n).astype(np.int32)
+    T = O.scale_table()
+    s = np.rint(rng.standard_normal(n) * T[idx] * 1.3).astype(np.int32)
+    s[::13] = rng.integers(-20000, 20000, len(s[::13]))
+    _v2_roundtrip(s, idx, tabs, S)
+
+
+def test_rans2_adversarial():
+    tabs = _random_tables()
+    n = 300
+    idx = np.zeros(n, np.int32)
+    s = np.array([(1 if i % 2 else -1) * (2 + (7 ** (i % 11))) for i in range(n)], np.int32)
+    s[:4] = [2 ** 30, -(2 ** 30), 2, -2]
+    _v2_roundtrip(s, idx, tabs, 2)
+    t = tabs[63]
+    s = np.array([-t.lo, t.hi] * 40, np.int32)
+    _v2_roundtrip(s, np.full(len(s), 63, np.int32), tabs, 1)
+
+
+def test_rans2_rans_words_equal_format1_without_escapes():
+    """Format 2 changes only where escapes go: with none, its rANS section is
+    format 1's stream word for word, and the substream is that plus nw."""
+    tabs = _random_tables()
+    n = 2000
+    idx = rng.integers(0, 64, n).astype(np.int32)
+    T = O.scale_table()
+    s = np.clip(np.rint(rng.standard_normal(n) * T[idx]), -1, 1).astype(np.int32)
+    w1 = O.rans_encode(s, idx, tabs)
+    w2, _ = O.rans2_encode(s, idx, tabs)
+    assert int(w2[0]) | (int(w2[1]) << 16) == len(w1)
+    assert w2[2:].tolist() == w1.tolist()
+
+
+def test_rans2_escape_bits_leave_the_word_stream():
+    """With escapes, format 2's rANS section has exactly as many words as a
+    format-1 stream of the same symbols with every escape payload removed
+    (the escape symbol alone), and the payload and count sections hold
+    4 bits per nibble: n_k + 1 nibbles per escape."""
+    tabs = _random_tables()
+    n = 640
+    idx = np.full(n, 5, np.int32)
+    t = tabs[5]
+    s = rng.integers(-t.lo, t.hi + 1, n).astype(np.int32)
+    esc = rng.random(n) < 0.2
+    s[esc] = t.hi + 1 + rng.integers(0, 5000, int(esc.sum()))
+    w2, _ = O.rans2_encode(s, idx, tabs)
+    nw = int(w2[0]) | (int(w2[1]) << 16)
+    s_plain = s.copy()
+    s_plain[esc] = t.hi + 1          # payload v = 0: one nibble in format 1
+    w1 = O.rans_encode(s_plain, idx, tabs)
+    # format 1 puts two uniform nibbles per such escape in the words; format 2 none
+    v = 2 * (s[esc] - t.hi - 1)
+    nn = np.array([max(1, (int(x).bit_length() + 3) // 4) for x in v])
+    assert len(w2) == 2 + nw + (nn.sum() + 3) // 4 + (int(esc.sum()) + 3) // 4
+    assert nw <= len(w1)
+
+
+def test_rans2_corrupt_is_detected():
+    tabs = _random_tables()
+    idx = np.full(200, 20, np.int32)
+    s = rng.integers(-3, 4, 200).astype(np.int32)
+    s[::7] = 9000
+    w, _ = O.rans2_encode(s, idx, tabs)
+    for bad in (w[:40], w[:-1], np.concatenate([w, [0]])):
+        with pytest.raises(ValueError):
+            O.rans2_decode(bad, 200, idx, tabs)
+    w2 = w.copy()
+    w2[-1] ^= 0x7          # count nibble 0 changed: the payload positions shift
+    with pytest.raises(ValueError):
+        O.rans2_decode(w2, 200, idx, tabs)
+
+
+def test_rans2_code_length_bound():
+    """As for format 1, per interleaved state (escape nibbles counted on
+    their lane): bits <= 1.01 * sum(-log2 p) + 64."""
+    tabs = _random_tables()
+    T = O.scale_table()
+    for k in (3, 30):
+        n = 32 * 400
+        idx = np.full(n, k, np.int32)
+        s = np.rint(rng.standard_normal(n) * T[k] * 1.5).astype(np.int32)
+        w, recs, lw, lb = O.rans2_encode(s, idx, tabs, with_stats=True)
+        nw = int(w[0]) | (int(w[1]) << 16)
+        assert nw == lw.sum() + 64
+        bits = 16.0 * (lw + 2)
+        extra = 16.0 * (len(w) - 2 - nw)     # the escape sections, all lanes
+        assert bits.sum() + extra <= 1.01 * lb.sum() + 64 * 32 + 32
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_format2_container_chain_and_strip(kind):
+    W = synth.make_weights(kind, 32, 64)
+    x = synth.make_frames(1, 200, 330, first=4)
+    oc1 = O.Codec(kind, 32, 64, W)
+    bs1, inter = O.encode(oc1, x)
+    for S in (0, 2):
+        oc = O.Codec(kind, 32, 64, W, version=2, S=S)
+        bs, inter2 = O.encode(oc, x)
+        assert np.array_equal(inter2["s_y"], inter["s_y"])
+        h = O.unpack_frame(bs[0])
+        assert h["version"] == 2 and h["S"] == S and (len(h["trailer"]) > 0) == (S > 0)
+        xr, di = O.decode(oc, bs)
+        assert np.array_equal(di[0]["s_y"], inter["s_y"][0])
+        st = O.strip_records(bs[0])
+        assert O.unpack_frame(st)["S"] == 0 and len(st) <= len(bs[0])
+        xr2, di2 = O.decode(oc, [st])
+        assert np.array_equal(xr2, xr)
+        if S == 0:
+            assert st == bs[0]
