@@ -91,11 +91,33 @@ typedef struct {
 
 typedef struct {
     int precision;   /* lic_precision (LIC_BF16 needs the tensor-core kernels) */
-    int band_rows;   /* latent rows per y substream; 0 -> 16 */
+    int band_rows;   /* latent rows per y substream; 0 -> 16 (a value >= the
+                        latent height makes each y plane one substream) */
     int conv_impl;   /* lic_conv_impl */
     int norm;        /* lic_norm: the normalisation between the g_a / g_s layers */
-    int reserved[4];
+    int format;      /* lic_format: the substream format; 0 -> LIC_FORMAT_1 */
+    int resume_groups; /* LIC_FORMAT_2: a resume record every this many groups
+                        of 32 symbols of a substream (0: none) */
+    int reserved[2]; /* 0 */
 } lic_options;
+
+/* Substream formats (the container's version field; the paper integrates
+ * CompressAI's coder and defines none).  Both code the same symbols with the
+ * same 32 interleaved rANS states per substream.
+ * LIC_FORMAT_1: an escape's payload is coded as uniform 4-bit rANS symbols
+ *   after it, inside the interleaved words.
+ * LIC_FORMAT_2: the escape symbol alone is rANS-coded; payload nibbles follow
+ *   the rANS words and count nibbles grow from the substream's end, so a
+ *   decoder resolves all escapes of a group of 32 at once (the
+ *   decoder-adaptive, higher-throughput coder the paper names as future
+ *   work, Sec. VII).  With resume_groups = S > 0 the encoder also writes, in
+ *   a trailer after the substreams, a resume record every S groups (the next
+ *   word's position, escape and payload positions, the 32 lane states); a
+ *   decoder set up with the same S decodes the segments between records in
+ *   parallel, any other decoder of the format (or one given a stream whose
+ *   records were stripped, lic_strip_resume_records) decodes each substream
+ *   from its start.  A codec encodes and decodes its own format only. */
+typedef enum { LIC_FORMAT_1 = 1, LIC_FORMAT_2 = 2 } lic_format;
 
 /* LIC_NORM_GDN: GDN / IGDN of Ballé et al. (the paper's [9]), gamma [C,C].
  * LIC_NORM_1DN: the cheaper activation of the paper's variant C (Sec. IV-C,
@@ -111,9 +133,11 @@ typedef struct lic_codec lic_codec;
  * y string, per frame).  Frame i occupies bytes [offsets[i], offsets[i] +
  * sizes[i]) of `data`.  Each frame is one self-describing container (magic
  * "LIC1", see the design notes):
- *   'LIC1' u16 version=1, u16 kind, u16 N, u16 M, u32 H, u32 W, u32 Hp,
- *   u32 Wp, u16 R, u16 0, u32 nsub, u32 off[nsub+1] (16-bit word offsets),
- *   u16 payload[off[nsub]]                               (little endian)
+ *   'LIC1' u16 version (1 or 2, the lic_format), u16 kind, u16 N, u16 M,
+ *   u32 H, u32 W, u32 Hp, u32 Wp, u16 R, u16 S (format 2: resume-record
+ *   spacing, else 0), u32 nsub, u32 off[nsub+1] (16-bit word offsets),
+ *   u16 payload[off[nsub]], then (format 2, S > 0) the resume records, 140
+ *   bytes each                                           (little endian)
  * A batch made by lic_encode is library-owned (owner != NULL) and stays
  * valid until lic_bitstreams_release; a batch a caller assembles from its
  * own memory has owner = NULL and is never touched by the library beyond
@@ -222,6 +246,16 @@ int64_t lic_bitstreams_download(const lic_bitstreams *in, uint8_t *dst, int64_t 
  * Returns INVALID_ARG / CORRUPT_STREAM on a bad header. */
 int lic_decoded_shape(const uint8_t *frame, int64_t size, int *kind, int *H, int *W);
 
+/* Host-only: copy one format-2 frame container without its resume records
+ * (the trailer dropped and the header's record spacing set to 0): what a
+ * sender transmits to a decoder that will not use them.  A frame without
+ * records is copied unchanged.  out may equal frame.  *out_size receives the
+ * new size; out_cap is out's capacity (the input size suffices).  Errors:
+ * INVALID_ARG (null pointers, capacity), CORRUPT_STREAM (not a container of
+ * either format, or a size that does not match its header). */
+int lic_strip_resume_records(const uint8_t *frame, int64_t size, uint8_t *out, int64_t out_cap,
+                             int64_t *out_size);
+
 /* ---------------------------------------------------------------------- */
 /* Stage-level calls (tests, diagnostics, custom pipelines)                */
 /* All tensors NCHW; device or host memory unless stated.                  */
@@ -293,9 +327,12 @@ int lic_encode_latents(lic_codec *codec, const int32_t *s_y, const uint8_t *idx,
  * from the same inputs (device pointers, NCHW, as there).  Outputs are the
  * caller's device buffers:
  *   data      containers, frame i at byte d_layout[i]; data_cap bytes, at
- *             least B * (36 + 4 (nsub+1) + 2 nsub (10 n_max + 64) + 16)
- *             (the worst case for escapes in every symbol; nsub substreams
- *             per frame, n_max symbols in the longest one), else INVALID_ARG;
+ *             least B * (36 + 4 (nsub+1) + 2 nsub c + 16) (the worst case for
+ *             escapes in every symbol; nsub substreams per frame, n_max
+ *             symbols in the longest; c = 10 n_max + 64 words in format 1,
+ *             8 + 2 ceil((n_max + 64) / 2) + 2 (n_max + 1 + n_max / 8 + 1 +
+ *             35 r) in format 2 with r = its records per substream plus 1,
+ *             0 without records), else INVALID_ARG;
  *   d_layout  2B+1 int64: byte offsets of the frames [0..B] followed by
  *             their sizes [B+1..2B].
  * Working memory comes from one array of LIC_NOALLOC_SCRATCH_BYTES inside

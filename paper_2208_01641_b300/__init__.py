@@ -25,6 +25,8 @@ FP32 = 0
 BF16 = 1
 NORM_GDN = 0
 NORM_1DN = 1
+FORMAT_1 = 1
+FORMAT_2 = 2
 FP8 = 2
 
 T_Y, T_SY, T_Z, T_SZ, T_SIGMA, T_IDX, T_XPRE, T_YHAT = range(8)
@@ -39,7 +41,7 @@ EXPORTED = [
     "lic_decode_latents", "lic_build_tables", "lic_scale_table", "lic_strerror",
     "lic_profile_enable", "lic_profile_report", "lic_launch_count", "lic_encode_latents_noalloc",
     "lic_test_bounded_wait", "lic_bitstreams_release", "lic_codec_device_bytes", "lic_codec_workspace_bytes",
-    "lic_probe_mma_rate",
+    "lic_probe_mma_rate", "lic_strip_resume_records",
     # include/lic_student.h (learned form)
     "lic_student_create", "lic_student_destroy", "lic_student_grad", "lic_student_step", "lic_student_read",
     "lic_student_read_activation", "lic_student_steps", "lic_student_forward", "lic_student_profile_enable", "lic_student_profile_report",
@@ -72,7 +74,8 @@ class _Weights(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("band_rows", ctypes.c_int),
-                ("conv_impl", ctypes.c_int), ("norm", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("conv_impl", ctypes.c_int), ("norm", ctypes.c_int), ("format", ctypes.c_int),
+                ("resume_groups", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class _StudentOptions(ctypes.Structure):
@@ -149,6 +152,7 @@ def _lib():
         L.lic_launch_count.restype = i64
         L.lic_test_bounded_wait.argtypes = [vp, i64, vp]
         L.lic_probe_mma_rate.argtypes = [i, i, ctypes.POINTER(ctypes.c_double)]
+        L.lic_strip_resume_records.argtypes = [vp, i64, vp, i64, ctypes.POINTER(i64)]
         L.lic_student_create.argtypes = [ctypes.POINTER(_Weights), i, i, ctypes.POINTER(_StudentOptions),
                                          ctypes.POINTER(vp)]
         L.lic_student_destroy.argtypes = [vp]
@@ -310,10 +314,11 @@ class Codec:
     """One codec on the current CUDA device (lic_codec_create)."""
 
     def __init__(self, kind: int, N: int, M: int, weights: Dict[str, np.ndarray], band_rows: int = 16,
-                 conv_impl: int = CONV_AUTO, precision: int = FP32, norm: int = NORM_GDN):
+                 conv_impl: int = CONV_AUTO, precision: int = FP32, norm: int = NORM_GDN,
+                 format: int = FORMAT_1, resume_groups: int = 0):
         self.kind, self.N, self.M = kind, N, M
         w, keep = _weights_struct(weights)
-        opt = _Options(precision, band_rows, conv_impl, norm)
+        opt = _Options(precision, band_rows, conv_impl, norm, format, resume_groups)
         h = ctypes.c_void_p()
         _check(_lib().lic_codec_create(kind, N, M, ctypes.byref(w), ctypes.byref(opt), ctypes.byref(h)),
                "lic_codec_create")
@@ -465,6 +470,16 @@ def mma_rate(kind: int, iters: int = 20000) -> float:
     t = ctypes.c_double()
     _check(_lib().lic_probe_mma_rate(kind, iters, ctypes.byref(t)), "lic_probe_mma_rate")
     return t.value
+
+
+def strip_resume_records(frame: bytes) -> bytes:
+    """A format-2 frame without its resume records (lic_strip_resume_records)."""
+    buf = np.frombuffer(frame, np.uint8).copy()
+    out = np.zeros(max(1, len(frame)), np.uint8)
+    n = ctypes.c_int64()
+    _check(_lib().lic_strip_resume_records(_ptr(buf), len(frame), _ptr(out), out.size, ctypes.byref(n)),
+           "lic_strip_resume_records")
+    return out[:n.value].tobytes()
 
 
 def decoded_shape(frame: bytes):

@@ -715,9 +715,8 @@ int entropy_plan(lic_codec *cd, const StreamGeom &g, int B, lic_codec::Batch *bb
     f(cd->counts, subs, 8);
     f(cd->sub_off, subs, 8);
     f(cd->frame_bytes, B, 8);
-    const int64_t frame_cap = g.header_bytes + 2 * (int64_t)g.nsub * g.cap_words + 16;
     f(bb->offs, 2 * (int64_t)B + 1, 8);
-    f(bb->data, (int64_t)B * frame_cap, 1);
+    f(bb->data, (int64_t)B * g.frame_cap, 1);
     return rc;
 }
 
@@ -897,11 +896,11 @@ int entropy_encode(lic_codec *cd, const StreamGeom &g, int B, const int32_t *s_y
     if (!bb) return rc;
     const double nsym = (double)B * ((double)g.M * g.Hy * g.Wy + (double)g.nz * g.Hz * g.Wz);
     timed(cd, "rans_encode", 0, 5 * nsym, 1, st, [&] {
-        launch_rans_encode(g, B, cd->dt, s_y, idx, s_z, cd->scratch.as<uint16_t>(), cd->counts.as<int64_t>(), st);
+        launch_entropy_encode(g, B, cd->dt, s_y, idx, s_z, cd->scratch.as<uint16_t>(), cd->counts.as<int64_t>(), st);
     });
     timed(cd, "rans_compact", 0, 0, 3, st, [&] {
-        launch_rans_compact(g, B, cd->scratch.as<uint16_t>(), cd->counts.as<int64_t>(), cd->sub_off.as<int64_t>(),
-                            cd->frame_bytes.as<int64_t>(), bb->offs.as<int64_t>(), bb->data.as<uint8_t>(), st);
+        launch_entropy_compact(g, B, cd->scratch.as<uint16_t>(), cd->counts.as<int64_t>(), cd->sub_off.as<int64_t>(),
+                               cd->frame_bytes.as<int64_t>(), bb->offs.as<int64_t>(), bb->data.as<uint8_t>(), st);
     });
     LIC_CUDA_TRY(cudaMemcpyAsync(bb->h_offs.p, bb->offs.p, (2 * (size_t)B + 1) * sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, st));
@@ -989,17 +988,17 @@ int entropy_decode(lic_codec *cd, const lic_bitstreams *in, int H, int W, cudaSt
     const uint8_t *data;
     const int64_t *offs, *sizes;
     if ((rc = stage_bitstreams(cd, in, &data, &offs, &sizes, st))) return rc;
-    StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows);
+    StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows, cd->opt.format, cd->opt.resume_groups);
     uint32_t *status = cd->status.as<uint32_t>();
     if (cd->kind == LIC_HYPERPRIOR) {
         timed(cd, "rans_decode_z", 0, 8.0 * B * g.nz * g.Hz * g.Wz, 1, st, [&] {
-            launch_rans_decode(g, B, 0, cd->dt, data, offs, sizes, nullptr, cd->med.as<float>(),
+            launch_entropy_decode(g, B, 0, cd->dt, data, offs, sizes, nullptr, cd->med.as<float>(),
                                cd->s_z.as<int32_t>(), cd->zhat.as<float>(), status, st);
         });
         hyper_synthesis(cd, cd->zhat.as<float>(), B, g.Hz, g.Wz, st);
     }
     timed(cd, "rans_decode_y", 0, 9.0 * B * g.M * g.Hy * g.Wy, 1, st, [&] {
-        launch_rans_decode(g, B, 1, cd->dt, data, offs, sizes,
+        launch_entropy_decode(g, B, 1, cd->dt, data, offs, sizes,
                            cd->kind == LIC_HYPERPRIOR ? cd->idx.as<uint8_t>() : nullptr, cd->med.as<float>(),
                            cd->s_y.as<int32_t>(), cd->yhat.as<float>(), status, st);
     });
@@ -1038,6 +1037,8 @@ int codec_entropy_view(const lic_codec *cd, CodecEntropyView *out) {
     out->N = cd->N;
     out->M = cd->M;
     out->R = cd->opt.band_rows;
+    out->version = cd->opt.format;
+    out->S = cd->opt.resume_groups;
     out->device = cd->device;
     out->tables = cd->dt;
     return LIC_OK;
@@ -1129,6 +1130,12 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
     cd->M = M;
     if (opts) cd->opt = *opts;
     if (cd->opt.band_rows <= 0) cd->opt.band_rows = 16;
+    if (cd->opt.format == 0) cd->opt.format = LIC_FORMAT_1;
+    if (cd->opt.format != LIC_FORMAT_1 && cd->opt.format != LIC_FORMAT_2) return LIC_E_INVALID_ARG;
+    if (cd->opt.resume_groups < 0 || cd->opt.resume_groups > 65535 ||
+        (cd->opt.format == LIC_FORMAT_1 && cd->opt.resume_groups != 0))
+        return LIC_E_INVALID_ARG;
+    if (cd->opt.reserved[0] || cd->opt.reserved[1]) return LIC_E_INVALID_ARG;
     if (cd->opt.norm != LIC_NORM_GDN && cd->opt.norm != LIC_NORM_1DN) return LIC_E_INVALID_ARG;
     if (cd->opt.precision < LIC_FP32 || cd->opt.precision > LIC_FP8) return LIC_E_UNSUPPORTED;
     if (cd->opt.precision != LIC_FP32 && cd->opt.conv_impl == LIC_CONV_SIMT) return LIC_E_UNSUPPORTED;
@@ -1221,6 +1228,12 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
     std::vector<double> P;
     if ((rc = pack_eb(pm, C, &P))) return rc;
     if ((rc = build_tables(P, C, kind == LIC_HYPERPRIOR, &cd->ht))) return rc;
+    if (cd->opt.format == LIC_FORMAT_2 && kind == LIC_HYPERPRIOR) {
+        // format 2 stages the 64 Gaussian CDFs in shared memory
+        int64_t gauss = 0;
+        for (int k = 0; k < 64; ++k) gauss += cd->ht.lo[C + k] + cd->ht.hi[C + k] + 2;
+        if (gauss > RANS2_GAUSS_CDF_CAP) return LIC_E_UNSUPPORTED;
+    }
     if ((rc = upload(cd->cdf, cd->ht.cdf.data(), cd->ht.cdf.size() * 4))) return rc;
     if ((rc = upload(cd->start, cd->ht.start.data(), cd->ht.start.size() * 8))) return rc;
     if ((rc = upload(cd->lo, cd->ht.lo.data(), cd->ht.lo.size() * 4))) return rc;
@@ -1285,7 +1298,7 @@ int lic_encode(lic_codec *cd, const float *frames, int B, int H, int W, lic_bits
     if ((rc = copy_in(cd, cd->stage_in, frames, (size_t)B * 3 * H * W * sizeof(float), &src, st))) return rc;
     analysis(cd, static_cast<const float *>(src), B, H, W, Hp, Wp, st);
     const int Hy = Hp / 16, Wy = Wp / 16;
-    StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows);
+    StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows, cd->opt.format, cd->opt.resume_groups);
     if (cd->kind == LIC_HYPERPRIOR) {
         timed(cd, "quantize_y", 0, 8.0 * B * Hy * Wy * cd->M, 1, st, [&] {
             launch_quantize(cd->y.as<float>(), B, Hy * Wy, cd->M, nullptr, cd->s_y.as<int32_t>(), nullptr, st);
@@ -1319,7 +1332,8 @@ int lic_encode_latents(lic_codec *cd, const int32_t *s_y, const uint8_t *idx, co
     if (cd->kind == LIC_HYPERPRIOR && (!idx || !s_z || Hy % 4 || Wy % 4)) return LIC_E_INVALID_ARG;
     if (!is_device_ptr(s_y) || (idx && !is_device_ptr(idx)) || (s_z && !is_device_ptr(s_z))) return LIC_E_INVALID_ARG;
     AllocScope scope(&cd->device_bytes);
-    StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, 16 * Hy, 16 * Wy, cd->opt.band_rows);
+    StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, 16 * Hy, 16 * Wy, cd->opt.band_rows, cd->opt.format,
+                             cd->opt.resume_groups);
     return entropy_encode(cd, g, B, s_y, idx, s_z, out, S(stream));
 }
 
@@ -1395,7 +1409,7 @@ int64_t lic_codec_workspace_bytes(const lic_codec *cd, int B, int H, int W) {
     };
     workspace_plan(c, B, Hp, Wp, add);
     lic_codec::Batch probe;
-    entropy_plan(c, make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows), B, &probe, add);
+    entropy_plan(c, make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows, cd->opt.format, cd->opt.resume_groups), B, &probe, add);
     return total;
 }
 
@@ -1473,10 +1487,32 @@ int lic_decoded_shape(const uint8_t *f, int64_t size, int *kind, int *H, int *W)
     memcpy(&k, f + 6, 2);
     memcpy(&h, f + 12, 4);
     memcpy(&w, f + 16, 4);
-    if (ver != 1 || k > 1) return LIC_E_CORRUPT_STREAM;
+    if ((ver != 1 && ver != 2) || k > 1) return LIC_E_CORRUPT_STREAM;
     if (kind) *kind = k;
     if (H) *H = (int)h;
     if (W) *W = (int)w;
+    return LIC_OK;
+}
+
+int lic_strip_resume_records(const uint8_t *f, int64_t size, uint8_t *out, int64_t out_cap, int64_t *out_size) {
+    if (!f || !out || !out_size || size < 36 || out_cap < 0) return LIC_E_INVALID_ARG;
+    int kind = 0, H = 0, W = 0;
+    if (lic_decoded_shape(f, size, &kind, &H, &W) != LIC_OK) return LIC_E_CORRUPT_STREAM;
+    uint16_t ver = 0, S = 0;
+    uint32_t nsub = 0, wend = 0;
+    memcpy(&ver, f + 4, 2);
+    memcpy(&S, f + 30, 2);
+    memcpy(&nsub, f + 32, 4);
+    const int64_t head = 36 + 4 * ((int64_t)nsub + 1);
+    if (head > size) return LIC_E_CORRUPT_STREAM;
+    memcpy(&wend, f + 36 + 4 * (int64_t)nsub, 4);
+    const int64_t body = head + 2 * (int64_t)wend;
+    if (body > size || (ver == 1 && body != size) || (ver == 2 && S == 0 && body != size)) return LIC_E_CORRUPT_STREAM;
+    if (ver == 2 && S > 0 && (size - body) % 140 != 0) return LIC_E_CORRUPT_STREAM;
+    if (out_cap < body) return LIC_E_INVALID_ARG;
+    if (out != f) memmove(out, f, (size_t)body);
+    if (ver == 2) out[30] = out[31] = 0;
+    *out_size = body;
     return LIC_OK;
 }
 

@@ -380,9 +380,24 @@ struct StreamGeom {
     int H, W, Hp, Wp;
     int64_t header_bytes;  // 36 + 4 (nsub + 1)
     int64_t cap_words;     // scratch words per substream, max over substreams
+    // substream format: 1 = escape nibbles inside the rANS words; 2 = escape
+    // payloads after them and optional resume records every S groups of 32
+    // symbols (decoder-adaptive parallel decoding)
+    int version;
+    int S;
+    // format 2: records per z substream, per full y band, per last y band,
+    // and per frame (all substreams); the scratch layout of one substream in
+    // 16-bit words: meta (nw, ne, np, nr as u32) at 0, the rANS words
+    // right-aligned in [8, 8 + cap_r), then cap_p32 u32 of payload nibbles,
+    // cap_c32 u32 of count nibbles and 35 u32 per resume record
+    int nr_z, nr_full, nr_last;
+    int64_t rec_per_frame;
+    int64_t cap_r, cap_p32, cap_c32;
+    // worst-case bytes of one frame container
+    int64_t frame_cap;
 };
 
-StreamGeom make_geom(int kind, int N, int M, int H, int W, int Hp, int Wp, int R);
+StreamGeom make_geom(int kind, int N, int M, int H, int W, int Hp, int Wp, int R, int version = 1, int S = 0);
 
 // Encoder: symbols NCHW (s_y [B][M][Hy][Wy], idx same, s_z [B][N][Hz][Wz])
 // -> per substream words in scratch (decoder order, right-aligned) + counts.
@@ -394,6 +409,42 @@ void launch_rans_encode(const StreamGeom &g, int B, const DevTables &t, const in
 void launch_rans_compact(const StreamGeom &g, int B, const uint16_t *scratch,
                          const int64_t *counts, int64_t *sub_off, int64_t *frame_bytes,
                          int64_t *offsets, uint8_t *data, cudaStream_t st);
+
+// The per-frame scan of substream lengths (counts, in 16-bit words) into
+// offsets and frame sizes (header + 2 * words + trailer_bytes), and the
+// frames' 16-byte aligned placement (offsets [B+1], then sizes [B]).
+void launch_rans_scan(const StreamGeom &g, int B, const int64_t *counts, int64_t *sub_off, int64_t *frame_bytes,
+                      int64_t trailer_bytes, cudaStream_t st);
+void launch_frame_place(int B, const int64_t *frame_bytes, int64_t *offsets, cudaStream_t st);
+
+// Entries of the 64 Gaussian CDFs (without each table's final 2^16) that the
+// format-2 kernels stage in shared memory; a codec whose tables exceed it
+// cannot use format 2.
+constexpr int RANS2_GAUSS_CDF_CAP = 27200;
+
+// Format 2 (rans2.cu): the same roles as the three calls above, for
+// substreams whose escape payloads follow the rANS words (g.version == 2).
+// The encoder fills each substream's scratch (layout in StreamGeom) and
+// counts[] with the substream's length in words; the compaction writes the
+// containers and the resume-record trailer; the decoder runs one warp per
+// segment between resume records (one per substream without records).
+void launch_rans2_encode(const StreamGeom &g, int B, const DevTables &t, const int32_t *s_y, const uint8_t *idx,
+                         const int32_t *s_z, uint16_t *scratch, int64_t *counts, cudaStream_t st);
+void launch_rans2_compact(const StreamGeom &g, int B, const uint16_t *scratch, const int64_t *counts,
+                          int64_t *sub_off, int64_t *frame_bytes, int64_t *offsets, uint8_t *data, cudaStream_t st);
+void launch_rans2_decode(const StreamGeom &g, int B, int part, const DevTables &t, const uint8_t *data,
+                         const int64_t *offsets, const int64_t *sizes, const uint8_t *idx, const float *med,
+                         int32_t *s_out, float *hat_out, uint32_t *status, cudaStream_t st);
+
+// Either format, by g.version.
+void launch_entropy_encode(const StreamGeom &g, int B, const DevTables &t, const int32_t *s_y, const uint8_t *idx,
+                           const int32_t *s_z, uint16_t *scratch, int64_t *counts, cudaStream_t st);
+void launch_entropy_compact(const StreamGeom &g, int B, const uint16_t *scratch, const int64_t *counts,
+                            int64_t *sub_off, int64_t *frame_bytes, int64_t *offsets, uint8_t *data,
+                            cudaStream_t st);
+void launch_entropy_decode(const StreamGeom &g, int B, int part, const DevTables &t, const uint8_t *data,
+                           const int64_t *offsets, const int64_t *sizes, const uint8_t *idx, const float *med,
+                           int32_t *s_out, float *hat_out, uint32_t *status, cudaStream_t st);
 // Decoder: validates headers, decodes the z substreams (part 0) or the y
 // substreams (part 1).  z: s_z NCHW + zhat NHWC (fl32(s + med)).  y: s_y
 // NCHW + yhat NHWC (factorized: fl32(s + med); hyperprior: s).
@@ -406,6 +457,7 @@ void launch_rans_decode(const StreamGeom &g, int B, int part, const DevTables &t
 // live outside api.cu.
 struct CodecEntropyView {
     int kind, N, M, R;
+    int version, S;  // substream format and resume-record spacing
     int device;      // the CUDA device the codec (and its tables) lives on
     DevTables tables;
 };

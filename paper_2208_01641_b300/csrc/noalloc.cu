@@ -74,7 +74,7 @@ extern "C" int lic_encode_latents_noalloc(lic_codec *codec, const int32_t *s_y, 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return LIC_E_CUDA;
     if (dev != v.device) return LIC_E_INVALID_ARG;
-    const StreamGeom g = make_geom(v.kind, v.N, v.M, H, W, 16 * Hy, 16 * Wy, v.R);
+    const StreamGeom g = make_geom(v.kind, v.N, v.M, H, W, 16 * Hy, 16 * Wy, v.R, v.version, v.S);
     const int64_t subs = (int64_t)B * g.nsub;
     // scratch carve-up: words | counts | sub_off | frame_bytes
     const int64_t words_bytes = align256(subs * g.cap_words * (int64_t)sizeof(uint16_t));
@@ -83,8 +83,7 @@ extern "C" int lic_encode_latents_noalloc(lic_codec *codec, const int32_t *s_y, 
     const int64_t need = words_bytes + 2 * counts_bytes + frame_bytes;
     if (need > (int64_t)LIC_NOALLOC_SCRATCH_BYTES) return LIC_E_UNSUPPORTED;
     // every frame is placed at a 16-byte aligned offset; worst-case sizes
-    const int64_t frame_cap = g.header_bytes + 2 * (int64_t)g.nsub * g.cap_words + 16;
-    if (data_cap < (int64_t)B * frame_cap) return LIC_E_INVALID_ARG;
+    if (data_cap < (int64_t)B * g.frame_cap) return LIC_E_INVALID_ARG;
     void *base = nullptr;
     int rc = scratch_address(dev, &base);
     if (rc != LIC_OK) return rc;
@@ -97,7 +96,7 @@ extern "C" int lic_encode_latents_noalloc(lic_codec *codec, const int32_t *s_y, 
     // No scratch word needs clearing: each kernel reads only what an earlier
     // kernel of this call wrote (the encoder writes every count and the
     // words it counts; the scan writes every offset and frame size).
-    launch_rans_encode(g, B, v.tables, s_y, idx, s_z, words, counts, st);
-    launch_rans_compact(g, B, words, counts, sub_off, fbytes, d_layout, data, st);
+    launch_entropy_encode(g, B, v.tables, s_y, idx, s_z, words, counts, st);
+    launch_entropy_compact(g, B, words, counts, sub_off, fbytes, d_layout, data, st);
     return cudaGetLastError() == cudaSuccess ? LIC_OK : LIC_E_CUDA;
 }

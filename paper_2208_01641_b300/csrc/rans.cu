@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(WARPS * 32) rans_encode_kernel(const StreamGeo
 
 // Per frame: exclusive scan of substream word counts, frame size in bytes.
 __global__ void rans_scan_kernel(const StreamGeom g, const int64_t *__restrict__ counts,
-                                 int64_t *__restrict__ sub_off, int64_t *__restrict__ frame_bytes) {
+                                 int64_t *__restrict__ sub_off, int64_t *__restrict__ frame_bytes,
+                                 int64_t trailer_bytes) {
     __shared__ int64_t part[1024];
     __shared__ int64_t carry;
     const int b = blockIdx.x;
@@ -201,7 +202,7 @@ __global__ void rans_scan_kernel(const StreamGeom g, const int64_t *__restrict__
         if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
         __syncthreads();
     }
-    if (threadIdx.x == 0) frame_bytes[b] = g.header_bytes + 2 * carry;
+    if (threadIdx.x == 0) frame_bytes[b] = g.header_bytes + 2 * carry + trailer_bytes;
 }
 
 // Frame placement: 16-byte aligned starts.  offsets has B+1 entries, then
@@ -495,7 +496,7 @@ int64_t blocks_for(int64_t warps) { return (warps + WARPS - 1) / WARPS; }
 
 }  // namespace
 
-StreamGeom make_geom(int kind, int N, int M, int H, int W, int Hp, int Wp, int R) {
+StreamGeom make_geom(int kind, int N, int M, int H, int W, int Hp, int Wp, int R, int version, int S) {
     StreamGeom g{};
     g.kind = kind;
     g.N = N;
@@ -515,7 +516,32 @@ StreamGeom make_geom(int kind, int N, int M, int H, int W, int Hp, int Wp, int R
     g.header_bytes = 36 + 4 * (int64_t)(g.nsub + 1);
     int64_t nmax = (int64_t)std::min(R, g.Hy) * g.Wy;
     if (kind == LIC_HYPERPRIOR) nmax = std::max<int64_t>(nmax, (int64_t)g.Hz * g.Wz);
-    g.cap_words = MAX_WORDS_PER_SYMBOL * nmax + 64;
+    g.version = version == 2 ? 2 : 1;
+    g.S = g.version == 2 && S > 0 ? S : 0;
+    auto nrec = [&](int64_t n) -> int {
+        const int64_t ng = (n + 31) / 32;
+        return (g.S > 0 && ng > 0) ? (int)((ng - 1) / g.S) : 0;
+    };
+    const int last_rows = g.Hy - (g.nbands - 1) * R;
+    g.nr_z = kind == LIC_HYPERPRIOR ? nrec((int64_t)g.Hz * g.Wz) : 0;
+    g.nr_full = nrec((int64_t)std::min(R, g.Hy) * g.Wy);
+    g.nr_last = nrec((int64_t)last_rows * g.Wy);
+    g.rec_per_frame = (int64_t)g.nz * g.nr_z + (int64_t)M * ((int64_t)(g.nbands - 1) * g.nr_full + g.nr_last);
+    if (g.version == 1) {
+        g.cap_words = MAX_WORDS_PER_SYMBOL * nmax + 64;
+        g.cap_r = g.cap_p32 = g.cap_c32 = 0;
+    } else {
+        // at most one rANS word per symbol plus the flush; 8 payload nibbles and one
+        // count nibble per escape; the records of the longest substream
+        const int64_t nr_max = (g.S > 0) ? ((nmax + 31) / 32 - 1) / g.S + 1 : 0;
+        g.cap_r = (nmax + 64 + 1) / 2 * 2;
+        g.cap_p32 = nmax + 1;
+        g.cap_c32 = nmax / 8 + 1;
+        g.cap_words = 8 + g.cap_r + 2 * (g.cap_p32 + g.cap_c32 + 35 * nr_max);
+    }
+    // every frame starts 16-byte aligned; format 2 adds its record trailer (at most the
+    // records' scratch, which cap_words holds)
+    g.frame_cap = g.header_bytes + 2 * (int64_t)g.nsub * g.cap_words + 16;
     return g;
 }
 
@@ -525,14 +551,43 @@ void launch_rans_encode(const StreamGeom &g, int B, const DevTables &t, const in
     rans_encode_kernel<<<(unsigned)blocks_for(warps), WARPS * 32, 0, st>>>(g, B, t, s_y, idx, s_z, scratch, counts);
 }
 
+void launch_rans_scan(const StreamGeom &g, int B, const int64_t *counts, int64_t *sub_off, int64_t *frame_bytes,
+                      int64_t trailer_bytes, cudaStream_t st) {
+    rans_scan_kernel<<<B, 1024, 0, st>>>(g, counts, sub_off, frame_bytes, trailer_bytes);
+}
+
+void launch_frame_place(int B, const int64_t *frame_bytes, int64_t *offsets, cudaStream_t st) {
+    frame_place_kernel<<<1, 32, 0, st>>>(B, frame_bytes, offsets);
+}
+
 void launch_rans_compact(const StreamGeom &g, int B, const uint16_t *scratch, const int64_t *counts,
                          int64_t *sub_off, int64_t *frame_bytes, int64_t *offsets, uint8_t *data,
                          cudaStream_t st) {
-    rans_scan_kernel<<<B, 1024, 0, st>>>(g, counts, sub_off, frame_bytes);
-    frame_place_kernel<<<1, 32, 0, st>>>(B, frame_bytes, offsets);
+    launch_rans_scan(g, B, counts, sub_off, frame_bytes, 0, st);
+    launch_frame_place(B, frame_bytes, offsets, st);
     int64_t warps = (int64_t)B * g.nsub;
     rans_write_kernel<<<(unsigned)blocks_for(warps), WARPS * 32, 0, st>>>(g, B, scratch, counts, sub_off, offsets,
                                                                           data);
+}
+
+void launch_entropy_encode(const StreamGeom &g, int B, const DevTables &t, const int32_t *s_y, const uint8_t *idx,
+                           const int32_t *s_z, uint16_t *scratch, int64_t *counts, cudaStream_t st) {
+    if (g.version == 2) launch_rans2_encode(g, B, t, s_y, idx, s_z, scratch, counts, st);
+    else launch_rans_encode(g, B, t, s_y, idx, s_z, scratch, counts, st);
+}
+
+void launch_entropy_compact(const StreamGeom &g, int B, const uint16_t *scratch, const int64_t *counts,
+                            int64_t *sub_off, int64_t *frame_bytes, int64_t *offsets, uint8_t *data,
+                            cudaStream_t st) {
+    if (g.version == 2) launch_rans2_compact(g, B, scratch, counts, sub_off, frame_bytes, offsets, data, st);
+    else launch_rans_compact(g, B, scratch, counts, sub_off, frame_bytes, offsets, data, st);
+}
+
+void launch_entropy_decode(const StreamGeom &g, int B, int part, const DevTables &t, const uint8_t *data,
+                           const int64_t *offsets, const int64_t *sizes, const uint8_t *idx, const float *med,
+                           int32_t *s_out, float *hat_out, uint32_t *status, cudaStream_t st) {
+    if (g.version == 2) launch_rans2_decode(g, B, part, t, data, offsets, sizes, idx, med, s_out, hat_out, status, st);
+    else launch_rans_decode(g, B, part, t, data, offsets, sizes, idx, med, s_out, hat_out, status, st);
 }
 
 void launch_rans_decode(const StreamGeom &g, int B, int part, const DevTables &t, const uint8_t *data,
