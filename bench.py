@@ -344,6 +344,11 @@ def main():
                     "of the states to flush (rate), a third of the decoder's warps (parallelism)"}
         cw.close()
 
+    # ---- substream format 2: escape payloads outside the rANS words (decoder-adaptive coder) ----
+    if not args.no_forms:
+        forms["fp32_format2"] = format2_form(args, lic, Wt, impl, frames, out, H, W, stream, flush, ws, B,
+                                             frame_bytes, rep)
+
     # ---- the precision form's own configuration: N=192 M=320, 8 x 1920x1080 ----
     if not args.no_forms and args.conv == "auto":
         forms["precision_1080p_n192_m320"] = wide_form(args, lic, synth, torch, np, stream, flush, rank)
@@ -709,6 +714,46 @@ def wide_form(args, lic, synth, torch, np, stream, flush, rank):
     res["note"] = ("hyperprior N=192 M=320, 8 x 1920x1080 (4 seeded frames twice) padded to 1920x1088; the 320-wide "
                    "layers as tensor-core column slices (192 + 128); BF16 GDN/IGDN unfused at 192 channels")
     return res
+
+
+def entropy_ms(codec, frames, out, stream):
+    """Per-launch device time (ms) of the entropy kernels in one profiled
+    encode + decode step: {name: ms per launch}."""
+    sid = stream.cuda_stream
+    codec.profile(True)
+    bs = codec.encode(frames, stream=sid)
+    codec.decode(bs, out, stream=sid)
+    codec.sync(sid)
+    rep = codec.profile_report()
+    codec.profile(False)
+    return {r["name"]: r["ms"] / r["launches"] for r in rep if r["name"].startswith("rans_")}
+
+
+def format2_form(args, lic, Wt, impl, frames, out, H, W, stream, flush, ws, B, frame_bytes, rep):
+    """Format 2 with whole latent planes as y substreams, no resume records
+    (the bench batch has enough planes to fill the GPU), against format 1's
+    16-row bands: frames/s, bits per pixel, entropy kernel times; and the
+    same with a record every 40 groups (a 16-row band's worth at 720p) for a
+    decoder short of planes."""
+    out_f = {}
+    for name, S in (("whole_planes", 0), ("whole_planes_records40", 40)):
+        c = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, conv_impl=impl, band_rows=PAD_H // 16, format=lic.FORMAT_2,
+                      resume_groups=S)
+        ms, status = time_steps(c, frames, out, H, W, args.steps, args.warmup, stream, flush)
+        sizes = c.encode(frames).sizes()
+        ent = entropy_ms(c, frames, out, stream)
+        out_f[name] = {"value": ws * B * args.steps / (sum(ms) / 1000.0), "unit": "frames/s",
+                       "ms_per_step": sum(ms) / args.steps, "decode_status": status,
+                       "bits_per_pixel": 8.0 * statistics.mean(sizes) / (H * W), "entropy_ms": ent}
+        c.close()
+    v1 = {r["name"]: r["ms"] / r["launches"] for r in rep if r["name"].startswith("rans_")}
+    out_f["format1_16_row_bands"] = {"bits_per_pixel": 8.0 * statistics.mean(frame_bytes) / (H * W),
+                                     "entropy_ms": v1}
+    out_f["note"] = ("format 2: an escape is the escape symbol alone in the rANS words, its payload and count "
+                     "nibbles in sections after them, so a warp decodes every group of 32 symbols in one step; "
+                     "whole latent planes as substreams (one 32-state flush per plane); records: resume points "
+                     "a decoder may use to split a plane into parallel segments (their bytes counted here)")
+    return out_f
 
 
 def time_steps(codec, frames, out, H, W, steps, warmup, stream, flush):

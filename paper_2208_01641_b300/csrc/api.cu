@@ -87,7 +87,7 @@ struct lic_codec {
     lic::Gdn gdn[3], igdn[3];
     // entropy models
     lic::HostTables ht;
-    lic::DevBuf cdf, start, lo, hi, med, lut;
+    lic::DevBuf cdf, start, lo, hi, med, lut, gimg;
     lic::DevTables dt{};
     lic::DevBuf status;
     // workspace
@@ -895,7 +895,7 @@ int entropy_encode(lic_codec *cd, const StreamGeom &g, int B, const int32_t *s_y
     lic_codec::Batch *bb = acquire_batch(cd, g, B, &rc);
     if (!bb) return rc;
     const double nsym = (double)B * ((double)g.M * g.Hy * g.Wy + (double)g.nz * g.Hz * g.Wz);
-    timed(cd, "rans_encode", 0, 5 * nsym, 1, st, [&] {
+    timed(cd, "rans_encode", 0, 5 * nsym, g.version == 2 ? 2 : 1, st, [&] {   // format 2: + the length sum
         launch_entropy_encode(g, B, cd->dt, s_y, idx, s_z, cd->scratch.as<uint16_t>(), cd->counts.as<int64_t>(), st);
     });
     timed(cd, "rans_compact", 0, 0, 3, st, [&] {
@@ -1228,12 +1228,7 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
     std::vector<double> P;
     if ((rc = pack_eb(pm, C, &P))) return rc;
     if ((rc = build_tables(P, C, kind == LIC_HYPERPRIOR, &cd->ht))) return rc;
-    if (cd->opt.format == LIC_FORMAT_2 && kind == LIC_HYPERPRIOR) {
-        // format 2 stages the 64 Gaussian CDFs in shared memory
-        int64_t gauss = 0;
-        for (int k = 0; k < 64; ++k) gauss += cd->ht.lo[C + k] + cd->ht.hi[C + k] + 2;
-        if (gauss > RANS2_GAUSS_CDF_CAP) return LIC_E_UNSUPPORTED;
-    }
+
     if ((rc = upload(cd->cdf, cd->ht.cdf.data(), cd->ht.cdf.size() * 4))) return rc;
     if ((rc = upload(cd->start, cd->ht.start.data(), cd->ht.start.size() * 8))) return rc;
     if ((rc = upload(cd->lo, cd->ht.lo.data(), cd->ht.lo.size() * 4))) return rc;
@@ -1255,7 +1250,14 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
             lut[t * LUT_N + LUT_N - 1] = (uint16_t)(n - 1);
         }
         if ((rc = upload(cd->lut, lut.data(), lut.size() * sizeof(uint16_t)))) return rc;
+        if (cd->opt.format == LIC_FORMAT_2 && kind == LIC_HYPERPRIOR) {
+            // the format-2 kernels' shared-memory image of the Gaussian tables
+            std::vector<uint8_t> img;
+            if (!build_gauss_image(cd->ht, C, lut, &img)) return LIC_E_UNSUPPORTED;
+            if ((rc = upload(cd->gimg, img.data(), img.size()))) return rc;
+        }
     }
+    cd->dt.gimg = cd->gimg.p;
     cd->dt.lut = cd->lut.as<uint16_t>();
     cd->dt.cdf = cd->cdf.as<uint32_t>();
     cd->dt.start = cd->start.as<int64_t>();

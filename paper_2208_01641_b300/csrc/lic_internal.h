@@ -365,7 +365,18 @@ struct DevTables {
     const uint16_t *lut;
     int n_eb;        // bottleneck tables: table c for channel c
     int gauss_base;  // first Gaussian table (or -1)
+    // format 2: the 64 Gaussian tables as the kernels hold them in shared
+    // memory (build_gauss_image), copied there with 16-byte loads; null when
+    // the codec has no Gaussian tables
+    const void *gimg;
 };
+
+// The shared-memory image of the 64 Gaussian tables for the format-2
+// kernels, in bytes: int32 lo[64], n[64] (symbols incl. the escape), cs[64]
+// (first entry of each CDF below), then RANS2_GAUSS_CDF_CAP 16-bit CDF
+// entries (each table's n entries, its final 2^16 implied), then the 64
+// slot lookups (LUT_N 16-bit entries each).  Multiple of 16 bytes.
+constexpr int RANS2_GIMG_HDR = 3 * 64 * 4;
 
 // Geometry of the substreams of one frame (identical for every frame).
 struct StreamGeom {
@@ -421,6 +432,12 @@ void launch_frame_place(int B, const int64_t *frame_bytes, int64_t *offsets, cud
 // format-2 kernels stage in shared memory; a codec whose tables exceed it
 // cannot use format 2.
 constexpr int RANS2_GAUSS_CDF_CAP = 27200;
+constexpr int RANS2_GIMG_CDF_BYTES = RANS2_GIMG_HDR + 2 * RANS2_GAUSS_CDF_CAP;   // header + CDFs
+constexpr int RANS2_GIMG_BYTES = RANS2_GIMG_CDF_BYTES + 2 * 64 * LUT_N;           // + slot lookups
+static_assert(RANS2_GIMG_CDF_BYTES % 16 == 0 && RANS2_GIMG_BYTES % 16 == 0, "16-byte copies");
+// Host: the image of Gaussian tables [first, first + 64) of ht (with their
+// slot lookups lut, LUT_N entries per table); false if they do not fit.
+bool build_gauss_image(const HostTables &ht, int first, const std::vector<uint16_t> &lut, std::vector<uint8_t> *img);
 
 // Format 2 (rans2.cu): the same roles as the three calls above, for
 // substreams whose escape payloads follow the rANS words (g.version == 2).
