@@ -87,7 +87,9 @@ struct lic_codec {
     lic::Gdn gdn[3], igdn[3];
     // entropy models
     lic::HostTables ht;
-    lic::DevBuf cdf, start, lo, hi, med, lut, gimg;
+    lic::DevBuf cdf, start, lo, hi, med, lut, gimg, scales;
+    // whether the last analysis / hyper analysis fused Q(y) / Q(z) into their epilogues
+    bool q_y_fused = false, q_z_fused = false;
     lic::DevTables dt{};
     lic::DevBuf status;
     // workspace
@@ -407,12 +409,36 @@ struct SplitScratch {
     int64_t frame_floats = 0;
 };
 
+// Quantisation a layer's epilogue is asked to fuse (ConvDesc q_*), and
+// whether every launch of the layer did (else the caller runs the separate
+// kernel).
+struct QFuse {
+    int mode = 0;
+    int32_t *sym = nullptr;
+    float *hat = nullptr;
+    const float *mu = nullptr;
+    uint8_t *idx = nullptr;
+    const float *tab = nullptr;
+    int C = 0;
+    bool done = false;
+};
+
 void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *in, int B, int Hi, int Wi,
             float *out, int Ho, int Wo, cudaStream_t st, const Gdn *G = nullptr, int out_dt = -1,
-            SplitScratch sk = {}) {
+            SplitScratch sk = {}, QFuse *qf = nullptr) {
     ConvDesc d = op_desc(cd, L, op, in, B, Hi, Wi, out, Ho, Wo);
     d.part = sk.p;
     d.part_frame_floats = sk.p ? sk.frame_floats : 0;
+    bool q_ok = false;   // set where a launch applies the fused quantisation
+    if (qf && qf->mode && !G) {
+        d.q_mode = qf->mode;
+        d.q_sym = qf->sym;
+        d.q_hat = qf->hat;
+        d.q_mu = qf->mu;
+        d.q_idx = qf->idx;
+        d.q_tab = qf->tab;
+        d.q_C = qf->C;
+    }
     if (out_dt >= 0) {   // the caller wants this storage instead of the layer's own
         d.out_dt = out_dt;
         d.out_scale = 1.f;
@@ -457,13 +483,18 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
         }
         if (ok) {
             nm += d.in_dt == DT_F32 ? ":tc" : (d.in_dt == DT_E4M3 ? ":e4m3" : ":bf16");
+            bool all = true;
             timed(const_cast<lic_codec *>(cd), nm, flop, bytes, (int)ds.size(), st, [&] {
                 for (size_t j = 0; j < ds.size(); ++j) {
                     const bool done = d.in_dt != DT_F32 ? tc::launch_lp(ds[j], *op.parts[j], st)
                                                         : tc::launch(ds[j], *op.parts[j], st);
                     if (!done) atomic_status(cd, ST_TIMEOUT);
+                    all = all && done;
                 }
             });
+            bool fq = d.in_dt == DT_F32 && d.q_mode;
+            for (const ConvDesc &dp : ds) fq = fq && tc::tc_fuses_quant(dp);
+            if (qf) qf->done = qf->mode && fq && all;
             return;
         }
     }
@@ -472,14 +503,19 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
         timed(const_cast<lic_codec *>(cd), nm, flop, bytes, 1, st, [&] {
             if (!tc::launch_lp(d, op.tcw, st)) atomic_status(cd, ST_TIMEOUT);
         });
+        if (qf) qf->done = false;   // the low-precision kernels leave quantisation to the caller
         return;
     }
     const bool use_tc = cd->opt.conv_impl != LIC_CONV_SIMT && tc::can_run(d, op.tcw);
+    if (use_tc && !tc::tc_fuses_quant(d)) d.q_mode = 0;
+    if (use_tc && d.q_mode) nm += d.q_mode == 1 ? "+q" : "+index";
     nm += use_tc ? ":tc" : ":simt";
     const int nl = use_tc && tc::split_k(d, op.tcw) > 1 ? 2 : 1;   // split K: + the sum of the slices
     timed(const_cast<lic_codec *>(cd), nm, flop, bytes, nl, st, [&] {
-        if (!use_tc || !tc::launch(d, op.tcw, st)) launch_conv_simt(d, st);
+        q_ok = use_tc && tc::launch(d, op.tcw, st);
+        if (!q_ok) launch_conv_simt(d, st);
     });
+    if (qf) qf->done = qf->mode && d.q_mode && q_ok && d.out_dt == DT_F32;
 }
 
 // Every GEMM launch of a layer.  The phases of a transposed conv are
@@ -487,7 +523,7 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
 // auxiliary stream k - 1, so the small launches of h_s and of the first
 // g_s layers fill the GPU together instead of one after another.
 void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out, int Ho, int Wo,
-             cudaStream_t st, const Gdn *G, int out_dt = -1, SplitScratch sk = {}) {
+             cudaStream_t st, const Gdn *G, int out_dt = -1, SplitScratch sk = {}, QFuse *qf = nullptr) {
     const int n = (int)L.ops.size();
     // while launches are being timed one by one (lic_profile_enable) the phases run in
     // sequence, so that each launch's event pair brackets that launch alone
@@ -498,9 +534,12 @@ void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi
     }
     // split K only for a single launch: the phases of a transposed conv already
     // fill the GPU together (slicing them measured slower)
+    // fused quantisation only for a layer of one launch (a convolution, not the phases
+    // of a transposed one)
+    if (qf) qf->done = false;
     for (int k = 0; k < n; ++k)
         run_op(cd, L, *L.ops[k], in, B, Hi, Wi, out, Ho, Wo, (fork && k > 0) ? cd->aux[k - 1] : st, G, out_dt,
-               n == 1 ? sk : SplitScratch{});
+               n == 1 ? sk : SplitScratch{}, n == 1 ? qf : nullptr);
     if (fork) {
         for (int k = 1; k < n; ++k) {
             cudaEventRecord(cd->ev_join[k - 1], cd->aux[k - 1]);
@@ -510,7 +549,9 @@ void run_ops(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi
 }
 
 void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int Hi, int Wi, float *out,
-               cudaStream_t st, int out_dt = -1, const DevBuf *scratch = nullptr, SplitScratch sk = {}) {
+               cudaStream_t st, int out_dt = -1, const DevBuf *scratch = nullptr, SplitScratch sk = {},
+               QFuse *qf = nullptr) {
+    if (qf) qf->done = false;
     int Ho, Wo;
     if (L.deconv) {
         Ho = 2 * Hi;
@@ -572,7 +613,7 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
         });
         return;
     }
-    run_ops(cd, L, in, B, Hi, Wi, out, Ho, Wo, st, nullptr, out_dt, sk);
+    run_ops(cd, L, in, B, Hi, Wi, out, Ho, Wo, st, nullptr, out_dt, sk, qf);
 }
 
 void run_gdn(const lic_codec *cd, const Gdn &G, const float *in, int B, int H, int W, float *out, cudaStream_t st) {
@@ -786,7 +827,14 @@ void analysis(lic_codec *cd, const float *frames, int B, int Hf, int Wf, int Hp,
         H /= 2;
         W /= 2;
     }
-    run_layer(cd, cd->ga[3], in, B, H, W, cd->y.as<float>(), st);
+    // y, and Q(y) in the same epilogue: s = rint(y) (hyperprior) or rint(fl32(y - median))
+    QFuse q;
+    q.mode = 1;
+    q.sym = cd->s_y.as<int32_t>();
+    q.mu = cd->kind == LIC_FACTORIZED ? cd->med.as<float>() : nullptr;
+    q.C = cd->M;
+    run_layer(cd, cd->ga[3], in, B, H, W, cd->y.as<float>(), st, -1, nullptr, {}, &q);
+    cd->q_y_fused = q.done;
 }
 
 // Split-K scratch of the hyper transforms: act0, free while they run, holds
@@ -800,11 +848,20 @@ SplitScratch hyper_scratch(lic_codec *cd, int B, int Hy, int Wy) {
 }
 
 // h_a: y -> z; conv3x3/1 on |y| + ReLU, conv5x5/2 + ReLU, conv5x5/2
+// (with Q(z) and z_hat in the last layer's epilogue: s_z = rint(fl32(z - median)),
+// z_hat = fl32(s_z + median); the caller quantises where the epilogue could not)
 void hyper_analysis(lic_codec *cd, const float *y, int B, int Hy, int Wy, cudaStream_t st) {
     const SplitScratch sk = hyper_scratch(cd, B, Hy, Wy);
     run_layer(cd, cd->ha[0], y, B, Hy, Wy, cd->h1.as<float>(), st, -1, nullptr, sk);
     run_layer(cd, cd->ha[1], cd->h1.as<float>(), B, Hy, Wy, cd->h2.as<float>(), st, -1, nullptr, sk);
-    run_layer(cd, cd->ha[2], cd->h2.as<float>(), B, Hy / 2, Wy / 2, cd->z.as<float>(), st, -1, nullptr, sk);
+    QFuse q;
+    q.mode = 1;
+    q.sym = cd->s_z.as<int32_t>();
+    q.hat = cd->zhat.as<float>();
+    q.mu = cd->med.as<float>();
+    q.C = cd->N;
+    run_layer(cd, cd->ha[2], cd->h2.as<float>(), B, Hy / 2, Wy / 2, cd->z.as<float>(), st, -1, nullptr, sk, &q);
+    cd->q_z_fused = q.done;
 }
 
 // h_s: z_hat -> sigma; deconv+ReLU, deconv+ReLU, conv3x3+ReLU; then the index
@@ -812,11 +869,19 @@ void hyper_synthesis(lic_codec *cd, const float *zhat, int B, int Hz, int Wz, cu
     const SplitScratch sk = hyper_scratch(cd, B, 4 * Hz, 4 * Wz);
     run_layer(cd, cd->hs[0], zhat, B, Hz, Wz, cd->g1.as<float>(), st, -1, nullptr, sk);
     run_layer(cd, cd->hs[1], cd->g1.as<float>(), B, 2 * Hz, 2 * Wz, cd->g2.as<float>(), st, -1, nullptr, sk);
-    run_layer(cd, cd->hs[2], cd->g2.as<float>(), B, 4 * Hz, 4 * Wz, cd->sigma.as<float>(), st, -1, nullptr, sk);
-    const double n = 16.0 * B * Hz * Wz * cd->M;
-    timed(cd, "scale_index", 0, 5 * n, 1, st, [&] {
-        launch_scale_index(cd->sigma.as<float>(), B, 16 * Hz * Wz, cd->M, cd->idx.as<uint8_t>(), nullptr, st);
-    });
+    // sigma, and its scale index in the same epilogue
+    QFuse q;
+    q.mode = 2;
+    q.idx = cd->idx.as<uint8_t>();
+    q.tab = cd->scales.as<float>();
+    q.C = cd->M;
+    run_layer(cd, cd->hs[2], cd->g2.as<float>(), B, 4 * Hz, 4 * Wz, cd->sigma.as<float>(), st, -1, nullptr, sk, &q);
+    if (!q.done) {
+        const double n = 16.0 * B * Hz * Wz * cd->M;
+        timed(cd, "scale_index", 0, 5 * n, 1, st, [&] {
+            launch_scale_index(cd->sigma.as<float>(), B, 16 * Hz * Wz, cd->M, cd->idx.as<uint8_t>(), nullptr, st);
+        });
+    }
 }
 
 // g_s: y_hat (NHWC) -> xpre (NHWC, 3 channels); deconvs with IGDN between
@@ -1147,6 +1212,12 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
     }
     LIC_CUDA_TRY(cudaEventCreateWithFlags(&cd->ev_fork, cudaEventDisableTiming));
     LIC_CUDA_TRY(upload_scale_table());
+    {
+        float T[64];
+        scale_table(T);   // the scale index fused into h_s's epilogue reads them from here
+        int rc0 = upload(cd->scales, T, sizeof(T));
+        if (rc0) return rc0;
+    }
     ParamMap pm = param_map(weights);
     int rc;
     const int ch[5] = {3, N, N, N, M};
@@ -1301,21 +1372,24 @@ int lic_encode(lic_codec *cd, const float *frames, int B, int H, int W, lic_bits
     analysis(cd, static_cast<const float *>(src), B, H, W, Hp, Wp, st);
     const int Hy = Hp / 16, Wy = Wp / 16;
     StreamGeom g = make_geom(cd->kind, cd->N, cd->M, H, W, Hp, Wp, cd->opt.band_rows, cd->opt.format, cd->opt.resume_groups);
+    // Q(y), Q(z) and the scale index run in the epilogues that produce y, z and sigma
+    // (q_*_fused); the separate kernels only where those launches could not
+    if (!cd->q_y_fused) {
+        timed(cd, "quantize_y", 0, 8.0 * B * Hy * Wy * cd->M, 1, st, [&] {
+            launch_quantize(cd->y.as<float>(), B, Hy * Wy, cd->M,
+                            cd->kind == LIC_FACTORIZED ? cd->med.as<float>() : nullptr, cd->s_y.as<int32_t>(), nullptr,
+                            st);
+        });
+    }
     if (cd->kind == LIC_HYPERPRIOR) {
-        timed(cd, "quantize_y", 0, 8.0 * B * Hy * Wy * cd->M, 1, st, [&] {
-            launch_quantize(cd->y.as<float>(), B, Hy * Wy, cd->M, nullptr, cd->s_y.as<int32_t>(), nullptr, st);
-        });
         hyper_analysis(cd, cd->y.as<float>(), B, Hy, Wy, st);
-        timed(cd, "quantize_z", 0, 12.0 * B * g.Hz * g.Wz * cd->N, 1, st, [&] {
-            launch_quantize(cd->z.as<float>(), B, g.Hz * g.Wz, cd->N, cd->med.as<float>(), cd->s_z.as<int32_t>(),
-                            cd->zhat.as<float>(), st);
-        });
+        if (!cd->q_z_fused) {
+            timed(cd, "quantize_z", 0, 12.0 * B * g.Hz * g.Wz * cd->N, 1, st, [&] {
+                launch_quantize(cd->z.as<float>(), B, g.Hz * g.Wz, cd->N, cd->med.as<float>(),
+                                cd->s_z.as<int32_t>(), cd->zhat.as<float>(), st);
+            });
+        }
         hyper_synthesis(cd, cd->zhat.as<float>(), B, g.Hz, g.Wz, st);
-    } else {
-        timed(cd, "quantize_y", 0, 8.0 * B * Hy * Wy * cd->M, 1, st, [&] {
-            launch_quantize(cd->y.as<float>(), B, Hy * Wy, cd->M, cd->med.as<float>(), cd->s_y.as<int32_t>(),
-                            nullptr, st);
-        });
     }
     if ((rc = entropy_encode(cd, g, B, cd->s_y.as<int32_t>(), cd->idx.as<uint8_t>(), cd->s_z.as<int32_t>(), out, st)))
         return rc;

@@ -92,6 +92,13 @@ struct Params {
     int ksplit;                   // conv_tcx_kernel: K slices a tile is cut into (1: none)
     int out_stream;               // conv_tcx_kernel: output read once soon after; evict it from L2 first
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
+    // quantisation fused into the epilogue (see ConvDesc)
+    int q_mode, q_C;
+    int32_t *q_sym;
+    float *q_hat;
+    const float *q_mu;
+    uint8_t *q_idx;
+    const float *q_tab;
 };
 
 // ------------------------------------------------------------------ PTX
@@ -390,6 +397,55 @@ __device__ __forceinline__ void store_row(const float *v, void *out, int64_t off
         float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(out) + off);
 #pragma unroll
         for (int q = 0; q < NV / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+}
+
+// ---- quantisation fused into an epilogue: the same arithmetic as the
+// separate quantisation and scale-index kernels (layout.cu), so both decide
+// every integer identically ----
+
+__device__ __forceinline__ int32_t fq_symbol(float y, float mu) {
+    const float d = __fsub_rn(y, mu);
+    float r = rintf(d);
+    if (r != r) r = 0.f;
+    r = fminf(fmaxf(r, -1073741824.f), 1073741824.f);
+    return (int32_t)r;
+}
+
+// The smallest k with tab[k] >= max(sg, tab[0]) (NaN or above tab[63]: 63):
+// the scales are log-spaced (0.11 .. 256 in 63 steps), so log(sg / 0.11)
+// over the step puts k within one of the answer, and comparisons with the
+// table itself settle it -- the same k as a binary search of the table.
+__device__ __forceinline__ uint8_t fq_index(float sg, const float *tab) {
+    if (sg != sg) return 63;
+    sg = fmaxf(sg, tab[0]);
+    if (sg > tab[63]) return 63;
+    constexpr float kPerLog = 8.1266f;   // 63 / ln(256 / 0.11)
+    int k = (int)ceilf(__logf(sg * (1.f / 0.11f)) * kPerLog);
+    k = min(max(k, 0), 63);
+    while (k < 63 && tab[k] < sg) ++k;
+    while (k > 0 && tab[k - 1] >= sg) --k;
+    return (uint8_t)k;
+}
+
+// Channels c .. c+NV-1 (whole-layer numbering) of output pixel hw of frame b
+// (NHWC pixel index opix for q_hat); tab: the scales in shared memory.
+template <int NV>
+__device__ __forceinline__ void fused_quant(const Params &p, const float *v, int b, int64_t hw, int64_t HW, int c,
+                                            int64_t opix, const float *tab) {
+    const int64_t o0 = ((int64_t)b * p.q_C + c) * HW + hw;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int cc = c + j;
+        const int64_t o = o0 + (int64_t)j * HW;
+        if (p.q_mode == 1) {
+            const float mu = p.q_mu ? __ldg(p.q_mu + cc) : 0.f;
+            const int32_t sy = fq_symbol(v[j], mu);
+            p.q_sym[o] = sy;
+            if (p.q_hat) p.q_hat[opix * p.q_C + cc] = __fadd_rn(__int2float_rn(sy), mu);
+        } else {
+            p.q_idx[o] = fq_index(v[j], tab);
+        }
     }
 }
 
@@ -976,6 +1032,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 store_row<HALF * 32>(master, p.out, opix * p.ostride + p.ocoff + cbase, p.out_dt, p.out_inv_scale);
             } else if (valid) {
                 float *dst = p.out + opix * p.ostride + p.ocoff + cbase;
+
 #pragma unroll
                 for (int q = 0; q < HALF * 8; ++q) {
                     float4 o;
@@ -995,6 +1052,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                         op[e] = y;
                     }
                     reinterpret_cast<float4 *>(dst)[q] = o;
+
                 }
             }
         }
@@ -1106,6 +1164,8 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
         *abort_flag = 0;
         fence_barrier_init();
     }
+    __shared__ float s_qtab[64];   // fused scale index: the 64 scales
+    if (p.q_mode == 2 && threadIdx.x < 64) s_qtab[threadIdx.x] = p.q_tab[threadIdx.x];
     if (warp == 1) tmem_alloc(tmem_slot, 512);
     tc_fence_before();
     __syncthreads();
@@ -1424,6 +1484,33 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                                                 master[32 * h + 4 * q + 2], master[32 * h + 4 * q + 3]);
                         }
                         fence_proxy_async();
+                        if (p.q_mode && p.ksplit == 1) {
+                            // quantisation fused: this thread's pixel, read back from the rows
+                            // it has just staged (no registers held for it)
+                            bool valid;
+                            int64_t opix;
+                            if (p.mode == MODE_FLAT) {
+                                valid = p0 + m < p.rows;
+                                opix = p0 + m;
+                            } else {
+                                const int gi = i0 + m / p.Wt, gj = j0 + m % p.Wt;
+                                valid = gi < p.Gh && gj < p.Gw;
+                                opix = ((int64_t)b * p.Ho + p.oym * gi + p.oyo) * p.Wo + p.oxm * gj + p.oxo;
+                            }
+                            if (valid) {
+                                const int64_t HW = (int64_t)p.Ho * p.Wo;
+                                const int fb = (int)(opix / HW);
+#pragma unroll 1
+                                for (int u = 0; u < HALF * 8; ++u) {
+                                    const int h = u >> 3, q = u & 7;
+                                    const float4 v4 = *reinterpret_cast<const float4 *>(otile + h * AREA + m * 128 +
+                                                                                        ((q ^ (m & 7)) << 4));
+                                    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+                                    fused_quant<4>(p, v, fb, opix - (int64_t)fb * HW, HW, p.ocoff + cbase + 32 * h + 4 * q,
+                                                   opix, s_qtab);
+                                }
+                            }
+                        }
                     }
                     esync();
                     if (ok && et == 0 && !*abort_flag) {
@@ -1912,6 +1999,9 @@ void launch_kernel(unsigned grid, int smem, cudaStream_t st, const CUtensorMap &
 // bias and ReLU, and writes them where the fused store would have (FLAT rows,
 // or pixel (i, j) of the tile's R x Wt block at output (i oym + oyo, j oxm + oxo)).
 __global__ void __launch_bounds__(256) tcx_splitk_sum_kernel(const float4 *__restrict__ part, const Params p) {
+    __shared__ float s_qtab[64];   // fused scale index: the 64 scales
+    if (p.q_mode == 2 && threadIdx.x < 64) s_qtab[threadIdx.x] = p.q_tab[threadIdx.x];
+    __syncthreads();
     const int64_t rows = (int64_t)p.ntiles * BLOCK_M;
     const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (idx >= rows * 32) return;
@@ -1919,15 +2009,17 @@ __global__ void __launch_bounds__(256) tcx_splitk_sum_kernel(const float4 *__res
     const int64_t row = idx / 32;
     const int tile = (int)(row / BLOCK_M), m = (int)(row % BLOCK_M);
     int64_t o;
+    int64_t opix;
     if (p.mode == MODE_FLAT) {
         if (row >= p.rows) return;
-        o = row * p.ostride;
+        opix = row;
     } else {
         const int tx = tile % p.tiles_x, t = tile / p.tiles_x;
         const int i = (t % p.tiles_y) * p.R + m / p.Wt, j = tx * p.Wt + m % p.Wt, b = t / p.tiles_y;
         if (i >= p.Gh || j >= p.Gw) return;
-        o = (((int64_t)b * p.Ho + (int64_t)i * p.oym + p.oyo) * p.Wo + (int64_t)j * p.oxm + p.oxo) * p.ostride;
+        opix = ((int64_t)b * p.Ho + (int64_t)i * p.oym + p.oyo) * p.Wo + (int64_t)j * p.oxm + p.oxo;
     }
+    o = opix * p.ostride;
     float4 acc = part[idx];
     for (int q = 1; q < p.ksplit; ++q) {
         const float4 x = part[q * rows * 32 + idx];
@@ -1948,6 +2040,12 @@ __global__ void __launch_bounds__(256) tcx_splitk_sum_kernel(const float4 *__res
         acc.w = fmaxf(acc.w, 0.f);
     }
     *reinterpret_cast<float4 *>(p.out + o + p.ocoff + 4 * c4) = acc;
+    if (p.q_mode) {
+        const int64_t HW = (int64_t)p.Ho * p.Wo;
+        const int fb = (int)(opix / HW);
+        const float v[4] = {acc.x, acc.y, acc.z, acc.w};
+        fused_quant<4>(p, v, fb, opix - (int64_t)fb * HW, HW, p.ocoff + 4 * c4, opix, s_qtab);
+    }
 }
 
 // ------------------------------------------------------------------ persistent low-precision kernel (Cout = 128)
@@ -2546,6 +2644,11 @@ bool can_run(const ConvDesc &d, const TcWeights &w) {
     return d.s == 1;
 }
 
+bool tc_fuses_quant(const ConvDesc &d) {
+    return d.q_mode != 0 && d.Cout == 128 && (d.epi == EPI_NONE || d.epi == EPI_RELU) && d.fuse_gdn == 0 &&
+           d.out_dt == DT_F32;
+}
+
 bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     Params p{};
     p.ksplit = 1;
@@ -2582,6 +2685,18 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.ocoff = d.out_coff;
     p.out_inv_scale = d.out_scale > 0.f ? 1.f / d.out_scale : 1.f;
     p.tmem_cols = 512;  // partial sums (+ A slots when Cout = 128)
+    // fused quantisation: the persistent Cout = 128 kernel and its split-K sum
+    // (their epilogues overlap the next tile); the one-tile-per-CTA kernel
+    // leaves it to the caller (tc_fuses_quant)
+    if (d.out_dt == DT_F32 && tc_fuses_quant(d)) {
+        p.q_mode = d.q_mode;
+        p.q_C = d.q_C;
+        p.q_sym = d.q_sym;
+        p.q_hat = d.q_hat;
+        p.q_mu = d.q_mu;
+        p.q_idx = d.q_idx;
+        p.q_tab = d.q_tab;
+    }
     for (int t = 0; t < d.T; ++t) {
         p.du[t] = d.du[t];
         p.dv[t] = d.dv[t];

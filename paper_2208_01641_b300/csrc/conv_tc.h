@@ -40,6 +40,11 @@ bool can_run(const ConvDesc &d, const TcWeights &w);
 // encoded, in which case the caller runs the CUDA-core kernel instead.
 bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
 
+// Whether launch() applies d.q_mode in the epilogue (the persistent Cout = 128
+// kernel and its split-K sum do; the one-tile-per-CTA kernel, whose epilogue
+// nothing overlaps, measured slower with it than the separate kernels).
+bool tc_fuses_quant(const ConvDesc &d);
+
 // The K slices launch() cuts each 128-pixel tile into (1: none).  Above 1 it
 // runs a second kernel that adds the slices' partial sums in slice order.  The
 // count depends on the layer and the frame size only (never on the batch, the

@@ -181,16 +181,19 @@ __global__ void quantize_kernel(QuantF fn, int B) { tile_nhwc_to_nchw(B, fn.P, f
 
 // tab: the 64 scales, in shared memory (the threads of a warp probe different
 // entries; constant memory would serialise those reads)
+// smallest k with scales[k] >= sg (scales increasing), else 63.  The scales
+// are log-spaced (0.11 .. 256 in 63 steps): log(sg / 0.11) over the step
+// lands within one of k, and comparisons with the table itself settle it.
 __device__ __forceinline__ uint8_t index_one(float sg, const float *tab) {
     if (sg != sg) return 63;
     sg = fmaxf(sg, tab[0]);
-    // smallest k with scales[k] >= sg (scales increasing), else 63
-    int lo = 0, hi = 63;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (tab[mid] >= sg) hi = mid; else lo = mid + 1;
-    }
-    return (uint8_t)lo;
+    if (sg > tab[63]) return 63;
+    constexpr float kPerLog = 8.1266f;   // 63 / ln(256 / 0.11)
+    int k = (int)ceilf(__logf(sg * (1.f / 0.11f)) * kPerLog);
+    k = min(max(k, 0), 63);
+    while (k < 63 && tab[k] < sg) ++k;
+    while (k > 0 && tab[k - 1] >= sg) --k;
+    return (uint8_t)k;
 }
 
 struct IndexF {

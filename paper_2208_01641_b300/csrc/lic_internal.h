@@ -287,6 +287,22 @@ struct ConvDesc {
     int T;
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
     int in_xform, epi;
+    // quantisation fused into the epilogue of a float32 output (tensor-core
+    // kernels; launch_conv_simt and the low-precision kernels ignore it):
+    // q_mode 1: q_sym[b][c][hw] = rint(fl32(y - q_mu[c])) (q_mu may be null),
+    //   saturated to +-2^30, NaN -> 0, and, if q_hat, q_hat (NHWC, q_C
+    //   channels) = fl32(s + q_mu[c]); q_mode 2: q_idx[b][c][hw] = the scale
+    //   index of y (smallest k with q_tab[k] >= max(y, q_tab[0]), NaN or above
+    //   q_tab[63] -> 63; q_tab = the 64 scales in device memory).  c counts
+    //   the whole layer's q_C channels (out_coff included); hw the output
+    //   pixel within its frame.
+    int q_mode;
+    int32_t *q_sym;
+    float *q_hat;
+    const float *q_mu;
+    uint8_t *q_idx;
+    const float *q_tab;
+    int q_C;
 };
 
 void launch_conv_simt(const ConvDesc &d, cudaStream_t st);
