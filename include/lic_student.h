@@ -39,7 +39,7 @@ typedef struct lic_student lic_student;
 #define LIC_STUDENT_MAX_BATCH 64
 
 typedef struct {
-    int precision;   /* LIC_FP32 (the only value accepted) */
+    int precision;   /* LIC_FP32, or LIC_BF16 (C = 64, M a multiple of 64): bf16 tensor-core form */
     int max_batch;   /* crops per training step, 1 .. LIC_STUDENT_MAX_BATCH */
     int crop;        /* crop side in output pixels, a multiple of 16, >= 32 */
     float lr, beta1, beta2, eps;   /* Adam hyper-parameters */
@@ -95,8 +95,16 @@ int lic_student_read(lic_student *student, const char *name, int what, float *ds
 /* Diagnostics: the post-ReLU activation h_layer (layer 1..3) of the last
  * lic_student_grad/step batch, NHWC [B, 16 L/2^(4-layer), same, C] float32,
  * copied to the host buffer dst of numel elements (must equal that size for
- * the batch's B).  Synchronous. */
+ * the batch's B).  layer 0 is the gathered y_hat window, NHWC [B, L, L, M].
+ * Values stored in bf16 (the BF16 form) are widened exactly.  Synchronous. */
 int lic_student_read_activation(lic_student *student, int layer, float *dst, int64_t numel);
+
+/* Diagnostics: dz_layer (layer 0..3), the loss gradient with respect to the
+ * pre-activation output of transposed conv `layer` in the last batch (the
+ * backward pass of the chain rule above), NHWC [B, 16 L/2^(3-layer), same,
+ * Cout] float32, as stored (bf16 values widened exactly), into dst of numel
+ * elements (must equal that size).  Synchronous. */
+int lic_student_read_output_grad(lic_student *student, int layer, float *dst, int64_t numel);
 
 /* Adam steps taken so far, or a negative LIC_E_*. */
 int64_t lic_student_steps(const lic_student *student);

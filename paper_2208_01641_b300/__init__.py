@@ -44,7 +44,7 @@ EXPORTED = [
     "lic_probe_mma_rate", "lic_strip_resume_records",
     # include/lic_student.h (learned form)
     "lic_student_create", "lic_student_destroy", "lic_student_grad", "lic_student_step", "lic_student_read",
-    "lic_student_read_activation", "lic_student_steps", "lic_student_forward", "lic_student_profile_enable", "lic_student_profile_report",
+    "lic_student_read_activation", "lic_student_read_output_grad", "lic_student_steps", "lic_student_forward", "lic_student_profile_enable", "lic_student_profile_report",
     "lic_student_launch_count", "lic_codec_set_student", "lic_codec_student_report",
     # include/lic_serve.h (serving form)
     "lic_server_create", "lic_server_destroy", "lic_server_prepare", "lic_server_submit", "lic_server_poll",
@@ -161,6 +161,7 @@ def _lib():
         L.lic_student_step.argtypes = [vp, vp, vp, i, i, i, vp, i, ctypes.POINTER(ctypes.c_float), vp]
         L.lic_student_read.argtypes = [vp, ctypes.c_char_p, i, vp, i64]
         L.lic_student_read_activation.argtypes = [vp, i, vp, i64]
+        L.lic_student_read_output_grad.argtypes = [vp, i, vp, i64]
         L.lic_student_steps.argtypes = [vp]
         L.lic_student_steps.restype = i64
         L.lic_student_forward.argtypes = [vp, vp, i, i, i, vp, vp]
@@ -548,11 +549,21 @@ class Student:
         return out
 
     def activation(self, layer: int, B: int) -> np.ndarray:
-        """Post-ReLU h_layer of the last training batch, NHWC."""
+        """Post-ReLU h_layer of the last training batch, NHWC (layer 0: the
+        gathered y_hat window)."""
         side = (self.crop + 32 * self.halo) >> (4 - layer)
-        out = np.zeros((B, side, side, self.C), np.float32)
+        out = np.zeros((B, side, side, self.M if layer == 0 else self.C), np.float32)
         _check(_lib().lic_student_read_activation(self.h, layer, _ptr(out), out.size),
                "lic_student_read_activation")
+        return out
+
+    def output_grad(self, layer: int, B: int) -> np.ndarray:
+        """dz_layer of the last training batch (the loss gradient at transposed
+        conv `layer`'s pre-activation output), NHWC."""
+        side = (self.crop + 32 * self.halo) >> (3 - layer)
+        out = np.zeros((B, side, side, 3 if layer == 3 else self.C), np.float32)
+        _check(_lib().lic_student_read_output_grad(self.h, layer, _ptr(out), out.size),
+               "lic_student_read_output_grad")
         return out
 
     def params(self) -> "Dict[str, np.ndarray]":

@@ -2958,6 +2958,292 @@ void launch_wait_probe(uint32_t *status, long long limit_cycles, cudaStream_t st
     wait_probe_kernel<<<1, 1, 0, st>>>(status, limit_cycles);
 }
 
+namespace {
+
+// ------------------------------------------------------------------ weight gradient (bf16)
+//
+// wgrad_tc_kernel: the weight gradient of a transposed conv 5x5 / stride 2
+// (pad 2) whose input x (NHWC [B][H][W][Cin], Cin = 64 CB) and output
+// gradient dz (NHWC [B][2H][2W][64]) are stored in bf16,
+//     dW[i][o][u][v] = sum_{b,a,c} x[b,a,c,i] dz[b, 2a+u-2, 2c+v-2, o],
+// as GEMMs over K = the input pixels on tcgen05 (kind::f16, bf16 x bf16 ->
+// float32 in TMEM).  The rows of an MMA are a pair of taps x the 64 output
+// channels (tap 2j in TMEM lanes 0..63, tap 2j+1 in 64..127; the thirteenth
+// pair loads tap 24 twice and drops its second half), the columns the Cin
+// input channels.  Both operands are activation boxes as TMA lands them --
+// one pixel per 128-byte swizzled row, channels contiguous -- read as
+// MN-major matrices: a K step of 16 pixels is 2048 bytes, the 64-channel
+// blocks (the two taps of A, the CB blocks of B) lie one box (8 KB) apart,
+// 8-pixel groups 1024 bytes apart.  dz of tap (u, v) over a block of input
+// pixels (a, c) is one box of the pixel-pair view (2*64, W, 2, H, B) of dz
+// at ((v-2) & 1) * 64, c + ((v-2) >> 1), (u-2) & 1, a + ((u-2) >> 1), b):
+// positions outside the output grid come back zero-filled and add nothing,
+// as they add nothing to the sum; so do the zero-filled pixels past H or W.
+// Work units (pair j, slice z of 64-pixel tiles) run over a persistent grid;
+// unit (j, z) stores its sums at part[z][i][tap * 64 + o], and the caller adds
+// the slices in slice order (fixed, so results do not depend on the launch).
+//   warp 0      TMA producer (a stage = one tile: CB x-boxes + two dz boxes)
+//   warp 1      TMEM allocation; one lane issues the MMAs
+//   warps 2..5  epilogue (TMEM lanes 32 (warp % 4) ..): two accumulators
+//               alternate, so a unit's store overlaps the next unit's MMAs
+// Every wait is bounded; one that runs out latches ST_TIMEOUT and the CTA
+// winds down after its copies and MMAs in flight have landed.
+constexpr int WG_KP = 64;                  // input pixels per stage (one tile, R x Wt)
+constexpr int WG_BOX = WG_KP * 128;        // bytes of one 64-channel box
+constexpr int WG_PAIRS = 13;               // tap pairs (25 taps)
+constexpr int WG_THREADS = 192;
+constexpr int WG_UNITS_TARGET = 2 * 148;   // work units aimed at (a constant: the split never depends on the device)
+
+struct WgParams {
+    float *part;
+    uint32_t *status;
+    int R, Wt, tiles_x, tiles_y, ntiles, tps, units;
+};
+
+// kind::f16 with both operands MN-major (bits 15 and 16: A and B transposed)
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
+    return idesc_bf16(M, N) | (1u << 15) | (1u << 16);
+}
+
+// MN-major shared-memory descriptor, 128-byte swizzle: 64-element blocks
+// along M / N `lbo` bytes apart, 8-row groups along K 1024 bytes apart
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;  // leading byte offset: between 64-element MN blocks
+    d |= (uint64_t)(1024u >> 4) << 32;            // stride byte offset: between 8-row K groups
+    d |= (uint64_t)1u << 46;                      // descriptor version
+    d |= (uint64_t)2u << 61;                      // SWIZZLE_128B
+    return d;
+}
+
+template <int CB, int STAGES>
+__global__ void __launch_bounds__(WG_THREADS, 1) wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                                 const __grid_constant__ CUtensorMap tmD,
+                                                                 const __grid_constant__ WgParams p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int CIN = 64 * CB;
+    constexpr int STAGE = (CB + 2) * WG_BOX;
+    constexpr uint32_t ACC = CIN <= 64 ? 64 : 256;     // TMEM columns between the two accumulators
+    constexpr uint32_t TCOLS = CIN <= 64 ? 128 : 512;
+    constexpr int N = 25 * 64;                          // columns of a part row
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
+    uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES, *tempty = tfull + 2;
+    uint64_t *drained = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drained + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&tfull[q], 1);
+            mbar_init(&tempty[q], 128);
+        }
+        mbar_init(drained, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, TCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(p.status, ST_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0, issued = 0;   // stages filled by this CTA, across its units
+            for (int u = blockIdx.x; u < p.units && !*abort_flag; u += gridDim.x) {
+                const int j = u % WG_PAIRS, z = u / WG_PAIRS;
+                const int taps[2] = {2 * j, min(2 * j + 1, 24)};
+                const int k1 = min(p.ntiles, (z + 1) * p.tps);
+                for (int k = z * p.tps; k < k1; ++k, ++it) {
+                    const int s = it % STAGES;
+                    if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1)) {
+                        fail();
+                        break;
+                    }
+                    int t = k;
+                    const int tx = t % p.tiles_x;
+                    t /= p.tiles_x;
+                    const int ty = t % p.tiles_y, b = t / p.tiles_y;
+                    const int a0 = ty * p.R, c0 = tx * p.Wt;
+                    uint8_t *st = smem + s * STAGE;
+                    mbar_expect_tx(&full[s], STAGE);
+#pragma unroll
+                    for (int cb = 0; cb < CB; ++cb) tma_load_4d(st + cb * WG_BOX, &tmX, &full[s], 64 * cb, c0, a0, b);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int du = taps[h] / 5 - 2, dv = taps[h] % 5 - 2;
+                        tma_load_5d(st + (CB + h) * WG_BOX, &tmD, &full[s], (dv & 1) * 64, c0 + (dv >> 1), du & 1,
+                                    a0 + (du >> 1), b);
+                    }
+                    issued = it + 1;
+                }
+            }
+            if (*abort_flag) {   // let the copies in flight land before the CTA exits
+                for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc)
+                    mbar_wait(&full[kc % STAGES], (kc / STAGES) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_mn(128, CIN);
+            int it = 0, n = 0;   // stages consumed, units done
+            for (int u = blockIdx.x; u < p.units; u += gridDim.x, ++n) {
+                const int z = u / WG_PAIRS;
+                const int k0 = z * p.tps, k1 = min(p.ntiles, k0 + p.tps);
+                const int q = n & 1;
+                if (n >= 2 && (*abort_flag || !mbar_wait(&tempty[q], ((n >> 1) - 1) & 1))) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + q * ACC;
+                bool ok = true;
+                for (int k = k0; k < k1; ++k, ++it) {
+                    const int s = it % STAGES;
+                    if (*abort_flag || !mbar_wait(&full[s], (it / STAGES) & 1)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t xb = smem_u32(smem + s * STAGE), db = xb + CB * WG_BOX;
+#pragma unroll
+                    for (int kk = 0; kk < WG_KP / 16; ++kk)
+                        mma_bf16(dt, sdesc_mn(db + kk * 2048, WG_BOX), sdesc_mn(xb + kk * 2048, WG_BOX), idesc,
+                                 (k > k0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&tfull[q]);
+            }
+            mma_commit(drained);   // arrives once every MMA issued above has completed
+        }
+    } else {
+        const int quarter = warp & 3;
+        const int m = quarter * 32 + lane;   // TMEM lane = GEMM row (tap half, output channel)
+        const int h = m >> 6, o = m & 63;
+        int n = 0;
+        for (int u = blockIdx.x; u < p.units; u += gridDim.x, ++n) {
+            const int j = u % WG_PAIRS, z = u / WG_PAIRS;
+            const int q = n & 1;
+            if (*abort_flag || !mbar_wait(&tfull[q], (n >> 1) & 1)) {
+                fail();
+                break;
+            }
+            tc_fence_after();
+            const int tap = 2 * j + h;
+            float *dst = p.part + (int64_t)z * CIN * N + tap * 64 + o;
+            const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + q * ACC;
+#pragma unroll 1
+            for (int c = 0; c < CIN; c += 32) {
+                float v[32];
+                tmem_ld32(ta + c, v);
+                if (tap < 25) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) dst[(int64_t)(c + i) * N] = v[i];   // a warp: 32 consecutive o
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[q]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        if (!mbar_wait(drained, 0)) {   // TMEM is released only after the MMAs are done
+            atomicOr(p.status, ST_TIMEOUT);
+            mbar_wait(drained, 0);
+        }
+        tmem_dealloc(tmem, TCOLS);
+    }
+}
+
+// 64-pixel tiles R x Wt of an H x W grid, the fewest padded pixels (ties: wider)
+void wgrad_tile(int H, int W, int *R, int *Wt) {
+    double best = 1e30;
+    for (int wt = 64; wt >= 8; wt /= 2) {
+        const int r = WG_KP / wt;
+        const double area = (double)((W + wt - 1) / wt * wt) * ((H + r - 1) / r * r);
+        if (area < best - 1e-9) {
+            best = area;
+            *R = r;
+            *Wt = wt;
+        }
+    }
+}
+
+void wgrad_plan(int B, int H, int W, WgParams *p) {
+    wgrad_tile(H, W, &p->R, &p->Wt);
+    p->tiles_x = (W + p->Wt - 1) / p->Wt;
+    p->tiles_y = (H + p->R - 1) / p->R;
+    p->ntiles = p->tiles_x * p->tiles_y * B;
+    int ns = std::max(1, std::min(p->ntiles, (WG_UNITS_TARGET + WG_PAIRS - 1) / WG_PAIRS));
+    p->tps = (p->ntiles + ns - 1) / ns;
+    ns = (p->ntiles + p->tps - 1) / p->tps;
+    p->units = ns * WG_PAIRS;
+}
+
+template <int CB, int STAGES>
+bool launch_wgrad_cb(const CUtensorMap &tmX, const CUtensorMap &tmD, const WgParams &p, cudaStream_t st) {
+    // stages, barriers, alignment, and 16 KB of slack past the last stage
+    const int smem = STAGES * (CB + 2) * WG_BOX + 256 + 1024 + 16384;
+    if (cudaFuncSetAttribute(wgrad_tc_kernel<CB, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return false;
+    const unsigned grid = (unsigned)std::min(p.units, sm_count());
+    wgrad_tc_kernel<CB, STAGES><<<grid, WG_THREADS, smem, st>>>(tmX, tmD, p);
+    return true;
+}
+
+}  // namespace
+
+int wgrad_bf16_slices(int B, int H, int W) {
+    WgParams p{};
+    wgrad_plan(B, H, W, &p);
+    return p.units / WG_PAIRS;
+}
+
+bool launch_wgrad_bf16(const void *x, const void *dz, int B, int H, int W, int Cin, float *part, uint32_t *status,
+                       cudaStream_t st) {
+    if ((Cin != 64 && Cin != 128 && Cin != 192) || B < 1 || H < 1 || W < 1 || !x || !dz || !part ||
+        (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(dz) & 15))
+        return false;
+    WgParams p{};
+    wgrad_plan(B, H, W, &p);
+    p.part = part;
+    p.status = status;
+    const uint64_t C = (uint64_t)Cin, E = 2;
+    CUtensorMap tmX, tmD;
+    {
+        const uint64_t dims[4] = {C, (uint64_t)W, (uint64_t)H, (uint64_t)B};
+        const uint64_t strides[3] = {C * E, (uint64_t)W * C * E, (uint64_t)H * W * C * E};
+        const uint32_t box[4] = {64, (uint32_t)p.Wt, (uint32_t)p.R, 1};
+        if (!make_map(&tmX, x, 4, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16)) return false;
+    }
+    {
+        // dz [B][2H][2W][64] as (2 * 64, W, 2, H, B): a pixel pair per row of 128 values, rows of one parity
+        const uint64_t row = 2ull * W * 64 * E;
+        const uint64_t dims[5] = {128, (uint64_t)W, 2, (uint64_t)H, (uint64_t)B};
+        const uint64_t strides[4] = {128 * E, row, 2 * row, 2ull * H * row};
+        const uint32_t box[5] = {64, (uint32_t)p.Wt, 1, (uint32_t)p.R, 1};
+        if (!make_map(&tmD, dz, 5, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16)) return false;
+    }
+    if (Cin == 64) return launch_wgrad_cb<1, 8>(tmX, tmD, p, st);
+    if (Cin == 128) return launch_wgrad_cb<2, 6>(tmX, tmD, p, st);
+    return launch_wgrad_cb<3, 5>(tmX, tmD, p, st);
+}
+
 // ------------------------------------------------------------------ MMA rate probe
 //
 // The dense rate of the tensor pipe, measured: every CTA (one per SM) issues

@@ -70,6 +70,16 @@ bool make_bf16_weight_map(TmaMap *m, const void *w, int Cout, int K);
 // may be null.  false = not launched.
 bool can_run_lp_map(const ConvDesc &d);
 
+// Weight gradient of a transposed conv 5x5 / stride 2 (pad 2) with bf16
+// operands on tcgen05: x NHWC [B][H][W][Cin] (Cin 64, 128 or 192), dz NHWC
+// [B][2H][2W][64], both device, 16-byte aligned.  Writes the float32 sums of
+// wgrad_bf16_slices(B, H, W) pixel slices into part[z][Cin][25 * 64] (column
+// tap * 64 + o, tap = 5u + v); the caller adds the slices in order.  false =
+// not launched (shape or tensor map not handled).
+int wgrad_bf16_slices(int B, int H, int W);
+bool launch_wgrad_bf16(const void *x, const void *dz, int B, int H, int W, int Cin, float *part, uint32_t *status,
+                       cudaStream_t st);
+
 // The bounded mbarrier wait of the kernels, on a barrier nothing arrives at:
 // gives up after limit_cycles and latches ST_TIMEOUT in *status.
 void launch_wait_probe(uint32_t *status, long long limit_cycles, cudaStream_t st);

@@ -616,6 +616,20 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
                                                               s->grad.as<float>() + s->boff[l]);
             });
         }
+        // weight gradient, BF16 form: the tcgen05 kernel over pixel slices, then the slices in order
+        if (s->bf16 && l < NL - 1) {
+            const double flop = 2.0 * P_in * (double)Cin * Cout * 25;
+            const double bytes = P_in * (double)Cin * 2 + P_out * (double)Cout * 2 + 4.0 * wsize(s, l);
+            const int ns = tc::wgrad_bf16_slices(B, H, H);
+            timed(s, "student.wgrad" + std::to_string(l) + ":tc", flop, bytes, 2, st, [&] {
+                float *part = s->part.as<float>();
+                if (!tc::launch_wgrad_bf16(hl, dzl, B, H, H, Cin, part, s->status.as<uint32_t>(), st))
+                    s->launch_failed = true;
+                const int64_t ne = (int64_t)Cin * 25 * Cout;
+                wgrad_reduce_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(part, ns, Cin, Cout,
+                                                                                  s->grad.as<float>() + s->woff[l]);
+            });
+        } else
         // weight gradient: split K so that the grid covers the SMs a few times
         {
             const int N = 25 * Cout;
@@ -849,6 +863,11 @@ int lic_student_create(const lic_weights *init, int M, int C, const lic_student_
         const int64_t P_in = Bm * (side / 2) * (side / 2);
         const int64_t splits = std::min<int64_t>(std::max<int64_t>(1, (4 * 148) / tiles), (P_in + WG_BK - 1) / WG_BK);
         part_max = std::max<int64_t>(part_max, (splits + 1) * (int64_t)s->cin[l] * N);
+        if (s->bf16 && l < NL - 1)   // the tensor-core weight gradient's slices, for any batch up to Bm
+            for (int b = 1; b <= Bm; ++b)
+                part_max = std::max<int64_t>(part_max, (int64_t)tc::wgrad_bf16_slices(b, (int)(side / 2),
+                                                                                      (int)(side / 2)) *
+                                                           s->cin[l] * N);
     }
     if ((rc = ensure_f(s->out, (int64_t)Bm * S * S * 3)) || (rc = ensure_f(s->part, part_max)) ||
         (rc = ensure_f(s->bpart, (int64_t)(BG_BLOCKS + 1) * RED_T)) ||
@@ -922,22 +941,37 @@ int lic_student_read(lic_student *s, const char *name, int what, float *dst, int
     return LIC_E_INVALID_ARG;
 }
 
-int lic_student_read_activation(lic_student *s, int layer, float *dst, int64_t numel) {
-    if (!s || !dst || layer < 1 || layer > 3 || s->last_B < 1) return LIC_E_INVALID_ARG;
-    const int64_t side = (int64_t)((16 * window_lat(s)) >> (4 - layer));
-    if (numel != (int64_t)s->last_B * side * side * s->C) return LIC_E_INVALID_ARG;
+namespace {
+// n values of a float32 or bf16 device tensor -> host float32 (synchronous)
+int copy_widened(const void *src, bool bf16, float *dst, int64_t n) {
     LIC_CUDA_TRY(cudaDeviceSynchronize());
-    if (act_bytes(s, layer) == 4) {
-        LIC_CUDA_TRY(cudaMemcpy(dst, s->h[layer].p, (size_t)numel * sizeof(float), cudaMemcpyDeviceToHost));
+    if (!bf16) {
+        LIC_CUDA_TRY(cudaMemcpy(dst, src, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
         return LIC_OK;
     }
-    std::vector<uint16_t> raw((size_t)numel);
-    LIC_CUDA_TRY(cudaMemcpy(raw.data(), s->h[layer].p, (size_t)numel * 2, cudaMemcpyDeviceToHost));
-    for (int64_t i = 0; i < numel; ++i) {
+    std::vector<uint16_t> raw((size_t)n);
+    LIC_CUDA_TRY(cudaMemcpy(raw.data(), src, (size_t)n * 2, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) {
         const uint32_t u = (uint32_t)raw[i] << 16;
         memcpy(dst + i, &u, 4);
     }
     return LIC_OK;
+}
+}  // namespace
+
+int lic_student_read_activation(lic_student *s, int layer, float *dst, int64_t numel) {
+    if (!s || !dst || layer < 0 || layer > 3 || s->last_B < 1) return LIC_E_INVALID_ARG;
+    const int64_t side = (int64_t)((16 * window_lat(s)) >> (4 - layer));
+    const int ch = layer == 0 ? s->M : s->C;
+    if (numel != (int64_t)s->last_B * side * side * ch) return LIC_E_INVALID_ARG;
+    return copy_widened(s->h[layer].p, act_bytes(s, layer) == 2, dst, numel);
+}
+
+int lic_student_read_output_grad(lic_student *s, int layer, float *dst, int64_t numel) {
+    if (!s || !dst || layer < 0 || layer > 3 || s->last_B < 1) return LIC_E_INVALID_ARG;
+    const int64_t side = (int64_t)((16 * window_lat(s)) >> (3 - layer));
+    if (numel != (int64_t)s->last_B * side * side * s->cout[layer]) return LIC_E_INVALID_ARG;
+    return copy_widened(s->dz[layer].p, act_bytes(s, layer) == 2, dst, numel);
 }
 
 int64_t lic_student_steps(const lic_student *s) { return s ? s->t : LIC_E_INVALID_ARG; }

@@ -352,3 +352,28 @@ def test_trained_student_gain_over_teacher_and_untrained(SW):
     assert stu_flop < gs_flop / 3, (stu_flop, gs_flop)
     codec.close()
     st.close()
+
+
+def test_bf16_weight_gradients_on_tensor_cores_sum_exactly(SW):
+    """The BF16 form's weight gradients of the three 64-channel layers come
+    from the tcgen05 kernel (bf16 operands as stored, float32 sums in TMEM,
+    pixel slices added in order).  Against the oracle's weight gradient of a
+    transposed conv evaluated in float64 on the GPU's own stored h_l and dz_l
+    they agree to 1e-5 of each tensor's largest magnitude: only the float32
+    summation differs.  The 7 x 7, 14 x 14 and 28 x 28 grids (crop 80, halo
+    1) leave ragged 64-pixel tiles, and the 28 x 28 layer runs 21 slices."""
+    yp, xp = pools(2, 9, 10, seed=21)
+    crops = np.array([[0, 0, 0], [1, 2, 3], [1, 1, 1]], np.int32)
+    B = len(crops)
+    st = lic.Student(SW, M, C, max_batch=4, crop=80, halo=1, precision=lic.BF16)
+    st.grad(torch.from_numpy(yp).cuda(), torch.from_numpy(xp).cuda(), crops)
+    for l in range(3):
+        x = st.activation(l, B).transpose(0, 3, 1, 2)
+        dz = st.output_grad(l, B).transpose(0, 3, 1, 2)
+        assert x.shape[-1] == 7 << l and dz.shape[-1] == 14 << l
+        want = O.deconv2d_wgrad(x, dz)
+        got = st.read(f"student.deconv{l}.weight", lic.STUDENT_GRAD)
+        assert np.abs(want).max() > 0
+        err = np.abs(got - want).max()
+        assert err <= 1e-5 * np.abs(want).max(), (l, err, np.abs(want).max())
+    st.close()
