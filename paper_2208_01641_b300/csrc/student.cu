@@ -267,16 +267,298 @@ __global__ void __launch_bounds__(WG_NT) wgrad_kernel(const TX *__restrict__ x, 
     }
 }
 
-// dW[i][o][u][v] = sum over z (in order) of part[z][i][(u*5+v)*Cout + o]
-__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int nz, int Cin, int Cout, float *__restrict__ dw) {
-    const int N = 25 * Cout;
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= (int64_t)Cin * N) return;
-    const int i = (int)(e / N), n = (int)(e % N);
-    float s = 0.f;
-    for (int z = 0; z < nz; ++z) s += part[((int64_t)z * Cin + i) * N + n];
-    dw[((int64_t)i * Cout + n % Cout) * 25 + n / Cout] = s;
+// Weight gradient of the 3-channel last layer (float32 h and dz):
+// dW[i][o][u][v] = sum_{b,a,c} h[b,a,c,i] dz[b, 2a+u-2, 2c+v-2, o].  Per
+// pixel that is a 64 x 75 outer product of h's channels with dz's 5 x 5 x 3
+// window, so the kernel is bound by FMA issue.  A work unit is 2 input rows
+// x 128 columns x 64 input channels of one frame: the dz rows it touches go
+// to shared memory as a zero-padded strip (7 rows x 260 columns x 3), h in
+// chunks of 32 pixels; both are double-buffered and fetched with cp.async one
+// chunk ahead, so the loads overlap the FMAs.  Warp u (0..4) owns the 15
+// window values of tap row u -- contiguous in the strip -- and each lane 8
+// channels (4 ig .. 4 ig + 3 and 32 + 4 ig ..: a quarter warp's 16-byte
+// loads cover 128 contiguous bytes) x those 15 values for every fourth pixel
+// of a chunk (lane = 8 pixel slot + ig): a pixel step is 2 x 16-byte h loads and 15
+// strip values for 120 FMAs.  The four pixel slots are added by shuffles at
+// the end, and block z's sums go to part[z][i][(5u+v)*3 + o]
+// (wgrad_reduce_kernel adds the blocks in order).
+constexpr int W3_TR = 2, W3_TC = 128, W3_PC = 32, W3_T = 160, W3_BLOCKS = 2 * 148;
+constexpr int W3_SR = 2 * W3_TR + 3, W3_SP = (2 * W3_TC + 4) * 3;   // strip rows, row pitch (floats)
+constexpr int W3_CPU = W3_TR * (W3_TC / W3_PC);                      // chunks per unit
+
+__device__ __forceinline__ uint32_t sh_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// global -> shared without registers; bytes past src_bytes (0 or all) are zero-filled
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sh_addr(dst)), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sh_addr(dst)), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+__global__ void __launch_bounds__(W3_T, 2) wgrad3_kernel(const float *__restrict__ h, const float *__restrict__ dz,
+                                                         int B, int H, int W, int Cin, int per_block,
+                                                         float *__restrict__ part) {
+    extern __shared__ __align__(16) float w3_smem[];
+    float *strip = w3_smem;                        // [2][W3_SR * W3_SP]
+    float *hs = w3_smem + 2 * W3_SR * W3_SP;       // [2][W3_PC][64]
+    const int tid = threadIdx.x, u = tid >> 5, lane = tid & 31, ig = lane & 7, ps = lane >> 3;
+    const int tiles_x = (W + W3_TC - 1) / W3_TC, rows = (H + W3_TR - 1) / W3_TR, ichunks = (Cin + 63) / 64;
+    const int nunits = tiles_x * rows * B * ichunks;
+    const int Ho = 2 * H, Wo = 2 * W;
+    const int u_begin = blockIdx.x * per_block, u_end = min(nunits, u_begin + per_block);
+    float acc[8][15];
+    for (int ic = 0; ic < ichunks; ++ic) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int k = 0; k < 15; ++k) acc[i][k] = 0.f;
+        // this chunk's units: un0, un0 + ichunks, ... below u_end (units interleave the channel chunks)
+        const int un0 = u_begin + ((ic - u_begin % ichunks) % ichunks + ichunks) % ichunks;
+        const int nu = un0 < u_end ? (u_end - 1 - un0) / ichunks + 1 : 0;
+        const int jobs = nu * W3_CPU;
+        // unit k's frame and corner
+        auto unit = [&](int k, int *b, int *a0, int *c0) {
+            int r = (un0 + k * ichunks) / ichunks;
+            const int tx = r % tiles_x;
+            r /= tiles_x;
+            *a0 = (r % rows) * W3_TR;
+            *b = r / rows;
+            *c0 = tx * W3_TC;
+        };
+        // issue job j's loads: its h chunk, and the unit's strip when j opens a unit
+        auto issue = [&](int j) {
+            if (j < jobs) {
+                int b, a0, c0;
+                unit(j / W3_CPU, &b, &a0, &c0);
+                const int c = j % W3_CPU, rr = c / (W3_TC / W3_PC), cc = (c % (W3_TC / W3_PC)) * W3_PC;
+                if (c == 0) {
+                    float *sb = strip + ((j / W3_CPU) & 1) * (W3_SR * W3_SP);
+                    for (int e = tid; e < W3_SR * W3_SP; e += W3_T) {
+                        const int sr = e / W3_SP, rem = e % W3_SP;
+                        const int y = 2 * a0 - 2 + sr, x = 2 * c0 - 2 + rem / 3;
+                        const bool ok = y >= 0 && y < Ho && x >= 0 && x < Wo;
+                        cp_async4(sb + e, ok ? dz + (((int64_t)b * Ho + y) * Wo + x) * 3 + rem % 3 : dz, ok);
+                    }
+                }
+                float *hb = hs + (j & 1) * (W3_PC * 64);
+                const int a = a0 + rr, n = (a < H) ? max(0, min(W3_PC, W - c0 - cc)) : 0;
+                for (int e = tid; e < W3_PC * 16; e += W3_T) {
+                    const int px = e >> 4, q = e & 15, ch = 64 * ic + 4 * q;
+                    const bool ok = px < n && ch < Cin;
+                    cp_async16(hb + px * 64 + 4 * q,
+                               ok ? h + (((int64_t)b * H + a) * W + c0 + cc + px) * Cin + ch : h, ok);
+                }
+            }
+            cp_async_commit();   // an empty group past the last job keeps the wait count uniform
+        };
+        issue(0);
+        for (int j = 0; j < jobs; ++j) {
+            issue(j + 1);
+            cp_async_wait1();    // job j's group has landed (this thread's copies)
+            __syncthreads();     // ... and every thread's
+            int b, a0, c0;
+            unit(j / W3_CPU, &b, &a0, &c0);
+            const int c = j % W3_CPU, rr = c / (W3_TC / W3_PC), cc = (c % (W3_TC / W3_PC)) * W3_PC;
+            const int n = (a0 + rr < H) ? max(0, min(W3_PC, W - c0 - cc)) : 0;
+            const float *hb = hs + (j & 1) * (W3_PC * 64);
+            // window of pixel (a0 + rr, c0 + cc + px), tap row u: strip row 2 rr + u, columns 2 (cc + px) ..
+            const float *wrow = strip + ((j / W3_CPU) & 1) * (W3_SR * W3_SP) + (2 * rr + u) * W3_SP + 2 * cc * 3;
+            for (int px = ps; px < n; px += 4) {
+                const float4 h0 = *reinterpret_cast<const float4 *>(hb + px * 64 + 4 * ig);
+                const float4 h1 = *reinterpret_cast<const float4 *>(hb + px * 64 + 32 + 4 * ig);
+                const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                const float *wp = wrow + 6 * px;   // 8-byte aligned: 15 values as 7 pairs + 1
+                float w[15];
+#pragma unroll
+                for (int k = 0; k < 7; ++k) {
+                    const float2 t = *reinterpret_cast<const float2 *>(wp + 2 * k);
+                    w[2 * k] = t.x;
+                    w[2 * k + 1] = t.y;
+                }
+                w[14] = wp[14];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int k = 0; k < 15; ++k) acc[i][k] = fmaf(hv[i], w[k], acc[i][k]);
+            }
+            __syncthreads();     // job j's buffers are free for job j + 2's loads
+        }
+        // the four pixel slots of a channel group, then one store per (i, k)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int k = 0; k < 15; ++k) {
+                float v = acc[i][k];
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                acc[i][k] = v;
+            }
+        if (ps == 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int ci = 64 * ic + (i < 4 ? 4 * ig + i : 32 + 4 * ig + i - 4);
+                if (ci < Cin)
+#pragma unroll
+                    for (int k = 0; k < 15; ++k) part[((int64_t)blockIdx.x * Cin + ci) * 75 + 15 * u + k] = acc[i][k];
+            }
+        }
+        __syncthreads();
+    }
+}
+constexpr int W3_SMEM = (2 * W3_SR * W3_SP + 2 * W3_PC * 64) * 4;
+
+// Input gradient through the 3-channel last layer and the ReLU before it:
+// dz_prev[b,a,c,i] = [h[b,a,c,i] > 0] sum_{u,v,o} dz[b, 2a+u-2, 2c+v-2, o]
+// W[i][o][u][v] -- the stride-2 conv with the transposed conv's weights, its
+// adjoint.  Per pixel a 75 x 64 matrix-vector product, so the kernel is
+// bound by FMA issue.  The weights sit in shared memory as [k][i] (k =
+// (5u+v)*3+o); a work unit is the same 2 x 128 block of pixels as in
+// wgrad3_kernel with the same double-buffered dz strip, and each thread
+// computes 8 consecutive pixels of a row x 8 channels (4 ig .. 4 ig + 3 and
+// 32 + 4 ig .. 32 + 4 ig + 3): per k, 8 strip values (a warp's four pixel
+// groups: four broadcast addresses) and 2 x 16-byte weight loads for 64 FMAs.
+// The mask and the store (float32 or bf16, as the activation before it is
+// stored) follow in the epilogue.
+constexpr int D3_T = 256;
+constexpr int D3_SMEM = (2 * W3_SR * W3_SP + 75 * 64) * 4;
+
+template <typename TO>
+__global__ void __launch_bounds__(D3_T, 2) dgrad3_kernel(const float *__restrict__ dz, const float *__restrict__ wd,
+                                                        const float *__restrict__ h, int B, int H, int W,
+                                                        int per_block, TO *__restrict__ out) {
+    extern __shared__ __align__(16) float d3_smem[];
+    float *strip = d3_smem;                       // [2][W3_SR * W3_SP]
+    float *ws = d3_smem + 2 * W3_SR * W3_SP;      // [75][64]
+    const int tid = threadIdx.x, lane = tid & 31, ig = lane & 7;
+    const int pg = (tid >> 5) * 4 + (lane >> 3);   // pixel group 0..31: row pg / 16, columns 8 (pg % 16) ..
+    const int tiles_x = (W + W3_TC - 1) / W3_TC, rows = (H + W3_TR - 1) / W3_TR;
+    const int nunits = tiles_x * rows * B;
+    const int Ho = 2 * H, Wo = 2 * W;
+    const int u_begin = blockIdx.x * per_block, u_end = min(nunits, u_begin + per_block);
+    // weights: wd [64][25][3] (i, tap, o) -> ws[k][i], k = tap * 3 + o
+    for (int e = tid; e < 75 * 64; e += D3_T) ws[(e % 75) * 64 + e / 75] = wd[e];
+    auto unit = [&](int un, int *b, int *a0, int *c0) {
+        int r = un;
+        const int tx = r % tiles_x;
+        r /= tiles_x;
+        *a0 = (r % rows) * W3_TR;
+        *b = r / rows;
+        *c0 = tx * W3_TC;
+    };
+    auto issue = [&](int un, int slot) {
+        if (un < u_end) {
+            int b, a0, c0;
+            unit(un, &b, &a0, &c0);
+            float *sb = strip + slot * (W3_SR * W3_SP);
+            for (int e = tid; e < W3_SR * W3_SP; e += D3_T) {
+                const int sr = e / W3_SP, rem = e % W3_SP;
+                const int y = 2 * a0 - 2 + sr, x = 2 * c0 - 2 + rem / 3;
+                const bool ok = y >= 0 && y < Ho && x >= 0 && x < Wo;
+                cp_async4(sb + e, ok ? dz + (((int64_t)b * Ho + y) * Wo + x) * 3 + rem % 3 : dz, ok);
+            }
+        }
+        cp_async_commit();
+    };
+    const int rr = pg / 16, cq = (pg % 16) * 8;   // the thread's row and first column within a unit
+    issue(u_begin, 0);
+    for (int un = u_begin; un < u_end; ++un) {
+        const int slot = (un - u_begin) & 1;
+        issue(un + 1, slot ^ 1);
+        cp_async_wait1();
+        __syncthreads();   // the strip (and, the first time, the weights) are in place
+        int b, a0, c0;
+        unit(un, &b, &a0, &c0);
+        const int a = a0 + rr;
+        float acc[8][8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[j][i] = 0.f;
+        // pixel j = column c0 + cq + j: window element (u, v, o) at strip row 2 rr + u, column 2 (cq + j) + v
+        const float *sb = strip + slot * (W3_SR * W3_SP) + 2 * rr * W3_SP + 2 * cq * 3;
+#pragma unroll 1
+        for (int u = 0; u < 5; ++u) {
+#pragma unroll 1
+            for (int vo = 0; vo < 15; ++vo) {
+                const int k = u * 15 + vo;
+                const float4 w0 = *reinterpret_cast<const float4 *>(ws + k * 64 + 4 * ig);
+                const float4 w1 = *reinterpret_cast<const float4 *>(ws + k * 64 + 32 + 4 * ig);
+                const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                const float *xp = sb + u * W3_SP + vo;
+                float xv[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) xv[j] = xp[6 * j];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) acc[j][i] = fmaf(xv[j], wv[i], acc[j][i]);
+            }
+        }
+        if (a < H) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + cq + j;
+                if (c >= W) break;
+                const int64_t o = (((int64_t)b * H + a) * W + c) * 64;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int ch = half * 32 + 4 * ig;
+                    const float4 m = ld4(h, o + ch);
+                    const float v0 = m.x > 0.f ? acc[j][4 * half] : 0.f, v1 = m.y > 0.f ? acc[j][4 * half + 1] : 0.f;
+                    const float v2 = m.z > 0.f ? acc[j][4 * half + 2] : 0.f, v3 = m.w > 0.f ? acc[j][4 * half + 3] : 0.f;
+                    st(out, o + ch, v0);
+                    st(out, o + ch + 1, v1);
+                    st(out, o + ch + 2, v2);
+                    st(out, o + ch + 3, v3);
+                }
+            }
+        }
+        __syncthreads();   // this strip slot is free for the unit after next
+    }
+}
+
+void dgrad3_plan(int B, int H, int W, int *blocks, int *per_block) {
+    const int nunits = ((W + W3_TC - 1) / W3_TC) * ((H + W3_TR - 1) / W3_TR) * B;
+    *per_block = (nunits + W3_BLOCKS - 1) / W3_BLOCKS;
+    *blocks = (nunits + *per_block - 1) / *per_block;
+}
+
+// blocks of wgrad3_kernel and the units each takes (2 rows x 128 columns x
+// 64 channels); the grid is a fixed count, so the sums do not depend on the device
+void wgrad3_plan(int B, int H, int W, int Cin, int *blocks, int *per_block) {
+    const int nunits = ((W + W3_TC - 1) / W3_TC) * ((H + W3_TR - 1) / W3_TR) * B * ((Cin + 63) / 64);
+    *per_block = (nunits + W3_BLOCKS - 1) / W3_BLOCKS;
+    *blocks = (nunits + *per_block - 1) / *per_block;
+}
+
+// dW[i][o][u][v] = sum over z of part[z][i][(u*5+v)*Cout + o], in a fixed
+// order: a block takes 32 consecutive (i, column) entries; thread (g, t) adds
+// slices z = g, g + 8, ... in order, then the 8 group sums are added as a
+// fixed tree.  Eight loads in flight per entry instead of one chain of nz.
+constexpr int WR_G = 8;
+__global__ void __launch_bounds__(32 * WR_G) wgrad_reduce_kernel(const float *__restrict__ part, int nz, int Cin,
+                                                                 int Cout, float *__restrict__ dw) {
+    __shared__ float red[WR_G][33];
+    const int N = 25 * Cout;
+    const int t = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t ne = (int64_t)Cin * N, e = blockIdx.x * (int64_t)32 + t;
+    float s = 0.f;
+    if (e < ne)
+        for (int z = g; z < nz; z += WR_G) s += part[(int64_t)z * ne + e];
+    red[g][t] = s;
+    __syncthreads();
+    if (g == 0 && e < ne) {
+        const float a = (red[0][t] + red[1][t]) + (red[2][t] + red[3][t]);
+        const float b = (red[4][t] + red[5][t]) + (red[6][t] + red[7][t]);
+        const int i = (int)(e / N), n = (int)(e % N);
+        dw[((int64_t)i * Cout + n % Cout) * 25 + n / Cout] = a + b;
+    }
+}
+inline unsigned wgrad_reduce_grid(int64_t ne) { return (unsigned)((ne + 31) / 32); }
 
 // Adam over the flat parameter vector; c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
 __global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
@@ -626,7 +908,21 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
                 if (!tc::launch_wgrad_bf16(hl, dzl, B, H, H, Cin, part, s->status.as<uint32_t>(), st))
                     s->launch_failed = true;
                 const int64_t ne = (int64_t)Cin * 25 * Cout;
-                wgrad_reduce_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(part, ns, Cin, Cout,
+                wgrad_reduce_kernel<<<wgrad_reduce_grid(ne), 32 * WR_G, 0, st>>>(part, ns, Cin, Cout,
+                                                                                  s->grad.as<float>() + s->woff[l]);
+            });
+        } else if (l == NL - 1) {
+            // the 3-channel layer: float32 outer products over dz windows staged in shared memory
+            const double flop = 2.0 * P_in * (double)Cin * Cout * 25;
+            const double bytes = P_in * (double)Cin * 4 + P_out * (double)Cout * 4 + 4.0 * wsize(s, l);
+            int nb = 0, per = 0;
+            wgrad3_plan(B, H, H, Cin, &nb, &per);
+            timed(s, "student.wgrad" + std::to_string(l), flop, bytes, 2, st, [&] {
+                float *part = s->part.as<float>();
+                wgrad3_kernel<<<nb, W3_T, W3_SMEM, st>>>(static_cast<const float *>(hl), static_cast<const float *>(dzl),
+                                                   B, H, H, Cin, per, part);
+                const int64_t ne = (int64_t)Cin * 25 * Cout;
+                wgrad_reduce_kernel<<<wgrad_reduce_grid(ne), 32 * WR_G, 0, st>>>(part, nb, Cin, Cout,
                                                                                   s->grad.as<float>() + s->woff[l]);
             });
         } else
@@ -652,7 +948,7 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
                 else
                     s->launch_failed = true;
                 const int64_t ne = (int64_t)Cin * N;
-                wgrad_reduce_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+                wgrad_reduce_kernel<<<wgrad_reduce_grid(ne), 32 * WR_G, 0, st>>>(
                     part, (int)splits, Cin, Cout, s->grad.as<float>() + s->woff[l]);
             });
         }
@@ -662,6 +958,20 @@ int grad_pass(lic_student *s, const float *yp, const float *xp, int P, int Hy, i
             const double bytes = P_out * (double)Cout * act_bytes(s, l) + 2.0 * P_in * Cin * act_bytes(s, l - 1) +
                                  4.0 * wsize(s, l);
             const bool tc = s->bf16 && l < NL - 1;
+            if (l == NL - 1 && Cin == 64) {
+                int nb = 0, per = 0;
+                dgrad3_plan(B, H, H, &nb, &per);
+                timed(s, "student.dgrad" + std::to_string(l), flop, bytes, 1, st, [&] {
+                    if (act_bytes(s, l - 1) == 2)
+                        dgrad3_kernel<<<nb, D3_T, D3_SMEM, st>>>(static_cast<const float *>(dzl), s->wd[l].as<float>(),
+                                                                 static_cast<const float *>(hl), B, H, H, per,
+                                                                 s->dz[l - 1].as<__nv_bfloat16>());
+                    else
+                        dgrad3_kernel<<<nb, D3_T, D3_SMEM, st>>>(static_cast<const float *>(dzl), s->wd[l].as<float>(),
+                                                                 static_cast<const float *>(hl), B, H, H, per,
+                                                                 s->dz[l - 1].as<float>());
+                });
+            } else
             timed(s, "student.dgrad" + std::to_string(l) + (tc ? ":tc" : ""), flop, bytes, 1, st, [&] {
                 ConvDesc d{};
                 d.in = static_cast<const float *>(dzl);
@@ -863,6 +1173,11 @@ int lic_student_create(const lic_weights *init, int M, int C, const lic_student_
         const int64_t P_in = Bm * (side / 2) * (side / 2);
         const int64_t splits = std::min<int64_t>(std::max<int64_t>(1, (4 * 148) / tiles), (P_in + WG_BK - 1) / WG_BK);
         part_max = std::max<int64_t>(part_max, (splits + 1) * (int64_t)s->cin[l] * N);
+        if (l == NL - 1) {   // the 3-channel layer's blocks
+            int nb = 0, per = 0;
+            wgrad3_plan(Bm, (int)(side / 2), (int)(side / 2), s->cin[l], &nb, &per);
+            part_max = std::max<int64_t>(part_max, (int64_t)W3_BLOCKS * s->cin[l] * N);
+        }
         if (s->bf16 && l < NL - 1)   // the tensor-core weight gradient's slices, for any batch up to Bm
             for (int b = 1; b <= Bm; ++b)
                 part_max = std::max<int64_t>(part_max, (int64_t)tc::wgrad_bf16_slices(b, (int)(side / 2),
@@ -876,6 +1191,12 @@ int lic_student_create(const lic_weights *init, int M, int C, const lic_student_
     if (s->lpart.ensure(sizeof(double) * 148 * 16) != cudaSuccess || s->status.ensure(16) != cudaSuccess)
         return fail(LIC_E_OOM);
     cudaMemset(s->status.p, 0, 16);
+    if (cudaFuncSetAttribute(wgrad3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, W3_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(dgrad3_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, D3_SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(dgrad3_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, D3_SMEM) !=
+            cudaSuccess)
+        return fail(LIC_E_CUDA);
     if ((rc = repack(s, 0))) return fail(rc);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(LIC_E_CUDA);
     *out = s;
