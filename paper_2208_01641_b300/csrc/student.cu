@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(WG_NT) wgrad_kernel(const TX *__restrict__ x, 
 // window, so the kernel is bound by FMA issue.  A work unit is 2 input rows
 // x 128 columns x 64 input channels of one frame: the dz rows it touches go
 // to shared memory as a zero-padded strip (7 rows x 260 columns x 3), h in
-// chunks of 32 pixels; both are double-buffered and fetched with cp.async one
+// chunks of 64 pixels; both are double-buffered and fetched with cp.async one
 // chunk ahead, so the loads overlap the FMAs.  Warp u (0..4) owns the 15
 // window values of tap row u -- contiguous in the strip -- and each lane 8
 // channels (4 ig .. 4 ig + 3 and 32 + 4 ig ..: a quarter warp's 16-byte
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(WG_NT) wgrad_kernel(const TX *__restrict__ x, 
 // strip values for 120 FMAs.  The four pixel slots are added by shuffles at
 // the end, and block z's sums go to part[z][i][(5u+v)*3 + o]
 // (wgrad_reduce_kernel adds the blocks in order).
-constexpr int W3_TR = 2, W3_TC = 128, W3_PC = 32, W3_T = 160, W3_BLOCKS = 2 * 148;
+constexpr int W3_TR = 2, W3_TC = 128, W3_PC = 64, W3_T = 160, W3_BLOCKS = 2 * 148;
 constexpr int W3_SR = 2 * W3_TR + 3, W3_SP = (2 * W3_TC + 4) * 3;   // strip rows, row pitch (floats)
 constexpr int W3_CPU = W3_TR * (W3_TC / W3_PC);                      // chunks per unit
 
