@@ -430,15 +430,16 @@ __device__ __forceinline__ uint8_t fq_index(float sg, const float *tab) {
 
 // Channels c .. c+NV-1 (whole-layer numbering) of output pixel hw of frame b
 // (NHWC pixel index opix for q_hat); tab: the scales in shared memory.
-template <int NV>
-__device__ __forceinline__ void fused_quant(const Params &p, const float *v, int b, int64_t hw, int64_t HW, int c,
-                                            int64_t opix, const float *tab) {
+// QM 1: symbols (and q_hat), 2: scale indices.
+template <int QM, int NV>
+__device__ __forceinline__ void fused_quant_m(const Params &p, const float *v, int b, int64_t hw, int64_t HW, int c,
+                                              int64_t opix, const float *tab) {
     const int64_t o0 = ((int64_t)b * p.q_C + c) * HW + hw;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const int cc = c + j;
         const int64_t o = o0 + (int64_t)j * HW;
-        if (p.q_mode == 1) {
+        if constexpr (QM == 1) {
             const float mu = p.q_mu ? __ldg(p.q_mu + cc) : 0.f;
             const int32_t sy = fq_symbol(v[j], mu);
             p.q_sym[o] = sy;
@@ -447,6 +448,13 @@ __device__ __forceinline__ void fused_quant(const Params &p, const float *v, int
             p.q_idx[o] = fq_index(v[j], tab);
         }
     }
+}
+
+template <int NV>
+__device__ __forceinline__ void fused_quant(const Params &p, const float *v, int b, int64_t hw, int64_t HW, int c,
+                                            int64_t opix, const float *tab) {
+    if (p.q_mode == 1) fused_quant_m<1, NV>(p, v, b, hw, HW, c, opix, tab);
+    else fused_quant_m<2, NV>(p, v, b, hw, HW, c, opix, tab);
 }
 
 // Four consecutive per-channel parameters (16-byte aligned; the launch checks
@@ -589,7 +597,10 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 // the float32 box and the weights (48 KB), so four stages fit and buffer
 // more MMA work against the latency of TMA plus the split; TMEM holds two
 // partial sums (2 x 128 columns) and a hi / lo A slot per stage (4 x 64).
-template <int STAGES, int HALF>  // HALF: 32-column blocks per epilogue thread (Cout = 64 * HALF)
+// QM: quantisation fused into the plain (no GDN) epilogue -- 0 none, 1 symbols
+// (q_sym, q_hat), 2 scale indices (q_idx) -- with the arithmetic of the
+// separate kernels, so both decide every integer identically.
+template <int STAGES, int HALF, int QM = 0>  // HALF: 32-column blocks per epilogue thread (Cout = 64 * HALF)
 __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                       const __grid_constant__ CUtensorMap tmBh,
                                                                       const __grid_constant__ CUtensorMap tmBl,
@@ -618,6 +629,8 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int groups = (p.kchunks + FOLD - 1) / FOLD;
+    __shared__ float s_qtab[QM == 2 ? 64 : 1];   // fused scale index: the 64 scales
+    if (QM == 2 && threadIdx.x < 64) s_qtab[threadIdx.x] = p.q_tab[threadIdx.x];
 
     int b = 0, i0 = 0, j0 = 0;
     int64_t p0 = 0;
@@ -1032,7 +1045,9 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                 store_row<HALF * 32>(master, p.out, opix * p.ostride + p.ocoff + cbase, p.out_dt, p.out_inv_scale);
             } else if (valid) {
                 float *dst = p.out + opix * p.ostride + p.ocoff + cbase;
-
+                const int64_t HW = (int64_t)p.Ho * p.Wo;
+                const int fb = (int)(opix / HW);
+                const int64_t hw = opix - (int64_t)fb * HW;
 #pragma unroll
                 for (int q = 0; q < HALF * 8; ++q) {
                     float4 o;
@@ -1052,7 +1067,11 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                         op[e] = y;
                     }
                     reinterpret_cast<float4 *>(dst)[q] = o;
-
+                    if constexpr (QM == 1) {
+                        fused_quant_m<1, 4>(p, op, fb, hw, HW, p.ocoff + cbase + 4 * q, opix, s_qtab);
+                    } else if constexpr (QM == 2) {
+                        fused_quant_m<2, 4>(p, op, fb, hw, HW, p.ocoff + cbase + 4 * q, opix, s_qtab);
+                    }
                 }
             }
         }
@@ -1985,11 +2004,14 @@ int smem_bytes(int stages, int Cout) {
     return stages * (a + 2 * Cout * KCH * 4) + 256 + 1024;
 }
 
-template <int STAGES, int HALF>
+template <int STAGES, int HALF, int QM = 0>
 void launch_kernel(unsigned grid, int smem, cudaStream_t st, const CUtensorMap &a, const CUtensorMap &bh,
                    const CUtensorMap &bl, const CUtensorMap &gh, const CUtensorMap &gl, const Params &p) {
-    cudaFuncSetAttribute(conv_tc_kernel<STAGES, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    conv_tc_kernel<STAGES, HALF><<<grid, 64 + EPI_THREADS, smem, st>>>(a, bh, bl, gh, gl, p);
+    if constexpr (HALF == 3 && QM == 0) {   // Cout = 192: Q(y) fused (tc_fuses_quant)
+        if (p.q_mode == 1) return launch_kernel<STAGES, HALF, 1>(grid, smem, st, a, bh, bl, gh, gl, p);
+    }
+    cudaFuncSetAttribute(conv_tc_kernel<STAGES, HALF, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    conv_tc_kernel<STAGES, HALF, QM><<<grid, 64 + EPI_THREADS, smem, st>>>(a, bh, bl, gh, gl, p);
 }
 
 
@@ -2645,8 +2667,11 @@ bool can_run(const ConvDesc &d, const TcWeights &w) {
 }
 
 bool tc_fuses_quant(const ConvDesc &d) {
-    return d.q_mode != 0 && d.Cout == 128 && (d.epi == EPI_NONE || d.epi == EPI_RELU) && d.fuse_gdn == 0 &&
-           d.out_dt == DT_F32;
+    // Cout = 192 runs one tile per CTA, an epilogue nothing overlaps: it takes
+    // the symbols (about as fast as the separate kernel) but not the scale
+    // index (its searches there cost more than the separate integer kernel)
+    return d.q_mode != 0 && (d.Cout == 128 || (d.Cout == 192 && d.q_mode == 1)) &&
+           (d.epi == EPI_NONE || d.epi == EPI_RELU) && d.fuse_gdn == 0 && d.out_dt == DT_F32;
 }
 
 bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
@@ -2685,9 +2710,8 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
     p.ocoff = d.out_coff;
     p.out_inv_scale = d.out_scale > 0.f ? 1.f / d.out_scale : 1.f;
     p.tmem_cols = 512;  // partial sums (+ A slots when Cout = 128)
-    // fused quantisation: the persistent Cout = 128 kernel and its split-K sum
-    // (their epilogues overlap the next tile); the one-tile-per-CTA kernel
-    // leaves it to the caller (tc_fuses_quant)
+    // fused quantisation: the persistent Cout = 128 kernel and its split-K sum,
+    // and symbols in the one-tile-per-CTA Cout = 192 kernel (tc_fuses_quant)
     if (d.out_dt == DT_F32 && tc_fuses_quant(d)) {
         p.q_mode = d.q_mode;
         p.q_C = d.q_C;

@@ -40,9 +40,10 @@ bool can_run(const ConvDesc &d, const TcWeights &w);
 // encoded, in which case the caller runs the CUDA-core kernel instead.
 bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st);
 
-// Whether launch() applies d.q_mode in the epilogue (the persistent Cout = 128
-// kernel and its split-K sum do; the one-tile-per-CTA kernel, whose epilogue
-// nothing overlaps, measured slower with it than the separate kernels).
+// Whether launch() applies d.q_mode in the epilogue: the persistent Cout = 128
+// kernel and its split-K sum (symbols or scale indices), the one-tile-per-CTA
+// Cout = 192 kernel (symbols only: its epilogue, which nothing overlaps, ran
+// the scale-index searches slower than the separate integer kernel).
 bool tc_fuses_quant(const ConvDesc &d);
 
 // The K slices launch() cuts each 128-pixel tile into (1: none).  Above 1 it

@@ -221,6 +221,34 @@ __global__ void index_kernel(IndexF fn, int B) {
     tile_nhwc_to_nchw(B, fn.P, fn.C, fn);
 }
 
+// The same indices when P % 4 == 0, four pixels per thread: a block (32 x 8
+// threads) reads a 128-pixel x 32-channel tile of sigma with coalesced rows,
+// then each thread writes the indices of 4 consecutive pixels of one channel
+// as one 4-byte word (a warp: 128 contiguous bytes of a channel's plane).
+constexpr int IX_P = 128;
+__global__ void __launch_bounds__(256) index4_kernel(const float *__restrict__ sigma, int P, int C,
+                                                     uint8_t *__restrict__ idx) {
+    __shared__ float tab[64];
+    __shared__ float tile[IX_P][33];
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+    if (t < 64) tab[t] = c_scales[t];
+    const int b = blockIdx.z, p0 = blockIdx.x * IX_P, c0 = blockIdx.y * 32;
+    for (int r = ty; r < IX_P; r += 8) {
+        const int p = p0 + r, c = c0 + tx;
+        tile[r][tx] = (p < P && c < C) ? sigma[((int64_t)b * P + p) * C + c] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int c = c0 + r, p = p0 + 4 * tx;
+        if (c >= C || p >= P) continue;
+        const uint32_t w = (uint32_t)index_one(tile[4 * tx][r], tab) |
+                           ((uint32_t)index_one(tile[4 * tx + 1][r], tab) << 8) |
+                           ((uint32_t)index_one(tile[4 * tx + 2][r], tab) << 16) |
+                           ((uint32_t)index_one(tile[4 * tx + 3][r], tab) << 24);
+        *reinterpret_cast<uint32_t *>(idx + ((int64_t)b * C + c) * P + p) = w;
+    }
+}
+
 int grid_for(int64_t n) {
     int64_t g = (n + 255) / 256;
     return (int)(g < 148 * 32 ? (g < 1 ? 1 : g) : 148 * 32);
@@ -295,6 +323,10 @@ void launch_quantize(const float *y, int B, int HW, int C, const float *mu, int3
 
 void launch_scale_index(const float *sigma, int B, int HW, int C, uint8_t *idx, float *sigma_nchw,
                         cudaStream_t st) {
+    if (!sigma_nchw && HW % 4 == 0 && (reinterpret_cast<uintptr_t>(idx) & 3) == 0) {
+        index4_kernel<<<dim3((HW + IX_P - 1) / IX_P, (C + 31) / 32, B), dim3(32, 8), 0, st>>>(sigma, HW, C, idx);
+        return;
+    }
     IndexF fn{sigma, idx, sigma_nchw, HW, C, nullptr};
     index_kernel<<<tile_grid(B, HW, C), dim3(32, 8), 0, st>>>(fn, B);
 }
