@@ -19,8 +19,11 @@
  * masked by the ReLU; weight gradient = a reduction over batch x pixels;
  * bias gradient = a per-channel sum) and the Adam update -- runs in the
  * library's CUDA kernels, float32, with fixed reduction orders (results do
- * not depend on the launch).  Conventions (return codes, streams, NCHW)
- * are those of lic.h.
+ * not depend on the launch).  The LIC_BF16 form stores the 64-channel
+ * layers' activations and output gradients in bf16 and runs their forward
+ * pass, input gradients and weight gradients on tcgen05 (bf16 x bf16 ->
+ * float32 sums).  Conventions (return codes, streams, NCHW) are those of
+ * lic.h.
  */
 #ifndef LIC_STUDENT_H
 #define LIC_STUDENT_H
