@@ -253,13 +253,20 @@ int make_deconv(Layer &L, const ParamMap &pm, const std::string &name, int Cin, 
         // codec's activation buffers hold when Cin >= 128; the choice depends on
         // the model only, so every batch size decodes through the same arithmetic
         if (Cin >= 128) {
+            // GEMM column of (du, dv, py, px, o): the neighbour-class layout of
+            // launch_deconv_gather (lic_internal.h); padding columns stay zero
             std::vector<float> ws((size_t)128 * Cin, 0.f), zb(128, 0.f);
-            for (int c = 0; c < Cin; ++c)
-                for (int o = 0; o < Cout; ++o)
-                    for (int u = 0; u < k; ++u)
-                        for (int v = 0; v < k; ++v)
-                            ws[((size_t)(u * 5 + v) * Cout + o) * Cin + c] =
-                                w[(((size_t)c * Cout + o) * k + u) * k + v];
+            for (int du = -1; du <= 1; ++du)
+                for (int dv = -1; dv <= 1; ++dv)
+                    for (int py = 0; py < scatter_n(du); ++py)
+                        for (int px = 0; px < scatter_n(dv); ++px)
+                            for (int o = 0; o < Cout; ++o) {
+                                const int u = py + 2 - 2 * du, v = px + 2 - 2 * dv;
+                                const size_t col = (size_t)scatter_offset(du, dv, Cout) +
+                                                   (size_t)(py * scatter_n(dv) + px) * Cout + o;
+                                for (int c = 0; c < Cin; ++c)
+                                    ws[col * Cin + c] = w[(((size_t)c * Cout + o) * k + u) * k + v];
+                            }
             tc::build_weights(ws.data(), 128, 1, Cin, &L.w_scatter);
             if ((rc = upload(L.zero_bias, zb.data(), zb.size() * sizeof(float)))) return rc;
         }

@@ -260,50 +260,118 @@ __global__ void __launch_bounds__(DS_THREADS) deconv_small_kernel(const float *_
 }
 
 
-// Second pass of the two-pass form (see launch_deconv_gather): one thread per
-// output pixel (2m + py, 2n + px) adds, for du, dv in {-1, 0, 1} with taps
-// u = py + 2 - 2 du and v = px + 2 - 2 dv in [0, 4], the contribution of
-// input position (m + du, n + dv) through (u, v).
+// Second pass of the two-pass form (see launch_deconv_gather).  A block takes
+// one row m of output quads (2m .. 2m+1, 2n .. 2n+1) for GQ_W consecutive n.
+// Row m - 1 of C feeds the quads only through its (du = -1) blocks, row m
+// through its (du = 0) blocks and row m + 1 through its (du = 1) blocks, each a
+// contiguous run of every position's record: the block copies those three runs
+// of the GQ_W + 2 positions it touches into a shared-memory record per position
+// (coalesced 16-byte loads, zeros outside the grid; every C entry is read once),
+// then thread t adds, in (du, dv) order, position n + dv's (du, dv) block to
+// its quad's pixels (16-byte shared loads: the record pitch spreads a quarter
+// warp over all 32 banks), adds the bias and writes the quad's two rows.
+constexpr int GQ_W = 128;
+
 template <int COUT>
-__global__ void __launch_bounds__(256) deconv_gather_kernel(const float *__restrict__ C, int B, int Hi, int Wi,
-                                                            const float *__restrict__ bias, float *__restrict__ out) {
-    const int Ho = 2 * Hi, Wo = 2 * Wi;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)B * Ho * Wo) return;
-    const int X = (int)(idx % Wo), Y = (int)((idx / Wo) % Ho);
-    const int b = (int)(idx / ((int64_t)Wo * Ho));
-    const int m = Y >> 1, py = Y & 1, n = X >> 1, px = X & 1;
-    float acc[COUT];
+__global__ void __launch_bounds__(GQ_W) deconv_gather_kernel(const float *__restrict__ C, int B, int Hi, int Wi,
+                                                             const float *__restrict__ bias,
+                                                             float *__restrict__ out) {
+    constexpr int S = deconv_scatter_stride(COUT);
+    extern __shared__ __align__(16) float rec[];   // [GQ_W + 2][S]: position n0 - 1 + k at k
+    const int t = threadIdx.x, n0 = blockIdx.x * GQ_W, m = blockIdx.y, b = blockIdx.z;
+    // every load of the three runs in flight before the first shared store
+    constexpr int IT = ((GQ_W + 2) * (S / 4) + GQ_W - 1) / GQ_W;   // float4s a thread copies, at most
+    float4 v[IT];
+    int dst[IT];
 #pragma unroll
-    for (int o = 0; o < COUT; ++o) acc[o] = __ldg(bias + o);
-#pragma unroll
-    for (int du = -1; du <= 1; ++du) {
-        const int u = py + 2 - 2 * du, mi = m + du;
-        if (u < 0 || u > 4 || mi < 0 || mi >= Hi) continue;
-#pragma unroll
-        for (int dv = -1; dv <= 1; ++dv) {
-            const int v = px + 2 - 2 * dv, ni = n + dv;
-            if (v < 0 || v > 4 || ni < 0 || ni >= Wi) continue;
-            const float *c = C + (((int64_t)b * Hi + mi) * Wi + ni) * deconv_scatter_stride(COUT) + (u * 5 + v) * COUT;
-#pragma unroll
-            for (int o = 0; o < COUT; ++o) acc[o] += __ldcs(c + o);   // read once: streaming
+    for (int i = 0; i < IT; ++i) {
+        const int e = t + i * GQ_W;   // float4 e of the block's (GQ_W + 2) x S / 4, row-part by row-part
+        dst[i] = -1;
+        v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        int du = -1, base = 0;
+        for (; du < 1; ++du) {        // the row part e falls in
+            const int cnt = (GQ_W + 2) * ((scatter_offset(du + 1, -1, COUT) - scatter_offset(du, -1, COUT)) / 4);
+            if (e < base + cnt) break;
+            base += cnt;
         }
+        const int off = scatter_offset(du, -1, COUT);
+        const int nf = (scatter_offset(du + 1, -1, COUT) - off) / 4;
+        const int r = e - base;
+        if (r >= (GQ_W + 2) * nf) continue;   // past the last part
+        const int k = r / nf, j = r % nf, ni = n0 - 1 + k, mi = m + du;
+        dst[i] = k * S + off + 4 * j;
+        if (mi >= 0 && mi < Hi && ni >= 0 && ni < Wi)
+            v[i] = __ldcs(reinterpret_cast<const float4 *>(C + (((int64_t)b * Hi + mi) * Wi + ni) * S + off) + j);
     }
 #pragma unroll
-    for (int o = 0; o < COUT; ++o) out[idx * COUT + o] = acc[o];
+    for (int i = 0; i < IT; ++i)
+        if (dst[i] >= 0) *reinterpret_cast<float4 *>(rec + dst[i]) = v[i];
+    __syncthreads();
+    const int n = n0 + t;
+    if (n >= Wi) return;
+    float acc[2][2][COUT];
+#pragma unroll
+    for (int py = 0; py < 2; ++py)
+#pragma unroll
+        for (int px = 0; px < 2; ++px)
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) acc[py][px][o] = 0.f;
+#pragma unroll
+    for (int du = -1; du <= 1; ++du) {
+#pragma unroll
+        for (int dv = -1; dv <= 1; ++dv) {
+            const int nb = scatter_block(du, dv, COUT) / 4, npx = scatter_n(dv);
+            const float4 *src = reinterpret_cast<const float4 *>(rec + (t + 1 + dv) * S + scatter_offset(du, dv, COUT));
+            float blk[16];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j < nb) {
+                    const float4 v = src[j];
+                    blk[4 * j] = v.x;
+                    blk[4 * j + 1] = v.y;
+                    blk[4 * j + 2] = v.z;
+                    blk[4 * j + 3] = v.w;
+                }
+            }
+#pragma unroll
+            for (int py = 0; py < scatter_n(du); ++py)
+#pragma unroll
+                for (int px = 0; px < npx; ++px)
+#pragma unroll
+                    for (int o = 0; o < COUT; ++o) acc[py][px][o] += blk[(py * npx + px) * COUT + o];
+        }
+    }
+    const int Ho = 2 * Hi, Wo = 2 * Wi;
+#pragma unroll
+    for (int py = 0; py < 2; ++py) {
+        float *dst = out + (((int64_t)b * Ho + 2 * m + py) * Wo + 2 * n) * COUT;
+#pragma unroll
+        for (int px = 0; px < 2; ++px)
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) dst[px * COUT + o] = __ldg(bias + o) + acc[py][px][o];
+    }
+}
+
+template <int COUT>
+void gather_launch(const float *C, int B, int Hi, int Wi, const float *bias, float *out, cudaStream_t st) {
+    const int smem = (GQ_W + 2) * deconv_scatter_stride(COUT) * (int)sizeof(float);
+    static const bool attr =
+        cudaFuncSetAttribute(deconv_gather_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+        cudaSuccess;
+    (void)attr;
+    const dim3 grid((unsigned)((Wi + GQ_W - 1) / GQ_W), (unsigned)Hi, (unsigned)B);
+    deconv_gather_kernel<COUT><<<grid, GQ_W, smem, st>>>(C, B, Hi, Wi, bias, out);
 }
 }  // namespace
 
 void launch_deconv_gather(const float *C, int B, int Hi, int Wi, int Cout, const float *bias, float *out,
                           cudaStream_t st) {
-    const int64_t n = (int64_t)B * 4 * Hi * Wi;
-    const unsigned grid = (unsigned)((n + 255) / 256);
-    if (n == 0) return;
+    if ((int64_t)B * Hi * Wi == 0) return;
     switch (Cout) {
-        case 1: deconv_gather_kernel<1><<<grid, 256, 0, st>>>(C, B, Hi, Wi, bias, out); break;
-        case 2: deconv_gather_kernel<2><<<grid, 256, 0, st>>>(C, B, Hi, Wi, bias, out); break;
-        case 3: deconv_gather_kernel<3><<<grid, 256, 0, st>>>(C, B, Hi, Wi, bias, out); break;
-        default: deconv_gather_kernel<4><<<grid, 256, 0, st>>>(C, B, Hi, Wi, bias, out); break;
+        case 1: gather_launch<1>(C, B, Hi, Wi, bias, out, st); break;
+        case 2: gather_launch<2>(C, B, Hi, Wi, bias, out, st); break;
+        case 3: gather_launch<3>(C, B, Hi, Wi, bias, out, st); break;
+        default: gather_launch<4>(C, B, Hi, Wi, bias, out, st); break;
     }
 }
 

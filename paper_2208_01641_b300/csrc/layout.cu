@@ -112,10 +112,14 @@ __device__ __forceinline__ void tile_nhwc_to_nchw(int B, int P, int C, Fn fn) {
     (void)B;
     int b = blockIdx.z;
     int p0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += 8) {
-        int p = p0 + r, c = c0 + threadIdx.x;
-        fn.load(b, p, c, p < P && c < C, tile[r][threadIdx.x]);
+    float v[4];   // the four loads in flight together, then the shared stores
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int p = p0 + threadIdx.y + 8 * k, c = c0 + threadIdx.x;
+        fn.load(b, p, c, p < P && c < C, v[k]);
     }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tile[threadIdx.y + 8 * k][threadIdx.x] = v[k];
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += 8) {
         int c = c0 + r, p = p0 + threadIdx.x;
@@ -233,10 +237,15 @@ __global__ void __launch_bounds__(256) index4_kernel(const float *__restrict__ s
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
     if (t < 64) tab[t] = c_scales[t];
     const int b = blockIdx.z, p0 = blockIdx.x * IX_P, c0 = blockIdx.y * 32;
-    for (int r = ty; r < IX_P; r += 8) {
-        const int p = p0 + r, c = c0 + tx;
-        tile[r][tx] = (p < P && c < C) ? sigma[((int64_t)b * P + p) * C + c] : 0.f;
+    // all sixteen loads in flight before the first shared store
+    float v[IX_P / 8];
+#pragma unroll
+    for (int k = 0; k < IX_P / 8; ++k) {
+        const int p = p0 + ty + 8 * k, c = c0 + tx;
+        v[k] = (p < P && c < C) ? sigma[((int64_t)b * P + p) * C + c] : 0.f;
     }
+#pragma unroll
+    for (int k = 0; k < IX_P / 8; ++k) tile[ty + 8 * k][tx] = v[k];
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         const int c = c0 + r, p = p0 + 4 * tx;

@@ -316,10 +316,31 @@ void launch_deconv_small(const float *in, int B, int Hi, int Wi, int Cin, const 
 
 // The same transposed conv in two passes, the first on the tensor cores: C
 // ([B][Hi][Wi][deconv_scatter_stride(Cout)], from a 1x1 GEMM) holds every input
-// position's 25 * Cout tap contributions (column (u * 5 + v) * Cout + o); this
-// sums them into out (NHWC [B][2Hi][2Wi][Cout]) and adds the bias.  Each C
-// entry lands in exactly one output pixel; the sum order per pixel is fixed.
-constexpr int deconv_scatter_stride(int cout) { return (25 * cout + 3) / 4 * 4; }   // 16-byte rows
+// position's 25 * Cout tap contributions; this sums them into out (NHWC
+// [B][2Hi][2Wi][Cout]) and adds the bias.  Each C entry lands in exactly one
+// output pixel; the sum order per pixel is fixed.
+//
+// Column layout: input position (mi, ni) is neighbour (du, dv) in {-1, 0, 1}^2
+// of the output quad (2m .. 2m+1, 2n .. 2n+1) with m = mi - du, n = ni - dv,
+// and feeds its pixel (2m + py, 2n + px) through tap u = py + 2 - 2du, v = px
+// + 2 - 2dv (py < scatter_n(du), px < scatter_n(dv)).  The columns come as nine
+// blocks in (du, dv) order, block (du, dv) holding (py, px, o) at (py *
+// scatter_n(dv) + px) * Cout + o, each padded to a multiple of 4 floats: the
+// second pass reads a quad's contributions as whole 16-byte runs.
+__host__ __device__ constexpr int scatter_n(int d) { return d < 0 ? 1 : 2; }
+__host__ __device__ constexpr int scatter_block(int du, int dv, int cout) {
+    return (scatter_n(du) * scatter_n(dv) * cout + 3) / 4 * 4;
+}
+__host__ __device__ constexpr int scatter_offset(int du, int dv, int cout) {
+    int off = 0;
+    for (int a = -1; a <= 1; ++a)
+        for (int c = -1; c <= 1; ++c) {
+            if (a == du && c == dv) return off;
+            off += scatter_block(a, c, cout);
+        }
+    return off;
+}
+constexpr int deconv_scatter_stride(int cout) { return scatter_offset(2, 2, cout); }   // all nine blocks
 void launch_deconv_gather(const float *C, int B, int Hi, int Wi, int Cout, const float *bias, float *out,
                           cudaStream_t st);
 
