@@ -46,9 +46,20 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / student / pipelined forms")
+    ap.add_argument("--forms", default="all",
+                    help="comma-separated forms to run after the FP32 chain (all, or any of: precision (BF16, "
+                         "FP8, FP32 with 1DN), substreams, format2, wide, two_streams, student, serving)")
     ap.add_argument("--student-steps", type=int, default=20000, help="training steps of the student form (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the serving form's workload (0: skip)")
     return ap.parse_args()
+
+
+def want(args, form):
+    """Whether the run includes `form` (--no-forms: none; --forms: a comma list or all)."""
+    if args.no_forms:
+        return False
+    names = {f.strip() for f in args.forms.split(",")}
+    return "all" in names or form in names
 
 
 def dist_env():
@@ -311,7 +322,7 @@ def main():
 
     # ---- the BF16 precision form, same workload ----
     forms = {}
-    if not args.no_forms and args.conv == "auto":
+    if want(args, "precision") and args.conv == "auto":
         notes = {"bf16": "g_a/g_s convs bf16 x bf16 -> fp32; GDN norms, h_a, h_s, index fp32",
                  "fp8": "g_a/g_s convs e4m3 x e4m3 -> fp32 (per-output-channel weight scales, activations "
                         "x*16; the 192-channel g_s input bf16); GDN norms, h_a, h_s, index fp32"}
@@ -332,7 +343,7 @@ def main():
             fcodec.close()
 
     # ---- the rate cost of interleaving: y substreams of whole latent planes instead of 16-row bands ----
-    if not args.no_forms:
+    if want(args, "substreams"):
         cw = lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, conv_impl=impl, band_rows=PAD_H // 16)
         wms, wstatus = time_steps(cw, frames, out, H, W, args.steps, args.warmup, stream, flush)
         wbytes = cw.encode(frames).sizes()
@@ -345,16 +356,16 @@ def main():
         cw.close()
 
     # ---- substream format 2: escape payloads outside the rANS words (decoder-adaptive coder) ----
-    if not args.no_forms:
+    if want(args, "format2"):
         forms["fp32_format2"] = format2_form(args, lic, Wt, impl, frames, out, H, W, stream, flush, ws, B,
                                              frame_bytes, rep)
 
     # ---- the precision form's own configuration: N=192 M=320, 8 x 1920x1080 ----
-    if not args.no_forms and args.conv == "auto":
+    if want(args, "wide") and args.conv == "auto":
         forms["precision_1080p_n192_m320"] = wide_form(args, lic, synth, torch, np, stream, flush, rank)
 
     # ---- frames pipelined: two codecs on two streams, batches in flight together ----
-    if not args.no_forms:
+    if want(args, "two_streams"):
         c2 = [lic.Codec(lic.HYPERPRIOR, N_CH, M_CH, Wt, conv_impl=impl) for _ in range(2)]
         st2 = [torch.cuda.Stream() for _ in range(2)]
         outs = [torch.empty_like(frames) for _ in range(2)]
@@ -387,11 +398,11 @@ def main():
             c_.close()
 
     # ---- the learned form: distilled student g_s, trained here, decoding in place of g_s ----
-    if not args.no_forms and args.student_steps > 0:
+    if want(args, "student") and args.student_steps > 0:
         forms["student"] = student_form(args, lic, synth, torch, np, Wt, frames, out, stream, flush, ws, peaks)
 
     # ---- the serving form: 16 Poisson streams of mixed resolutions through the BF16 codec ----
-    if not args.no_forms and args.serve_seconds > 0:
+    if want(args, "serving") and args.serve_seconds > 0:
         forms["serving"] = serving_form(args, lic, synth, torch, np, Wt)
 
     # ---- end to end through the C ABI with host buffers ----
