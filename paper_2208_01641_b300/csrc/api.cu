@@ -577,7 +577,11 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
         // of Cin >= 128 channels), then their per-pixel sums
         const int cs = deconv_scatter_stride(L.Cout);
         const size_t need = (size_t)B * Hi * Wi * cs * sizeof(float);
-        if (scratch && L.w_scatter.valid && cd->opt.conv_impl != LIC_CONV_SIMT && L.in_dt == DT_F32) {
+        // the precision forms hand this layer bf16 activations: the tap GEMM then runs on the
+        // bf16 kernel (bf16 x bf16 -> float32 contributions), the gather as in FP32
+        const bool lp = L.in_dt == DT_BF16;
+        if (scratch && L.w_scatter.valid && cd->opt.conv_impl != LIC_CONV_SIMT &&
+            (L.in_dt == DT_F32 || (lp && L.w_scatter.bvalid))) {
             if (!scratch->p || scratch->bytes < need) {   // not reached: the buffers hold Cin >= 128 channels
                 atomic_status(cd, ST_TIMEOUT);
                 return;
@@ -598,22 +602,29 @@ void run_layer(const lic_codec *cd, const Layer &L, const float *in, int B, int 
             d.oym = d.oxm = 1;
             d.in_xform = IN_NONE;
             d.epi = EPI_NONE;
-            d.in_dt = d.out_dt = DT_F32;
+            d.in_dt = lp ? DT_BF16 : DT_F32;
+            d.out_dt = DT_F32;
             d.in_scale = d.out_scale = 1.f;
             d.out_stream = 1;
             d.out_stride = cs;
-            if (tc::can_run(d, L.w_scatter)) {
+            if (lp ? tc::can_run_lp(d, L.w_scatter) : tc::can_run(d, L.w_scatter)) {
                 const double rows = (double)B * Hi * Wi;
+                const double esz = lp ? 2.0 : 4.0;
                 // algorithmic bytes: the input and weights for the GEMM, the output for
                 // the gather (the tap contributions in between are this build's staging)
-                timed(const_cast<lic_codec *>(cd), L.name + ":tc", flop, 4.0 * (rows * L.Cin + 25.0 * L.Cout * L.Cin),
-                      1, st, [&] {
-                          if (!tc::launch(d, L.w_scatter, st)) atomic_status(cd, ST_TIMEOUT);
+                timed(const_cast<lic_codec *>(cd), L.name + (lp ? ":bf16" : ":tc"), flop,
+                      esz * (rows * L.Cin + 25.0 * L.Cout * L.Cin), 1, st, [&] {
+                          const bool done = lp ? tc::launch_lp(d, L.w_scatter, st) : tc::launch(d, L.w_scatter, st);
+                          if (!done) atomic_status(cd, ST_TIMEOUT);
                       });
                 timed(const_cast<lic_codec *>(cd), L.name + ".gather", 0.0, 4.0 * (double)B * Ho * Wo * L.Cout, 1, st,
                       [&] { launch_deconv_gather(cbuf, B, Hi, Wi, L.Cout, L.bias.as<float>(), out, st); });
                 return;
             }
+        }
+        if (L.in_dt != DT_F32) {   // not reached: a bf16 input is set only where the two-pass form runs
+            atomic_status(cd, ST_TIMEOUT);
+            return;
         }
         timed(const_cast<lic_codec *>(cd), L.name + ":small", flop, bytes, 1, st, [&] {
             launch_deconv_small(in, B, Hi, Wi, L.Cin, L.w_small.as<float>(), L.bias.as<float>(), L.Cout, out, st);
@@ -1270,8 +1281,11 @@ int lic_codec_create(int kind, int N, int M, const lic_weights *weights, const l
         for (int i = 0; i < 3; ++i) lp_in(cd->gs[i]);
         cd->gs[0].in_dt = DT_BF16;   // y_hat is converted to bf16 once
         cd->gs[0].in_scale = 1.f;
+        // the last layer of g_s: bf16 input where its two-pass form runs on the tensor cores
+        // (N >= 128; the bf16 tap GEMM), float32 for the CUDA-core form
+        if (cd->gs[3].w_scatter.bvalid) cd->gs[3].in_dt = DT_BF16;
         for (int i = 0; i < 3; ++i) lp_out_for(cd->ga[i], cd->ga[i + 1]);
-        for (int i = 0; i < 2; ++i) lp_out_for(cd->gs[i], cd->gs[i + 1]);
+        for (int i = 0; i < 3; ++i) lp_out_for(cd->gs[i], cd->gs[i + 1]);
         auto check = [&](const Layer &L) {
             for (auto &op : L.ops) {
                 bool ok = L.in_dt == DT_E4M3 ? op->tcw.f8valid : op->tcw.bvalid;

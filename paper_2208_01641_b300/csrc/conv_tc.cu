@@ -2933,13 +2933,19 @@ bool launch_lp_impl(const ConvDesc &d, const CUtensorMap &bm, const float *w_sca
                                       : &bm;
     const CUtensorMap &gh = g[0];
     const CUtensorMap &gl = gemm_norm ? g[1] : g[0];
+    // a narrow output (the leading ostride - ocoff channels of each pixel stored) needs the
+    // persistent kernel's clipped TMA stores
+    const bool narrow = p.ostride - p.ocoff < d.Cout;
+    if (narrow && (d.Cout != 128 || (d.epi != EPI_NONE && d.epi != EPI_RELU))) return false;
     if (d.Cout == 64) {
         // 4 stages (99.6 KB of shared memory, 128 TMEM columns): two CTAs share an SM, so one
         // CTA's epilogue overlaps the other's main loop on these short-K launches
         launch_lp_kernel<4, 1, 2>(grid, st, tmA, bm, gh, gl, p);
     } else if (d.Cout == 128) {
         CUtensorMap tmO;
-        if ((d.epi == EPI_NONE || d.epi == EPI_RELU) && make_out_map(&tmO, d, p)) {
+        const bool omap = (d.epi == EPI_NONE || d.epi == EPI_RELU) && make_out_map(&tmO, d, p);
+        if (narrow && !omap) return false;
+        if (omap) {
             // persistent, one CTA per SM: six stages of 32 KB + half the output tile
             constexpr int ST = 6;
             const int smem = ST * 2 * AB_BYTES + 2 * AB_BYTES + 256 + 1024;
