@@ -1158,7 +1158,12 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
     uint64_t *full = bars, *conv = bars + STAGES, *empty = bars + 2 * STAGES;
     uint64_t *pfull = bars + 3 * STAGES, *pempty = pfull + 2, *ebar = pempty + 2, *ready = ebar + 1;
     uint64_t *done = ready + 1;   // the epilogue warps' last TMEM access is behind them
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    // gamma entry ge's loads, one phase per tile: full[s] then counts stage s's K chunks alone,
+    // every one of which the split warps wait for, so none of their waits runs ahead of a phase
+    // (a gamma load on full[s], which only the MMA waits for, could let a split warp's parity wait
+    // on that stage pass before it)
+    uint64_t *gfull = done + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gfull + NGE);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -1180,6 +1185,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
         mbar_init(ebar, TCX_EPI);
         mbar_init(ready, TCX_EPI);
         mbar_init(done, TCX_EPI);
+        for (int ge = 0; ge < NGE; ++ge) mbar_init(&gfull[ge], 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -1213,8 +1219,11 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
         if (lane == 0) {
             const uint32_t tx_bytes = (p.mode == MODE_IM2COL ? 0 : AREA) + 2 * AREA;
             uint32_t v = 0;
+            // bit s / ge: parity of the last phase issued on full[s] / gfull[ge]; whether one was
+            uint32_t fph = 0, fis = 0, gph = 0, gis = 0;
+            int tk = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++tk) {
                 const int tile = u / p.ksplit, kc0 = kbegin(u % p.ksplit), nk = kbegin(u % p.ksplit + 1) - kc0;
                 int b, i0, j0;
                 int64_t p0;
@@ -1242,18 +1251,25 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                         }
                         tma_load_2d(area(s, 2), &tmBh, &full[s], kc * KCH, 0);
                         tma_load_2d(area(s, 3), &tmBl, &full[s], kc * KCH, 0);
+                        if (fis >> s & 1) fph ^= 1u << s;
+                        fis |= 1u << s;
                     } else {   // gamma entry ge: chunks 2 ge, 2 ge + 1 as [hi | lo] pairs
                         const int ge = e - nk;
-                        mbar_expect_tx(&full[s], 4 * AREA);
+                        mbar_expect_tx(&gfull[ge], 4 * AREA);
                         for (int j = 0; j < 2; ++j) {
-                            tma_load_2d(area(s, 2 * j), &tmGh, &full[s], (2 * ge + j) * KCH, 0);
-                            tma_load_2d(area(s, 2 * j + 1), &tmGl, &full[s], (2 * ge + j) * KCH, 0);
+                            tma_load_2d(area(s, 2 * j), &tmGh, &gfull[ge], (2 * ge + j) * KCH, 0);
+                            tma_load_2d(area(s, 2 * j + 1), &tmGl, &gfull[ge], (2 * ge + j) * KCH, 0);
                         }
+                        gph = (gph & ~(1u << ge)) | (uint32_t)(tk & 1) << ge;
+                        gis |= 1u << ge;
                     }
                 }
             }
-            if (!ok) {   // wait (bounded) for loads still in flight
-                for (uint32_t u = v > STAGES ? v - STAGES : 0; u < v; ++u) mbar_wait(&full[u % STAGES], (u / STAGES) & 1);
+            if (!ok) {   // wait (bounded) for the last phase issued on every load barrier
+                for (int s = 0; s < STAGES; ++s)
+                    if (fis >> s & 1) mbar_wait(&full[s], fph >> s & 1);
+                for (int ge = 0; ge < NGE; ++ge)
+                    if (gis >> ge & 1) mbar_wait(&gfull[ge], gph >> ge & 1);
             }
         }
     } else if (warp == 1) {
@@ -1317,7 +1333,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                     const uint32_t ve = v + c / 2;
                     const int s = ve % STAGES;
                     if (c % 2 == 0) {
-                        if (*abort_flag || !mbar_wait(&full[s], (ve / STAGES) & 1)) {
+                        if (*abort_flag || !mbar_wait(&gfull[c / 2], tk & 1)) {
                             fail();
                             ok = false;
                             break;
@@ -1345,17 +1361,18 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
     } else if (warp < 8) {
         // ---------------- split (warps 2..7) ----------------
         const int st = threadIdx.x - 64;   // 0 .. TCX_SPLIT - 1
-        uint32_t v = 0;
+        uint32_t v = 0, fph = 0;   // bit s: parity of stage s's next K-chunk phase on full[s]
         bool ok = true;
         for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
             const int nk = kbegin(u % p.ksplit + 1) - kbegin(u % p.ksplit);
             for (int kc = 0; kc < nk; ++kc, ++v) {
                 const int s = v % STAGES;
-                if (*abort_flag || !mbar_wait(&full[s], (v / STAGES) & 1)) {
+                if (*abort_flag || !mbar_wait(&full[s], fph >> s & 1)) {
                     fail();
                     ok = false;
                     break;
                 }
+                fph ^= 1u << s;
                 // The MMA reads an FP32 operand as TF32 by dropping its low 13 mantissa
                 // bits (checked on this part), so the raw activation serves as A_hi and
                 // only A_lo = x - trunc(x), exact in FP32, is written (elementwise, the
