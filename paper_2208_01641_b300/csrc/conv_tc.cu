@@ -778,24 +778,35 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
                     break;
                 }
                 tc_fence_after();
+                // All terms are positive and the accumulator truncates each addition by up to a
+                // unit in its last place: a pass's small products (hi x lo, lo x hi, ~2^-11 of the
+                // sum) go in before its large ones (hi x hi), while the accumulator is smaller
 #pragma unroll
-                for (int c = 0; c < GCH; ++c) {
-                    const uint32_t bh = smem_u32(stage_bh(c)), bl = smem_u32(stage_bl(c));
+                for (int part = 0; part < 2; ++part) {
 #pragma unroll
-                    for (int kk = 0; kk < KCH / 8; ++kk) {
-                        const uint32_t off = kk * 32;
-                        const uint64_t dbh = sdesc(bh + off), dbl = sdesc(bl + off);
-                        const uint32_t acc = (h > 0 || c > 0 || kk > 0) ? 1u : 0u;
-                        if constexpr (ATM) {
-                            mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dbh, idesc, acc);
-                            mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dbl, idesc, 1u);
-                            mma_tf32_ts(tmem, slot_lo(c) + 8 * kk, dbh, idesc, 1u);
-                        } else {
-                            const uint64_t dah = sdesc(smem_u32(stage_a(c)) + off);
-                            const uint64_t dal = sdesc(smem_u32(stage_alo(c)) + off);
-                            mma_tf32(tmem, dah, dbh, idesc, acc);
-                            mma_tf32(tmem, dah, dbl, idesc, 1u);
-                            mma_tf32(tmem, dal, dbh, idesc, 1u);
+                    for (int c = 0; c < GCH; ++c) {
+                        const uint32_t bh = smem_u32(stage_bh(c)), bl = smem_u32(stage_bl(c));
+#pragma unroll
+                        for (int kk = 0; kk < KCH / 8; ++kk) {
+                            const uint32_t off = kk * 32;
+                            const uint64_t dbh = sdesc(bh + off), dbl = sdesc(bl + off);
+                            const uint32_t acc = (h > 0 || part > 0 || c > 0 || kk > 0) ? 1u : 0u;
+                            if constexpr (ATM) {
+                                if (part == 0) {
+                                    mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dbl, idesc, acc);
+                                    mma_tf32_ts(tmem, slot_lo(c) + 8 * kk, dbh, idesc, 1u);
+                                } else {
+                                    mma_tf32_ts(tmem, slot_hi(c) + 8 * kk, dbh, idesc, 1u);
+                                }
+                            } else {
+                                const uint64_t dah = sdesc(smem_u32(stage_a(c)) + off);
+                                if (part == 0) {
+                                    mma_tf32(tmem, dah, dbl, idesc, acc);
+                                    mma_tf32(tmem, sdesc(smem_u32(stage_alo(c)) + off), dbh, idesc, 1u);
+                                } else {
+                                    mma_tf32(tmem, dah, dbh, idesc, 1u);
+                                }
+                            }
                         }
                     }
                 }
@@ -1110,8 +1121,12 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
 //   * per 8-wide K step two MMAs: A_hi x [B_hi | B_lo] (N = 256: one
 //     descriptor spans the adjacent B areas; the two halves of the partial
 //     sum accumulate apart and the fold adds them) and A_lo x B_hi (N = 128,
-//     into the first half); with 256-column partials the two ping-pong
-//     buffers fill TMEM, so A is read from shared memory;
+//     into the second half, with the other small product: the accumulator
+//     truncates each addition by up to a unit in its last place, so the half
+//     that holds the large products drifts half as far when it takes one
+//     addition per K step instead of two; the norm GEMM likewise); with
+//     256-column partials the two ping-pong buffers fill TMEM, so A is read
+//     from shared memory;
 //   * the split only writes A_lo = x - trunc(x), exact in FP32 (the MMA's
 //     own truncation of it costs at most 2^-20 of a product);
 //   * the fused norm's gamma rides the ring as two entries of two
@@ -1310,7 +1325,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                     for (int kk = 0; kk < KCH / 8; ++kk) {
                         const uint64_t db = sdesc(bh + kk * 32);
                         mma_tf32(dt, sdesc(ah + kk * 32), db, idw, (!first || kk > 0) ? 1u : 0u);   // [hi | lo]
-                        mma_tf32(dt, sdesc(al + kk * 32), db, idn, 1u);                             // A lo x B hi
+                        mma_tf32(dt + COUT, sdesc(al + kk * 32), db, idn, 1u);   // A lo x B hi: small, second half
                     }
                     mma_commit(&empty[s]);
                     if (last) {
@@ -1345,7 +1360,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                     for (int kk = 0; kk < KCH / 8; ++kk) {
                         const uint64_t db = sdesc(bh + kk * 32);
                         mma_tf32_ts(dt, ysl + KCH * c + 8 * kk, db, idw, (c > 0 || kk > 0) ? 1u : 0u);
-                        mma_tf32_ts(dt, ysl + COUT + KCH * c + 8 * kk, db, idn, 1u);
+                        mma_tf32_ts(dt + COUT, ysl + COUT + KCH * c + 8 * kk, db, idn, 1u);   // small: second half
                     }
                     if (c % 2 == 1) {   // the entry's two chunks are issued: back to the producer
                         mbar_arrive_n(&conv[s], TCX_SPLIT);   // one conv phase per ring entry

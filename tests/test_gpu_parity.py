@@ -70,12 +70,16 @@ def test_analysis_matches_oracle(codecs, weights, impl):
     assert err <= TOL, err
 
 
+# 24 x 40 latents: 384 x 640 outputs, many tiles a CTA and long K walks (the
+# tensor-core accumulator's truncation drift shows there first)
 @pytest.mark.parametrize("impl", IMPLS)
-def test_synthesis_matches_oracle(codecs, weights, impl):
+@pytest.mark.parametrize("hw", [(6, 9), (24, 40)])
+def test_synthesis_matches_oracle(codecs, weights, impl, hw):
     rng = np.random.default_rng(3)
-    yhat = np.rint(rng.standard_normal((2, M, 6, 9)) * 2).astype(np.float32)
+    h, w = hw
+    yhat = np.rint(rng.standard_normal((2, M, h, w)) * 2).astype(np.float32)
     c = codecs[(0, impl)]
-    x = torch.empty(2, 3, 96, 144, device="cuda")
+    x = torch.empty(2, 3, 16 * h, 16 * w, device="cuda")
     c.synthesis(dev(yhat), x)
     torch.cuda.synchronize()
     ref = O.g_s(weights[0], yhat)
