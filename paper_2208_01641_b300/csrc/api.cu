@@ -31,6 +31,9 @@ namespace {
 struct ConvOp {
     DevBuf w;     // [Cout][T][Cin] float32
     tc::TcWeights tcw;  // tensor-core operand copy (built when the op qualifies)
+    // g_a conv0's patch GEMM over the padded 4-channel frame (ConvDesc::frame):
+    // [Cout][FRAME_K], K index 4 (5u + v) + c (built for Cin = 3, Cout = 128)
+    tc::TcWeights tcw4;
     // Cout the tensor-core kernels take only in slices (Cout not 128 or 192,
     // e.g. M = 320): one operand copy per column slice of 192 or 128 channels
     std::vector<std::unique_ptr<tc::TcWeights>> parts;
@@ -84,6 +87,9 @@ struct lic_codec {
     // kernel then loads its A operand with TMA instead of gathering it
     lic::Layer ga0p;
     bool use_patch = false;
+    // while analysis runs ga0p on the persistent FP32 kernel: the padded 4-channel
+    // frame it builds its A rows from (no patch rows in HBM)
+    const float *frame_src = nullptr;
     lic::Gdn gdn[3], igdn[3];
     // entropy models
     lic::HostTables ht;
@@ -335,6 +341,15 @@ int make_patch_layer(Layer &P, const Layer &L, const ParamMap &pm) {
     if ((rc = upload(op->w, r.data(), r.size() * sizeof(float)))) return rc;
     tc::build_weights(r.data(), Cout, 1, PATCH_K, &op->tcw);
     if (!op->tcw.valid) return LIC_E_UNSUPPORTED;
+    if (Cin == 3 && Cout == 128) {   // the same weights for the padded 4-channel frame (K = 4 t + c)
+        std::vector<float> r4((size_t)Cout * FRAME_K, 0.f);
+        for (int o = 0; o < Cout; ++o)
+            for (int u = 0; u < k; ++u)
+                for (int v = 0; v < k; ++v)
+                    for (int c = 0; c < Cin; ++c)
+                        r4[(size_t)o * FRAME_K + 4 * (u * k + v) + c] = w[(((size_t)o * Cin + c) * k + u) * k + v];
+        tc::build_weights(r4.data(), Cout, 1, FRAME_K, &op->tcw4);
+    }
     P.ops.clear();
     P.ops.push_back(std::move(op));
     return upload(P.bias, b, Cout * sizeof(float));
@@ -403,6 +418,10 @@ ConvDesc op_desc(const lic_codec *cd, const Layer &L, const ConvOp &op, const fl
         d.oyo = 0;
         d.oxm = 1;
         d.oxo = 0;
+    }
+    if (L.def_cin > 0 && cd->frame_src) {
+        d.frame = cd->frame_src;
+        d.Cin = FRAME_K;
     }
     return d;
 }
@@ -513,14 +532,16 @@ void run_op(const lic_codec *cd, const Layer &L, const ConvOp &op, const float *
         if (qf) qf->done = false;   // the low-precision kernels leave quantisation to the caller
         return;
     }
-    const bool use_tc = cd->opt.conv_impl != LIC_CONV_SIMT && tc::can_run(d, op.tcw);
+    const tc::TcWeights &tw = d.frame ? op.tcw4 : op.tcw;
+    const bool use_tc = cd->opt.conv_impl != LIC_CONV_SIMT && tc::can_run(d, tw);
     if (use_tc && !tc::tc_fuses_quant(d)) d.q_mode = 0;
     if (use_tc && d.q_mode) nm += d.q_mode == 1 ? "+q" : "+index";
     nm += use_tc ? ":tc" : ":simt";
-    const int nl = use_tc && tc::split_k(d, op.tcw) > 1 ? 2 : 1;   // split K: + the sum of the slices
+    const int nl = use_tc && tc::split_k(d, tw) > 1 ? 2 : 1;   // split K: + the sum of the slices
     timed(const_cast<lic_codec *>(cd), nm, flop, bytes, nl, st, [&] {
-        q_ok = use_tc && tc::launch(d, op.tcw, st);
-        if (!q_ok) launch_conv_simt(d, st);
+        q_ok = use_tc && tc::launch(d, tw, st);
+        if (!q_ok && d.frame) atomic_status(cd, ST_TIMEOUT);   // not reached: analysis checked the form
+        else if (!q_ok) launch_conv_simt(d, st);
     });
     if (qf) qf->done = qf->mode && d.q_mode && q_ok && d.out_dt == DT_F32;
 }
@@ -703,7 +724,7 @@ float *run_layer_gdn(const lic_codec *cd, const Layer &L, const Gdn &G, const fl
         d.gdn_beta = G.beta.as<float>();
         d.gdn_w = &G.tcw;
         d.gdn_gamma = G.gamma.as<float>();
-        fuse = d.in_dt != DT_F32 ? tc::can_run_lp(d, op->tcw) : tc::can_run(d, op->tcw);
+        fuse = d.in_dt != DT_F32 ? tc::can_run_lp(d, op->tcw) : tc::can_run(d, d.frame ? op->tcw4 : op->tcw);
     }
     if (fuse) {
         run_ops(cd, L, in, B, Hi, Wi, out, Ho, Wo, st, &G);
@@ -827,7 +848,20 @@ void analysis(lic_codec *cd, const float *frames, int B, int Hf, int Wf, int Hp,
     int H = Hp, W = Wp;
     const float *in = cd->xin.as<float>();
     int first = 0;
-    if (cd->use_patch) {
+    if (cd->use_patch && cd->ga0p.ops[0]->tcw4.valid) {
+        // the frame padded once with 4 channels (into the patch buffer, a sixth of whose
+        // size it takes); the persistent FP32 kernel loads each tap of the patch rows by TMA
+        // algorithmic bytes: the frame read once
+        float *f4 = cd->patches.as<float>();
+        timed(cd, "frame_pad4", 0, 12.0 * B * Hf * Wf, 1, st,
+              [&] { launch_frame_pad4(frames, B, Hf, Wf, Hp, Wp, f4, st); });
+        cd->frame_src = f4;
+        in = run_layer_gdn(cd, cd->ga0p, cd->gdn[0], f4, B, Hp / 2, Wp / 2, a, b, st);
+        cd->frame_src = nullptr;
+        H /= 2;
+        W /= 2;
+        first = 1;
+    } else if (cd->use_patch) {
         // the first layer's patches straight from the frames (no padded copy)
         // algorithmic bytes: the frame read once (the patch rows are this build's staging)
         timed(cd, "patch_pack", 0, 12.0 * B * Hf * Wf, 1, st,

@@ -63,7 +63,13 @@ constexpr int EPI_THREADS = EPI_WARPS * 32;
 // epilogue warps gather each 128 x 32 slice of the im2col matrix (K index
 // t * Cin + c, zero past T * Cin) straight from global memory, split it and
 // write it swizzled into the stage; TMA brings only the weights.
-enum Mode : int { MODE_S2 = 0, MODE_S1 = 1, MODE_FLAT = 2, MODE_IM2COL = 3 };
+// MODE_TAPS (persistent kernel, g_a conv0 over the padded 4-channel frame):
+// K index 4 t + c, tap t = 5u + v; a K chunk is eight taps, each one TMA box
+// of the 128 pixels' 4 channels (2 KB) through the stride-2 view, stacked in
+// the no-swizzle K-major layout (8-row core matrices 128 bytes apart, taps
+// 2 KB apart), so no patch rows exist in HBM.
+enum Mode : int { MODE_S2 = 0, MODE_S1 = 1, MODE_FLAT = 2, MODE_IM2COL = 3, MODE_TAPS = 4 };
+constexpr int TAP_BYTES = BLOCK_M * 16;   // one tap's box: 128 pixels x 4 float32
 
 struct Params {
     float *out;
@@ -560,6 +566,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset
     d |= (uint64_t)1u << 46;            // descriptor version
     d |= (uint64_t)2u << 61;            // SWIZZLE_128B
+    return d;
+}
+
+// The same for the no-swizzle K-major layout of MODE_TAPS: 8-row core
+// matrices (8 x 16 bytes, contiguous) 128 bytes apart along M (stride byte
+// offset), taps TAP_BYTES apart along K (leading byte offset).
+__device__ __forceinline__ uint64_t sdesc_taps(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((TAP_BYTES >> 4) & 0x3FFFu) << 16;   // leading byte offset: the next tap
+    d |= (uint64_t)(128u >> 4) << 32;                    // stride byte offset: the next 8 pixels
+    d |= (uint64_t)1u << 46;                             // descriptor version; layout type 0: no swizzle
     return d;
 }
 
@@ -1151,7 +1169,7 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
 //                                                    (TMEM lanes 32 (warp % 4) ..)
 constexpr int TCX_THREADS = 512, TCX_SPLIT = 192, TCX_EPI = 256;
 
-template <int STAGES>
+template <int STAGES, bool TAPS>   // TAPS: MODE_TAPS only (g_a conv0 over the padded 4-channel frame)
 __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                        const __grid_constant__ CUtensorMap tmBh,
                                                                        const __grid_constant__ CUtensorMap tmBl,
@@ -1263,6 +1281,15 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                             tma_load_4d(area(s, 0), &tmA, &full[s], c0, j0 + p.dv[t], i0 + p.du[t], b);
                         } else if (p.mode == MODE_FLAT) {
                             tma_load_2d(area(s, 0), &tmA, &full[s], c0, (int)p0);
+                        } else if (TAPS) {
+                            // taps 8 kc .. 8 kc + 7 (past tap 24 its box again: finite values
+                            // against zero weights) at pixel (2i + u - 2, 2j + v - 2)
+#pragma unroll 1
+                            for (int j = 0; j < KCH / 4; ++j) {
+                                const int tt = min(kc * (KCH / 4) + j, 24), du = tt / 5 - 2, dv = tt % 5 - 2;
+                                tma_load_5d(area(s, 0) + j * TAP_BYTES, &tmA, &full[s], (dv & 1) * 4, j0 + (dv >> 1),
+                                            du & 1, i0 + (du >> 1), b);
+                            }
                         }
                         tma_load_2d(area(s, 2), &tmBh, &full[s], kc * KCH, 0);
                         tma_load_2d(area(s, 3), &tmBl, &full[s], kc * KCH, 0);
@@ -1321,11 +1348,21 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                     tc_fence_after();
                     const uint32_t dt = tmem + q * 2 * COUT;
                     const uint32_t ah = smem_u32(area(s, 0)), al = smem_u32(area(s, 1)), bh = smem_u32(area(s, 2));
+                    if constexpr (!TAPS) {
 #pragma unroll
-                    for (int kk = 0; kk < KCH / 8; ++kk) {
-                        const uint64_t db = sdesc(bh + kk * 32);
-                        mma_tf32(dt, sdesc(ah + kk * 32), db, idw, (!first || kk > 0) ? 1u : 0u);   // [hi | lo]
-                        mma_tf32(dt + COUT, sdesc(al + kk * 32), db, idn, 1u);   // A lo x B hi: small, second half
+                        for (int kk = 0; kk < KCH / 8; ++kk) {
+                            const uint64_t db = sdesc(bh + kk * 32);
+                            mma_tf32(dt, sdesc(ah + kk * 32), db, idw, (!first || kk > 0) ? 1u : 0u);   // [hi | lo]
+                            mma_tf32(dt + COUT, sdesc(al + kk * 32), db, idn, 1u);   // A lo x B hi: small, second half
+                        }
+                    } else {
+                        // the last chunk's data is its first K step (tap 24 and a zero one)
+                        const int ksteps = kc == kc1 - 1 ? 1 : KCH / 8;
+                        for (int kk = 0; kk < ksteps; ++kk) {
+                            const uint64_t db = sdesc(bh + kk * 32);
+                            mma_tf32(dt, sdesc_taps(ah + kk * 2 * TAP_BYTES), db, idw, (!first || kk > 0) ? 1u : 0u);
+                            mma_tf32(dt + COUT, sdesc_taps(al + kk * 2 * TAP_BYTES), db, idn, 1u);
+                        }
                     }
                     mma_commit(&empty[s]);
                     if (last) {
@@ -2001,7 +2038,8 @@ EncodeFn encode_fn() {
 }
 
 bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
-              const uint32_t *box, CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32) {
+              const uint32_t *box, CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+              CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
     EncodeFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t gd[5], gs[4];
@@ -2013,7 +2051,7 @@ bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, 
         if (i > 0) gs[i - 1] = strides_bytes[i - 1];
     }
     CUresult r = fn(m, dt, rank, const_cast<void *>(base), gd, gs, bx, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -2769,6 +2807,22 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
         p.tiles_y = (d.Gh + p.R - 1) / p.R;
         grid = (unsigned)(p.tiles_x * p.tiles_y * d.B);
         tmA = reinterpret_cast<const CUtensorMap *>(w.maps)[0];   // unused in this mode
+    } else if (d.frame) {
+        // g_a conv0 over the padded 4-channel frame [B][2 Hi][2 Wi][4], viewed as pixel pairs
+        // (8, Wp / 2, 2, Hp / 2, B); one tap's box: 4 channels of an R x Wt block
+        if (d.Cout != 128 || d.Cin != FRAME_K || d.T != 1 || !is_flat(d) || (reinterpret_cast<uintptr_t>(d.frame) & 15))
+            return false;
+        p.mode = MODE_TAPS;
+        pick_tile(d.Gh, d.Gw, &p.R, &p.Wt);
+        p.tiles_x = (d.Gw + p.Wt - 1) / p.Wt;
+        p.tiles_y = (d.Gh + p.R - 1) / p.R;
+        grid = (unsigned)(p.tiles_x * p.tiles_y * d.B);
+        const uint64_t Wp = 2ull * d.Wi, Hp = 2ull * d.Hi;
+        const uint64_t dims[5] = {8, Wp / 2, 2, Hp / 2, (uint64_t)d.B};
+        const uint64_t strides[4] = {32, Wp * 16, 2 * Wp * 16, Hp * Wp * 16};
+        const uint32_t box[5] = {4, (uint32_t)p.Wt, 1, (uint32_t)p.R, 1};
+        if (!make_map(&tmA, d.frame, 5, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, CU_TENSOR_MAP_SWIZZLE_NONE))
+            return false;
     } else if (is_flat(d)) {
         p.mode = MODE_FLAT;
         p.rows = (int64_t)d.B * d.Hi * d.Wi;
@@ -2822,8 +2876,15 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
         p.ksplit = ks;
         const unsigned pgrid = std::min<unsigned>(grid * ks, (unsigned)sm_count());
         const int smem = STAGES * 4 * A_BYTES + 2 * A_BYTES + 256 + 1024;
-        cudaFuncSetAttribute(conv_tcx_kernel<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        conv_tcx_kernel<STAGES><<<pgrid, TCX_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1], tmO, p);
+        if (p.mode == MODE_TAPS) {
+            cudaFuncSetAttribute(conv_tcx_kernel<STAGES, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            conv_tcx_kernel<STAGES, true>
+                <<<pgrid, TCX_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1], tmO, p);
+        } else {
+            cudaFuncSetAttribute(conv_tcx_kernel<STAGES, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            conv_tcx_kernel<STAGES, false>
+                <<<pgrid, TCX_THREADS, smem, st>>>(tmA, maps[0], maps[1], gmaps[0], gmaps[1], tmO, p);
+        }
         if (ks > 1) {
             const int64_t n = (int64_t)grid * BLOCK_M * 32;
             tcx_splitk_sum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const float4 *>(d.part),
@@ -2832,6 +2893,7 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
         return true;
     }
     if (ks > 1) return false;   // not reached: split_k admits only launches of the persistent kernel
+    if (p.mode == MODE_TAPS) return false;   // not reached: the caller builds this form for the persistent kernel
     if (p.ostride - p.ocoff < d.Cout) return false;   // a narrow output needs the clipped TMA store
     const int smem = smem_bytes(stages_for(d.Cout), d.Cout);
     if (d.Cout == 128)

@@ -33,6 +33,21 @@ __global__ void pad_pack_kernel(const float *__restrict__ f, int B, int H, int W
     }
 }
 
+// frames [B][3][H][W] -> [B][Hp][Wp][4] (channel 3 zero), replicate-padded:
+// one thread per pixel, three plane reads and one 16-byte store, both
+// coalesced across the warp
+__global__ void frame_pad4_kernel(const float *__restrict__ f, int B, int H, int W, int Hp, int Wp,
+                                  float4 *__restrict__ out) {
+    const int64_t n = (int64_t)B * Hp * Wp, HW = (int64_t)H * W;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(p % Wp);
+        const int y = (int)((p / Wp) % Hp);
+        const int64_t b = p / ((int64_t)Wp * Hp);
+        const float *src = f + b * 3 * HW + (int64_t)min(y, H - 1) * W + min(x, W - 1);
+        out[p] = make_float4(__ldg(src), __ldg(src + HW), __ldg(src + 2 * HW), 0.f);
+    }
+}
+
 // Patches of a 5x5 / stride-2 convolution of a 3-channel Hp x Wp image:
 // row (b, i, j) of the output holds, at K index k = (5u + v) * 3 + c, the
 // input value x[b][2i + u - 2][2j + v - 2][c] (0 outside the image), and 0
@@ -299,6 +314,11 @@ void launch_to_bf16(const float *in, int64_t n, void *out, cudaStream_t st) {
 
 void launch_pad_pack(const float *frames, int B, int H, int W, int Hp, int Wp, float *out, cudaStream_t st) {
     pad_pack_kernel<<<grid_for((int64_t)B * Hp * Wp), 256, 0, st>>>(frames, B, H, W, Hp, Wp, out);
+}
+
+void launch_frame_pad4(const float *frames, int B, int H, int W, int Hp, int Wp, float *out, cudaStream_t st) {
+    frame_pad4_kernel<<<grid_for((int64_t)B * Hp * Wp), 256, 0, st>>>(frames, B, H, W, Hp, Wp,
+                                                                      reinterpret_cast<float4 *>(out));
 }
 
 void launch_patch_pack(const float *x, int B, int Hp, int Wp, float *out, cudaStream_t st) {

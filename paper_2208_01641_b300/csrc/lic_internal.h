@@ -284,6 +284,12 @@ struct ConvDesc {
     // holds B * part_frame_floats floats; null: no split
     float *part;
     int64_t part_frame_floats;
+    // g_a conv0 as a 1x1 GEMM of K = FRAME_K over its (Hp/2) x (Wp/2) output
+    // pixels: non-null, the kernel builds each A row from this padded frame
+    // [B][Hp][Wp][4] (device, 16-byte aligned, channel 3 zero; see
+    // launch_frame_pad4), K index 4 (5u + v) + c, and `in` is not read (the
+    // persistent FP32 kernel, Cout = 128, only)
+    const float *frame;
     int T;
     int8_t du[MAX_TAPS], dv[MAX_TAPS];
     int in_xform, epi;
@@ -376,6 +382,12 @@ void launch_to_bf16(const float *in, int64_t n, void *out, cudaStream_t st);
 // the rows of its 5x5 / stride-2 patches [B][Hp/2][Wp/2][PATCH_K], K index
 // (5u + v) * 3 + c, zero-padded from 75 to PATCH_K.
 constexpr int PATCH_K = 96;
+// The same layer over the padded frame with 4 channels (ConvDesc::frame): K
+// index 4 (5u + v) + c, zero-padded from 100 to FRAME_K.
+constexpr int FRAME_K = 128;
+// frames [B][3][H][W] (device) -> [B][Hp][Wp][4], replicate-padded as
+// launch_pad_pack pads, channel 3 zero.
+void launch_frame_pad4(const float *frames, int B, int H, int W, int Hp, int Wp, float *out, cudaStream_t st);
 void launch_patch_pack(const float *x, int B, int Hp, int Wp, float *out, cudaStream_t st);
 // The same patches straight from the caller's frames [B][3][H][W] (device),
 // replicate-padded to Hp x Wp on the fly (as launch_pad_pack pads).
