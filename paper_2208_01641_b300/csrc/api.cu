@@ -748,6 +748,12 @@ float *run_layer_gdn(const lic_codec *cd, const Layer &L, const Gdn &G, const fl
 
 int pad64(int v) { return (v + 63) / 64 * 64; }
 
+// g_a conv0 runs in the tap form (the padded 4-channel frame, each tap TMA-loaded)
+// when its weights were built for it (Cin = 3, Cout = 128, tensor-core path)
+bool frame_form(const lic_codec *cd) {
+    return cd->use_patch && !cd->ga0p.ops.empty() && cd->ga0p.ops[0]->tcw4.valid;
+}
+
 // The grow-only workspace of a batch of B frames padded to Hp x Wp, as a
 // list of (buffer, bytes) handed to need(): ensure_workspace allocates it,
 // lic_codec_workspace_bytes adds it up without allocating.
@@ -761,7 +767,9 @@ int workspace_plan(lic_codec *cd, int B, int Hp, int Wp, F &&need) {
         if (!rc) rc = need(b, n * elem + 256);
     };
     if (!cd->use_patch) f(cd->xin, (int64_t)B * Hp * Wp * 3, 4);   // else unused
-    if (cd->use_patch) f(cd->patches, (int64_t)B * (Hp / 2) * (Wp / 2) * PATCH_K, 4);
+    // the patch rows, or (the tap form of g_a conv0) the frame padded to 4 channels
+    if (cd->use_patch && frame_form(cd)) f(cd->patches, (int64_t)B * Hp * Wp * 4, 4);
+    else if (cd->use_patch) f(cd->patches, (int64_t)B * (Hp / 2) * (Wp / 2) * PATCH_K, 4);
     f(cd->act0, big, 4);
     f(cd->act1, big, 4);
     f(cd->y, (int64_t)B * Hy * Wy * M, 4);
@@ -848,9 +856,9 @@ void analysis(lic_codec *cd, const float *frames, int B, int Hf, int Wf, int Hp,
     int H = Hp, W = Wp;
     const float *in = cd->xin.as<float>();
     int first = 0;
-    if (cd->use_patch && cd->ga0p.ops[0]->tcw4.valid) {
-        // the frame padded once with 4 channels (into the patch buffer, a sixth of whose
-        // size it takes); the persistent FP32 kernel loads each tap of the patch rows by TMA
+    if (cd->use_patch && frame_form(cd)) {
+        // the frame padded once with 4 channels (into the patch buffer); the persistent FP32
+        // kernel loads each tap of the patch rows by TMA
         // algorithmic bytes: the frame read once
         float *f4 = cd->patches.as<float>();
         timed(cd, "frame_pad4", 0, 12.0 * B * Hf * Wf, 1, st,
