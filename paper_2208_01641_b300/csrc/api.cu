@@ -83,8 +83,9 @@ struct lic_codec {
     int device = 0;
     // transforms
     lic::Layer ga[4], gs[4], ha[3], hs[3];
-    // g_a conv0 as a GEMM over packed 5x5 patches (tensor-core path): the
-    // kernel then loads its A operand with TMA instead of gathering it
+    // g_a conv0 as a GEMM over its 5x5 patches (tensor-core path), A loaded by
+    // TMA: tap by tap from the padded 4-channel frame (Cout = 128, the tap
+    // form), else from patch rows packed in HBM
     lic::Layer ga0p;
     bool use_patch = false;
     // while analysis runs ga0p on the persistent FP32 kernel: the padded 4-channel
