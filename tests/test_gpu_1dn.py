@@ -68,3 +68,45 @@ def test_1dn_codec_bitstreams_and_roundtrip(W1):
     ref, inter = O.decode(oc, got)
     assert np.abs(out.cpu().numpy() - ref).max() <= TOL
     c.close()
+
+
+def test_1dn_full_size_720p_sampled(W1):
+    """1DN at the bench's size (2 x 1280x720, padded to 1280x768): g_a conv0's tap
+    form and every persistent layer walk many tiles a CTA here.  Sampled y against
+    the oracle's g_a on a crop whose receptive field lies inside it, sampled x_hat
+    against the oracle's g_s on a window of the decoded symbols, encoder and
+    decoder indices identical, and the decoded symbols equal the encoded ones."""
+    B, H, Wd = 2, 720, 1280
+    c = lic.Codec(1, N, M, W1, norm=lic.NORM_1DN)
+    x = synth.make_frames(B, H, Wd, first=80)
+    xd = torch.from_numpy(x).cuda()
+    Hy, Wy = 48, 80
+    bs = c.encode(xd)
+    y = np.zeros((B, M, Hy, Wy), np.float32)
+    sy_enc = np.zeros((B, M, Hy, Wy), np.int32)
+    idx_enc = np.zeros((B, M, Hy, Wy), np.uint8)
+    c.read_tensor(lic.T_Y, y)
+    c.read_tensor(lic.T_SY, sy_enc)
+    c.read_tensor(lic.T_IDX, idx_enc)
+    out = torch.empty(B, 3, H, Wd, device="cuda")
+    c.decode(bs, out)
+    assert c.sync_status() == lic.OK
+    sy = np.zeros_like(sy_enc)
+    idx = np.zeros_like(idx_enc)
+    xpre = np.zeros((B, 3, 768, 1280), np.float32)
+    c.read_tensor(lic.T_SY, sy)
+    c.read_tensor(lic.T_IDX, idx)
+    c.read_tensor(lic.T_XPRE, xpre)
+    assert np.array_equal(sy, sy_enc)
+    assert np.array_equal(idx, idx_enc)
+    xp = pad(x)
+    for (b, oy, ox) in [(0, 320, 704), (1, 576, 1088)]:
+        ry = O.g_a(W1, xp[b:b + 1, :, oy:oy + 192, ox:ox + 192])[0]
+        gy = y[b, :, oy // 16:oy // 16 + 12, ox // 16:ox // 16 + 12]
+        assert np.abs(gy[:, 4:8, 4:8] - ry[:, 4:8, 4:8]).max() <= TOL
+    yhat = sy.astype(np.float32)
+    for (b, iy, ix) in [(0, 10, 40), (1, 30, 60)]:
+        rx = O.g_s(W1, yhat[b:b + 1, :, iy:iy + 12, ix:ix + 12])[0]
+        gx = xpre[b, :, 16 * iy:16 * iy + 192, 16 * ix:16 * ix + 192]
+        assert np.abs(gx[:, 64:128, 64:128] - rx[:, 64:128, 64:128]).max() <= TOL
+    c.close()
