@@ -371,3 +371,25 @@ def test_full_size_720p_batch8_sampled(codecs, ocodecs, weights):
     for b in (0, 7):
         subs = O.encode_latents(oc, sy_enc[b], idx[b], sz[b])
         assert g_bytes[b] == O.pack_frame(1, N, M, H, W, 768, 1280, oc.R, subs)
+
+
+def test_degenerate_inputs(codecs, ocodecs):
+    """An empty batch is refused before any device work; the smallest and the
+    thinnest frames (almost all replicate padding, a 64 x 64 or 64 x 1280 padded
+    grid with one 4 x 4 latent row) code losslessly, and the decoder's output
+    equals the oracle's decoding of the GPU's own bytes."""
+    c, oc = codecs[(1, lic.CONV_AUTO)], ocodecs[1]
+    with pytest.raises(lic.LicError) as e:
+        c.encode(torch.empty(0, 3, 64, 64, device="cuda"))
+    assert e.value.code == lic.E_INVALID_ARG
+    for (H, Wd) in [(1, 1), (1, 1280), (65, 3)]:
+        x = synth.make_frames(1, H, Wd, first=40)
+        bs = c.encode(dev(x))
+        out = torch.empty(1, 3, H, Wd, device="cuda")
+        c.decode(bs, out)
+        assert c.sync_status() == lic.OK
+        got = bs.to_bytes()
+        assert lic.decoded_shape(got[0])[1:] == (H, Wd)
+        ref, _ = O.decode(oc, got)
+        assert np.abs(out.cpu().numpy() - ref).max() <= TOL, (H, Wd)
+        bs.release()
