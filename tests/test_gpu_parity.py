@@ -393,3 +393,48 @@ def test_degenerate_inputs(codecs, ocodecs):
         ref, _ = O.decode(oc, got)
         assert np.abs(out.cpu().numpy() - ref).max() <= TOL, (H, Wd)
         bs.release()
+
+
+def test_4k_frame_sampled(codecs, ocodecs, weights):
+    """The largest frame size exercised: one 3840x2160 frame (padded to
+    3840x2176; latent grid 136 x 240): lossless symbols, encoder and decoder
+    indices identical, sampled y and x_hat against the oracle as at 720p, and
+    the entropy coder's bytes equal the oracle's coding of the GPU's symbols."""
+    B, H, Wd = 1, 2160, 3840
+    Hp, Wp = O.pad_size(H, Wd)
+    Hy, Wy = Hp // 16, Wp // 16
+    c, oc = codecs[(1, lic.CONV_AUTO)], ocodecs[1]
+    x = synth.make_frames(B, H, Wd, first=50)
+    bs = c.encode(dev(x))
+    y = np.zeros((B, M, Hy, Wy), np.float32)
+    sy_enc = np.zeros((B, M, Hy, Wy), np.int32)
+    idx_enc = np.zeros((B, M, Hy, Wy), np.uint8)
+    sz = np.zeros((B, N, Hy // 4, Wy // 4), np.int32)
+    c.read_tensor(lic.T_Y, y)
+    c.read_tensor(lic.T_SY, sy_enc)
+    c.read_tensor(lic.T_IDX, idx_enc)
+    c.read_tensor(lic.T_SZ, sz)
+    got = bs.to_bytes()
+    out = torch.empty(B, 3, H, Wd, device="cuda")
+    c.decode(bs, out)
+    assert c.sync_status() == lic.OK
+    sy = np.zeros_like(sy_enc)
+    idx = np.zeros_like(idx_enc)
+    xpre = np.zeros((B, 3, Hp, Wp), np.float32)
+    c.read_tensor(lic.T_SY, sy)
+    c.read_tensor(lic.T_IDX, idx)
+    c.read_tensor(lic.T_XPRE, xpre)
+    assert np.array_equal(sy, sy_enc) and np.array_equal(idx, idx_enc)
+    xp = pad(x)
+    for (oy, ox) in [(1984, 3648), (1024, 2048)]:   # the bottom-right corner's padding, an interior
+        ry = O.g_a(weights[1], xp[:, :, oy:oy + 192, ox:ox + 192])[0]
+        gy = y[0, :, oy // 16:oy // 16 + 12, ox // 16:ox // 16 + 12]
+        i1 = 12 if oy + 192 == Hp else 8
+        j1 = 12 if ox + 192 == Wp else 8
+        assert np.abs(gy[:, 4:i1, 4:j1] - ry[:, 4:i1, 4:j1]).max() <= TOL
+    for (iy, ix) in [(120, 220), (60, 100)]:
+        rx = O.g_s(weights[1], sy[:, :, iy:iy + 12, ix:ix + 12].astype(np.float32))[0]
+        gx = xpre[0, :, 16 * iy:16 * iy + 192, 16 * ix:16 * ix + 192]
+        assert np.abs(gx[:, 64:128, 64:128] - rx[:, 64:128, 64:128]).max() <= TOL
+    subs = O.encode_latents(oc, sy_enc[0], idx_enc[0], sz[0])
+    assert got[0] == O.pack_frame(1, N, M, H, Wd, Hp, Wp, oc.R, subs)
