@@ -350,6 +350,13 @@ def main():
                            "ms_per_step": sum(fms) / args.steps,
                            "p99_ms": sorted(fms)[min(len(fms) - 1, int(0.99 * len(fms)))],
                            "decode_status": fstatus, "note": notes[name]}
+            # its rooflines: the dominant launch, the dominant launch of the form's own low-precision
+            # type, and the whole step, from a profiled pass of three steps (launches timed one by one)
+            frep = profile_steps(fcodec, frames, out, stream, flush, 3)
+            forms[name]["roofline"] = roofline(frep, peaks)
+            own = [r for r in frep if r["name"].endswith({"bf16": ":bf16", "fp8": ":e4m3"}.get(name, ":tc"))]
+            forms[name]["roofline_own_type"] = roofline(own, peaks)
+            forms[name]["chain_roofline"] = chain_roofline(frep, peaks, forms[name]["ms_per_step"], steps=3)
             if rank == 0 and not args.no_cpu_baseline:
                 forms[name]["psnr_vs_oracle_db"] = psnr_vs_oracle(fcodec, wts, B)
                 forms[name]["y_maxabs_vs_oracle"] = sampled_errors(fcodec, wts, frames_np, B)
@@ -789,6 +796,25 @@ def format2_form(args, lic, Wt, impl, frames, out, H, W, stream, flush, ws, B, f
                      "whole latent planes as substreams (one 32-state flush per plane); records: resume points "
                      "a decoder may use to split a plane into parallel segments (their bytes counted here)")
     return out_f
+
+
+def profile_steps(codec, frames, out, stream, flush, n):
+    """The library's per-launch report (name, launches, ms, algorithmic flop and
+    bytes) over n encode+decode steps, each launch timed with its own events (the
+    phases of a transposed conv then run one after another), L2 flushed before
+    each step."""
+    import torch
+    sid = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        codec.profile(True)
+        for _ in range(n):
+            flush.zero_()
+            bs = codec.encode(frames, stream=sid)
+            codec.decode(bs, out, stream=sid)
+        codec.sync(sid)
+        rep = codec.profile_report()
+        codec.profile(False)
+    return rep
 
 
 def capture_step(codec, frames, out, stream):
