@@ -748,6 +748,16 @@ def wide_form(args, lic, synth, torch, np, stream, flush, rank):
         r = {"value": B3 * args.steps / (sum(fms) / 1000.0), "unit": "frames/s",
              "ms_per_step": sum(fms) / args.steps, "p99_ms": sorted(fms)[min(len(fms) - 1, int(0.99 * len(fms)))],
              "decode_status": max(status, st), "indices_identical_enc_dec": bool(torch.equal(idx_e, idx_d))}
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        rep3 = profile_steps(c, fr, out, stream, flush, 1)
+        r["roofline"] = roofline(rep3, peaks, steps=1)
+        own = [q for q in rep3 if q["name"].endswith({"bf16": ":bf16", "fp8": ":e4m3"}.get(name, ":tc"))]
+        r["roofline_own_type"] = roofline(own, peaks, steps=1)
+        r["chain_roofline"] = chain_roofline(rep3, peaks, r["ms_per_step"], steps=1)
         if prec != lic.FP32 and rank == 0 and not args.no_cpu_baseline:
             r["psnr_vs_oracle_db"] = psnr_vs_oracle(c, Wt3, B3, M3, Hp3, Wp3)
             r["y_maxabs_vs_oracle"] = sampled_errors(c, Wt3, fr_np, B3, M3, Hp3, Wp3)
@@ -891,9 +901,10 @@ def sampled_errors(codec, Wt, frames_np, B, M=M_CH, Hp=PAD_H, Wp=PAD_W):
     return yerr
 
 
-def roofline(rep, peaks):
+def roofline(rep, peaks, steps=3):
     """Dominant launch name by total time; achieved = algorithmic work per
-    launch / mean launch time; peak from MEASURED_PEAKS.json."""
+    launch / mean launch time; peak from MEASURED_PEAKS.json (rep covers
+    `steps` steps)."""
     if not rep:
         return None
     top = max(rep, key=lambda r: r["ms"])
@@ -929,7 +940,7 @@ def roofline(rep, peaks):
         bound, unit = "hbm", "GB/s"
         note = "measured HBM copy bandwidth"
     out = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-           "traffic": TRAFFIC.get(name), "launch_ms": per_ms, "launches_per_step": top["launches"] / 3,
+           "traffic": TRAFFIC.get(name), "launch_ms": per_ms, "launches_per_step": top["launches"] / steps,
            "note": note, "peak_source": "MEASURED_PEAKS.json" if peaks else "fallback"}
     out.update(extra)
     return out
