@@ -515,6 +515,7 @@ def main():
                                   if graphs else "direct launches")},
             "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
             "enc_fps": B * args.steps / (sum(enc_ms) / 1000), "dec_fps": B * args.steps / (sum(dec_ms) / 1000),
+            "paper_context": PAPER_CONTEXT,
             "bits_per_pixel": 8.0 * statistics.mean(frame_bytes) / (H * W),
             "psnr_vs_oracle_db": psnr if psnr is None or psnr < 1e9 else "inf", "decode_status": status,
             "roofline": roof, "chain_roofline": chain, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -976,6 +977,18 @@ def chain_roofline(rep, peaks, measured_ms, steps, floor_bytes=None):
                     "measured HBM); algorithmic FLOP and bytes as the library counts them; FP32 convs "
                     "against the 3xTF32 ceiling (a third of the TF32 peak)",
             "peak_source": "MEASURED_PEAKS.json" if peaks else "fallback"}
+
+
+# The paper's own figures for this codec and frame size (Table 4: scale hyperprior, N=128 M=192,
+# 1280x720, FP16, encoder and decoder timed separately, per-frame latency), with the hardware it
+# names; context only (another machine, another precision, no combined enc+dec figure)
+PAPER_CONTEXT = {
+    "source": "Table 4 (scale hyperprior, 1280x720)",
+    "hardware": "Dell T630: 2x Xeon E5-2680 v4 + RTX 2080 Ti; TensorRT FP16 transforms, CPU entropy coding",
+    "pipelined_gdn": {"enc_fps": 279, "dec_fps": 157, "enc_latency_ms": 36, "dec_latency_ms": 33},
+    "pipelined_1dn": {"enc_fps": 281, "dec_fps": 161, "enc_latency_ms": 36, "dec_latency_ms": 37},
+    "baseline_pytorch_fp16": {"enc_fps": 11, "dec_fps": 16, "enc_latency_ms": 86, "dec_latency_ms": 61},
+}
 
 
 # DRAM bytes (read + write) per launch of the dominant kernels, from the ncu
