@@ -279,6 +279,24 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
         : "memory");
 }
 
+// 32 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+        "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+        "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])),
+        "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
+        "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])),
+        "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])),
+        "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])),
+        "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -1518,19 +1536,16 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
 #pragma unroll
                 for (int h = 0; h < HALF; ++h) {
                     const uint32_t slot = ysl + KCH * (HALF * half + h);
+                    // hi is y^2 itself (the MMA takes it as trunc(y^2)), lo the exact rest
+                    float hv[32], lv[32];
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        // hi is y^2 itself (the MMA takes it as trunc(y^2)), lo the exact rest
-                        float hv[16], lv[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const float sq = master[32 * h + 16 * q + i] * master[32 * h + 16 * q + i];
-                            hv[i] = sq;
-                            lv[i] = sq - tf32_trunc(sq);
-                        }
-                        tmem_st16(slot + 16 * q, hv);
-                        tmem_st16(slot + COUT + 16 * q, lv);
+                    for (int i = 0; i < 32; ++i) {
+                        const float sq = master[32 * h + i] * master[32 * h + i];
+                        hv[i] = sq;
+                        lv[i] = sq - tf32_trunc(sq);
                     }
+                    tmem_st32(slot, hv);
+                    tmem_st32(slot + COUT, lv);
                 }
                 tmem_st_wait();
                 tc_fence_before();
