@@ -1181,13 +1181,22 @@ __global__ void __launch_bounds__(64 + EPI_THREADS, 1) conv_tc_kernel(const __gr
 //     tile's last fold is on the tensor pipe's critical path);
 //   * split K (ksplit > 1, launches without a fused norm): the work units are
 //     (tile, K slice) pairs; a slice stores its folded partial sums raw and
-//     tcx_splitk_sum_kernel adds the slices, the bias and ReLU.
+//     tcx_splitk_sum_kernel adds the slices, the bias and ReLU;
+//   * resident weights (NB > 0: 1x1 GEMMs of at most four K chunks whose
+//     stored columns lie below NB, i.e. the tap contributions of a transposed
+//     conv to three channels): the first NB rows of B_hi and B_lo are loaded
+//     once per CTA and stay in shared memory (96 KB at NB = 96), so the ring
+//     carries A alone (32 KB a stage) instead of re-streaming 128 KB of
+//     constants a tile; the
+//     products go as three N = NB MMAs (hi x hi into the first half, hi x lo
+//     and lo x hi into the second) so the partial sums keep their layout.
 //   warp 0       TMA producer            warp 1      TMEM allocation, MMA issue
 //   warps 2..7   split A                 warps 8..15 fold, bias / norm, output
 //                                                    (TMEM lanes 32 (warp % 4) ..)
 constexpr int TCX_THREADS = 512, TCX_SPLIT = 192, TCX_EPI = 256;
 
-template <int STAGES, bool TAPS>   // TAPS: MODE_TAPS only (g_a conv0 over the padded 4-channel frame)
+// TAPS: MODE_TAPS only (g_a conv0 over the padded 4-channel frame); NB > 0: weights resident (MODE_FLAT)
+template <int STAGES, bool TAPS, int NB = 0>
 __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                        const __grid_constant__ CUtensorMap tmBh,
                                                                        const __grid_constant__ CUtensorMap tmBl,
@@ -1199,12 +1208,19 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int COUT = 128, HALF = 2;
     constexpr int AREA = A_BYTES;                     // 128 rows x 128 bytes
-    constexpr int STAGE_BYTES = 4 * AREA;             // A (split in place to hi), A lo, B hi, B lo
+    constexpr bool BRES = NB > 0;
+    // a stage: A (split in place to hi), A lo, and unless the weights are resident B hi, B lo
+    constexpr int STAGE_BYTES = (BRES ? 2 : 4) * AREA;
+    constexpr int RES_AREA = NB * KCH * 4;            // one resident weight slice: NB rows x 128 bytes
+    constexpr int RES_CH = 4;                         // K chunks the resident weights hold at most
     constexpr int GCH = COUT / KCH;                   // gamma chunks of the norm GEMM
     constexpr int NGE = GCH / 2;                      // gamma entries: two chunks ([hi | lo] each) per stage
     static_assert(NGE <= STAGES, "the gamma entries fit the ring at once");
     static_assert(COUT * KCH * 4 == AREA, "a weight slice fills one area");
-    uint8_t *otile = smem + STAGES * STAGE_BYTES;     // two output boxes of 32 channels
+    static_assert(NB % 16 == 0 && NB <= COUT, "N = NB is an MMA shape; its slices keep 1024-byte swizzle atoms");
+    // [resident weights: RES_CH x (B hi, B lo)] [ring] [output staging]
+    uint8_t *ring = smem + (BRES ? RES_CH * 2 * RES_AREA : 0);
+    uint8_t *otile = ring + STAGES * STAGE_BYTES;     // two output boxes of 32 channels
     uint64_t *bars = reinterpret_cast<uint64_t *>(otile + 2 * AREA);
     uint64_t *full = bars, *conv = bars + STAGES, *empty = bars + 2 * STAGES;
     uint64_t *pfull = bars + 3 * STAGES, *pempty = pfull + 2, *ebar = pempty + 2, *ready = ebar + 1;
@@ -1214,11 +1230,12 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
     // (a gamma load on full[s], which only the MMA waits for, could let a split warp's parity wait
     // on that stage pass before it)
     uint64_t *gfull = done + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gfull + NGE);
+    uint64_t *bfull = gfull + NGE;   // the resident weights have landed (NB > 0)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bfull + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const bool gdn = p.fuse_gdn == 1 || p.fuse_gdn == 2;   // (never with ksplit > 1)
+    const bool gdn = !BRES && (p.fuse_gdn == 1 || p.fuse_gdn == 2);   // (never with ksplit > 1)
     // work units u = tile * ksplit + slice; slice q covers K chunks [kbegin(q), kbegin(q + 1))
     const int nunits = p.ntiles * p.ksplit;
     auto kbegin = [&](int q) { return (int)((int64_t)q * p.kchunks / p.ksplit); };
@@ -1237,6 +1254,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
         mbar_init(ready, TCX_EPI);
         mbar_init(done, TCX_EPI);
         for (int ge = 0; ge < NGE; ++ge) mbar_init(&gfull[ge], 1);
+        mbar_init(bfull, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -1248,7 +1266,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    auto area = [&](int s, int a) { return smem + s * STAGE_BYTES + a * AREA; };
+    auto area = [&](int s, int a) { return ring + s * STAGE_BYTES + a * AREA; };
     auto fail = [&]() {
         *abort_flag = 1;
         atomicOr(p.status, ST_TIMEOUT);
@@ -1268,12 +1286,21 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            const uint32_t tx_bytes = (p.mode == MODE_IM2COL ? 0 : AREA) + 2 * AREA;
+            const uint32_t tx_bytes = BRES ? AREA : (p.mode == MODE_IM2COL ? 0 : AREA) + 2 * AREA;
             uint32_t v = 0;
             // bit s / ge: parity of the last phase issued on full[s] / gfull[ge]; whether one was
             uint32_t fph = 0, fis = 0, gph = 0, gis = 0;
             int tk = 0;
-            bool ok = true;
+            bool ok = true, bis = false;   // bis: the resident weights' load was issued
+            if (BRES && blockIdx.x < nunits) {
+                // NB rows of every K chunk's B hi and B lo, once: one phase of bfull
+                mbar_expect_tx(bfull, (uint32_t)(p.kchunks * 2 * RES_AREA));
+                for (int kc = 0; kc < p.kchunks; ++kc) {
+                    tma_load_2d(smem + kc * 2 * RES_AREA, &tmBh, bfull, kc * KCH, 0);
+                    tma_load_2d(smem + kc * 2 * RES_AREA + RES_AREA, &tmBl, bfull, kc * KCH, 0);
+                }
+                bis = true;
+            }
             for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++tk) {
                 const int tile = u / p.ksplit, kc0 = kbegin(u % p.ksplit), nk = kbegin(u % p.ksplit + 1) - kc0;
                 int b, i0, j0;
@@ -1309,8 +1336,10 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                                             du & 1, i0 + (du >> 1), b);
                             }
                         }
-                        tma_load_2d(area(s, 2), &tmBh, &full[s], kc * KCH, 0);
-                        tma_load_2d(area(s, 3), &tmBl, &full[s], kc * KCH, 0);
+                        if constexpr (!BRES) {
+                            tma_load_2d(area(s, 2), &tmBh, &full[s], kc * KCH, 0);
+                            tma_load_2d(area(s, 3), &tmBl, &full[s], kc * KCH, 0);
+                        }
                         if (fis >> s & 1) fph ^= 1u << s;
                         fis |= 1u << s;
                     } else {   // gamma entry ge: chunks 2 ge, 2 ge + 1 as [hi | lo] pairs
@@ -1330,6 +1359,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                     if (fis >> s & 1) mbar_wait(&full[s], fph >> s & 1);
                 for (int ge = 0; ge < NGE; ++ge)
                     if (gis >> ge & 1) mbar_wait(&gfull[ge], gph >> ge & 1);
+                if (bis) mbar_wait(bfull, 0);
             }
         }
     } else if (warp == 1) {
@@ -1339,6 +1369,13 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
             uint32_t v = 0, g = 0;   // ring entry, partial-buffer group
             bool ok = true;
             int tk = 0;
+            if (BRES && blockIdx.x < nunits) {   // the resident weights, before the first MMA
+                if (*abort_flag || !mbar_wait(bfull, 0)) {
+                    fail();
+                    ok = false;
+                }
+                tc_fence_after();
+            }
             for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++tk) {
                 const int kc0 = kbegin(u % p.ksplit), kc1 = kbegin(u % p.ksplit + 1);
                 // the previous tile's norm GEMM read its y^2 from the buffer this tile's
@@ -1365,8 +1402,22 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                     }
                     tc_fence_after();
                     const uint32_t dt = tmem + q * 2 * COUT;
-                    const uint32_t ah = smem_u32(area(s, 0)), al = smem_u32(area(s, 1)), bh = smem_u32(area(s, 2));
-                    if constexpr (!TAPS) {
+                    const uint32_t ah = smem_u32(area(s, 0)), al = smem_u32(area(s, 1));
+                    if constexpr (BRES) {
+                        // chunk kc's resident slices; the same products and order as the
+                        // wide form, as N = NB MMAs into the two halves of the partial
+                        const uint32_t wh = smem_u32(smem + kc * 2 * RES_AREA), wl = wh + RES_AREA;
+                        const uint32_t idb = idesc_tf32(BLOCK_M, NB);
+#pragma unroll
+                        for (int kk = 0; kk < KCH / 8; ++kk) {
+                            const uint64_t da = sdesc(ah + kk * 32), dh = sdesc(wh + kk * 32);
+                            const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+                            mma_tf32(dt, da, dh, idb, acc);                             // A hi x B hi
+                            mma_tf32(dt + COUT, da, sdesc(wl + kk * 32), idb, acc);     // A hi x B lo
+                            mma_tf32(dt + COUT, sdesc(al + kk * 32), dh, idb, 1u);      // A lo x B hi
+                        }
+                    } else if constexpr (!TAPS) {
+                        const uint32_t bh = smem_u32(area(s, 2));
 #pragma unroll
                         for (int kk = 0; kk < KCH / 8; ++kk) {
                             const uint64_t db = sdesc(bh + kk * 32);
@@ -1375,6 +1426,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                         }
                     } else {
                         // the last chunk's data is its first K step (tap 24 and a zero one)
+                        const uint32_t bh = smem_u32(area(s, 2));
                         const int ksteps = kc == kc1 - 1 ? 1 : KCH / 8;
                         for (int kk = 0; kk < ksteps; ++kk) {
                             const uint64_t db = sdesc(bh + kk * 32);
@@ -1570,7 +1622,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1) conv_tcx_kernel(const __grid_c
                 mbar_arrive(&pempty[g & 1]);
                 ++g;
             }
-            if (p.out_dt == DT_F32) {
+            if (BRES || p.out_dt == DT_F32) {   // (the resident-weights form is launched for float32 only)
                 // the output in two halves of 64 channels (threads of half 0, then 1)
 #pragma unroll
                 for (int ph = 0; ph < 2; ++ph) {
@@ -2890,6 +2942,25 @@ bool launch(const ConvDesc &d, const TcWeights &w, cudaStream_t st) {
         p.ntiles = (int)grid;
         p.ksplit = ks;
         const unsigned pgrid = std::min<unsigned>(grid * ks, (unsigned)sm_count());
+        // a 1x1 GEMM of at most four K chunks that stores at most 96 columns (the 84 tap
+        // contribution columns of g_s's last transposed conv): its weights' first 96 rows
+        // stay resident in shared memory and the ring carries A alone
+        constexpr int NBR = 96;
+        if (p.mode == MODE_FLAT && ks == 1 && d.fuse_gdn == 0 && p.q_mode == 0 && d.out_dt == DT_F32 &&
+            p.kchunks >= 1 && p.kchunks * KCH == w.Kpad && p.kchunks <= 4 && w.Npad == 128 &&
+            p.ostride - p.ocoff <= NBR) {
+            CUtensorMap rbh, rbl;
+            const uint64_t dims[2] = {(uint64_t)w.Kpad, (uint64_t)w.Npad};
+            const uint64_t strides[1] = {(uint64_t)w.Kpad * 4};
+            const uint32_t box[2] = {KCH, NBR};
+            if (make_map(&rbh, w.hi, 2, dims, strides, box) && make_map(&rbl, w.lo, 2, dims, strides, box)) {
+                const int smem_r = 4 * 2 * NBR * KCH * 4 + STAGES * 2 * A_BYTES + 2 * A_BYTES + 256 + 1024;
+                cudaFuncSetAttribute(conv_tcx_kernel<STAGES, false, NBR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem_r);
+                conv_tcx_kernel<STAGES, false, NBR><<<pgrid, TCX_THREADS, smem_r, st>>>(tmA, rbh, rbl, rbh, rbl, tmO, p);
+                return true;
+            }
+        }
         const int smem = STAGES * 4 * A_BYTES + 2 * A_BYTES + 256 + 1024;
         if (p.mode == MODE_TAPS) {
             cudaFuncSetAttribute(conv_tcx_kernel<STAGES, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
