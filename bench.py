@@ -71,30 +71,134 @@ def dist_env():
 
 # ----------------------------------------------------------------- clocks
 
+class _NvmlCtypes:
+    """The five read-only NVML calls the clock sampler makes, through ctypes on
+    the driver's libnvidia-ml (for hosts without the pynvml package); the
+    constants are NVML's public ones."""
+    NVML_CLOCK_SM = 1
+    nvmlClocksEventReasonSwPowerCap = 0x4
+    nvmlClocksEventReasonHwSlowdown = 0x8
+    nvmlClocksEventReasonSwThermalSlowdown = 0x20
+    nvmlClocksEventReasonHwThermalSlowdown = 0x40
+
+    def __init__(self):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, r):
+        if r != 0:
+            raise RuntimeError(f"NVML error {r}")
+
+    def nvmlInit(self):
+        self._ok(self.lib.nvmlInit_v2())
+
+    def nvmlDeviceGetHandleByUUID(self, uuid):
+        h = self.c.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByUUID(self.c.c_char_p(uuid.encode()), self.c.byref(h)))
+        return h
+
+    def _clock(self, fn, h, kind):
+        v = self.c.c_uint()
+        self._ok(fn(h, self.c.c_int(kind), self.c.byref(v)))
+        return v.value
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo, h, kind)
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo, h, kind)
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.c.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        if fn is None:
+            fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self._ok(fn(h, self.c.byref(v)))
+        return v.value
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    """SM clock and clock-event (throttle) reasons while running, read only.
+
+    NVML (pynvml, else the driver's library through ctypes) polled every 10 ms
+    from a thread, the device found by the UUID the CUDA runtime reports (so the
+    samples are of the GPU the work runs on, whatever CUDA_VISIBLE_DEVICES says);
+    without NVML, nvidia-smi every 50 ms. Nothing is set: only clocks and
+    reasons are queried."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.010
+    # the reasons a run is judged by, with their NVML bit names
+    REASONS = (("hw_slowdown", "HwSlowdown"), ("hw_thermal_slowdown", "HwThermalSlowdown"),
+               ("sw_thermal_slowdown", "SwThermalSlowdown"), ("sw_power_cap", "SwPowerCap"))
 
-    def __init__(self, gpu_index, tag="main"):
+    def __init__(self, gpu_index, tag="main", nvml=None, uuid=None):
         self.gpu = gpu_index
         self.proc = None
+        self.thread = None
+        self.nvml = nvml          # a module with pynvml's interface (tests pass a fake)
+        self.uuid = uuid
+        self.samples = []         # (sm MHz, max sm MHz, reasons bitmask)
+        self.source = None
         self.path = os.path.join(tempfile.gettempdir(),
                                  f"lic_bench_clocks_gpu{gpu_index}_{os.getpid()}_{tag}.csv")
 
+    def _nvml_open(self):
+        nv = self.nvml
+        if nv is None:
+            try:
+                import pynvml as nv
+            except ImportError:
+                nv = _NvmlCtypes()
+            self.nvml = nv
+        nv.nvmlInit()
+        uuid = self.uuid
+        if uuid is None:
+            import torch
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(self.gpu).uuid)
+        h = nv.nvmlDeviceGetHandleByUUID(uuid)
+        return nv, h
+
+    def _poll(self, nv, h):
+        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        smax = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        while True:
+            try:
+                self.samples.append((nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM), smax, get_reasons(h)))
+            except Exception:
+                pass
+            if self.stop.wait(self.PERIOD_S):
+                break
+
     def __enter__(self):
+        import threading
+        try:
+            nv, h = self._nvml_open()
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, args=(nv, h), daemon=True)
+            self.thread.start()
+            self.source = "nvml, 10 ms"
+            return self
+        except Exception:
+            self.thread = None
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            self.source = "nvidia-smi, 50 ms"
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *a):
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -104,10 +208,24 @@ class ClockSampler:
             self.f.close()
 
     def summary(self):
+        if self.thread is not None:
+            nv = self.nvml
+            sm = [float(x[0]) for x in self.samples]
+            smax = float(self.samples[-1][1]) if self.samples else None
+            reasons = set()
+            for _, _, bits in self.samples:
+                for name, nvname in self.REASONS:
+                    bit = getattr(nv, "nvmlClocksEventReason" + nvname, None)
+                    if bit is None:
+                        bit = getattr(nv, "nvmlClocksThrottleReason" + nvname, 0)
+                    if bits & bit:
+                        reasons.add(name)
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                    "samples": len(sm), "reasons": sorted(reasons), "source": self.source}
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        names = [n for n, _ in self.REASONS]
         for line in open(self.path):
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
@@ -121,7 +239,7 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "reasons": sorted(reasons), "source": self.source}
 
 
 # ------------------------------------------------------------ CPU oracle
